@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: forward + adjoint vector spherical harmonic transform throughput.
+
+Workload (the precision form): L = 1023 on the 1024 x 2048 Gauss-Legendre grid, a
+batch of 32 fields, coefficients with complex parts i.i.d. N(0,1)*(l+1)^-1.5 (seed 2),
+tangent components complex64.  One step = AdjVSHT of the batch (coefficients -> grid)
+followed by FwdVSHT of the synthesised fields (grid -> coefficients); the metric is
+fields / (t_adj + t_fwd).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16x3|fp64]
+  python bench.py --impl reference ...     (the CPU oracle, timed on a bounded sample)
+
+Under torchrun (N > 1) every rank runs the same batch on its own GPU (replicas, weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adj VSHT fields/s at L=1023 (split-prec vs FP64), max rel err vs FP64 oracle"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default=None, choices=["f16x3", "fp64"])
+    ap.add_argument("--L", type=int, default=1023)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the Legendre stage (documented in the design doc)
+# ---------------------------------------------------------------------------
+def legendre_rows(L):
+    """(l, mu) pairs per transform, l = mu..L+1, mu = 0..L."""
+    return sum(L + 2 - mu for mu in range(L + 1))
+
+
+def fp64_flops_per_launch(L, batch, precision):
+    """FP64 flops the Legendre kernel must perform per launch.  Recurrence: one
+    multiply (A_l x) and one FMA per (l, mu, folded latitude) = 3 flops.  FP64
+    contraction (FP64 precision only): one complex column needs 2 FMAs = 4 flops per
+    (l, mu, folded latitude); 4B columns per order (2B at mu = 0)."""
+    J = (L + 2) // 2
+    rows = legendre_rows(L)
+    rec = 3.0 * rows * J
+    if precision != "fp64":
+        return rec
+    cols = 4.0 * batch * (rows - (L + 2)) + 2.0 * batch * (L + 2)
+    return rec + 4.0 * cols * J
+
+
+# ---------------------------------------------------------------------------
+def reference_arm(args, rank):
+    """The CPU oracle (separable FP64 form) on a bounded sample: each step computes
+    one field's AdjVSHT + FwdVSHT restricted to every 64th order (1/64 of the
+    orders), i.e. 1/64 of one field; value = sampled fraction / time."""
+    import numpy as np
+    import oracle
+    from paper_1908_00041_gb300 import synthetic
+    if rank != 0:
+        return None
+    L = args.L
+    x, W, theta, phi = oracle.grid(L)
+    a, b = synthetic.coefficients(L, 1, seed=2, decay=1.5)
+    mstep = 64
+    starts = list(range(mstep))
+    nm = 2 * L + 1
+
+    def step(i):
+        s0 = starts[i % mstep]
+        tt, tp = oracle.adj_sep_orders(L, x, a[0], b[0], 2 * (L + 1), s0, mstep)
+        tt = tt.astype(np.complex64).astype(np.complex128)
+        tp = tp.astype(np.complex64).astype(np.complex128)
+        oracle.fwd_sep_orders(L, x, W, tt, tp, s0, mstep)
+        return len(range(s0, nm, mstep)) / nm
+
+    steps = args.steps or 5
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    frac = 0.0
+    for i in range(steps):
+        frac += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    val = frac / dt
+    cores = oracle.num_threads()
+    sample = ("one field, every 64th order of the L=1023 adjoint+forward (separable FP64 "
+              "oracle, exact per-ring DFT), %d steps" % steps)
+    return {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "fields/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "L=1023 GL 1024x2048, coefficients N(0,1)(l+1)^-1.5, seed 2 "
+                               "(bounded sample of the batch-32 precision form)",
+                   "L": L, "batch": 1, "sample_orders_step": mstep},
+        "cpu_baseline": {"value": val, "unit": "fields/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline(args):
+    """Oracle O3 on the host cores, one field, every 8th order (1/8 of the work)."""
+    import numpy as np
+    import oracle
+    from paper_1908_00041_gb300 import synthetic
+    L = args.L
+    x, W, theta, phi = oracle.grid(L)
+    a, b = synthetic.coefficients(L, 1, seed=2, decay=1.5)
+    mstep = 8
+    nm = 2 * L + 1
+    t0 = time.perf_counter()
+    tt, tp = oracle.adj_sep_orders(L, x, a[0], b[0], 2 * (L + 1), 0, mstep)
+    oracle.fwd_sep_orders(L, x, W, tt, tp, 0, mstep)
+    dt = time.perf_counter() - t0
+    frac = len(range(0, nm, mstep)) / nm
+    return {"value": frac / dt, "unit": "fields/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one field of the L=1023 workload, adjoint+forward over every 8th order "
+                      "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (frac, dt)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        rec = reference_arm(args, rank)
+        if rec is not None:
+            print(json.dumps(rec), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    api.lib(build_if_missing=True)
+    prec_name = args.precision
+    if prec_name is None:
+        prec_name = "f16x3"
+        try:
+            p = api.Plan(16, 1, api.FAVEST_F16X3, api.FAVEST_IO_C64)
+            p.close()
+        except api.FavestError:
+            prec_name = "fp64"
+    prec = api.FAVEST_F16X3 if prec_name == "f16x3" else api.FAVEST_FP64
+    L, B = args.L, args.batch
+    steps = args.steps or (200 if prec_name == "f16x3" else 10)
+
+    plan = api.Plan(L, B, prec, api.FAVEST_IO_C64)
+    a_h, b_h = synthetic.coefficients(L, B, seed=2, decay=1.5)
+    a = torch.as_tensor(a_h).to(torch.complex64).cuda()
+    b = torch.as_tensor(b_h).to(torch.complex64).cuda()
+    tt = torch.empty(plan.field_shape(), dtype=torch.complex64, device="cuda")
+    tp = torch.empty_like(tt)
+    a2 = torch.empty_like(a)
+    b2 = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.adj(a, b, tt, tp, stream=stream)
+        plan.fwd(tt, tp, a2, b2, stream=stream)
+
+    args.warmup = max(args.warmup, 3)      # at least three untimed warm-up steps
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    plan.profile(True)
+    plan.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = plan.profile_read()
+    plan.profile(False)
+    assert plan.status() == 0
+    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms * 1e-3)
+    launches = steps * (plan.launches_per_call(0) + plan.launches_per_call(1))
+
+    # roofline of the dominant kernel (longest total time in the timed region)
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    top_name, (top_ms, top_n) = top
+    fp64_peak, fp32_peak = api.favest_probe_peaks()
+    roofline = None
+    if top_name.startswith("legendre"):
+        flops = fp64_flops_per_launch(L, B, prec_name)
+        achieved = flops / (top_ms / top_n * 1e-3) / 1e12
+        roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64",
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None,
+                    "peak_source": "FP64 FMA throughput measured live by favest_probe_peaks",
+                    "ms_per_launch": top_ms / top_n,
+                    "algorithmic_flops_per_launch": flops}
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                   "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+
+    # end-to-end through the public API with host buffers (pinned), per step:
+    # H2D of the coefficients, adjoint + forward, D2H of the recovered coefficients
+    e2e = None
+    if not args.no_e2e:
+        ha = torch.as_tensor(a_h).to(torch.complex64).pin_memory()
+        hb = torch.as_tensor(b_h).to(torch.complex64).pin_memory()
+        oa = torch.empty_like(ha).pin_memory()
+        ob = torch.empty_like(hb).pin_memory()
+        da = torch.empty_like(a)
+        db = torch.empty_like(b)
+        ke = max(2, min(steps, 20))
+
+        def e2e_step():
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            plan.adj(da, db, tt, tp, stream=stream)
+            plan.fwd(tt, tp, a2, b2, stream=stream)
+            oa.copy_(a2, non_blocking=True)
+            ob.copy_(b2, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ke
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        nbytes = ha.numel() * 8 * 2
+        e2e = {"value": world * B / dt, "unit": "fields/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": ke}
+
+    # accuracy (outside the timed region): recovered vs drawn coefficients, and the
+    # split form against the FP64 path on the same complex64 field
+    errors = None
+    if not args.no_check and rank == 0:
+        ra = a2.cpu().numpy().astype(np.complex128)
+        rb = b2.cpu().numpy().astype(np.complex128)
+
+        def nerr(g, r):
+            return float(np.max(np.max(np.abs(g - r), axis=-1) / np.max(np.abs(r), axis=-1)))
+
+        def rerr(g, r):
+            return float(np.linalg.norm(g - r) / np.linalg.norm(r))
+        errors = {"roundtrip_max_rel": max(nerr(ra, a_h), nerr(rb, b_h)),
+                  "roundtrip_rms_rel": max(rerr(ra, a_h), rerr(rb, b_h))}
+        if prec_name != "fp64":
+            p64 = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_C64)
+            fa, fb = p64.fwd(tt, tp)
+            torch.cuda.synchronize()
+            fa = fa.cpu().numpy().astype(np.complex128)
+            fb = fb.cpu().numpy().astype(np.complex128)
+            errors["fwd_vs_fp64_max_rel"] = max(nerr(ra, fa), nerr(rb, fb))
+            errors["fwd_vs_fp64_rms_rel"] = max(rerr(ra, fa), rerr(rb, fb))
+            p64.close()
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        ws = plan.workspace_bytes()
+        rec = {
+            "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x3" if prec_name == "f16x3" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "precision form: L=1023, Gauss-Legendre grid 1024x2048, batch %d "
+                                   "fields, coefficients N(0,1)(l+1)^-1.5 seed 2, complex64 tangent "
+                                   "components; step = AdjVSHT then FwdVSHT" % B,
+                       "L": L, "batch": B, "precision": prec_name, "io": "complex64",
+                       "l2": "inputs larger than L2 (%.2f GB per step vs 129 MB L2)"
+                             % ((a.numel() * 16 + tt.numel() * 16) / 1e9),
+                       "parallelism": "replicas x%d" % world, "workspace_bytes": ws},
+            "roofline": roofline, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "errors": errors, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
+        }
+        print(json.dumps(rec), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

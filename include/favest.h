@@ -1,0 +1,172 @@
+/*
+ * favest.h -- C ABI of the GB300 (sm_103a) vector spherical harmonic transform
+ * library: forward and adjoint transforms (FwdVSHT / AdjVSHT) of tangent fields on
+ * a Gauss-Legendre tensor grid, after Le Gia, Li and Wang, "FaVeST -- Fast Vector
+ * Spherical Harmonic Transforms" (arXiv 1908.00041).
+ *
+ * Definitions (paper Sec. 3 and Sec. 4):
+ *   Y^div_lm  = grad* Y_lm / sqrt(l(l+1))          (B-family of eqs. Blm1, vsh)
+ *   Y^curl_lm = x cross grad* Y_lm / sqrt(l(l+1))  (D-family of eqs. Blm2, vsh)
+ *   FwdVSHT (Def. FwdVSHT, eq. fwdvsht2):
+ *       a_lm = sum_k w_k Y^div_lm(x_k)^* T_k,   b_lm = sum_k w_k Y^curl_lm(x_k)^* T_k
+ *   AdjVSHT (Def. AdjVSHT, eq. SLvec):
+ *       S_L(a, b; x) = sum_{l=1}^{L} sum_{m=-l}^{l} a_lm Y^div_lm(x) + b_lm Y^curl_lm(x)
+ * where the family names follow the paper's equations literally: Y^div (the paper's
+ * "divergence-free" family) is the surface gradient family and Y^curl the surface
+ * curl family.  Y_lm uses the Condon-Shortley phase and Y_{l,-m} = (-1)^m conj(Y_lm).
+ *
+ * Grid (Sec. 5.1, Gauss-Legendre tensor product rule): nlat = L+1 latitudes with
+ * nodes x_j = cos(theta_j) in descending order (theta ascending) and latitude weights
+ * W_j (sum 2); nphi = 2(L+1) longitudes phi_k = 2 pi k / nphi.  The quadrature weight
+ * of point (j, k) is W_j * 2 pi / nphi.  This rule integrates every product of two
+ * degree-L vector harmonics exactly, so favest_fwd(favest_adj(a, b)) == (a, b).
+ *
+ * Data layouts (all device memory unless stated):
+ *   tangent field, per component (T_theta and T_phi are separate planes):
+ *       [batch][nlat][nphi] complex, row-major; T = T_theta e_theta + T_phi e_phi
+ *   coefficients a, b: [batch][L^2 + 2L] complex, l-major: index l^2 + l + m - 1
+ *       for l = 1..L, m = -l..l  (paper Sec. 4.4, FaVeST_fwd output order).
+ *   complex = interleaved (re, im); element type set by the plan's io type:
+ *       FAVEST_IO_C128 = double, FAVEST_IO_C64 = float.
+ *
+ * Ownership: the caller owns every data buffer and stream.  A plan owns its constant
+ * tables and its device workspace; both are freed by favest_plan_destroy.
+ *
+ * Errors: every call returns a status code and never aborts the process.  Argument
+ * errors are detected on the host before anything is launched.  Transform calls are
+ * asynchronous on the given stream (a cudaStream_t passed as void*, NULL = legacy
+ * default stream); a device-side failure is recorded in the plan's status word and
+ * reported by favest_status.  Calls on one plan must not overlap in time (the plan's
+ * workspace is shared by its calls).
+ */
+#ifndef FAVEST_H
+#define FAVEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct favest_plan_s *favest_plan;
+
+enum favest_status_code {
+    FAVEST_OK = 0,
+    FAVEST_EINVAL = -1,        /* bad argument (size, pointer, alignment, grid)   */
+    FAVEST_ENOMEM = -2,        /* device or host allocation failed                */
+    FAVEST_ECUDA = -3,         /* a CUDA runtime call failed                      */
+    FAVEST_EUNSUPPORTED = -4,  /* valid request this build or device cannot serve */
+    FAVEST_ETIMEOUT = -5,      /* a bounded device-side wait gave up              */
+    FAVEST_EDEVICE = -6        /* a kernel recorded an internal error             */
+};
+
+/* Arithmetic of the Legendre contraction.  The recurrence, its underflow scaling,
+ * the normalisation constants and the quadrature weights are FP64 in every mode. */
+enum favest_precision {
+    FAVEST_FP64 = 0,   /* FP64 everywhere (FFT, recurrence, contraction)                 */
+    FAVEST_F16X3 = 1   /* FP32 FFT; FP64 recurrence; contraction on tcgen05 tensor cores
+                          with FP16 hi/lo splits of both operands (3 products) and FP32
+                          accumulation over short K blocks, summed in FP32 with error
+                          compensation                                                  */
+};
+
+enum favest_io_type {
+    FAVEST_IO_C128 = 0,  /* complex double */
+    FAVEST_IO_C64 = 1    /* complex float  */
+};
+
+/*
+ * Gauss-Legendre rule on [-1, 1] (host).  x[nlat] receives the nodes in descending
+ * order, w[nlat] the weights (sum 2).  Returns FAVEST_EINVAL if nlat < 1 or a
+ * pointer is NULL.
+ */
+int favest_gl_grid(int nlat, double *x, double *w);
+
+/*
+ * Create a plan for degree L (1 <= L <= 4095) and a batch of `batch` fields
+ * (1 <= batch <= 4096) on the current CUDA device.
+ *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
+ *       and latitude weights; NULL selects the built-in Gauss-Legendre rule.  When
+ *       given, the nodes must lie strictly inside (-1, 1) and both arrays must be
+ *       symmetric about the equator (x_{n-1-j} = -x_j, w_{n-1-j} = w_j to 1e-14);
+ *       otherwise FAVEST_EINVAL.
+ *   precision: enum favest_precision; io_type: enum favest_io_type.
+ * Allocates the plan's constant tables and workspace on the device (FAVEST_ENOMEM on
+ * failure).  *out receives the plan (NULL on failure).
+ */
+int favest_plan_create(int L, int batch, int precision, int io_type,
+                       const double *cos_theta, const double *w_lat, favest_plan *out);
+
+/*
+ * FwdVSHT (Def. FwdVSHT, eq. fwdvsht2) of `batch` fields.
+ *   Tth, Tph: device, [batch][nlat][nphi] complex (plan io type), read only.
+ *   a, b:     device, [batch][L^2+2L] complex (plan io type), written.
+ * Pointers must be aligned to the complex element size.  Asynchronous on `stream`.
+ */
+int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b,
+               void *stream);
+
+/*
+ * AdjVSHT (Def. AdjVSHT, eq. SLvec) of `batch` coefficient sets, evaluated on the
+ * plan's grid.
+ *   a, b:     device, [batch][L^2+2L] complex, read only.
+ *   Tth, Tph: device, [batch][nlat][nphi] complex, written (the Nyquist longitude
+ *             bin m = L+1 carries no coefficient and is zero).
+ */
+int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph,
+               void *stream);
+
+/*
+ * Weighting of the forward transform.  flag = 0 (default): the quadrature weights of
+ * eq. fwdvsht2.  flag = 1: unit weights, i.e. favest_fwd computes A^H T, the exact
+ * adjoint of favest_adj (used by reverse-mode differentiation of AdjVSHT).
+ */
+int favest_set_weights_unit(favest_plan plan, int flag);
+
+/* Plan properties (host). */
+int favest_plan_L(favest_plan plan);
+int favest_plan_batch(favest_plan plan);
+int favest_plan_precision(favest_plan plan);
+size_t favest_plan_workspace_bytes(favest_plan plan);
+
+/*
+ * Synchronise `stream` and return the plan's device status word (FAVEST_OK, or the
+ * first device-side error recorded since the last call); clears the word.
+ */
+int favest_status(favest_plan plan, void *stream);
+
+/* Release the plan and everything it owns.  NULL is ignored. */
+void favest_plan_destroy(favest_plan plan);
+
+/* Static description of a status code. */
+const char *favest_strerror(int status);
+
+/* Number of kernels each transform call launches (for launch accounting). */
+int favest_launches_per_call(favest_plan plan, int adjoint);
+
+/*
+ * Per-kernel timing (a profiling aid).  While enabled (enable = 1), every transform
+ * call records a CUDA event pair around each kernel it launches, on the call's
+ * stream.  favest_profile_read synchronises those events and returns, for up to
+ * max_kernels distinct kernels, the name (NUL-terminated, at most 31 characters, in
+ * names[k*32]), the accumulated milliseconds ms[k] and the launch count launches[k];
+ * it then clears the records.  Returns the number of kernels written (>= 0) or a
+ * negative status.  Leave timing disabled while capturing a CUDA graph.
+ */
+int favest_profile_enable(favest_plan plan, int enable);
+int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *ms,
+                        long long *launches);
+
+/*
+ * Measure the current device's FP64 and FP32 fused multiply-add throughput
+ * (TFLOP/s, an FMA counted as 2 flops) with short register-resident FMA streams,
+ * ~20 ms.  Used as the roofline denominator of the FP64-pipe-bound kernels.
+ */
+int favest_probe_peaks(double *fp64_tflops, double *fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAVEST_H */

@@ -65,6 +65,8 @@ def lib():
             L.orc_adj_literal_grid_points.argtypes = [i, i, i, dp, dp, dp, i, ip, ip, dp, dp, dp]
             L.orc_fwd_sep.argtypes = [i, i, i, dp, dp, dp, dp, dp, dp]
             L.orc_adj_sep.argtypes = [i, i, i, dp, dp, dp, dp, dp]
+            L.orc_fwd_sep_orders.argtypes = [i, i, i, dp, dp, dp, dp, dp, dp, i, i]
+            L.orc_adj_sep_orders.argtypes = [i, i, i, dp, dp, dp, dp, dp, i, i]
             L.orc_num_threads.restype = i
             L.orc_set_num_threads.argtypes = [i]
             _lib = L
@@ -217,6 +219,32 @@ def adj_sep(L, x, a, b, nphi):
     tp = np.empty((nlat, nphi), dtype=np.complex128)
     lib().orc_adj_sep(L, nlat, nphi, _d(x), _d(a.view(np.float64)), _d(b.view(np.float64)),
                       _d(tt.view(np.float64)), _d(tp.view(np.float64)))
+    return tt, tp
+
+
+def fwd_sep_orders(L, x, W, Tth, Tph, mstart, mstep):
+    """O3 forward restricted to orders m = mstart-L, mstart-L+mstep, ... (others left 0)."""
+    Tth, Tph = _c128(Tth), _c128(Tph)
+    nlat, nphi = Tth.shape
+    x, W = _f64(x), _f64(W)
+    K = ncoef(L)
+    a = np.zeros(K, dtype=np.complex128)
+    b = np.zeros(K, dtype=np.complex128)
+    lib().orc_fwd_sep_orders(L, nlat, nphi, _d(x), _d(W), _d(Tth.view(np.float64)),
+                             _d(Tph.view(np.float64)), _d(a.view(np.float64)),
+                             _d(b.view(np.float64)), int(mstart), int(mstep))
+    return a, b
+
+
+def adj_sep_orders(L, x, a, b, nphi, mstart, mstep):
+    """O3 adjoint summing only the orders m = mstart-L, mstart-L+mstep, ..."""
+    a, b = _c128(a), _c128(b)
+    x = _f64(x)
+    nlat = len(x)
+    tt = np.empty((nlat, nphi), dtype=np.complex128)
+    tp = np.empty((nlat, nphi), dtype=np.complex128)
+    lib().orc_adj_sep_orders(L, nlat, nphi, _d(x), _d(a.view(np.float64)), _d(b.view(np.float64)),
+                             _d(tt.view(np.float64)), _d(tp.view(np.float64)), int(mstart), int(mstep))
     return tt, tp
 
 

@@ -483,14 +483,15 @@ static void lam_dlam(int L, int m, double ct, double st, double *lam, double *dl
  * Legendre sums.  Tth, Tph: nlat x nphi complex.  a, b: K complex.
  * Requires nphi >= 2L+1 (all |m| <= L resolved) and nodes strictly inside (0, pi).
  */
-void orc_fwd_sep(int L, int nlat, int nphi, const double *x, const double *W,
-                 const double *Tthc, const double *Tphc, double *aout, double *bout)
+void orc_fwd_sep_orders(int L, int nlat, int nphi, const double *x, const double *W,
+                        const double *Tthc, const double *Tphc, double *aout, double *bout,
+                        int mstart, int mstep)
 {
     const cplx *Tth = (const cplx *)Tthc, *Tph = (const cplx *)Tphc;
     cplx *a = (cplx *)aout, *b = (cplx *)bout;
     const double dphi = 2.0 * M_PI / nphi;
     #pragma omp parallel for schedule(dynamic)
-    for (int mi = 0; mi < 2 * L + 1; ++mi) {
+    for (int mi = mstart; mi < 2 * L + 1; mi += mstep) {
         int m = mi - L;
         double *lam = malloc(sizeof(double) * (L + 2)), *dlam = malloc(sizeof(double) * (L + 2));
         cplx *Fth = malloc(sizeof(cplx) * nlat), *Fph = malloc(sizeof(cplx) * nlat);
@@ -524,17 +525,25 @@ void orc_fwd_sep(int L, int nlat, int nphi, const double *x, const double *W,
     }
 }
 
-/* Full AdjVSHT on the grid, O(L^3): Legendre sums per (ring, m), then an exact
- * direct inverse DFT per ring.  Output Tth, Tph: nlat x nphi complex. */
-void orc_adj_sep(int L, int nlat, int nphi, const double *x, const double *ain,
-                 const double *bin, double *Tthout, double *Tphout)
+void orc_fwd_sep(int L, int nlat, int nphi, const double *x, const double *W,
+                 const double *Tthc, const double *Tphc, double *aout, double *bout)
+{
+    orc_fwd_sep_orders(L, nlat, nphi, x, W, Tthc, Tphc, aout, bout, 0, 1);
+}
+
+/* AdjVSHT on the grid restricted to the orders m = mstart - L, mstart - L + mstep, ...
+ * (all orders for mstart = 0, mstep = 1), O(L^3): Legendre sums per (ring, m), then
+ * an exact direct inverse DFT per ring over those orders.  Output Tth, Tph: nlat x
+ * nphi complex. */
+void orc_adj_sep_orders(int L, int nlat, int nphi, const double *x, const double *ain,
+                        const double *bin, double *Tthout, double *Tphout, int mstart, int mstep)
 {
     const cplx *a = (const cplx *)ain, *b = (const cplx *)bin;
     cplx *Tth = (cplx *)Tthout, *Tph = (cplx *)Tphout;
     const int nm = 2 * L + 1;
-    cplx *Gth = malloc(sizeof(cplx) * (size_t)nlat * nm), *Gph = malloc(sizeof(cplx) * (size_t)nlat * nm);
+    cplx *Gth = calloc((size_t)nlat * nm, sizeof(cplx)), *Gph = calloc((size_t)nlat * nm, sizeof(cplx));
     #pragma omp parallel for schedule(dynamic)
-    for (int mi = 0; mi < nm; ++mi) {
+    for (int mi = mstart; mi < nm; mi += mstep) {
         int m = mi - L;
         double *lam = malloc(sizeof(double) * (L + 2)), *dlam = malloc(sizeof(double) * (L + 2));
         int l0 = abs(m) > 1 ? abs(m) : 1;
@@ -558,7 +567,7 @@ void orc_adj_sep(int L, int nlat, int nphi, const double *x, const double *ain,
     for (int j = 0; j < nlat; ++j) {
         for (int k = 0; k < nphi; ++k) {
             cplx s1 = 0.0, s2 = 0.0;
-            for (int mi = 0; mi < nm; ++mi) {
+            for (int mi = mstart; mi < nm; mi += mstep) {
                 cplx e = unit_root((long long)(mi - L) * k, nphi);
                 s1 += Gth[(size_t)j * nm + mi] * e;
                 s2 += Gph[(size_t)j * nm + mi] * e;
@@ -568,6 +577,12 @@ void orc_adj_sep(int L, int nlat, int nphi, const double *x, const double *ain,
         }
     }
     free(Gth); free(Gph);
+}
+
+void orc_adj_sep(int L, int nlat, int nphi, const double *x, const double *ain,
+                 const double *bin, double *Tthout, double *Tphout)
+{
+    orc_adj_sep_orders(L, nlat, nphi, x, ain, bin, Tthout, Tphout, 0, 1);
 }
 
 int orc_num_threads(void)

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of the favest C ABI (include/favest.h).
+
+Every function here only marshals arguments (tensor pointers, sizes, streams) and
+checks the returned status; all arithmetic runs in the CUDA library.  If the
+library cannot be loaded the first call raises ``FavestError`` -- there is no
+fallback path.
+"""
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FAVEST_OK = 0
+FAVEST_EINVAL = -1
+FAVEST_ENOMEM = -2
+FAVEST_ECUDA = -3
+FAVEST_EUNSUPPORTED = -4
+FAVEST_ETIMEOUT = -5
+FAVEST_EDEVICE = -6
+
+FAVEST_FP64 = 0
+FAVEST_F16X3 = 1
+FAVEST_IO_C128 = 0
+FAVEST_IO_C64 = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FavestError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = "favest error %d" % status
+        if _lib is not None:
+            msg += " (%s)" % _lib.favest_strerror(status).decode()
+        super().__init__(msg + (": " + what if what else ""))
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=False):
+    """Load libfavest.so (built in-tree by paper_1908_00041_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise FavestError(FAVEST_EUNSUPPORTED,
+                                      "CUDA library %s is not built (run __graft_entry__.build())" % path)
+                _build.build()
+            L = ctypes.CDLL(path)
+            vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+            L.favest_gl_grid.argtypes = [i, d, d]
+            L.favest_plan_create.argtypes = [i, i, i, i, d, d, ctypes.POINTER(vp)]
+            L.favest_fwd.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.favest_adj.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.favest_set_weights_unit.argtypes = [vp, i]
+            L.favest_plan_L.argtypes = [vp]
+            L.favest_plan_batch.argtypes = [vp]
+            L.favest_plan_precision.argtypes = [vp]
+            L.favest_plan_workspace_bytes.argtypes = [vp]
+            L.favest_plan_workspace_bytes.restype = ctypes.c_size_t
+            L.favest_status.argtypes = [vp, vp]
+            L.favest_plan_destroy.argtypes = [vp]
+            L.favest_plan_destroy.restype = None
+            L.favest_strerror.argtypes = [i]
+            L.favest_strerror.restype = ctypes.c_char_p
+            L.favest_launches_per_call.argtypes = [vp, i]
+            L.favest_probe_peaks.argtypes = [d, d]
+            L.favest_profile_enable.argtypes = [vp, i]
+            L.favest_profile_read.argtypes = [vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_longlong)]
+            _lib = L
+    return _lib
+
+
+def header_symbols():
+    """Function names declared in include/favest.h."""
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "include", "favest.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(favest_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def _check(status, what=""):
+    if status != FAVEST_OK:
+        raise FavestError(status, what)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def favest_gl_grid(nlat):
+    """Gauss-Legendre nodes (descending) and weights from the library (host)."""
+    x = np.empty(nlat)
+    w = np.empty(nlat)
+    _check(lib().favest_gl_grid(nlat, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "favest_gl_grid")
+    return x, w
+
+
+def favest_plan_create(L, batch, precision=FAVEST_FP64, io_type=FAVEST_IO_C128,
+                       cos_theta=None, w_lat=None):
+    """Returns an opaque plan handle (int)."""
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    if cos_theta is not None:
+        cos_theta = np.ascontiguousarray(cos_theta, dtype=np.float64)
+        w_lat = np.ascontiguousarray(w_lat, dtype=np.float64)
+        xp, wp = cos_theta.ctypes.data_as(dp), w_lat.ctypes.data_as(dp)
+    else:
+        xp = wp = None
+    _check(lib().favest_plan_create(int(L), int(batch), int(precision), int(io_type), xp, wp,
+                                    ctypes.byref(h)), "favest_plan_create")
+    return h.value
+
+
+def favest_fwd(plan, Tth, Tph, a, b, stream=None):
+    _check(lib().favest_fwd(ctypes.c_void_p(plan), _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b),
+                            _stream(stream)), "favest_fwd")
+
+
+def favest_adj(plan, a, b, Tth, Tph, stream=None):
+    _check(lib().favest_adj(ctypes.c_void_p(plan), _ptr(a), _ptr(b), _ptr(Tth), _ptr(Tph),
+                            _stream(stream)), "favest_adj")
+
+
+def favest_set_weights_unit(plan, flag):
+    _check(lib().favest_set_weights_unit(ctypes.c_void_p(plan), int(flag)), "favest_set_weights_unit")
+
+
+def favest_status(plan, stream=None):
+    return lib().favest_status(ctypes.c_void_p(plan), _stream(stream))
+
+
+def favest_plan_destroy(plan):
+    lib().favest_plan_destroy(ctypes.c_void_p(plan))
+
+
+def favest_plan_workspace_bytes(plan):
+    return lib().favest_plan_workspace_bytes(ctypes.c_void_p(plan))
+
+
+def favest_launches_per_call(plan, adjoint=0):
+    return lib().favest_launches_per_call(ctypes.c_void_p(plan), int(adjoint))
+
+
+def favest_profile_enable(plan, enable):
+    _check(lib().favest_profile_enable(ctypes.c_void_p(plan), int(enable)), "favest_profile_enable")
+
+
+def favest_profile_read(plan, max_kernels=16):
+    """{kernel name: (milliseconds, launches)} accumulated since the last read."""
+    names = ctypes.create_string_buffer(32 * max_kernels)
+    ms = (ctypes.c_double * max_kernels)()
+    cnt = (ctypes.c_longlong * max_kernels)()
+    k = lib().favest_profile_read(ctypes.c_void_p(plan), max_kernels, names, ms, cnt)
+    if k < 0:
+        raise FavestError(k, "favest_profile_read")
+    raw = names.raw
+    out = {}
+    for i in range(k):
+        nm = raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+        out[nm] = (ms[i], cnt[i])
+    return out
+
+
+def favest_probe_peaks():
+    """(fp64_tflops, fp32_tflops) measured on the current device."""
+    f64 = ctypes.c_double()
+    f32 = ctypes.c_double()
+    _check(lib().favest_probe_peaks(ctypes.byref(f64), ctypes.byref(f32)), "favest_probe_peaks")
+    return f64.value, f32.value
+
+
+def favest_strerror(status):
+    return lib().favest_strerror(int(status)).decode()
+
+
+class Plan:
+    """Owning wrapper around a favest plan with tensor allocation helpers."""
+
+    def __init__(self, L, batch=1, precision=FAVEST_FP64, io_type=FAVEST_IO_C128,
+                 cos_theta=None, w_lat=None):
+        import torch
+        self.L, self.batch, self.precision, self.io_type = int(L), int(batch), precision, io_type
+        self.nlat, self.nphi = L + 1, 2 * (L + 1)
+        self.K = L * L + 2 * L
+        self.cdtype = torch.complex128 if io_type == FAVEST_IO_C128 else torch.complex64
+        self.handle = favest_plan_create(L, batch, precision, io_type, cos_theta, w_lat)
+        self._unit = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            favest_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t, shape, name):
+        import torch
+        if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError("%s: expected contiguous CUDA %s tensor of shape %s, got %s %s %s"
+                             % (name, self.cdtype, shape, t.device, t.dtype, tuple(t.shape)))
+
+    def field_shape(self):
+        return (self.batch, self.nlat, self.nphi)
+
+    def coef_shape(self):
+        return (self.batch, self.K)
+
+    def set_unit_weights(self, flag):
+        if flag != self._unit:
+            favest_set_weights_unit(self.handle, flag)
+            self._unit = flag
+
+    def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False):
+        import torch
+        self._check_tensor(Tth, self.field_shape(), "Tth")
+        self._check_tensor(Tph, self.field_shape(), "Tph")
+        if a is None:
+            a = torch.empty(self.coef_shape(), dtype=self.cdtype, device=Tth.device)
+        if b is None:
+            b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=Tth.device)
+        self._check_tensor(a, self.coef_shape(), "a")
+        self._check_tensor(b, self.coef_shape(), "b")
+        self.set_unit_weights(1 if unit_weights else 0)
+        favest_fwd(self.handle, Tth, Tph, a, b, stream)
+        return a, b
+
+    def adj(self, a, b, Tth=None, Tph=None, stream=None):
+        import torch
+        self._check_tensor(a, self.coef_shape(), "a")
+        self._check_tensor(b, self.coef_shape(), "b")
+        if Tth is None:
+            Tth = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device)
+        if Tph is None:
+            Tph = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device)
+        self._check_tensor(Tth, self.field_shape(), "Tth")
+        self._check_tensor(Tph, self.field_shape(), "Tph")
+        favest_adj(self.handle, a, b, Tth, Tph, stream)
+        return Tth, Tph
+
+    def status(self, stream=None):
+        return favest_status(self.handle, stream)
+
+    def workspace_bytes(self):
+        return favest_plan_workspace_bytes(self.handle)
+
+    def launches_per_call(self, adjoint=0):
+        return favest_launches_per_call(self.handle, adjoint)
+
+    def profile(self, enable=True):
+        favest_profile_enable(self.handle, 1 if enable else 0)
+
+    def profile_read(self):
+        return favest_profile_read(self.handle)

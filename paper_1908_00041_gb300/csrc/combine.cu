@@ -1,0 +1,130 @@
+// O(L^2) coefficient-side stages.
+//   combine   (forward): scalar sums Q_theta, Q_phi (degrees |m|..L+1) -> a_lm, b_lm
+//   uncombine (adjoint): a_lm, b_lm -> scaled scalar coefficients g_theta, g_phi
+// Both use the per-(l, mu) coefficients P, M, R (with the recurrence scaling kappa
+// folded in), which make uncombine the exact transpose of combine:
+//   a = P_l Qt(l+1) - M_l Qt(l-1) - i m R_l Qp(l)
+//   b = i m R_l Qt(l) + P_l Qp(l+1) - M_l Qp(l-1)
+//   gt(l') = P_{l'-1} a(l'-1) - M_{l'+1} a(l'+1) - i m R_{l'} b(l')
+//   gp(l') = i m R_{l'} a(l') + P_{l'-1} b(l'-1) - M_{l'+1} b(l'+1)
+// For m < 0 the Legendre stage uses lambda^{|m|}; lambda^{-mu} = (-1)^mu lambda^{mu}
+// supplies the sign.
+#include "favest_internal.h"
+#include "fft_device.cuh"
+
+namespace favest {
+
+namespace {
+
+template <typename TO>
+__global__ void k_combine_fp64(const double2 *__restrict__ Q, TO *__restrict__ a, TO *__restrict__ b,
+                               const double *__restrict__ P, const double *__restrict__ M,
+                               const double *__restrict__ R, int L, int K, int ncol, int B)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)B * K) return;
+    const int bi = (int)(t / K), k = (int)(t % K);
+    int l = (int)sqrt((double)(k + 1));
+    while (l * l + 2 * l < k + 1) ++l;
+    while ((l - 1) * (l - 1) + 2 * (l - 1) >= k + 1) --l;
+    const int m = k - l * l - l + 1;
+    const int mu = m < 0 ? -m : m, s = m < 0;
+    const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
+    const long long t0 = tab_off(L, mu);
+    const long long row = t0 + (l - mu);
+    const int cth = (bi * 2 + 0) * 2 + s, cph = (bi * 2 + 1) * 2 + s;
+    const double Pl = P[row], Ml = M[row], Rl = R[row] * m;
+    double2 qt1 = Q[(size_t)(row + 1) * ncol + cth], qp1 = Q[(size_t)(row + 1) * ncol + cph];
+    double2 qt0 = Q[(size_t)row * ncol + cth], qp0 = Q[(size_t)row * ncol + cph];
+    double2 qtm = make_double2(0.0, 0.0), qpm = make_double2(0.0, 0.0);
+    if (l > mu) {
+        qtm = Q[(size_t)(row - 1) * ncol + cth];
+        qpm = Q[(size_t)(row - 1) * ncol + cph];
+    }
+    // -i m R Qp = (m R Qp.y, -m R Qp.x);  i m R Qt = (-m R Qt.y, m R Qt.x)
+    double2 av = make_double2(sg * (Pl * qt1.x - Ml * qtm.x + Rl * qp0.y),
+                              sg * (Pl * qt1.y - Ml * qtm.y - Rl * qp0.x));
+    double2 bv = make_double2(sg * (-Rl * qt0.y + Pl * qp1.x - Ml * qpm.x),
+                              sg * (Rl * qt0.x + Pl * qp1.y - Ml * qpm.y));
+    a[(size_t)bi * K + k] = from_d2<TO>(av);
+    b[(size_t)bi * K + k] = from_d2<TO>(bv);
+}
+
+template <typename TI>
+__device__ __forceinline__ double2 coef(const TI *__restrict__ c, int L, int l, int m, int bi, int K)
+{
+    int am = m < 0 ? -m : m;
+    if (l < 1 || l > L || am > l) return make_double2(0.0, 0.0);
+    return to_d2(c[(size_t)bi * K + l * l + l + m - 1]);
+}
+
+// grid.x = mu, grid.y = b*2 + s; threads stride over rows l' = mu..L+1
+template <typename TI>
+__global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict__ b,
+                                 double2 *__restrict__ g, const double *__restrict__ P,
+                                 const double *__restrict__ M, const double *__restrict__ R, int L,
+                                 int K, int ncol)
+{
+    const int mu = blockIdx.x;
+    const int bi = blockIdx.y >> 1, s = blockIdx.y & 1;
+    const int m = s ? -mu : mu;
+    const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
+    const long long t0 = tab_off(L, mu);
+    const int nrow = L + 2 - mu;
+    const int cth = (bi * 2 + 0) * 2 + s, cph = (bi * 2 + 1) * 2 + s;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+        const int l = mu + r;
+        double2 gt = make_double2(0.0, 0.0), gp = make_double2(0.0, 0.0);
+        if (!(mu == 0 && s == 1)) {
+            const double Pm = (r > 0) ? P[t0 + r - 1] : 0.0;
+            const double Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.0;
+            const double Rl = (l <= L) ? R[t0 + r] * m : 0.0;
+            double2 am1 = coef(a, L, l - 1, m, bi, K), ap1 = coef(a, L, l + 1, m, bi, K);
+            double2 bm1 = coef(b, L, l - 1, m, bi, K), bp1 = coef(b, L, l + 1, m, bi, K);
+            double2 a0 = coef(a, L, l, m, bi, K), b0 = coef(b, L, l, m, bi, K);
+            gt = make_double2(sg * (Pm * am1.x - Mp * ap1.x + Rl * b0.y),
+                              sg * (Pm * am1.y - Mp * ap1.y - Rl * b0.x));
+            gp = make_double2(sg * (-Rl * a0.y + Pm * bm1.x - Mp * bp1.x),
+                              sg * (Rl * a0.x + Pm * bm1.y - Mp * bp1.y));
+        }
+        g[(size_t)(t0 + r) * ncol + cth] = gt;
+        g[(size_t)(t0 + r) * ncol + cph] = gp;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    long long n = (long long)p.B * K;
+    int th = 256;
+    long long grid = (n + th - 1) / th;
+    if (p.io == FAVEST_IO_C128)
+        k_combine_fp64<double2><<<(unsigned)grid, th, 0, s>>>((const double2 *)p.d_Q, (double2 *)a,
+                                                              (double2 *)b, p.d_P, p.d_M, p.d_R, p.L, K,
+                                                              p.ncol, p.B);
+    else
+        k_combine_fp64<float2><<<(unsigned)grid, th, 0, s>>>((const double2 *)p.d_Q, (float2 *)a,
+                                                             (float2 *)b, p.d_P, p.d_M, p.d_R, p.L, K,
+                                                             p.ncol, p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    dim3 grid(p.L + 1, p.B * 2);
+    int th = p.L + 2 >= 256 ? 256 : 64;
+    if (p.io == FAVEST_IO_C128)
+        k_uncombine_fp64<double2><<<grid, th, 0, s>>>((const double2 *)a, (const double2 *)b,
+                                                      (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, K,
+                                                      p.ncol);
+    else
+        k_uncombine_fp64<float2><<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b,
+                                                     (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, K,
+                                                     p.ncol);
+    return cudaGetLastError();
+}
+
+}  // namespace favest

@@ -1,0 +1,433 @@
+// C ABI of the favest library: plan construction (host FP64 tables), argument
+// validation and launch sequencing.  See include/favest.h for the contract.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "favest_internal.h"
+
+using namespace favest;
+
+struct favest_plan_s {
+    Plan p;
+};
+
+namespace {
+
+const char *kErrStr[] = {
+    "success",
+    "invalid argument",
+    "out of memory",
+    "CUDA runtime error",
+    "unsupported request",
+    "device-side wait timed out",
+    "device-side error",
+};
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rule: Newton's method on P_n from Tricomi's asymptotic initial
+// guess; P_n and P_n' by the three-term recurrence and (1-x^2) P_n' = n (P_{n-1} - x P_n).
+// ---------------------------------------------------------------------------
+void legendre_pn(int n, double x, double &pn, double &dpn)
+{
+    double pm1 = 1.0, p = x;
+    if (n == 0) { pn = 1.0; dpn = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double pp1 = ((2 * k + 1) * x * p - k * pm1) / (k + 1);
+        pm1 = p;
+        p = pp1;
+    }
+    pn = p;
+    dpn = n * (pm1 - x * p) / ((1.0 - x) * (1.0 + x));
+}
+
+int gl_rule(int n, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        // Tricomi: x_i ~ (1 - (n-1)/(8 n^3)) cos(pi (4i + 3) / (4n + 2))
+        double t = pi * (4.0 * i + 3.0) / (4.0 * n + 2.0);
+        double z = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(t);
+        double pn = 0, dpn = 1;
+        for (int it = 0; it < 60; ++it) {
+            legendre_pn(n, z, pn, dpn);
+            double dz = pn / dpn;
+            z -= dz;
+            if (std::fabs(dz) <= 4e-17 * std::fabs(z) + 1e-300) break;
+        }
+        legendre_pn(n, z, pn, dpn);
+        double wt = 2.0 / ((1.0 - z) * (1.0 + z) * dpn * dpn);
+        x[i] = z;
+        w[i] = wt;
+        x[n - 1 - i] = -z;
+        w[n - 1 - i] = wt;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+    return FAVEST_OK;
+}
+
+double eps_lm(int l, int mu)
+{
+    double num = (double)(l - mu) * (double)(l + mu);
+    double den = (double)(2 * l - 1) * (double)(2 * l + 1);
+    return num > 0 ? std::sqrt(num / den) : 0.0;
+}
+
+int factorize(int n, int *rad)
+{
+    int k = 0;
+    while (n % 4 == 0 && k < kMaxRadixStages) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < kMaxRadixStages) { rad[k++] = 2; n /= 2; }
+    for (int f = 3; n > 1 && k < kMaxRadixStages; f += 2)
+        while (n % f == 0 && k < kMaxRadixStages) { rad[k++] = f; n /= f; }
+    return n == 1 ? k : -1;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T **p, const std::vector<T> &h)
+{
+    cudaError_t e = dalloc(p, h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_plan(Plan &p)
+{
+    void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
+                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    std::free(p.h_x);
+    std::free(p.h_w);
+}
+
+int build_tables(Plan &p)
+{
+    const int L = p.L;
+    const int J = p.J;
+    cudaError_t e;
+    std::vector<double> x(J), s(J), om(J), omu(J);
+    for (int j = 0; j < J; ++j) {
+        double xj = p.h_x[j];
+        double sj = std::sqrt((1.0 - xj) * (1.0 + xj));
+        x[j] = xj;
+        s[j] = sj;
+        om[j] = p.h_w[j] * (2.0 * 3.14159265358979323846 / p.nphi) / sj;
+        omu[j] = 1.0 / sj;
+    }
+    if ((e = upload(&p.d_x, x)) || (e = upload(&p.d_sin, s)) || (e = upload(&p.d_omega, om)) ||
+        (e = upload(&p.d_omega_unit, omu)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+
+    std::vector<double> cmu(L + 1);
+    cmu[0] = 1.0 / std::sqrt(4.0 * 3.14159265358979323846);
+    for (int mu = 1; mu <= L; ++mu) cmu[mu] = cmu[mu - 1] * std::sqrt((2.0 * mu + 1.0) / (2.0 * mu));
+
+    const long long ntab = tab_off(L, L + 1);
+    p.ntab = ntab;
+    std::vector<double> A(ntab), P(ntab), M(ntab), R(ntab), kap(L + 3);
+    for (int mu = 0; mu <= L; ++mu) {
+        const long long t0 = tab_off(L, mu);
+        // kappa_l = lambda_l / y_l with kappa_mu = kappa_{mu+1} = 1
+        kap[mu] = 1.0;
+        if (mu + 1 <= L + 2) kap[mu + 1] = 1.0;
+        for (int l = mu + 2; l <= L + 2; ++l) kap[l] = kap[l - 2] * eps_lm(l - 1, mu) / eps_lm(l, mu);
+        for (int l = mu; l <= L + 1; ++l) {
+            const long long t = t0 + (l - mu);
+            double a = 0.0;
+            if (l == mu + 1) a = std::sqrt(2.0 * mu + 3.0);
+            else if (l >= mu + 2) a = kap[l - 1] / (eps_lm(l - 1, mu) * kap[l - 2]);
+            A[t] = a;
+            const double sl = l >= 1 ? 1.0 / std::sqrt((double)l * (l + 1.0)) : 0.0;
+            P[t] = sl * l * eps_lm(l + 1, mu) * kap[l + 1];
+            M[t] = (l > mu) ? sl * (l + 1.0) * eps_lm(l, mu) * kap[l - 1] : 0.0;
+            R[t] = sl * kap[l];
+        }
+    }
+    if ((e = upload(&p.d_cmu, cmu)) || (e = upload(&p.d_A, A)) || (e = upload(&p.d_P, P)) ||
+        (e = upload(&p.d_M, M)) || (e = upload(&p.d_R, R)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+
+    // FFT twiddles exp(-2 pi i k / n), angles reduced exactly
+    const int n = p.nphi;
+    p.fft.n = n;
+    p.fft.nstages = factorize(n, p.fft.radix);
+    if (p.fft.nstages < 0) return FAVEST_EUNSUPPORTED;
+    std::vector<double2> tw(n);
+    std::vector<float2> tw32(n);
+    for (int k = 0; k < n; ++k) {
+        long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)k / (long double)n;
+        double cr = (double)cosl(ang), ci = -(double)sinl(ang);
+        tw[k] = make_double2(cr, ci);
+        tw32[k] = make_float2((float)cr, (float)ci);
+    }
+    if ((e = upload(&p.fft.tw64, tw)) || (e = upload(&p.fft.tw32, tw32)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    return FAVEST_OK;
+}
+
+int alloc_workspace(Plan &p)
+{
+    size_t fbytes = (size_t)(p.L + 1) * p.ncol * p.nlat * sizeof(double2);
+    size_t qbytes = (size_t)p.ntab * p.ncol * sizeof(double2);
+    size_t gbytes = (size_t)p.B * 2 * p.nlat * p.nphi * sizeof(double2);
+    if (cudaMalloc(&p.d_F, fbytes) != cudaSuccess || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
+        cudaMalloc(&p.d_G, gbytes) != cudaSuccess ||
+        cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return FAVEST_ENOMEM;
+    }
+    cudaMemset(p.d_status, 0, sizeof(int));
+    p.ws_bytes = fbytes + qbytes + gbytes;
+    return FAVEST_OK;
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+int check_device(const Plan &p)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FAVEST_ECUDA;
+    return dev == p.device ? FAVEST_OK : FAVEST_EINVAL;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_ECUDA; }
+
+const char *kKernelNames[KID_COUNT] = {
+    "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
+};
+
+cudaEvent_t take_event(Plan &p)
+{
+    cudaEvent_t e = nullptr;
+    if (!p.event_pool.empty()) {
+        e = p.event_pool.back();
+        p.event_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// Launch `fn` on stream s, bracketed by events when profiling is enabled.
+template <typename Fn>
+cudaError_t timed(Plan &p, int kid, cudaStream_t s, Fn fn)
+{
+    if (!p.profiling) return fn();
+    cudaEvent_t e0 = take_event(p), e1 = take_event(p);
+    if (e0) cudaEventRecord(e0, s);
+    cudaError_t err = fn();
+    if (e1) cudaEventRecord(e1, s);
+    if (e0 && e1) p.recs.push_back({kid, e0, e1});
+    else {
+        if (e0) p.event_pool.push_back(e0);
+        if (e1) p.event_pool.push_back(e1);
+    }
+    return err;
+}
+
+void release_events(Plan &p)
+{
+    for (auto &r : p.recs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    p.recs.clear();
+    for (auto e : p.event_pool) cudaEventDestroy(e);
+    p.event_pool.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *favest_strerror(int status)
+{
+    int i = -status;
+    if (i < 0 || i >= (int)(sizeof(kErrStr) / sizeof(kErrStr[0]))) return "unknown status";
+    return kErrStr[i];
+}
+
+int favest_gl_grid(int nlat, double *x, double *w)
+{
+    if (nlat < 1 || !x || !w) return FAVEST_EINVAL;
+    return gl_rule(nlat, x, w);
+}
+
+int favest_plan_create(int L, int batch, int precision, int io_type, const double *cos_theta,
+                       const double *w_lat, favest_plan *out)
+{
+    if (!out) return FAVEST_EINVAL;
+    *out = nullptr;
+    if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
+    if (precision != FAVEST_FP64 && precision != FAVEST_F16X3) return FAVEST_EINVAL;
+    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64) return FAVEST_EINVAL;
+    if ((cos_theta == nullptr) != (w_lat == nullptr)) return FAVEST_EINVAL;
+    const int nlat = L + 1;
+    if (cos_theta) {
+        for (int j = 0; j < nlat; ++j) {
+            double xj = cos_theta[j], xm = cos_theta[nlat - 1 - j];
+            if (!(xj > -1.0 && xj < 1.0) || !(w_lat[j] > 0.0)) return FAVEST_EINVAL;
+            if (std::fabs(xj + xm) > 1e-14 || std::fabs(w_lat[j] - w_lat[nlat - 1 - j]) > 1e-14)
+                return FAVEST_EINVAL;
+            if (j > 0 && !(cos_theta[j] < cos_theta[j - 1])) return FAVEST_EINVAL;
+        }
+    }
+    if (precision == FAVEST_F16X3) return FAVEST_EUNSUPPORTED;
+
+    favest_plan_s *h = new (std::nothrow) favest_plan_s();
+    if (!h) return FAVEST_ENOMEM;
+    Plan &p = h->p;
+    p.L = L;
+    p.B = batch;
+    p.precision = precision;
+    p.io = io_type;
+    p.nlat = nlat;
+    p.nphi = 2 * (L + 1);
+    p.J = (nlat + 1) / 2;
+    p.has_eq = nlat & 1;
+    p.ncol = 4 * batch;
+    p.ct = (batch % 2 == 0) ? 8 : 4;
+    p.ng = p.ncol / p.ct;
+    if (cudaGetDevice(&p.device) != cudaSuccess) { delete h; return FAVEST_ECUDA; }
+    cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+    p.h_x = (double *)std::malloc(sizeof(double) * nlat);
+    p.h_w = (double *)std::malloc(sizeof(double) * nlat);
+    if (!p.h_x || !p.h_w) { free_plan(p); delete h; return FAVEST_ENOMEM; }
+    if (cos_theta) {
+        std::memcpy(p.h_x, cos_theta, sizeof(double) * nlat);
+        std::memcpy(p.h_w, w_lat, sizeof(double) * nlat);
+    } else {
+        gl_rule(nlat, p.h_x, p.h_w);
+    }
+    if (p.J > 512) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
+    int st = build_tables(p);
+    if (st == FAVEST_OK) st = alloc_workspace(p);
+    if (st != FAVEST_OK) {
+        cudaGetLastError();
+        free_plan(p);
+        delete h;
+        return st;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(p); delete h; return FAVEST_ECUDA; }
+    *out = h;
+    return FAVEST_OK;
+}
+
+int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, void *stream)
+{
+    if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    size_t el = p.io == FAVEST_IO_C128 ? 16 : 8;
+    if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
+    int st = check_device(p);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, Tth, Tph, s); });
+    if (e == cudaSuccess) e = timed(p, KID_ANALYSIS, s, [&] { return launch_analysis_fp64(p, s); });
+    if (e == cudaSuccess) e = timed(p, KID_COMBINE, s, [&] { return launch_combine_fp64(p, a, b, s); });
+    return cuda_status(e);
+}
+
+int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, void *stream)
+{
+    if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    size_t el = p.io == FAVEST_IO_C128 ? 16 : 8;
+    if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
+    int st = check_device(p);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_fp64(p, a, b, s); });
+    if (e == cudaSuccess) e = timed(p, KID_SYNTHESIS, s, [&] { return launch_synthesis_fp64(p, s); });
+    if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, Tth, Tph, s); });
+    return cuda_status(e);
+}
+
+int favest_set_weights_unit(favest_plan plan, int flag)
+{
+    if (!plan || (flag != 0 && flag != 1)) return FAVEST_EINVAL;
+    plan->p.unit_weights = flag;
+    return FAVEST_OK;
+}
+
+int favest_plan_L(favest_plan plan) { return plan ? plan->p.L : FAVEST_EINVAL; }
+int favest_plan_batch(favest_plan plan) { return plan ? plan->p.B : FAVEST_EINVAL; }
+int favest_plan_precision(favest_plan plan) { return plan ? plan->p.precision : FAVEST_EINVAL; }
+size_t favest_plan_workspace_bytes(favest_plan plan) { return plan ? plan->p.ws_bytes : 0; }
+
+int favest_launches_per_call(favest_plan plan, int adjoint)
+{
+    if (!plan) return FAVEST_EINVAL;
+    (void)adjoint;
+    return 3;
+}
+
+int favest_status(favest_plan plan, void *stream)
+{
+    if (!plan) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FAVEST_ECUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, p.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FAVEST_ECUDA;
+    if (v != 0) cudaMemset(p.d_status, 0, sizeof(int));
+    return v;
+}
+
+int favest_profile_enable(favest_plan plan, int enable)
+{
+    if (!plan || (enable != 0 && enable != 1)) return FAVEST_EINVAL;
+    plan->p.profiling = enable;
+    return FAVEST_OK;
+}
+
+int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *ms, long long *launches)
+{
+    if (!plan || max_kernels < 0 || (max_kernels > 0 && (!names || !ms || !launches))) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    double tot[KID_COUNT] = {0};
+    long long cnt[KID_COUNT] = {0};
+    int status = FAVEST_OK;
+    for (auto &r : p.recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess)
+            status = FAVEST_ECUDA;
+        tot[r.kernel] += t;
+        cnt[r.kernel] += 1;
+        p.event_pool.push_back(r.e0);
+        p.event_pool.push_back(r.e1);
+    }
+    p.recs.clear();
+    if (status != FAVEST_OK) return status;
+    int k = 0;
+    for (int i = 0; i < KID_COUNT && k < max_kernels; ++i) {
+        if (!cnt[i]) continue;
+        std::snprintf(names + 32 * k, 32, "%s", kKernelNames[i]);
+        ms[k] = tot[i];
+        launches[k] = cnt[i];
+        ++k;
+    }
+    return k;
+}
+
+void favest_plan_destroy(favest_plan plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    release_events(plan->p);
+    free_plan(plan->p);
+    delete plan;
+}
+
+}  // extern "C"

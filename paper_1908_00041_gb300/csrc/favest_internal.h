@@ -1,0 +1,100 @@
+// Internal declarations of the favest CUDA library (not part of the C ABI).
+//
+// Transform structure (both precisions).  For every order mu = |m| the vector
+// transform reduces to two scalar Legendre transforms of degree L+1 plus an O(L)
+// combine per order, because
+//     sin(theta) d_theta lambda_l^m = l eps_{l+1}^m lambda_{l+1}^m - (l+1) eps_l^m lambda_{l-1}^m
+// (eps_l^m = sqrt((l^2-m^2)/(4l^2-1))).  This is the theta/phi-component analogue of
+// the paper's Thm. 1 and Thm. 2 (vector transform = combination of scalar transforms
+// of degrees L-1..L+1); the paper reaches it through Cartesian components and
+// Clebsch-Gordan coefficients.
+//
+// Forward, per field and component c in {theta, phi}:
+//   F_c(j, m)  = sum_k T_c(j, k) e^{-i m phi_k}                       (longitude FFT)
+//   Q_c(l, m)  = sum_j lambda_l^m(theta_j) omega_j F_c(j, m),  l = |m|..L+1
+//                omega_j = W_j (2 pi / nphi) / sin(theta_j)         (Legendre stage)
+//   a_lm = P_l Q_th(l+1) - M_l Q_th(l-1) - i m R_l Q_ph(l)
+//   b_lm = i m R_l Q_th(l) + P_l Q_ph(l+1) - M_l Q_ph(l-1)           (combine)
+// Adjoint: the exact transpose (uncombine -> Legendre synthesis -> 1/sin -> inverse FFT).
+//
+// The recurrence runs on rescaled values y_l = lambda_l / kappa_l chosen so that
+//   y_l = A_l x y_{l-1} - y_{l-2}   (two FP64 instructions per value);
+// kappa is folded into the per-(l, mu) combine coefficients P, M, R.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "../../include/favest.h"
+
+namespace favest {
+
+constexpr int kMaxRadixStages = 24;
+
+struct FftPlan {
+    int n = 0;
+    int nstages = 0;
+    int radix[kMaxRadixStages];
+    double2 *tw64 = nullptr;   // device, e^{-2 pi i k / n}, k = 0..n-1
+    float2 *tw32 = nullptr;    // device, same rounded to float
+};
+
+struct Plan {
+    int L = 0, B = 0, precision = 0, io = 0;
+    int nlat = 0, nphi = 0, J = 0, has_eq = 0;
+    int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
+    int ct = 0, ng = 0;       // FP64 column group width and count
+    int unit_weights = 0;
+    int device = 0;
+    int num_sms = 0;
+    long long ntab = 0;       // sum_mu (L + 2 - mu): rows of every per-(l, mu) table
+
+    // host copies
+    double *h_x = nullptr, *h_w = nullptr;
+
+    // device constant tables
+    double *d_x = nullptr;        // [J] cos(theta_j), northern half (+ equator)
+    double *d_sin = nullptr;      // [J] sin(theta_j)
+    double *d_omega = nullptr;    // [J] quadrature weight / sin(theta_j)
+    double *d_omega_unit = nullptr;  // [J] 1 / sin(theta_j)
+    double *d_cmu = nullptr;      // [L+1] sectoral normalisation sqrt((2mu+1)!!/(4pi (2mu)!!))
+    double *d_A = nullptr;        // [ntab] recurrence multipliers A_l^mu
+    double *d_P = nullptr;        // [ntab] combine coefficient P_l^mu
+    double *d_M = nullptr;        // [ntab] combine coefficient M_l^mu
+    double *d_R = nullptr;        // [ntab] combine coefficient R_l^mu
+    int *d_status = nullptr;      // device status word
+
+    // workspace
+    void *d_F = nullptr;          // forward: raw longitude spectra [mu][col][nlat]
+    void *d_Q = nullptr;          // scalar coefficients Q or g: [tab row][col]
+    void *d_G = nullptr;          // adjoint: spectra rows [B][2][nlat][nphi]
+    size_t ws_bytes = 0;
+
+    FftPlan fft;
+
+    // profiling: event pairs recorded around each launch while enabled
+    int profiling = 0;
+    struct Rec { int kernel; cudaEvent_t e0, e1; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+enum KernelId {
+    KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
+    KID_COUNT
+};
+
+__host__ __device__ inline long long tab_off(int L, int mu) {
+    return (long long)mu * (L + 2) - (long long)mu * (mu - 1) / 2;
+}
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s);
+cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
+cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s);
+cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s);
+cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s);
+cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, cudaStream_t s);
+
+}  // namespace favest

@@ -1,0 +1,109 @@
+// Longitude DFT stage: one complex DFT of length nphi = 2(L+1) per latitude ring,
+// component and field, done in shared memory by a mixed-radix Stockham FFT
+// (radices 4, 2, then odd primes; an odd prime p uses a direct p-point DFT).
+// Twiddles are FP64 values of exp(-2 pi i k / n) formed on the host from exactly
+// reduced angles.
+#include "favest_internal.h"
+#include "fft_device.cuh"
+
+namespace favest {
+
+namespace {
+
+// Forward: read ring (b, c, j) of T (io type TI), FFT in FP64, scatter bins m = -L..L
+// into Fraw[mu][col][j], col = (b*2 + c)*2 + (m < 0).
+template <typename TI>
+__global__ void __launch_bounds__(256) k_fft_fwd_fp64(
+    const TI *__restrict__ Tth, const TI *__restrict__ Tph, double2 *__restrict__ Fraw,
+    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat, int ncol)
+{
+    extern __shared__ double2 sm_fft[];
+    const int n = rp.n;
+    const int ring = blockIdx.x;               // ((b*2 + c) * nlat + j)
+    const int j = ring % nlat;
+    const int bc = ring / nlat;
+    const int c = bc & 1, b = bc >> 1;
+    const TI *src = (c == 0 ? Tth : Tph) + ((size_t)b * nlat + j) * n;
+    double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = to_d2(src[k]);
+    __syncthreads();
+    const double2 *out = stockham<false>(buf0, buf1, tw, rp);
+    for (int m = -L + (int)threadIdx.x; m <= L; m += blockDim.x) {
+        int bin = m < 0 ? m + n : m;
+        double2 v = out[bin];
+        int mu = m < 0 ? -m : m;
+        int col0 = (b * 2 + c) * 2;
+        size_t base = (size_t)mu * ncol;
+        if (m <= 0) Fraw[(base + col0 + 1) * nlat + j] = v;
+        if (m >= 0) Fraw[(base + col0 + 0) * nlat + j] = v;
+    }
+}
+
+// Inverse: read spectrum row G[b][c][j][bin] (Nyquist bin L+1 taken as zero), inverse
+// FFT (no 1/n), write ring to T (io type TO).
+template <typename TO>
+__global__ void __launch_bounds__(256) k_fft_inv_fp64(
+    const double2 *__restrict__ G, TO *__restrict__ Tth, TO *__restrict__ Tph,
+    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat)
+{
+    extern __shared__ double2 sm_fft[];
+    const int n = rp.n;
+    const int ring = blockIdx.x;
+    const int j = ring % nlat;
+    const int bc = ring / nlat;
+    const int c = bc & 1, b = bc >> 1;
+    const double2 *src = G + (size_t)ring * n;
+    double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        buf0[k] = (k == L + 1) ? make_double2(0.0, 0.0) : src[k];
+    __syncthreads();
+    const double2 *out = stockham<true>(buf0, buf1, tw, rp);
+    TO *dst = (c == 0 ? Tth : Tph) + ((size_t)b * nlat + j) * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = from_d2<TO>(out[k]);
+}
+
+int fft_threads(int n) { return n >= 512 ? 256 : (n >= 128 ? 128 : 64); }
+
+}  // namespace
+
+cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
+{
+    RadixPlanArg rp = make_radix_arg(p.fft);
+    int grid = p.B * 2 * p.nlat;
+    size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
+    int th = fft_threads(p.nphi);
+    if (p.io == FAVEST_IO_C128) {
+        auto k = k_fft_fwd_fp64<double2>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, th, smem, s>>>((const double2 *)Tth, (const double2 *)Tph, (double2 *)p.d_F,
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol);
+    } else {
+        auto k = k_fft_fwd_fp64<float2>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, th, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (double2 *)p.d_F,
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
+{
+    RadixPlanArg rp = make_radix_arg(p.fft);
+    int grid = p.B * 2 * p.nlat;
+    size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
+    int th = fft_threads(p.nphi);
+    if (p.io == FAVEST_IO_C128) {
+        auto k = k_fft_inv_fp64<double2>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (double2 *)Tth, (double2 *)Tph, rp,
+                                 p.fft.tw64, p.L, p.nlat);
+    } else {
+        auto k = k_fft_inv_fp64<float2>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (float2 *)Tth, (float2 *)Tph, rp,
+                                 p.fft.tw64, p.L, p.nlat);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace favest

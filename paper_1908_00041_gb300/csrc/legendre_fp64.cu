@@ -1,0 +1,288 @@
+// FP64 Legendre stage: the scaled FP64 recurrence fused with the quadrature-weighted
+// contraction (forward) or with the coefficient sum (adjoint), one CTA per
+// (order mu, column group).  Equatorial symmetry lambda_l^m(-x) = (-1)^{l+m} lambda_l^m(x)
+// folds each latitude pair (j, nlat-1-j) into one recurrence.
+#include "favest_internal.h"
+#include "recurrence.cuh"
+
+namespace favest {
+
+namespace {
+
+constexpr int kAnaThreads = 64;   // two warps
+constexpr int kAnaJpt = 8;        // latitudes per thread (J <= 512)
+constexpr int kWin = 4;           // rows per reduction window (even)
+
+template <int V>
+__device__ __forceinline__ void warp_transpose_reduce(double (&v)[V])
+{
+    // After the call lane l holds in v[0 .. V/32) the warp totals of the values with
+    // indices l*V/32 .. l*V/32 + V/32 - 1.
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+        const int o = 16 >> lev;
+        const int h = V >> (lev + 1);
+        const bool up = (threadIdx.x & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            double send = up ? v[i] : v[i + h];
+            double keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+// Forward Legendre stage.  Fraw: [mu][ncol][nlat] raw longitude spectra; Q: [tab][ncol].
+template <int CT>
+__global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
+    const double2 *__restrict__ Fraw, double2 *__restrict__ Q, const double *__restrict__ xj,
+    const double *__restrict__ sj, const double *__restrict__ omega, const double *__restrict__ cmu,
+    const double *__restrict__ Atab, int L, int nlat, int J, int has_eq, int ncol, int ng)
+{
+    constexpr int V = kWin * CT * 2;
+    static_assert(V % 32 == 0, "window values must fill the warp");
+    extern __shared__ double sm_ana[];
+    const int mu = blockIdx.x / ng, g = blockIdx.x % ng;
+    const int nrow = L + 2 - mu;
+    const long long t0 = tab_off(L, mu);
+    double2 *Fs = reinterpret_cast<double2 *>(sm_ana);          // [2][CT][J]
+    double *As = sm_ana + 2 * 2 * CT * J;                       // [nrow]
+    double *red = As + ((nrow + 1) & ~1);                       // [2 warps][V]
+
+    for (int idx = threadIdx.x; idx < CT * J; idx += blockDim.x) {
+        int ct = idx / J, j = idx % J;
+        const double2 *src = Fraw + ((size_t)mu * ncol + g * CT + ct) * nlat;
+        double2 f1 = src[j];
+        double w = omega[j];
+        double2 fp, fm;
+        if (has_eq && j == J - 1) {
+            fp = make_double2(w * f1.x, w * f1.y);
+            fm = make_double2(0.0, 0.0);
+        } else {
+            double2 f2 = src[nlat - 1 - j];
+            fp = make_double2(w * (f1.x + f2.x), w * (f1.y + f2.y));
+            fm = make_double2(w * (f1.x - f2.x), w * (f1.y - f2.y));
+        }
+        Fs[(0 * CT + ct) * J + j] = fp;
+        Fs[(1 * CT + ct) * J + j] = fm;
+    }
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
+    __syncthreads();
+
+    double x[kAnaJpt], y1[kAnaJpt], y2[kAnaJpt];
+    int c[kAnaJpt];
+    const double cm = cmu[mu];
+#pragma unroll
+    for (int i = 0; i < kAnaJpt; ++i) {
+        int j = threadIdx.x + i * kAnaThreads;
+        x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;   // inactive lanes stay silent
+        if (j < J) {
+            x[i] = xj[j];
+            sectoral_start(cm, sj[j], mu, y1[i], c[i]);
+        }
+    }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r0 = 0; r0 < nrow; r0 += kWin) {
+        double acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWin; ++w) {
+            const int r = r0 + w;
+            if (r < nrow) {
+                const double a = As[r];
+                const int p = w & 1;          // parity of l + mu = parity of r (r0 even)
+#pragma unroll
+                for (int i = 0; i < kAnaJpt; ++i) {
+                    const int j = threadIdx.x + i * kAnaThreads;
+                    if (j < J) {
+                        double yl = y1[i];
+                        if (r > 0) {
+                            yl = fma(a * x[i], y1[i], -y2[i]);
+                            y2[i] = y1[i];
+                            y1[i] = yl;
+                        }
+                        const double yv = (c[i] == 0) ? yl : 0.0;
+#pragma unroll
+                        for (int ct = 0; ct < CT; ++ct) {
+                            double2 f = Fs[(p * CT + ct) * J + j];
+                            acc[(w * CT + ct) * 2 + 0] = fma(yv, f.x, acc[(w * CT + ct) * 2 + 0]);
+                            acc[(w * CT + ct) * 2 + 1] = fma(yv, f.y, acc[(w * CT + ct) * 2 + 1]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kAnaJpt; ++i) renorm(y1[i], y2[i], c[i]);
+        warp_transpose_reduce<V>(acc);
+        constexpr int per = V / 32;
+#pragma unroll
+        for (int q = 0; q < per; ++q) red[warp * V + lane * per + q] = acc[q];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < per; ++q) {
+                const int vi = lane * per + q;
+                const double tot = red[vi] + red[V + vi];
+                const int w = vi / (CT * 2), ct = (vi / 2) % CT, im = vi & 1;
+                const int r = r0 + w;
+                if (r < nrow) {
+                    double *dst = reinterpret_cast<double *>(Q + (size_t)(t0 + r) * ncol + g * CT + ct);
+                    dst[im] = tot;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kSynThreads = 256;
+constexpr int kSynJpt = 2;        // J <= 512
+
+// Adjoint Legendre stage.  gtab: [tab][ncol] scaled coefficients; G: [B][2][nlat][nphi].
+template <int CT>
+__global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
+    const double2 *__restrict__ gtab, double2 *__restrict__ G, const double *__restrict__ xj,
+    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
+    int L, int nlat, int nphi, int J, int has_eq, int ncol, int ng)
+{
+    extern __shared__ double sm_syn[];
+    const int mu = blockIdx.x / ng, g = blockIdx.x % ng;
+    const int nrow = L + 2 - mu;
+    const long long t0 = tab_off(L, mu);
+    double2 *gs = reinterpret_cast<double2 *>(sm_syn);   // [nrow][CT]
+    double *As = sm_syn + 2 * CT * nrow;                 // [nrow]
+    for (int idx = threadIdx.x; idx < nrow * CT; idx += blockDim.x) {
+        int r = idx / CT, ct = idx % CT;
+        gs[idx] = gtab[(size_t)(t0 + r) * ncol + g * CT + ct];
+    }
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
+    __syncthreads();
+
+    double x[kSynJpt], y1[kSynJpt], y2[kSynJpt];
+    int c[kSynJpt];
+    double2 accE[kSynJpt][CT], accO[kSynJpt][CT];
+    const double cm = cmu[mu];
+#pragma unroll
+    for (int i = 0; i < kSynJpt; ++i) {
+        int j = threadIdx.x + i * kSynThreads;
+        x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;
+        if (j < J) {
+            x[i] = xj[j];
+            sectoral_start(cm, sj[j], mu, y1[i], c[i]);
+        }
+#pragma unroll
+        for (int ct = 0; ct < CT; ++ct) {
+            accE[i][ct] = make_double2(0.0, 0.0);
+            accO[i][ct] = make_double2(0.0, 0.0);
+        }
+    }
+    for (int r0 = 0; r0 < nrow; r0 += kWin) {
+#pragma unroll
+        for (int w = 0; w < kWin; ++w) {
+            const int r = r0 + w;
+            if (r < nrow) {
+                const double a = As[r];
+#pragma unroll
+                for (int i = 0; i < kSynJpt; ++i) {
+                    double yl = y1[i];
+                    if (r > 0) {
+                        yl = fma(a * x[i], y1[i], -y2[i]);
+                        y2[i] = y1[i];
+                        y1[i] = yl;
+                    }
+                    const double yv = (c[i] == 0) ? yl : 0.0;
+#pragma unroll
+                    for (int ct = 0; ct < CT; ++ct) {
+                        double2 gv = gs[r * CT + ct];
+                        if (w & 1) {
+                            accO[i][ct].x = fma(yv, gv.x, accO[i][ct].x);
+                            accO[i][ct].y = fma(yv, gv.y, accO[i][ct].y);
+                        } else {
+                            accE[i][ct].x = fma(yv, gv.x, accE[i][ct].x);
+                            accE[i][ct].y = fma(yv, gv.y, accE[i][ct].y);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kSynJpt; ++i) renorm(y1[i], y2[i], c[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kSynJpt; ++i) {
+        const int j = threadIdx.x + i * kSynThreads;
+        if (j >= J) continue;
+        const double is = 1.0 / sj[j];
+        const bool eq = has_eq && j == J - 1;
+#pragma unroll
+        for (int ct = 0; ct < CT; ++ct) {
+            const int col = g * CT + ct;
+            const int s = col & 1, bc = col >> 1;     // bc = b*2 + component
+            if (mu == 0 && s == 1) continue;
+            const int bin = s ? nphi - mu : mu;
+            double2 e = accE[i][ct], o = accO[i][ct];
+            G[((size_t)bc * nlat + j) * nphi + bin] = make_double2((e.x + o.x) * is, (e.y + o.y) * is);
+            if (!eq)
+                G[((size_t)bc * nlat + (nlat - 1 - j)) * nphi + bin] =
+                    make_double2((e.x - o.x) * is, (e.y - o.y) * is);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
+{
+    if (p.J > kAnaThreads * kAnaJpt) return cudaErrorInvalidValue;
+    int grid = (p.L + 1) * p.ng;
+    int nrowmax = p.L + 2;
+    size_t smem;
+    if (p.ct == 8) {
+        constexpr int CT = 8, V = kWin * CT * 2;
+        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + 2 * V) * sizeof(double);
+        auto k = k_analysis_fp64<CT>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
+                                          p.unit_weights ? p.d_omega_unit : p.d_omega, p.d_cmu, p.d_A,
+                                          p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+    } else {
+        constexpr int CT = 4, V = kWin * CT * 2;
+        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + 2 * V) * sizeof(double);
+        auto k = k_analysis_fp64<CT>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
+                                          p.unit_weights ? p.d_omega_unit : p.d_omega, p.d_cmu, p.d_A,
+                                          p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
+{
+    if (p.J > kSynThreads * kSynJpt) return cudaErrorInvalidValue;
+    int grid = (p.L + 1) * p.ng;
+    int nrowmax = p.L + 2;
+    if (p.ct == 8) {
+        constexpr int CT = 8;
+        size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
+        auto k = k_synthesis_fp64<CT>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
+                                          p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
+                                          p.ng);
+    } else {
+        constexpr int CT = 4;
+        size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
+        auto k = k_synthesis_fp64<CT>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
+                                          p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
+                                          p.ng);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace favest

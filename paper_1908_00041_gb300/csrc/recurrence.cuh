@@ -1,0 +1,74 @@
+// FP64 scaled three-term recurrence for normalised associated Legendre functions
+// (device helpers shared by the FP64 and tensor-core Legendre kernels).
+//
+// For order mu >= 0 the library runs
+//     y_mu     = lambda_mu^mu(theta) * 2^(600 c)          (sectoral start, scaled)
+//     y_{mu+1} = A_{mu+1} x y_mu
+//     y_l      = A_l x y_{l-1} - y_{l-2},   l >= mu+2,   x = cos(theta)
+// where y_l = lambda_l^mu / kappa_l (kappa folded into the combine coefficients).
+// c >= 0 counts factors 2^600 by which the running values are scaled up while the
+// true values lie below the double range (near the poles at high order); while c > 0
+// the true value is below 2^-300 and contributes nothing at FP64 resolution, so it is
+// emitted as zero.  Renormalisation checks use integer operations on the exponent
+// bits, so they cost no FP64 pipe slots.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace favest {
+
+constexpr int kScaleBits = 600;       // one scale step = 2^600
+constexpr int kStartFloor = -200;     // start values are lifted to >= 2^-200
+constexpr int kRenormAt = 300;        // scaled values >= 2^300 are stepped down
+
+// f (> 0, normal) -> f in [0.5, 1), e += exponent
+__device__ __forceinline__ void frexp_acc(double &f, int &e)
+{
+    int hi = __double2hiint(f);
+    int lo = __double2loint(f);
+    int k = ((unsigned)hi >> 20 & 0x7ff) - 1022;
+    hi = (hi & 0x800fffff) | (1022 << 20);
+    f = __hiloint2double(hi, lo);
+    e += k;
+}
+
+// lambda_mu^mu(theta) = (-1)^mu cmu sin(theta)^mu as (y, c): true = y * 2^(-600 c)
+__device__ __forceinline__ void sectoral_start(double cmu, double s, int mu, double &y, int &c)
+{
+    double f = 1.0, base = s;
+    int e = 0, eb = 0;
+    frexp_acc(base, eb);
+    int n = mu;
+    while (n) {
+        if (n & 1) {
+            f *= base;
+            e += eb;
+            frexp_acc(f, e);
+        }
+        n >>= 1;
+        if (n) {
+            base *= base;
+            eb *= 2;
+            frexp_acc(base, eb);
+        }
+    }
+    double v = (mu & 1) ? -cmu * f : cmu * f;
+    int cc = 0;
+    if (e < kStartFloor) cc = (kStartFloor - e + kScaleBits - 1) / kScaleBits;
+    y = ldexp(v, e + kScaleBits * cc);
+    c = cc;
+}
+
+// Step a scaled pair down by 2^600 when the newest value reached 2^300.
+__device__ __forceinline__ void renorm(double &y1, double &y2, int &c)
+{
+    if (c > 0) {
+        int ex = ((unsigned)__double2hiint(y1) >> 20) & 0x7ff;
+        if (ex >= 1023 + kRenormAt) {
+            y1 *= 0x1p-600;
+            y2 *= 0x1p-600;
+            c -= 1;
+        }
+    }
+}
+
+}  // namespace favest

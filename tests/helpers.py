@@ -1,0 +1,37 @@
+"""Shared test helpers: error metrics and grid construction (no transform arithmetic)."""
+import numpy as np
+
+
+def normwise_err(got, ref):
+    """max |got - ref| / max |ref| over the last axis, maximised over leading axes."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    if ref.ndim == 1:
+        ref = ref[None]
+        got = got[None]
+    den = np.max(np.abs(ref), axis=-1)
+    num = np.max(np.abs(got - ref), axis=-1)
+    den = np.where(den == 0, 1.0, den)
+    return float(np.max(num / den))
+
+
+def rms_err(got, ref):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    return float(np.linalg.norm((got - ref).ravel()) / max(np.linalg.norm(ref.ravel()), 1e-300))
+
+
+def cidx(l, m):
+    return l * l + l + m - 1
+
+
+def sample_coefs(L, n, rng):
+    """n distinct (l, m) positions including the corners l = 1, l = L, m = +-l, 0."""
+    fixed = [(1, -1), (1, 0), (1, 1), (L, -L), (L, 0), (L, L), (L, L - 1), (max(1, L // 2), 0)]
+    out = {p for p in fixed}
+    while len(out) < n:
+        l = int(rng.integers(1, L + 1))
+        m = int(rng.integers(-l, l + 1))
+        out.add((l, m))
+    out = sorted(out)
+    return np.array([p[0] for p in out]), np.array([p[1] for p in out])
