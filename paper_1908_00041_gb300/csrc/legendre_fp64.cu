@@ -9,8 +9,11 @@ namespace favest {
 
 namespace {
 
-constexpr int kAnaThreads = 64;   // two warps
-constexpr int kAnaJpt = 8;        // latitudes per thread (J <= 512)
+// Eight warps per CTA: the FP64 units sit in the SM's four sub-partitions, so fewer
+// than four resident warps cannot keep the FP64 pipe full.
+constexpr int kAnaThreads = 256;
+constexpr int kAnaWarps = kAnaThreads / 32;
+constexpr int kAnaJpt = 2;        // latitudes per thread (J <= 512)
 constexpr int kWin = 4;           // rows per reduction window (even)
 
 template <int V>
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
     const long long t0 = tab_off(L, mu);
     double2 *Fs = reinterpret_cast<double2 *>(sm_ana);          // [2][CT][J]
     double *As = sm_ana + 2 * 2 * CT * J;                       // [nrow]
-    double *red = As + ((nrow + 1) & ~1);                       // [2 warps][V]
+    double *red = As + ((nrow + 1) & ~1);                       // [warps][V]
 
     for (int idx = threadIdx.x; idx < CT * J; idx += blockDim.x) {
         int ct = idx / J, j = idx % J;
@@ -121,17 +124,16 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
 #pragma unroll
         for (int q = 0; q < per; ++q) red[warp * V + lane * per + q] = acc[q];
         __syncthreads();
-        if (warp == 0) {
+        if (threadIdx.x < V) {
+            const int vi = threadIdx.x;
+            double tot = 0.0;
 #pragma unroll
-            for (int q = 0; q < per; ++q) {
-                const int vi = lane * per + q;
-                const double tot = red[vi] + red[V + vi];
-                const int w = vi / (CT * 2), ct = (vi / 2) % CT, im = vi & 1;
-                const int r = r0 + w;
-                if (r < nrow) {
-                    double *dst = reinterpret_cast<double *>(Q + (size_t)(t0 + r) * ncol + g * CT + ct);
-                    dst[im] = tot;
-                }
+            for (int wq = 0; wq < kAnaWarps; ++wq) tot += red[wq * V + vi];
+            const int w = vi / (CT * 2), ct = (vi / 2) % CT, im = vi & 1;
+            const int r = r0 + w;
+            if (r < nrow) {
+                double *dst = reinterpret_cast<double *>(Q + (size_t)(t0 + r) * ncol + g * CT + ct);
+                dst[im] = tot;
             }
         }
         __syncthreads();
@@ -242,7 +244,7 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
     size_t smem;
     if (p.ct == 8) {
         constexpr int CT = 8, V = kWin * CT * 2;
-        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + 2 * V) * sizeof(double);
+        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
@@ -250,7 +252,7 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
                                           p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
     } else {
         constexpr int CT = 4, V = kWin * CT * 2;
-        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + 2 * V) * sizeof(double);
+        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
