@@ -7,7 +7,7 @@ tangent components complex64.  One step = AdjVSHT of the batch (coefficients -> 
 followed by FwdVSHT of the synthesised fields (grid -> coefficients); the metric is
 fields / (t_adj + t_fwd).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16x3|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6|fp64]
   python bench.py --impl reference ...     (the CPU oracle, timed on a bounded sample)
 
 Under torchrun (N > 1) every rank runs the same batch on its own GPU (replicas, weak
@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default=None, choices=["f16x3", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["bf16x6", "fp64"])
     ap.add_argument("--L", type=int, default=1023)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
@@ -218,15 +218,15 @@ def main():
     api.lib(build_if_missing=True)
     prec_name = args.precision
     if prec_name is None:
-        prec_name = "f16x3"
+        prec_name = "bf16x6"
         try:
-            p = api.Plan(16, 1, api.FAVEST_F16X3, api.FAVEST_IO_C64)
+            p = api.Plan(16, 1, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
             p.close()
         except api.FavestError:
             prec_name = "fp64"
-    prec = api.FAVEST_F16X3 if prec_name == "f16x3" else api.FAVEST_FP64
+    prec = api.FAVEST_BF16X6 if prec_name == "bf16x6" else api.FAVEST_FP64
     L, B = args.L, args.batch
-    steps = args.steps or (200 if prec_name == "f16x3" else 10)
+    steps = args.steps or (200 if prec_name == "bf16x6" else 10)
 
     plan = api.Plan(L, B, prec, api.FAVEST_IO_C64)
     a_h, b_h = synthetic.coefficients(L, B, seed=2, decay=1.5)
@@ -363,7 +363,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world,
             "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x3" if prec_name == "f16x3" else "f64",
+            "dtype": "bf16x6" if prec_name == "bf16x6" else "f64",
             "data": "synthetic",
             "config": {"workload": "precision form: L=1023, Gauss-Legendre grid 1024x2048, batch %d "
                                    "fields, coefficients N(0,1)(l+1)^-1.5 seed 2, complex64 tangent "

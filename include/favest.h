@@ -64,11 +64,13 @@ enum favest_status_code {
 /* Arithmetic of the Legendre contraction.  The recurrence, its underflow scaling,
  * the normalisation constants and the quadrature weights are FP64 in every mode. */
 enum favest_precision {
-    FAVEST_FP64 = 0,   /* FP64 everywhere (FFT, recurrence, contraction)                 */
-    FAVEST_F16X3 = 1   /* FP32 FFT; FP64 recurrence; contraction on tcgen05 tensor cores
-                          with FP16 hi/lo splits of both operands (3 products) and FP32
-                          accumulation over short K blocks, summed in FP32 with error
-                          compensation                                                  */
+    FAVEST_FP64 = 0,    /* FP64 everywhere (FFT, recurrence, contraction)                */
+    FAVEST_BF16X6 = 1   /* FP32 FFT; FP64 recurrence; Legendre contraction on tcgen05
+                           tensor cores: both operands split into three bf16 pieces
+                           (24 significant bits, full FP32 exponent range), the 6 piece
+                           products of weight >= 2^-16 formed, the leading product
+                           accumulated over K blocks of 64 and summed in FP32 with
+                           round-to-nearest; complex64 fields and coefficients only     */
 };
 
 enum favest_io_type {
@@ -84,8 +86,11 @@ enum favest_io_type {
 int favest_gl_grid(int nlat, double *x, double *w);
 
 /*
- * Create a plan for degree L (1 <= L <= 4095) and a batch of `batch` fields
- * (1 <= batch <= 4096) on the current CUDA device.
+ * Create a plan for degree L and a batch of `batch` fields (1 <= batch <= 4096) on the
+ * current CUDA device.  L >= 1; degrees beyond 1023 (more than 512 latitude pairs)
+ * return FAVEST_EUNSUPPORTED in this version.  FAVEST_BF16X6
+ * requires io_type FAVEST_IO_C64 (FAVEST_EUNSUPPORTED otherwise) and a device with
+ * tcgen05 tensor cores (sm_100 family).
  *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
  *       and latitude weights; NULL selects the built-in Gauss-Legendre rule.  When
  *       given, the nodes must lie strictly inside (-1, 1) and both arrays must be

@@ -23,7 +23,7 @@ FAVEST_ETIMEOUT = -5
 FAVEST_EDEVICE = -6
 
 FAVEST_FP64 = 0
-FAVEST_F16X3 = 1
+FAVEST_BF16X6 = 1
 FAVEST_IO_C128 = 0
 FAVEST_IO_C64 = 1
 

@@ -1,0 +1,149 @@
+// Coefficient-side stages of the split-precision path (same formulas as combine.cu):
+//   combine  : FP32 scalar sums Q (tensor-core GEMM output, rows l - mu, 8 columns per
+//              field: component c, sign s of m, re/im) -> a_lm, b_lm (complex64), FP64 math
+//   uncombine: a_lm, b_lm (complex64) -> scaled scalar coefficients g, written as three
+//              bf16 pieces in the tensor-core B-operand layout.
+#include "favest_internal.h"
+
+#include <cuda_bf16.h>
+
+namespace favest {
+
+namespace {
+
+constexpr int kChunkBytes = 3 * 16384;
+
+// grid.x over (b, l): one CTA per (field, degree); threads over mu = 0..l
+__global__ void k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a, float2 *__restrict__ bo,
+                               const double *__restrict__ P, const double *__restrict__ M,
+                               const double *__restrict__ R, int L, int K, int ncolr)
+{
+    const int bi = blockIdx.x / L, l = blockIdx.x % L + 1;
+    for (int mu = threadIdx.x; mu <= l; mu += blockDim.x) {
+        const long long row = tab_off(L, mu) + (l - mu);
+        const double Pl = P[row], Ml = M[row], Rl = R[row];
+        const float *q1 = Q + (size_t)(row + 1) * ncolr + 8 * bi;
+        const float *q0 = Q + (size_t)row * ncolr + 8 * bi;
+        const float *qm = Q + (size_t)(row - 1) * ncolr + 8 * bi;
+        const bool has_m = l > mu;
+        for (int s = 0; s < 2; ++s) {
+            if (mu == 0 && s == 1) continue;
+            const int m = s ? -mu : mu;
+            const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
+            const double Rm = Rl * m;
+            // th: cols s*2 + {0,1}; ph: 4 + s*2 + {0,1}
+            const int ct = s * 2, cp = 4 + s * 2;
+            double t1x = q1[ct], t1y = q1[ct + 1], p1x = q1[cp], p1y = q1[cp + 1];
+            double t0x = q0[ct], t0y = q0[ct + 1], p0x = q0[cp], p0y = q0[cp + 1];
+            double tmx = has_m ? qm[ct] : 0.0, tmy = has_m ? qm[ct + 1] : 0.0;
+            double pmx = has_m ? qm[cp] : 0.0, pmy = has_m ? qm[cp + 1] : 0.0;
+            double ax = sg * (Pl * t1x - Ml * tmx + Rm * p0y);
+            double ay = sg * (Pl * t1y - Ml * tmy - Rm * p0x);
+            double bx = sg * (-Rm * t0y + Pl * p1x - Ml * pmx);
+            double by = sg * (Rm * t0x + Pl * p1y - Ml * pmy);
+            const size_t k = (size_t)bi * K + l * l + l + m - 1;
+            a[k] = make_float2((float)ax, (float)ay);
+            bo[k] = make_float2((float)bx, (float)by);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 cf(const float2 *__restrict__ c, int L, int l, int m, int bi, int K)
+{
+    int am = m < 0 ? -m : m;
+    if (l < 1 || l > L || am > l) return make_float2(0.f, 0.f);
+    return c[(size_t)bi * K + l * l + l + m - 1];
+}
+
+__device__ __forceinline__ void split3u(float f, unsigned short &h, unsigned short &m, unsigned short &l)
+{
+    __nv_bfloat16 bh = __float2bfloat16_rn(f);
+    float r1 = f - __bfloat162float(bh);
+    __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    float r2 = r1 - __bfloat162float(bm);
+    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
+}
+
+// grid (L+1, B): threads over rows l' = mu..L+1
+__global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__restrict__ b,
+                                 unsigned char *__restrict__ gb, const long long *__restrict__ g_off,
+                                 const double *__restrict__ P, const double *__restrict__ M,
+                                 const double *__restrict__ R, int L, int K, int n_tiles)
+{
+    const int mu = blockIdx.x, bi = blockIdx.y;
+    const long long t0 = tab_off(L, mu);
+    const int nrow = L + 2 - mu;
+    const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
+    const int nka0 = (nrow_p0 + 63) / 64, nka1 = (nrow_p1 + 63) / 64;
+    const int nt = bi / 16, bg = bi % 16;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+        const int l = mu + r;
+        float v[8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int m = s ? -mu : mu;
+            double gtx = 0, gty = 0, gpx = 0, gpy = 0;
+            if (!(mu == 0 && s == 1)) {
+                const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
+                const double Pm = (r > 0) ? P[t0 + r - 1] : 0.0;
+                const double Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.0;
+                const double Rl = (l <= L) ? R[t0 + r] * m : 0.0;
+                float2 am1 = cf(a, L, l - 1, m, bi, K), ap1 = cf(a, L, l + 1, m, bi, K);
+                float2 bm1 = cf(b, L, l - 1, m, bi, K), bp1 = cf(b, L, l + 1, m, bi, K);
+                float2 a0 = cf(a, L, l, m, bi, K), b0 = cf(b, L, l, m, bi, K);
+                gtx = sg * (Pm * am1.x - Mp * ap1.x + Rl * b0.y);
+                gty = sg * (Pm * am1.y - Mp * ap1.y - Rl * b0.x);
+                gpx = sg * (-Rl * a0.y + Pm * bm1.x - Mp * bp1.x);
+                gpy = sg * (Rl * a0.x + Pm * bm1.y - Mp * bp1.y);
+            }
+            v[0 * 4 + s * 2 + 0] = (float)gtx;
+            v[0 * 4 + s * 2 + 1] = (float)gty;
+            v[1 * 4 + s * 2 + 0] = (float)gpx;
+            v[1 * 4 + s * 2 + 1] = (float)gpy;
+        }
+        const int p = r & 1, rp = r >> 1;
+        const int nka = p ? nka1 : nka0;
+        const int kc = rp / 64, rr = rp % 64;
+        unsigned char *dst = gb + g_off[mu * 2 + p] + ((size_t)nt * nka + kc) * kChunkBytes +
+                             (size_t)(rr / 8) * 2048 + bg * 128 + (rr % 8) * 16;
+        unsigned w[3][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            unsigned short h0, m0, l0, h1, m1, l1;
+            split3u(v[2 * i], h0, m0, l0);
+            split3u(v[2 * i + 1], h1, m1, l1);
+            w[0][i] = (unsigned)h0 | ((unsigned)h1 << 16);
+            w[1][i] = (unsigned)m0 | ((unsigned)m1 << 16);
+            w[2][i] = (unsigned)l0 | ((unsigned)l1 << 16);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            *reinterpret_cast<uint4 *>(dst + q * 16384) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    const int th = p.L >= 128 ? 128 : 32;
+    k_combine_bf16<<<p.B * p.L, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P, p.d_M,
+                                             p.d_R, p.L, K, p.ncolr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    dim3 grid(p.L + 1, p.B);
+    const int th = p.L + 2 >= 256 ? 256 : 64;
+    k_uncombine_bf16<<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb,
+                                         p.d_g_off, p.d_P, p.d_M, p.d_R, p.L, K, p.n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace favest

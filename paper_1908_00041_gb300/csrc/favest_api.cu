@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -105,7 +106,8 @@ cudaError_t upload(T **p, const std::vector<T> &h)
 void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
-                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32};
+                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
+                    p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -177,6 +179,89 @@ int build_tables(Plan &p)
     return FAVEST_OK;
 }
 
+// Split-precision path: operand tile offsets, GEMM work items, buffers.
+int alloc_workspace_bf16(Plan &p)
+{
+    const int L = p.L;
+    const long long CH = 3LL * 16384;          // bytes per operand chunk (3 bf16 pieces)
+    p.JP = (p.J + 127) / 128 * 128;
+    p.ncolr = (8 * p.B + 127) / 128 * 128;
+    p.n_tiles = p.ncolr / 128;
+    p.nk_f = p.JP / 64;
+    std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
+    long long lam_f = 0, lam_a = 0, gsz = 0;
+    std::vector<TcItem> itf, ita;
+    for (int mu = 0; mu <= L; ++mu) {
+        const int nrow = L + 2 - mu;
+        for (int par = 0; par < 2; ++par) {
+            const int np = par ? nrow / 2 : (nrow + 1) / 2;
+            const int mt = (np + 127) / 128;
+            const int nka = (np + 63) / 64;
+            const int jt = p.JP / 128;
+            const int idx = mu * 2 + par;
+            off_f[idx] = lam_f;
+            off_a[idx] = lam_a;
+            off_g[idx] = gsz;
+            for (int m = 0; m < mt; ++m)
+                for (int nt = 0; nt < p.n_tiles; ++nt) {
+                    TcItem I{};
+                    I.a_off = lam_f + (long long)m * p.nk_f * CH;
+                    I.b_off = (((long long)idx * p.n_tiles + nt) * p.nk_f) * CH;
+                    I.out_off = (tab_off(L, mu) + par + 256LL * m) * p.ncolr + 128LL * nt;
+                    I.nk = p.nk_f;
+                    I.rows = np - 128 * m < 128 ? np - 128 * m : 128;
+                    I.a_stride = (int)CH;
+                    I.b_stride = (int)CH;
+                    I.out_ld = 2 * p.ncolr;
+                    itf.push_back(I);
+                }
+            for (int t = 0; t < jt; ++t)
+                for (int nt = 0; nt < p.n_tiles; ++nt) {
+                    TcItem I{};
+                    I.a_off = lam_a + (long long)t * nka * CH;
+                    I.b_off = gsz + (long long)nt * nka * CH;
+                    I.out_off = ((long long)idx * p.JP + 128LL * t) * p.ncolr + 128LL * nt;
+                    I.nk = nka;
+                    I.rows = 128;
+                    I.a_stride = (int)CH;
+                    I.b_stride = (int)CH;
+                    I.out_ld = p.ncolr;
+                    ita.push_back(I);
+                }
+            lam_f += (long long)mt * p.nk_f * CH;
+            lam_a += (long long)jt * nka * CH;
+            gsz += (long long)p.n_tiles * nka * CH;
+        }
+    }
+    // heaviest items first (adjoint items differ in K depth)
+    std::stable_sort(ita.begin(), ita.end(), [](const TcItem &x, const TcItem &y) { return x.nk > y.nk; });
+    p.n_items_f = (int)itf.size();
+    p.n_items_a = (int)ita.size();
+    const size_t lam_bytes = (size_t)(lam_f > lam_a ? lam_f : lam_a);
+    const size_t fb_bytes = (size_t)(2 * (L + 1)) * p.n_tiles * p.nk_f * CH;
+    const size_t q_bytes = (size_t)p.ntab * p.ncolr * sizeof(float);
+    const size_t s_bytes = (size_t)(2 * (L + 1)) * p.JP * p.ncolr * sizeof(float);
+    if (cudaMalloc(&p.d_lam, lam_bytes) != cudaSuccess || cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
+        cudaMalloc(&p.d_gb, (size_t)gsz) != cudaSuccess || cudaMalloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
+        cudaMalloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
+        cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return FAVEST_ENOMEM;
+    }
+    // padded operand positions (latitudes >= J, rows beyond each order's range) must
+    // hold zeros; they are never written afterwards
+    if (cudaMemset(p.d_lam, 0, lam_bytes) != cudaSuccess || cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
+        cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess || cudaMemset(p.d_status, 0, sizeof(int)) != cudaSuccess)
+        return FAVEST_ECUDA;
+    cudaError_t e;
+    std::vector<TcItem> all;
+    if ((e = upload(&p.d_lam_off_f, off_f)) || (e = upload(&p.d_lam_off_a, off_a)) ||
+        (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    p.ws_bytes = lam_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
+    return FAVEST_OK;
+}
+
 int alloc_workspace(Plan &p)
 {
     size_t fbytes = (size_t)(p.L + 1) * p.ncol * p.nlat * sizeof(double2);
@@ -206,6 +291,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_EC
 
 const char *kKernelNames[KID_COUNT] = {
     "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
+    "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj",
 };
 
 cudaEvent_t take_event(Plan &p)
@@ -271,7 +357,8 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
     if (!out) return FAVEST_EINVAL;
     *out = nullptr;
     if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
-    if (precision != FAVEST_FP64 && precision != FAVEST_F16X3) return FAVEST_EINVAL;
+    if (L > 1023) return FAVEST_EUNSUPPORTED;
+    if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
     if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64) return FAVEST_EINVAL;
     if ((cos_theta == nullptr) != (w_lat == nullptr)) return FAVEST_EINVAL;
     const int nlat = L + 1;
@@ -284,7 +371,7 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
             if (j > 0 && !(cos_theta[j] < cos_theta[j - 1])) return FAVEST_EINVAL;
         }
     }
-    if (precision == FAVEST_F16X3) return FAVEST_EUNSUPPORTED;
+    if (precision == FAVEST_BF16X6 && io_type != FAVEST_IO_C64) return FAVEST_EUNSUPPORTED;
 
     favest_plan_s *h = new (std::nothrow) favest_plan_s();
     if (!h) return FAVEST_ENOMEM;
@@ -302,6 +389,12 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
     p.ng = p.ncol / p.ct;
     if (cudaGetDevice(&p.device) != cudaSuccess) { delete h; return FAVEST_ECUDA; }
     cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+    if (precision == FAVEST_BF16X6) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p.device);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p.device);
+        if (major != 10 || minor != 3) { delete h; return FAVEST_EUNSUPPORTED; }
+    }
     p.h_x = (double *)std::malloc(sizeof(double) * nlat);
     p.h_w = (double *)std::malloc(sizeof(double) * nlat);
     if (!p.h_x || !p.h_w) { free_plan(p); delete h; return FAVEST_ENOMEM; }
@@ -313,7 +406,7 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
     }
     if (p.J > 512) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
     int st = build_tables(p);
-    if (st == FAVEST_OK) st = alloc_workspace(p);
+    if (st == FAVEST_OK) st = (precision == FAVEST_BF16X6) ? alloc_workspace_bf16(p) : alloc_workspace(p);
     if (st != FAVEST_OK) {
         cudaGetLastError();
         free_plan(p);
@@ -334,7 +427,15 @@ int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void
     int st = check_device(p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, Tth, Tph, s); });
+    cudaError_t e;
+    if (p.precision == FAVEST_BF16X6) {
+        e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_bf16(p, Tth, Tph, s); });
+        if (e == cudaSuccess) e = timed(p, KID_GEN_FWD, s, [&] { return launch_gen_lambda(p, true, s); });
+        if (e == cudaSuccess) e = timed(p, KID_GEMM_FWD, s, [&] { return launch_tc_gemm(p, true, s); });
+        if (e == cudaSuccess) e = timed(p, KID_COMBINE, s, [&] { return launch_combine_bf16(p, a, b, s); });
+        return cuda_status(e);
+    }
+    e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, Tth, Tph, s); });
     if (e == cudaSuccess) e = timed(p, KID_ANALYSIS, s, [&] { return launch_analysis_fp64(p, s); });
     if (e == cudaSuccess) e = timed(p, KID_COMBINE, s, [&] { return launch_combine_fp64(p, a, b, s); });
     return cuda_status(e);
@@ -349,7 +450,15 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
     int st = check_device(p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_fp64(p, a, b, s); });
+    cudaError_t e;
+    if (p.precision == FAVEST_BF16X6) {
+        e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_bf16(p, a, b, s); });
+        if (e == cudaSuccess) e = timed(p, KID_GEN_ADJ, s, [&] { return launch_gen_lambda(p, false, s); });
+        if (e == cudaSuccess) e = timed(p, KID_GEMM_ADJ, s, [&] { return launch_tc_gemm(p, false, s); });
+        if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_bf16(p, Tth, Tph, s); });
+        return cuda_status(e);
+    }
+    e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_fp64(p, a, b, s); });
     if (e == cudaSuccess) e = timed(p, KID_SYNTHESIS, s, [&] { return launch_synthesis_fp64(p, s); });
     if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, Tth, Tph, s); });
     return cuda_status(e);
@@ -371,7 +480,7 @@ int favest_launches_per_call(favest_plan plan, int adjoint)
 {
     if (!plan) return FAVEST_EINVAL;
     (void)adjoint;
-    return 3;
+    return plan->p.precision == FAVEST_BF16X6 ? 4 : 3;
 }
 
 int favest_status(favest_plan plan, void *stream)

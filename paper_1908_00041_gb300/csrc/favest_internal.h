@@ -40,6 +40,19 @@ struct FftPlan {
     float2 *tw32 = nullptr;    // device, same rounded to float
 };
 
+// One tensor-core GEMM output tile: out[rows][128 cols] = sum over nk K-chunks of A_c * B_c.
+struct TcItem {
+    long long a_off;    // byte offset of chunk 0 of A (three 16 KB bf16 pieces per chunk)
+    long long b_off;    // byte offset of chunk 0 of B
+    long long out_off;  // float offset of output element (row 0, col 0)
+    int nk;             // K-chunks (64 deep)
+    int rows;           // valid output rows (<= 128)
+    int a_stride;       // bytes between consecutive A chunks
+    int b_stride;       // bytes between consecutive B chunks
+    int out_ld;         // output row pitch (floats)
+    int pad;
+};
+
 struct Plan {
     int L = 0, B = 0, precision = 0, io = 0;
     int nlat = 0, nphi = 0, J = 0, has_eq = 0;
@@ -65,6 +78,20 @@ struct Plan {
     double *d_R = nullptr;        // [ntab] combine coefficient R_l^mu
     int *d_status = nullptr;      // device status word
 
+    // split-precision (BF16X6) path
+    int JP = 0;               // folded latitudes padded to a multiple of 128
+    int ncolr = 0;            // real columns per order: 8 per field, padded to 128
+    int n_tiles = 0;          // ncolr / 128
+    int nk_f = 0;             // forward K-chunks: JP / 64
+    int n_items_f = 0, n_items_a = 0;
+    void *d_lam = nullptr;        // Legendre operand tiles (bf16 x 3)
+    void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
+    void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
+    float *d_Q32 = nullptr;       // forward GEMM output [tab row][ncolr]
+    float *d_S32 = nullptr;       // adjoint GEMM output [mu][parity][JP][ncolr]
+    long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
+    TcItem *d_items_f = nullptr, *d_items_a = nullptr;
+
     // workspace
     void *d_F = nullptr;          // forward: raw longitude spectra [mu][col][nlat]
     void *d_Q = nullptr;          // scalar coefficients Q or g: [tab row][col]
@@ -82,6 +109,7 @@ struct Plan {
 
 enum KernelId {
     KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
+    KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ,
     KID_COUNT
 };
 
@@ -96,5 +124,13 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s);
 cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s);
 cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, cudaStream_t s);
+
+cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s);
+cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
+cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
+cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s);
+cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s);
+cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s);
+size_t tc_gemm_smem_bytes();
 
 }  // namespace favest

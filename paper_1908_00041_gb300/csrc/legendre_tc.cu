@@ -1,0 +1,387 @@
+// Split-precision Legendre stage on tcgen05 tensor cores (precision FAVEST_BF16X6).
+//
+// Per order mu and parity p the Legendre stage is a dense product:
+//   forward : Q[rows, n]   = sum_j  Lam[rows, j] * Fb[j, n]      (rows = l - mu of parity p)
+//   adjoint : S_p[j, n]    = sum_r  Lam[r, j]   * g[r, n]
+// Lam (the FP64 recurrence values) is produced by a generator kernel and stored as
+// three bf16 pieces (hi + mid + lo = the FP64 value truncated to 24 bits); Fb and g
+// carry three bf16 pieces as well.  The GEMM kernel forms 6 of the 9 piece products
+// (those with combined weight >= 2^-16 of the leading one).  Because the tensor core
+// accumulates in FP32 with truncation (products below one ulp of the running sum are
+// dropped), the leading hi*hi product is accumulated in a fresh TMEM buffer for each
+// K-chunk of 64 and added to an FP32 register sum (round-to-nearest) by the epilogue;
+// the five correction products, 2^-8 smaller, accumulate in TMEM over the whole K.
+//
+// Operand tiles in global memory are pre-arranged so that one K-chunk of one piece is
+// a contiguous 16 KB block in the shared-memory core-matrix layout (see tc.cuh):
+//   forward A (Lam, M = rows, K = j, MN-major): [K/8 groups][M/8 groups][8 j][8 rows]
+//   adjoint A (Lam^T, M = j, K = rows, K-major): [M/8][K/8][8 j][8 rows]
+//   B (Fb or g, K x N, MN-major):               [K/8][N/8][8 k][8 n]
+#include "favest_internal.h"
+#include "recurrence.cuh"
+#include "tc.cuh"
+
+#include <cuda_bf16.h>
+
+namespace favest {
+
+namespace {
+
+constexpr int kGenThreads = 128;
+constexpr int kChunkK = 64;                      // K depth of one operand chunk
+constexpr int kTileM = 128, kTileN = 128;
+constexpr int kPieceBytes = kTileM * kChunkK * 2;  // 16 KB (also 64 x 128 for B)
+constexpr int kPieces = 3;
+constexpr int kChunkBytes = kPieces * kPieceBytes;  // 48 KB
+
+// FP64 value -> three bf16 pieces.  The value is first truncated to FP32 with integer
+// operations (FP64->FP32 conversion instructions run on the FP64 pipe), then split
+// exactly: hi = bf16(f), mid = bf16(f - hi), lo = bf16(f - hi - mid).
+__device__ __forceinline__ float d2f_trunc(double y)
+{
+    const unsigned hi = (unsigned)__double2hiint(y), lo = (unsigned)__double2loint(y);
+    const unsigned ab = hi & 0x7fffffffu;
+    unsigned fb = ((ab - (896u << 20)) << 3) | (lo >> 29);
+    fb = (ab >= (897u << 20)) ? fb : 0u;          // |y| < 2^-126 -> 0
+    return __uint_as_float(fb | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ void split3(float f, unsigned short &h, unsigned short &m, unsigned short &l)
+{
+    __nv_bfloat16 bh = __float2bfloat16_rn(f);
+    float r1 = f - __bfloat162float(bh);
+    __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    float r2 = r1 - __bfloat162float(bm);
+    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
+}
+
+// Generator: one CTA per (mu, block of 128 folded latitudes), one latitude per thread.
+// Each thread runs the scaled FP64 recurrence over all rows l = mu..L+1 and packs, per
+// parity, 8 consecutive rows into one 16-byte core-matrix row per piece.
+//   fwd = true : forward A layout, item (mu, p, m_tile) at lam_off[mu*2+p] + m_tile*nkf*48KB
+//   fwd = false: adjoint A layout, item (mu, p, j_tile) at lam_off[mu*2+p] + j_tile*nka*48KB
+template <bool FWD>
+__global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
+    unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
+    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
+    int J, int JP)
+{
+    extern __shared__ double sm_gen[];
+    const int jblocks = JP / kGenThreads;
+    const int mu = blockIdx.x / jblocks, jb = blockIdx.x % jblocks;
+    const int j = jb * kGenThreads + threadIdx.x;
+    const int nrow = L + 2 - mu;
+    const long long t0 = tab_off(L, mu);
+    double *As = sm_gen;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
+    __syncthreads();
+
+    double x = 0.0, y1 = 0.0, y2 = 0.0;
+    int c = 1 << 20;
+    const bool live = j < J;
+    if (live) {
+        x = xj[j];
+        sectoral_start(cmu[mu], sj[j], mu, y1, c);
+    }
+    const int nk_f = JP / kChunkK;                 // forward K chunks (latitudes)
+    const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
+    const int nk_a0 = (nrow_p0 + kChunkK - 1) / kChunkK, nk_a1 = (nrow_p1 + kChunkK - 1) / kChunkK;
+
+    unsigned pk[2][kPieces][4];   // [parity][piece][4 x 2 bf16]
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < kPieces; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) pk[p][q][w] = 0u;
+
+    for (int r0 = 0; r0 < nrow; r0 += 16) {
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+            const int r = r0 + w;
+            if (r < nrow) {
+                double yl = y1;
+                if (r > 0) {
+                    yl = fma(As[r] * x, y1, -y2);
+                    y2 = y1;
+                    y1 = yl;
+                }
+                const float f = (c == 0) ? d2f_trunc(yl) : 0.0f;
+                unsigned short h, m, l;
+                split3(f, h, m, l);
+                const int p = w & 1, slot = w >> 1;         // r0 is a multiple of 16
+                const int word = slot >> 1, half = slot & 1;
+                pk[p][0][word] |= (unsigned)h << (16 * half);
+                pk[p][1][word] |= (unsigned)m << (16 * half);
+                pk[p][2][word] |= (unsigned)l << (16 * half);
+            }
+        }
+        renorm(y1, y2, c);   // growth over 16 rows stays far below 2^700
+        // flush: rows r0/2 .. r0/2+7 of each parity
+        const int rp = r0 >> 1;                        // multiple of 8
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int np = p ? nrow_p1 : nrow_p0;
+            if (rp < np) {
+                const long long base = lam_off[mu * 2 + p];
+                long long off;
+                if (FWD) {
+                    const int mt = rp / kTileM, mi = rp % kTileM;
+                    const int kc = j / kChunkK, jj = j % kChunkK;
+                    off = base + ((long long)mt * nk_f + kc) * kChunkBytes +
+                          (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
+                } else {
+                    const int nka = p ? nk_a1 : nk_a0;
+                    const int jt = j / kTileM, jj = j % kTileM;
+                    const int kc = rp / kChunkK, rr = rp % kChunkK;
+                    off = base + ((long long)jt * nka + kc) * kChunkBytes +
+                          (jj / 8) * 1024 + (rr / 8) * 128 + (jj % 8) * 16;
+                }
+#pragma unroll
+                for (int q = 0; q < kPieces; ++q) {
+                    uint4 v = make_uint4(pk[p][q][0], pk[p][q][1], pk[p][q][2], pk[p][q][3]);
+                    *reinterpret_cast<uint4 *>(lam + off + q * kPieceBytes) = v;
+                    pk[p][q][0] = pk[p][q][1] = pk[p][q][2] = pk[p][q][3] = 0u;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent GEMM: every item computes out[rows 0..127][cols 0..127] =
+//   sum_{c < nk} A_c * B_c  (three bf16 pieces each, 6 products)
+// ---------------------------------------------------------------------------
+constexpr int kStages = 2;
+constexpr int kGemmThreads = 192;   // warp 0 producer, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t kTmemCols = 512;
+constexpr int kColMain0 = 0, kColMain1 = 128, kColCorr = 256;
+
+struct GemmSmem {
+    unsigned char a[kStages][kChunkBytes];
+    unsigned char b[kStages][kChunkBytes];
+    uint64_t full[kStages], empty[kStages];
+    uint64_t dmain_full[2], dmain_empty[2], dcorr_full, dcorr_empty;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// Wait that also gives up when another role aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023) == 1023 && *abort) return false;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
+    const unsigned char *__restrict__ Abuf, const unsigned char *__restrict__ Bbuf,
+    const TcItem *__restrict__ items, int nitems, float *__restrict__ out, int a_mn_major,
+    int *__restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    GemmSmem &S = *reinterpret_cast<GemmSmem *>(sm_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) tc::tmem_alloc(&S.tmem_base, kTmemCols);
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&S.full[s], 1);
+            tc::mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&S.dmain_full[b], 1);
+            tc::mbar_init(&S.dmain_empty[b], 4);
+        }
+        tc::mbar_init(&S.dcorr_full, 1);
+        tc::mbar_init(&S.dcorr_empty, 4);
+        S.abort = 0;
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem_base;
+    volatile int *abort = &S.abort;
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            uint32_t use[kStages] = {0, 0};
+            int stage = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const TcItem I = items[it];
+                for (int c = 0; c < I.nk; ++c) {
+                    if (!wait_or_abort(&S.empty[stage], (use[stage] & 1) ^ 1, abort)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&S.full[stage], 2 * kChunkBytes);
+                    tc::bulk_g2s(S.a[stage], Abuf + I.a_off + (long long)c * I.a_stride, kChunkBytes,
+                                 &S.full[stage]);
+                    tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkBytes,
+                                 &S.full[stage]);
+                    use[stage]++;
+                    stage = (stage + 1) % kStages;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16(kTileM, kTileN, a_mn_major, 1) | (1u << 7) | (1u << 10);
+            uint32_t use[kStages] = {0, 0}, mu_use[2] = {0, 0}, corr_use = 0;
+            int stage = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const TcItem I = items[it];
+                if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                for (int c = 0; c < I.nk; ++c) {
+                    const int buf = c & 1;
+                    if (!wait_or_abort(&S.full[stage], use[stage] & 1, abort) ||
+                        !wait_or_abort(&S.dmain_empty[buf], (mu_use[buf] & 1) ^ 1, abort)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(S.a[stage]), b0 = tc::smem_u32(S.b[stage]);
+                    const uint32_t dmain = tmem + (buf ? kColMain1 : kColMain0), dcorr = tmem + kColCorr;
+#pragma unroll
+                    for (int s = 0; s < kChunkK / 16; ++s) {
+                        uint64_t ad[3], bd[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            // A: MN-major (fwd): K-step = 2 K-groups of 2048 B; LBO 2048, SBO 128
+                            //    K-major (adj):  K-step = 2 K-groups of 128 B;   LBO 128, SBO 1024
+                            ad[q] = a_mn_major ? tc::sdesc(a0 + q * kPieceBytes + s * 4096, 2048, 128)
+                                               : tc::sdesc(a0 + q * kPieceBytes + s * 256, 128, 1024);
+                            bd[q] = tc::sdesc(b0 + q * kPieceBytes + s * 4096, 2048, 128);
+                        }
+                        tc::mma_f16(dmain, ad[0], bd[0], idesc, s > 0);
+                        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+                        tc::mma_f16(dcorr, ad[0], bd[1], idesc, acc);
+                        tc::mma_f16(dcorr, ad[1], bd[0], idesc, 1);
+                        tc::mma_f16(dcorr, ad[0], bd[2], idesc, 1);
+                        tc::mma_f16(dcorr, ad[1], bd[1], idesc, 1);
+                        tc::mma_f16(dcorr, ad[2], bd[0], idesc, 1);
+                    }
+                    tc::mma_commit(&S.empty[stage]);
+                    tc::mma_commit(&S.dmain_full[buf]);
+                    use[stage]++;
+                    mu_use[buf]++;
+                    stage = (stage + 1) % kStages;
+                }
+                if (*abort) break;
+                tc::mma_commit(&S.dcorr_full);
+                corr_use++;
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2,3,0,1) ----------------
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        uint32_t mu_use[2] = {0, 0}, corr_use = 0;
+        float acc[kTileN];
+        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            const TcItem I = items[it];
+#pragma unroll
+            for (int i = 0; i < kTileN; ++i) acc[i] = 0.f;
+            bool ok = true;
+            for (int c = 0; c < I.nk; ++c) {
+                const int buf = c & 1;
+                if (!wait_or_abort(&S.dmain_full[buf], mu_use[buf] & 1, abort)) { ok = false; break; }
+                tc::fence_after_sync();
+                const uint32_t col0 = tmem + lane_base + (buf ? kColMain1 : kColMain0);
+#pragma unroll
+                for (int q = 0; q < kTileN / 32; ++q) {
+                    float v[32];
+                    tc::tmem_ld32(col0 + q * 32, v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) acc[q * 32 + i] += v[i];
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.dmain_empty[buf]);
+                mu_use[buf]++;
+            }
+            if (!ok || !wait_or_abort(&S.dcorr_full, corr_use & 1, abort)) {
+                set_status(status, FAVEST_ETIMEOUT);
+                *abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int q = 0; q < kTileN / 32; ++q) {
+                float v[32];
+                tc::tmem_ld32(tmem + lane_base + kColCorr + q * 32, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[q * 32 + i] += v[i];
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&S.dcorr_empty);
+            corr_use++;
+            if (row < I.rows) {
+                float4 *dst = reinterpret_cast<float4 *>(out + I.out_off + (long long)row * I.out_ld);
+#pragma unroll
+                for (int i = 0; i < kTileN / 4; ++i)
+                    dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s)
+{
+    const int jblocks = p.JP / kGenThreads;
+    const int grid = (p.L + 1) * jblocks;
+    const size_t smem = (size_t)(p.L + 2) * sizeof(double);
+    if (fwd)
+        k_gen_lambda<true><<<grid, kGenThreads, smem, s>>>((unsigned char *)p.d_lam, p.d_lam_off_f, p.d_x,
+                                                           p.d_sin, p.d_cmu, p.d_A, p.L, p.J, p.JP);
+    else
+        k_gen_lambda<false><<<grid, kGenThreads, smem, s>>>((unsigned char *)p.d_lam, p.d_lam_off_a, p.d_x,
+                                                            p.d_sin, p.d_cmu, p.d_A, p.L, p.J, p.JP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s)
+{
+    const size_t smem = sizeof(GemmSmem) + 1024;
+    auto k = k_tc_gemm;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nitems = fwd ? p.n_items_f : p.n_items_a;
+    const int grid = nitems < p.num_sms ? nitems : p.num_sms;
+    if (grid <= 0) return cudaSuccess;
+    k<<<grid, kGemmThreads, smem, s>>>((const unsigned char *)p.d_lam,
+                                       (const unsigned char *)(fwd ? p.d_Fb : p.d_gb),
+                                       fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
+                                       fwd ? 1 : 0, p.d_status);
+    return cudaGetLastError();
+}
+
+size_t tc_gemm_smem_bytes() { return sizeof(GemmSmem) + 1024; }
+
+}  // namespace favest
