@@ -67,7 +67,13 @@ __device__ __forceinline__ void split3u(float f, unsigned short &h, unsigned sho
     l = __bfloat16_as_ushort(bl);
 }
 
-// grid (L+1, B): threads over rows l' = mu..L+1
+// grid (L+1, B): threads over rows l' = mu..L+1.
+// Order 0 is special: sin(theta) d_theta lambda_l^0 vanishes at the poles, so forming
+// G(j, 0) as (sum_l lambda_l^0 g_l) / sin(theta_j) would amplify rounding errors near
+// the poles by 1/sin(theta_1).  Instead d_theta lambda_l^0 = sqrt(l(l+1)) lambda_l^1 gives
+//   G_th(j, 0) = sum_l a_l0 lambda_l^1(theta_j),  G_ph(j, 0) = sum_l b_l0 lambda_l^1(theta_j)
+// with no division: order 0 is synthesised on the order-1 Legendre tiles (rows l = 1..L+1)
+// and the inverse FFT stage skips the 1/sin(theta) factor for it.
 __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__restrict__ b,
                                  unsigned char *__restrict__ gb, const long long *__restrict__ g_off,
                                  const double *__restrict__ P, const double *__restrict__ M,
@@ -75,13 +81,20 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
 {
     const int mu = blockIdx.x, bi = blockIdx.y;
     const long long t0 = tab_off(L, mu);
-    const int nrow = L + 2 - mu;
+    const int nrow = L + 2 - (mu == 0 ? 1 : mu);
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
     const int nka0 = (nrow_p0 + 63) / 64, nka1 = (nrow_p1 + 63) / 64;
     const int nt = bi / 16, bg = bi % 16;
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
-        const int l = mu + r;
+        const int l = (mu == 0 ? 1 : mu) + r;
         float v[8];
+        if (mu == 0) {
+            // the order-1 tiles hold lambda_l^1 / kappa_l^(1); kappa^(1) = R^(1) sqrt(l(l+1))
+            const double k1 = (l <= L) ? R[tab_off(L, 1) + (l - 1)] * sqrt((double)l * (l + 1.0)) : 0.0;
+            const float2 a0 = cf(a, L, l, 0, bi, K), b0 = cf(b, L, l, 0, bi, K);
+            v[0] = (float)(k1 * a0.x); v[1] = (float)(k1 * a0.y); v[2] = 0.f; v[3] = 0.f;
+            v[4] = (float)(k1 * b0.x); v[5] = (float)(k1 * b0.y); v[6] = 0.f; v[7] = 0.f;
+        } else
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int m = s ? -mu : mu;

@@ -191,21 +191,32 @@ int alloc_workspace_bf16(Plan &p)
     std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
     long long lam_f = 0, lam_a = 0, gsz = 0;
     std::vector<TcItem> itf, ita;
+    auto nrow_p = [&](int mu, int par) { const int n = L + 2 - mu; return par ? n / 2 : (n + 1) / 2; };
+    // pass 1: operand storage offsets per (mu, parity)
     for (int mu = 0; mu <= L; ++mu) {
-        const int nrow = L + 2 - mu;
         for (int par = 0; par < 2; ++par) {
-            const int np = par ? nrow / 2 : (nrow + 1) / 2;
-            const int mt = (np + 127) / 128;
-            const int nka = (np + 63) / 64;
-            const int jt = p.JP / 128;
+            const int np = nrow_p(mu, par);
+            // the adjoint of order 0 runs on the order-1 Legendre functions (see uncombine)
+            const int npa = nrow_p(mu == 0 ? 1 : mu, par);
             const int idx = mu * 2 + par;
             off_f[idx] = lam_f;
             off_a[idx] = lam_a;
             off_g[idx] = gsz;
+            lam_f += (long long)((np + 127) / 128) * p.nk_f * CH;
+            lam_a += (long long)(p.JP / 128) * ((np + 63) / 64) * CH;
+            gsz += (long long)p.n_tiles * ((npa + 63) / 64) * CH;
+        }
+    }
+    // pass 2: GEMM work items
+    for (int mu = 0; mu <= L; ++mu) {
+        for (int par = 0; par < 2; ++par) {
+            const int idx = mu * 2 + par;
+            const int np = nrow_p(mu, par);
+            const int mt = (np + 127) / 128;
             for (int m = 0; m < mt; ++m)
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = lam_f + (long long)m * p.nk_f * CH;
+                    I.a_off = off_f[idx] + (long long)m * p.nk_f * CH;
                     I.b_off = (((long long)idx * p.n_tiles + nt) * p.nk_f) * CH;
                     I.out_off = (tab_off(L, mu) + par + 256LL * m) * p.ncolr + 128LL * nt;
                     I.nk = p.nk_f;
@@ -215,11 +226,13 @@ int alloc_workspace_bf16(Plan &p)
                     I.out_ld = 2 * p.ncolr;
                     itf.push_back(I);
                 }
-            for (int t = 0; t < jt; ++t)
+            const int amu = mu == 0 ? 1 : mu;
+            const int nka = (nrow_p(amu, par) + 63) / 64;
+            for (int t = 0; t < p.JP / 128; ++t)
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = lam_a + (long long)t * nka * CH;
-                    I.b_off = gsz + (long long)nt * nka * CH;
+                    I.a_off = off_a[amu * 2 + par] + (long long)t * nka * CH;
+                    I.b_off = off_g[idx] + (long long)nt * nka * CH;
                     I.out_off = ((long long)idx * p.JP + 128LL * t) * p.ncolr + 128LL * nt;
                     I.nk = nka;
                     I.rows = 128;
@@ -228,9 +241,6 @@ int alloc_workspace_bf16(Plan &p)
                     I.out_ld = p.ncolr;
                     ita.push_back(I);
                 }
-            lam_f += (long long)mt * p.nk_f * CH;
-            lam_a += (long long)jt * nka * CH;
-            gsz += (long long)p.n_tiles * nka * CH;
         }
     }
     // heaviest items first (adjoint items differ in K depth)

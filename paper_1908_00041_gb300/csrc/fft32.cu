@@ -184,6 +184,8 @@ __global__ void __launch_bounds__(256) k_fft_inv_bf16(
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
+        // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
+        const float sc = mu == 0 ? 1.0f : is;
         const float4 *e = reinterpret_cast<const float4 *>(S32 + (((size_t)mu * 2 + 0) * JP + j) * ncolr + 8 * b);
         const float4 *o = reinterpret_cast<const float4 *>(S32 + (((size_t)mu * 2 + 1) * JP + j) * ncolr + 8 * b);
         float4 e0 = e[0], e1 = e[1], o0 = o[0], o1 = o[1];
@@ -196,8 +198,8 @@ __global__ void __launch_bounds__(256) k_fft_inv_bf16(
                 if (mu == 0 && s == 1) continue;
                 const int bin = s ? n - mu : mu;
                 const int k = c * 4 + s * 2;
-                buf0[c * n + bin] = make_float2((ev[k] + ov[k]) * is, (ev[k + 1] + ov[k + 1]) * is);
-                if (!eq) buf0[(2 + c) * n + bin] = make_float2((ev[k] - ov[k]) * is, (ev[k + 1] - ov[k + 1]) * is);
+                buf0[c * n + bin] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
+                if (!eq) buf0[(2 + c) * n + bin] = make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
             }
         }
     }
