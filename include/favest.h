@@ -170,6 +170,33 @@ int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *
  */
 int favest_probe_peaks(double *fp64_tflops, double *fp32_tflops);
 
+/*
+ * FwdVSHT in FP64 without allocating device memory (this entry point has no
+ * counterpart in the paper; it serves callers that cannot call cudaMalloc where they
+ * need the transform -- inside a stream capture that must not allocate, in real-time
+ * loops that cannot risk allocation latency or failure, or in plug-ins whose device
+ * memory is reserved by someone else's pool).
+ *
+ * Computes exactly what favest_fwd computes for an FP64 plan with the built-in
+ * Gauss-Legendre grid and FAVEST_IO_C128 data: Tth, Tph device [batch][L+1][2(L+1)]
+ * complex double in, a, b device [batch][L^2+2L] complex double out (16-byte
+ * aligned), asynchronously on `stream`.
+ *
+ * Scratch: a single file-scope device array of favest_noalloc_scratch_bytes() = 32 MB,
+ * held by every GPU that loads the library until the process exits.  A request whose
+ * scratch (grid and recurrence tables, spectra, scalar sums; about
+ * 96 (L+1)^2 batch + 24 (L+1)^2 bytes) exceeds it, or L > 1023, returns
+ * FAVEST_EINVAL before anything is launched.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call rewrites the tables it needs, but all calls
+ * share the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ */
+int favest_fwd_fp64_noalloc(int L, int batch, const void *Tth, const void *Tph, void *a, void *b,
+                            void *stream);
+size_t favest_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

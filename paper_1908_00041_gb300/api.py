@@ -74,6 +74,8 @@ def lib(build_if_missing=False):
             L.favest_strerror.restype = ctypes.c_char_p
             L.favest_launches_per_call.argtypes = [vp, i]
             L.favest_probe_peaks.argtypes = [d, d]
+            L.favest_fwd_fp64_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp]
+            L.favest_noalloc_scratch_bytes.restype = ctypes.c_size_t
             L.favest_profile_enable.argtypes = [vp, i]
             L.favest_profile_read.argtypes = [vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_longlong)]
@@ -180,6 +182,17 @@ def favest_profile_read(plan, max_kernels=16):
         nm = raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
         out[nm] = (ms[i], cnt[i])
     return out
+
+
+def favest_fwd_fp64_noalloc(L, batch, Tth, Tph, a, b, stream=None):
+    """FP64 forward transform using only the library's static 32 MB device scratch
+    (no device allocation); see include/favest.h."""
+    _check(lib().favest_fwd_fp64_noalloc(int(L), int(batch), _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b),
+                                         _stream(stream)), "favest_fwd_fp64_noalloc")
+
+
+def favest_noalloc_scratch_bytes():
+    return lib().favest_noalloc_scratch_bytes()
 
 
 def favest_probe_peaks():
