@@ -107,7 +107,8 @@ int favest_plan_create(int L, int batch, int precision, int io_type,
  * FwdVSHT (Def. FwdVSHT, eq. fwdvsht2) of `batch` fields.
  *   Tth, Tph: device, [batch][nlat][nphi] complex (plan io type), read only.
  *   a, b:     device, [batch][L^2+2L] complex (plan io type), written.
- * Pointers must be aligned to the complex element size.  Asynchronous on `stream`.
+ * Pointers must be aligned to the complex element size (to 16 bytes for
+ * FAVEST_BF16X6 plans).  Asynchronous on `stream`.
  */
 int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b,
                void *stream);

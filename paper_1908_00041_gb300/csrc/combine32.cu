@@ -13,37 +13,41 @@ namespace {
 
 constexpr int kChunkBytes = 3 * 16384;
 
-// grid.x over (b, l): one CTA per (field, degree); threads over mu = 0..l
+// grid.x over (b, l): one CTA per (field, degree); threads over mu = 0..l.
+// Q = [field][l][mu][8] (l = 0..L+1, mu = 0..L): consecutive threads read consecutive
+// 32-byte entries and write consecutive coefficients.
 __global__ void k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a, float2 *__restrict__ bo,
-                               const double *__restrict__ P, const double *__restrict__ M,
-                               const double *__restrict__ R, int L, int K, int ncolr)
+                               const float *__restrict__ P, const float *__restrict__ M,
+                               const float *__restrict__ R, int L, int K)
 {
     const int bi = blockIdx.x / L, l = blockIdx.x % L + 1;
+    const size_t L1 = (size_t)L + 1;
+    const float *qb = Q + (size_t)bi * (L + 2) * L1 * 8;
     for (int mu = threadIdx.x; mu <= l; mu += blockDim.x) {
         const long long row = tab_off(L, mu) + (l - mu);
-        const double Pl = P[row], Ml = M[row], Rl = R[row];
-        const float *q1 = Q + (size_t)(row + 1) * ncolr + 8 * bi;
-        const float *q0 = Q + (size_t)row * ncolr + 8 * bi;
-        const float *qm = Q + (size_t)(row - 1) * ncolr + 8 * bi;
+        const float Pl = P[row], Ml = M[row], Rl = R[row];
+        const float *q1 = qb + ((size_t)(l + 1) * L1 + mu) * 8;
+        const float *q0 = qb + ((size_t)l * L1 + mu) * 8;
+        const float *qm = qb + ((size_t)(l - 1) * L1 + mu) * 8;
         const bool has_m = l > mu;
         for (int s = 0; s < 2; ++s) {
             if (mu == 0 && s == 1) continue;
             const int m = s ? -mu : mu;
-            const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
-            const double Rm = Rl * m;
+            const float sg = (s && (mu & 1)) ? -1.f : 1.f;
+            const float Rm = Rl * (float)m;
             // th: cols s*2 + {0,1}; ph: 4 + s*2 + {0,1}
             const int ct = s * 2, cp = 4 + s * 2;
-            double t1x = q1[ct], t1y = q1[ct + 1], p1x = q1[cp], p1y = q1[cp + 1];
-            double t0x = q0[ct], t0y = q0[ct + 1], p0x = q0[cp], p0y = q0[cp + 1];
-            double tmx = has_m ? qm[ct] : 0.0, tmy = has_m ? qm[ct + 1] : 0.0;
-            double pmx = has_m ? qm[cp] : 0.0, pmy = has_m ? qm[cp + 1] : 0.0;
-            double ax = sg * (Pl * t1x - Ml * tmx + Rm * p0y);
-            double ay = sg * (Pl * t1y - Ml * tmy - Rm * p0x);
-            double bx = sg * (-Rm * t0y + Pl * p1x - Ml * pmx);
-            double by = sg * (Rm * t0x + Pl * p1y - Ml * pmy);
+            const float t1x = q1[ct], t1y = q1[ct + 1], p1x = q1[cp], p1y = q1[cp + 1];
+            const float t0x = q0[ct], t0y = q0[ct + 1], p0x = q0[cp], p0y = q0[cp + 1];
+            const float tmx = has_m ? qm[ct] : 0.f, tmy = has_m ? qm[ct + 1] : 0.f;
+            const float pmx = has_m ? qm[cp] : 0.f, pmy = has_m ? qm[cp + 1] : 0.f;
+            const float ax = sg * fmaf(Pl, t1x, fmaf(-Ml, tmx, Rm * p0y));
+            const float ay = sg * fmaf(Pl, t1y, fmaf(-Ml, tmy, -Rm * p0x));
+            const float bx = sg * fmaf(Pl, p1x, fmaf(-Ml, pmx, -Rm * t0y));
+            const float by = sg * fmaf(Pl, p1y, fmaf(-Ml, pmy, Rm * t0x));
             const size_t k = (size_t)bi * K + l * l + l + m - 1;
-            a[k] = make_float2((float)ax, (float)ay);
-            bo[k] = make_float2((float)bx, (float)by);
+            a[k] = make_float2(ax, ay);
+            bo[k] = make_float2(bx, by);
         }
     }
 }
@@ -76,8 +80,9 @@ __device__ __forceinline__ void split3u(float f, unsigned short &h, unsigned sho
 // and the inverse FFT stage skips the 1/sin(theta) factor for it.
 __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__restrict__ b,
                                  unsigned char *__restrict__ gb, const long long *__restrict__ g_off,
-                                 const double *__restrict__ P, const double *__restrict__ M,
-                                 const double *__restrict__ R, int L, int K, int n_tiles)
+                                 const float *__restrict__ P, const float *__restrict__ M,
+                                 const float *__restrict__ R, const float *__restrict__ k1tab, int L, int K,
+                                 int n_tiles)
 {
     const int mu = blockIdx.x, bi = blockIdx.y;
     const long long t0 = tab_off(L, mu);
@@ -89,33 +94,33 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
         const int l = (mu == 0 ? 1 : mu) + r;
         float v[8];
         if (mu == 0) {
-            // the order-1 tiles hold lambda_l^1 / kappa_l^(1); kappa^(1) = R^(1) sqrt(l(l+1))
-            const double k1 = (l <= L) ? R[tab_off(L, 1) + (l - 1)] * sqrt((double)l * (l + 1.0)) : 0.0;
+            // the order-1 tiles hold lambda_l^1 / kappa_l^(1)
+            const float k1 = (l <= L) ? k1tab[l] : 0.f;
             const float2 a0 = cf(a, L, l, 0, bi, K), b0 = cf(b, L, l, 0, bi, K);
-            v[0] = (float)(k1 * a0.x); v[1] = (float)(k1 * a0.y); v[2] = 0.f; v[3] = 0.f;
-            v[4] = (float)(k1 * b0.x); v[5] = (float)(k1 * b0.y); v[6] = 0.f; v[7] = 0.f;
+            v[0] = k1 * a0.x; v[1] = k1 * a0.y; v[2] = 0.f; v[3] = 0.f;
+            v[4] = k1 * b0.x; v[5] = k1 * b0.y; v[6] = 0.f; v[7] = 0.f;
         } else
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int m = s ? -mu : mu;
-            double gtx = 0, gty = 0, gpx = 0, gpy = 0;
+            float gtx = 0.f, gty = 0.f, gpx = 0.f, gpy = 0.f;
             if (!(mu == 0 && s == 1)) {
-                const double sg = (s && (mu & 1)) ? -1.0 : 1.0;
-                const double Pm = (r > 0) ? P[t0 + r - 1] : 0.0;
-                const double Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.0;
-                const double Rl = (l <= L) ? R[t0 + r] * m : 0.0;
+                const float sg = (s && (mu & 1)) ? -1.f : 1.f;
+                const float Pm = (r > 0) ? P[t0 + r - 1] : 0.f;
+                const float Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.f;
+                const float Rl = (l <= L) ? R[t0 + r] * (float)m : 0.f;
                 float2 am1 = cf(a, L, l - 1, m, bi, K), ap1 = cf(a, L, l + 1, m, bi, K);
                 float2 bm1 = cf(b, L, l - 1, m, bi, K), bp1 = cf(b, L, l + 1, m, bi, K);
                 float2 a0 = cf(a, L, l, m, bi, K), b0 = cf(b, L, l, m, bi, K);
-                gtx = sg * (Pm * am1.x - Mp * ap1.x + Rl * b0.y);
-                gty = sg * (Pm * am1.y - Mp * ap1.y - Rl * b0.x);
-                gpx = sg * (-Rl * a0.y + Pm * bm1.x - Mp * bp1.x);
-                gpy = sg * (Rl * a0.x + Pm * bm1.y - Mp * bp1.y);
+                gtx = sg * fmaf(Pm, am1.x, fmaf(-Mp, ap1.x, Rl * b0.y));
+                gty = sg * fmaf(Pm, am1.y, fmaf(-Mp, ap1.y, -Rl * b0.x));
+                gpx = sg * fmaf(Pm, bm1.x, fmaf(-Mp, bp1.x, -Rl * a0.y));
+                gpy = sg * fmaf(Pm, bm1.y, fmaf(-Mp, bp1.y, Rl * a0.x));
             }
-            v[0 * 4 + s * 2 + 0] = (float)gtx;
-            v[0 * 4 + s * 2 + 1] = (float)gty;
-            v[1 * 4 + s * 2 + 0] = (float)gpx;
-            v[1 * 4 + s * 2 + 1] = (float)gpy;
+            v[0 * 4 + s * 2 + 0] = gtx;
+            v[0 * 4 + s * 2 + 1] = gty;
+            v[1 * 4 + s * 2 + 0] = gpx;
+            v[1 * 4 + s * 2 + 1] = gpy;
         }
         const int p = r & 1, rp = r >> 1;
         const int nka = p ? nka1 : nka0;
@@ -144,8 +149,8 @@ cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
 {
     const int K = p.L * p.L + 2 * p.L;
     const int th = p.L >= 128 ? 128 : 32;
-    k_combine_bf16<<<p.B * p.L, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P, p.d_M,
-                                             p.d_R, p.L, K, p.ncolr);
+    k_combine_bf16<<<p.B * p.L, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32,
+                                             p.d_M32, p.d_R32, p.L, K);
     return cudaGetLastError();
 }
 
@@ -155,7 +160,7 @@ cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, c
     dim3 grid(p.L + 1, p.B);
     const int th = p.L + 2 >= 256 ? 256 : 64;
     k_uncombine_bf16<<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb,
-                                         p.d_g_off, p.d_P, p.d_M, p.d_R, p.L, K, p.n_tiles);
+                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.n_tiles);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "favest_internal.h"
 
 using namespace favest;
@@ -107,7 +109,8 @@ void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
-                    p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a};
+                    p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
+                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -160,12 +163,27 @@ int build_tables(Plan &p)
     if ((e = upload(&p.d_cmu, cmu)) || (e = upload(&p.d_A, A)) || (e = upload(&p.d_P, P)) ||
         (e = upload(&p.d_M, M)) || (e = upload(&p.d_R, R)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    if (p.precision == FAVEST_BF16X6) {
+        std::vector<float> P32(ntab), M32(ntab), R32(ntab), k1(L + 1, 0.f);
+        for (long long t = 0; t < ntab; ++t) {
+            P32[t] = (float)P[t];
+            M32[t] = (float)M[t];
+            R32[t] = (float)R[t];
+        }
+        for (int l = 1; l <= L; ++l) k1[l] = (float)(R[tab_off(L, 1) + (l - 1)] * std::sqrt((double)l * (l + 1.0)));
+        if ((e = upload(&p.d_P32, P32)) || (e = upload(&p.d_M32, M32)) || (e = upload(&p.d_R32, R32)) ||
+            (e = upload(&p.d_k1, k1)))
+            return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    }
 
     // FFT twiddles exp(-2 pi i k / n), angles reduced exactly
     const int n = p.nphi;
     p.fft.n = n;
     p.fft.nstages = factorize(n, p.fft.radix);
     if (p.fft.nstages < 0) return FAVEST_EUNSUPPORTED;
+    if (p.precision == FAVEST_BF16X6)
+        for (int st = 0; st < p.fft.nstages; ++st)
+            if (p.fft.radix[st] > 128) return FAVEST_EUNSUPPORTED;
     std::vector<double2> tw(n);
     std::vector<float2> tw32(n);
     for (int k = 0; k < n; ++k) {
@@ -176,10 +194,58 @@ int build_tables(Plan &p)
     }
     if ((e = upload(&p.fft.tw64, tw)) || (e = upload(&p.fft.tw32, tw32)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    // in-place decimation-in-frequency FFT leaves frequency m at position pos(m):
+    //   pos(m; n, r0 r1 ..) = (m mod r0) * (n / r0) + pos(m div r0; n / r0, r1 ..)
+    // The split path transforms power-of-two lengths 2^6..2^11 with its own radix-16
+    // engine (natural order in and out); other lengths use the mixed-radix list and perm.
+    p.fft_log2n = 0;
+    if (p.precision == FAVEST_BF16X6 && n >= 64 && n <= 2048 && (n & (n - 1)) == 0)
+        while ((1 << p.fft_log2n) < n) ++p.fft_log2n;
+    std::vector<int> perm(n);
+    for (int m = 0; m < n; ++m) {
+        int pos = 0, len = n, mm = m;
+        for (int st = 0; st < p.fft.nstages; ++st) {
+            const int r = p.fft.radix[st];
+            len /= r;
+            pos += (mm % r) * len;
+            mm /= r;
+        }
+        perm[m] = pos;
+    }
+    if ((e = upload(&p.d_perm, perm)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     return FAVEST_OK;
 }
 
+// Tensor map of the forward B operand Fb[j/8][field][j%8][mu][parity][piece][8] (bf16):
+// a box {8, 1, 8, 16, 8} at (x0 = (parity*3 + piece)*8, mu, 0, 16*field_tile, 8*K_chunk)
+// lands in shared memory as [K/8][N/8][8 j][8 n], the MN-major core-matrix layout.
+int make_fb_tensor_map(Plan &p)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return FAVEST_EUNSUPPORTED;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t L1 = (cuuint64_t)(p.L + 1);
+    cuuint64_t dims[5] = {48, L1, 8, (cuuint64_t)p.nf, (cuuint64_t)(p.JP / 8)};
+    cuuint64_t strides[4] = {96, 96 * L1, 768 * L1, 768 * L1 * (cuuint64_t)p.nf};
+    cuuint32_t box[5] = {8, 1, 8, 16, 8};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = encode(&p.tmap_fb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p.d_Fb, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
+}
+
 // Split-precision path: operand tile offsets, GEMM work items, buffers.
+//   Lam (A operands): contiguous 48 KB chunks (three 16 KB bf16 pieces), bulk copies
+//   Fb  (forward B):  [JP/8][nf][8][L+1][2][3][8] bf16, loaded through the tensor map
+//   g   (adjoint B):  contiguous 48 KB chunks
+//   Q32 (forward out): [nf][L+2][L+1][8] fp32, entry (field, l, mu)
+//   S32 (adjoint out): [JP][nf][L+1][2][8] fp32, entry (latitude, field, mu, parity)
 int alloc_workspace_bf16(Plan &p)
 {
     const int L = p.L;
@@ -187,7 +253,9 @@ int alloc_workspace_bf16(Plan &p)
     p.JP = (p.J + 127) / 128 * 128;
     p.ncolr = (8 * p.B + 127) / 128 * 128;
     p.n_tiles = p.ncolr / 128;
+    p.nf = p.ncolr / 8;
     p.nk_f = p.JP / 64;
+    const long long L1 = L + 1, L2 = L + 2;
     std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
     long long lam_f = 0, lam_a = 0, gsz = 0;
     std::vector<TcItem> itf, ita;
@@ -217,13 +285,18 @@ int alloc_workspace_bf16(Plan &p)
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
                     I.a_off = off_f[idx] + (long long)m * p.nk_f * CH;
-                    I.b_off = (((long long)idx * p.n_tiles + nt) * p.nk_f) * CH;
-                    I.out_off = (tab_off(L, mu) + par + 256LL * m) * p.ncolr + 128LL * nt;
+                    I.a_stride = (int)CH;
+                    I.b_tma = 1;
+                    I.bx = par * 3 * 8;
+                    I.by = 16 * nt;
+                    I.bz0 = 0;
+                    I.bw = mu;
+                    const long long l0 = mu + par + 256LL * m;       // degree of output row 0
+                    I.out_off = ((16LL * nt * L2 + l0) * L1 + mu) * 8;
+                    I.out_ld = 2 * L1 * 8;
+                    I.col_gs = L2 * L1 * 8;
                     I.nk = p.nk_f;
                     I.rows = np - 128 * m < 128 ? np - 128 * m : 128;
-                    I.a_stride = (int)CH;
-                    I.b_stride = (int)CH;
-                    I.out_ld = 2 * p.ncolr;
                     itf.push_back(I);
                 }
             const int amu = mu == 0 ? 1 : mu;
@@ -233,12 +306,14 @@ int alloc_workspace_bf16(Plan &p)
                     TcItem I{};
                     I.a_off = off_a[amu * 2 + par] + (long long)t * nka * CH;
                     I.b_off = off_g[idx] + (long long)nt * nka * CH;
-                    I.out_off = ((long long)idx * p.JP + 128LL * t) * p.ncolr + 128LL * nt;
-                    I.nk = nka;
-                    I.rows = 128;
                     I.a_stride = (int)CH;
                     I.b_stride = (int)CH;
-                    I.out_ld = p.ncolr;
+                    I.b_tma = 0;
+                    I.out_off = (((128LL * t) * p.nf + 16LL * nt) * L1 + mu) * 16 + par * 8;
+                    I.out_ld = (long long)p.nf * L1 * 16;
+                    I.col_gs = L1 * 16;
+                    I.nk = nka;
+                    I.rows = 128;
                     ita.push_back(I);
                 }
         }
@@ -248,9 +323,9 @@ int alloc_workspace_bf16(Plan &p)
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
     const size_t lam_bytes = (size_t)(lam_f > lam_a ? lam_f : lam_a);
-    const size_t fb_bytes = (size_t)(2 * (L + 1)) * p.n_tiles * p.nk_f * CH;
-    const size_t q_bytes = (size_t)p.ntab * p.ncolr * sizeof(float);
-    const size_t s_bytes = (size_t)(2 * (L + 1)) * p.JP * p.ncolr * sizeof(float);
+    const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 96;
+    const size_t q_bytes = (size_t)p.nf * L2 * L1 * 8 * sizeof(float);
+    const size_t s_bytes = (size_t)p.JP * p.nf * L1 * 16 * sizeof(float);
     if (cudaMalloc(&p.d_lam, lam_bytes) != cudaSuccess || cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         cudaMalloc(&p.d_gb, (size_t)gsz) != cudaSuccess || cudaMalloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
@@ -258,18 +333,20 @@ int alloc_workspace_bf16(Plan &p)
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
-    // padded operand positions (latitudes >= J, rows beyond each order's range) must
-    // hold zeros; they are never written afterwards
+    // padded operand positions (latitudes >= J, fields >= B, rows beyond each order's
+    // range) must hold zeros; they are never written afterwards
     if (cudaMemset(p.d_lam, 0, lam_bytes) != cudaSuccess || cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
         cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess || cudaMemset(p.d_status, 0, sizeof(int)) != cudaSuccess)
         return FAVEST_ECUDA;
     cudaError_t e;
-    std::vector<TcItem> all;
     if ((e = upload(&p.d_lam_off_f, off_f)) || (e = upload(&p.d_lam_off_a, off_a)) ||
         (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     p.ws_bytes = lam_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
-    return FAVEST_OK;
+    const int pst = build_polar_tables(p);
+    if (pst != FAVEST_OK) return pst;
+    p.ws_bytes += (size_t)p.pol_jc * (L + 1) * p.pol_muc * sizeof(float2);
+    return make_fb_tensor_map(p);
 }
 
 int alloc_workspace(Plan &p)
@@ -301,7 +378,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_EC
 
 const char *kKernelNames[KID_COUNT] = {
     "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
-    "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj",
+    "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj", "polar_patch",
 };
 
 cudaEvent_t take_event(Plan &p)
@@ -432,7 +509,7 @@ int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
     Plan &p = plan->p;
-    size_t el = p.io == FAVEST_IO_C128 ? 16 : 8;
+    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
     if (st) return st;
@@ -455,7 +532,7 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
     Plan &p = plan->p;
-    size_t el = p.io == FAVEST_IO_C128 ? 16 : 8;
+    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
     if (st) return st;
@@ -465,6 +542,8 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
         e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_bf16(p, a, b, s); });
         if (e == cudaSuccess) e = timed(p, KID_GEN_ADJ, s, [&] { return launch_gen_lambda(p, false, s); });
         if (e == cudaSuccess) e = timed(p, KID_GEMM_ADJ, s, [&] { return launch_tc_gemm(p, false, s); });
+        if (e == cudaSuccess && p.pol_jc > 0)
+            e = timed(p, KID_POLAR, s, [&] { return launch_polar_patch(p, a, b, s); });
         if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_bf16(p, Tth, Tph, s); });
         return cuda_status(e);
     }
@@ -489,8 +568,8 @@ size_t favest_plan_workspace_bytes(favest_plan plan) { return plan ? plan->p.ws_
 int favest_launches_per_call(favest_plan plan, int adjoint)
 {
     if (!plan) return FAVEST_EINVAL;
-    (void)adjoint;
-    return plan->p.precision == FAVEST_BF16X6 ? 4 : 3;
+    if (plan->p.precision != FAVEST_BF16X6) return 3;
+    return (adjoint && plan->p.pol_jc > 0) ? 5 : 4;
 }
 
 int favest_status(favest_plan plan, void *stream)

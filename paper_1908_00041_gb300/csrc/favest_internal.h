@@ -23,6 +23,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <vector>
 
@@ -41,15 +42,19 @@ struct FftPlan {
 };
 
 // One tensor-core GEMM output tile: out[rows][128 cols] = sum over nk K-chunks of A_c * B_c.
+// Output element (r, c) goes to out[out_off + r*out_ld + (c/8)*col_gs + c%8].
 struct TcItem {
     long long a_off;    // byte offset of chunk 0 of A (three 16 KB bf16 pieces per chunk)
-    long long b_off;    // byte offset of chunk 0 of B
+    long long b_off;    // byte offset of chunk 0 of B (bulk mode)
     long long out_off;  // float offset of output element (row 0, col 0)
+    long long out_ld;   // output row pitch (floats)
+    long long col_gs;   // output stride between groups of 8 columns (floats)
     int nk;             // K-chunks (64 deep)
     int rows;           // valid output rows (<= 128)
     int a_stride;       // bytes between consecutive A chunks
     int b_stride;       // bytes between consecutive B chunks
-    int out_ld;         // output row pitch (floats)
+    int b_tma;          // 1: B through the tensor map at the coordinates below
+    int bx, by, bz0, bw;  // tensor-map coordinates: x0 (piece 0), field group, K-group of chunk 0, order
     int pad;
 };
 
@@ -87,9 +92,18 @@ struct Plan {
     void *d_lam = nullptr;        // Legendre operand tiles (bf16 x 3)
     void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
-    float *d_Q32 = nullptr;       // forward GEMM output [tab row][ncolr]
-    float *d_S32 = nullptr;       // adjoint GEMM output [mu][parity][JP][ncolr]
+    float *d_Q32 = nullptr;       // forward GEMM output [field][l(l+1)/2 + mu][8]
+    float *d_S32 = nullptr;       // adjoint GEMM output [JP][field][mu][parity][8]
+    int nf = 0;                   // fields padded to a multiple of 16 (ncolr / 8)
+    CUtensorMap tmap_fb;          // forward B operand: Fb[JP][nf][L+1][parity][piece][8] bf16
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
+    float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
+    float *d_k1 = nullptr;        // [L+1] kappa of order 1 (order-0 adjoint on order-1 tiles)
+    int *d_perm = nullptr;        // [nphi] digit-reversal positions of the in-place FFT
+    int fft_log2n = 0;            // log2(nphi) when nphi = 2^6..2^11 (power-of-two engine), else 0
+    // polar patch of the split adjoint: rings j < pol_jc, orders 1 <= mu < pol_muc
+    int pol_jc = 0, pol_muc = 0;
+    float2 *d_pol = nullptr;      // [pol_jc][L+1][pol_muc] (D_l, Lambda_l) in fp32
     TcItem *d_items_f = nullptr, *d_items_a = nullptr;
 
     // workspace
@@ -109,7 +123,7 @@ struct Plan {
 
 enum KernelId {
     KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
-    KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ,
+    KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ, KID_POLAR,
     KID_COUNT
 };
 
@@ -131,6 +145,8 @@ cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
 cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s);
 cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s);
+cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s);
+int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
 size_t tc_gemm_smem_bytes();
 
 }  // namespace favest

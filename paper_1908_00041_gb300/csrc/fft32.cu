@@ -28,64 +28,182 @@ __device__ __forceinline__ float2 twf(const float2 *__restrict__ tw, int q)
     return INV ? make_float2(t.x, -t.y) : t;
 }
 
-// one Stockham pass of radix R over `nr` rings of n points stored back to back
+constexpr int kMaxInlineRadix = 128;   // largest odd prime factor of nphi supported
+
+// In-place decimation-in-frequency FFT of `nr` rings of n points stored back to back.
+// Stage s (radix R, block length Nb, h = Nb/R): for every block and k < h the R points
+// x[k + t h] are replaced by their R-point DFT, output q scaled by w_Nb^{q k}.  Frequency m
+// ends at position perm[m] (mixed-radix digit reversal, precomputed on the host).  Each
+// butterfly reads and writes the same addresses, so one buffer suffices.
 template <bool INV>
-__device__ __forceinline__ void pass_f32(const float2 *__restrict__ x, float2 *__restrict__ y,
-                                         const float2 *__restrict__ tw, int n, int R, int Ns, int nr)
+__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr)
 {
-    const int nb = n / R;
-    const int tstep = n / (Ns * R);
-    for (int t = threadIdx.x; t < nb * nr; t += blockDim.x) {
-        const int ring = t / nb, i = t % nb;
-        const float2 *xr = x + ring * n;
-        float2 *yr = y + ring * n;
-        const int k = i % Ns;
-        const int obase = (i / Ns) * Ns * R + k;
-        if (R == 2) {
-            float2 v0 = xr[i], v1 = cmulf(xr[i + nb], twf<INV>(tw, k * tstep));
-            yr[obase] = caddf(v0, v1);
-            yr[obase + Ns] = csubf(v0, v1);
-        } else if (R == 4) {
-            float2 v0 = xr[i];
-            float2 v1 = cmulf(xr[i + nb], twf<INV>(tw, k * tstep));
-            float2 v2 = cmulf(xr[i + 2 * nb], twf<INV>(tw, 2 * k * tstep));
-            float2 v3 = cmulf(xr[i + 3 * nb], twf<INV>(tw, 3 * k * tstep));
-            float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
-            float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
-            float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-            yr[obase] = caddf(s02, s13);
-            yr[obase + Ns] = caddf(d02, rot);
-            yr[obase + 2 * Ns] = csubf(s02, s13);
-            yr[obase + 3 * Ns] = csubf(d02, rot);
-        } else {
-            const int rstep = n / R;
-            for (int q = 0; q < R; ++q) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int r = 0; r < R; ++r) {
-                    int t1 = (int)(((long long)k * r * tstep) % n);
-                    int tq = t1 + ((q * r) % R) * rstep;
-                    if (tq >= n) tq -= n;
-                    acc = caddf(acc, cmulf(xr[i + r * nb], twf<INV>(tw, tq)));
+    const int n = rp.n;
+    int Nb = n;
+    for (int st = 0; st < rp.nstages; ++st) {
+        const int R = rp.radix[st];
+        const int h = Nb / R;
+        const int ts = n / Nb;
+        const int nbf = n / R;
+        for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+            const int ring = t / nbf, i = t % nbf;
+            const int blk = i / h, k = i % h;
+            float2 *xr = x + ring * n + blk * Nb + k;
+            if (R == 4) {
+                const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
+                const float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
+                const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
+                const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+                xr[0] = caddf(s02, s13);
+                xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
+                xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
+                xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
+            } else if (R == 2) {
+                const float2 v0 = xr[0], v1 = xr[h];
+                xr[0] = caddf(v0, v1);
+                xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
+            } else {
+                float2 v[kMaxInlineRadix];
+                for (int q = 0; q < R; ++q) v[q] = xr[q * h];
+                const int rstep = n / R;
+                for (int q = 0; q < R; ++q) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int r = 0; r < R; ++r) acc = caddf(acc, cmulf(v[r], twf<INV>(tw, ((q * r) % R) * rstep)));
+                    xr[q * h] = cmulf(acc, twf<INV>(tw, (int)(((long long)q * k * ts) % n)));
                 }
-                yr[obase + q * Ns] = acc;
+            }
+        }
+        __syncthreads();
+        Nb = h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Power-of-two lengths n = 2^LOG2N (64..2048): in-place decimation in frequency with
+// radix-16 butterflies held in registers, then one last radix-2^r stage (r = LOG2N mod 4,
+// or 16 when that is 0).  The last stage has no twiddles and writes its outputs back in
+// natural frequency order, so no digit-reversal table is needed on either side.  All
+// index arithmetic is shifts and masks.  Shared memory holds one padding complex after
+// every 16, which makes every stage's accesses (stride 1, 8 or 16 complexes across a
+// half-warp) and the natural-order write free of bank conflicts.
+// ---------------------------------------------------------------------------
+constexpr int kFftThreads = 256;
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// cos and sin of 2 pi j / 16
+__host__ __device__ constexpr float cos16(int j)
+{
+    constexpr float t[16] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                             0.f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                             -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                             0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+    return t[j & 15];
+}
+__host__ __device__ constexpr float sin16(int j) { return cos16(j + 12); }
+
+template <int R>
+struct Log2c { static constexpr int v = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4; };
+
+// R-point DFT in registers by radix-2 decimation in frequency (forward: exp(-2 pi i qt/R),
+// inverse: exp(+...)); output q ends in v[bitrev(q)]
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R])
+{
+#pragma unroll
+    for (int s = R / 2; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * s) {
+#pragma unroll
+            for (int j = 0; j < s; ++j) {
+                const float2 a = v[g + j], b = v[g + j + s];
+                v[g + j] = caddf(a, b);
+                const float2 d = csubf(a, b);
+                const int e = j * (16 / (2 * s));        // w_{2s}^j = w_16^e
+                if (e == 0) {
+                    v[g + j + s] = d;
+                } else if (e == 4) {                     // -i (forward) or +i (inverse)
+                    v[g + j + s] = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+                } else {
+                    const float c = cos16(e), sn = INV ? sin16(e) : -sin16(e);
+                    v[g + j + s] = make_float2(fmaf(c, d.x, -sn * d.y), fmaf(c, d.y, sn * d.x));
+                }
             }
         }
     }
 }
 
-template <bool INV>
-__device__ float2 *stockham_f32(float2 *b0, float2 *b1, const float2 *__restrict__ tw, const RadixPlanArg &rp,
-                                int nr)
+__host__ __device__ constexpr int bitrev(int x, int bits)
 {
-    float2 *x = b0, *y = b1;
-    int Ns = 1;
-    for (int s = 0; s < rp.nstages; ++s) {
-        pass_f32<INV>(x, y, tw, rp.n, rp.radix[s], Ns, nr);
-        __syncthreads();
-        Ns *= rp.radix[s];
-        float2 *t = x; x = y; y = t;
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// one in-place radix-16 stage at block length NB over nr rings
+template <int LOG2N, int NB, bool INV>
+__device__ __forceinline__ void dif_stage16(float2 *x, const float2 *__restrict__ tw, int nr)
+{
+    constexpr int n = 1 << LOG2N, R = 16;
+    constexpr int h = NB / R, ts = n / NB, nbf = n / R;
+    for (int t = threadIdx.x; t < nbf * nr; t += kFftThreads) {
+        const int ring = t >> (LOG2N - 4);
+        const int i = t & (nbf - 1);
+        const int k = i & (h - 1);
+        const int base = ring * n + (i - k) * R + k;     // block (i / h) * NB, offset k
+        float2 v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = x[padi(base + q * h)];
+        dft_reg<R, INV>(v);
+        x[padi(base)] = v[0];
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[padi(base + q * h)] = cmulf(v[bitrev(q, 4)], twf<INV>(tw, q * k * ts));
     }
-    return x;
+    __syncthreads();
+}
+
+// last stage (h = 1, no twiddles): blocks of RL consecutive points; output q of block blk
+// is frequency m = nibble_reverse(blk) + q * n / RL, stored back at position m.  All of a
+// ring's blocks are read before any of its points is rewritten.
+template <int LOG2N, int RL, bool INV>
+__device__ __forceinline__ void dif_last(float2 *x, int nr)
+{
+    constexpr int n = 1 << LOG2N, LB = Log2c<RL>::v;
+    constexpr int nblk = n / RL, ndig = (LOG2N - LB) / 4;
+    static_assert(nblk <= kFftThreads && (LOG2N - LB) % 4 == 0, "unsupported length");
+    constexpr int rings_per_round = kFftThreads / nblk;
+    const int t = threadIdx.x;
+    for (int r0 = 0; r0 < nr; r0 += rings_per_round) {
+        const int ring = r0 + t / nblk, blk = t & (nblk - 1);
+        const bool act = t < nblk * rings_per_round && ring < nr;
+        float2 v[RL];
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < RL; ++q) v[q] = x[padi(ring * n + blk * RL + q)];
+            dft_reg<RL, INV>(v);
+        }
+        __syncthreads();
+        if (act) {
+            int m0 = 0;
+#pragma unroll
+            for (int d = 0; d < ndig; ++d) m0 |= ((blk >> (4 * d)) & 15) << (4 * (ndig - 1 - d));
+#pragma unroll
+            for (int q = 0; q < RL; ++q) x[padi(ring * n + m0 + q * nblk)] = v[bitrev(q, LB)];
+        }
+        __syncthreads();
+    }
+}
+
+// full transform of nr rings: natural order in, natural order out
+template <int LOG2N, bool INV>
+__device__ void fft_p2(float2 *x, const float2 *__restrict__ tw, int nr)
+{
+    constexpr int n = 1 << LOG2N, n16 = LOG2N / 4, rem = LOG2N % 4;
+    constexpr int nfull = rem ? n16 : n16 - 1;           // radix-16 stages before the last
+    static_assert(nfull <= 2, "lengths above 4096 are not instantiated");
+    if constexpr (nfull >= 1) dif_stage16<LOG2N, n, INV>(x, tw, nr);
+    if constexpr (nfull >= 2) dif_stage16<LOG2N, n / 16, INV>(x, tw, nr);
+    dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
 }
 
 __device__ __forceinline__ void split3f(float f, unsigned short &h, unsigned short &m, unsigned short &l)
@@ -118,125 +236,180 @@ __device__ __forceinline__ void store_row3(unsigned char *dst, const float (&v)[
         *reinterpret_cast<uint4 *>(dst + q * piece_bytes) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
-constexpr int kChunkBytes = 3 * 16384;
 
-// grid: B * J CTAs (field-major); shared: 2 * 4 * n float2
-__global__ void __launch_bounds__(256) k_fft_fwd_bf16(
+// grid: B * J CTAs (field-major); shared: 4 * n float2 (+ padding for LOG2N > 0).
+// LOG2N > 0 selects the power-of-two engine, 0 the generic mixed-radix one.
+template <int LOG2N>
+__global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const float2 *__restrict__ Tth, const float2 *__restrict__ Tph, unsigned char *__restrict__ Fb,
-    RadixPlanArg rp, const float2 *__restrict__ tw, const double *__restrict__ omega, int L, int nlat, int J,
-    int has_eq, int n_tiles, int nk_f)
+    RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
+    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf)
 {
-    extern __shared__ float2 sm_f[];
+    extern __shared__ float4 sm_f4[];
+    float2 *buf = reinterpret_cast<float2 *>(sm_f4);
     const int n = rp.n;
     const int b = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;    // rings: (th, j), (ph, j), (th, j'), (ph, j')
-    float2 *buf0 = sm_f, *buf1 = sm_f + 4 * n;
     const int jm = nlat - 1 - j;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        const int ring = idx / n, k = idx % n;
+    const int n2 = n / 2;         // float4 per ring
+    for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
+        const int ring = idx / n2, k2 = idx % n2;
         const float2 *src = (ring & 1) ? Tph : Tth;
         const int jj = (ring < 2) ? j : jm;
-        buf0[idx] = src[((size_t)b * nlat + jj) * n + k];
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(src + ((size_t)b * nlat + jj) * n) + k2);
+        if (LOG2N > 0) {
+            buf[padi(2 * idx)] = make_float2(v.x, v.y);
+            buf[padi(2 * idx + 1)] = make_float2(v.z, v.w);
+        } else {
+            sm_f4[idx] = v;
+        }
     }
     __syncthreads();
-    const float2 *F = stockham_f32<false>(buf0, buf1, tw, rp, nr);
+    if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
+    else dif_f32<false>(buf, tw, rp, nr);
     const float w = (float)omega[j];
-    const int nt = b / 16, bg = b % 16, kc = j / 64, jj = j % 64;
+    // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
+    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 96;
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
         float vp[8], vm[8];
         // n % 8 = c*4 + s*2 + im ; s = 0: +mu (bin mu), s = 1: -mu (bin n - mu, or 0 at mu = 0)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int bin = (sgn == 0 || mu == 0) ? mu : n - mu;
+            const int pos = LOG2N > 0 ? bin : __ldg(perm + bin);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int bin = (s == 0 || mu == 0) ? mu : n - mu;
-                float2 a = F[c * n + bin];
-                float2 z = eq ? make_float2(0.f, 0.f) : F[(2 + c) * n + bin];
-                const int base = c * 4 + s * 2;
+            for (int c = 0; c < 2; ++c) {
+                const int i0 = c * n + pos, i1 = (2 + c) * n + pos;
+                const float2 a = buf[LOG2N > 0 ? padi(i0) : i0];
+                const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(i1) : i1];
+                const int base = c * 4 + sgn * 2;
                 vp[base] = w * (a.x + z.x);
                 vp[base + 1] = w * (a.y + z.y);
                 vm[base] = eq ? 0.f : w * (a.x - z.x);
                 vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
             }
         }
-        const size_t row_off = (size_t)(jj / 8) * 2048 + bg * 128 + (jj % 8) * 16;
-        unsigned char *dp = Fb + (((size_t)(mu * 2 + 0) * n_tiles + nt) * nk_f + kc) * kChunkBytes + row_off;
-        unsigned char *dm = Fb + (((size_t)(mu * 2 + 1) * n_tiles + nt) * nk_f + kc) * kChunkBytes + row_off;
-        store_row3(dp, vp, 16384);
-        store_row3(dm, vm, 16384);
+        unsigned char *dp = dst_base + (size_t)mu * 96;
+        store_row3(dp, vp, 16);
+        store_row3(dp + 48, vm, 16);
     }
 }
 
-// grid: B * J; S32 = [mu][p][JP][ncolr] fp32; shared 2 * 4 * n float2
-__global__ void __launch_bounds__(256) k_fft_inv_bf16(
+// grid: B * J; S32 = [JP][nf][L+1][parity][8] fp32; shared 4 * n float2 (+ padding)
+template <int LOG2N>
+__global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const double *__restrict__ sj, int L, int nlat, int J, int JP, int has_eq,
-    int ncolr)
+    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj, int L, int nlat,
+    int J, int has_eq, int nf)
 {
-    extern __shared__ float2 sm_i[];
+    extern __shared__ float4 sm_i4[];
+    float2 *buf = reinterpret_cast<float2 *>(sm_i4);
     const int n = rp.n;
     const int b = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;
-    float2 *buf0 = sm_i, *buf1 = sm_i + 4 * n;
     const float is = (float)(1.0 / sj[j]);
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = make_float2(0.f, 0.f);
-    __syncthreads();
+    if (LOG2N > 0) {
+        // every bin but n/2 is written below
+        if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
+    } else {
+        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
         // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
         const float sc = mu == 0 ? 1.0f : is;
-        const float4 *e = reinterpret_cast<const float4 *>(S32 + (((size_t)mu * 2 + 0) * JP + j) * ncolr + 8 * b);
-        const float4 *o = reinterpret_cast<const float4 *>(S32 + (((size_t)mu * 2 + 1) * JP + j) * ncolr + 8 * b);
-        float4 e0 = e[0], e1 = e[1], o0 = o[0], o1 = o[1];
-        float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-        float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+        const float4 *e = reinterpret_cast<const float4 *>(S32 + ((((size_t)j * nf + b) * (L + 1) + mu) * 2) * 8);
+        const float4 *o = e + 2;
+        const float4 e0 = __ldg(e), e1 = __ldg(e + 1), o0 = __ldg(o), o1 = __ldg(o + 1);
+        const float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+        const float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                if (mu == 0 && s == 1) continue;
-                const int bin = s ? n - mu : mu;
-                const int k = c * 4 + s * 2;
-                buf0[c * n + bin] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
-                if (!eq) buf0[(2 + c) * n + bin] = make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                if (mu == 0 && sgn == 1) continue;
+                const int bin = sgn ? n - mu : mu;
+                const int k = c * 4 + sgn * 2;
+                const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
+                buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
+                if (!eq)
+                    buf[LOG2N > 0 ? padi(i1) : i1] =
+                        make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
             }
         }
     }
     __syncthreads();
-    const float2 *T = stockham_f32<true>(buf0, buf1, tw, rp, nr);
+    if constexpr (LOG2N > 0) fft_p2<LOG2N, true>(buf, tw, nr);
+    else dif_f32<true>(buf, tw, rp, nr);
     const int jm = nlat - 1 - j;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        const int ring = idx / n, k = idx % n;
+    const int n2 = n / 2;
+    for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
+        const int ring = idx / n2, k2 = idx % n2;
+        const int i0 = ring * n + (LOG2N > 0 ? 2 * k2 : __ldg(perm + 2 * k2));
+        const int i1 = ring * n + (LOG2N > 0 ? 2 * k2 + 1 : __ldg(perm + 2 * k2 + 1));
+        const float2 v0 = buf[LOG2N > 0 ? padi(i0) : i0];
+        const float2 v1 = buf[LOG2N > 0 ? padi(i1) : i1];
         float2 *dst = (ring & 1) ? Tph : Tth;
         const int jj = (ring < 2) ? j : jm;
-        dst[((size_t)b * nlat + jj) * n + k] = T[idx];
+        reinterpret_cast<float4 *>(dst + ((size_t)b * nlat + jj) * n)[k2] = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
+template <int LOG2N>
+cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const size_t smem = 2 * 4 * (size_t)p.nphi * sizeof(float2);
-    auto k = k_fft_fwd_bf16;
+    const int ne = 4 * p.nphi;
+    const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    auto k = k_fft_fwd_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<p.B * p.J, 256, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, rp,
-                                   p.fft.tw32, p.unit_weights ? p.d_omega_unit : p.d_omega, p.L, p.nlat, p.J,
-                                   p.has_eq, p.n_tiles, p.nk_f);
+    k<<<p.B * p.J, kFftThreads, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, rp,
+                                   p.fft.tw32, p.d_perm, p.unit_weights ? p.d_omega_unit : p.d_omega, p.L,
+                                   p.nlat, p.J, p.has_eq, p.nf);
     return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
+{
+    RadixPlanArg rp = make_radix_arg(p.fft);
+    const int ne = 4 * p.nphi;
+    const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    auto k = k_fft_inv_bf16<LOG2N>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
+                                   p.d_perm, p.d_sin, p.L, p.nlat, p.J, p.has_eq, p.nf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
+{
+    switch (p.fft_log2n) {
+    case 6: return launch_fwd_t<6>(p, Tth, Tph, s);
+    case 7: return launch_fwd_t<7>(p, Tth, Tph, s);
+    case 8: return launch_fwd_t<8>(p, Tth, Tph, s);
+    case 9: return launch_fwd_t<9>(p, Tth, Tph, s);
+    case 10: return launch_fwd_t<10>(p, Tth, Tph, s);
+    case 11: return launch_fwd_t<11>(p, Tth, Tph, s);
+    default: return launch_fwd_t<0>(p, Tth, Tph, s);
+    }
 }
 
 cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
-    RadixPlanArg rp = make_radix_arg(p.fft);
-    const size_t smem = 2 * 4 * (size_t)p.nphi * sizeof(float2);
-    auto k = k_fft_inv_bf16;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<p.B * p.J, 256, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
-                                   p.d_sin, p.L, p.nlat, p.J, p.JP, p.has_eq, p.ncolr);
-    return cudaGetLastError();
+    switch (p.fft_log2n) {
+    case 6: return launch_inv_t<6>(p, Tth, Tph, s);
+    case 7: return launch_inv_t<7>(p, Tth, Tph, s);
+    case 8: return launch_inv_t<8>(p, Tth, Tph, s);
+    case 9: return launch_inv_t<9>(p, Tth, Tph, s);
+    case 10: return launch_inv_t<10>(p, Tth, Tph, s);
+    case 11: return launch_inv_t<11>(p, Tth, Tph, s);
+    default: return launch_inv_t<0>(p, Tth, Tph, s);
+    }
 }
 
 }  // namespace favest

@@ -186,8 +186,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
 
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
     const unsigned char *__restrict__ Abuf, const unsigned char *__restrict__ Bbuf,
-    const TcItem *__restrict__ items, int nitems, float *__restrict__ out, int a_mn_major,
-    int *__restrict__ status)
+    const __grid_constant__ CUtensorMap tmap_b, const TcItem *__restrict__ items, int nitems,
+    float *__restrict__ out, int a_mn_major, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     GemmSmem &S = *reinterpret_cast<GemmSmem *>(sm_raw);
@@ -230,8 +230,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
                     tc::mbar_arrive_expect_tx(&S.full[stage], 2 * kChunkBytes);
                     tc::bulk_g2s(S.a[stage], Abuf + I.a_off + (long long)c * I.a_stride, kChunkBytes,
                                  &S.full[stage]);
-                    tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkBytes,
-                                 &S.full[stage]);
+                    if (I.b_tma) {
+                        for (int q = 0; q < kPieces; ++q)
+                            tc::tma_load_5d(S.b[stage] + q * kPieceBytes, &tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
+                                            I.bz0 + 8 * c, &S.full[stage]);
+                    } else {
+                        tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkBytes,
+                                     &S.full[stage]);
+                    }
                     use[stage]++;
                     stage = (stage + 1) % kStages;
                 }
@@ -338,10 +344,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
             if (lane == 0) tc::mbar_arrive(&S.dcorr_empty);
             corr_use++;
             if (row < I.rows) {
-                float4 *dst = reinterpret_cast<float4 *>(out + I.out_off + (long long)row * I.out_ld);
+                float *dst = out + I.out_off + (long long)row * I.out_ld;
 #pragma unroll
-                for (int i = 0; i < kTileN / 4; ++i)
-                    dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+                for (int g = 0; g < kTileN / 8; ++g) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dst + g * I.col_gs);
+                    d4[0] = make_float4(acc[8 * g], acc[8 * g + 1], acc[8 * g + 2], acc[8 * g + 3]);
+                    d4[1] = make_float4(acc[8 * g + 4], acc[8 * g + 5], acc[8 * g + 6], acc[8 * g + 7]);
+                }
             }
         }
     }
@@ -376,7 +385,7 @@ cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s)
     const int grid = nitems < p.num_sms ? nitems : p.num_sms;
     if (grid <= 0) return cudaSuccess;
     k<<<grid, kGemmThreads, smem, s>>>((const unsigned char *)p.d_lam,
-                                       (const unsigned char *)(fwd ? p.d_Fb : p.d_gb),
+                                       (const unsigned char *)(fwd ? p.d_Fb : p.d_gb), p.tmap_fb,
                                        fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
                                        fwd ? 1 : 0, p.d_status);
     return cudaGetLastError();

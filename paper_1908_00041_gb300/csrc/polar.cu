@@ -1,0 +1,250 @@
+// Polar patch of the split-precision adjoint.
+//
+// The adjoint forms, per order mu and folded latitude j, the scalar sums
+//   S_p(j) = sum_{l' = l - mu of parity p} g_l' lambda~_l'(theta_j),
+//   g_l'   = P_{l'-1} a_{l'-1} - M_{l'+1} a_{l'+1} - i m R_l' b_l'        (theta part),
+// and divides them by sin(theta_j).  Regrouping the sum by coefficient gives
+//   S = sum_l a_l D_l - i m sum_l b_l Lambda_l,
+//   D_l = P_l lambda~_{l+1} - M_l lambda~_{l-1} = sin(theta) d_theta lambda_l / sqrt(l(l+1)),
+//   Lambda_l = R_l lambda~_l = lambda_l / sqrt(l(l+1)),
+// (the identity sin(theta) d_theta lambda_l = l eps_{l+1} lambda_{l+1} - (l+1) eps_l lambda_{l-1}).
+// Close to a pole D_l is O(sin(theta)) while its two parts are O(1): the tensor-core
+// sum, which carries the parts separately at FP32-level precision, loses a factor of
+// about 1/sin(theta_j) of its relative accuracy there, and the division by sin(theta_j)
+// turns that into an absolute error of the field.  For the few rings with
+// sin(theta_j) < kPolarSin this kernel recomputes S in the regrouped form, from D_l and
+// Lambda_l evaluated in FP64 at plan time and stored in FP32, so nothing cancels.
+// Orders mu >= pol_muc are left to the tensor-core sums: at these rings every
+// lambda_l^mu with l <= L lies beyond its turning point (mu > 1.5 L sin(theta_j)) and is
+// exponentially small, so their error is negligible.
+//
+// Only the theta/phi structure of the combine stage and the E/O parity split of the
+// folded grid are used; the output goes to the same buffer S32 the GEMM writes,
+//   S32[j][field][mu][parity][8], columns c*4 + s*2 + (re, im): c = theta/phi,
+//   s = 0: m = +mu, s = 1: m = -mu (with the factor (-1)^mu of lambda^{-mu}).
+#include <cmath>
+#include <vector>
+
+#include "favest_internal.h"
+
+namespace favest {
+
+namespace {
+
+constexpr double kPolarSin = 0.06;   // rings with sin(theta_j) below this are patched
+constexpr int kPolarJ = 2;           // rings per thread
+constexpr int kPolarChunk = 8;       // degrees summed in plain FP32 before a compensated add
+
+double eps_pl(int l, int mu)
+{
+    const double num = (double)(l - mu) * (double)(l + mu);
+    const double den = (double)(2 * l - 1) * (double)(2 * l + 1);
+    return num > 0 ? std::sqrt(num / den) : 0.0;
+}
+
+constexpr int kPolarWarps = 8;       // warps per CTA, each over its own range of degrees
+
+// grid (pol_muc / 32, B, ceil(pol_jc / kPolarJ)), 256 threads.  Lane = order mu within the
+// tile; warp w sums degrees l in the w-th of 8 equal ranges.  Per ring the thread keeps
+// 2 banks x 8 columns: bank k collects, for even l, the D terms (k = 1) and Lambda terms
+// (k = 0), for odd l the reverse, so that bank k holds output parity k ^ (mu & 1).
+// Terms are summed in FP32 over chunks of kPolarChunk degrees, chunk sums go into a
+// Kahan-compensated running sum per warp, and the 8 warp sums are added in a fixed tree
+// order through shared memory (a plain FP32 running sum over ~L terms would lose about
+// sqrt(L) ulps).  Orders beyond the ring group's turning-point bound keep the tensor-core
+// values.
+__global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
+    const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
+    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int nf)
+{
+    __shared__ float part[kPolarWarps][kPolarJ * 16][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int mu0 = blockIdx.x * 32;
+    const int mu = mu0 + lane;
+    const int f = blockIdx.y;
+    const int j0 = blockIdx.z * kPolarJ;
+    const int jlast = (j0 + kPolarJ < jc ? j0 + kPolarJ : jc) - 1;
+    const int mulim = (int)ceil(1.5 * (L + 1) * sin_j[jlast]) + 16;
+    if (mu0 >= mulim) return;                          // uniform over the CTA
+    const bool active = mu >= 1 && mu <= L && mu < muc;
+    const float2 *af = a + (size_t)f * K;
+    const float2 *bf = b + (size_t)f * K;
+    const float w = (float)mu;
+    float sum[kPolarJ][2][8], cmp[kPolarJ][2][8];
+#pragma unroll
+    for (int q = 0; q < kPolarJ; ++q)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sum[q][k][c] = cmp[q][k][c] = 0.f;
+
+    // this warp's degrees: [lo, hi), lo even, length a multiple of kPolarChunk
+    const int span = L + 1 - mu0;
+    const int per = ((span + kPolarWarps - 1) / kPolarWarps + kPolarChunk - 1) / kPolarChunk * kPolarChunk;
+    const int lo = mu0 + warp * per, hi = lo + per;
+    for (int lc = lo; active && lc < hi && lc <= L; lc += kPolarChunk) {
+        float acc[kPolarJ][2][8];
+#pragma unroll
+        for (int q = 0; q < kPolarJ; ++q)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[q][k][c] = 0.f;
+#pragma unroll
+        for (int h = 0; h < kPolarChunk; ++h) {
+            const int l = lc + h;
+            if (l < mu || l > L) continue;
+            const size_t c0 = (size_t)l * l + l - 1;
+            const float2 ap = af[c0 + mu], am = af[c0 - mu], bp = bf[c0 + mu], bm = bf[c0 - mu];
+            const int kd = (h & 1) ? 0 : 1, kl = (h & 1) ? 1 : 0;   // banks of the D and Lambda terms
+#pragma unroll
+            for (int q = 0; q < kPolarJ; ++q) {
+                if (j0 + q >= jc) break;
+                const float2 t = tab[((size_t)(j0 + q) * (L + 1) + l) * muc + mu];
+                const float D = t.x, wl = w * t.y;
+                float *ad = acc[q][kd], *al = acc[q][kl];
+                ad[0] = fmaf(ap.x, D, ad[0]);
+                ad[1] = fmaf(ap.y, D, ad[1]);
+                ad[2] = fmaf(am.x, D, ad[2]);
+                ad[3] = fmaf(am.y, D, ad[3]);
+                ad[4] = fmaf(bp.x, D, ad[4]);
+                ad[5] = fmaf(bp.y, D, ad[5]);
+                ad[6] = fmaf(bm.x, D, ad[6]);
+                ad[7] = fmaf(bm.y, D, ad[7]);
+                // theta: -i m b Lambda ; phi: +i m a Lambda  (m = +mu for s = 0, -mu for s = 1)
+                al[0] = fmaf(wl, bp.y, al[0]);
+                al[1] = fmaf(-wl, bp.x, al[1]);
+                al[2] = fmaf(-wl, bm.y, al[2]);
+                al[3] = fmaf(wl, bm.x, al[3]);
+                al[4] = fmaf(-wl, ap.y, al[4]);
+                al[5] = fmaf(wl, ap.x, al[5]);
+                al[6] = fmaf(wl, am.y, al[6]);
+                al[7] = fmaf(-wl, am.x, al[7]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPolarJ; ++q)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float y = acc[q][k][c] - cmp[q][k][c];
+                    const float t = sum[q][k][c] + y;
+                    cmp[q][k][c] = (t - sum[q][k][c]) - y;
+                    sum[q][k][c] = t;
+                }
+    }
+#pragma unroll
+    for (int q = 0; q < kPolarJ; ++q)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) part[warp][q * 16 + k * 8 + c][lane] = sum[q][k][c] - cmp[q][k][c];
+    __syncthreads();
+    // thread -> (lane, 4 consecutive values of one ring and bank)
+    constexpr int kGroups = kPolarJ * 4;               // groups of 4 values
+    for (int g = warp; g < kGroups; g += kPolarWarps) {
+        const int q = g >> 2, k = (g >> 1) & 1, c4 = (g & 1) * 4;
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int vi = q * 16 + k * 8 + c4 + i;
+            float t[kPolarWarps];
+#pragma unroll
+            for (int ww = 0; ww < kPolarWarps; ++ww) t[ww] = part[ww][vi][lane];
+#pragma unroll
+            for (int st = 1; st < kPolarWarps; st *= 2)
+#pragma unroll
+                for (int ww = 0; ww < kPolarWarps; ww += 2 * st) t[ww] += t[ww + st];
+            v[i] = t[0];
+        }
+        if (active && j0 + q < jc) {
+            const int par = k ^ (mu & 1);
+            const float sg = (mu & 1) ? -1.f : 1.f;     // columns of m = -mu
+            float *dst = S32 + (((size_t)(j0 + q) * nf + f) * (L + 1) + mu) * 16 + par * 8 + c4;
+            *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
+        }
+    }
+}
+
+}  // namespace
+
+// Host: ring and order ranges, and the FP64 tables D_l, Lambda_l of every patched
+// (ring, order) pair from the normalised three-term recurrence
+//   lambda_mu^mu = (-1)^mu c_mu sin^mu(theta),
+//   lambda_{l+1} = (cos(theta) lambda_l - eps_l lambda_{l-1}) / eps_{l+1},
+// run on a mantissa with a separate binary exponent so that the polar starting values
+// (far below the double range at high order) stay exact.
+int build_polar_tables(Plan &p)
+{
+    const int L = p.L;
+    int jc = 0;
+    while (jc < p.J - (p.has_eq ? 1 : 0)) {
+        const double x = p.h_x[jc];
+        if (std::sqrt((1.0 - x) * (1.0 + x)) >= kPolarSin) break;
+        ++jc;
+    }
+    int muc = (int)std::ceil(1.5 * (L + 1) * kPolarSin) + 16;
+    muc = (muc + 31) / 32 * 32;
+    const int mumax = (L + 1 + 31) / 32 * 32;
+    if (muc > mumax) muc = mumax;
+    p.pol_jc = jc;
+    p.pol_muc = muc;
+    if (jc == 0) return FAVEST_OK;
+
+    std::vector<float2> tab((size_t)jc * (L + 1) * muc, make_float2(0.f, 0.f));
+    std::vector<double> eps(L + 3), lam(L + 3);
+    double cmu = 1.0 / std::sqrt(4.0 * 3.14159265358979323846);
+    for (int mu = 1; mu < muc && mu <= L; ++mu) {
+        cmu *= std::sqrt((2.0 * mu + 1.0) / (2.0 * mu));
+        for (int l = mu; l <= L + 2; ++l) eps[l] = eps_pl(l, mu);
+        for (int j = 0; j < jc; ++j) {
+            const double x = p.h_x[j], s = std::sqrt((1.0 - x) * (1.0 + x));
+            // start: (-1)^mu cmu s^mu as y * 2^e
+            double y = (mu & 1) ? -cmu : cmu;
+            int e = 0;
+            for (int k = 0; k < mu; ++k) {
+                int ex;
+                y = std::frexp(y * s, &ex);
+                e += ex;
+            }
+            double ym = 0.0;   // lambda_{l-1}
+            lam[mu - 1] = 0.0;
+            lam[mu] = std::ldexp(y, e);
+            for (int l = mu; l <= L; ++l) {
+                const double yn = (x * y - eps[l] * ym) / eps[l + 1];
+                ym = y;
+                y = yn;
+                if (std::fabs(y) > 0x1p200) {
+                    y *= 0x1p-200;
+                    ym *= 0x1p-200;
+                    e += 200;
+                }
+                lam[l + 1] = std::ldexp(y, e);
+            }
+            for (int l = mu; l <= L; ++l) {
+                const double sl = 1.0 / std::sqrt((double)l * (l + 1.0));
+                const double D = sl * (l * eps[l + 1] * lam[l + 1] - (l + 1.0) * eps[l] * lam[l - 1]);
+                tab[((size_t)j * (L + 1) + l) * muc + mu] = make_float2((float)D, (float)(sl * lam[l]));
+            }
+        }
+    }
+    if (cudaMalloc((void **)&p.d_pol, tab.size() * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return FAVEST_ENOMEM;
+    }
+    if (cudaMemcpy(p.d_pol, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FAVEST_ECUDA;
+    return FAVEST_OK;
+}
+
+cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    dim3 grid(p.pol_muc / 32, p.B, (p.pol_jc + kPolarJ - 1) / kPolarJ);
+    k_polar_patch<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin,
+                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.nf);
+    return cudaGetLastError();
+}
+
+}  // namespace favest

@@ -38,7 +38,9 @@ def _run(L, B, prec, fn, *args):
     return [_h(o) for o in out]
 
 
-@pytest.mark.parametrize("L,B", [(1, 1), (2, 1), (8, 1), (16, 1), (31, 3), (63, 2), (100, 1), (127, 17)])
+@pytest.mark.parametrize(
+    "L,B", [(1, 1), (2, 1), (8, 1), (16, 1), (31, 3), (63, 2), (100, 1), (127, 17), (255, 2), (511, 1)]
+)
 def test_bf16x6_vs_oracle(orc, L, B):
     a, b = synthetic.coefficients(L, B, seed=300 + L)
     a = a.astype(np.complex64).astype(np.complex128)
@@ -103,3 +105,25 @@ def test_bf16x6_roundtrip():
         ref_b = b.astype(np.complex64).astype(np.complex128)
         assert normwise_err(_h(a2), ref_a) < 2 * TOL
         assert normwise_err(_h(b2), ref_b) < 2 * TOL
+
+
+@pytest.mark.parametrize("decay", [1.0, 0.5])
+def test_bf16x6_polar_rings_flat_spectrum(decay):
+    """Flatter spectra than (l+1)^-1.5 put more weight on the polar rings, where the
+    adjoint divides the scalar sums by sin(theta_j); the split form must stay within
+    the bar against the FP64 path there too (L = 1023, 4 fields)."""
+    L, B = 1023, 4
+    a, b = synthetic.coefficients(L, B, seed=71, decay=decay)
+    da, db = _c64(a), _c64(b)
+    p16 = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+    p64 = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_C64)
+    t16, q16 = p16.adj(da, db)
+    t64, q64 = p64.adj(da, db)
+    torch.cuda.synchronize()
+    assert p16.status() == 0 and p64.status() == 0
+    for g, r in ((t16, t64), (q16, q64)):
+        g, r = _h(g), _h(r)
+        assert normwise_err(g.reshape(B, -1), r.reshape(B, -1)) < TOL
+        # the polar rings themselves, relative to the field's maximum
+        pole = np.concatenate([g[:, :3] - r[:, :3], g[:, -3:] - r[:, -3:]], axis=1)
+        assert np.abs(pole).max() < TOL * np.abs(r).max()
