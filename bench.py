@@ -101,25 +101,63 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work of the Legendre stage (documented in the design doc)
+# per-kernel roofline
 # ---------------------------------------------------------------------------
-def legendre_rows(L):
-    """(l, mu) pairs per transform, l = mu..L+1, mu = 0..L."""
-    return sum(L + 2 - mu for mu in range(L + 1))
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1700.0, "fallback"
 
 
-def fp64_flops_per_launch(L, batch, precision):
-    """FP64 flops the Legendre kernel must perform per launch.  Recurrence: one
-    multiply (A_l x) and one FMA per (l, mu, folded latitude) = 3 flops.  FP64
-    contraction (FP64 precision only): one complex column needs 2 FMAs = 4 flops per
-    (l, mu, folded latitude); 4B columns per order (2B at mu = 0)."""
-    J = (L + 2) // 2
-    rows = legendre_rows(L)
-    rec = 3.0 * rows * J
-    if precision != "fp64":
-        return rec
-    cols = 4.0 * batch * (rows - (L + 2)) + 2.0 * batch * (L + 2)
-    return rec + 4.0 * cols * J
+def ncu_traffic(kernel, L, B):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to this
+    workload; None when there is none or the kernel's source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        rec = d[kernel]
+        src = os.path.join(ROOT, "paper_1908_00041_gb300", "csrc", rec["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+        if rec["L"] != L:
+            return None
+        return rec["dram_bytes_per_launch"] * B / rec["batch"]
+    except Exception:
+        return None
+
+
+def kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B):
+    hbm, bf16, src = measured_peaks()
+    units = {0: ("hbm", "GB/s", hbm, "HBM copy bandwidth, MEASURED_PEAKS.json (%s)" % src),
+             1: ("alu", "TFLOP/s", fp64_peak, "FP64 FMA throughput measured live by favest_probe_peaks"),
+             2: ("tensor", "TFLOP/s", bf16, "bf16 dense sustained, MEASURED_PEAKS.json (%s)" % src),
+             3: ("alu", "TFLOP/s", fp32_peak, "FP32 FMA throughput measured live by favest_probe_peaks")}
+    total = sum(v[0] for v in prof.values())
+    kernels = {}
+    for name, (tot_ms, n) in prof.items():
+        nbytes, flops, pipe = plan.kernel_work(name)
+        t = tot_ms / n * 1e-3
+        bound, unit, peak, psrc = units[pipe]
+        achieved = nbytes / t / 1e9 if pipe == 0 else flops / t / 1e12
+        kernels[name] = {"ms_per_launch": tot_ms / n, "launches": n, "share": tot_ms / total,
+                         "bound": bound, "pipe": ["hbm", "fp64", "tensor", "fp32"][pipe],
+                         "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                         "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+                         "hbm_frac": nbytes / t / 1e9 / hbm}
+    top = max(kernels, key=lambda k: kernels[k]["share"])
+    k = kernels[top]
+    roofline = {"kernel": top, "bound": k["bound"], "achieved": k["achieved"], "peak": k["peak"],
+                "unit": k["unit"], "frac": k["frac"], "traffic": ncu_traffic(top, L, B),
+                "peak_source": units[{"hbm": 0, "fp64": 1, "tensor": 2, "fp32": 3}[k["pipe"]]][3],
+                "ms_per_launch": k["ms_per_launch"],
+                "algorithmic_bytes_per_launch": k["algorithmic_bytes"],
+                "algorithmic_flops_per_launch": k["algorithmic_flops"]}
+    return kernels, roofline
 
 
 # ---------------------------------------------------------------------------
@@ -275,22 +313,11 @@ def main():
     value = world * B / (ms * 1e-3)
     launches = steps * (plan.launches_per_call(0) + plan.launches_per_call(1))
 
-    # roofline of the dominant kernel (longest total time in the timed region)
-    top = max(prof.items(), key=lambda kv: kv[1][0])
-    top_name, (top_ms, top_n) = top
+    # roofline: every kernel's algorithmic work (favest_kernel_work) per launch over its
+    # CUDA-event duration, against the peak of the unit that binds it; the line's
+    # roofline object is the kernel with the largest share of the timed region
     fp64_peak, fp32_peak = api.favest_probe_peaks()
-    roofline = None
-    if top_name.startswith("legendre"):
-        flops = fp64_flops_per_launch(L, B, prec_name)
-        achieved = flops / (top_ms / top_n * 1e-3) / 1e12
-        roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64",
-                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None,
-                    "peak_source": "FP64 FMA throughput measured live by favest_probe_peaks",
-                    "ms_per_launch": top_ms / top_n,
-                    "algorithmic_flops_per_launch": flops}
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
-                   "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+    kernels, roofline = kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B)
 
     # end-to-end through the public API with host buffers (pinned), per step:
     # H2D of the coefficients, adjoint + forward, D2H of the recovered coefficients

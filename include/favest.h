@@ -130,6 +130,24 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
  */
 int favest_set_weights_unit(favest_plan plan, int flag);
 
+/*
+ * The two transforms with per-call options (the operators reverse-mode
+ * differentiation needs; with flags = 0 they are favest_fwd and favest_adj).  Writing
+ * A for AdjVSHT (coefficients -> grid) and W for the diagonal of point weights
+ * W_j * 2 pi / nphi, FwdVSHT is A^H W, so
+ *   d/dT of FwdVSHT  is  (A^H W)^H = W A:  favest_adj_ex with FAVEST_FLAG_WEIGHTED,
+ *                        which multiplies the synthesised field by W in the inverse
+ *                        longitude DFT stage;
+ *   d/dc of AdjVSHT  is  A^H:              favest_fwd_ex with FAVEST_FLAG_UNIT_WEIGHTS.
+ * Any other flag bit is FAVEST_EINVAL.  Calls on one plan must not overlap in time on
+ * the host (the flags live in the plan for the duration of the call).
+ */
+enum { FAVEST_FLAG_UNIT_WEIGHTS = 1, FAVEST_FLAG_WEIGHTED = 2 };
+int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags,
+                  void *stream);
+int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags,
+                  void *stream);
+
 /* Plan properties (host). */
 int favest_plan_L(favest_plan plan);
 int favest_plan_batch(favest_plan plan);
@@ -163,6 +181,17 @@ int favest_launches_per_call(favest_plan plan, int adjoint);
 int favest_profile_enable(favest_plan plan, int enable);
 int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *ms,
                         long long *launches);
+
+/*
+ * Algorithmic work of one launch of a kernel of this plan, by the name that
+ * favest_profile_read reports: *bytes = the minimum DRAM traffic (every operand read
+ * once, every result written once, no re-reads, no padding), *flops = arithmetic
+ * (an FMA counted as 2; for the FP64 recurrence every FP64 instruction is counted as
+ * one FMA slot, i.e. 2), *pipe = the unit that bounds it in this design
+ * (0 = HBM, 1 = FP64 pipe, 2 = tensor pipe, 3 = FP32 pipe).  Host-only, no GPU work.
+ * Returns FAVEST_OK, or FAVEST_EINVAL for an unknown name.
+ */
+int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, double *flops, int *pipe);
 
 /*
  * Measure the current device's FP64 and FP32 fused multiply-add throughput

@@ -26,6 +26,8 @@ FAVEST_FP64 = 0
 FAVEST_BF16X6 = 1
 FAVEST_IO_C128 = 0
 FAVEST_IO_C64 = 1
+FAVEST_FLAG_UNIT_WEIGHTS = 1
+FAVEST_FLAG_WEIGHTED = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +63,8 @@ def lib(build_if_missing=False):
             L.favest_plan_create.argtypes = [i, i, i, i, d, d, ctypes.POINTER(vp)]
             L.favest_fwd.argtypes = [vp, vp, vp, vp, vp, vp]
             L.favest_adj.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.favest_fwd_ex.argtypes = [vp, vp, vp, vp, vp, i, vp]
+            L.favest_adj_ex.argtypes = [vp, vp, vp, vp, vp, i, vp]
             L.favest_set_weights_unit.argtypes = [vp, i]
             L.favest_plan_L.argtypes = [vp]
             L.favest_plan_batch.argtypes = [vp]
@@ -74,6 +78,7 @@ def lib(build_if_missing=False):
             L.favest_strerror.restype = ctypes.c_char_p
             L.favest_launches_per_call.argtypes = [vp, i]
             L.favest_probe_peaks.argtypes = [d, d]
+            L.favest_kernel_work.argtypes = [vp, ctypes.c_char_p, d, d, ctypes.POINTER(ctypes.c_int)]
             L.favest_fwd_fp64_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp]
             L.favest_noalloc_scratch_bytes.restype = ctypes.c_size_t
             L.favest_profile_enable.argtypes = [vp, i]
@@ -142,6 +147,16 @@ def favest_fwd(plan, Tth, Tph, a, b, stream=None):
 def favest_adj(plan, a, b, Tth, Tph, stream=None):
     _check(lib().favest_adj(ctypes.c_void_p(plan), _ptr(a), _ptr(b), _ptr(Tth), _ptr(Tph),
                             _stream(stream)), "favest_adj")
+
+
+def favest_fwd_ex(plan, Tth, Tph, a, b, flags, stream=None):
+    _check(lib().favest_fwd_ex(ctypes.c_void_p(plan), _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b), int(flags),
+                               _stream(stream)), "favest_fwd_ex")
+
+
+def favest_adj_ex(plan, a, b, Tth, Tph, flags, stream=None):
+    _check(lib().favest_adj_ex(ctypes.c_void_p(plan), _ptr(a), _ptr(b), _ptr(Tth), _ptr(Tph), int(flags),
+                               _stream(stream)), "favest_adj_ex")
 
 
 def favest_set_weights_unit(plan, flag):
@@ -258,11 +273,10 @@ class Plan:
             b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=Tth.device)
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
-        self.set_unit_weights(1 if unit_weights else 0)
-        favest_fwd(self.handle, Tth, Tph, a, b, stream)
+        favest_fwd_ex(self.handle, Tth, Tph, a, b, FAVEST_FLAG_UNIT_WEIGHTS if unit_weights else 0, stream)
         return a, b
 
-    def adj(self, a, b, Tth=None, Tph=None, stream=None):
+    def adj(self, a, b, Tth=None, Tph=None, stream=None, weighted=False):
         import torch
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
@@ -272,7 +286,7 @@ class Plan:
             Tph = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device)
         self._check_tensor(Tth, self.field_shape(), "Tth")
         self._check_tensor(Tph, self.field_shape(), "Tph")
-        favest_adj(self.handle, a, b, Tth, Tph, stream)
+        favest_adj_ex(self.handle, a, b, Tth, Tph, FAVEST_FLAG_WEIGHTED if weighted else 0, stream)
         return Tth, Tph
 
     def status(self, stream=None):
@@ -289,3 +303,13 @@ class Plan:
 
     def profile_read(self):
         return favest_profile_read(self.handle)
+
+    def kernel_work(self, name):
+        """(algorithmic bytes, flops, pipe) of one launch of kernel `name` (0 = HBM,
+        1 = FP64 pipe, 2 = tensor pipe, 3 = FP32 pipe)."""
+        nb = ctypes.c_double()
+        fl = ctypes.c_double()
+        pipe = ctypes.c_int()
+        _check(lib().favest_kernel_work(ctypes.c_void_p(self.handle), name.encode(), ctypes.byref(nb),
+                                        ctypes.byref(fl), ctypes.byref(pipe)), "favest_kernel_work")
+        return nb.value, fl.value, pipe.value

@@ -1,0 +1,76 @@
+"""Reverse-mode differentiation of FwdVSHT and AdjVSHT (torch.autograd.Function).
+
+Writing A for AdjVSHT (coefficients (a, b) -> tangent field (T_theta, T_phi) on the
+grid, Def. AdjVSHT, eq. SLvec) and W for the diagonal of point weights W_j 2 pi / nphi,
+FwdVSHT (Def. FwdVSHT, eq. fwdvsht2) is A^H W.  Both maps are complex-linear, so the
+vector-Jacobian product of each is its Hermitian transpose applied to the incoming
+gradient (PyTorch's complex gradients are conjugate Wirtinger derivatives, for which a
+linear map M back-propagates by M^H):
+
+    FwdVSHT backward:  grad_T = W A grad_(a,b)       weighted adjoint kernel path
+    AdjVSHT backward:  grad_(a,b) = A^H grad_T       forward kernel path, unit weights
+
+Both backward passes run the library's own kernels (favest_adj_ex with
+FAVEST_FLAG_WEIGHTED, favest_fwd_ex with FAVEST_FLAG_UNIT_WEIGHTS); the Legendre
+values are regenerated by the recurrence inside those kernels, nothing is stored
+between the forward and the backward pass.
+"""
+import torch
+
+from . import api
+
+
+def _contig(t, dtype):
+    if t is None:
+        return None
+    return t.to(dtype).contiguous()
+
+
+class _FwdVSHT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Tth, Tph, plan):
+        ctx.plan = plan
+        a, b = plan.fwd(_contig(Tth, plan.cdtype), _contig(Tph, plan.cdtype),
+                        stream=torch.cuda.current_stream().cuda_stream)
+        return a, b
+
+    @staticmethod
+    def backward(ctx, ga, gb):
+        plan = ctx.plan
+        if ga is None:
+            ga = torch.zeros(plan.coef_shape(), dtype=plan.cdtype, device="cuda")
+        if gb is None:
+            gb = torch.zeros(plan.coef_shape(), dtype=plan.cdtype, device="cuda")
+        gt, gp = plan.adj(_contig(ga, plan.cdtype), _contig(gb, plan.cdtype), weighted=True,
+                          stream=torch.cuda.current_stream().cuda_stream)
+        return gt, gp, None
+
+
+class _AdjVSHT(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, a, b, plan):
+        ctx.plan = plan
+        Tth, Tph = plan.adj(_contig(a, plan.cdtype), _contig(b, plan.cdtype),
+                            stream=torch.cuda.current_stream().cuda_stream)
+        return Tth, Tph
+
+    @staticmethod
+    def backward(ctx, gt, gp):
+        plan = ctx.plan
+        if gt is None:
+            gt = torch.zeros(plan.field_shape(), dtype=plan.cdtype, device="cuda")
+        if gp is None:
+            gp = torch.zeros(plan.field_shape(), dtype=plan.cdtype, device="cuda")
+        ga, gb = plan.fwd(_contig(gt, plan.cdtype), _contig(gp, plan.cdtype), unit_weights=True,
+                          stream=torch.cuda.current_stream().cuda_stream)
+        return ga, gb, None
+
+
+def fwd_vsht(plan, Tth, Tph):
+    """Differentiable FwdVSHT: (Tth, Tph) [batch, L+1, 2(L+1)] -> (a, b) [batch, L^2+2L]."""
+    return _FwdVSHT.apply(Tth, Tph, plan)
+
+
+def adj_vsht(plan, a, b):
+    """Differentiable AdjVSHT: (a, b) [batch, L^2+2L] -> (Tth, Tph) [batch, L+1, 2(L+1)]."""
+    return _AdjVSHT.apply(a, b, plan)

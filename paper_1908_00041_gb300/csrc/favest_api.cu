@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -110,7 +111,7 @@ void free_plan(Plan &p)
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
-                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol};
+                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -131,8 +132,10 @@ int build_tables(Plan &p)
         om[j] = p.h_w[j] * (2.0 * 3.14159265358979323846 / p.nphi) / sj;
         omu[j] = 1.0 / sj;
     }
+    std::vector<double> wring(p.nlat);
+    for (int j = 0; j < p.nlat; ++j) wring[j] = p.h_w[j] * (2.0 * 3.14159265358979323846 / p.nphi);
     if ((e = upload(&p.d_x, x)) || (e = upload(&p.d_sin, s)) || (e = upload(&p.d_omega, om)) ||
-        (e = upload(&p.d_omega_unit, omu)))
+        (e = upload(&p.d_omega_unit, omu)) || (e = upload(&p.d_wring, wring)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
 
     std::vector<double> cmu(L + 1);
@@ -507,8 +510,31 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
 
 int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, void *stream)
 {
+    return favest_fwd_ex(plan, Tth, Tph, a, b, 0, stream);
+}
+
+int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, void *stream)
+{
+    return favest_adj_ex(plan, a, b, Tth, Tph, 0, stream);
+}
+
+namespace {
+
+// Restores a plan field when the call returns.
+struct FlagScope {
+    int &ref, saved;
+    FlagScope(int &r, int v) : ref(r), saved(r) { ref = v; }
+    ~FlagScope() { ref = saved; }
+};
+
+}  // namespace
+
+int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags, void *stream)
+{
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
+    if (flags & ~FAVEST_FLAG_UNIT_WEIGHTS) return FAVEST_EINVAL;
     Plan &p = plan->p;
+    FlagScope unit(p.unit_weights, p.unit_weights | ((flags & FAVEST_FLAG_UNIT_WEIGHTS) ? 1 : 0));
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
@@ -528,10 +554,12 @@ int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void
     return cuda_status(e);
 }
 
-int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, void *stream)
+int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags, void *stream)
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
+    if (flags & ~FAVEST_FLAG_WEIGHTED) return FAVEST_EINVAL;
     Plan &p = plan->p;
+    FlagScope weighted(p.adj_weighted, (flags & FAVEST_FLAG_WEIGHTED) ? 1 : 0);
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
@@ -617,6 +645,52 @@ int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *
         ++k;
     }
     return k;
+}
+
+int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, double *flops, int *pipe)
+{
+    if (!plan || !kernel || !bytes || !flops || !pipe) return FAVEST_EINVAL;
+    const Plan &p = plan->p;
+    const double L = p.L, B = p.B, J = p.J, L1 = p.L + 1, K = (double)p.L * p.L + 2.0 * p.L;
+    const double nlat = p.nlat, nphi = p.nphi;
+    // recurrence steps: rows l = mu..L+1 of every order, at every folded latitude
+    double rows = 0;
+    for (int mu = 0; mu <= p.L; ++mu) rows += p.L + 2 - mu;
+    const double steps = rows * J;
+    const std::string k(kernel);
+    *bytes = 0;
+    *flops = 0;
+    *pipe = 0;
+    if (p.precision == FAVEST_BF16X6) {
+        const double grid = 2.0 * B * nlat * nphi * 8.0;       // complex64 components
+        if (k == "fft_fwd") { *bytes = grid + J * B * L1 * 96.0; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+        else if (k == "fft_inv") { *bytes = J * B * L1 * 64.0 + grid; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = steps * 6.0; *flops = steps * 4.0; *pipe = 1; }
+        else if (k == "tc_gemm_fwd") { *bytes = steps * 6.0 + J * B * L1 * 96.0 + rows * B * 32.0; *flops = 12.0 * steps * 8.0 * B; }
+        else if (k == "tc_gemm_adj") { *bytes = steps * 6.0 + rows * B * 48.0 + J * B * L1 * 64.0; *flops = 12.0 * steps * 8.0 * B; }
+        else if (k == "combine") { *bytes = rows * B * 32.0 + 2.0 * B * K * 8.0; *flops = 16.0 * B * K; }
+        else if (k == "uncombine") { *bytes = 2.0 * B * K * 8.0 + rows * B * 48.0; *flops = 24.0 * B * K; }
+        else if (k == "polar_patch") {
+            const double jc = p.pol_jc, mc = p.pol_muc;
+            *bytes = jc * L1 * mc * 8.0 + 2.0 * B * L * 2.0 * mc * 8.0 + jc * B * mc * 64.0;
+            *flops = jc * mc * L * B * 32.0;
+            *pipe = 3;
+        } else return FAVEST_EINVAL;
+        return FAVEST_OK;
+    }
+    const double io = p.io == FAVEST_IO_C128 ? 16.0 : 8.0;
+    const double grid = 2.0 * B * nlat * nphi * io;
+    const double fbuf = L1 * p.ncol * nlat * 16.0, qbuf = (double)p.ntab * p.ncol * 16.0;
+    // per step: 2 recurrence instructions + 2 FMAs (re, im) per column
+    const double leg = steps * (4.0 + 4.0 * p.ncol);
+    if (k == "fft_fwd") { *bytes = grid + fbuf; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+    else if (k == "fft_inv") { *bytes = B * 2.0 * nlat * nphi * 16.0 + grid; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+    else if (k == "legendre_analysis") { *bytes = fbuf + qbuf; *flops = leg; *pipe = 1; }
+    else if (k == "legendre_synthesis") { *bytes = qbuf + B * 2.0 * nlat * nphi * 16.0; *flops = leg; *pipe = 1; }
+    else if (k == "combine") { *bytes = qbuf + 2.0 * B * K * io; *flops = 16.0 * B * K; }
+    else if (k == "uncombine") { *bytes = 2.0 * B * K * io + qbuf; *flops = 24.0 * B * K; }
+    else return FAVEST_EINVAL;
+    return FAVEST_OK;
 }
 
 void favest_plan_destroy(favest_plan plan)

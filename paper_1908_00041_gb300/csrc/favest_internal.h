@@ -64,6 +64,7 @@ struct Plan {
     int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
     int ct = 0, ng = 0;       // FP64 column group width and count
     int unit_weights = 0;
+    int adj_weighted = 0;         // set for the duration of a weighted adjoint call
     int device = 0;
     int num_sms = 0;
     long long ntab = 0;       // sum_mu (L + 2 - mu): rows of every per-(l, mu) table
@@ -76,6 +77,7 @@ struct Plan {
     double *d_sin = nullptr;      // [J] sin(theta_j)
     double *d_omega = nullptr;    // [J] quadrature weight / sin(theta_j)
     double *d_omega_unit = nullptr;  // [J] 1 / sin(theta_j)
+    double *d_wring = nullptr;    // [nlat] point weights W_j * 2 pi / nphi
     double *d_cmu = nullptr;      // [L+1] sectoral normalisation sqrt((2mu+1)!!/(4pi (2mu)!!))
     double *d_A = nullptr;        // [ntab] recurrence multipliers A_l^mu
     double *d_P = nullptr;        // [ntab] combine coefficient P_l^mu

@@ -40,11 +40,12 @@ __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
 }
 
 // Inverse: read spectrum row G[b][c][j][bin] (Nyquist bin L+1 taken as zero), inverse
-// FFT (no 1/n), write ring to T (io type TO).
+// FFT (no 1/n), scale by wring[j] when given (the weighted adjoint W A c), write ring
+// to T (io type TO).
 template <typename TO>
 __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     const double2 *__restrict__ G, TO *__restrict__ Tth, TO *__restrict__ Tph,
-    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat)
+    RadixPlanArg rp, const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -59,7 +60,15 @@ __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     __syncthreads();
     const double2 *out = stockham<true>(buf0, buf1, tw, rp);
     TO *dst = (c == 0 ? Tth : Tph) + ((size_t)b * nlat + j) * n;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = from_d2<TO>(out[k]);
+    if (wring) {
+        const double w = wring[j];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const double2 v = out[k];
+            dst[k] = from_d2<TO>(make_double2(w * v.x, w * v.y));
+        }
+    } else {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = from_d2<TO>(out[k]);
+    }
 }
 
 int fft_threads(int n) { return n >= 512 ? 256 : (n >= 128 ? 128 : 64); }
@@ -96,12 +105,12 @@ cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_
         auto k = k_fft_inv_fp64<double2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (double2 *)Tth, (double2 *)Tph, rp,
-                                 p.fft.tw64, p.L, p.nlat);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat);
     } else {
         auto k = k_fft_inv_fp64<float2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (float2 *)Tth, (float2 *)Tph, rp,
-                                 p.fft.tw64, p.L, p.nlat);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat);
     }
     return cudaGetLastError();
 }

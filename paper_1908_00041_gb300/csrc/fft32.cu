@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
 template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj, int L, int nlat,
-    int J, int has_eq, int nf)
+    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
+    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int nf)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -309,7 +309,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const int b = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;
-    const float is = (float)(1.0 / sj[j]);
+    // 1/sin(theta_j), times the point weight of rings j and nlat-1-j (equal) for the
+    // weighted adjoint
+    const double wj = wring ? wring[j] : 1.0;
+    const float is = (float)(wj / sj[j]);
+    const float w0 = (float)wj;
     if (LOG2N > 0) {
         // every bin but n/2 is written below
         if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     }
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
         // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
-        const float sc = mu == 0 ? 1.0f : is;
+        const float sc = mu == 0 ? w0 : is;
         const float4 *e = reinterpret_cast<const float4 *>(S32 + ((((size_t)j * nf + b) * (L + 1) + mu) * 2) * 8);
         const float4 *o = e + 2;
         const float4 e0 = __ldg(e), e1 = __ldg(e + 1), o0 = __ldg(o), o1 = __ldg(o + 1);
@@ -382,7 +386,8 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
     auto k = k_fft_inv_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
-                                   p.d_perm, p.d_sin, p.L, p.nlat, p.J, p.has_eq, p.nf);
+                                   p.d_perm, p.d_sin, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
+                                   p.has_eq, p.nf);
     return cudaGetLastError();
 }
 
