@@ -43,7 +43,9 @@ class FavestError(RuntimeError):
 
 
 def library_path():
-    return _build.LIB
+    """The in-tree library, or the file named by FAVEST_LIBRARY (an alternative build
+    of the same sources, e.g. one made with different compile flags)."""
+    return os.environ.get("FAVEST_LIBRARY") or _build.LIB
 
 
 def lib(build_if_missing=False):
@@ -51,7 +53,7 @@ def lib(build_if_missing=False):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = library_path()
             if not os.path.exists(path):
                 if not build_if_missing:
                     raise FavestError(FAVEST_EUNSUPPORTED,

@@ -2,7 +2,8 @@
 //   combine  : FP32 scalar sums Q (tensor-core GEMM output, rows l - mu, 8 columns per
 //              field: component c, sign s of m, re/im) -> a_lm, b_lm (complex64), FP64 math
 //   uncombine: a_lm, b_lm (complex64) -> scaled scalar coefficients g, written as three
-//              bf16 pieces in the tensor-core B-operand layout.
+//              bf16 pieces in the tensor-core B-operand layout (K-chunks of 32 rows by
+//              N = 128 or 256 columns).
 #include "favest_internal.h"
 
 #include <cuda_bf16.h>
@@ -11,25 +12,28 @@ namespace favest {
 
 namespace {
 
-constexpr int kChunkBytes = 3 * 16384;
 
-// grid.x over (b, l): one CTA per (field, degree); threads over mu = 0..l.
-// Q = [field][l][mu][8] (l = 0..L+1, mu = 0..L): consecutive threads read consecutive
-// 32-byte entries and write consecutive coefficients.
+// grid (L+1, B): one CTA per (order mu, field); threads over degrees l = max(mu,1)..L.
+// Q = [field][ntab rows][8]: the rows of order mu start at tab_off(L, mu), the
+// n0 = ceil((L+2-mu)/2) rows l = mu, mu+2, .. first, then l = mu+1, mu+3, ..; a warp
+// reads two contiguous runs of 32-byte records.  The coefficient stores of one CTA are
+// 8-byte words 2l+1 apart; the CTAs of neighbouring orders fill the rest of each line.
 __global__ void k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a, float2 *__restrict__ bo,
                                const float *__restrict__ P, const float *__restrict__ M,
                                const float *__restrict__ R, int L, int K)
 {
-    const int bi = blockIdx.x / L, l = blockIdx.x % L + 1;
-    const size_t L1 = (size_t)L + 1;
-    const float *qb = Q + (size_t)bi * (L + 2) * L1 * 8;
-    for (int mu = threadIdx.x; mu <= l; mu += blockDim.x) {
-        const long long row = tab_off(L, mu) + (l - mu);
-        const float Pl = P[row], Ml = M[row], Rl = R[row];
-        const float *q1 = qb + ((size_t)(l + 1) * L1 + mu) * 8;
-        const float *q0 = qb + ((size_t)l * L1 + mu) * 8;
-        const float *qm = qb + ((size_t)(l - 1) * L1 + mu) * 8;
-        const bool has_m = l > mu;
+    const int mu = blockIdx.x, bi = blockIdx.y;
+    const long long t0 = tab_off(L, mu);
+    const float *qb = Q + ((size_t)bi * tab_off(L, L + 1) + t0) * 8;
+    const int n0 = (L + 3 - mu) / 2;            // rows of even l - mu
+    auto qrow = [&](int r) { return qb + (((r & 1) ? n0 : 0) + (r >> 1)) * 8; };
+    for (int l = (mu > 1 ? mu : 1) + threadIdx.x; l <= L; l += blockDim.x) {
+        const int r = l - mu;
+        const float Pl = P[t0 + r], Ml = M[t0 + r], Rl = R[t0 + r];
+        const float *q1 = qrow(r + 1);
+        const float *q0 = qrow(r);
+        const bool has_m = r > 0;
+        const float *qm = qrow(has_m ? r - 1 : r);
         for (int s = 0; s < 2; ++s) {
             if (mu == 0 && s == 1) continue;
             const int m = s ? -mu : mu;
@@ -82,14 +86,17 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
                                  unsigned char *__restrict__ gb, const long long *__restrict__ g_off,
                                  const float *__restrict__ P, const float *__restrict__ M,
                                  const float *__restrict__ R, const float *__restrict__ k1tab, int L, int K,
-                                 int n_tiles)
+                                 int N)
 {
     const int mu = blockIdx.x, bi = blockIdx.y;
     const long long t0 = tab_off(L, mu);
     const int nrow = L + 2 - (mu == 0 ? 1 : mu);
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
-    const int nka0 = (nrow_p0 + 63) / 64, nka1 = (nrow_p1 + 63) / 64;
-    const int nt = bi / 16, bg = bi % 16;
+    constexpr int KC = kGemmChunkK;
+    const int nka0 = (nrow_p0 + KC - 1) / KC, nka1 = (nrow_p1 + KC - 1) / KC;
+    const int fpt = N / 8;                        // fields per column tile
+    const int nt = bi / fpt, bg = bi % fpt;
+    const long long piece = (long long)KC * N * 2, chunk = 3 * piece;
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
         const int l = (mu == 0 ? 1 : mu) + r;
         float v[8];
@@ -124,9 +131,10 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
         }
         const int p = r & 1, rp = r >> 1;
         const int nka = p ? nka1 : nka0;
-        const int kc = rp / 64, rr = rp % 64;
-        unsigned char *dst = gb + g_off[mu * 2 + p] + ((size_t)nt * nka + kc) * kChunkBytes +
-                             (size_t)(rr / 8) * 2048 + bg * 128 + (rr % 8) * 16;
+        const int kc = rp / KC, rr = rp % KC;
+        // chunk [K/8][N/8][8 k][8 n]: row group rr/8, column group = this field
+        unsigned char *dst = gb + g_off[mu * 2 + p] + ((long long)nt * nka + kc) * chunk +
+                             (long long)(rr / 8) * (fpt * 128) + bg * 128 + (rr % 8) * 16;
         unsigned w[3][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -139,7 +147,7 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            *reinterpret_cast<uint4 *>(dst + q * 16384) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            *reinterpret_cast<uint4 *>(dst + q * piece) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
     }
 }
 
@@ -148,9 +156,10 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
 cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
 {
     const int K = p.L * p.L + 2 * p.L;
-    const int th = p.L >= 128 ? 128 : 32;
-    k_combine_bf16<<<p.B * p.L, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32,
-                                             p.d_M32, p.d_R32, p.L, K);
+    const int th = p.L >= 255 ? 256 : (p.L >= 63 ? 64 : 32);
+    dim3 grid(p.L + 1, p.B);
+    k_combine_bf16<<<grid, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32, p.d_M32,
+                                       p.d_R32, p.L, K);
     return cudaGetLastError();
 }
 
@@ -160,7 +169,7 @@ cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, c
     dim3 grid(p.L + 1, p.B);
     const int th = p.L + 2 >= 256 ? 256 : 64;
     k_uncombine_bf16<<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb,
-                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.n_tiles);
+                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n);
     return cudaGetLastError();
 }
 

@@ -235,7 +235,7 @@ int make_fb_tensor_map(Plan &p)
     const cuuint64_t L1 = (cuuint64_t)(p.L + 1);
     cuuint64_t dims[5] = {48, L1, 8, (cuuint64_t)p.nf, (cuuint64_t)(p.JP / 8)};
     cuuint64_t strides[4] = {96, 96 * L1, 768 * L1, 768 * L1 * (cuuint64_t)p.nf};
-    cuuint32_t box[5] = {8, 1, 8, 16, 8};
+    cuuint32_t box[5] = {8, 1, 8, (cuuint32_t)(p.gemm_n / 8), (cuuint32_t)(kGemmChunkK / 8)};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = encode(&p.tmap_fb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p.d_Fb, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -244,21 +244,30 @@ int make_fb_tensor_map(Plan &p)
 }
 
 // Split-precision path: operand tile offsets, GEMM work items, buffers.
-//   Lam (A operands): contiguous 48 KB chunks (three 16 KB bf16 pieces), bulk copies
+//   Lam (A operands): contiguous 24 KB chunks (three 8 KB bf16 pieces of 128 x 32), bulk copies
 //   Fb  (forward B):  [JP/8][nf][8][L+1][2][3][8] bf16, loaded through the tensor map
-//   g   (adjoint B):  contiguous 48 KB chunks
-//   Q32 (forward out): [nf][L+2][L+1][8] fp32, entry (field, l, mu)
-//   S32 (adjoint out): [JP][nf][L+1][2][8] fp32, entry (latitude, field, mu, parity)
+//   g   (adjoint B):  contiguous chunks of three 32 x N bf16 pieces (N = gemm_n)
+//   Q32 (forward out): [nf][ntab][8] fp32: field, then for each order mu (from row
+//                      tab_off(L, mu)) its rows l = mu, mu+2, .. followed by l = mu+1, ..
+//   S32 (adjoint out): [nf][JP/4][L+1][2][4][8] fp32: field, latitude group of 4, mu,
+//                      parity, latitude within the group
+// The GEMM epilogue stores 128-byte groups of 4 rows (one per 4 lanes of a warp); the
+// inverse FFT of latitude j reads the 32-byte record of j, and the blocks of the 4
+// latitudes of a group, adjacent in launch order, share each 128-byte line.
 int alloc_workspace_bf16(Plan &p)
 {
     const int L = p.L;
-    const long long CH = 3LL * 16384;          // bytes per operand chunk (3 bf16 pieces)
+    const int KC = kGemmChunkK;
+    const long long CHA = 3LL * 128 * KC * 2;    // bytes per A chunk (3 bf16 pieces of 128 x KC)
+    p.gemm_n = 8 * p.B > 128 ? 256 : 128;
+    const long long CHB = 3LL * KC * p.gemm_n * 2;   // bytes per B chunk (3 pieces of KC x N)
     p.JP = (p.J + 127) / 128 * 128;
-    p.ncolr = (8 * p.B + 127) / 128 * 128;
-    p.n_tiles = p.ncolr / 128;
+    p.ncolr = (8 * p.B + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
+    p.n_tiles = p.ncolr / p.gemm_n;
     p.nf = p.ncolr / 8;
-    p.nk_f = p.JP / 64;
-    const long long L1 = L + 1, L2 = L + 2;
+    p.nk_f = p.JP / KC;
+    const int fpt = p.gemm_n / 8;                  // fields per column tile
+    const long long L1 = L + 1;
     std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
     long long lam_f = 0, lam_a = 0, gsz = 0;
     std::vector<TcItem> itf, ita;
@@ -273,9 +282,9 @@ int alloc_workspace_bf16(Plan &p)
             off_f[idx] = lam_f;
             off_a[idx] = lam_a;
             off_g[idx] = gsz;
-            lam_f += (long long)((np + 127) / 128) * p.nk_f * CH;
-            lam_a += (long long)(p.JP / 128) * ((np + 63) / 64) * CH;
-            gsz += (long long)p.n_tiles * ((npa + 63) / 64) * CH;
+            lam_f += (long long)((np + 127) / 128) * p.nk_f * CHA;
+            lam_a += (long long)(p.JP / 128) * ((np + KC - 1) / KC) * CHA;
+            gsz += (long long)p.n_tiles * ((npa + KC - 1) / KC) * CHB;
         }
     }
     // pass 2: GEMM work items
@@ -287,34 +296,35 @@ int alloc_workspace_bf16(Plan &p)
             for (int m = 0; m < mt; ++m)
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_f[idx] + (long long)m * p.nk_f * CH;
-                    I.a_stride = (int)CH;
+                    I.a_off = off_f[idx] + (long long)m * p.nk_f * CHA;
+                    I.a_stride = (int)CHA;
                     I.b_tma = 1;
                     I.bx = par * 3 * 8;
-                    I.by = 16 * nt;
+                    I.by = fpt * nt;
                     I.bz0 = 0;
                     I.bw = mu;
-                    const long long l0 = mu + par + 256LL * m;       // degree of output row 0
-                    I.out_off = ((16LL * nt * L2 + l0) * L1 + mu) * 8;
-                    I.out_ld = 2 * L1 * 8;
-                    I.col_gs = L2 * L1 * 8;
+                    // rows of (mu, par) are consecutive in Q32 (see the layout note above)
+                    const long long qrow = tab_off(L, mu) + (par ? nrow_p(mu, 0) : 0) + 128LL * m;
+                    I.out_off = ((long long)fpt * nt * p.ntab + qrow) * 8;
+                    I.out_ld = 32;
+                    I.col_gs = p.ntab * 8;
                     I.nk = p.nk_f;
                     I.rows = np - 128 * m < 128 ? np - 128 * m : 128;
                     itf.push_back(I);
                 }
             const int amu = mu == 0 ? 1 : mu;
-            const int nka = (nrow_p(amu, par) + 63) / 64;
+            const int nka = (nrow_p(amu, par) + KC - 1) / KC;
             for (int t = 0; t < p.JP / 128; ++t)
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_a[amu * 2 + par] + (long long)t * nka * CH;
-                    I.b_off = off_g[idx] + (long long)nt * nka * CH;
-                    I.a_stride = (int)CH;
-                    I.b_stride = (int)CH;
+                    I.a_off = off_a[amu * 2 + par] + (long long)t * nka * CHA;
+                    I.b_off = off_g[idx] + (long long)nt * nka * CHB;
+                    I.a_stride = (int)CHA;
+                    I.b_stride = (int)CHB;
                     I.b_tma = 0;
-                    I.out_off = (((128LL * t) * p.nf + 16LL * nt) * L1 + mu) * 16 + par * 8;
-                    I.out_ld = (long long)p.nf * L1 * 16;
-                    I.col_gs = L1 * 16;
+                    I.out_off = ((((long long)fpt * nt * (p.JP / 4) + 32LL * t) * L1 + mu) * 2 + par) * 32;
+                    I.out_ld = L1 * 2 * 32;
+                    I.col_gs = (long long)(p.JP / 4) * L1 * 2 * 32;
                     I.nk = nka;
                     I.rows = 128;
                     ita.push_back(I);
@@ -327,8 +337,8 @@ int alloc_workspace_bf16(Plan &p)
     p.n_items_a = (int)ita.size();
     const size_t lam_bytes = (size_t)(lam_f > lam_a ? lam_f : lam_a);
     const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 96;
-    const size_t q_bytes = (size_t)p.nf * L2 * L1 * 8 * sizeof(float);
-    const size_t s_bytes = (size_t)p.JP * p.nf * L1 * 16 * sizeof(float);
+    const size_t q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
+    const size_t s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
     if (cudaMalloc(&p.d_lam, lam_bytes) != cudaSuccess || cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         cudaMalloc(&p.d_gb, (size_t)gsz) != cudaSuccess || cudaMalloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||

@@ -43,6 +43,10 @@ struct FftPlan {
 
 // One tensor-core GEMM output tile: out[rows][128 cols] = sum over nk K-chunks of A_c * B_c.
 // Output element (r, c) goes to out[out_off + r*out_ld + (c/8)*col_gs + c%8].
+constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk
+
+// One GEMM work item.  Output row r (< rows) of field column group g is written at
+// out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs (8 floats per field).
 struct TcItem {
     long long a_off;    // byte offset of chunk 0 of A (three 16 KB bf16 pieces per chunk)
     long long b_off;    // byte offset of chunk 0 of B (bulk mode)
@@ -87,16 +91,17 @@ struct Plan {
 
     // split-precision (BF16X6) path
     int JP = 0;               // folded latitudes padded to a multiple of 128
-    int ncolr = 0;            // real columns per order: 8 per field, padded to 128
-    int n_tiles = 0;          // ncolr / 128
-    int nk_f = 0;             // forward K-chunks: JP / 64
+    int gemm_n = 128;         // GEMM tile width: 256 columns (32 fields) or 128 (16 fields)
+    int ncolr = 0;            // columns per order: 8 per field, padded to gemm_n
+    int n_tiles = 0;          // ncolr / gemm_n
+    int nk_f = 0;             // forward K-chunks: JP / kGemmChunkK
     int n_items_f = 0, n_items_a = 0;
     void *d_lam = nullptr;        // Legendre operand tiles (bf16 x 3)
     void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
-    float *d_Q32 = nullptr;       // forward GEMM output [field][l(l+1)/2 + mu][8]
+    float *d_Q32 = nullptr;       // forward GEMM output [field][l][mu][8]
     float *d_S32 = nullptr;       // adjoint GEMM output [JP][field][mu][parity][8]
-    int nf = 0;                   // fields padded to a multiple of 16 (ncolr / 8)
+    int nf = 0;                   // fields padded to a multiple of gemm_n / 8 (ncolr / 8)
     CUtensorMap tmap_fb;          // forward B operand: Fb[JP][nf][L+1][parity][piece][8] bf16
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
@@ -149,6 +154,5 @@ cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
 cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s);
 cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s);
 int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
-size_t tc_gemm_smem_bytes();
 
 }  // namespace favest

@@ -296,12 +296,12 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     }
 }
 
-// grid: B * J; S32 = [JP][nf][L+1][parity][8] fp32; shared 4 * n float2 (+ padding)
+// grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
 template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
     const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
-    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int nf)
+    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -324,8 +324,9 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
         // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
         const float sc = mu == 0 ? w0 : is;
-        const float4 *e = reinterpret_cast<const float4 *>(S32 + ((((size_t)j * nf + b) * (L + 1) + mu) * 2) * 8);
-        const float4 *o = e + 2;
+        const float4 *e = reinterpret_cast<const float4 *>(
+            S32 + ((((size_t)b * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
+        const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
         const float4 e0 = __ldg(e), e1 = __ldg(e + 1), o0 = __ldg(o), o1 = __ldg(o + 1);
         const float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
         const float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
@@ -387,7 +388,7 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
                                    p.d_perm, p.d_sin, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
-                                   p.has_eq, p.nf);
+                                   p.has_eq, p.JP);
     return cudaGetLastError();
 }
 

@@ -12,11 +12,13 @@
 // K-chunk of 64 and added to an FP32 register sum (round-to-nearest) by the epilogue;
 // the five correction products, 2^-8 smaller, accumulate in TMEM over the whole K.
 //
-// Operand tiles in global memory are pre-arranged so that one K-chunk of one piece is
-// a contiguous 16 KB block in the shared-memory core-matrix layout (see tc.cuh):
-//   forward A (Lam, M = rows, K = j, MN-major): [K/8 groups][M/8 groups][8 j][8 rows]
-//   adjoint A (Lam^T, M = j, K = rows, K-major): [M/8][K/8][8 j][8 rows]
-//   B (Fb or g, K x N, MN-major):               [K/8][N/8][8 k][8 n]
+// One work item is a 128 x N output tile (N = 256 columns, i.e. 32 fields, or 128 for
+// small batches) over its whole K range, in K-chunks of 32.  Operand tiles in global
+// memory are pre-arranged so that one K-chunk of one piece is a contiguous block in the
+// shared-memory core-matrix layout (see tc.cuh):
+//   forward A (Lam, M = rows, K = j, MN-major): [K/8 groups][M/8 groups][8 j][8 rows]  8 KB
+//   adjoint A (Lam^T, M = j, K = rows, K-major): [M/8][K/8][8 j][8 rows]               8 KB
+//   B (Fb or g, K x N, MN-major):               [K/8][N/8][8 k][8 n]           K32 x N x 2 B
 #include "favest_internal.h"
 #include "recurrence.cuh"
 #include "tc.cuh"
@@ -28,11 +30,11 @@ namespace favest {
 namespace {
 
 constexpr int kGenThreads = 128;
-constexpr int kChunkK = 64;                      // K depth of one operand chunk
-constexpr int kTileM = 128, kTileN = 128;
-constexpr int kPieceBytes = kTileM * kChunkK * 2;  // 16 KB (also 64 x 128 for B)
+constexpr int kChunkK = kGemmChunkK;              // K depth of one operand chunk (32)
+constexpr int kTileM = 128;
+constexpr int kPieceBytes = kTileM * kChunkK * 2;  // 8 KB: one bf16 piece of an A chunk
 constexpr int kPieces = 3;
-constexpr int kChunkBytes = kPieces * kPieceBytes;  // 48 KB
+constexpr int kChunkBytes = kPieces * kPieceBytes;  // 24 KB
 
 // FP64 value -> three bf16 pieces.  The value is first truncated to FP32 with integer
 // operations (FP64->FP32 conversion instructions run on the FP64 pipe), then split
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
                     const int jt = j / kTileM, jj = j % kTileM;
                     const int kc = rp / kChunkK, rr = rp % kChunkK;
                     off = base + ((long long)jt * nka + kc) * kChunkBytes +
-                          (jj / 8) * 1024 + (rr / 8) * 128 + (jj % 8) * 16;
+                          (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
                 }
 #pragma unroll
                 for (int q = 0; q < kPieces; ++q) {
@@ -152,22 +154,32 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
 }
 
 // ---------------------------------------------------------------------------
-// Persistent GEMM: every item computes out[rows 0..127][cols 0..127] =
+// Persistent GEMM: every item computes out[rows 0..127][cols 0..N-1] =
 //   sum_{c < nk} A_c * B_c  (three bf16 pieces each, 6 products)
+// Warp 0 loads operands (bulk copies; the forward B operand through a TMA tensor map),
+// warp 1 issues the MMAs, warps 2.. drain TMEM (each a 32-lane quadrant and 128 columns).
+// TMEM: columns [0, N) hold the hi*hi product of the current K-chunk (drained into FP32
+// register sums after every chunk), columns [N, 2N) accumulate the five correction
+// products over the whole item.  Per chunk the MMA warp issues the corrections first,
+// which gives the epilogue time to drain the previous chunk's hi*hi columns.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 2;
-constexpr int kGemmThreads = 192;   // warp 0 producer, warp 1 MMA, warps 2..5 epilogue
+constexpr int kStages = 3;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kColMain0 = 0, kColMain1 = 128, kColCorr = 256;
 
+template <int N>
 struct GemmSmem {
     unsigned char a[kStages][kChunkBytes];
-    unsigned char b[kStages][kChunkBytes];
+    unsigned char b[kStages][kPieces * kChunkK * N * 2];
     uint64_t full[kStages], empty[kStages];
-    uint64_t dmain_full[2], dmain_empty[2], dcorr_full, dcorr_empty;
+    uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
     uint32_t tmem_base;
     int abort;
 };
+
+constexpr int kEpiCols = 128;       // TMEM columns drained by one epilogue warp
+
+template <int N>
+constexpr int gemm_threads() { return 64 + 32 * 4 * (N / kEpiCols); }
 
 __device__ __forceinline__ void set_status(int *status, int code)
 {
@@ -184,13 +196,17 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     return false;
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
+template <int N>
+__global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     const unsigned char *__restrict__ Abuf, const unsigned char *__restrict__ Bbuf,
     const __grid_constant__ CUtensorMap tmap_b, const TcItem *__restrict__ items, int nitems,
     float *__restrict__ out, int a_mn_major, int *__restrict__ status)
 {
+    constexpr int kEpiWarps = 4 * (N / kEpiCols);   // 4 lane quadrants x N / 128 column parts
+    constexpr int kPieceB = kChunkK * N * 2;        // bytes of one B piece per chunk
+    constexpr int kChunkB = kPieces * kPieceB;
     extern __shared__ __align__(1024) unsigned char sm_raw[];
-    GemmSmem &S = *reinterpret_cast<GemmSmem *>(sm_raw);
+    GemmSmem<N> &S = *reinterpret_cast<GemmSmem<N> *>(sm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) tc::tmem_alloc(&S.tmem_base, kTmemCols);
@@ -199,12 +215,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
             tc::mbar_init(&S.full[s], 1);
             tc::mbar_init(&S.empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&S.dmain_full[b], 1);
-            tc::mbar_init(&S.dmain_empty[b], 4);
-        }
+        tc::mbar_init(&S.dmain_full, 1);
+        tc::mbar_init(&S.dmain_empty, kEpiWarps);
         tc::mbar_init(&S.dcorr_full, 1);
-        tc::mbar_init(&S.dcorr_empty, 4);
+        tc::mbar_init(&S.dcorr_empty, kEpiWarps);
         S.abort = 0;
         tc::mbar_fence_init();
     }
@@ -217,28 +231,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
     if (warp == 0) {
         // ---------------- producer ----------------
         if (lane == 0) {
-            uint32_t use[kStages] = {0, 0};
+            uint32_t phase = 0;                     // bit s: parity of stage s's next use
             int stage = 0;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const TcItem I = items[it];
                 for (int c = 0; c < I.nk; ++c) {
-                    if (!wait_or_abort(&S.empty[stage], (use[stage] & 1) ^ 1, abort)) {
+                    if (!wait_or_abort(&S.empty[stage], ((phase >> stage) & 1) ^ 1, abort)) {
                         set_status(status, FAVEST_ETIMEOUT);
                         *abort = 1;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&S.full[stage], 2 * kChunkBytes);
+                    tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkB);
                     tc::bulk_g2s(S.a[stage], Abuf + I.a_off + (long long)c * I.a_stride, kChunkBytes,
                                  &S.full[stage]);
                     if (I.b_tma) {
                         for (int q = 0; q < kPieces; ++q)
-                            tc::tma_load_5d(S.b[stage] + q * kPieceBytes, &tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
-                                            I.bz0 + 8 * c, &S.full[stage]);
+                            tc::tma_load_5d(S.b[stage] + q * kPieceB, &tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
+                                            I.bz0 + (kChunkK / 8) * c, &S.full[stage]);
                     } else {
-                        tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkBytes,
+                        tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkB,
                                      &S.full[stage]);
                     }
-                    use[stage]++;
+                    phase ^= 1u << stage;
                     stage = (stage + 1) % kStages;
                 }
             }
@@ -246,9 +260,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_f16(kTileM, kTileN, a_mn_major, 1) | (1u << 7) | (1u << 10);
-            uint32_t use[kStages] = {0, 0}, mu_use[2] = {0, 0}, corr_use = 0;
+            const uint32_t idesc = tc::idesc_f16(kTileM, N, a_mn_major, 1) | (1u << 7) | (1u << 10);
+            uint32_t phase = 0, main_use = 0, corr_use = 0;
             int stage = 0;
+            const uint32_t dmain = tmem, dcorr = tmem + N;
+            // A: MN-major (fwd): K-groups of 16 x 128 B, K-step = 2 groups;
+            //    K-major (adj):  [M/8][K/8] core matrices, K-step = 2 x 128 B.
+            // B: MN-major, K-groups of N/8 x 128 B.
+            const uint32_t a_step = a_mn_major ? 4096u : 256u;
+            const uint32_t a_lbo = a_mn_major ? 2048u : 128u, a_sbo = a_mn_major ? 128u : kChunkK / 8 * 128u;
+            constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const TcItem I = items[it];
                 if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort)) {
@@ -257,39 +278,44 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
                     break;
                 }
                 for (int c = 0; c < I.nk; ++c) {
-                    const int buf = c & 1;
-                    if (!wait_or_abort(&S.full[stage], use[stage] & 1, abort) ||
-                        !wait_or_abort(&S.dmain_empty[buf], (mu_use[buf] & 1) ^ 1, abort)) {
+                    if (!wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort)) {
                         set_status(status, FAVEST_ETIMEOUT);
                         *abort = 1;
                         break;
                     }
                     tc::fence_after_sync();
                     const uint32_t a0 = tc::smem_u32(S.a[stage]), b0 = tc::smem_u32(S.b[stage]);
-                    const uint32_t dmain = tmem + (buf ? kColMain1 : kColMain0), dcorr = tmem + kColCorr;
+                    // corrections (weights 2^-8 and 2^-16 of hi*hi) accumulate over the item
 #pragma unroll
                     for (int s = 0; s < kChunkK / 16; ++s) {
-                        uint64_t ad[3], bd[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            // A: MN-major (fwd): K-step = 2 K-groups of 2048 B; LBO 2048, SBO 128
-                            //    K-major (adj):  K-step = 2 K-groups of 128 B;   LBO 128, SBO 1024
-                            ad[q] = a_mn_major ? tc::sdesc(a0 + q * kPieceBytes + s * 4096, 2048, 128)
-                                               : tc::sdesc(a0 + q * kPieceBytes + s * 256, 128, 1024);
-                            bd[q] = tc::sdesc(b0 + q * kPieceBytes + s * 4096, 2048, 128);
-                        }
-                        tc::mma_f16(dmain, ad[0], bd[0], idesc, s > 0);
-                        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-                        tc::mma_f16(dcorr, ad[0], bd[1], idesc, acc);
-                        tc::mma_f16(dcorr, ad[1], bd[0], idesc, 1);
-                        tc::mma_f16(dcorr, ad[0], bd[2], idesc, 1);
-                        tc::mma_f16(dcorr, ad[1], bd[1], idesc, 1);
-                        tc::mma_f16(dcorr, ad[2], bd[0], idesc, 1);
+                        const uint32_t as = a0 + s * a_step, bs = b0 + s * b_step;
+                        const uint64_t A0 = tc::sdesc(as, a_lbo, a_sbo);
+                        const uint64_t A1 = tc::sdesc(as + kPieceBytes, a_lbo, a_sbo);
+                        const uint64_t A2 = tc::sdesc(as + 2 * kPieceBytes, a_lbo, a_sbo);
+                        const uint64_t B0 = tc::sdesc(bs, b_lbo, 128);
+                        const uint64_t B1 = tc::sdesc(bs + kPieceB, b_lbo, 128);
+                        const uint64_t B2 = tc::sdesc(bs + 2 * kPieceB, b_lbo, 128);
+                        tc::mma_f16(dcorr, A0, B1, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                        tc::mma_f16(dcorr, A1, B0, idesc, 1);
+                        tc::mma_f16(dcorr, A0, B2, idesc, 1);
+                        tc::mma_f16(dcorr, A1, B1, idesc, 1);
+                        tc::mma_f16(dcorr, A2, B0, idesc, 1);
                     }
+                    // hi*hi of this chunk into the drained main columns
+                    if (!wait_or_abort(&S.dmain_empty, (main_use & 1) ^ 1, abort)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int s = 0; s < kChunkK / 16; ++s)
+                        tc::mma_f16(dmain, tc::sdesc(a0 + s * a_step, a_lbo, a_sbo),
+                                    tc::sdesc(b0 + s * b_step, b_lbo, 128), idesc, s > 0);
                     tc::mma_commit(&S.empty[stage]);
-                    tc::mma_commit(&S.dmain_full[buf]);
-                    use[stage]++;
-                    mu_use[buf]++;
+                    tc::mma_commit(&S.dmain_full);
+                    phase ^= 1u << stage;
+                    main_use++;
                     stage = (stage + 1) % kStages;
                 }
                 if (*abort) break;
@@ -298,33 +324,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
             }
         }
     } else {
-        // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2,3,0,1) ----------------
+        // ------ epilogue (warp w >= 2: TMEM lane quadrant w % 4, columns 128 * ((w-2) / 4) ..) ------
         const int quad = warp & 3;
+        const int part = (warp - 2) >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        uint32_t mu_use[2] = {0, 0}, corr_use = 0;
-        float acc[kTileN];
+        uint32_t main_use = 0, corr_use = 0;
+        float acc[kEpiCols];
         for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
-            const TcItem I = items[it];
+            const int nk = __ldg(&items[it].nk);   // the rest of the item is read at the end
 #pragma unroll
-            for (int i = 0; i < kTileN; ++i) acc[i] = 0.f;
+            for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
             bool ok = true;
-            for (int c = 0; c < I.nk; ++c) {
-                const int buf = c & 1;
-                if (!wait_or_abort(&S.dmain_full[buf], mu_use[buf] & 1, abort)) { ok = false; break; }
+            for (int c = 0; c < nk; ++c) {
+                if (!wait_or_abort(&S.dmain_full, main_use & 1, abort)) { ok = false; break; }
                 tc::fence_after_sync();
-                const uint32_t col0 = tmem + lane_base + (buf ? kColMain1 : kColMain0);
+                const uint32_t col0 = tmem + lane_base + part * kEpiCols;
 #pragma unroll
-                for (int q = 0; q < kTileN / 32; ++q) {
-                    float v[32];
-                    tc::tmem_ld32(col0 + q * 32, v);
+                for (int q = 0; q < kEpiCols / 16; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(col0 + q * 16, v);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) acc[q * 32 + i] += v[i];
+                    for (int i = 0; i < 16; ++i) acc[q * 16 + i] += v[i];
                 }
                 tc::fence_before_sync();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&S.dmain_empty[buf]);
-                mu_use[buf]++;
+                if (lane == 0) tc::mbar_arrive(&S.dmain_empty);
+                main_use++;
             }
             if (!ok || !wait_or_abort(&S.dcorr_full, corr_use & 1, abort)) {
                 set_status(status, FAVEST_ETIMEOUT);
@@ -333,21 +359,25 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
             }
             tc::fence_after_sync();
 #pragma unroll
-            for (int q = 0; q < kTileN / 32; ++q) {
-                float v[32];
-                tc::tmem_ld32(tmem + lane_base + kColCorr + q * 32, v);
+            for (int q = 0; q < kEpiCols / 16; ++q) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + N + part * kEpiCols + q * 16, v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) acc[q * 32 + i] += v[i];
+                for (int i = 0; i < 16; ++i) acc[q * 16 + i] += v[i];
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&S.dcorr_empty);
             corr_use++;
-            if (row < I.rows) {
-                float *dst = out + I.out_off + (long long)row * I.out_ld;
+            if (row < __ldg(&items[it].rows)) {
+                // 8 columns per field: this warp writes fields part*16 .. part*16+15 of the tile
+                const long long col_gs = __ldg(&items[it].col_gs);
+                // rows come in groups of 4 consecutive 32-byte records; out_ld = group stride
+                float *dst = out + __ldg(&items[it].out_off) + (long long)(row >> 2) * __ldg(&items[it].out_ld) +
+                             (row & 3) * 8 + (long long)(part * (kEpiCols / 8)) * col_gs;
 #pragma unroll
-                for (int g = 0; g < kTileN / 8; ++g) {
-                    float4 *d4 = reinterpret_cast<float4 *>(dst + g * I.col_gs);
+                for (int g = 0; g < kEpiCols / 8; ++g) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dst + g * col_gs);
                     d4[0] = make_float4(acc[8 * g], acc[8 * g + 1], acc[8 * g + 2], acc[8 * g + 3]);
                     d4[1] = make_float4(acc[8 * g + 4], acc[8 * g + 5], acc[8 * g + 6], acc[8 * g + 7]);
                 }
@@ -357,6 +387,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int N>
+cudaError_t launch_gemm_n(const Plan &p, bool fwd, cudaStream_t s)
+{
+    const size_t smem = sizeof(GemmSmem<N>) + 1024;
+    auto k = k_tc_gemm<N>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nitems = fwd ? p.n_items_f : p.n_items_a;
+    const int grid = nitems < p.num_sms ? nitems : p.num_sms;
+    if (grid <= 0) return cudaSuccess;
+    k<<<grid, gemm_threads<N>(), smem, s>>>((const unsigned char *)p.d_lam,
+                                            (const unsigned char *)(fwd ? p.d_Fb : p.d_gb), p.tmap_fb,
+                                            fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
+                                            fwd ? 1 : 0, p.d_status);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -377,20 +424,7 @@ cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s)
 
 cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s)
 {
-    const size_t smem = sizeof(GemmSmem) + 1024;
-    auto k = k_tc_gemm;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int nitems = fwd ? p.n_items_f : p.n_items_a;
-    const int grid = nitems < p.num_sms ? nitems : p.num_sms;
-    if (grid <= 0) return cudaSuccess;
-    k<<<grid, kGemmThreads, smem, s>>>((const unsigned char *)p.d_lam,
-                                       (const unsigned char *)(fwd ? p.d_Fb : p.d_gb), p.tmap_fb,
-                                       fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
-                                       fwd ? 1 : 0, p.d_status);
-    return cudaGetLastError();
+    return p.gemm_n == 256 ? launch_gemm_n<256>(p, fwd, s) : launch_gemm_n<128>(p, fwd, s);
 }
-
-size_t tc_gemm_smem_bytes() { return sizeof(GemmSmem) + 1024; }
 
 }  // namespace favest

@@ -20,7 +20,7 @@
 //
 // Only the theta/phi structure of the combine stage and the E/O parity split of the
 // folded grid are used; the output goes to the same buffer S32 the GEMM writes,
-//   S32[j][field][mu][parity][8], columns c*4 + s*2 + (re, im): c = theta/phi,
+//   S32[field][JP/4][mu][parity][4][8], columns c*4 + s*2 + (re, im): c = theta/phi,
 //   s = 0: m = +mu, s = 1: m = -mu (with the factor (-1)^mu of lambda^{-mu}).
 #include <cmath>
 #include <vector>
@@ -55,7 +55,7 @@ constexpr int kPolarWarps = 8;       // warps per CTA, each over its own range o
 // values.
 __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
-    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int nf)
+    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP)
 {
     __shared__ float part[kPolarWarps][kPolarJ * 16][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
         if (active && j0 + q < jc) {
             const int par = k ^ (mu & 1);
             const float sg = (mu & 1) ? -1.f : 1.f;     // columns of m = -mu
-            float *dst = S32 + (((size_t)(j0 + q) * nf + f) * (L + 1) + mu) * 16 + par * 8 + c4;
+            const int j = j0 + q;
+            float *dst = S32 + ((((size_t)f * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2 + par) * 32 + (j & 3) * 8 + c4;
             *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
         }
     }
@@ -243,7 +244,7 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
     const int K = p.L * p.L + 2 * p.L;
     dim3 grid(p.pol_muc / 32, p.B, (p.pol_jc + kPolarJ - 1) / kPolarJ);
     k_polar_patch<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin,
-                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.nf);
+                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.JP);
     return cudaGetLastError();
 }
 
