@@ -243,9 +243,31 @@ int make_fb_tensor_map(Plan &p)
     return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
 }
 
+// A GEMM operand buffer as seen by the TMA: a 2-D array of 512-byte rows (256 bf16 each),
+// loaded in boxes of box_rows whole rows (one operand chunk).
+int make_row_tensor_map(void *base, size_t bytes, int box_rows, CUtensorMap *out)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return FAVEST_EUNSUPPORTED;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    if (bytes % 512 || bytes / 512 > 0x7fffffffULL || box_rows < 1 || box_rows > 256) return FAVEST_EINVAL;
+    cuuint64_t dims[2] = {256, (cuuint64_t)(bytes / 512)};
+    cuuint64_t strides[1] = {512};
+    cuuint32_t box[2] = {256, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
+}
+
 // Split-precision path: operand tile offsets, GEMM work items, buffers.
 //   Lam (A operands): contiguous 24 KB chunks (three 8 KB bf16 pieces of 128 x 32), bulk copies
-//   Fb  (forward B):  [JP/8][nf][8][L+1][2][3][8] bf16, loaded through the tensor map
+//   Fb  (forward B):  [JP/8][nf][8][L+1][2][3][8] bf16, gathered by a 5-D TMA box
 //   g   (adjoint B):  contiguous chunks of three 32 x N bf16 pieces (N = gemm_n)
 //   Q32 (forward out): [nf][ntab][8] fp32: field, then for each order mu (from row
 //                      tab_off(L, mu)) its rows l = mu, mu+2, .. followed by l = mu+1, ..
@@ -298,10 +320,9 @@ int alloc_workspace_bf16(Plan &p)
                     TcItem I{};
                     I.a_off = off_f[idx] + (long long)m * p.nk_f * CHA;
                     I.a_stride = (int)CHA;
-                    I.b_tma = 1;
+                    I.b_box = 1;
                     I.bx = par * 3 * 8;
                     I.by = fpt * nt;
-                    I.bz0 = 0;
                     I.bw = mu;
                     // rows of (mu, par) are consecutive in Q32 (see the layout note above)
                     const long long qrow = tab_off(L, mu) + (par ? nrow_p(mu, 0) : 0) + 128LL * m;
@@ -321,7 +342,6 @@ int alloc_workspace_bf16(Plan &p)
                     I.b_off = off_g[idx] + (long long)nt * nka * CHB;
                     I.a_stride = (int)CHA;
                     I.b_stride = (int)CHB;
-                    I.b_tma = 0;
                     I.out_off = ((((long long)fpt * nt * (p.JP / 4) + 32LL * t) * L1 + mu) * 2 + par) * 32;
                     I.out_ld = L1 * 2 * 32;
                     I.col_gs = (long long)(p.JP / 4) * L1 * 2 * 32;
@@ -359,7 +379,10 @@ int alloc_workspace_bf16(Plan &p)
     const int pst = build_polar_tables(p);
     if (pst != FAVEST_OK) return pst;
     p.ws_bytes += (size_t)p.pol_jc * (L + 1) * p.pol_muc * sizeof(float2);
-    return make_fb_tensor_map(p);
+    int st = make_row_tensor_map(p.d_lam, lam_bytes, (int)(CHA / 512), &p.tmap_lam);
+    if (st == FAVEST_OK) st = make_fb_tensor_map(p);
+    if (st == FAVEST_OK) st = make_row_tensor_map(p.d_gb, (size_t)gsz, (int)(CHB / 512), &p.tmap_gb);
+    return st;
 }
 
 int alloc_workspace(Plan &p)

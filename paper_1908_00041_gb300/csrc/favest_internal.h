@@ -41,25 +41,26 @@ struct FftPlan {
     float2 *tw32 = nullptr;    // device, same rounded to float
 };
 
-// One tensor-core GEMM output tile: out[rows][128 cols] = sum over nk K-chunks of A_c * B_c.
-// Output element (r, c) goes to out[out_off + r*out_ld + (c/8)*col_gs + c%8].
 constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk
 
-// One GEMM work item.  Output row r (< rows) of field column group g is written at
-// out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs (8 floats per field).
+// One tensor-core GEMM work item: out[rows][N] = sum over nk K-chunks of A_c * B_c, each
+// chunk three bf16 pieces.  Chunk c of A starts a_off + c * a_stride bytes into the A
+// buffer (a multiple of 512: the TMA addresses the buffer as rows of 512 bytes); B
+// likewise (b_box = 0), or (b_box = 1) through the forward operand's 5-D tensor map at
+// coordinates (bx + 8 * piece, bw, 0, by, 4 * c).  Output row r (< rows) of field
+// column group g (8 floats) is written at
+//   out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs.
 struct TcItem {
-    long long a_off;    // byte offset of chunk 0 of A (three 16 KB bf16 pieces per chunk)
-    long long b_off;    // byte offset of chunk 0 of B (bulk mode)
-    long long out_off;  // float offset of output element (row 0, col 0)
-    long long out_ld;   // output row pitch (floats)
-    long long col_gs;   // output stride between groups of 8 columns (floats)
-    int nk;             // K-chunks (64 deep)
+    long long a_off, b_off;
+    long long out_off;  // floats
+    long long out_ld;   // floats between groups of 4 rows
+    long long col_gs;   // floats between field column groups
+    int nk;             // K-chunks
     int rows;           // valid output rows (<= 128)
     int a_stride;       // bytes between consecutive A chunks
     int b_stride;       // bytes between consecutive B chunks
-    int b_tma;          // 1: B through the tensor map at the coordinates below
-    int bx, by, bz0, bw;  // tensor-map coordinates: x0 (piece 0), field group, K-group of chunk 0, order
-    int pad;
+    int b_box;          // 1: B through the 5-D tensor map
+    int bx, by, bw;     // 5-D box coordinates: x of piece 0, first field, order
 };
 
 struct Plan {
@@ -102,7 +103,9 @@ struct Plan {
     float *d_Q32 = nullptr;       // forward GEMM output [field][l][mu][8]
     float *d_S32 = nullptr;       // adjoint GEMM output [JP][field][mu][parity][8]
     int nf = 0;                   // fields padded to a multiple of gemm_n / 8 (ncolr / 8)
-    CUtensorMap tmap_fb;          // forward B operand: Fb[JP][nf][L+1][parity][piece][8] bf16
+    // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
+    // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
+    CUtensorMap tmap_lam, tmap_fb, tmap_gb;
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
     float *d_k1 = nullptr;        // [L+1] kappa of order 1 (order-0 adjoint on order-1 tiles)

@@ -237,6 +237,8 @@ __device__ __forceinline__ void store_row3(unsigned char *dst, const float (&v)[
 }
 
 
+constexpr int kLoadBatch = 8;    // independent global loads per thread in flight
+
 // grid: B * J CTAs (field-major); shared: 4 * n float2 (+ padding for LOG2N > 0).
 // LOG2N > 0 selects the power-of-two engine, 0 the generic mixed-radix one.
 template <int LOG2N>
@@ -253,16 +255,30 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const int nr = eq ? 2 : 4;    // rings: (th, j), (ph, j), (th, j'), (ph, j')
     const int jm = nlat - 1 - j;
     const int n2 = n / 2;         // float4 per ring
-    for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
-        const int ring = idx / n2, k2 = idx % n2;
-        const float2 *src = (ring & 1) ? Tph : Tth;
-        const int jj = (ring < 2) ? j : jm;
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(src + ((size_t)b * nlat + jj) * n) + k2);
-        if (LOG2N > 0) {
-            buf[padi(2 * idx)] = make_float2(v.x, v.y);
-            buf[padi(2 * idx + 1)] = make_float2(v.z, v.w);
-        } else {
-            sm_f4[idx] = v;
+    // loads are issued in batches of kLoadBatch per thread before any is stored
+    for (int i0 = threadIdx.x; i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
+        float4 v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int idx = i0 + u * kFftThreads;
+            if (idx < nr * n2) {
+                const int ring = idx / n2, k2 = idx % n2;
+                const float2 *src = (ring & 1) ? Tph : Tth;
+                const int jj = (ring < 2) ? j : jm;
+                v[u] = __ldg(reinterpret_cast<const float4 *>(src + ((size_t)b * nlat + jj) * n) + k2);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int idx = i0 + u * kFftThreads;
+            if (idx < nr * n2) {
+                if (LOG2N > 0) {
+                    buf[padi(2 * idx)] = make_float2(v[u].x, v[u].y);
+                    buf[padi(2 * idx + 1)] = make_float2(v[u].z, v[u].w);
+                } else {
+                    sm_f4[idx] = v[u];
+                }
+            }
         }
     }
     __syncthreads();
@@ -321,27 +337,45 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
         for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
-        // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
-        const float sc = mu == 0 ? w0 : is;
-        const float4 *e = reinterpret_cast<const float4 *>(
-            S32 + ((((size_t)b * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
-        const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
-        const float4 e0 = __ldg(e), e1 = __ldg(e + 1), o0 = __ldg(o), o1 = __ldg(o + 1);
-        const float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-        const float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += 2 * blockDim.x) {
+        // two orders per iteration: the 8 loads are issued before any is used
+        float4 ld[2][4];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int h = 0; h < 2; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu <= L) {
+                const float4 *e = reinterpret_cast<const float4 *>(
+                    S32 + ((((size_t)b * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
+                const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
+                ld[h][0] = __ldg(e);
+                ld[h][1] = __ldg(e + 1);
+                ld[h][2] = __ldg(o);
+                ld[h][3] = __ldg(o + 1);
+            }
+        }
 #pragma unroll
-            for (int sgn = 0; sgn < 2; ++sgn) {
-                if (mu == 0 && sgn == 1) continue;
-                const int bin = sgn ? n - mu : mu;
-                const int k = c * 4 + sgn * 2;
-                const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
-                buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
-                if (!eq)
-                    buf[LOG2N > 0 ? padi(i1) : i1] =
-                        make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
+        for (int h = 0; h < 2; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu > L) break;
+            // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
+            const float sc = mu == 0 ? w0 : is;
+            const float ev[8] = {ld[h][0].x, ld[h][0].y, ld[h][0].z, ld[h][0].w,
+                                 ld[h][1].x, ld[h][1].y, ld[h][1].z, ld[h][1].w};
+            const float ov[8] = {ld[h][2].x, ld[h][2].y, ld[h][2].z, ld[h][2].w,
+                                 ld[h][3].x, ld[h][3].y, ld[h][3].z, ld[h][3].w};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    if (mu == 0 && sgn == 1) continue;
+                    const int bin = sgn ? n - mu : mu;
+                    const int k = c * 4 + sgn * 2;
+                    const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
+                    buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
+                    if (!eq)
+                        buf[LOG2N > 0 ? padi(i1) : i1] =
+                            make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
+                }
             }
         }
     }

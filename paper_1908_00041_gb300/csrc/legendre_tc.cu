@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
 // ---------------------------------------------------------------------------
 // Persistent GEMM: every item computes out[rows 0..127][cols 0..N-1] =
 //   sum_{c < nk} A_c * B_c  (three bf16 pieces each, 6 products)
-// Warp 0 loads operands (bulk copies; the forward B operand through a TMA tensor map),
+// Warp 0 loads operand chunks with TMA (whole 512-byte rows; the forward B operand as
+// 5-D boxes gathering the 16-byte rows of 8 latitudes),
 // warp 1 issues the MMAs, warps 2.. drain TMEM (each a 32-lane quadrant and 128 columns).
 // TMEM: columns [0, N) hold the hi*hi product of the current K-chunk (drained into FP32
 // register sums after every chunk), columns [N, 2N) accumulate the five correction
@@ -198,8 +199,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
 
 template <int N>
 __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
-    const unsigned char *__restrict__ Abuf, const unsigned char *__restrict__ Bbuf,
-    const __grid_constant__ CUtensorMap tmap_b, const TcItem *__restrict__ items, int nitems,
+    const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+    const TcItem *__restrict__ items, int nitems,
     float *__restrict__ out, int a_mn_major, int *__restrict__ status)
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);   // 4 lane quadrants x N / 128 column parts
@@ -242,15 +243,17 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                         break;
                     }
                     tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkB);
-                    tc::bulk_g2s(S.a[stage], Abuf + I.a_off + (long long)c * I.a_stride, kChunkBytes,
-                                 &S.full[stage]);
-                    if (I.b_tma) {
+                    // operand buffers are 2-D arrays of 512-byte rows: a chunk is a box
+                    // of whole rows starting at its byte offset / 512
+                    tc::tma_load_2d(S.a[stage], &tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
+                                    &S.full[stage]);
+                    if (I.b_box) {
                         for (int q = 0; q < kPieces; ++q)
                             tc::tma_load_5d(S.b[stage] + q * kPieceB, &tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
-                                            I.bz0 + (kChunkK / 8) * c, &S.full[stage]);
+                                            (kChunkK / 8) * c, &S.full[stage]);
                     } else {
-                        tc::bulk_g2s(S.b[stage], Bbuf + I.b_off + (long long)c * I.b_stride, kChunkB,
-                                     &S.full[stage]);
+                        tc::tma_load_2d(S.b[stage], &tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
+                                        &S.full[stage]);
                     }
                     phase ^= 1u << stage;
                     stage = (stage + 1) % kStages;
@@ -399,8 +402,7 @@ cudaError_t launch_gemm_n(const Plan &p, bool fwd, cudaStream_t s)
     const int nitems = fwd ? p.n_items_f : p.n_items_a;
     const int grid = nitems < p.num_sms ? nitems : p.num_sms;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, gemm_threads<N>(), smem, s>>>((const unsigned char *)p.d_lam,
-                                            (const unsigned char *)(fwd ? p.d_Fb : p.d_gb), p.tmap_fb,
+    k<<<grid, gemm_threads<N>(), smem, s>>>(p.tmap_lam, fwd ? p.tmap_fb : p.tmap_gb,
                                             fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
                                             fwd ? 1 : 0, p.d_status);
     return cudaGetLastError();

@@ -97,6 +97,16 @@ __device__ __forceinline__ void tma_load_5d(void *sdst, const void *tmap, int c0
         : "memory");
 }
 
+// 2-D tiled TMA load (global -> shared) through a tensor map, completing on bar.
+__device__ __forceinline__ void tma_load_2d(void *sdst, const void *tmap, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(sdst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
