@@ -170,6 +170,49 @@ const char *favest_strerror(int status);
 int favest_launches_per_call(favest_plan plan, int adjoint);
 
 /*
+ * Autotuner of the split-precision path's FP64 recurrence generator.  The generator
+ * runs 128 threads per block as (128 / lt) orders x lt latitudes (lt = 32, 64, 128),
+ * each block covering mb order groups in turn (mb = 1, 2, 4).  favest_plan_tune times
+ * the candidate (lt, mb) shapes for this plan's degree on `stream` (synchronising it,
+ * a few milliseconds) and keeps the fastest; favest_plan_gen_shape reports the shape in
+ * use.  Plans start with (128, 1).  FP64 plans have nothing to tune (returns FAVEST_OK).
+ */
+int favest_plan_tune(favest_plan plan, void *stream);
+int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
+
+/*
+ * Ragged batches: nfields fields of individual degrees L[i] (host array), each on its
+ * own (L[i]+1) x 2(L[i]+1) Gauss-Legendre grid.  The caller's buffers hold the fields
+ * packed: component plane of field i at element offset field_off[i] of Tth and of Tph
+ * (complex elements, even offsets), its coefficients (L[i]^2 + 2 L[i] of each family)
+ * at element offset coef_off[i] of a and of b; null offset arrays mean packed in field
+ * order.  favest_batch_field_elems / favest_batch_coef_elems give the buffer lengths.
+ *
+ * Fields are grouped by degree.  In the split-precision form the tensor-core Legendre
+ * stage of all groups is one persistent kernel launch over a merged work queue of
+ * (degree group, order, parity, row or latitude tile) items; the longitude DFTs, combine
+ * and generator stages run once per degree group.  Flags:
+ *   FAVEST_BATCH_AUTOTUNE  tune each group's generator shape at creation (favest_plan_tune)
+ *   FAVEST_BATCH_GRAPH     replay each direction as a CUDA graph: the first call with a
+ *                          given set of buffers runs directly, the second captures the
+ *                          launch sequence, later ones launch the captured graph
+ * Errors as for the single-field calls; favest_batch_status reads and clears the device
+ * status words of all groups.  Calls on one batch must not overlap on the host.
+ */
+typedef struct favest_batch_s *favest_batch;
+enum { FAVEST_BATCH_AUTOTUNE = 1, FAVEST_BATCH_GRAPH = 2 };
+int favest_batch_create(int nfields, const int *L, const long long *field_off, const long long *coef_off,
+                        int precision, int io_type, int flags, favest_batch *out);
+int favest_fwd_batched(favest_batch batch, const void *Tth, const void *Tph, void *a, void *b, void *stream);
+int favest_adj_batched(favest_batch batch, const void *a, const void *b, void *Tth, void *Tph, void *stream);
+int favest_batch_ngroups(favest_batch batch);
+int favest_batch_group(favest_batch batch, int g, int *L, int *nfields, int *gen_lt, int *gen_mb);
+long long favest_batch_field_elems(favest_batch batch);
+long long favest_batch_coef_elems(favest_batch batch);
+int favest_batch_status(favest_batch batch, void *stream);
+void favest_batch_destroy(favest_batch batch);
+
+/*
  * Per-kernel timing (a profiling aid).  While enabled (enable = 1), every transform
  * call records a CUDA event pair around each kernel it launches, on the call's
  * stream.  favest_profile_read synchronises those events and returns, for up to

@@ -28,6 +28,8 @@ FAVEST_IO_C128 = 0
 FAVEST_IO_C64 = 1
 FAVEST_FLAG_UNIT_WEIGHTS = 1
 FAVEST_FLAG_WEIGHTED = 2
+FAVEST_BATCH_AUTOTUNE = 1
+FAVEST_BATCH_GRAPH = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -81,6 +83,20 @@ def lib(build_if_missing=False):
             L.favest_launches_per_call.argtypes = [vp, i]
             L.favest_probe_peaks.argtypes = [d, d]
             L.favest_kernel_work.argtypes = [vp, ctypes.c_char_p, d, d, ctypes.POINTER(ctypes.c_int)]
+            pi, pll = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)
+            L.favest_plan_tune.argtypes = [vp, vp]
+            L.favest_plan_gen_shape.argtypes = [vp, pi, pi]
+            L.favest_batch_create.argtypes = [i, pi, pll, pll, i, i, i, ctypes.POINTER(vp)]
+            L.favest_fwd_batched.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.favest_adj_batched.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.favest_batch_ngroups.argtypes = [vp]
+            L.favest_batch_group.argtypes = [vp, i, pi, pi, pi, pi]
+            L.favest_batch_field_elems.argtypes = [vp]
+            L.favest_batch_field_elems.restype = ctypes.c_longlong
+            L.favest_batch_coef_elems.argtypes = [vp]
+            L.favest_batch_coef_elems.restype = ctypes.c_longlong
+            L.favest_batch_status.argtypes = [vp, vp]
+            L.favest_batch_destroy.argtypes = [vp]
             L.favest_fwd_fp64_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp]
             L.favest_noalloc_scratch_bytes.restype = ctypes.c_size_t
             L.favest_profile_enable.argtypes = [vp, i]
@@ -297,6 +313,17 @@ class Plan:
     def workspace_bytes(self):
         return favest_plan_workspace_bytes(self.handle)
 
+    def tune(self, stream=None):
+        """Pick the fastest generator block shape for this plan (split precision)."""
+        _check(lib().favest_plan_tune(ctypes.c_void_p(self.handle), _stream(stream)), "favest_plan_tune")
+        return self.gen_shape()
+
+    def gen_shape(self):
+        lt, mb = ctypes.c_int(), ctypes.c_int()
+        _check(lib().favest_plan_gen_shape(ctypes.c_void_p(self.handle), ctypes.byref(lt), ctypes.byref(mb)),
+               "favest_plan_gen_shape")
+        return lt.value, mb.value
+
     def launches_per_call(self, adjoint=0):
         return favest_launches_per_call(self.handle, adjoint)
 
@@ -315,3 +342,88 @@ class Plan:
         _check(lib().favest_kernel_work(ctypes.c_void_p(self.handle), name.encode(), ctypes.byref(nb),
                                         ctypes.byref(fl), ctypes.byref(pipe)), "favest_kernel_work")
         return nb.value, fl.value, pipe.value
+
+
+class BatchPlan:
+    """Ragged batch: fields of individual degrees Ls[i] packed back to back (see
+    favest_batch_create).  Grid buffers are flat complex tensors of field_elems elements
+    (one per component), coefficient buffers flat tensors of coef_elems elements."""
+
+    def __init__(self, Ls, precision=FAVEST_BF16X6, io_type=FAVEST_IO_C64, field_off=None, coef_off=None,
+                 autotune=False, graph=True):
+        import torch
+        self.Ls = [int(x) for x in Ls]
+        self.precision, self.io_type = precision, io_type
+        self.cdtype = torch.complex128 if io_type == FAVEST_IO_C128 else torch.complex64
+        n = len(self.Ls)
+        Larr = (ctypes.c_int * n)(*self.Ls)
+        fo = (ctypes.c_longlong * n)(*field_off) if field_off is not None else None
+        co = (ctypes.c_longlong * n)(*coef_off) if coef_off is not None else None
+        flags = (FAVEST_BATCH_AUTOTUNE if autotune else 0) | (FAVEST_BATCH_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib().favest_batch_create(n, Larr, fo, co, precision, io_type, flags, ctypes.byref(h)),
+               "favest_batch_create")
+        self.handle = h.value
+        self.field_elems = lib().favest_batch_field_elems(ctypes.c_void_p(self.handle))
+        self.coef_elems = lib().favest_batch_coef_elems(ctypes.c_void_p(self.handle))
+        self.field_off, self.coef_off = [], []
+        f = c = 0
+        for i, L in enumerate(self.Ls):
+            self.field_off.append(field_off[i] if field_off is not None else f)
+            self.coef_off.append(coef_off[i] if coef_off is not None else c)
+            f += (L + 1) * 2 * (L + 1)
+            c += L * L + 2 * L
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().favest_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def groups(self):
+        out = []
+        for g in range(lib().favest_batch_ngroups(ctypes.c_void_p(self.handle))):
+            v = [ctypes.c_int() for _ in range(4)]
+            _check(lib().favest_batch_group(ctypes.c_void_p(self.handle), g, *[ctypes.byref(x) for x in v]),
+                   "favest_batch_group")
+            out.append({"L": v[0].value, "fields": v[1].value, "gen_lt": v[2].value, "gen_mb": v[3].value})
+        return out
+
+    def field(self, buf, i):
+        """View of field i's component plane in a flat grid buffer, [L+1, 2(L+1)]."""
+        L = self.Ls[i]
+        o = self.field_off[i]
+        return buf[o:o + (L + 1) * 2 * (L + 1)].view(L + 1, 2 * (L + 1))
+
+    def coef(self, buf, i):
+        L = self.Ls[i]
+        o = self.coef_off[i]
+        return buf[o:o + L * L + 2 * L]
+
+    def fwd(self, Tth, Tph, a=None, b=None, stream=None):
+        import torch
+        if a is None:
+            a = torch.empty(self.coef_elems, dtype=self.cdtype, device=Tth.device)
+        if b is None:
+            b = torch.empty(self.coef_elems, dtype=self.cdtype, device=Tth.device)
+        _check(lib().favest_fwd_batched(ctypes.c_void_p(self.handle), _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b),
+                                        _stream(stream)), "favest_fwd_batched")
+        return a, b
+
+    def adj(self, a, b, Tth=None, Tph=None, stream=None):
+        import torch
+        if Tth is None:
+            Tth = torch.empty(self.field_elems, dtype=self.cdtype, device=a.device)
+        if Tph is None:
+            Tph = torch.empty(self.field_elems, dtype=self.cdtype, device=a.device)
+        _check(lib().favest_adj_batched(ctypes.c_void_p(self.handle), _ptr(a), _ptr(b), _ptr(Tth), _ptr(Tph),
+                                        _stream(stream)), "favest_adj_batched")
+        return Tth, Tph
+
+    def status(self, stream=None):
+        return lib().favest_batch_status(ctypes.c_void_p(self.handle), _stream(stream))

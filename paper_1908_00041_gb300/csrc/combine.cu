@@ -19,7 +19,8 @@ namespace {
 template <typename TO>
 __global__ void k_combine_fp64(const double2 *__restrict__ Q, TO *__restrict__ a, TO *__restrict__ b,
                                const double *__restrict__ P, const double *__restrict__ M,
-                               const double *__restrict__ R, int L, int K, int ncol, int B)
+                               const double *__restrict__ R, int L, int K, int ncol, int B,
+                               const long long *__restrict__ coff)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)B * K) return;
@@ -46,16 +47,17 @@ __global__ void k_combine_fp64(const double2 *__restrict__ Q, TO *__restrict__ a
                               sg * (Pl * qt1.y - Ml * qtm.y - Rl * qp0.x));
     double2 bv = make_double2(sg * (-Rl * qt0.y + Pl * qp1.x - Ml * qpm.x),
                               sg * (Rl * qt0.x + Pl * qp1.y - Ml * qpm.y));
-    a[(size_t)bi * K + k] = from_d2<TO>(av);
-    b[(size_t)bi * K + k] = from_d2<TO>(bv);
+    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
+    a[cb + k] = from_d2<TO>(av);
+    b[cb + k] = from_d2<TO>(bv);
 }
 
 template <typename TI>
-__device__ __forceinline__ double2 coef(const TI *__restrict__ c, int L, int l, int m, int bi, int K)
+__device__ __forceinline__ double2 coef(const TI *__restrict__ c, int L, int l, int m, size_t cb)
 {
     int am = m < 0 ? -m : m;
     if (l < 1 || l > L || am > l) return make_double2(0.0, 0.0);
-    return to_d2(c[(size_t)bi * K + l * l + l + m - 1]);
+    return to_d2(c[cb + l * l + l + m - 1]);
 }
 
 // grid.x = mu, grid.y = b*2 + s; threads stride over rows l' = mu..L+1
@@ -63,7 +65,7 @@ template <typename TI>
 __global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict__ b,
                                  double2 *__restrict__ g, const double *__restrict__ P,
                                  const double *__restrict__ M, const double *__restrict__ R, int L,
-                                 int K, int ncol)
+                                 int K, int ncol, const long long *__restrict__ coff)
 {
     const int mu = blockIdx.x;
     const int bi = blockIdx.y >> 1, s = blockIdx.y & 1;
@@ -72,6 +74,7 @@ __global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict_
     const long long t0 = tab_off(L, mu);
     const int nrow = L + 2 - mu;
     const int cth = (bi * 2 + 0) * 2 + s, cph = (bi * 2 + 1) * 2 + s;
+    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
         const int l = mu + r;
         double2 gt = make_double2(0.0, 0.0), gp = make_double2(0.0, 0.0);
@@ -79,9 +82,9 @@ __global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict_
             const double Pm = (r > 0) ? P[t0 + r - 1] : 0.0;
             const double Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.0;
             const double Rl = (l <= L) ? R[t0 + r] * m : 0.0;
-            double2 am1 = coef(a, L, l - 1, m, bi, K), ap1 = coef(a, L, l + 1, m, bi, K);
-            double2 bm1 = coef(b, L, l - 1, m, bi, K), bp1 = coef(b, L, l + 1, m, bi, K);
-            double2 a0 = coef(a, L, l, m, bi, K), b0 = coef(b, L, l, m, bi, K);
+            double2 am1 = coef(a, L, l - 1, m, cb), ap1 = coef(a, L, l + 1, m, cb);
+            double2 bm1 = coef(b, L, l - 1, m, cb), bp1 = coef(b, L, l + 1, m, cb);
+            double2 a0 = coef(a, L, l, m, cb), b0 = coef(b, L, l, m, cb);
             gt = make_double2(sg * (Pm * am1.x - Mp * ap1.x + Rl * b0.y),
                               sg * (Pm * am1.y - Mp * ap1.y - Rl * b0.x));
             gp = make_double2(sg * (-Rl * a0.y + Pm * bm1.x - Mp * bp1.x),
@@ -103,11 +106,11 @@ cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s)
     if (p.io == FAVEST_IO_C128)
         k_combine_fp64<double2><<<(unsigned)grid, th, 0, s>>>((const double2 *)p.d_Q, (double2 *)a,
                                                               (double2 *)b, p.d_P, p.d_M, p.d_R, p.L, K,
-                                                              p.ncol, p.B);
+                                                              p.ncol, p.B, p.d_coff);
     else
         k_combine_fp64<float2><<<(unsigned)grid, th, 0, s>>>((const double2 *)p.d_Q, (float2 *)a,
                                                              (float2 *)b, p.d_P, p.d_M, p.d_R, p.L, K,
-                                                             p.ncol, p.B);
+                                                             p.ncol, p.B, p.d_coff);
     return cudaGetLastError();
 }
 
@@ -119,11 +122,11 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
     if (p.io == FAVEST_IO_C128)
         k_uncombine_fp64<double2><<<grid, th, 0, s>>>((const double2 *)a, (const double2 *)b,
                                                       (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, K,
-                                                      p.ncol);
+                                                      p.ncol, p.d_coff);
     else
         k_uncombine_fp64<float2><<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b,
                                                      (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, K,
-                                                     p.ncol);
+                                                     p.ncol, p.d_coff);
     return cudaGetLastError();
 }
 

@@ -20,9 +20,10 @@ namespace {
 // 8-byte words 2l+1 apart; the CTAs of neighbouring orders fill the rest of each line.
 __global__ void k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a, float2 *__restrict__ bo,
                                const float *__restrict__ P, const float *__restrict__ M,
-                               const float *__restrict__ R, int L, int K)
+                               const float *__restrict__ R, int L, int K, const long long *__restrict__ coff)
 {
     const int mu = blockIdx.x, bi = blockIdx.y;
+    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
     const long long t0 = tab_off(L, mu);
     const float *qb = Q + ((size_t)bi * tab_off(L, L + 1) + t0) * 8;
     const int n0 = (L + 3 - mu) / 2;            // rows of even l - mu
@@ -49,18 +50,18 @@ __global__ void k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__
             const float ay = sg * fmaf(Pl, t1y, fmaf(-Ml, tmy, -Rm * p0x));
             const float bx = sg * fmaf(Pl, p1x, fmaf(-Ml, pmx, -Rm * t0y));
             const float by = sg * fmaf(Pl, p1y, fmaf(-Ml, pmy, Rm * t0x));
-            const size_t k = (size_t)bi * K + l * l + l + m - 1;
+            const size_t k = cb + l * l + l + m - 1;
             a[k] = make_float2(ax, ay);
             bo[k] = make_float2(bx, by);
         }
     }
 }
 
-__device__ __forceinline__ float2 cf(const float2 *__restrict__ c, int L, int l, int m, int bi, int K)
+__device__ __forceinline__ float2 cf(const float2 *__restrict__ c, int L, int l, int m, size_t cb)
 {
     int am = m < 0 ? -m : m;
     if (l < 1 || l > L || am > l) return make_float2(0.f, 0.f);
-    return c[(size_t)bi * K + l * l + l + m - 1];
+    return c[cb + l * l + l + m - 1];
 }
 
 __device__ __forceinline__ void split3u(float f, unsigned short &h, unsigned short &m, unsigned short &l)
@@ -86,9 +87,10 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
                                  unsigned char *__restrict__ gb, const long long *__restrict__ g_off,
                                  const float *__restrict__ P, const float *__restrict__ M,
                                  const float *__restrict__ R, const float *__restrict__ k1tab, int L, int K,
-                                 int N)
+                                 int N, const long long *__restrict__ coff)
 {
     const int mu = blockIdx.x, bi = blockIdx.y;
+    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
     const long long t0 = tab_off(L, mu);
     const int nrow = L + 2 - (mu == 0 ? 1 : mu);
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
@@ -103,7 +105,7 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
         if (mu == 0) {
             // the order-1 tiles hold lambda_l^1 / kappa_l^(1)
             const float k1 = (l <= L) ? k1tab[l] : 0.f;
-            const float2 a0 = cf(a, L, l, 0, bi, K), b0 = cf(b, L, l, 0, bi, K);
+            const float2 a0 = cf(a, L, l, 0, cb), b0 = cf(b, L, l, 0, cb);
             v[0] = k1 * a0.x; v[1] = k1 * a0.y; v[2] = 0.f; v[3] = 0.f;
             v[4] = k1 * b0.x; v[5] = k1 * b0.y; v[6] = 0.f; v[7] = 0.f;
         } else
@@ -116,9 +118,9 @@ __global__ void k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__r
                 const float Pm = (r > 0) ? P[t0 + r - 1] : 0.f;
                 const float Mp = (l + 1 <= L) ? M[t0 + r + 1] : 0.f;
                 const float Rl = (l <= L) ? R[t0 + r] * (float)m : 0.f;
-                float2 am1 = cf(a, L, l - 1, m, bi, K), ap1 = cf(a, L, l + 1, m, bi, K);
-                float2 bm1 = cf(b, L, l - 1, m, bi, K), bp1 = cf(b, L, l + 1, m, bi, K);
-                float2 a0 = cf(a, L, l, m, bi, K), b0 = cf(b, L, l, m, bi, K);
+                float2 am1 = cf(a, L, l - 1, m, cb), ap1 = cf(a, L, l + 1, m, cb);
+                float2 bm1 = cf(b, L, l - 1, m, cb), bp1 = cf(b, L, l + 1, m, cb);
+                float2 a0 = cf(a, L, l, m, cb), b0 = cf(b, L, l, m, cb);
                 gtx = sg * fmaf(Pm, am1.x, fmaf(-Mp, ap1.x, Rl * b0.y));
                 gty = sg * fmaf(Pm, am1.y, fmaf(-Mp, ap1.y, -Rl * b0.x));
                 gpx = sg * fmaf(Pm, bm1.x, fmaf(-Mp, bp1.x, -Rl * a0.y));
@@ -159,7 +161,7 @@ cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
     const int th = p.L >= 255 ? 256 : (p.L >= 63 ? 64 : 32);
     dim3 grid(p.L + 1, p.B);
     k_combine_bf16<<<grid, th, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32, p.d_M32,
-                                       p.d_R32, p.L, K);
+                                       p.d_R32, p.L, K, p.d_coff);
     return cudaGetLastError();
 }
 
@@ -169,7 +171,7 @@ cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, c
     dim3 grid(p.L + 1, p.B);
     const int th = p.L + 2 >= 256 ? 256 : 64;
     k_uncombine_bf16<<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb,
-                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n);
+                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n, p.d_coff);
     return cudaGetLastError();
 }
 

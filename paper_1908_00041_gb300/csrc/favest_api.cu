@@ -15,9 +15,6 @@
 
 using namespace favest;
 
-struct favest_plan_s {
-    Plan p;
-};
 
 namespace {
 
@@ -111,7 +108,7 @@ void free_plan(Plan &p)
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
-                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring};
+                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -281,7 +278,7 @@ int alloc_workspace_bf16(Plan &p)
     const int L = p.L;
     const int KC = kGemmChunkK;
     const long long CHA = 3LL * 128 * KC * 2;    // bytes per A chunk (3 bf16 pieces of 128 x KC)
-    p.gemm_n = 8 * p.B > 128 ? 256 : 128;
+    p.gemm_n = (p.force_gemm_n == 256 || 8 * p.B > 128) ? 256 : 128;
     const long long CHB = 3LL * KC * p.gemm_n * 2;   // bytes per B chunk (3 pieces of KC x N)
     p.JP = (p.J + 127) / 128 * 128;
     p.ncolr = (8 * p.B + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
@@ -331,6 +328,7 @@ int alloc_workspace_bf16(Plan &p)
                     I.col_gs = p.ntab * 8;
                     I.nk = p.nk_f;
                     I.rows = np - 128 * m < 128 ? np - 128 * m : 128;
+                    I.group = 0;
                     itf.push_back(I);
                 }
             const int amu = mu == 0 ? 1 : mu;
@@ -347,6 +345,7 @@ int alloc_workspace_bf16(Plan &p)
                     I.col_gs = (long long)(p.JP / 4) * L1 * 2 * 32;
                     I.nk = nka;
                     I.rows = 128;
+                    I.group = 1;
                     ita.push_back(I);
                 }
         }
@@ -382,7 +381,18 @@ int alloc_workspace_bf16(Plan &p)
     int st = make_row_tensor_map(p.d_lam, lam_bytes, (int)(CHA / 512), &p.tmap_lam);
     if (st == FAVEST_OK) st = make_fb_tensor_map(p);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_gb, (size_t)gsz, (int)(CHB / 512), &p.tmap_gb);
-    return st;
+    if (st != FAVEST_OK) return st;
+    std::vector<GemmGroup> gg(2);
+    gg[0].tmap_a = p.tmap_lam;
+    gg[0].tmap_b = p.tmap_fb;
+    gg[0].out = p.d_Q32;
+    gg[1].tmap_a = p.tmap_lam;
+    gg[1].tmap_b = p.tmap_gb;
+    gg[1].out = p.d_S32;
+    if ((e = upload(&p.d_ggroups, gg))) return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    p.h_items_f = itf;
+    p.h_items_a = ita;
+    return FAVEST_OK;
 }
 
 int alloc_workspace(Plan &p)
@@ -474,8 +484,12 @@ int favest_gl_grid(int nlat, double *x, double *w)
     return gl_rule(nlat, x, w);
 }
 
-int favest_plan_create(int L, int batch, int precision, int io_type, const double *cos_theta,
-                       const double *w_lat, favest_plan *out)
+}  // extern "C"
+
+namespace favest {
+
+int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
+                         const double *w_lat, int force_gemm_n, favest_plan *out)
 {
     if (!out) return FAVEST_EINVAL;
     *out = nullptr;
@@ -499,6 +513,7 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
     favest_plan_s *h = new (std::nothrow) favest_plan_s();
     if (!h) return FAVEST_ENOMEM;
     Plan &p = h->p;
+    p.force_gemm_n = force_gemm_n;
     p.L = L;
     p.B = batch;
     p.precision = precision;
@@ -539,6 +554,16 @@ int favest_plan_create(int L, int batch, int precision, int io_type, const doubl
     if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(p); delete h; return FAVEST_ECUDA; }
     *out = h;
     return FAVEST_OK;
+}
+
+}  // namespace favest
+
+extern "C" {
+
+int favest_plan_create(int L, int batch, int precision, int io_type, const double *cos_theta,
+                       const double *w_lat, favest_plan *out)
+{
+    return favest::plan_create_internal(L, batch, precision, io_type, cos_theta, w_lat, 0, out);
 }
 
 int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, void *stream)

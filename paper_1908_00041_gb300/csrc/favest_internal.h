@@ -61,6 +61,14 @@ struct TcItem {
     int b_stride;       // bytes between consecutive B chunks
     int b_box;          // 1: B through the 5-D tensor map
     int bx, by, bw;     // 5-D box coordinates: x of piece 0, first field, order
+    int group;          // index into the launch's GemmGroup array
+};
+
+// Operand tensor maps and output buffer shared by the items of one group (one plan and
+// one direction); a launch may serve the items of several groups (ragged batches).
+struct __align__(64) GemmGroup {
+    CUtensorMap tmap_a, tmap_b;
+    float *out;
 };
 
 struct Plan {
@@ -83,6 +91,9 @@ struct Plan {
     double *d_omega = nullptr;    // [J] quadrature weight / sin(theta_j)
     double *d_omega_unit = nullptr;  // [J] 1 / sin(theta_j)
     double *d_wring = nullptr;    // [nlat] point weights W_j * 2 pi / nphi
+    // ragged batches: element offsets of field b's grid (per component plane) and of its
+    // coefficients in the caller's buffers; null = dense [batch][...] layout
+    const long long *d_toff = nullptr, *d_coff = nullptr;
     double *d_cmu = nullptr;      // [L+1] sectoral normalisation sqrt((2mu+1)!!/(4pi (2mu)!!))
     double *d_A = nullptr;        // [ntab] recurrence multipliers A_l^mu
     double *d_P = nullptr;        // [ntab] combine coefficient P_l^mu
@@ -106,6 +117,10 @@ struct Plan {
     // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
     // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
     CUtensorMap tmap_lam, tmap_fb, tmap_gb;
+    GemmGroup *d_ggroups = nullptr;   // [2]: forward (Lam, Fb, Q32), adjoint (Lam, g, S32)
+    std::vector<TcItem> h_items_f, h_items_a;   // host copies (merged by ragged batches)
+    int gen_lt = 128, gen_mb = 1;  // generator shape: latitudes per block, orders per thread
+    int force_gemm_n = 0;          // 256: use 256-column GEMM tiles whatever the batch
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
     float *d_k1 = nullptr;        // [L+1] kappa of order 1 (order-0 adjoint on order-1 tiles)
@@ -152,10 +167,21 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
 cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s);
 cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
 cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
+cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s);
+// one persistent GEMM launch over an explicit item list (items[i].group indexes groups)
+cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,
+                                 int a_mn_major, int *status, int num_sms, cudaStream_t s);
 cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s);
 cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s);
 cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s);
 int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
 
+int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
+                         const double *w_lat, int force_gemm_n, favest_plan *out);
+
 }  // namespace favest
+
+struct favest_plan_s {
+    favest::Plan p;
+};

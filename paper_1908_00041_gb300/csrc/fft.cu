@@ -15,7 +15,7 @@ namespace {
 template <typename TI>
 __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
     const TI *__restrict__ Tth, const TI *__restrict__ Tph, double2 *__restrict__ Fraw,
-    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat, int ncol)
+    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat, int ncol, const long long *__restrict__ toff)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
     const int j = ring % nlat;
     const int bc = ring / nlat;
     const int c = bc & 1, b = bc >> 1;
-    const TI *src = (c == 0 ? Tth : Tph) + ((size_t)b * nlat + j) * n;
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
+    const TI *src = (c == 0 ? Tth : Tph) + fb + (size_t)j * n;
     double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
     for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = to_d2(src[k]);
     __syncthreads();
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
 template <typename TO>
 __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     const double2 *__restrict__ G, TO *__restrict__ Tth, TO *__restrict__ Tph,
-    RadixPlanArg rp, const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat)
+    RadixPlanArg rp, const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat,
+    const long long *__restrict__ toff)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -59,7 +61,8 @@ __global__ void __launch_bounds__(256) k_fft_inv_fp64(
         buf0[k] = (k == L + 1) ? make_double2(0.0, 0.0) : src[k];
     __syncthreads();
     const double2 *out = stockham<true>(buf0, buf1, tw, rp);
-    TO *dst = (c == 0 ? Tth : Tph) + ((size_t)b * nlat + j) * n;
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+    TO *dst = (c == 0 ? Tth : Tph) + fb + (size_t)j * n;
     if (wring) {
         const double w = wring[j];
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -85,12 +88,12 @@ cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph,
         auto k = k_fft_fwd_fp64<double2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)Tth, (const double2 *)Tph, (double2 *)p.d_F,
-                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol);
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
     } else {
         auto k = k_fft_fwd_fp64<float2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (double2 *)p.d_F,
-                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol);
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
     }
     return cudaGetLastError();
 }
@@ -105,12 +108,12 @@ cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_
         auto k = k_fft_inv_fp64<double2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (double2 *)Tth, (double2 *)Tph, rp,
-                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff);
     } else {
         auto k = k_fft_inv_fp64<float2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (float2 *)Tth, (float2 *)Tph, rp,
-                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff);
     }
     return cudaGetLastError();
 }

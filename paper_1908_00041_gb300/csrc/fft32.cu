@@ -245,7 +245,8 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const float2 *__restrict__ Tth, const float2 *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
-    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf)
+    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf,
+    const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_f4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_f4);
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const int nr = eq ? 2 : 4;    // rings: (th, j), (ph, j), (th, j'), (ph, j')
     const int jm = nlat - 1 - j;
     const int n2 = n / 2;         // float4 per ring
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
     // loads are issued in batches of kLoadBatch per thread before any is stored
     for (int i0 = threadIdx.x; i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
         float4 v[kLoadBatch];
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
                 const int ring = idx / n2, k2 = idx % n2;
                 const float2 *src = (ring & 1) ? Tph : Tth;
                 const int jj = (ring < 2) ? j : jm;
-                v[u] = __ldg(reinterpret_cast<const float4 *>(src + ((size_t)b * nlat + jj) * n) + k2);
+                v[u] = __ldg(reinterpret_cast<const float4 *>(src + fb + (size_t)jj * n) + k2);
             }
         }
 #pragma unroll
@@ -317,7 +319,8 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
     const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
-    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP)
+    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP,
+    const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -392,7 +395,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
         const float2 v1 = buf[LOG2N > 0 ? padi(i1) : i1];
         float2 *dst = (ring & 1) ? Tph : Tth;
         const int jj = (ring < 2) ? j : jm;
-        reinterpret_cast<float4 *>(dst + ((size_t)b * nlat + jj) * n)[k2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+        reinterpret_cast<float4 *>(dst + fb + (size_t)jj * n)[k2] = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
 }
 
@@ -408,7 +412,7 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, rp,
                                    p.fft.tw32, p.d_perm, p.unit_weights ? p.d_omega_unit : p.d_omega, p.L,
-                                   p.nlat, p.J, p.has_eq, p.nf);
+                                   p.nlat, p.J, p.has_eq, p.nf, p.d_toff);
     return cudaGetLastError();
 }
 
@@ -422,7 +426,7 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
                                    p.d_perm, p.d_sin, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
-                                   p.has_eq, p.JP);
+                                   p.has_eq, p.JP, p.d_toff);
     return cudaGetLastError();
 }
 

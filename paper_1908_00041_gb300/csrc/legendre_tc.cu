@@ -60,26 +60,22 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
     l = __bfloat16_as_ushort(bl);
 }
 
-// Generator: one CTA per (mu, block of 128 folded latitudes), one latitude per thread.
-// Each thread runs the scaled FP64 recurrence over all rows l = mu..L+1 and packs, per
-// parity, 8 consecutive rows into one 16-byte core-matrix row per piece.
+// Generator: 128 threads per CTA arranged as (128 / lt) orders x lt latitudes (lt = 32,
+// 64 or 128, a multiple of the warp so each warp runs one order); a CTA covers mb such
+// order groups in turn.  One thread runs the scaled FP64 recurrence of one (order,
+// latitude) over all rows l = mu..L+1 and packs, per parity, 8 consecutive rows into
+// one 16-byte core-matrix row per piece.  (lt, mb) is the block shape the autotuner
+// picks per degree.
 //   fwd = true : forward A layout, item (mu, p, m_tile) at lam_off[mu*2+p] + m_tile*nkf*48KB
 //   fwd = false: adjoint A layout, item (mu, p, j_tile) at lam_off[mu*2+p] + j_tile*nka*48KB
 template <bool FWD>
-__global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
-    unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
-    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
-    int J, int JP)
+__device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const long long *__restrict__ lam_off,
+                                          const double *__restrict__ xj, const double *__restrict__ sj,
+                                          const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
+                                          int J, int JP, int mu, int j)
 {
-    extern __shared__ double sm_gen[];
-    const int jblocks = JP / kGenThreads;
-    const int mu = blockIdx.x / jblocks, jb = blockIdx.x % jblocks;
-    const int j = jb * kGenThreads + threadIdx.x;
     const int nrow = L + 2 - mu;
-    const long long t0 = tab_off(L, mu);
-    double *As = sm_gen;
-    for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
-    __syncthreads();
+    const double *As = Atab + tab_off(L, mu);   // recurrence multipliers of this order
 
     double x = 0.0, y1 = 0.0, y2 = 0.0;
     int c = 1 << 20;
@@ -107,7 +103,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
             if (r < nrow) {
                 double yl = y1;
                 if (r > 0) {
-                    yl = fma(As[r] * x, y1, -y2);
+                    yl = fma(__ldg(As + r) * x, y1, -y2);
                     y2 = y1;
                     y1 = yl;
                 }
@@ -150,6 +146,23 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
                 }
             }
         }
+    }
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
+    unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
+    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
+    int J, int JP, int lt, int mb)
+{
+    const int olanes = kGenThreads / lt;
+    const int jblocks = JP / lt;
+    const int jb = blockIdx.x % jblocks, og = blockIdx.x / jblocks;
+    const int j = jb * lt + threadIdx.x % lt;
+    for (int k = 0; k < mb; ++k) {
+        const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
+        if (mu > L) break;
+        gen_order<FWD>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, j);
     }
 }
 
@@ -199,9 +212,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
 
 template <int N>
 __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
-    const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-    const TcItem *__restrict__ items, int nitems,
-    float *__restrict__ out, int a_mn_major, int *__restrict__ status)
+    const GemmGroup *__restrict__ groups, const TcItem *__restrict__ items, int nitems, int a_mn_major,
+    int *__restrict__ status)
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);   // 4 lane quadrants x N / 128 column parts
     constexpr int kPieceB = kChunkK * N * 2;        // bytes of one B piece per chunk
@@ -236,6 +248,8 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
             int stage = 0;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const TcItem I = items[it];
+                // the group's tensor maps live in global memory (generic addresses)
+                const CUtensorMap *tmap_a = &groups[I.group].tmap_a, *tmap_b = &groups[I.group].tmap_b;
                 for (int c = 0; c < I.nk; ++c) {
                     if (!wait_or_abort(&S.empty[stage], ((phase >> stage) & 1) ^ 1, abort)) {
                         set_status(status, FAVEST_ETIMEOUT);
@@ -245,14 +259,14 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                     tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkB);
                     // operand buffers are 2-D arrays of 512-byte rows: a chunk is a box
                     // of whole rows starting at its byte offset / 512
-                    tc::tma_load_2d(S.a[stage], &tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
+                    tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
                                     &S.full[stage]);
                     if (I.b_box) {
                         for (int q = 0; q < kPieces; ++q)
-                            tc::tma_load_5d(S.b[stage] + q * kPieceB, &tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
+                            tc::tma_load_5d(S.b[stage] + q * kPieceB, tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
                                             (kChunkK / 8) * c, &S.full[stage]);
                     } else {
-                        tc::tma_load_2d(S.b[stage], &tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
+                        tc::tma_load_2d(S.b[stage], tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
                                         &S.full[stage]);
                     }
                     phase ^= 1u << stage;
@@ -376,7 +390,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                 // 8 columns per field: this warp writes fields part*16 .. part*16+15 of the tile
                 const long long col_gs = __ldg(&items[it].col_gs);
                 // rows come in groups of 4 consecutive 32-byte records; out_ld = group stride
-                float *dst = out + __ldg(&items[it].out_off) + (long long)(row >> 2) * __ldg(&items[it].out_ld) +
+                float *dst = groups[__ldg(&items[it].group)].out + __ldg(&items[it].out_off) + (long long)(row >> 2) * __ldg(&items[it].out_ld) +
                              (row & 3) * 8 + (long long)(part * (kEpiCols / 8)) * col_gs;
 #pragma unroll
                 for (int g = 0; g < kEpiCols / 8; ++g) {
@@ -393,40 +407,52 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
 }
 
 template <int N>
-cudaError_t launch_gemm_n(const Plan &p, bool fwd, cudaStream_t s)
+cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nitems, int a_mn_major, int *status,
+                          int num_sms, cudaStream_t s)
 {
     const size_t smem = sizeof(GemmSmem<N>) + 1024;
     auto k = k_tc_gemm<N>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int nitems = fwd ? p.n_items_f : p.n_items_a;
-    const int grid = nitems < p.num_sms ? nitems : p.num_sms;
+    const int grid = nitems < num_sms ? nitems : num_sms;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, gemm_threads<N>(), smem, s>>>(p.tmap_lam, fwd ? p.tmap_fb : p.tmap_gb,
-                                            fwd ? p.d_items_f : p.d_items_a, nitems, fwd ? p.d_Q32 : p.d_S32,
-                                            fwd ? 1 : 0, p.d_status);
+    k<<<grid, gemm_threads<N>(), smem, s>>>(groups, items, nitems, a_mn_major, status);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s)
+{
+    if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
+    const int olanes = kGenThreads / lt;
+    const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
+    const int grid = (p.JP / lt) * ogroups;
+    if (fwd)
+        k_gen_lambda<true><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam, p.d_lam_off_f, p.d_x, p.d_sin,
+                                                        p.d_cmu, p.d_A, p.L, p.J, p.JP, lt, mb);
+    else
+        k_gen_lambda<false><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam, p.d_lam_off_a, p.d_x, p.d_sin,
+                                                         p.d_cmu, p.d_A, p.L, p.J, p.JP, lt, mb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s)
 {
-    const int jblocks = p.JP / kGenThreads;
-    const int grid = (p.L + 1) * jblocks;
-    const size_t smem = (size_t)(p.L + 2) * sizeof(double);
-    if (fwd)
-        k_gen_lambda<true><<<grid, kGenThreads, smem, s>>>((unsigned char *)p.d_lam, p.d_lam_off_f, p.d_x,
-                                                           p.d_sin, p.d_cmu, p.d_A, p.L, p.J, p.JP);
-    else
-        k_gen_lambda<false><<<grid, kGenThreads, smem, s>>>((unsigned char *)p.d_lam, p.d_lam_off_a, p.d_x,
-                                                            p.d_sin, p.d_cmu, p.d_A, p.L, p.J, p.JP);
-    return cudaGetLastError();
+    return launch_gen_lambda_shape(p, fwd, p.gen_lt, p.gen_mb, s);
+}
+
+cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,
+                                 int a_mn_major, int *status, int num_sms, cudaStream_t s)
+{
+    return gemm_n == 256 ? launch_gemm_n<256>(groups, items, nitems, a_mn_major, status, num_sms, s)
+                         : launch_gemm_n<128>(groups, items, nitems, a_mn_major, status, num_sms, s);
 }
 
 cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s)
 {
-    return p.gemm_n == 256 ? launch_gemm_n<256>(p, fwd, s) : launch_gemm_n<128>(p, fwd, s);
+    return launch_tc_gemm_items(p.gemm_n, p.d_ggroups, fwd ? p.d_items_f : p.d_items_a,
+                                fwd ? p.n_items_f : p.n_items_a, fwd ? 1 : 0, p.d_status, p.num_sms, s);
 }
 
 }  // namespace favest

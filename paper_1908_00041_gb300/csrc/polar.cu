@@ -55,7 +55,8 @@ constexpr int kPolarWarps = 8;       // warps per CTA, each over its own range o
 // values.
 __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
-    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP)
+    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
+    const long long *__restrict__ coff)
 {
     __shared__ float part[kPolarWarps][kPolarJ * 16][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -67,8 +68,9 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const int mulim = (int)ceil(1.5 * (L + 1) * sin_j[jlast]) + 16;
     if (mu0 >= mulim) return;                          // uniform over the CTA
     const bool active = mu >= 1 && mu <= L && mu < muc;
-    const float2 *af = a + (size_t)f * K;
-    const float2 *bf = b + (size_t)f * K;
+    const size_t cb = coff ? (size_t)coff[f] : (size_t)f * K;
+    const float2 *af = a + cb;
+    const float2 *bf = b + cb;
     const float w = (float)mu;
     float sum[kPolarJ][2][8], cmp[kPolarJ][2][8];
 #pragma unroll
@@ -244,7 +246,7 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
     const int K = p.L * p.L + 2 * p.L;
     dim3 grid(p.pol_muc / 32, p.B, (p.pol_jc + kPolarJ - 1) / kPolarJ);
     k_polar_patch<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin,
-                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.JP);
+                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.JP, p.d_coff);
     return cudaGetLastError();
 }
 
