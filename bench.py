@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP64 / small-degree / ragged-batch form measurements")
     return ap.parse_args()
 
 
@@ -161,6 +163,100 @@ def kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B):
 
 
 # ---------------------------------------------------------------------------
+# the other forms: FP64 path at the same workload, the two FP64 configurations, the
+# ragged batch (each a few CUDA-event-timed steps after warm-up)
+# ---------------------------------------------------------------------------
+def time_steps(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_forms(L, B, a, b, split_value, fp64_peak):
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    stream = torch.cuda.current_stream()
+    forms = {}
+    # FP64 path, same workload (complex64 fields in and out)
+    p64 = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_C64)
+    tt = torch.empty(p64.field_shape(), dtype=torch.complex64, device="cuda")
+    tp = torch.empty_like(tt)
+    a2 = torch.empty_like(a)
+    b2 = torch.empty_like(b)
+
+    def st64():
+        p64.adj(a, b, tt, tp, stream=stream)
+        p64.fwd(tt, tp, a2, b2, stream=stream)
+    p64.profile(True)
+    ms = time_steps(st64, 2, 1, stream)
+    prof = p64.profile_read()
+    p64.profile(False)
+    kern = {}
+    for name, (tot, n) in prof.items():
+        nb, fl, pipe = p64.kernel_work(name)
+        t = tot / n * 1e-3
+        kern[name] = {"ms_per_launch": tot / n, "fp64_frac": (fl / t / 1e12 / fp64_peak) if pipe == 1 else None}
+    v64 = B / (ms * 1e-3)
+    forms["fp64_same_workload"] = {"value": v64, "unit": "fields/s", "ms_per_step": ms, "kernels": kern}
+    forms["split_speedup_over_fp64"] = split_value / v64
+    p64.close()
+    del tt, tp, a2, b2
+    # C1: FP64, L = 16, one field (complex128)
+    for name, Lc, seed in (("fp64_L16_one_field", 16, 0), ("fp64_L511_one_field", 511, 1)):
+        ca, cb = synthetic.coefficients(Lc, 1, seed=seed, decay=1.0)
+        pc = api.Plan(Lc, 1, api.FAVEST_FP64, api.FAVEST_IO_C128)
+        da = torch.as_tensor(ca).cuda()
+        db = torch.as_tensor(cb).cuda()
+        xt = torch.empty(pc.field_shape(), dtype=torch.complex128, device="cuda")
+        xp = torch.empty_like(xt)
+        ra = torch.empty_like(da)
+        rb = torch.empty_like(db)
+        nst = 200 if Lc == 16 else 5
+        t_adj = time_steps(lambda: pc.adj(da, db, xt, xp, stream=stream), nst, 3, stream)
+        t_fwd = time_steps(lambda: pc.fwd(xt, xp, ra, rb, stream=stream), nst, 3, stream)
+        torch.cuda.synchronize()
+        rt = float(np.max(np.abs(ra.cpu().numpy() - ca)) / np.max(np.abs(ca)))
+        forms[name] = {"adj_ms": t_adj, "fwd_ms": t_fwd, "fields_per_s": 1.0 / ((t_adj + t_fwd) * 1e-3),
+                       "roundtrip_max_rel": rt}
+        pc.close()
+    # ragged batch: 256 fields, L uniform over {31, 63, 127, 255, 511} (seed 3), (l+1)^-1
+    Ls, rng = synthetic.ragged_degrees(256, [31, 63, 127, 255, 511], seed=3)
+    Ls = [int(x) for x in Ls]
+    bp = api.BatchPlan(Ls, api.FAVEST_BF16X6, api.FAVEST_IO_C64, autotune=True, graph=True)
+    ga = torch.zeros(bp.coef_elems, dtype=torch.complex64, device="cuda")
+    gb = torch.zeros_like(ga)
+    for i, Lr in enumerate(Ls):
+        ca, cb = synthetic.coefficients(Lr, 1, seed=None, decay=1.0, rng=rng)
+        bp.coef(ga, i).copy_(torch.as_tensor(ca[0]).to(torch.complex64))
+        bp.coef(gb, i).copy_(torch.as_tensor(cb[0]).to(torch.complex64))
+    gt = torch.empty(bp.field_elems, dtype=torch.complex64, device="cuda")
+    gp = torch.empty_like(gt)
+    fa = torch.empty_like(ga)
+    fb = torch.empty_like(gb)
+
+    def stb():
+        bp.adj(ga, gb, gt, gp, stream=stream)
+        bp.fwd(gt, gp, fa, fb, stream=stream)
+    ms = time_steps(stb, 10, 3, stream)     # warm-up includes the eager run and the capture
+    assert bp.status() == 0
+    forms["ragged_batch"] = {"value": len(Ls) / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms,
+                             "fields": len(Ls), "graph": True, "groups": bp.groups(),
+                             "launches_per_step": None}
+    bp.close()
+    return forms
+
+
+# ---------------------------------------------------------------------------
 def reference_arm(args, rank):
     """The CPU oracle (separable FP64 form) on a bounded sample: each step computes
     one field's AdjVSHT + FwdVSHT restricted to every 64th order (1/64 of the
@@ -212,14 +308,14 @@ def reference_arm(args, rank):
 
 
 def cpu_baseline(args):
-    """Oracle O3 on the host cores, one field, every 8th order (1/8 of the work)."""
+    """Oracle O3 on the host cores, one field, every 2nd order (half of the work)."""
     import numpy as np
     import oracle
     from paper_1908_00041_gb300 import synthetic
     L = args.L
     x, W, theta, phi = oracle.grid(L)
     a, b = synthetic.coefficients(L, 1, seed=2, decay=1.5)
-    mstep = 8
+    mstep = 2
     nm = 2 * L + 1
     t0 = time.perf_counter()
     tt, tp = oracle.adj_sep_orders(L, x, a[0], b[0], 2 * (L + 1), 0, mstep)
@@ -227,7 +323,7 @@ def cpu_baseline(args):
     dt = time.perf_counter() - t0
     frac = len(range(0, nm, mstep)) / nm
     return {"value": frac / dt, "unit": "fields/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "one field of the L=1023 workload, adjoint+forward over every 8th order "
+            "sample": "one field of the L=1023 workload, adjoint+forward over every 2nd order "
                       "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (frac, dt)}
 
 
@@ -380,6 +476,10 @@ def main():
             errors["fwd_vs_fp64_rms_rel"] = max(rerr(ra, fa), rerr(rb, fb))
             p64.close()
 
+    forms = None
+    if not args.no_forms and rank == 0 and prec_name == "bf16x6":
+        forms = measure_forms(L, B, a, b, value, fp64_peak)
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
@@ -402,6 +502,7 @@ def main():
             "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "errors": errors, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
+            "forms": forms,
         }
         print(json.dumps(rec), flush=True)
     plan.close()
