@@ -226,6 +226,18 @@ int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *
                         long long *launches);
 
 /*
+ * Failure-path self-test (no counterpart in the paper).  Launches the split-precision
+ * tensor-core GEMM of this plan on one work item with its operand loads switched off and
+ * every device-side wait bounded by poll_limit mbarrier polls, on the legacy stream, and
+ * synchronises.  The waits cannot complete, so the kernel must give up, record
+ * FAVEST_ETIMEOUT in the plan's status word, release its tensor memory and return; the
+ * call returns that status (read and cleared as favest_status does) and, if elapsed_ms
+ * is not null, the kernel's duration.  The context stays usable.  FAVEST_EUNSUPPORTED for
+ * FP64 plans.
+ */
+int favest_selftest_wait_timeout(favest_plan plan, unsigned poll_limit, double *elapsed_ms);
+
+/*
  * Algorithmic work of one launch of a kernel of this plan, by the name that
  * favest_profile_read reports: *bytes = the minimum DRAM traffic (every operand read
  * once, every result written once, no re-reads, no padding), *flops = arithmetic

@@ -85,6 +85,7 @@ def lib(build_if_missing=False):
             L.favest_kernel_work.argtypes = [vp, ctypes.c_char_p, d, d, ctypes.POINTER(ctypes.c_int)]
             pi, pll = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)
             L.favest_plan_tune.argtypes = [vp, vp]
+            L.favest_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint, d]
             L.favest_plan_gen_shape.argtypes = [vp, pi, pi]
             L.favest_batch_create.argtypes = [i, pi, pll, pll, i, i, i, ctypes.POINTER(vp)]
             L.favest_fwd_batched.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -312,6 +313,12 @@ class Plan:
 
     def workspace_bytes(self):
         return favest_plan_workspace_bytes(self.handle)
+
+    def selftest_wait_timeout(self, poll_limit=1 << 14):
+        """Run the failure-path self-test (see include/favest.h): returns (status, ms)."""
+        ms = ctypes.c_double()
+        st = lib().favest_selftest_wait_timeout(ctypes.c_void_p(self.handle), int(poll_limit), ctypes.byref(ms))
+        return st, ms.value
 
     def tune(self, stream=None):
         """Pick the fastest generator block shape for this plan (split precision)."""

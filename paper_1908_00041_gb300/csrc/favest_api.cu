@@ -705,6 +705,28 @@ int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *
     return k;
 }
 
+int favest_selftest_wait_timeout(favest_plan plan, unsigned poll_limit, double *elapsed_ms)
+{
+    if (!plan || poll_limit == 0) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    if (p.precision != FAVEST_BF16X6) return FAVEST_EUNSUPPORTED;
+    int st = check_device(p);
+    if (st) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FAVEST_ECUDA;
+    cudaEventRecord(e0, 0);
+    cudaError_t e = launch_gemm_selftest(p, poll_limit, 0);
+    cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return FAVEST_ECUDA;
+    if (elapsed_ms) *elapsed_ms = ms;
+    return favest_status(plan, nullptr);   // reads and clears the status word
+}
+
 int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, double *flops, int *pipe)
 {
     if (!plan || !kernel || !bytes || !flops || !pipe) return FAVEST_EINVAL;

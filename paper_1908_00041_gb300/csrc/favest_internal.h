@@ -168,6 +168,8 @@ cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph,
 cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
 cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
 cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s);
+// failure-path self-test: one GEMM item with no operand loads and the given wait bound
+cudaError_t launch_gemm_selftest(const Plan &p, uint32_t poll_limit, cudaStream_t s);
 // one persistent GEMM launch over an explicit item list (items[i].group indexes groups)
 cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,
                                  int a_mn_major, int *status, int num_sms, cudaStream_t s);

@@ -200,10 +200,13 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
-// Wait that also gives up when another role aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+// Polls of an mbarrier before a wait gives up (about a second).
+constexpr uint32_t kWaitPolls = 1u << 26;
+
+// Wait that also gives up after `limit` polls, or when another role aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort, uint32_t limit)
 {
-    for (uint32_t i = 0; i < (1u << 26); ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
         if ((i & 1023) == 1023 && *abort) return false;
     }
@@ -213,7 +216,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
 template <int N>
 __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     const GemmGroup *__restrict__ groups, const TcItem *__restrict__ items, int nitems, int a_mn_major,
-    int *__restrict__ status)
+    int *__restrict__ status, uint32_t poll_limit, int skip_loads)
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);   // 4 lane quadrants x N / 128 column parts
     constexpr int kPieceB = kChunkK * N * 2;        // bytes of one B piece per chunk
@@ -243,7 +246,9 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
 
     if (warp == 0) {
         // ---------------- producer ----------------
-        if (lane == 0) {
+        // (skip_loads: failure-path self-test -- nothing is loaded, so the MMA and epilogue
+        // waits must run out, report FAVEST_ETIMEOUT and return)
+        if (lane == 0 && !skip_loads) {
             uint32_t phase = 0;                     // bit s: parity of stage s's next use
             int stage = 0;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                 // the group's tensor maps live in global memory (generic addresses)
                 const CUtensorMap *tmap_a = &groups[I.group].tmap_a, *tmap_b = &groups[I.group].tmap_b;
                 for (int c = 0; c < I.nk; ++c) {
-                    if (!wait_or_abort(&S.empty[stage], ((phase >> stage) & 1) ^ 1, abort)) {
+                    if (!wait_or_abort(&S.empty[stage], ((phase >> stage) & 1) ^ 1, abort, poll_limit)) {
                         set_status(status, FAVEST_ETIMEOUT);
                         *abort = 1;
                         break;
@@ -289,13 +294,13 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
             constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const TcItem I = items[it];
-                if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort)) {
+                if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort, poll_limit)) {
                     set_status(status, FAVEST_ETIMEOUT);
                     *abort = 1;
                     break;
                 }
                 for (int c = 0; c < I.nk; ++c) {
-                    if (!wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort)) {
+                    if (!wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort, poll_limit)) {
                         set_status(status, FAVEST_ETIMEOUT);
                         *abort = 1;
                         break;
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                         tc::mma_f16(dcorr, A2, B0, idesc, 1);
                     }
                     // hi*hi of this chunk into the drained main columns
-                    if (!wait_or_abort(&S.dmain_empty, (main_use & 1) ^ 1, abort)) {
+                    if (!wait_or_abort(&S.dmain_empty, (main_use & 1) ^ 1, abort, poll_limit)) {
                         set_status(status, FAVEST_ETIMEOUT);
                         *abort = 1;
                         break;
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
             for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
             bool ok = true;
             for (int c = 0; c < nk; ++c) {
-                if (!wait_or_abort(&S.dmain_full, main_use & 1, abort)) { ok = false; break; }
+                if (!wait_or_abort(&S.dmain_full, main_use & 1, abort, poll_limit)) { ok = false; break; }
                 tc::fence_after_sync();
                 const uint32_t col0 = tmem + lane_base + part * kEpiCols;
 #pragma unroll
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                 if (lane == 0) tc::mbar_arrive(&S.dmain_empty);
                 main_use++;
             }
-            if (!ok || !wait_or_abort(&S.dcorr_full, corr_use & 1, abort)) {
+            if (!ok || !wait_or_abort(&S.dcorr_full, corr_use & 1, abort, poll_limit)) {
                 set_status(status, FAVEST_ETIMEOUT);
                 *abort = 1;
                 break;
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
 
 template <int N>
 cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nitems, int a_mn_major, int *status,
-                          int num_sms, cudaStream_t s)
+                          int num_sms, cudaStream_t s, uint32_t poll_limit = kWaitPolls, int skip_loads = 0)
 {
     const size_t smem = sizeof(GemmSmem<N>) + 1024;
     auto k = k_tc_gemm<N>;
@@ -416,7 +421,7 @@ cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nite
     if (e != cudaSuccess) return e;
     const int grid = nitems < num_sms ? nitems : num_sms;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, gemm_threads<N>(), smem, s>>>(groups, items, nitems, a_mn_major, status);
+    k<<<grid, gemm_threads<N>(), smem, s>>>(groups, items, nitems, a_mn_major, status, poll_limit, skip_loads);
     return cudaGetLastError();
 }
 
@@ -447,6 +452,13 @@ cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcIt
 {
     return gemm_n == 256 ? launch_gemm_n<256>(groups, items, nitems, a_mn_major, status, num_sms, s)
                          : launch_gemm_n<128>(groups, items, nitems, a_mn_major, status, num_sms, s);
+}
+
+cudaError_t launch_gemm_selftest(const Plan &p, uint32_t poll_limit, cudaStream_t s)
+{
+    // one adjoint item, nothing loaded
+    return p.gemm_n == 256 ? launch_gemm_n<256>(p.d_ggroups, p.d_items_a, 1, 0, p.d_status, p.num_sms, s, poll_limit, 1)
+                           : launch_gemm_n<128>(p.d_ggroups, p.d_items_a, 1, 0, p.d_status, p.num_sms, s, poll_limit, 1);
 }
 
 cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s)
