@@ -253,7 +253,73 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
                              "fields": len(Ls), "graph": True, "groups": bp.groups(),
                              "launches_per_step": None}
     bp.close()
+    del ga, gb, gt, gp, fa, fb
+    # real fields (half-spectrum coefficients), L as the main workload, 32 and 64 fields
+    for Br in (B, 2 * B):
+        forms["real_fields_B%d" % Br] = measure_real(L, Br, stream)
     return forms
+
+
+def measure_real(L, B, stream):
+    """Split form on real fields: B fields, coefficients m >= 0 drawn as for the main
+    workload ((l+1)^-1.5, seed 2, m = 0 entries real), adj + fwd per step; errors of two
+    sampled fields against the FP64 complex path on the Hermitian-extended input."""
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    ha, hb = synthetic.half_coefficients(L, B, seed=2, decay=1.5)
+    pr = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_R32)
+    da = torch.as_tensor(ha).to(torch.complex64).cuda()
+    db = torch.as_tensor(hb).to(torch.complex64).cuda()
+    tt = torch.empty(pr.field_shape(), dtype=torch.float32, device="cuda")
+    tp = torch.empty_like(tt)
+    ra = torch.empty_like(da)
+    rb = torch.empty_like(db)
+
+    def step():
+        pr.adj(da, db, tt, tp, stream=stream)
+        pr.fwd(tt, tp, ra, rb, stream=stream)
+    ms = time_steps(step, 10, 3, stream)
+    pr.profile(True)
+    time_steps(step, 3, 0, stream)
+    prof = {k: v[0] / v[1] for k, v in pr.profile_read().items()}
+    pr.profile(False)
+    assert pr.status() == 0
+    # accuracy: sampled fields against the FP64 complex path
+    pick = [0, B - 1]
+    ls = np.concatenate([np.full(l + 1, l) for l in range(1, L + 1)])
+    ms_ = np.concatenate([np.arange(l + 1) for l in range(1, L + 1)])
+    full = ls * ls + ls + ms_ - 1
+    neg = ls * ls + ls - ms_ - 1
+    sg = np.where(ms_ % 2 == 1, -1.0, 1.0)
+
+    def extend(h):
+        out = np.zeros(h.shape[:-1] + (L * L + 2 * L,), np.complex128)
+        out[..., full] = h
+        out[..., neg[ms_ > 0]] = (sg * np.conj(h))[..., ms_ > 0]
+        return out
+    p64 = api.Plan(L, len(pick), api.FAVEST_FP64, api.FAVEST_IO_C128)
+    h32a = da.cpu().numpy()[pick].astype(np.complex128)
+    h32b = db.cpu().numpy()[pick].astype(np.complex128)
+    ct, cp = p64.adj(torch.as_tensor(extend(h32a)).cuda(), torch.as_tensor(extend(h32b)).cuda())
+    xt = tt[pick].to(torch.float64).to(torch.complex128).contiguous()
+    xp = tp[pick].to(torch.float64).to(torch.complex128).contiguous()
+    ca, cb = p64.fwd(xt, xp)
+    torch.cuda.synchronize()
+
+    def nerr(g, r):
+        g = np.asarray(g).reshape(len(pick), -1)
+        r = np.asarray(r).reshape(len(pick), -1)
+        return float(np.max(np.max(np.abs(g - r), axis=1) / np.max(np.abs(r), axis=1)))
+    err_adj = max(nerr(tt[pick].cpu().numpy(), ct.real.cpu().numpy()),
+                  nerr(tp[pick].cpu().numpy(), cp.real.cpu().numpy()))
+    err_fwd = max(nerr(ra[pick].cpu().numpy(), ca.cpu().numpy()[:, full]),
+                  nerr(rb[pick].cpu().numpy(), cb.cpu().numpy()[:, full]))
+    p64.close()
+    pr.close()
+    return {"value": B / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms, "fields": B,
+            "coefficients_per_family": L * (L + 3) // 2, "max_rel_err_adj_vs_fp64": err_adj,
+            "max_rel_err_fwd_vs_fp64": err_fwd, "sampled_fields": pick, "kernel_ms": prof}
 
 
 # ---------------------------------------------------------------------------

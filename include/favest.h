@@ -29,6 +29,17 @@
  *   complex = interleaved (re, im); element type set by the plan's io type:
  *       FAVEST_IO_C128 = double, FAVEST_IO_C64 = float.
  *
+ * Real fields (FAVEST_IO_R32; the paper's fields are real, T_k in R^3, Sec. 3): both
+ * components are real planes [batch][nlat][nphi] of float, and since then
+ * a_{l,-m} = (-1)^m conj(a_lm) (likewise b), only orders m >= 0 are stored:
+ *       a, b: [batch][L(L+3)/2] complex float, l-major: index l(l+1)/2 - 1 + m
+ *       for l = 1..L, m = 0..l.
+ * The forward transform of a real field returns exactly these entries of the complex
+ * transform (a_l0 and b_l0 are real).  The adjoint evaluates the real field
+ * Re S_L(a~, b~) of the Hermitian extension a~_{l,-m} = (-1)^m conj(a_lm) (m >= 1),
+ * i.e. S_L of the extension with the imaginary parts of a_l0, b_l0 ignored; for
+ * coefficients of a real field that is S_L itself.
+ *
  * Ownership: the caller owns every data buffer and stream.  A plan owns its constant
  * tables and its device workspace; both are freed by favest_plan_destroy.
  *
@@ -75,7 +86,8 @@ enum favest_precision {
 
 enum favest_io_type {
     FAVEST_IO_C128 = 0,  /* complex double */
-    FAVEST_IO_C64 = 1    /* complex float  */
+    FAVEST_IO_C64 = 1,   /* complex float  */
+    FAVEST_IO_R32 = 2    /* real fields (float), half-spectrum complex float coefficients */
 };
 
 /*
@@ -89,8 +101,9 @@ int favest_gl_grid(int nlat, double *x, double *w);
  * Create a plan for degree L and a batch of `batch` fields (1 <= batch <= 4096) on the
  * current CUDA device.  L >= 1; degrees beyond 1023 (more than 512 latitude pairs)
  * return FAVEST_EUNSUPPORTED in this version.  FAVEST_BF16X6
- * requires io_type FAVEST_IO_C64 (FAVEST_EUNSUPPORTED otherwise) and a device with
- * tcgen05 tensor cores (sm_100 family).
+ * requires io_type FAVEST_IO_C64 or FAVEST_IO_R32 (FAVEST_EUNSUPPORTED otherwise) and
+ * a device with tcgen05 tensor cores (sm_100 family); FAVEST_IO_R32 requires
+ * FAVEST_BF16X6 (FAVEST_EUNSUPPORTED otherwise).
  *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
  *       and latitude weights; NULL selects the built-in Gauss-Legendre rule.  When
  *       given, the nodes must lie strictly inside (-1, 1) and both arrays must be
@@ -107,6 +120,7 @@ int favest_plan_create(int L, int batch, int precision, int io_type,
  * FwdVSHT (Def. FwdVSHT, eq. fwdvsht2) of `batch` fields.
  *   Tth, Tph: device, [batch][nlat][nphi] complex (plan io type), read only.
  *   a, b:     device, [batch][L^2+2L] complex (plan io type), written.
+ *   (FAVEST_IO_R32: real float fields and [batch][L(L+3)/2] coefficients, m >= 0.)
  * Pointers must be aligned to the complex element size (to 16 bytes for
  * FAVEST_BF16X6 plans).  Asynchronous on `stream`.
  */
@@ -119,6 +133,8 @@ int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void
  *   a, b:     device, [batch][L^2+2L] complex, read only.
  *   Tth, Tph: device, [batch][nlat][nphi] complex, written (the Nyquist longitude
  *             bin m = L+1 carries no coefficient and is zero).
+ *   (FAVEST_IO_R32: [batch][L(L+3)/2] coefficients, m >= 0, and real float fields;
+ *   see the real-field note at the top of this file.)
  */
 int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph,
                void *stream);
@@ -198,6 +214,7 @@ int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
  *                          launch sequence, later ones launch the captured graph
  * Errors as for the single-field calls; favest_batch_status reads and clears the device
  * status words of all groups.  Calls on one batch must not overlap on the host.
+ * Real fields (FAVEST_IO_R32) are not batched in this version: FAVEST_EUNSUPPORTED.
  */
 typedef struct favest_batch_s *favest_batch;
 enum { FAVEST_BATCH_AUTOTUNE = 1, FAVEST_BATCH_GRAPH = 2 };

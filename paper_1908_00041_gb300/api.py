@@ -26,6 +26,7 @@ FAVEST_FP64 = 0
 FAVEST_BF16X6 = 1
 FAVEST_IO_C128 = 0
 FAVEST_IO_C64 = 1
+FAVEST_IO_R32 = 2
 FAVEST_FLAG_UNIT_WEIGHTS = 1
 FAVEST_FLAG_WEIGHTED = 2
 FAVEST_BATCH_AUTOTUNE = 1
@@ -249,8 +250,11 @@ class Plan:
         import torch
         self.L, self.batch, self.precision, self.io_type = int(L), int(batch), precision, io_type
         self.nlat, self.nphi = L + 1, 2 * (L + 1)
-        self.K = L * L + 2 * L
+        # real fields keep orders m >= 0 only: L(L+3)/2 coefficients per family
+        self.real = io_type == FAVEST_IO_R32
+        self.K = L * (L + 3) // 2 if self.real else L * L + 2 * L
         self.cdtype = torch.complex128 if io_type == FAVEST_IO_C128 else torch.complex64
+        self.fdtype = torch.float32 if self.real else self.cdtype
         self.handle = favest_plan_create(L, batch, precision, io_type, cos_theta, w_lat)
         self._unit = 0
 
@@ -265,11 +269,11 @@ class Plan:
         except Exception:
             pass
 
-    def _check_tensor(self, t, shape, name):
-        import torch
-        if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == shape):
+    def _check_tensor(self, t, shape, name, dtype=None):
+        dtype = dtype or self.cdtype
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == shape):
             raise ValueError("%s: expected contiguous CUDA %s tensor of shape %s, got %s %s %s"
-                             % (name, self.cdtype, shape, t.device, t.dtype, tuple(t.shape)))
+                             % (name, dtype, shape, t.device, t.dtype, tuple(t.shape)))
 
     def field_shape(self):
         return (self.batch, self.nlat, self.nphi)
@@ -284,8 +288,8 @@ class Plan:
 
     def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False):
         import torch
-        self._check_tensor(Tth, self.field_shape(), "Tth")
-        self._check_tensor(Tph, self.field_shape(), "Tph")
+        self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
+        self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
         if a is None:
             a = torch.empty(self.coef_shape(), dtype=self.cdtype, device=Tth.device)
         if b is None:
@@ -300,11 +304,11 @@ class Plan:
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
         if Tth is None:
-            Tth = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device)
+            Tth = torch.empty(self.field_shape(), dtype=self.fdtype, device=a.device)
         if Tph is None:
-            Tph = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device)
-        self._check_tensor(Tth, self.field_shape(), "Tth")
-        self._check_tensor(Tph, self.field_shape(), "Tph")
+            Tph = torch.empty(self.field_shape(), dtype=self.fdtype, device=a.device)
+        self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
+        self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
         favest_adj_ex(self.handle, a, b, Tth, Tph, FAVEST_FLAG_WEIGHTED if weighted else 0, stream)
         return Tth, Tph
 

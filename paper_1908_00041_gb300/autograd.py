@@ -66,11 +66,18 @@ class _AdjVSHT(torch.autograd.Function):
         return ga, gb, None
 
 
+def _complex_plan(plan):
+    if getattr(plan, "real", False):
+        raise NotImplementedError("differentiation is provided for complex-field plans only")
+
+
 def fwd_vsht(plan, Tth, Tph):
     """Differentiable FwdVSHT: (Tth, Tph) [batch, L+1, 2(L+1)] -> (a, b) [batch, L^2+2L]."""
+    _complex_plan(plan)
     return _FwdVSHT.apply(Tth, Tph, plan)
 
 
 def adj_vsht(plan, a, b):
     """Differentiable AdjVSHT: (a, b) [batch, L^2+2L] -> (Tth, Tph) [batch, L+1, 2(L+1)]."""
+    _complex_plan(plan)
     return _AdjVSHT.apply(a, b, plan)

@@ -233,6 +233,7 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
     *out = nullptr;
     if (nfields < 1 || !L) return FAVEST_EINVAL;
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
+    if (io_type == FAVEST_IO_R32) return FAVEST_EUNSUPPORTED;
     if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64) return FAVEST_EINVAL;
     if (flags & ~(FAVEST_BATCH_AUTOTUNE | FAVEST_BATCH_GRAPH)) return FAVEST_EINVAL;
     for (int i = 0; i < nfields; ++i)

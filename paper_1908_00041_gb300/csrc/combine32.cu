@@ -1,9 +1,12 @@
 // Coefficient-side stages of the split-precision path (same formulas as combine.cu):
 //   combine  : FP32 scalar sums Q (tensor-core GEMM output, rows l - mu, 8 columns per
-//              field: component c, sign s of m, re/im) -> a_lm, b_lm (complex64), FP64 math
+//              column group: component c, sign s of m, re/im) -> a_lm, b_lm (complex64)
 //   uncombine: a_lm, b_lm (complex64) -> scaled scalar coefficients g, written as three
 //              bf16 pieces in the tensor-core B-operand layout (K-chunks of 32 rows by
 //              N = 128 or 256 columns).
+// Real fields (REAL = true): a column group is a pair of fields 2q, 2q+1 at m = +mu, in the
+// slots the complex layout gives to m = +mu and m = -mu; coefficients are stored for
+// m >= 0 only, at l(l+1)/2 - 1 + m of a field's KR = L(L+3)/2.
 #include "favest_internal.h"
 
 #include <cuda_bf16.h>
@@ -22,10 +25,11 @@ constexpr int kCTRows = kCT + 2;  // degrees l0 - 1 .. l0 + 32 (one-row halo eac
 // (rows of order mu from tab_off(L, mu): l = mu, mu+2, .. then l = mu+1, ..) in shared
 // memory.  Phase 2: warp w takes degrees l0 + w, l0 + w + 8, ..; lane = order, so the
 // stores of a_{l,+mu} (ascending) and a_{l,-mu} (descending) are contiguous runs.
+template <bool REAL>
 __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a,
                                                       float2 *__restrict__ bo, const float *__restrict__ P,
                                                       const float *__restrict__ M, const float *__restrict__ R,
-                                                      int L, int K, const long long *__restrict__ coff)
+                                                      int L, int K, const long long *__restrict__ coff, int B)
 {
     // [order][(degree - (l0 - 1)) * 2 + half]; the odd row length (69 x 16 B) spreads the
     // lanes (orders) of a quarter-warp over distinct bank groups
@@ -71,9 +75,10 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
         const float qm[8] = {qma.x, qma.y, qma.z, qma.w, qmb.x, qmb.y, qmb.z, qmb.w};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            if (mu == 0 && s == 1) continue;
-            const int m = s ? -mu : mu;
-            const float sg = (s && (mu & 1)) ? -1.f : 1.f;
+            if (!REAL && mu == 0 && s == 1) continue;
+            if (REAL && 2 * bi + s >= B) continue;
+            const int m = (!REAL && s) ? -mu : mu;
+            const float sg = (!REAL && s && (mu & 1)) ? -1.f : 1.f;
             const float Rm = Rl * (float)m;
             // th: cols s*2 + {0,1}; ph: 4 + s*2 + {0,1}
             const int ct = s * 2, cp = 4 + s * 2;
@@ -83,7 +88,8 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
             const float ay = sg * fmaf(Pl, q1[ct + 1], fmaf(-Ml, tmy, -Rm * q0[cp]));
             const float bx = sg * fmaf(Pl, q1[cp], fmaf(-Ml, pmx, -Rm * q0[ct + 1]));
             const float by = sg * fmaf(Pl, q1[cp + 1], fmaf(-Ml, pmy, Rm * q0[ct]));
-            const size_t k = cb + (size_t)l * l + l + m - 1;
+            const size_t k = REAL ? (size_t)(2 * bi + s) * K + (size_t)l * (l + 1) / 2 - 1 + mu
+                                  : cb + (size_t)l * l + l + m - 1;
             a[k] = make_float2(ax, ay);
             bo[k] = make_float2(bx, by);
         }
@@ -123,14 +129,16 @@ constexpr int kUS = 4 * (kCT + 1) + 1;  // shared row stride (float2, odd) of th
 //   G_th(j, 0) = sum_l a_l0 lambda_l^1(theta_j),  G_ph(j, 0) = sum_l b_l0 lambda_l^1(theta_j)
 // with no division: order 0 is synthesised on the order-1 Legendre tiles (rows l = 1..L+1)
 // and the inverse FFT stage skips the 1/sin(theta) factor for it.
+template <bool REAL>
 __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict__ a, const float2 *__restrict__ b,
                                                         unsigned char *__restrict__ gb,
                                                         const long long *__restrict__ g_off,
                                                         const float *__restrict__ P, const float *__restrict__ M,
                                                         const float *__restrict__ R, const float *__restrict__ k1tab,
-                                                        int L, int K, int N, const long long *__restrict__ coff)
+                                                        int L, int K, int N, const long long *__restrict__ coff, int B)
 {
-    // cs[(l - (l0 - 1)) * kUS + q * (kCT + 1) + order], q = (a+, a-, b+, b-)
+    // cs[(l - (l0 - 1)) * kUS + q * (kCT + 1) + order], q = (a+, a-, b+, b-); real fields:
+    // (a of field 2q, a of 2q+1, b of 2q, b of 2q+1), all at m = +mu
     __shared__ float2 cs[kCTRows * kUS];
     int t = blockIdx.x, lb = 0;
     while (t > lb) {
@@ -144,10 +152,16 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
     for (int e = threadIdx.x; e < kCTRows * 4 * kCT; e += blockDim.x) {
         const int i = e % kCT, q = (e / kCT) & 3, d = e / (4 * kCT);
         const int mu = mu0 + i, l = l0 - 1 + d;
-        const int m = (q & 1) ? -mu : mu;
         float2 v = make_float2(0.f, 0.f);
-        if (l >= 1 && l <= L && mu <= l && !(mu == 0 && (q & 1)))
-            v = __ldg(((q & 2) ? b : a) + cb + (size_t)l * l + l + m - 1);
+        if (REAL) {
+            const int bf = 2 * bi + (q & 1);
+            if (l >= 1 && l <= L && mu <= l && bf < B)
+                v = __ldg(((q & 2) ? b : a) + (size_t)bf * K + (size_t)l * (l + 1) / 2 - 1 + mu);
+        } else {
+            const int m = (q & 1) ? -mu : mu;
+            if (l >= 1 && l <= L && mu <= l && !(mu == 0 && (q & 1)))
+                v = __ldg(((q & 2) ? b : a) + cb + (size_t)l * l + l + m - 1);
+        }
         cs[d * kUS + q * (kCT + 1) + i] = v;
     }
     __syncthreads();
@@ -173,6 +187,11 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
             const float2 a0 = cs[d * kUS + 0 * (kCT + 1) + i], b0 = cs[d * kUS + 2 * (kCT + 1) + i];
             v[0] = k1 * a0.x; v[1] = k1 * a0.y; v[2] = 0.f; v[3] = 0.f;
             v[4] = k1 * b0.x; v[5] = k1 * b0.y; v[6] = 0.f; v[7] = 0.f;
+            if (REAL) {   // the pair's second field in the slots of m = -0
+                const float2 a1 = cs[d * kUS + 1 * (kCT + 1) + i], b1 = cs[d * kUS + 3 * (kCT + 1) + i];
+                v[2] = k1 * a1.x; v[3] = k1 * a1.y;
+                v[6] = k1 * b1.x; v[7] = k1 * b1.y;
+            }
         } else {
             const long long t0 = tab_off(L, mu);
             const float Pm = (r > 0) ? P[t0 + r - 1] : 0.f;
@@ -180,8 +199,8 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
             const float Rr = (l <= L) ? R[t0 + r] : 0.f;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const int m = s ? -mu : mu;
-                const float sg = (s && (mu & 1)) ? -1.f : 1.f;
+                const int m = (!REAL && s) ? -mu : mu;
+                const float sg = (!REAL && s && (mu & 1)) ? -1.f : 1.f;
                 const float Rl = Rr * (float)m;
                 const float2 am1 = cs[(d - 1) * kUS + s * (kCT + 1) + i];
                 const float2 ap1 = cs[(d + 1) * kUS + s * (kCT + 1) + i];
@@ -220,23 +239,25 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
 
 cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
 {
-    const int K = p.L * p.L + 2 * p.L;
+    const int K = p.real ? p.L * (p.L + 3) / 2 : p.L * p.L + 2 * p.L;
     const int nb = (p.L + 1 + kCT - 1) / kCT;
-    dim3 grid(nb * (nb + 1) / 2, p.B);
-    k_combine_bf16<<<grid, 256, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32, p.d_M32,
-                                        p.d_R32, p.L, K, p.d_coff);
+    dim3 grid(nb * (nb + 1) / 2, p.ncg);
+    auto k = p.real ? k_combine_bf16<true> : k_combine_bf16<false>;
+    k<<<grid, 256, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32, p.d_M32, p.d_R32, p.L, K,
+                           p.d_coff, p.B);
     return cudaGetLastError();
 }
 
 cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s)
 {
-    const int K = p.L * p.L + 2 * p.L;
+    const int K = p.real ? p.L * (p.L + 3) / 2 : p.L * p.L + 2 * p.L;
     const int ob_n = (p.L + 1 + kCT - 1) / kCT, lb_n = (p.L + 2 + kCT - 1) / kCT;
     // tiles (ob <= lb) of the row triangle; order blocks never exceed row blocks
-    dim3 grid(lb_n * (lb_n + 1) / 2, p.B);
+    dim3 grid(lb_n * (lb_n + 1) / 2, p.ncg);
     (void)ob_n;
-    k_uncombine_bf16<<<grid, 256, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb,
-                                         p.d_g_off, p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n, p.d_coff);
+    auto k = p.real ? k_uncombine_bf16<true> : k_uncombine_bf16<false>;
+    k<<<grid, 256, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb, p.d_g_off, p.d_P32,
+                           p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n, p.d_coff, p.B);
     return cudaGetLastError();
 }
 

@@ -278,14 +278,14 @@ int alloc_workspace_bf16(Plan &p)
     const int L = p.L;
     const int KC = kGemmChunkK;
     const long long CHA = 3LL * 128 * KC * 2;    // bytes per A chunk (3 bf16 pieces of 128 x KC)
-    p.gemm_n = (p.force_gemm_n == 256 || 8 * p.B > 128) ? 256 : 128;
+    p.gemm_n = (p.force_gemm_n == 256 || 8 * p.ncg > 128) ? 256 : 128;
     const long long CHB = 3LL * KC * p.gemm_n * 2;   // bytes per B chunk (3 pieces of KC x N)
     p.JP = (p.J + 127) / 128 * 128;
-    p.ncolr = (8 * p.B + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
+    p.ncolr = (8 * p.ncg + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
     p.n_tiles = p.ncolr / p.gemm_n;
     p.nf = p.ncolr / 8;
     p.nk_f = p.JP / KC;
-    const int fpt = p.gemm_n / 8;                  // fields per column tile
+    const int fpt = p.gemm_n / 8;                  // column groups per column tile
     const long long L1 = L + 1;
     std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
     long long lam_f = 0, lam_a = 0, gsz = 0;
@@ -496,7 +496,7 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
     if (L > 1023) return FAVEST_EUNSUPPORTED;
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
-    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64) return FAVEST_EINVAL;
+    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64 && io_type != FAVEST_IO_R32) return FAVEST_EINVAL;
     if ((cos_theta == nullptr) != (w_lat == nullptr)) return FAVEST_EINVAL;
     const int nlat = L + 1;
     if (cos_theta) {
@@ -508,7 +508,8 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
             if (j > 0 && !(cos_theta[j] < cos_theta[j - 1])) return FAVEST_EINVAL;
         }
     }
-    if (precision == FAVEST_BF16X6 && io_type != FAVEST_IO_C64) return FAVEST_EUNSUPPORTED;
+    if (precision == FAVEST_BF16X6 && io_type == FAVEST_IO_C128) return FAVEST_EUNSUPPORTED;
+    if (precision != FAVEST_BF16X6 && io_type == FAVEST_IO_R32) return FAVEST_EUNSUPPORTED;
 
     favest_plan_s *h = new (std::nothrow) favest_plan_s();
     if (!h) return FAVEST_ENOMEM;
@@ -518,6 +519,8 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     p.B = batch;
     p.precision = precision;
     p.io = io_type;
+    p.real = io_type == FAVEST_IO_R32;
+    p.ncg = p.real ? (batch + 1) / 2 : batch;
     p.nlat = nlat;
     p.nphi = 2 * (L + 1);
     p.J = (nlat + 1) / 2;
@@ -742,18 +745,24 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
     *flops = 0;
     *pipe = 0;
     if (p.precision == FAVEST_BF16X6) {
-        const double grid = 2.0 * B * nlat * nphi * 8.0;       // complex64 components
-        if (k == "fft_fwd") { *bytes = grid + J * B * L1 * 96.0; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
-        else if (k == "fft_inv") { *bytes = J * B * L1 * 64.0 + grid; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+        // G column groups of 8 (a complex field, or a pair of real fields); real fields
+        // are 4-byte values and keep KR = L(L+3)/2 coefficients per family
+        const double G = p.ncg;
+        const double grid = 2.0 * B * nlat * nphi * (p.real ? 4.0 : 8.0);
+        const double coef = 2.0 * B * (p.real ? (double)p.L * (p.L + 3) / 2.0 : K) * 8.0;
+        const double kc = p.real ? (double)p.L * (p.L + 3) / 2.0 : K;
+        const double fftf = 2.0 * G * nlat * 5.0 * nphi * std::log2(nphi);
+        if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 96.0; *flops = fftf; }
+        else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
         else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = steps * 6.0; *flops = steps * 4.0; *pipe = 1; }
-        else if (k == "tc_gemm_fwd") { *bytes = steps * 6.0 + J * B * L1 * 96.0 + rows * B * 32.0; *flops = 12.0 * steps * 8.0 * B; }
-        else if (k == "tc_gemm_adj") { *bytes = steps * 6.0 + rows * B * 48.0 + J * B * L1 * 64.0; *flops = 12.0 * steps * 8.0 * B; }
-        else if (k == "combine") { *bytes = rows * B * 32.0 + 2.0 * B * K * 8.0; *flops = 16.0 * B * K; }
-        else if (k == "uncombine") { *bytes = 2.0 * B * K * 8.0 + rows * B * 48.0; *flops = 24.0 * B * K; }
+        else if (k == "tc_gemm_fwd") { *bytes = steps * 6.0 + J * G * L1 * 96.0 + rows * G * 32.0; *flops = 12.0 * steps * 8.0 * G; }
+        else if (k == "tc_gemm_adj") { *bytes = steps * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * steps * 8.0 * G; }
+        else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }
+        else if (k == "uncombine") { *bytes = coef + rows * G * 48.0; *flops = 24.0 * B * kc; }
         else if (k == "polar_patch") {
             const double jc = p.pol_jc, mc = p.pol_muc;
-            *bytes = jc * L1 * mc * 8.0 + 2.0 * B * L * 2.0 * mc * 8.0 + jc * B * mc * 64.0;
-            *flops = jc * mc * L * B * 32.0;
+            *bytes = jc * L1 * mc * 8.0 + 2.0 * B * L * (p.real ? 1.0 : 2.0) * mc * 8.0 + jc * G * mc * 64.0;
+            *flops = jc * mc * L * G * 32.0;
             *pipe = 3;
         } else return FAVEST_EINVAL;
         return FAVEST_OK;

@@ -73,6 +73,12 @@ struct __align__(64) GemmGroup {
 
 struct Plan {
     int L = 0, B = 0, precision = 0, io = 0;
+    // real fields (FAVEST_IO_R32): orders m >= 0 only; the tensor-core stages see one
+    // column group of 8 per PAIR of fields (columns c*4 + f*2 + re/im, f = field in the
+    // pair) where complex fields take one group each (columns c*4 + s*2 + re/im, s = sign
+    // of m)
+    int real = 0;
+    int ncg = 0;              // column groups: B (complex) or ceil(B / 2) (real)
     int nlat = 0, nphi = 0, J = 0, has_eq = 0;
     int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
     int ct = 0, ng = 0;       // FP64 column group width and count
@@ -103,17 +109,17 @@ struct Plan {
 
     // split-precision (BF16X6) path
     int JP = 0;               // folded latitudes padded to a multiple of 128
-    int gemm_n = 128;         // GEMM tile width: 256 columns (32 fields) or 128 (16 fields)
-    int ncolr = 0;            // columns per order: 8 per field, padded to gemm_n
+    int gemm_n = 128;         // GEMM tile width: 256 columns (32 groups) or 128 (16 groups)
+    int ncolr = 0;            // columns per order: 8 per column group, padded to gemm_n
     int n_tiles = 0;          // ncolr / gemm_n
     int nk_f = 0;             // forward K-chunks: JP / kGemmChunkK
     int n_items_f = 0, n_items_a = 0;
     void *d_lam = nullptr;        // Legendre operand tiles (bf16 x 3)
     void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
-    float *d_Q32 = nullptr;       // forward GEMM output [field][l][mu][8]
-    float *d_S32 = nullptr;       // adjoint GEMM output [JP][field][mu][parity][8]
-    int nf = 0;                   // fields padded to a multiple of gemm_n / 8 (ncolr / 8)
+    float *d_Q32 = nullptr;       // forward GEMM output [group][l][mu][8]
+    float *d_S32 = nullptr;       // adjoint GEMM output [group][JP/4][mu][parity][4][8]
+    int nf = 0;                   // column groups padded to a multiple of gemm_n / 8 (ncolr / 8)
     // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
     // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
     CUtensorMap tmap_lam, tmap_fb, tmap_gb;

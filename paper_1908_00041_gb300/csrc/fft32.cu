@@ -1,6 +1,6 @@
 // Longitude DFT stage of the split-precision path (FP32 arithmetic, FP64-derived
 // twiddles rounded to FP32).  One CTA per (field b, folded latitude j) handles the four
-// rings theta/phi x (j, nlat-1-j):
+// rings theta/phi x (j, nlat-1-j) (real fields: see k_rfft_fwd_bf16):
 //   forward: T -> FFT -> weighted equatorial fold F+- = omega_j (F_j +- F_j') -> three
 //            bf16 pieces written straight into the tensor-core B-operand layout.
 //   inverse: gathers the even/odd Legendre sums E, O of every order, forms
@@ -400,6 +400,211 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Real fields.  A real field's two components are packed into one complex ring
+// z = T_th + i T_ph, whose spectrum Z gives both component spectra (T_th, T_ph real):
+//   F_th(m) = (Z(m) + conj Z(-m)) / 2,   F_ph(m) = (Z(m) - conj Z(-m)) / (2 i),
+// of which only m >= 0 is kept (F(-m) = conj F(m)).  One CTA takes the fields 2q and
+// 2q+1 at the folded latitude pair (j, nlat-1-j): four complex rings, the same shared
+// memory and transform count as one complex field.  The B-operand record of the pair
+// holds columns c*4 + f*2 + (re, im) for component c and field f of the pair, at +mu.
+// Rows are read with float4 loads when nphi is a power of two (rows are then 16-byte
+// aligned) and float2 loads otherwise.
+// ---------------------------------------------------------------------------
+template <int V>
+__device__ __forceinline__ void load_v(const float *p, float (&v)[V])
+{
+    if constexpr (V == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_v(float *p, const float (&v)[V])
+{
+    if constexpr (V == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// grid: ceil(B / 2) * J CTAs (pair-major); shared as for the complex kernel
+template <int LOG2N>
+__global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
+    const float *__restrict__ Tth, const float *__restrict__ Tph, unsigned char *__restrict__ Fb,
+    RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
+    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B)
+{
+    extern __shared__ float4 sm_r4[];
+    float2 *buf = reinterpret_cast<float2 *>(sm_r4);
+    constexpr int V = LOG2N > 0 ? 4 : 2;
+    constexpr int kU = kLoadBatch / 2;             // vector pairs (th, ph) in flight per thread
+    const int n = rp.n;
+    const int q = blockIdx.x / J, j = blockIdx.x % J;
+    const bool eq = has_eq && j == J - 1;
+    const int nr = eq ? 2 : 4;    // rings: (2q, j), (2q+1, j), (2q, j'), (2q+1, j')
+    const int jm = nlat - 1 - j;
+    const int nv = n / V;
+    for (int i0 = threadIdx.x; i0 < nr * nv; i0 += kU * kFftThreads) {
+        float th[kU][V], ph[kU][V];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = i0 + u * kFftThreads;
+#pragma unroll
+            for (int i = 0; i < V; ++i) th[u][i] = ph[u][i] = 0.f;
+            if (idx < nr * nv) {
+                const int ring = idx / nv, kv = idx % nv;
+                const int bf = 2 * q + (ring & 1);
+                if (bf < B) {
+                    const size_t off = ((size_t)bf * nlat + (ring < 2 ? j : jm)) * n + (size_t)kv * V;
+                    load_v<V>(Tth + off, th[u]);
+                    load_v<V>(Tph + off, ph[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = i0 + u * kFftThreads;
+            if (idx < nr * nv) {
+                const int ring = idx / nv, kv = idx % nv;
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const int e = ring * n + kv * V + i;
+                    buf[LOG2N > 0 ? padi(e) : e] = make_float2(th[u][i], ph[u][i]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
+    else dif_f32<false>(buf, tw, rp, nr);
+    const float w = 0.5f * (float)omega[j];      // the 1/2 of the component split folded in
+    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
+    for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
+        const int bp = mu, bm = mu == 0 ? 0 : n - mu;
+        const int pp = LOG2N > 0 ? bp : __ldg(perm + bp), pm = LOG2N > 0 ? bm : __ldg(perm + bm);
+        float vp[8], vm[8];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const int e0 = f * n + pp, e1 = f * n + pm, e2 = (2 + f) * n + pp, e3 = (2 + f) * n + pm;
+            const float2 a = buf[LOG2N > 0 ? padi(e0) : e0], a2 = buf[LOG2N > 0 ? padi(e1) : e1];
+            const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e2) : e2];
+            const float2 z2 = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e3) : e3];
+            // 2 F_th = Z(m) + conj Z(-m), 2 F_ph = -i (Z(m) - conj Z(-m)), rings j and j'
+            const float tjx = a.x + a2.x, tjy = a.y - a2.y, pjx = a.y + a2.y, pjy = a2.x - a.x;
+            const float tkx = z.x + z2.x, tky = z.y - z2.y, pkx = z.y + z2.y, pky = z2.x - z.x;
+            vp[f * 2] = w * (tjx + tkx);
+            vp[f * 2 + 1] = w * (tjy + tky);
+            vp[4 + f * 2] = w * (pjx + pkx);
+            vp[4 + f * 2 + 1] = w * (pjy + pky);
+            vm[f * 2] = eq ? 0.f : w * (tjx - tkx);
+            vm[f * 2 + 1] = eq ? 0.f : w * (tjy - tky);
+            vm[4 + f * 2] = eq ? 0.f : w * (pjx - pkx);
+            vm[4 + f * 2 + 1] = eq ? 0.f : w * (pjy - pky);
+        }
+        unsigned char *dp = dst_base + (size_t)mu * 96;
+        store_row3(dp, vp, 16);
+        store_row3(dp + 48, vm, 16);
+    }
+}
+
+// Real fields, inverse: for field f of the pair, the spectrum of z = T_th + i T_ph is
+//   Z(m) = G_th(m) + i G_ph(m),  Z(-m) = conj G_th(m) + i conj G_ph(m)   (m >= 1),
+//   Z(0) = Re G_th(0) + i Re G_ph(0),
+// so one inverse transform per field and ring yields both real components.
+template <int LOG2N>
+__global__ void __launch_bounds__(kFftThreads, 3) k_rfft_inv_bf16(
+    const float *__restrict__ S32, float *__restrict__ Tth, float *__restrict__ Tph, RadixPlanArg rp,
+    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
+    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP, int B)
+{
+    extern __shared__ float4 sm_s4[];
+    float2 *buf = reinterpret_cast<float2 *>(sm_s4);
+    constexpr int V = LOG2N > 0 ? 4 : 2;
+    const int n = rp.n;
+    const int q = blockIdx.x / J, j = blockIdx.x % J;
+    const bool eq = has_eq && j == J - 1;
+    const int nr = eq ? 2 : 4;
+    const double wj = wring ? wring[j] : 1.0;
+    const float is = (float)(wj / sj[j]);
+    const float w0 = (float)wj;
+    if (LOG2N > 0) {
+        if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
+    } else {
+        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += 2 * blockDim.x) {
+        float4 ld[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu <= L) {
+                const float4 *e = reinterpret_cast<const float4 *>(
+                    S32 + ((((size_t)q * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
+                const float4 *o = e + 8;
+                ld[h][0] = __ldg(e);
+                ld[h][1] = __ldg(e + 1);
+                ld[h][2] = __ldg(o);
+                ld[h][3] = __ldg(o + 1);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu > L) break;
+            const float sc = mu == 0 ? w0 : is;
+            const float ev[8] = {ld[h][0].x, ld[h][0].y, ld[h][0].z, ld[h][0].w,
+                                 ld[h][1].x, ld[h][1].y, ld[h][1].z, ld[h][1].w};
+            const float ov[8] = {ld[h][2].x, ld[h][2].y, ld[h][2].z, ld[h][2].w,
+                                 ld[h][3].x, ld[h][3].y, ld[h][3].z, ld[h][3].w};
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 1 && eq) continue;
+                    const float sg = side ? -1.f : 1.f;   // ring j: E + O, ring j': E - O
+                    const int kt = f * 2, kp = 4 + f * 2;
+                    const float gtx = (ev[kt] + sg * ov[kt]) * sc, gty = (ev[kt + 1] + sg * ov[kt + 1]) * sc;
+                    const float gpx = (ev[kp] + sg * ov[kp]) * sc, gpy = (ev[kp + 1] + sg * ov[kp + 1]) * sc;
+                    const int rb = (2 * side + f) * n;
+                    if (mu == 0) {
+                        buf[LOG2N > 0 ? padi(rb) : rb] = make_float2(gtx, gpx);
+                    } else {
+                        const int i0 = rb + mu, i1 = rb + n - mu;
+                        buf[LOG2N > 0 ? padi(i0) : i0] = make_float2(gtx - gpy, gty + gpx);
+                        buf[LOG2N > 0 ? padi(i1) : i1] = make_float2(gtx + gpy, gpx - gty);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if constexpr (LOG2N > 0) fft_p2<LOG2N, true>(buf, tw, nr);
+    else dif_f32<true>(buf, tw, rp, nr);
+    const int jm = nlat - 1 - j;
+    const int nv = n / V;
+    for (int idx = threadIdx.x; idx < nr * nv; idx += blockDim.x) {
+        const int ring = idx / nv, kv = idx % nv;
+        const int bf = 2 * q + (ring & 1);
+        if (bf >= B) continue;
+        float th[V], ph[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int k = kv * V + i;
+            const int e = ring * n + (LOG2N > 0 ? k : __ldg(perm + k));
+            const float2 z = buf[LOG2N > 0 ? padi(e) : e];
+            th[i] = z.x;
+            ph[i] = z.y;
+        }
+        const size_t off = ((size_t)bf * nlat + (ring < 2 ? j : jm)) * n + (size_t)kv * V;
+        store_v<V>(Tth + off, th);
+        store_v<V>(Tph + off, ph);
+    }
+}
+
 }  // namespace
 
 template <int LOG2N>
@@ -408,6 +613,15 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
     RadixPlanArg rp = make_radix_arg(p.fft);
     const int ne = 4 * p.nphi;
     const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    if (p.real) {
+        auto k = k_rfft_fwd_bf16<LOG2N>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)Tth, (const float *)Tph, (unsigned char *)p.d_Fb,
+                                                 rp, p.fft.tw32, p.d_perm,
+                                                 p.unit_weights ? p.d_omega_unit : p.d_omega, p.L, p.nlat, p.J,
+                                                 p.has_eq, p.nf, p.B);
+        return cudaGetLastError();
+    }
     auto k = k_fft_fwd_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, rp,
@@ -422,6 +636,15 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
     RadixPlanArg rp = make_radix_arg(p.fft);
     const int ne = 4 * p.nphi;
     const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    if (p.real) {
+        auto k = k_rfft_inv_bf16<LOG2N>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float *)Tth, (float *)Tph, rp,
+                                                 p.fft.tw32, p.d_perm, p.d_sin,
+                                                 p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
+                                                 p.has_eq, p.JP, p.B);
+        return cudaGetLastError();
+    }
     auto k = k_fft_inv_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,

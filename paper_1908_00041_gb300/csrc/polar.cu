@@ -20,8 +20,10 @@
 //
 // Only the theta/phi structure of the combine stage and the E/O parity split of the
 // folded grid are used; the output goes to the same buffer S32 the GEMM writes,
-//   S32[field][JP/4][mu][parity][4][8], columns c*4 + s*2 + (re, im): c = theta/phi,
-//   s = 0: m = +mu, s = 1: m = -mu (with the factor (-1)^mu of lambda^{-mu}).
+//   S32[group][JP/4][mu][parity][4][8], columns c*4 + s*2 + (re, im): c = theta/phi,
+//   s = 0: m = +mu, s = 1: m = -mu (with the factor (-1)^mu of lambda^{-mu}); for real
+//   fields (REAL = true) slot s holds field 2q + s of the pair q at m = +mu, with the
+//   half-spectrum coefficients (index l(l+1)/2 - 1 + mu of a field's K).
 #include <cmath>
 #include <vector>
 
@@ -53,10 +55,11 @@ constexpr int kPolarWarps = 8;       // warps per CTA, each over its own range o
 // order through shared memory (a plain FP32 running sum over ~L terms would lose about
 // sqrt(L) ulps).  Orders beyond the ring group's turning-point bound keep the tensor-core
 // values.
+template <bool REAL>
 __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
     const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
-    const long long *__restrict__ coff)
+    const long long *__restrict__ coff, int B)
 {
     __shared__ float part[kPolarWarps][kPolarJ * 16][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -68,9 +71,10 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const int mulim = (int)ceil(1.5 * (L + 1) * sin_j[jlast]) + 16;
     if (mu0 >= mulim) return;                          // uniform over the CTA
     const bool active = mu >= 1 && mu <= L && mu < muc;
-    const size_t cb = coff ? (size_t)coff[f] : (size_t)f * K;
+    const size_t cb = REAL ? (size_t)(2 * f) * K : coff ? (size_t)coff[f] : (size_t)f * K;
     const float2 *af = a + cb;
     const float2 *bf = b + cb;
+    const bool has1 = !REAL || 2 * f + 1 < B;       // the pair's second field exists
     const float w = (float)mu;
     float sum[kPolarJ][2][8], cmp[kPolarJ][2][8];
 #pragma unroll
@@ -96,14 +100,27 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
         for (int h = 0; h < kPolarChunk; ++h) {
             const int l = lc + h;
             if (l < mu || l > L) continue;
-            const size_t c0 = (size_t)l * l + l - 1;
-            const float2 ap = af[c0 + mu], am = af[c0 - mu], bp = bf[c0 + mu], bm = bf[c0 - mu];
+            float2 ap, am, bp, bm;
+            if (REAL) {
+                const size_t c0 = (size_t)l * (l + 1) / 2 - 1 + mu;
+                ap = af[c0];
+                bp = bf[c0];
+                am = has1 ? af[K + c0] : make_float2(0.f, 0.f);
+                bm = has1 ? bf[K + c0] : make_float2(0.f, 0.f);
+            } else {
+                const size_t c0 = (size_t)l * l + l - 1;
+                ap = af[c0 + mu];
+                am = af[c0 - mu];
+                bp = bf[c0 + mu];
+                bm = bf[c0 - mu];
+            }
             const int kd = (h & 1) ? 0 : 1, kl = (h & 1) ? 1 : 0;   // banks of the D and Lambda terms
 #pragma unroll
             for (int q = 0; q < kPolarJ; ++q) {
                 if (j0 + q >= jc) break;
                 const float2 t = tab[((size_t)(j0 + q) * (L + 1) + l) * muc + mu];
                 const float D = t.x, wl = w * t.y;
+                const float wl1 = REAL ? wl : -wl;      // m of slot 1: +mu (real) or -mu
                 float *ad = acc[q][kd], *al = acc[q][kl];
                 ad[0] = fmaf(ap.x, D, ad[0]);
                 ad[1] = fmaf(ap.y, D, ad[1]);
@@ -116,12 +133,12 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
                 // theta: -i m b Lambda ; phi: +i m a Lambda  (m = +mu for s = 0, -mu for s = 1)
                 al[0] = fmaf(wl, bp.y, al[0]);
                 al[1] = fmaf(-wl, bp.x, al[1]);
-                al[2] = fmaf(-wl, bm.y, al[2]);
-                al[3] = fmaf(wl, bm.x, al[3]);
+                al[2] = fmaf(wl1, bm.y, al[2]);
+                al[3] = fmaf(-wl1, bm.x, al[3]);
                 al[4] = fmaf(-wl, ap.y, al[4]);
                 al[5] = fmaf(wl, ap.x, al[5]);
-                al[6] = fmaf(wl, am.y, al[6]);
-                al[7] = fmaf(-wl, am.x, al[7]);
+                al[6] = fmaf(-wl1, am.y, al[6]);
+                al[7] = fmaf(wl1, am.x, al[7]);
             }
         }
 #pragma unroll
@@ -162,7 +179,7 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
         }
         if (active && j0 + q < jc) {
             const int par = k ^ (mu & 1);
-            const float sg = (mu & 1) ? -1.f : 1.f;     // columns of m = -mu
+            const float sg = (!REAL && (mu & 1)) ? -1.f : 1.f;     // columns of m = -mu
             const int j = j0 + q;
             float *dst = S32 + ((((size_t)f * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2 + par) * 32 + (j & 3) * 8 + c4;
             *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
@@ -243,10 +260,11 @@ int build_polar_tables(Plan &p)
 
 cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s)
 {
-    const int K = p.L * p.L + 2 * p.L;
-    dim3 grid(p.pol_muc / 32, p.B, (p.pol_jc + kPolarJ - 1) / kPolarJ);
-    k_polar_patch<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin,
-                                                    p.d_S32, p.L, K, p.pol_jc, p.pol_muc, p.JP, p.d_coff);
+    const int K = p.real ? p.L * (p.L + 3) / 2 : p.L * p.L + 2 * p.L;
+    dim3 grid(p.pol_muc / 32, p.ncg, (p.pol_jc + kPolarJ - 1) / kPolarJ);
+    auto k = p.real ? k_polar_patch<true> : k_polar_patch<false>;
+    k<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin, p.d_S32, p.L, K,
+                                        p.pol_jc, p.pol_muc, p.JP, p.d_coff, p.B);
     return cudaGetLastError();
 }
 

@@ -51,3 +51,30 @@ def grid_field(L, batch, seed):
 def mask(L, seed_rng):
     """Positive latitude-longitude mask g ~ U[0.5, 1.5] on the grid."""
     return seed_rng.uniform(0.5, 1.5, (L + 1, 2 * (L + 1)))
+
+
+def real_grid_field(L, batch, seed):
+    """Random real tangent field components on the (L+1) x 2(L+1) grid: float64
+    [batch, L+1, 2(L+1)] each, i.i.d. standard normal (theta plane drawn first)."""
+    rng = np.random.default_rng(seed)
+    shape = (batch, L + 1, 2 * (L + 1))
+    return rng.standard_normal(shape), rng.standard_normal(shape)
+
+
+def half_coefficients(L, batch, seed, decay=1.0, rng=None):
+    """Coefficients of real fields, orders m >= 0 only: complex128 [batch, L(L+3)/2],
+    l-major (l = 1..L, m = 0..l); per field a then b, (re, im) i.i.d. standard normal
+    times (l+1)^-decay, with the imaginary part of every m = 0 entry set to zero."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    KR = L * (L + 3) // 2
+    deg = np.concatenate([np.full(l + 1, l) for l in range(1, L + 1)])
+    m0 = np.concatenate([np.arange(l + 1) == 0 for l in range(1, L + 1)])
+    s = (deg + 1.0) ** (-float(decay))
+    a = np.empty((batch, KR), np.complex128)
+    b = np.empty((batch, KR), np.complex128)
+    for f in range(batch):
+        for arr in (a, b):
+            z = rng.standard_normal((KR, 2))
+            z[m0, 1] = 0.0
+            arr[f] = (z[:, 0] + 1j * z[:, 1]) * s
+    return a, b

@@ -35,3 +35,33 @@ def sample_coefs(L, n, rng):
         out.add((l, m))
     out = sorted(out)
     return np.array([p[0] for p in out]), np.array([p[1] for p in out])
+
+
+def hidx(l, m):
+    """Position of (l, m >= 0) in a half-spectrum (real-field) coefficient array."""
+    return l * (l + 1) // 2 - 1 + m
+
+
+def _half_positions(L):
+    ls = np.concatenate([np.full(l + 1, l) for l in range(1, L + 1)])
+    ms = np.concatenate([np.arange(l + 1) for l in range(1, L + 1)])
+    return ls, ms
+
+
+def half_of_full(c, L):
+    """The m >= 0 entries of full l-major coefficient arrays [..., L^2+2L]."""
+    ls, ms = _half_positions(L)
+    return np.asarray(c)[..., cidx(ls, ms)]
+
+
+def full_of_half(c, L):
+    """Hermitian extension c_{l,-m} = (-1)^m conj(c_lm) of half-spectrum arrays
+    [..., L(L+3)/2] to full l-major arrays [..., L^2+2L]."""
+    c = np.asarray(c)
+    ls, ms = _half_positions(L)
+    out = np.zeros(c.shape[:-1] + (L * L + 2 * L,), np.result_type(c, np.complex64))
+    out[..., cidx(ls, ms)] = c
+    pos = ms > 0
+    sg = np.where(ms[pos] % 2 == 1, -1.0, 1.0)
+    out[..., cidx(ls[pos], -ms[pos])] = sg * np.conj(c[..., pos])
+    return out
