@@ -304,10 +304,10 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
             const Plan &p = gp->p;
             const int g0 = (int)gg.size();
             GemmGroup f, a;
-            f.tmap_a = p.tmap_lam;
+            f.tmap_a = p.tmap_lam_f;
             f.tmap_b = p.tmap_fb;
             f.out = p.d_Q32;
-            a.tmap_a = p.tmap_lam;
+            a.tmap_a = p.tmap_lam_a;
             a.tmap_b = p.tmap_gb;
             a.out = p.d_S32;
             gg.push_back(f);

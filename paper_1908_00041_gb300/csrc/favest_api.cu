@@ -106,7 +106,8 @@ cudaError_t upload(T **p, const std::vector<T> &h)
 void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
-                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
+                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam_f, p.d_lam_a, p.d_Fb, p.d_gb,
+                    p.d_jcmin,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups};
     for (void *q : ptrs)
@@ -262,6 +263,52 @@ int make_row_tensor_map(void *base, size_t bytes, int box_rows, CUtensorMap *out
     return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
 }
 
+// Turning-point bounds of the split path.  Below its turning point (sin theta <
+// mu / (l + 1/2)) lambda_l^mu(theta) decays exponentially towards the pole, and far below
+// it the values are smaller than any FP32 rounding of the sums they enter.  For every
+// order mu and folded latitude j this returns the first degree l >= mu at which
+// |lambda_l^mu(theta_j)| (orthonormal) reaches kTurnEps, or L + 2 if no l <= L + 1 does.
+// The values are run on a mantissa with a separate (logarithmic) exponent, so that the
+// polar starting values far below the double range are handled exactly.  Every
+// (l, mu, j) left out by the generator and the GEMM item ranges lies below this bound,
+// i.e. is smaller than kTurnEps in magnitude.
+constexpr double kTurnEps = 1e-13;
+
+std::vector<int> turning_bounds(const Plan &p)
+{
+    const int L = p.L, J = p.J;
+    std::vector<int> lf((size_t)(L + 1) * J, L + 2);
+    const double leps = std::log(kTurnEps);
+    const double lbig = std::log(0x1p200);
+    double lcmu = 0.5 * std::log(1.0 / (4.0 * 3.14159265358979323846));   // log c_mu
+    std::vector<double> eps(L + 3);
+    for (int mu = 0; mu <= L; ++mu) {
+        if (mu > 0) lcmu += 0.5 * std::log((2.0 * mu + 1.0) / (2.0 * mu));
+        for (int l = mu; l <= L + 2; ++l) eps[l] = eps_lm(l, mu);
+        for (int j = 0; j < J; ++j) {
+            const double x = p.h_x[j], sn = std::sqrt((1.0 - x) * (1.0 + x));
+            // lambda_l = y * exp(e), starting from lambda_mu^mu = (-1)^mu c_mu sin^mu (sign dropped)
+            double y = 1.0, ym = 0.0, e = lcmu + mu * std::log(sn);
+            double thr = std::exp(leps - e);       // |y| >= thr  <=>  |lambda| >= kTurnEps
+            int l = mu;
+            while (l <= L + 1 && !(std::fabs(y) >= thr)) {
+                const double yn = (x * y - eps[l] * ym) / eps[l + 1];
+                ym = y;
+                y = yn;
+                ++l;
+                if (std::fabs(y) > 0x1p200) {
+                    y *= 0x1p-200;
+                    ym *= 0x1p-200;
+                    e += lbig;
+                    thr = std::exp(leps - e);
+                }
+            }
+            lf[(size_t)mu * J + j] = l;
+        }
+    }
+    return lf;
+}
+
 // Split-precision path: operand tile offsets, GEMM work items, buffers.
 //   Lam (A operands): contiguous 24 KB chunks (three 8 KB bf16 pieces of 128 x 32), bulk copies
 //   Fb  (forward B):  [JP/8][nf][8][L+1][2][3][8] bf16, gathered by a 5-D TMA box
@@ -288,6 +335,20 @@ int alloc_workspace_bf16(Plan &p)
     const int fpt = p.gemm_n / 8;                  // column groups per column tile
     const long long L1 = L + 1;
     std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
+    const int J = p.J;
+    const std::vector<int> lf = turning_bounds(p);
+    // generator: first latitude per order, rounded down to a K-chunk of 32
+    std::vector<int> jcmin(L + 1);
+    p.gen_values = 0;
+    for (int mu = 0; mu <= L; ++mu) {
+        int jmin = J;
+        for (int j = 0; j < J; ++j)
+            if (lf[(size_t)mu * J + j] <= L + 1) { jmin = j; break; }
+        const int jc = jmin / KC * KC, jlast = (J - 1) / KC * KC;
+        jcmin[mu] = jc < jlast ? jc : jlast;
+        p.gen_values += (double)(L + 2 - mu) * (J - jcmin[mu]);
+    }
+    p.gemm_pairs_f = p.gemm_pairs_a = 0;
     long long lam_f = 0, lam_a = 0, gsz = 0;
     std::vector<TcItem> itf, ita;
     auto nrow_p = [&](int mu, int par) { const int n = L + 2 - mu; return par ? n / 2 : (n + 1) / 2; };
@@ -312,53 +373,82 @@ int alloc_workspace_bf16(Plan &p)
             const int idx = mu * 2 + par;
             const int np = nrow_p(mu, par);
             const int mt = (np + 127) / 128;
-            for (int m = 0; m < mt; ++m)
+            for (int m = 0; m < mt; ++m) {
+                // first latitude chunk holding a value above the bound for a row of the tile
+                const int rhi = (128 * m + 127 < np - 1) ? 128 * m + 127 : np - 1;
+                const int lhi = mu + par + 2 * rhi;
+                int kc0 = p.nk_f - 1;
+                for (int c = 0; c < p.nk_f - 1 && kc0 == p.nk_f - 1; ++c)
+                    for (int j = c * KC; j < (c + 1) * KC && j < J; ++j)
+                        if (lf[(size_t)mu * J + j] <= lhi) { kc0 = c; break; }
+                const int trows = np - 128 * m < 128 ? np - 128 * m : 128;
+                p.gemm_pairs_f += (double)trows * (J - kc0 * KC > 0 ? J - kc0 * KC : 0);
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_f[idx] + (long long)m * p.nk_f * CHA;
+                    I.a_off = off_f[idx] + ((long long)m * p.nk_f + kc0) * CHA;
                     I.a_stride = (int)CHA;
                     I.b_box = 1;
                     I.bx = par * 3 * 8;
                     I.by = fpt * nt;
                     I.bw = mu;
+                    I.bk = kc0;
                     // rows of (mu, par) are consecutive in Q32 (see the layout note above)
                     const long long qrow = tab_off(L, mu) + (par ? nrow_p(mu, 0) : 0) + 128LL * m;
                     I.out_off = ((long long)fpt * nt * p.ntab + qrow) * 8;
                     I.out_ld = 32;
                     I.col_gs = p.ntab * 8;
-                    I.nk = p.nk_f;
-                    I.rows = np - 128 * m < 128 ? np - 128 * m : 128;
+                    I.nk = p.nk_f - kc0;
+                    I.rows = trows;
                     I.group = 0;
                     itf.push_back(I);
                 }
+            }
             const int amu = mu == 0 ? 1 : mu;
-            const int nka = (nrow_p(amu, par) + KC - 1) / KC;
-            for (int t = 0; t < p.JP / 128; ++t)
+            const int npa = nrow_p(amu, par);
+            const int nka = (npa + KC - 1) / KC;
+            for (int t = 0; t < p.JP / 128; ++t) {
+                // first row chunk (rows l = amu + par + 2 r) reaching the tile's lowest bound
+                int lmin = L + 2;
+                for (int j = 128 * t; j < 128 * t + 128 && j < J; ++j) {
+                    const int v = lf[(size_t)amu * J + j];
+                    lmin = v < lmin ? v : lmin;
+                }
+                int kc0 = nka - 1;
+                for (int c = 0; c < nka - 1; ++c)
+                    if (amu + par + 2 * (KC * c + KC - 1) >= lmin) { kc0 = c; break; }
+                const int tl = J - 128 * t < 128 ? J - 128 * t : 128;
+                p.gemm_pairs_a += (double)(tl > 0 ? tl : 0) * (npa - KC * kc0);
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_a[amu * 2 + par] + (long long)t * nka * CHA;
-                    I.b_off = off_g[idx] + (long long)nt * nka * CHB;
+                    I.a_off = off_a[amu * 2 + par] + ((long long)t * nka + kc0) * CHA;
+                    I.b_off = off_g[idx] + ((long long)nt * nka + kc0) * CHB;
                     I.a_stride = (int)CHA;
                     I.b_stride = (int)CHB;
                     I.out_off = ((((long long)fpt * nt * (p.JP / 4) + 32LL * t) * L1 + mu) * 2 + par) * 32;
                     I.out_ld = L1 * 2 * 32;
                     I.col_gs = (long long)(p.JP / 4) * L1 * 2 * 32;
-                    I.nk = nka;
+                    I.nk = nka - kc0;
                     I.rows = 128;
                     I.group = 1;
                     ita.push_back(I);
                 }
+            }
         }
     }
-    // heaviest items first (adjoint items differ in K depth)
+    // Heaviest adjoint items first (measured: better than keeping the latitude tiles of an
+    // order adjacent); the forward items keep (order, parity, row tile) order, so that the
+    // row tiles of one order, which read the same B operand, run at the same time on
+    // neighbouring CTAs and share it through L2 (measured: sorting them by K depth cost
+    // 30% of the forward GEMM's time).
     std::stable_sort(ita.begin(), ita.end(), [](const TcItem &x, const TcItem &y) { return x.nk > y.nk; });
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
-    const size_t lam_bytes = (size_t)(lam_f > lam_a ? lam_f : lam_a);
+    const size_t lamf_bytes = (size_t)lam_f, lama_bytes = (size_t)lam_a;
     const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 96;
     const size_t q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
     const size_t s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
-    if (cudaMalloc(&p.d_lam, lam_bytes) != cudaSuccess || cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
+    if (cudaMalloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || cudaMalloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
+        cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         cudaMalloc(&p.d_gb, (size_t)gsz) != cudaSuccess || cudaMalloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
@@ -366,27 +456,31 @@ int alloc_workspace_bf16(Plan &p)
         return FAVEST_ENOMEM;
     }
     // padded operand positions (latitudes >= J, fields >= B, rows beyond each order's
-    // range) must hold zeros; they are never written afterwards
-    if (cudaMemset(p.d_lam, 0, lam_bytes) != cudaSuccess || cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
+    // range) and the latitudes below each order's turning bound must hold zeros; they
+    // are never written afterwards
+    if (cudaMemset(p.d_lam_f, 0, lamf_bytes) != cudaSuccess || cudaMemset(p.d_lam_a, 0, lama_bytes) != cudaSuccess ||
+        cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
         cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess || cudaMemset(p.d_status, 0, sizeof(int)) != cudaSuccess)
         return FAVEST_ECUDA;
     cudaError_t e;
     if ((e = upload(&p.d_lam_off_f, off_f)) || (e = upload(&p.d_lam_off_a, off_a)) ||
-        (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)))
+        (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)) ||
+        (e = upload(&p.d_jcmin, jcmin)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
-    p.ws_bytes = lam_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
+    p.ws_bytes = lamf_bytes + lama_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
     const int pst = build_polar_tables(p);
     if (pst != FAVEST_OK) return pst;
     p.ws_bytes += (size_t)p.pol_jc * (L + 1) * p.pol_muc * sizeof(float2);
-    int st = make_row_tensor_map(p.d_lam, lam_bytes, (int)(CHA / 512), &p.tmap_lam);
+    int st = make_row_tensor_map(p.d_lam_f, lamf_bytes, (int)(CHA / 512), &p.tmap_lam_f);
+    if (st == FAVEST_OK) st = make_row_tensor_map(p.d_lam_a, lama_bytes, (int)(CHA / 512), &p.tmap_lam_a);
     if (st == FAVEST_OK) st = make_fb_tensor_map(p);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_gb, (size_t)gsz, (int)(CHB / 512), &p.tmap_gb);
     if (st != FAVEST_OK) return st;
     std::vector<GemmGroup> gg(2);
-    gg[0].tmap_a = p.tmap_lam;
+    gg[0].tmap_a = p.tmap_lam_f;
     gg[0].tmap_b = p.tmap_fb;
     gg[0].out = p.d_Q32;
-    gg[1].tmap_a = p.tmap_lam;
+    gg[1].tmap_a = p.tmap_lam_a;
     gg[1].tmap_b = p.tmap_gb;
     gg[1].out = p.d_S32;
     if ((e = upload(&p.d_ggroups, gg))) return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
@@ -752,11 +846,14 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         const double coef = 2.0 * B * (p.real ? (double)p.L * (p.L + 3) / 2.0 : K) * 8.0;
         const double kc = p.real ? (double)p.L * (p.L + 3) / 2.0 : K;
         const double fftf = 2.0 * G * nlat * 5.0 * nphi * std::log2(nphi);
+        // generator and GEMMs: the values and (row, latitude) pairs above the turning
+        // bound, i.e. the work these kernels are given (the rest is below 1e-13)
+        const double gv = p.gen_values, pf = p.gemm_pairs_f, pa = p.gemm_pairs_a;
         if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 96.0; *flops = fftf; }
         else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
-        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = steps * 6.0; *flops = steps * 4.0; *pipe = 1; }
-        else if (k == "tc_gemm_fwd") { *bytes = steps * 6.0 + J * G * L1 * 96.0 + rows * G * 32.0; *flops = 12.0 * steps * 8.0 * G; }
-        else if (k == "tc_gemm_adj") { *bytes = steps * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * steps * 8.0 * G; }
+        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; *pipe = 1; }
+        else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 96.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
+        else if (k == "tc_gemm_adj") { *bytes = pa * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * pa * 8.0 * G; }
         else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }
         else if (k == "uncombine") { *bytes = coef + rows * G * 48.0; *flops = 24.0 * B * kc; }
         else if (k == "polar_patch") {

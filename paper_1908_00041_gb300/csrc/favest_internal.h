@@ -47,7 +47,7 @@ constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk
 // chunk three bf16 pieces.  Chunk c of A starts a_off + c * a_stride bytes into the A
 // buffer (a multiple of 512: the TMA addresses the buffer as rows of 512 bytes); B
 // likewise (b_box = 0), or (b_box = 1) through the forward operand's 5-D tensor map at
-// coordinates (bx + 8 * piece, bw, 0, by, 4 * c).  Output row r (< rows) of field
+// coordinates (bx + 8 * piece, bw, 0, by, 4 * (bk + c)).  Output row r (< rows) of field
 // column group g (8 floats) is written at
 //   out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs.
 struct TcItem {
@@ -61,6 +61,7 @@ struct TcItem {
     int b_stride;       // bytes between consecutive B chunks
     int b_box;          // 1: B through the 5-D tensor map
     int bx, by, bw;     // 5-D box coordinates: x of piece 0, first field, order
+    int bk;             // 5-D box: first K-chunk (chunks below it are skipped)
     int group;          // index into the launch's GemmGroup array
 };
 
@@ -114,7 +115,13 @@ struct Plan {
     int n_tiles = 0;          // ncolr / gemm_n
     int nk_f = 0;             // forward K-chunks: JP / kGemmChunkK
     int n_items_f = 0, n_items_a = 0;
-    void *d_lam = nullptr;        // Legendre operand tiles (bf16 x 3)
+    // Legendre operand tiles (bf16 x 3), forward and adjoint layouts.  Both buffers are
+    // zeroed at plan creation; the generator never writes the latitudes below an
+    // order's turning bound (jc_min), which therefore stay zero.
+    void *d_lam_f = nullptr, *d_lam_a = nullptr;
+    int *d_jcmin = nullptr;       // [L+1] first latitude (multiple of 32) generated per order
+    double gen_values = 0;        // recurrence values generated per direction
+    double gemm_pairs_f = 0, gemm_pairs_a = 0;   // (row, latitude) pairs the GEMMs contract
     void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
     float *d_Q32 = nullptr;       // forward GEMM output [group][l][mu][8]
@@ -122,7 +129,7 @@ struct Plan {
     int nf = 0;                   // column groups padded to a multiple of gemm_n / 8 (ncolr / 8)
     // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
     // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
-    CUtensorMap tmap_lam, tmap_fb, tmap_gb;
+    CUtensorMap tmap_lam_f, tmap_lam_a, tmap_fb, tmap_gb;
     GemmGroup *d_ggroups = nullptr;   // [2]: forward (Lam, Fb, Q32), adjoint (Lam, g, S32)
     std::vector<TcItem> h_items_f, h_items_a;   // host copies (merged by ragged batches)
     int gen_lt = 128, gen_mb = 1;  // generator shape: latitudes per block, orders per thread

@@ -65,25 +65,25 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 // order groups in turn.  One thread runs the scaled FP64 recurrence of one (order,
 // latitude) over all rows l = mu..L+1 and packs, per parity, 8 consecutive rows into
 // one 16-byte core-matrix row per piece.  (lt, mb) is the block shape the autotuner
-// picks per degree.
+// picks per degree.  Latitudes below jc0 (the order's turning bound rounded down to a
+// K-chunk: every value there is below 1e-13) and padding latitudes are not generated;
+// their operand positions were zeroed when the plan was created.
 //   fwd = true : forward A layout, item (mu, p, m_tile) at lam_off[mu*2+p] + m_tile*nkf*48KB
 //   fwd = false: adjoint A layout, item (mu, p, j_tile) at lam_off[mu*2+p] + j_tile*nka*48KB
 template <bool FWD>
 __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const long long *__restrict__ lam_off,
                                           const double *__restrict__ xj, const double *__restrict__ sj,
                                           const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
-                                          int J, int JP, int mu, int j)
+                                          int J, int JP, int mu, int j, int jc0)
 {
     const int nrow = L + 2 - mu;
     const double *As = Atab + tab_off(L, mu);   // recurrence multipliers of this order
 
-    double x = 0.0, y1 = 0.0, y2 = 0.0;
+    if (j >= J || j < jc0) return;
+    double y1 = 0.0, y2 = 0.0;
     int c = 1 << 20;
-    const bool live = j < J;
-    if (live) {
-        x = xj[j];
-        sectoral_start(cmu[mu], sj[j], mu, y1, c);
-    }
+    const double x = xj[j];
+    sectoral_start(cmu[mu], sj[j], mu, y1, c);
     const int nk_f = JP / kChunkK;                 // forward K chunks (latitudes)
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
     const int nk_a0 = (nrow_p0 + kChunkK - 1) / kChunkK, nk_a1 = (nrow_p1 + kChunkK - 1) / kChunkK;
@@ -152,8 +152,8 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const
 template <bool FWD>
 __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
-    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
-    int J, int JP, int lt, int mb)
+    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
+    const int *__restrict__ jcmin, int L, int J, int JP, int lt, int mb)
 {
     const int olanes = kGenThreads / lt;
     const int jblocks = JP / lt;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     for (int k = 0; k < mb; ++k) {
         const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
         if (mu > L) break;
-        gen_order<FWD>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, j);
+        gen_order<FWD>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, j, __ldg(jcmin + mu));
     }
 }
 
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                     if (I.b_box) {
                         for (int q = 0; q < kPieces; ++q)
                             tc::tma_load_5d(S.b[stage] + q * kPieceB, tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
-                                            (kChunkK / 8) * c, &S.full[stage]);
+                                            (kChunkK / 8) * (I.bk + c), &S.full[stage]);
                     } else {
                         tc::tma_load_2d(S.b[stage], tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
                                         &S.full[stage]);
@@ -434,11 +434,11 @@ cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cud
     const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
     const int grid = (p.JP / lt) * ogroups;
     if (fwd)
-        k_gen_lambda<true><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam, p.d_lam_off_f, p.d_x, p.d_sin,
-                                                        p.d_cmu, p.d_A, p.L, p.J, p.JP, lt, mb);
+        k_gen_lambda<true><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f, p.d_x,
+                                                        p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
     else
-        k_gen_lambda<false><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam, p.d_lam_off_a, p.d_x, p.d_sin,
-                                                         p.d_cmu, p.d_A, p.L, p.J, p.JP, lt, mb);
+        k_gen_lambda<false><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x,
+                                                         p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
     return cudaGetLastError();
 }
 
