@@ -107,7 +107,7 @@ void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam_f, p.d_lam_a, p.d_Fb, p.d_gb,
-                    p.d_jcmin,
+                    p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups};
     for (void *q : ptrs)
@@ -172,8 +172,17 @@ int build_tables(Plan &p)
             R32[t] = (float)R[t];
         }
         for (int l = 1; l <= L; ++l) k1[l] = (float)(R[tab_off(L, 1) + (l - 1)] * std::sqrt((double)l * (l + 1.0)));
+        std::vector<float> om32(J), omu32(J);
+        std::vector<float2> isc(2 * J);
+        for (int j = 0; j < J; ++j) {
+            om32[j] = (float)om[j];
+            omu32[j] = (float)omu[j];
+            isc[j] = make_float2((float)(1.0 / s[j]), 1.0f);
+            isc[J + j] = make_float2((float)(wring[j] / s[j]), (float)wring[j]);
+        }
         if ((e = upload(&p.d_P32, P32)) || (e = upload(&p.d_M32, M32)) || (e = upload(&p.d_R32, R32)) ||
-            (e = upload(&p.d_k1, k1)))
+            (e = upload(&p.d_k1, k1)) || (e = upload(&p.d_omega32, om32)) ||
+            (e = upload(&p.d_omega_unit32, omu32)) || (e = upload(&p.d_isc32, isc)))
             return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     }
 

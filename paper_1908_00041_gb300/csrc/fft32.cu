@@ -245,7 +245,7 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const float2 *__restrict__ Tth, const float2 *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
-    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf,
+    const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf,
     const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_f4[];
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     __syncthreads();
     if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
     else dif_f32<false>(buf, tw, rp, nr);
-    const float w = (float)omega[j];
+    const float w = omega[j];
     // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 96;
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
@@ -315,12 +315,17 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
 }
 
 // grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
+// Inverse kernels: 2 blocks per SM.  At 3 (85 registers) the n = 2048 instantiation
+// spills about 128 bytes per thread (the first radix-16 stage); with the registers it
+// needs (111) the inverse DFT at L = 1023 runs in 0.79 ms instead of 1.05 ms (the forward
+// kernel does not gain and keeps 3).
+constexpr int kInvBlocksPerSm = 2;
+
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
+__global__ void __launch_bounds__(kFftThreads, kInvBlocksPerSm) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
-    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP,
-    const long long *__restrict__ toff)
+    const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
+    int nlat, int J, int has_eq, int JP, const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -329,10 +334,9 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_inv_bf16(
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;
     // 1/sin(theta_j), times the point weight of rings j and nlat-1-j (equal) for the
-    // weighted adjoint
-    const double wj = wring ? wring[j] : 1.0;
-    const float is = (float)(wj / sj[j]);
-    const float w0 = (float)wj;
+    // weighted adjoint (isc[j] = (scale, weight))
+    const float2 sc2 = __ldg(isc + j);
+    const float is = sc2.x, w0 = sc2.y;
     if (LOG2N > 0) {
         // every bin but n/2 is written below
         if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
@@ -435,7 +439,7 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
     const float *__restrict__ Tth, const float *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
-    const double *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B)
+    const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B)
 {
     extern __shared__ float4 sm_r4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_r4);
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
     __syncthreads();
     if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
     else dif_f32<false>(buf, tw, rp, nr);
-    const float w = 0.5f * (float)omega[j];      // the 1/2 of the component split folded in
+    const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
     for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
         const int bp = mu, bm = mu == 0 ? 0 : n - mu;
@@ -515,10 +519,10 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
 //   Z(0) = Re G_th(0) + i Re G_ph(0),
 // so one inverse transform per field and ring yields both real components.
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, 3) k_rfft_inv_bf16(
+__global__ void __launch_bounds__(kFftThreads, kInvBlocksPerSm) k_rfft_inv_bf16(
     const float *__restrict__ S32, float *__restrict__ Tth, float *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const int *__restrict__ perm, const double *__restrict__ sj,
-    const double *__restrict__ wring, int L, int nlat, int J, int has_eq, int JP, int B)
+    const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
+    int nlat, int J, int has_eq, int JP, int B)
 {
     extern __shared__ float4 sm_s4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_s4);
@@ -527,9 +531,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_inv_bf16(
     const int q = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;
-    const double wj = wring ? wring[j] : 1.0;
-    const float is = (float)(wj / sj[j]);
-    const float w0 = (float)wj;
+    const float2 sc2 = __ldg(isc + j);
+    const float is = sc2.x, w0 = sc2.y;
     if (LOG2N > 0) {
         if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
     } else {
@@ -618,14 +621,14 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)Tth, (const float *)Tph, (unsigned char *)p.d_Fb,
                                                  rp, p.fft.tw32, p.d_perm,
-                                                 p.unit_weights ? p.d_omega_unit : p.d_omega, p.L, p.nlat, p.J,
-                                                 p.has_eq, p.nf, p.B);
+                                                 p.unit_weights ? p.d_omega_unit32 : p.d_omega32, p.L, p.nlat,
+                                                 p.J, p.has_eq, p.nf, p.B);
         return cudaGetLastError();
     }
     auto k = k_fft_fwd_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, rp,
-                                   p.fft.tw32, p.d_perm, p.unit_weights ? p.d_omega_unit : p.d_omega, p.L,
+                                   p.fft.tw32, p.d_perm, p.unit_weights ? p.d_omega_unit32 : p.d_omega32, p.L,
                                    p.nlat, p.J, p.has_eq, p.nf, p.d_toff);
     return cudaGetLastError();
 }
@@ -640,15 +643,14 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
         auto k = k_rfft_inv_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float *)Tth, (float *)Tph, rp,
-                                                 p.fft.tw32, p.d_perm, p.d_sin,
-                                                 p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
-                                                 p.has_eq, p.JP, p.B);
+                                                 p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0),
+                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B);
         return cudaGetLastError();
     }
     auto k = k_fft_inv_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
-                                   p.d_perm, p.d_sin, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.J,
+                                   p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0), p.L, p.nlat, p.J,
                                    p.has_eq, p.JP, p.d_toff);
     return cudaGetLastError();
 }
