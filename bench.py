@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["bf16x6", "fp64"])
     ap.add_argument("--L", type=int, default=1023)
     ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default generator shape (profiling runs: no tuner launches)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -257,7 +259,61 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     # real fields (half-spectrum coefficients), L as the main workload, 32 and 64 fields
     for Br in (B, 2 * B):
         forms["real_fields_B%d" % Br] = measure_real(L, Br, stream)
+    forms["field_a_tables"] = measure_field_a()
     return forms
+
+
+def measure_field_a():
+    """Tangent Field A (Sec. 5.2), the paper's GL-row experiments on the FP64 path:
+    Table 1 (relative L2 error of AdjVSHT(FwdVSHT(T)), L = 10..150) and Table 2 (repeated
+    transforms at L = 40).  T0 is synthesised by the FP64 path from the field's exact
+    coefficients (tests/golden/field_a.txt, which also holds the paper's values; the GPU
+    test samples T0 with the oracle instead)."""
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api
+    coefs, t1, t2 = [], {}, None
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "field_a.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] in ("a", "b"):
+            coefs.append((line[0], int(line[1]), int(line[2]), float(line[3]) + 1j * float(line[4])))
+        elif line[0] == "table1":
+            t1[int(line[1])] = float(line[2])
+        elif line[0] == "table2":
+            t2 = [float(v) for v in line[2:]]
+
+    def exact(L):
+        a = torch.zeros((1, L * L + 2 * L), dtype=torch.complex128, device="cuda")
+        b = torch.zeros_like(a)
+        for fam, l, m, v in coefs:
+            (a if fam == "a" else b)[0, l * l + l + m - 1] = v
+        return a, b
+    out = {"T0": "synthesised from the exact coefficients by the FP64 path", "table1_gl": {}}
+    for L in sorted(t1):
+        p = api.Plan(L, 1, api.FAVEST_FP64, api.FAVEST_IO_C128)
+        x, W = api.favest_gl_grid(L + 1)
+        w = torch.as_tensor(np.repeat(W, 2 * (L + 1)) * (np.pi / (L + 1))).cuda()
+        tt, tp = p.adj(*exact(L))
+        rt, rp = p.adj(*p.fwd(tt, tp))
+        num = (w * ((rt - tt).abs() ** 2 + (rp - tp).abs() ** 2).reshape(-1)).sum()
+        den = (w * (tt.abs() ** 2 + tp.abs() ** 2).reshape(-1)).sum()
+        out["table1_gl"][str(L)] = {"fp64": float(torch.sqrt(num / den)), "paper": t1[L]}
+        p.close()
+    p = api.Plan(40, 1, api.FAVEST_FP64, api.FAVEST_IO_C128)
+    T0 = p.adj(*exact(40))
+    c0 = p.fwd(*T0)
+    T1 = p.adj(*c0)
+    c1 = p.fwd(*T1)
+    T2 = p.adj(*c1)
+
+    def sup(u, v):
+        return max(float((u[0] - v[0]).abs().max()), float((u[1] - v[1]).abs().max()))
+    out["table2_gl_L40"] = {"fp64": [sup(T1, T0), sup(T2, T0), sup(T2, T1), sup(c1, c0)], "paper": t2,
+                            "columns": ["|T1-T0|inf", "|T2-T0|inf", "|T2-T1|inf", "max coefficient difference"]}
+    p.close()
+    return out
 
 
 def measure_real(L, B, stream):
@@ -431,7 +487,9 @@ def main():
 
     plan = api.Plan(L, B, prec, api.FAVEST_IO_C64)
     # plan set-up (untimed): the generator's block shape picked by the autotuner
-    gen_shape = plan.tune() if prec == api.FAVEST_BF16X6 else None
+    gen_shape = None
+    if prec == api.FAVEST_BF16X6:
+        gen_shape = plan.gen_shape() if args.no_tune else plan.tune()
     a_h, b_h = synthetic.coefficients(L, B, seed=2, decay=1.5)
     a = torch.as_tensor(a_h).to(torch.complex64).cuda()
     b = torch.as_tensor(b_h).to(torch.complex64).cuda()

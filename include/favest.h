@@ -102,8 +102,10 @@ int favest_gl_grid(int nlat, double *x, double *w);
  * current CUDA device.  L >= 1; degrees beyond 1023 (more than 512 latitude pairs)
  * return FAVEST_EUNSUPPORTED in this version.  FAVEST_BF16X6
  * requires io_type FAVEST_IO_C64 or FAVEST_IO_R32 (FAVEST_EUNSUPPORTED otherwise) and
- * a device with tcgen05 tensor cores (sm_100 family); FAVEST_IO_R32 requires
- * FAVEST_BF16X6 (FAVEST_EUNSUPPORTED otherwise).
+ * a device with tcgen05 tensor cores (sm_100 family), and its FP32 longitude DFT takes
+ * nphi = 2(L+1) with prime factors up to 128 only (FAVEST_EUNSUPPORTED otherwise, e.g.
+ * L = 150: nphi = 2 * 151); FAVEST_IO_R32 requires FAVEST_BF16X6 (FAVEST_EUNSUPPORTED
+ * otherwise).
  *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
  *       and latitude weights; NULL selects the built-in Gauss-Legendre rule.  When
  *       given, the nodes must lie strictly inside (-1, 1) and both arrays must be

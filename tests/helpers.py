@@ -1,4 +1,6 @@
 """Shared test helpers: error metrics and grid construction (no transform arithmetic)."""
+import os
+
 import numpy as np
 
 
@@ -65,3 +67,22 @@ def full_of_half(c, L):
     sg = np.where(ms[pos] % 2 == 1, -1.0, 1.0)
     out[..., cidx(ls[pos], -ms[pos])] = sg * np.conj(c[..., pos])
     return out
+
+
+def read_field_a():
+    """Tangent Field A fixture (tests/golden/field_a.txt): its exact coefficients
+    [(family, l, m, value)], the paper's Table 1 GL row {L: error} and Table 2 GL row
+    [|T1-T0|, |T2-T0|, |T2-T1|, coefficient difference] at L = 40."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "field_a.txt")
+    coefs, t1, t2 = [], {}, None
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] in ("a", "b"):
+            coefs.append((line[0], int(line[1]), int(line[2]), float(line[3]) + 1j * float(line[4])))
+        elif line[0] == "table1":
+            t1[int(line[1])] = float(line[2])
+        elif line[0] == "table2":
+            t2 = [float(v) for v in line[2:]]
+    return coefs, t1, t2

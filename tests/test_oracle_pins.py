@@ -10,6 +10,8 @@ import numpy as np
 import pytest
 from scipy.special import sph_harm_y
 
+from helpers import read_field_a
+
 RNG = np.random.default_rng(12345)
 
 
@@ -332,19 +334,7 @@ def test_single_mode_fields(orc, l0, m0):
 
 
 def _read_field_a():
-    path = os.path.join(os.path.dirname(__file__), "golden", "field_a.txt")
-    coefs, t1, t2 = [], {}, None
-    for line in open(path):
-        line = line.split("#")[0].split()
-        if not line:
-            continue
-        if line[0] in ("a", "b"):
-            coefs.append((line[0], int(line[1]), int(line[2]), float(line[3]) + 1j * float(line[4])))
-        elif line[0] == "table1":
-            t1[int(line[1])] = float(line[2])
-        elif line[0] == "table2":
-            t2 = [float(v) for v in line[2:]]
-    return coefs, t1, t2
+    return read_field_a()
 
 
 def _field_a(orc, L):
