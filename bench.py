@@ -260,7 +260,49 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     for Br in (B, 2 * B):
         forms["real_fields_B%d" % Br] = measure_real(L, Br, stream)
     forms["field_a_tables"] = measure_field_a()
+    forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
     return forms
+
+
+def measure_cg_route(L, stream):
+    """The paper's Clebsch-Gordan route (Thm. 1, Thm. 2) on the FP64 path: one field of
+    degree L from Cartesian components, forward and adjoint timed separately; checked
+    against the theta/phi FP64 path on the same field (same coefficients, and the same
+    field in Cartesian components)."""
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    ca, cb = synthetic.coefficients(L, 1, seed=1, decay=1.0)
+    da, db = torch.as_tensor(ca).cuda(), torch.as_tensor(cb).cuda()
+    p64 = api.Plan(L, 1, api.FAVEST_FP64, api.FAVEST_IO_C128)
+    cp = api.CgPlan(L, 1)
+    tt, tp = p64.adj(da, db)
+    x, _ = api.favest_gl_grid(L + 1)
+    th = torch.as_tensor(np.arccos(x)).cuda()[:, None]
+    ph = torch.as_tensor(2 * np.pi * np.arange(2 * (L + 1)) / (2 * (L + 1))).cuda()[None, :]
+    ct, st, cph, sph = torch.cos(th), torch.sin(th), torch.cos(ph), torch.sin(ph)
+    T = torch.stack([tt[0] * ct * cph - tp[0] * sph, tt[0] * ct * sph + tp[0] * cph,
+                     -tt[0] * st.expand_as(tt[0])])[None].contiguous()
+    a, b = cp.fwd(T)
+    Tr = torch.empty_like(T)
+    t_fwd = time_steps(lambda: cp.fwd(T, a, b, stream=stream), 5, 2, stream)
+    t_adj = time_steps(lambda: cp.adj(da, db, Tr, stream=stream), 5, 2, stream)
+    cp.profile(True)
+    cp.fwd(T, a, b, stream=stream)
+    cp.adj(da, db, Tr, stream=stream)
+    prof = {k: v[0] / v[1] for k, v in cp.profile_read().items()}
+    cp.profile(False)
+    torch.cuda.synchronize()
+
+    def nerr(g, r):
+        return float((g - r).abs().max() / r.abs().max())
+    out = {"fwd_ms": t_fwd, "adj_ms": t_adj, "fields_per_s": 1.0 / ((t_fwd + t_adj) * 1e-3),
+           "fwd_vs_synthesising_coefficients": max(nerr(a, da), nerr(b, db)),
+           "adj_vs_theta_phi_path": nerr(Tr, T), "kernel_ms": prof,
+           "input": "coefficients N(0,1)(l+1)^-1, seed 1; T = the theta/phi FP64 adjoint in Cartesian components"}
+    cp.close()
+    p64.close()
+    return out
 
 
 def measure_field_a():

@@ -142,6 +142,33 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
                void *stream);
 
 /*
+ * The paper's Clebsch-Gordan route (Sec. 4, Thm. 1, Thm. 2, Algs. 1-2), FP64: the same
+ * transforms for fields given by Cartesian components, T = T^(1) e_x + T^(2) e_y + T^(3) e_z
+ * (as FaVeST_fwd(T, L, X, w) takes them, Sec. 4.4), computed through scalar spherical
+ * harmonic transforms of degree L+1 of the three components on the plan's grid:
+ *   forward (Thm. 1): a_lm, b_lm as fixed combinations, with the Clebsch-Gordan values of
+ *     eq. ninecoeff and c_l, d_l of eq. cl,dl,betal, of the FwdSHTs (eq. Flm) of T^(1),
+ *     T^(2), T^(3) at degrees l-1, l, l+1 and orders m-1, m, m+1;
+ *   adjoint (Thm. 2): the nu/eta coefficient sets (eqs. nulm1, nulm2, etalm; a, b read as
+ *     zero outside 1 <= l <= L, |m| <= l) summed per component into one scalar synthesis
+ *     of degree L+1 each (the AdjSHTs S_{L-1}, S_L, S_{L+1} of the theorem are linear).
+ * Both are identities for any point set; on the Gauss-Legendre grid they equal favest_fwd
+ * and favest_adj of the theta/phi components to rounding (tested).
+ *
+ * favest_cg_plan_create: an FP64 plan for `batch` such fields (1 <= batch <= 1366),
+ *   arguments and errors as favest_plan_create.  The plan serves only the two calls below;
+ *   favest_fwd/favest_adj on it return FAVEST_EINVAL, and these calls on other plans too.
+ * favest_fwd_cart: T device [batch][3][nlat][nphi] complex double (component planes x, y,
+ *   z of each field), read only; a, b device [batch][L^2+2L] complex double, written.
+ * favest_adj_cart: a, b read; T written in the same layout.
+ * Pointers 16-byte aligned; asynchronous on `stream`.
+ */
+int favest_cg_plan_create(int L, int batch, const double *cos_theta, const double *w_lat,
+                          favest_plan *out);
+int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *stream);
+int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, void *stream);
+
+/*
  * Weighting of the forward transform.  flag = 0 (default): the quadrature weights of
  * eq. fwdvsht2.  flag = 1: unit weights, i.e. favest_fwd computes A^H T, the exact
  * adjoint of favest_adj (used by reverse-mode differentiation of AdjVSHT).

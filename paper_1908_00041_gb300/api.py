@@ -101,6 +101,9 @@ def lib(build_if_missing=False):
             L.favest_batch_destroy.argtypes = [vp]
             L.favest_fwd_fp64_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp]
             L.favest_noalloc_scratch_bytes.restype = ctypes.c_size_t
+            L.favest_cg_plan_create.argtypes = [i, i, d, d, ctypes.POINTER(vp)]
+            L.favest_fwd_cart.argtypes = [vp, vp, vp, vp, vp]
+            L.favest_adj_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_profile_enable.argtypes = [vp, i]
             L.favest_profile_read.argtypes = [vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_longlong)]
@@ -353,6 +356,78 @@ class Plan:
         _check(lib().favest_kernel_work(ctypes.c_void_p(self.handle), name.encode(), ctypes.byref(nb),
                                         ctypes.byref(fl), ctypes.byref(pipe)), "favest_kernel_work")
         return nb.value, fl.value, pipe.value
+
+
+class CgPlan:
+    """FP64 plan of the Clebsch-Gordan route (Thm. 1, Thm. 2): fields as Cartesian
+    components, T [batch, 3, L+1, 2(L+1)] complex128; coefficients [batch, L^2+2L]."""
+
+    def __init__(self, L, batch=1, cos_theta=None, w_lat=None):
+        import torch
+        self.L, self.batch = int(L), int(batch)
+        self.nlat, self.nphi = L + 1, 2 * (L + 1)
+        self.K = L * L + 2 * L
+        self.cdtype = torch.complex128
+        h = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
+        xp = wp = None
+        if cos_theta is not None:
+            cos_theta = np.ascontiguousarray(cos_theta, dtype=np.float64)
+            w_lat = np.ascontiguousarray(w_lat, dtype=np.float64)
+            xp, wp = cos_theta.ctypes.data_as(dp), w_lat.ctypes.data_as(dp)
+        _check(lib().favest_cg_plan_create(self.L, self.batch, xp, wp, ctypes.byref(h)), "favest_cg_plan_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            favest_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_shape(self):
+        return (self.batch, 3, self.nlat, self.nphi)
+
+    def coef_shape(self):
+        return (self.batch, self.K)
+
+    def _check(self, t, shape, name):
+        if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError("%s: expected contiguous CUDA complex128 tensor of shape %s" % (name, shape))
+
+    def fwd(self, T, a=None, b=None, stream=None):
+        import torch
+        self._check(T, self.field_shape(), "T")
+        a = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if a is None else a
+        b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if b is None else b
+        self._check(a, self.coef_shape(), "a")
+        self._check(b, self.coef_shape(), "b")
+        _check(lib().favest_fwd_cart(ctypes.c_void_p(self.handle), _ptr(T), _ptr(a), _ptr(b), _stream(stream)),
+               "favest_fwd_cart")
+        return a, b
+
+    def adj(self, a, b, T=None, stream=None):
+        import torch
+        self._check(a, self.coef_shape(), "a")
+        self._check(b, self.coef_shape(), "b")
+        T = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device) if T is None else T
+        self._check(T, self.field_shape(), "T")
+        _check(lib().favest_adj_cart(ctypes.c_void_p(self.handle), _ptr(a), _ptr(b), _ptr(T), _stream(stream)),
+               "favest_adj_cart")
+        return T
+
+    def status(self, stream=None):
+        return favest_status(self.handle, stream)
+
+    def profile(self, enable=True):
+        favest_profile_enable(self.handle, 1 if enable else 0)
+
+    def profile_read(self):
+        return favest_profile_read(self.handle)
 
 
 class BatchPlan:

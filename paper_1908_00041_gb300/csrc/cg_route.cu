@@ -1,0 +1,187 @@
+// The paper's Clebsch-Gordan route on the FP64 path (Sec. 4, Thm. 1 and Thm. 2): vector
+// transforms of fields given by their Cartesian components T^(1), T^(2), T^(3), through
+// scalar spherical harmonic transforms of degree L+1.
+//
+// The scalar transforms run on the FP64 kernels in scalar mode: scalar field s = 3f + c
+// (component c of vector field f) occupies the column pair (s, sign of m) of the sums
+//   Q[row (l, mu)][2 s + (m < 0)] = sum_j y_l^mu(theta_j) w_j F_s(j, m),   l = mu..L+1,
+// with the plain point weights w_j and the scaled recurrence values y = lambda / kappa, so
+//   F_lm(T^(c)) = kappa_l^mu Q[.][2 s] (m >= 0),  (-1)^mu kappa_l^mu Q[.][2 s + 1] (m < 0)
+// (lambda_l^{-mu} = (-1)^mu lambda_l^mu).  The synthesis reads the same layout.
+//
+// Forward (Thm. 1, eq. almblmviaFlm).  Every xi/mu factor of the theorem at its shifted
+// index is a product of c_l, d_l (eq. cl,dl,betal) and a Clebsch-Gordan value of the
+// OUTPUT index (l, m) (eq. Blm1/Blm2), e.g. xi^(1)_{l-1,m-1} = c_l C^{l,m}_{l-1,m-1,1,1}:
+//   a_lm = 1/sqrt2 [ c_l C0 Fm(l-1, m-1) + d_l C1 Fm(l+1, m-1) + c_l C4 Fp(l-1, m+1)
+//                  + d_l C5 Fp(l+1, m+1) ] + c_l C2 F3(l-1, m) + d_l C3 F3(l+1, m),
+//   b_lm = -i/sqrt2 [ C6 Fm(l, m-1) + C7 Fp(l, m+1) ] - i C8 F3(l, m),
+// with Fm = -F(T1) + i F(T2), Fp = F(T1) + i F(T2), F3 = F(T3), Ck = C_k(l, m) below, and
+// F(l', m') = 0 unless |m'| <= l' <= L+1.
+//
+// Adjoint (Thm. 2, eq. SLvecviascal).  Since S_K is linear and zero-padding a sequence
+// beyond degree K leaves S_K unchanged, the three syntheses of each component are one
+// synthesis of degree L+1 of the summed coefficients
+//   g1 = -(nu1 + nu2 + eta1)/sqrt2,  g2 = -(nu3 + nu4 - eta2)/sqrt2,  g3 = nu5 + nu6 + eta3
+// (eqs. nulm1, nulm2, etalm), with a, b read as zero outside 1 <= l <= L, |m| <= l and
+// every nu evaluated for all |m| <= l (the reading of their garbled support conditions).
+#include <cmath>
+
+#include "favest_internal.h"
+
+namespace favest {
+
+namespace {
+
+// The nine Clebsch-Gordan closed forms of eq. ninecoeff for the coupled state (l, m):
+//   0: C^{l,m}_{l-1,m-1,1,1}  1: C^{l,m}_{l+1,m-1,1,1}  2: C^{l,m}_{l-1,m,1,0}
+//   3: C^{l,m}_{l+1,m,1,0}    4: C^{l,m}_{l-1,m+1,1,-1} 5: C^{l,m}_{l+1,m+1,1,-1}
+//   6: C^{l,m}_{l,m-1,1,1}    7: C^{l,m}_{l,m+1,1,-1}   8: C^{l,m}_{l,m,1,0}
+// Callers use a value only where its uncoupled state (l', m') exists, with l >= 1.
+__device__ double clebsch(int k, int l, int m)
+{
+    const double L = l, M = m;
+    double num, den, sg = 1.0;
+    switch (k) {
+    case 0: num = (L + M) * (L + M - 1.0); den = (2.0 * L) * (2.0 * L - 1.0); break;
+    case 1: num = (L - M + 1.0) * (L - M + 2.0); den = (2.0 * L + 2.0) * (2.0 * L + 3.0); break;
+    case 2: num = (L + M) * (L - M); den = L * (2.0 * L - 1.0); break;
+    case 3: num = (L - M + 1.0) * (L + M + 1.0); den = (2.0 * L + 3.0) * (L + 1.0); sg = -1.0; break;
+    case 4: num = (L - M) * (L - M - 1.0); den = (2.0 * L) * (2.0 * L - 1.0); break;
+    case 5: num = (L + M + 1.0) * (L + M + 2.0); den = (2.0 * L + 3.0) * (2.0 * L + 2.0); break;
+    case 6: num = (L + M) * (L - M + 1.0); den = L * (2.0 * L + 2.0); sg = -1.0; break;
+    case 7: num = (L + M + 1.0) * (L - M); den = L * (2.0 * L + 2.0); break;
+    default: return M / sqrt(L * (L + 1.0));
+    }
+    return num > 0.0 ? sg * sqrt(num / den) : 0.0;
+}
+
+__device__ __forceinline__ double cl_of(int l) { return sqrt((l + 1.0) / (2.0 * l + 1.0)); }
+__device__ __forceinline__ double dl_of(int l) { return sqrt(l / (2.0 * l + 1.0)); }
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }   // i a
+
+// FwdSHT F_{l,m} of scalar field s from the scaled sums; 0 outside |m| <= l <= L+1
+__device__ __forceinline__ double2 fsht(const double2 *__restrict__ Q, const double *__restrict__ kap, int L,
+                                        int ncol, int s, int l, int m)
+{
+    const int mu = m < 0 ? -m : m;
+    if (l < 0 || l > L + 1 || mu > l) return make_double2(0.0, 0.0);
+    const long long row = tab_off(L, mu) + (l - mu);
+    const double k = kap[row] * ((m < 0 && (mu & 1)) ? -1.0 : 1.0);
+    return cscale(k, Q[row * ncol + 2 * s + (m < 0)]);
+}
+
+// one thread per (field, coefficient (l, m), l = 1..L)
+__global__ void k_cg_combine(const double2 *__restrict__ Q, const double *__restrict__ kap, double2 *__restrict__ a,
+                             double2 *__restrict__ b, int L, int K, int ncol, int B)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)B * K) return;
+    const int f = (int)(t / K), k = (int)(t % K);
+    int l = (int)sqrt((double)(k + 1));
+    while (l * l + 2 * l < k + 1) ++l;
+    while ((l - 1) * (l - 1) + 2 * (l - 1) >= k + 1) --l;
+    const int m = k - l * l - l + 1;
+    const int s1 = 3 * f, s2 = s1 + 1, s3 = s1 + 2;
+    auto Fm = [&](int ll, int mm) {          // -F(T1) + i F(T2)
+        const double2 x = fsht(Q, kap, L, ncol, s1, ll, mm), y = fsht(Q, kap, L, ncol, s2, ll, mm);
+        return make_double2(-x.x - y.y, -x.y + y.x);
+    };
+    auto Fp = [&](int ll, int mm) {          // F(T1) + i F(T2)
+        const double2 x = fsht(Q, kap, L, ncol, s1, ll, mm), y = fsht(Q, kap, L, ncol, s2, ll, mm);
+        return make_double2(x.x - y.y, x.y + y.x);
+    };
+    const double cl = cl_of(l), dl = dl_of(l), r2 = 0.70710678118654752440;
+    double2 sum = cscale(cl * clebsch(0, l, m), Fm(l - 1, m - 1));
+    sum = cadd(sum, cscale(dl * clebsch(1, l, m), Fm(l + 1, m - 1)));
+    sum = cadd(sum, cscale(cl * clebsch(4, l, m), Fp(l - 1, m + 1)));
+    sum = cadd(sum, cscale(dl * clebsch(5, l, m), Fp(l + 1, m + 1)));
+    double2 av = cscale(r2, sum);
+    av = cadd(av, cscale(cl * clebsch(2, l, m), fsht(Q, kap, L, ncol, s3, l - 1, m)));
+    av = cadd(av, cscale(dl * clebsch(3, l, m), fsht(Q, kap, L, ncol, s3, l + 1, m)));
+    double2 t2 = cscale(clebsch(6, l, m), Fm(l, m - 1));
+    t2 = cadd(t2, cscale(clebsch(7, l, m), Fp(l, m + 1)));
+    // b = -i/sqrt2 t2 - i C8 F3
+    const double2 bv = cadd(cscale(-r2, cmuli(t2)), cscale(-clebsch(8, l, m), cmuli(fsht(Q, kap, L, ncol, s3, l, m))));
+    a[(size_t)f * K + k] = av;
+    b[(size_t)f * K + k] = bv;
+}
+
+__device__ __forceinline__ double2 coef(const double2 *__restrict__ c, int L, int K, int f, int l, int m)
+{
+    if (l < 1 || l > L || m < -l || m > l) return make_double2(0.0, 0.0);
+    return c[(size_t)f * K + l * l + l + m - 1];
+}
+
+// one thread per (field, scalar coefficient (l, m), l = 0..L+1)
+__global__ void k_cg_uncombine(const double2 *__restrict__ a, const double2 *__restrict__ b,
+                               const double *__restrict__ kap, double2 *__restrict__ Q, int L, int K, int ncol, int B)
+{
+    const int n = (L + 2) * (L + 2);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)B * n) return;
+    const int f = (int)(t / n), idx = (int)(t % n);
+    int l = (int)sqrt((double)idx);
+    while (l * l > idx) --l;
+    while ((l + 1) * (l + 1) <= idx) ++l;
+    const int m = idx - l * l - l;
+    const double2 z = make_double2(0.0, 0.0);
+    // a and b terms where the coefficient exists (the CG value of its coupled state)
+    const double2 ap1p = coef(a, L, K, f, l + 1, m + 1), ap1m = coef(a, L, K, f, l + 1, m - 1);
+    const double2 am1p = coef(a, L, K, f, l - 1, m + 1), am1m = coef(a, L, K, f, l - 1, m - 1);
+    const double2 ap10 = coef(a, L, K, f, l + 1, m), am10 = coef(a, L, K, f, l - 1, m);
+    const double2 bp = coef(b, L, K, f, l, m + 1), bm = coef(b, L, K, f, l, m - 1), b0 = coef(b, L, K, f, l, m);
+    const double c1 = cl_of(l + 1), d1 = l >= 2 ? dl_of(l - 1) : 0.0;
+    const double2 u1 = (l + 1 <= L && m + 1 <= l + 1) ? cscale(clebsch(0, l + 1, m + 1), ap1p) : z;
+    const double2 v1 = (l + 1 <= L && m - 1 >= -(l + 1)) ? cscale(clebsch(4, l + 1, m - 1), ap1m) : z;
+    const double2 u2 = (l >= 2 && m + 1 <= l - 1) ? cscale(clebsch(1, l - 1, m + 1), am1p) : z;
+    const double2 v2 = (l >= 2 && m - 1 >= -(l - 1)) ? cscale(clebsch(5, l - 1, m - 1), am1m) : z;
+    const double2 w5 = (l + 1 <= L) ? cscale(c1 * clebsch(2, l + 1, m), ap10) : z;
+    const double2 w6 = (l >= 2 && m >= -(l - 1) && m <= l - 1) ? cscale(d1 * clebsch(3, l - 1, m), am10) : z;
+    const double2 e6 = (l >= 1 && m + 1 <= l) ? cscale(clebsch(6, l, m + 1), bp) : z;
+    const double2 e7 = (l >= 1 && m - 1 >= -l) ? cscale(clebsch(7, l, m - 1), bm) : z;
+    const double2 e8 = (l >= 1) ? cscale(clebsch(8, l, m), b0) : z;
+    // nu1 = c (u1 - v1), nu2 = d (u2 - v2), nu3 = i c (u1 + v1), nu4 = i d (u2 + v2)
+    const double2 nu1 = cscale(c1, make_double2(u1.x - v1.x, u1.y - v1.y));
+    const double2 nu2 = cscale(d1, make_double2(u2.x - v2.x, u2.y - v2.y));
+    const double2 nu3 = cmuli(cscale(c1, cadd(u1, v1)));
+    const double2 nu4 = cmuli(cscale(d1, cadd(u2, v2)));
+    // eta1 = i (e6 - e7), eta2 = e6 + e7, eta3 = i e8
+    const double2 eta1 = cmuli(make_double2(e6.x - e7.x, e6.y - e7.y));
+    const double2 eta2 = cadd(e6, e7);
+    const double2 eta3 = cmuli(e8);
+    const double r2 = 0.70710678118654752440;
+    const double2 g1 = cscale(-r2, cadd(cadd(nu1, nu2), eta1));
+    const double2 g2 = cscale(-r2, make_double2(nu3.x + nu4.x - eta2.x, nu3.y + nu4.y - eta2.y));
+    const double2 g3 = cadd(cadd(w5, w6), eta3);
+    const int mu = m < 0 ? -m : m;
+    const long long row = tab_off(L, mu) + (l - mu);
+    const double kk = kap[row] * ((m < 0 && (mu & 1)) ? -1.0 : 1.0);
+    const double2 g[3] = {g1, g2, g3};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Q[row * ncol + 2 * (3 * f + c) + (m < 0)] = cscale(kk, g[c]);
+}
+
+}  // namespace
+
+cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    const long long n = (long long)p.B * K;
+    k_cg_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)p.d_Q, p.d_kap, (double2 *)a,
+                                                           (double2 *)b, p.L, K, p.ncol, p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cudaStream_t s)
+{
+    const int K = p.L * p.L + 2 * p.L;
+    const long long n = (long long)p.B * (p.L + 2) * (p.L + 2);
+    k_cg_uncombine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)a, (const double2 *)b, p.d_kap,
+                                                             (double2 *)p.d_Q, p.L, K, p.ncol, p.B);
+    return cudaGetLastError();
+}
+
+}  // namespace favest

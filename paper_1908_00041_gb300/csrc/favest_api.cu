@@ -107,7 +107,7 @@ void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam_f, p.d_lam_a, p.d_Fb, p.d_gb,
-                    p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32,
+                    p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups};
     for (void *q : ptrs)
@@ -136,14 +136,16 @@ int build_tables(Plan &p)
         (e = upload(&p.d_omega_unit, omu)) || (e = upload(&p.d_wring, wring)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
 
-    std::vector<double> cmu(L + 1);
+    std::vector<double> cmu(L + 2);
     cmu[0] = 1.0 / std::sqrt(4.0 * 3.14159265358979323846);
-    for (int mu = 1; mu <= L; ++mu) cmu[mu] = cmu[mu - 1] * std::sqrt((2.0 * mu + 1.0) / (2.0 * mu));
+    for (int mu = 1; mu <= L + 1; ++mu) cmu[mu] = cmu[mu - 1] * std::sqrt((2.0 * mu + 1.0) / (2.0 * mu));
 
-    const long long ntab = tab_off(L, L + 1);
+    // orders 0..L (0..L+1 for the degree-(L+1) scalar transforms of the CG route)
+    const int mumax = L + (p.nscal > 0 ? 1 : 0);
+    const long long ntab = tab_off(L, mumax + 1);
     p.ntab = ntab;
-    std::vector<double> A(ntab), P(ntab), M(ntab), R(ntab), kap(L + 3);
-    for (int mu = 0; mu <= L; ++mu) {
+    std::vector<double> A(ntab), P(ntab), M(ntab), R(ntab), kap(L + 3), K(ntab);
+    for (int mu = 0; mu <= mumax; ++mu) {
         const long long t0 = tab_off(L, mu);
         // kappa_l = lambda_l / y_l with kappa_mu = kappa_{mu+1} = 1
         kap[mu] = 1.0;
@@ -159,11 +161,13 @@ int build_tables(Plan &p)
             P[t] = sl * l * eps_lm(l + 1, mu) * kap[l + 1];
             M[t] = (l > mu) ? sl * (l + 1.0) * eps_lm(l, mu) * kap[l - 1] : 0.0;
             R[t] = sl * kap[l];
+            K[t] = kap[l];
         }
     }
     if ((e = upload(&p.d_cmu, cmu)) || (e = upload(&p.d_A, A)) || (e = upload(&p.d_P, P)) ||
         (e = upload(&p.d_M, M)) || (e = upload(&p.d_R, R)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    if (p.nscal > 0 && (e = upload(&p.d_kap, K))) return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     if (p.precision == FAVEST_BF16X6) {
         std::vector<float> P32(ntab), M32(ntab), R32(ntab), k1(L + 1, 0.f);
         for (long long t = 0; t < ntab; ++t) {
@@ -500,9 +504,10 @@ int alloc_workspace_bf16(Plan &p)
 
 int alloc_workspace(Plan &p)
 {
-    size_t fbytes = (size_t)(p.L + 1) * p.ncol * p.nlat * sizeof(double2);
+    const int nmu = p.L + 1 + (p.nscal > 0 ? 1 : 0);
+    size_t fbytes = (size_t)nmu * p.ncol * p.nlat * sizeof(double2);
     size_t qbytes = (size_t)p.ntab * p.ncol * sizeof(double2);
-    size_t gbytes = (size_t)p.B * 2 * p.nlat * p.nphi * sizeof(double2);
+    size_t gbytes = (size_t)(p.ncol / 4) * 2 * p.nlat * p.nphi * sizeof(double2);
     if (cudaMalloc(&p.d_F, fbytes) != cudaSuccess || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
         cudaMalloc(&p.d_G, gbytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
@@ -510,6 +515,8 @@ int alloc_workspace(Plan &p)
         return FAVEST_ENOMEM;
     }
     cudaMemset(p.d_status, 0, sizeof(int));
+    // the CG route's padding columns (an odd count of scalar fields) read as zero
+    if (p.nscal > 0 && cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess) return FAVEST_ECUDA;
     p.ws_bytes = fbytes + qbytes + gbytes;
     return FAVEST_OK;
 }
@@ -527,7 +534,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_EC
 
 const char *kKernelNames[KID_COUNT] = {
     "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
-    "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj", "polar_patch",
+    "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj", "polar_patch", "cg_combine", "cg_uncombine",
 };
 
 cudaEvent_t take_event(Plan &p)
@@ -592,7 +599,7 @@ int favest_gl_grid(int nlat, double *x, double *w)
 namespace favest {
 
 int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
-                         const double *w_lat, int force_gemm_n, favest_plan *out)
+                         const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route)
 {
     if (!out) return FAVEST_EINVAL;
     *out = nullptr;
@@ -629,7 +636,12 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     p.J = (nlat + 1) / 2;
     p.has_eq = nlat & 1;
     p.ncol = 4 * batch;
-    p.ct = (batch % 2 == 0) ? 8 : 4;
+    if (cg_route) {
+        // 3 scalar fields per vector field, 2 per group of 4 columns (sign of m, re/im)
+        p.nscal = 3 * batch;
+        p.ncol = 4 * ((p.nscal + 1) / 2);
+    }
+    p.ct = (p.ncol % 8 == 0) ? 8 : 4;
     p.ng = p.ncol / p.ct;
     if (cudaGetDevice(&p.device) != cudaSuccess) { delete h; return FAVEST_ECUDA; }
     cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
@@ -677,6 +689,12 @@ int favest_fwd(favest_plan plan, const void *Tth, const void *Tph, void *a, void
     return favest_fwd_ex(plan, Tth, Tph, a, b, 0, stream);
 }
 
+int favest_cg_plan_create(int L, int batch, const double *cos_theta, const double *w_lat, favest_plan *out)
+{
+    if (batch > 4096 / 3 + 1) return FAVEST_EINVAL;
+    return favest::plan_create_internal(L, batch, FAVEST_FP64, FAVEST_IO_C128, cos_theta, w_lat, 0, out, 1);
+}
+
 int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, void *stream)
 {
     return favest_adj_ex(plan, a, b, Tth, Tph, 0, stream);
@@ -698,6 +716,7 @@ int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, v
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
     if (flags & ~FAVEST_FLAG_UNIT_WEIGHTS) return FAVEST_EINVAL;
     Plan &p = plan->p;
+    if (p.nscal > 0) return FAVEST_EINVAL;     // Clebsch-Gordan plans take favest_fwd_cart
     FlagScope unit(p.unit_weights, p.unit_weights | ((flags & FAVEST_FLAG_UNIT_WEIGHTS) ? 1 : 0));
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
@@ -723,6 +742,7 @@ int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, voi
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
     if (flags & ~FAVEST_FLAG_WEIGHTED) return FAVEST_EINVAL;
     Plan &p = plan->p;
+    if (p.nscal > 0) return FAVEST_EINVAL;
     FlagScope weighted(p.adj_weighted, (flags & FAVEST_FLAG_WEIGHTED) ? 1 : 0);
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
@@ -742,6 +762,38 @@ int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, voi
     e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_fp64(p, a, b, s); });
     if (e == cudaSuccess) e = timed(p, KID_SYNTHESIS, s, [&] { return launch_synthesis_fp64(p, s); });
     if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, Tth, Tph, s); });
+    return cuda_status(e);
+}
+
+int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *stream)
+{
+    if (!plan || !T || !a || !b) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    if (p.nscal == 0) return FAVEST_EINVAL;
+    if (!aligned(T, 16) || !aligned(a, 16) || !aligned(b, 16)) return FAVEST_EINVAL;
+    int st = check_device(p);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // three scalar FwdSHTs of degree L+1 (DFT, analysis with the point weights), Thm. 1
+    cudaError_t e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, T, T, s); });
+    if (e == cudaSuccess) e = timed(p, KID_ANALYSIS, s, [&] { return launch_analysis_fp64(p, s); });
+    if (e == cudaSuccess) e = timed(p, KID_CG_COMBINE, s, [&] { return launch_cg_combine(p, a, b, s); });
+    return cuda_status(e);
+}
+
+int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, void *stream)
+{
+    if (!plan || !T || !a || !b) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    if (p.nscal == 0) return FAVEST_EINVAL;
+    if (!aligned(T, 16) || !aligned(a, 16) || !aligned(b, 16)) return FAVEST_EINVAL;
+    int st = check_device(p);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // Thm. 2: summed nu/eta coefficients, three scalar syntheses of degree L+1
+    cudaError_t e = timed(p, KID_CG_UNCOMBINE, s, [&] { return launch_cg_uncombine(p, a, b, s); });
+    if (e == cudaSuccess) e = timed(p, KID_SYNTHESIS, s, [&] { return launch_synthesis_fp64(p, s); });
+    if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, T, T, s); });
     return cuda_status(e);
 }
 
@@ -841,7 +893,7 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
     const double nlat = p.nlat, nphi = p.nphi;
     // recurrence steps: rows l = mu..L+1 of every order, at every folded latitude
     double rows = 0;
-    for (int mu = 0; mu <= p.L; ++mu) rows += p.L + 2 - mu;
+    for (int mu = 0; mu <= p.L + (p.nscal > 0 ? 1 : 0); ++mu) rows += p.L + 2 - mu;
     const double steps = rows * J;
     const std::string k(kernel);
     *bytes = 0;
@@ -874,16 +926,23 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         return FAVEST_OK;
     }
     const double io = p.io == FAVEST_IO_C128 ? 16.0 : 8.0;
-    const double grid = 2.0 * B * nlat * nphi * io;
-    const double fbuf = L1 * p.ncol * nlat * 16.0, qbuf = (double)p.ntab * p.ncol * 16.0;
+    // component planes: 2 per field, or the 3 Cartesian scalar fields of the CG route
+    const double planes = p.nscal > 0 ? (double)p.nscal : 2.0 * B;
+    const double grid = planes * nlat * nphi * io;
+    const double nmu = p.L + 1 + (p.nscal > 0 ? 1 : 0);
+    const double fbuf = nmu * p.ncol * nlat * 16.0, qbuf = (double)p.ntab * p.ncol * 16.0;
+    const double gbuf = p.ncol / 2.0 * nlat * nphi * 16.0;
     // per step: 2 recurrence instructions + 2 FMAs (re, im) per column
     const double leg = steps * (4.0 + 4.0 * p.ncol);
-    if (k == "fft_fwd") { *bytes = grid + fbuf; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
-    else if (k == "fft_inv") { *bytes = B * 2.0 * nlat * nphi * 16.0 + grid; *flops = 2 * B * nlat * 5.0 * nphi * std::log2(nphi); }
+    const double fftf = planes * nlat * 5.0 * nphi * std::log2(nphi);
+    if (k == "fft_fwd") { *bytes = grid + fbuf; *flops = fftf; }
+    else if (k == "fft_inv") { *bytes = gbuf + grid; *flops = fftf; }
     else if (k == "legendre_analysis") { *bytes = fbuf + qbuf; *flops = leg; *pipe = 1; }
-    else if (k == "legendre_synthesis") { *bytes = qbuf + B * 2.0 * nlat * nphi * 16.0; *flops = leg; *pipe = 1; }
+    else if (k == "legendre_synthesis") { *bytes = qbuf + gbuf; *flops = leg; *pipe = 1; }
     else if (k == "combine") { *bytes = qbuf + 2.0 * B * K * io; *flops = 16.0 * B * K; }
     else if (k == "uncombine") { *bytes = 2.0 * B * K * io + qbuf; *flops = 24.0 * B * K; }
+    else if (k == "cg_combine") { *bytes = qbuf + 2.0 * B * K * io; *flops = 120.0 * B * K; }
+    else if (k == "cg_uncombine") { *bytes = 2.0 * B * K * io + qbuf; *flops = 120.0 * B * (L + 2) * (L + 2); }
     else return FAVEST_EINVAL;
     return FAVEST_OK;
 }

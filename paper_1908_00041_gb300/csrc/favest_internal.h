@@ -80,6 +80,12 @@ struct Plan {
     // of m)
     int real = 0;
     int ncg = 0;              // column groups: B (complex) or ceil(B / 2) (real)
+    // Clebsch-Gordan route (FP64 plans from favest_cg_plan_create): the columns carry
+    // nscal = 3B scalar fields (the Cartesian components of the B vector fields), the
+    // scalar transforms run to degree L+1 (orders 0..L+1) with the plain quadrature
+    // weights, and d_kap holds kappa_l^mu for every table row; 0 for the other plans
+    int nscal = 0;
+    double *d_kap = nullptr;
     int nlat = 0, nphi = 0, J = 0, has_eq = 0;
     int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
     int ct = 0, ng = 0;       // FP64 column group width and count
@@ -164,7 +170,7 @@ struct Plan {
 
 enum KernelId {
     KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
-    KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ, KID_POLAR,
+    KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ, KID_POLAR, KID_CG_COMBINE, KID_CG_UNCOMBINE,
     KID_COUNT
 };
 
@@ -193,10 +199,13 @@ cudaError_t launch_tc_gemm(const Plan &p, bool fwd, cudaStream_t s);
 cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, cudaStream_t s);
 cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s);
+// Clebsch-Gordan route (FP64): scalar sums -> a, b (Thm. 1); a, b -> scalar coefficients (Thm. 2)
+cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s);
+cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cudaStream_t s);
 int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
 
 int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
-                         const double *w_lat, int force_gemm_n, favest_plan *out);
+                         const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route = 0);
 
 }  // namespace favest
 

@@ -12,10 +12,15 @@ namespace {
 
 // Forward: read ring (b, c, j) of T (io type TI), FFT in FP64, scatter bins m = -L..L
 // into Fraw[mu][col][j], col = (b*2 + c)*2 + (m < 0).
+// Scalar mode (nscal > 0, the Clebsch-Gordan route): ring (s = b*2 + c, j) is plane s of
+// Tth (planes of nlat*nphi elements back to back), rings s >= nscal are zero, and the
+// bins run to m = +-(L+1): both take the Nyquist bin n/2, which is order L+1 of the
+// degree-(L+1) scalar transforms on this grid.
 template <typename TI>
 __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
     const TI *__restrict__ Tth, const TI *__restrict__ Tph, double2 *__restrict__ Fraw,
-    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat, int ncol, const long long *__restrict__ toff)
+    RadixPlanArg rp, const double2 *__restrict__ tw, int L, int nlat, int ncol, const long long *__restrict__ toff,
+    int nscal)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -23,13 +28,20 @@ __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
     const int j = ring % nlat;
     const int bc = ring / nlat;
     const int c = bc & 1, b = bc >> 1;
-    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
-    const TI *src = (c == 0 ? Tth : Tph) + fb + (size_t)j * n;
     double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = to_d2(src[k]);
+    if (nscal > 0) {
+        const bool live = bc < nscal;
+        const TI *src = Tth + ((size_t)bc * nlat + j) * n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = live ? to_d2(src[k]) : make_double2(0.0, 0.0);
+    } else {
+        const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
+        const TI *src = (c == 0 ? Tth : Tph) + fb + (size_t)j * n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = to_d2(src[k]);
+    }
     __syncthreads();
     const double2 *out = stockham<false>(buf0, buf1, tw, rp);
-    for (int m = -L + (int)threadIdx.x; m <= L; m += blockDim.x) {
+    const int mmax = nscal > 0 ? L + 1 : L;
+    for (int m = -mmax + (int)threadIdx.x; m <= mmax; m += blockDim.x) {
         int bin = m < 0 ? m + n : m;
         double2 v = out[bin];
         int mu = m < 0 ? -m : m;
@@ -42,12 +54,13 @@ __global__ void __launch_bounds__(256) k_fft_fwd_fp64(
 
 // Inverse: read spectrum row G[b][c][j][bin] (Nyquist bin L+1 taken as zero), inverse
 // FFT (no 1/n), scale by wring[j] when given (the weighted adjoint W A c), write ring
-// to T (io type TO).
+// to T (io type TO).  Scalar mode (nscal > 0): ring s goes to plane s of Tth (s < nscal)
+// and the Nyquist bin, written by the synthesis for order L+1, is kept.
 template <typename TO>
 __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     const double2 *__restrict__ G, TO *__restrict__ Tth, TO *__restrict__ Tph,
     RadixPlanArg rp, const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat,
-    const long long *__restrict__ toff)
+    const long long *__restrict__ toff, int nscal)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -55,14 +68,15 @@ __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     const int j = ring % nlat;
     const int bc = ring / nlat;
     const int c = bc & 1, b = bc >> 1;
+    if (nscal > 0 && bc >= nscal) return;      // uniform over the CTA
     const double2 *src = G + (size_t)ring * n;
     double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
     for (int k = threadIdx.x; k < n; k += blockDim.x)
-        buf0[k] = (k == L + 1) ? make_double2(0.0, 0.0) : src[k];
+        buf0[k] = (k == L + 1 && nscal == 0) ? make_double2(0.0, 0.0) : src[k];
     __syncthreads();
     const double2 *out = stockham<true>(buf0, buf1, tw, rp);
-    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
-    TO *dst = (c == 0 ? Tth : Tph) + fb + (size_t)j * n;
+    const size_t fb = nscal > 0 ? (size_t)bc * nlat * n : toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+    TO *dst = (nscal > 0 || c == 0 ? Tth : Tph) + fb + (size_t)j * n;
     if (wring) {
         const double w = wring[j];
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -81,19 +95,19 @@ int fft_threads(int n) { return n >= 512 ? 256 : (n >= 128 ? 128 : 64); }
 cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    int grid = p.B * 2 * p.nlat;
+    int grid = p.ncol / 4 * 2 * p.nlat;        // rings: 2 per group of 4 columns (b, c)
     size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
     int th = fft_threads(p.nphi);
     if (p.io == FAVEST_IO_C128) {
         auto k = k_fft_fwd_fp64<double2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)Tth, (const double2 *)Tph, (double2 *)p.d_F,
-                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff, p.nscal);
     } else {
         auto k = k_fft_fwd_fp64<float2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const float2 *)Tth, (const float2 *)Tph, (double2 *)p.d_F,
-                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
+                                 rp, p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff, p.nscal);
     }
     return cudaGetLastError();
 }
@@ -101,19 +115,21 @@ cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph,
 cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    int grid = p.B * 2 * p.nlat;
+    int grid = p.ncol / 4 * 2 * p.nlat;
     size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
     int th = fft_threads(p.nphi);
     if (p.io == FAVEST_IO_C128) {
         auto k = k_fft_inv_fp64<double2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (double2 *)Tth, (double2 *)Tph, rp,
-                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff,
+                                 p.nscal);
     } else {
         auto k = k_fft_inv_fp64<float2>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, th, smem, s>>>((const double2 *)p.d_G, (float2 *)Tth, (float2 *)Tph, rp,
-                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff);
+                                 p.fft.tw64, p.adj_weighted ? p.d_wring : nullptr, p.L, p.nlat, p.d_toff,
+                                 p.nscal);
     }
     return cudaGetLastError();
 }

@@ -144,11 +144,14 @@ constexpr int kSynThreads = 256;
 constexpr int kSynJpt = 2;        // J <= 512
 
 // Adjoint Legendre stage.  gtab: [tab][ncol] scaled coefficients; G: [B][2][nlat][nphi].
+// Vector mode divides the sums by sin(theta_j).  Scalar mode (the Clebsch-Gordan route)
+// does not, and order L+1 exists there: its orders +-(L+1) share the Nyquist bin, so the
+// two sign columns are added into it.
 template <int CT>
 __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     const double2 *__restrict__ gtab, double2 *__restrict__ G, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
-    int L, int nlat, int nphi, int J, int has_eq, int ncol, int ng)
+    int L, int nlat, int nphi, int J, int has_eq, int ncol, int ng, int scalar)
 {
     extern __shared__ double sm_syn[];
     const int mu = blockIdx.x / ng, g = blockIdx.x % ng;
@@ -217,15 +220,22 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     for (int i = 0; i < kSynJpt; ++i) {
         const int j = threadIdx.x + i * kSynThreads;
         if (j >= J) continue;
-        const double is = 1.0 / sj[j];
+        const double is = scalar ? 1.0 : 1.0 / sj[j];
         const bool eq = has_eq && j == J - 1;
+        const bool nyq = mu == L + 1;                 // scalar mode only
 #pragma unroll
         for (int ct = 0; ct < CT; ++ct) {
             const int col = g * CT + ct;
             const int s = col & 1, bc = col >> 1;     // bc = b*2 + component
-            if (mu == 0 && s == 1) continue;
+            if ((mu == 0 || nyq) && s == 1) continue;
             const int bin = s ? nphi - mu : mu;
             double2 e = accE[i][ct], o = accO[i][ct];
+            if (nyq && ct + 1 < CT) {                 // add the m = -(L+1) column (ct + 1)
+                e.x += accE[i][ct + 1].x;
+                e.y += accE[i][ct + 1].y;
+                o.x += accO[i][ct + 1].x;
+                o.y += accO[i][ct + 1].y;
+            }
             G[((size_t)bc * nlat + j) * nphi + bin] = make_double2((e.x + o.x) * is, (e.y + o.y) * is);
             if (!eq)
                 G[((size_t)bc * nlat + (nlat - 1 - j)) * nphi + bin] =
@@ -239,7 +249,9 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
 cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 {
     if (p.J > kAnaThreads * kAnaJpt) return cudaErrorInvalidValue;
-    int grid = (p.L + 1) * p.ng;
+    // orders 0..L, and L+1 for the scalar transforms of degree L+1 (Clebsch-Gordan route)
+    int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
+    const double *omega = p.nscal > 0 ? p.d_wring : p.unit_weights ? p.d_omega_unit : p.d_omega;
     int nrowmax = p.L + 2;
     size_t smem;
     if (p.ct == 8) {
@@ -247,17 +259,15 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
         smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
-                                          p.unit_weights ? p.d_omega_unit : p.d_omega, p.d_cmu, p.d_A,
-                                          p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega,
+                                          p.d_cmu, p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
     } else {
         constexpr int CT = 4, V = kWin * CT * 2;
         smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin,
-                                          p.unit_weights ? p.d_omega_unit : p.d_omega, p.d_cmu, p.d_A,
-                                          p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega,
+                                          p.d_cmu, p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
     }
     return cudaGetLastError();
 }
@@ -265,7 +275,7 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
 {
     if (p.J > kSynThreads * kSynJpt) return cudaErrorInvalidValue;
-    int grid = (p.L + 1) * p.ng;
+    int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
     int nrowmax = p.L + 2;
     if (p.ct == 8) {
         constexpr int CT = 8;
@@ -274,7 +284,7 @@ cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
                                           p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng);
+                                          p.ng, p.nscal > 0);
     } else {
         constexpr int CT = 4;
         size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
@@ -282,7 +292,7 @@ cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
                                           p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng);
+                                          p.ng, p.nscal > 0);
     }
     return cudaGetLastError();
 }
