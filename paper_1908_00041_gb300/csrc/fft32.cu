@@ -218,6 +218,37 @@ __device__ __forceinline__ void split3f(float f, unsigned short &h, unsigned sho
     l = __bfloat16_as_ushort(bl);
 }
 
+// 8 floats (one core-matrix row) as three bf16 pieces of 16 bytes
+__device__ __forceinline__ void pack_row3(const float (&v)[8], uint4 (&out)[3])
+{
+    unsigned w[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned short h0, m0, l0, h1, m1, l1;
+        split3f(v[2 * i], h0, m0, l0);
+        split3f(v[2 * i + 1], h1, m1, l1);
+        w[0][i] = (unsigned)h0 | ((unsigned)h1 << 16);
+        w[1][i] = (unsigned)m0 | ((unsigned)m1 << 16);
+        w[2][i] = (unsigned)l0 | ((unsigned)l1 << 16);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[q] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+}
+
+// The forward DFT's B-operand records (96 bytes per order: parity x piece x 16 bytes)
+// are staged per warp in shared memory and stored as consecutive 16-byte chunks: the
+// records of a warp's 32 consecutive orders are 3 KB of consecutive bytes, which a direct
+// per-thread store would touch at a 96-byte stride (24 cache lines per instruction).
+constexpr int kRecUint4 = 6;                               // 16-byte chunks per record
+constexpr int kStageBytes = (kFftThreads / 32) * 32 * kRecUint4 * 16;   // 24 KB
+
+__device__ __forceinline__ void flush_records(unsigned char *__restrict__ dst, const uint4 *stg, int nrec, int lane)
+{
+    __syncwarp();
+    for (int i = lane; i < nrec * kRecUint4; i += 32) reinterpret_cast<uint4 *>(dst)[i] = stg[i];
+    __syncwarp();
+}
+
 // write 8 floats (one core-matrix row) as three bf16 pieces
 __device__ __forceinline__ void store_row3(unsigned char *dst, const float (&v)[8], int piece_bytes)
 {
@@ -239,10 +270,24 @@ __device__ __forceinline__ void store_row3(unsigned char *dst, const float (&v)[
 
 constexpr int kLoadBatch = 8;    // independent global loads per thread in flight
 
-// grid: B * J CTAs (field-major); shared: 4 * n float2 (+ padding for LOG2N > 0).
-// LOG2N > 0 selects the power-of-two engine, 0 the generic mixed-radix one.
+// bytes of the DFT buffer of 4 rings of n points (padded for the power-of-two engine)
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
+__host__ __device__ constexpr int fft_smem_bytes(int n)
+{
+    return (LOG2N > 0 ? 4 * n + 4 * n / 16 : 4 * n) * 8;
+}
+
+// Blocks per SM the DFT kernels are compiled for.  At 3 (85 registers) the n = 2048
+// instantiations spill about 128 bytes per thread in the first radix-16 stage; they get
+// the 111 registers they need at 2 (inverse DFT at L = 1023: 1.05 -> 0.79 ms), and the
+// forward kernel's 24 KB record staging allows only 2 of them per SM there anyway.
+template <int LOG2N>
+constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
+
+// grid: B * J CTAs (field-major); shared: 4 * n float2 (+ padding for LOG2N > 0) and the
+// record staging.  LOG2N > 0 selects the power-of-two engine, 0 the generic one.
+template <int LOG2N>
+__global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft_fwd_bf16(
     const float2 *__restrict__ Tth, const float2 *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
     const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf,
@@ -289,40 +334,46 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_fft_fwd_bf16(
     const float w = omega[j];
     // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 96;
-    for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
-        float vp[8], vm[8];
-        // n % 8 = c*4 + s*2 + im ; s = 0: +mu (bin mu), s = 1: -mu (bin n - mu, or 0 at mu = 0)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint4 *stg = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)) +
+                 warp * 32 * kRecUint4;
+    for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
+        const int mu = mu0 + lane;
+        if (mu <= L) {
+            float vp[8], vm[8];
+            // n % 8 = c*4 + s*2 + im ; s = 0: +mu (bin mu), s = 1: -mu (bin n - mu, or 0 at mu = 0)
 #pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-            const int bin = (sgn == 0 || mu == 0) ? mu : n - mu;
-            const int pos = LOG2N > 0 ? bin : __ldg(perm + bin);
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                const int bin = (sgn == 0 || mu == 0) ? mu : n - mu;
+                const int pos = LOG2N > 0 ? bin : __ldg(perm + bin);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int i0 = c * n + pos, i1 = (2 + c) * n + pos;
-                const float2 a = buf[LOG2N > 0 ? padi(i0) : i0];
-                const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(i1) : i1];
-                const int base = c * 4 + sgn * 2;
-                vp[base] = w * (a.x + z.x);
-                vp[base + 1] = w * (a.y + z.y);
-                vm[base] = eq ? 0.f : w * (a.x - z.x);
-                vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
+                for (int c = 0; c < 2; ++c) {
+                    const int i0 = c * n + pos, i1 = (2 + c) * n + pos;
+                    const float2 a = buf[LOG2N > 0 ? padi(i0) : i0];
+                    const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(i1) : i1];
+                    const int base = c * 4 + sgn * 2;
+                    vp[base] = w * (a.x + z.x);
+                    vp[base + 1] = w * (a.y + z.y);
+                    vm[base] = eq ? 0.f : w * (a.x - z.x);
+                    vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
+                }
             }
+            uint4 pk[3];
+            pack_row3(vp, pk);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) stg[lane * kRecUint4 + q] = pk[q];
+            pack_row3(vm, pk);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) stg[lane * kRecUint4 + 3 + q] = pk[q];
         }
-        unsigned char *dp = dst_base + (size_t)mu * 96;
-        store_row3(dp, vp, 16);
-        store_row3(dp + 48, vm, 16);
+        const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
+        flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
     }
 }
 
 // grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
-// Inverse kernels: 2 blocks per SM.  At 3 (85 registers) the n = 2048 instantiation
-// spills about 128 bytes per thread (the first radix-16 stage); with the registers it
-// needs (111) the inverse DFT at L = 1023 runs in 0.79 ms instead of 1.05 ms (the forward
-// kernel does not gain and keeps 3).
-constexpr int kInvBlocksPerSm = 2;
-
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, kInvBlocksPerSm) k_fft_inv_bf16(
+__global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft_inv_bf16(
     const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
     const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
     int nlat, int J, int has_eq, int JP, const long long *__restrict__ toff)
@@ -436,7 +487,7 @@ __device__ __forceinline__ void store_v(float *p, const float (&v)[V])
 
 // grid: ceil(B / 2) * J CTAs (pair-major); shared as for the complex kernel
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
+__global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rfft_fwd_bf16(
     const float *__restrict__ Tth, const float *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
     const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B)
@@ -486,31 +537,43 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
     else dif_f32<false>(buf, tw, rp, nr);
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
-    for (int mu = threadIdx.x; mu <= L; mu += blockDim.x) {
-        const int bp = mu, bm = mu == 0 ? 0 : n - mu;
-        const int pp = LOG2N > 0 ? bp : __ldg(perm + bp), pm = LOG2N > 0 ? bm : __ldg(perm + bm);
-        float vp[8], vm[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint4 *stg = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)) +
+                 warp * 32 * kRecUint4;
+    for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
+        const int mu = mu0 + lane;
+        if (mu <= L) {
+            const int bp = mu, bm = mu == 0 ? 0 : n - mu;
+            const int pp = LOG2N > 0 ? bp : __ldg(perm + bp), pm = LOG2N > 0 ? bm : __ldg(perm + bm);
+            float vp[8], vm[8];
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            const int e0 = f * n + pp, e1 = f * n + pm, e2 = (2 + f) * n + pp, e3 = (2 + f) * n + pm;
-            const float2 a = buf[LOG2N > 0 ? padi(e0) : e0], a2 = buf[LOG2N > 0 ? padi(e1) : e1];
-            const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e2) : e2];
-            const float2 z2 = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e3) : e3];
-            // 2 F_th = Z(m) + conj Z(-m), 2 F_ph = -i (Z(m) - conj Z(-m)), rings j and j'
-            const float tjx = a.x + a2.x, tjy = a.y - a2.y, pjx = a.y + a2.y, pjy = a2.x - a.x;
-            const float tkx = z.x + z2.x, tky = z.y - z2.y, pkx = z.y + z2.y, pky = z2.x - z.x;
-            vp[f * 2] = w * (tjx + tkx);
-            vp[f * 2 + 1] = w * (tjy + tky);
-            vp[4 + f * 2] = w * (pjx + pkx);
-            vp[4 + f * 2 + 1] = w * (pjy + pky);
-            vm[f * 2] = eq ? 0.f : w * (tjx - tkx);
-            vm[f * 2 + 1] = eq ? 0.f : w * (tjy - tky);
-            vm[4 + f * 2] = eq ? 0.f : w * (pjx - pkx);
-            vm[4 + f * 2 + 1] = eq ? 0.f : w * (pjy - pky);
+            for (int f = 0; f < 2; ++f) {
+                const int e0 = f * n + pp, e1 = f * n + pm, e2 = (2 + f) * n + pp, e3 = (2 + f) * n + pm;
+                const float2 a = buf[LOG2N > 0 ? padi(e0) : e0], a2 = buf[LOG2N > 0 ? padi(e1) : e1];
+                const float2 z = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e2) : e2];
+                const float2 z2 = eq ? make_float2(0.f, 0.f) : buf[LOG2N > 0 ? padi(e3) : e3];
+                // 2 F_th = Z(m) + conj Z(-m), 2 F_ph = -i (Z(m) - conj Z(-m)), rings j and j'
+                const float tjx = a.x + a2.x, tjy = a.y - a2.y, pjx = a.y + a2.y, pjy = a2.x - a.x;
+                const float tkx = z.x + z2.x, tky = z.y - z2.y, pkx = z.y + z2.y, pky = z2.x - z.x;
+                vp[f * 2] = w * (tjx + tkx);
+                vp[f * 2 + 1] = w * (tjy + tky);
+                vp[4 + f * 2] = w * (pjx + pkx);
+                vp[4 + f * 2 + 1] = w * (pjy + pky);
+                vm[f * 2] = eq ? 0.f : w * (tjx - tkx);
+                vm[f * 2 + 1] = eq ? 0.f : w * (tjy - tky);
+                vm[4 + f * 2] = eq ? 0.f : w * (pjx - pkx);
+                vm[4 + f * 2 + 1] = eq ? 0.f : w * (pjy - pky);
+            }
+            uint4 pk[3];
+            pack_row3(vp, pk);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stg[lane * kRecUint4 + c] = pk[c];
+            pack_row3(vm, pk);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stg[lane * kRecUint4 + 3 + c] = pk[c];
         }
-        unsigned char *dp = dst_base + (size_t)mu * 96;
-        store_row3(dp, vp, 16);
-        store_row3(dp + 48, vm, 16);
+        const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
+        flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
     }
 }
 
@@ -519,7 +582,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_rfft_fwd_bf16(
 //   Z(0) = Re G_th(0) + i Re G_ph(0),
 // so one inverse transform per field and ring yields both real components.
 template <int LOG2N>
-__global__ void __launch_bounds__(kFftThreads, kInvBlocksPerSm) k_rfft_inv_bf16(
+__global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rfft_inv_bf16(
     const float *__restrict__ S32, float *__restrict__ Tth, float *__restrict__ Tph, RadixPlanArg rp,
     const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
     int nlat, int J, int has_eq, int JP, int B)
@@ -614,8 +677,7 @@ template <int LOG2N>
 cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const int ne = 4 * p.nphi;
-    const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + kStageBytes;
     if (p.real) {
         auto k = k_rfft_fwd_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
