@@ -261,7 +261,37 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
         forms["real_fields_B%d" % Br] = measure_real(L, Br, stream)
     forms["field_a_tables"] = measure_field_a()
     forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
+    forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
     return forms
+
+
+def measure_fp64_real(L, B, stream):
+    """The FP64 path on B real fields (FAVEST_IO_R64, half-spectrum coefficients) against
+    the same fields as complex ones (FAVEST_IO_C128): fields/s of adj + fwd steps."""
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    out = {}
+    for name, io in (("real", api.FAVEST_IO_R64), ("complex", api.FAVEST_IO_C128)):
+        p = api.Plan(L, B, api.FAVEST_FP64, io)
+        if p.real:
+            ha, hb = synthetic.half_coefficients(L, B, seed=1, decay=1.0)
+        else:
+            ha, hb = synthetic.coefficients(L, B, seed=1, decay=1.0)
+        a = torch.as_tensor(ha).cuda()
+        b = torch.as_tensor(hb).cuda()
+        tt = torch.empty(p.field_shape(), dtype=p.fdtype, device="cuda")
+        tp = torch.empty_like(tt)
+        ra, rb = torch.empty_like(a), torch.empty_like(b)
+
+        def step():
+            p.adj(a, b, tt, tp, stream=stream)
+            p.fwd(tt, tp, ra, rb, stream=stream)
+        ms = time_steps(step, 5, 2, stream)
+        err = float(max((ra - a).abs().max() / a.abs().max(), (rb - b).abs().max() / b.abs().max()))
+        out[name] = {"fields_per_s": B / (ms * 1e-3), "ms_per_step": ms, "roundtrip_max_rel": err}
+        p.close()
+    out["real_speedup"] = out["real"]["fields_per_s"] / out["complex"]["fields_per_s"]
+    return out
 
 
 def measure_cg_route(L, stream):

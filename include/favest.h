@@ -29,10 +29,10 @@
  *   complex = interleaved (re, im); element type set by the plan's io type:
  *       FAVEST_IO_C128 = double, FAVEST_IO_C64 = float.
  *
- * Real fields (FAVEST_IO_R32; the paper's fields are real, T_k in R^3, Sec. 3): both
- * components are real planes [batch][nlat][nphi] of float, and since then
+ * Real fields (FAVEST_IO_R32 / FAVEST_IO_R64; the paper's fields are real, T_k in R^3,
+ * Sec. 3): both components are real planes [batch][nlat][nphi] of float / double, and since then
  * a_{l,-m} = (-1)^m conj(a_lm) (likewise b), only orders m >= 0 are stored:
- *       a, b: [batch][L(L+3)/2] complex float, l-major: index l(l+1)/2 - 1 + m
+ *       a, b: [batch][L(L+3)/2] complex float / double, l-major: index l(l+1)/2 - 1 + m
  *       for l = 1..L, m = 0..l.
  * The forward transform of a real field returns exactly these entries of the complex
  * transform (a_l0 and b_l0 are real).  The adjoint evaluates the real field
@@ -87,7 +87,8 @@ enum favest_precision {
 enum favest_io_type {
     FAVEST_IO_C128 = 0,  /* complex double */
     FAVEST_IO_C64 = 1,   /* complex float  */
-    FAVEST_IO_R32 = 2    /* real fields (float), half-spectrum complex float coefficients */
+    FAVEST_IO_R32 = 2,   /* real fields (float), half-spectrum complex float coefficients */
+    FAVEST_IO_R64 = 3    /* real fields (double), half-spectrum complex double coefficients */
 };
 
 /*
@@ -104,8 +105,9 @@ int favest_gl_grid(int nlat, double *x, double *w);
  * requires io_type FAVEST_IO_C64 or FAVEST_IO_R32 (FAVEST_EUNSUPPORTED otherwise) and
  * a device with tcgen05 tensor cores (sm_100 family), and its FP32 longitude DFT takes
  * nphi = 2(L+1) with prime factors up to 128 only (FAVEST_EUNSUPPORTED otherwise, e.g.
- * L = 150: nphi = 2 * 151); FAVEST_IO_R32 requires FAVEST_BF16X6 (FAVEST_EUNSUPPORTED
- * otherwise).
+ * L = 150: nphi = 2 * 151); FAVEST_IO_R64 requires FAVEST_FP64 (FAVEST_EUNSUPPORTED
+ * otherwise), FAVEST_IO_R32 works with both precisions.  Real-field plans take 16-byte
+ * aligned pointers.
  *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
  *       and latitude weights; NULL selects the built-in Gauss-Legendre rule.  When
  *       given, the nodes must lie strictly inside (-1, 1) and both arrays must be

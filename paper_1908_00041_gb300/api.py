@@ -27,6 +27,7 @@ FAVEST_BF16X6 = 1
 FAVEST_IO_C128 = 0
 FAVEST_IO_C64 = 1
 FAVEST_IO_R32 = 2
+FAVEST_IO_R64 = 3
 FAVEST_FLAG_UNIT_WEIGHTS = 1
 FAVEST_FLAG_WEIGHTED = 2
 FAVEST_BATCH_AUTOTUNE = 1
@@ -254,10 +255,10 @@ class Plan:
         self.L, self.batch, self.precision, self.io_type = int(L), int(batch), precision, io_type
         self.nlat, self.nphi = L + 1, 2 * (L + 1)
         # real fields keep orders m >= 0 only: L(L+3)/2 coefficients per family
-        self.real = io_type == FAVEST_IO_R32
+        self.real = io_type in (FAVEST_IO_R32, FAVEST_IO_R64)
         self.K = L * (L + 3) // 2 if self.real else L * L + 2 * L
-        self.cdtype = torch.complex128 if io_type == FAVEST_IO_C128 else torch.complex64
-        self.fdtype = torch.float32 if self.real else self.cdtype
+        self.cdtype = torch.complex128 if io_type in (FAVEST_IO_C128, FAVEST_IO_R64) else torch.complex64
+        self.fdtype = {FAVEST_IO_R32: torch.float32, FAVEST_IO_R64: torch.float64}.get(io_type, self.cdtype)
         self.handle = favest_plan_create(L, batch, precision, io_type, cos_theta, w_lat)
         self._unit = 0
 

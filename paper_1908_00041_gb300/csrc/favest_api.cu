@@ -507,7 +507,8 @@ int alloc_workspace(Plan &p)
     const int nmu = p.L + 1 + (p.nscal > 0 ? 1 : 0);
     size_t fbytes = (size_t)nmu * p.ncol * p.nlat * sizeof(double2);
     size_t qbytes = (size_t)p.ntab * p.ncol * sizeof(double2);
-    size_t gbytes = (size_t)(p.ncol / 4) * 2 * p.nlat * p.nphi * sizeof(double2);
+    // inverse DFT rows: 2 per group of 4 columns, or 2 per real field (2 fields per group)
+    size_t gbytes = (size_t)(p.real ? p.ncol : p.ncol / 2) * p.nlat * p.nphi * sizeof(double2);
     if (cudaMalloc(&p.d_F, fbytes) != cudaSuccess || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
         cudaMalloc(&p.d_G, gbytes) != cudaSuccess ||
         cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
@@ -515,8 +516,10 @@ int alloc_workspace(Plan &p)
         return FAVEST_ENOMEM;
     }
     cudaMemset(p.d_status, 0, sizeof(int));
-    // the CG route's padding columns (an odd count of scalar fields) read as zero
-    if (p.nscal > 0 && cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess) return FAVEST_ECUDA;
+    // the padding columns (an odd count of scalar or real fields) read as zero
+    if ((p.nscal > 0 || p.real) &&
+        (cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess || cudaMemset(p.d_F, 0, fbytes) != cudaSuccess))
+        return FAVEST_ECUDA;
     p.ws_bytes = fbytes + qbytes + gbytes;
     return FAVEST_OK;
 }
@@ -606,7 +609,8 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
     if (L > 1023) return FAVEST_EUNSUPPORTED;
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
-    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64 && io_type != FAVEST_IO_R32) return FAVEST_EINVAL;
+    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64 && io_type != FAVEST_IO_R32 && io_type != FAVEST_IO_R64)
+        return FAVEST_EINVAL;
     if ((cos_theta == nullptr) != (w_lat == nullptr)) return FAVEST_EINVAL;
     const int nlat = L + 1;
     if (cos_theta) {
@@ -618,8 +622,9 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
             if (j > 0 && !(cos_theta[j] < cos_theta[j - 1])) return FAVEST_EINVAL;
         }
     }
-    if (precision == FAVEST_BF16X6 && io_type == FAVEST_IO_C128) return FAVEST_EUNSUPPORTED;
-    if (precision != FAVEST_BF16X6 && io_type == FAVEST_IO_R32) return FAVEST_EUNSUPPORTED;
+    if (precision == FAVEST_BF16X6 && (io_type == FAVEST_IO_C128 || io_type == FAVEST_IO_R64)) return FAVEST_EUNSUPPORTED;
+    const bool real_io = io_type == FAVEST_IO_R32 || io_type == FAVEST_IO_R64;
+    if (real_io && cg_route) return FAVEST_EINVAL;
 
     favest_plan_s *h = new (std::nothrow) favest_plan_s();
     if (!h) return FAVEST_ENOMEM;
@@ -629,13 +634,14 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     p.B = batch;
     p.precision = precision;
     p.io = io_type;
-    p.real = io_type == FAVEST_IO_R32;
+    p.real = real_io ? 1 : 0;
     p.ncg = p.real ? (batch + 1) / 2 : batch;
     p.nlat = nlat;
     p.nphi = 2 * (L + 1);
     p.J = (nlat + 1) / 2;
     p.has_eq = nlat & 1;
     p.ncol = 4 * batch;
+    if (p.real) p.ncol = 4 * ((batch + 1) / 2);   // a pair of real fields per group of 4 columns
     if (cg_route) {
         // 3 scalar fields per vector field, 2 per group of 4 columns (sign of m, re/im)
         p.nscal = 3 * batch;
@@ -718,7 +724,7 @@ int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, v
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;     // Clebsch-Gordan plans take favest_fwd_cart
     FlagScope unit(p.unit_weights, p.unit_weights | ((flags & FAVEST_FLAG_UNIT_WEIGHTS) ? 1 : 0));
-    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
+    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6 || p.real) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
     if (st) return st;
@@ -744,7 +750,7 @@ int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, voi
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;
     FlagScope weighted(p.adj_weighted, (flags & FAVEST_FLAG_WEIGHTED) ? 1 : 0);
-    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6) ? 16 : 8;
+    size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6 || p.real) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
     if (st) return st;
@@ -925,7 +931,10 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         } else return FAVEST_EINVAL;
         return FAVEST_OK;
     }
-    const double io = p.io == FAVEST_IO_C128 ? 16.0 : 8.0;
+    // field and coefficient element bytes
+    const double io = p.io == FAVEST_IO_C128 ? 16.0 : (p.io == FAVEST_IO_R32 ? 4.0 : 8.0);
+    const double cio = (p.io == FAVEST_IO_C128 || p.io == FAVEST_IO_R64) ? 16.0 : 8.0;
+    const double kc = p.real ? (double)p.L * (p.L + 3) / 2.0 : K;
     // component planes: 2 per field, or the 3 Cartesian scalar fields of the CG route
     const double planes = p.nscal > 0 ? (double)p.nscal : 2.0 * B;
     const double grid = planes * nlat * nphi * io;
@@ -934,15 +943,15 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
     const double gbuf = p.ncol / 2.0 * nlat * nphi * 16.0;
     // per step: 2 recurrence instructions + 2 FMAs (re, im) per column
     const double leg = steps * (4.0 + 4.0 * p.ncol);
-    const double fftf = planes * nlat * 5.0 * nphi * std::log2(nphi);
+    const double fftf = (p.real ? B : planes) * nlat * 5.0 * nphi * std::log2(nphi);
     if (k == "fft_fwd") { *bytes = grid + fbuf; *flops = fftf; }
     else if (k == "fft_inv") { *bytes = gbuf + grid; *flops = fftf; }
     else if (k == "legendre_analysis") { *bytes = fbuf + qbuf; *flops = leg; *pipe = 1; }
     else if (k == "legendre_synthesis") { *bytes = qbuf + gbuf; *flops = leg; *pipe = 1; }
-    else if (k == "combine") { *bytes = qbuf + 2.0 * B * K * io; *flops = 16.0 * B * K; }
-    else if (k == "uncombine") { *bytes = 2.0 * B * K * io + qbuf; *flops = 24.0 * B * K; }
-    else if (k == "cg_combine") { *bytes = qbuf + 2.0 * B * K * io; *flops = 120.0 * B * K; }
-    else if (k == "cg_uncombine") { *bytes = 2.0 * B * K * io + qbuf; *flops = 120.0 * B * (L + 2) * (L + 2); }
+    else if (k == "combine") { *bytes = qbuf + 2.0 * B * kc * cio; *flops = 16.0 * B * kc; }
+    else if (k == "uncombine") { *bytes = 2.0 * B * kc * cio + qbuf; *flops = 24.0 * B * kc; }
+    else if (k == "cg_combine") { *bytes = qbuf + 2.0 * B * K * cio; *flops = 120.0 * B * K; }
+    else if (k == "cg_uncombine") { *bytes = 2.0 * B * K * cio + qbuf; *flops = 120.0 * B * (L + 2) * (L + 2); }
     else return FAVEST_EINVAL;
     return FAVEST_OK;
 }

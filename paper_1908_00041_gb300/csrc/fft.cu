@@ -88,6 +88,73 @@ __global__ void __launch_bounds__(256) k_fft_inv_fp64(
     }
 }
 
+// Real fields.  Ring (field b, j) carries z = T_th + i T_ph (both real), whose spectrum Z
+// gives both component spectra: F_th(m) = (Z(m) + conj Z(-m)) / 2, F_ph(m) = (Z(m) -
+// conj Z(-m)) / (2i), kept for m = 0..L (F(-m) = conj F(m)).  The fields 2q and 2q+1 share
+// the column group of 4 of pair q: col = (q*2 + c)*2 + (b % 2).
+template <typename TR>
+__global__ void __launch_bounds__(256) k_rfft_fwd_fp64(
+    const TR *__restrict__ Tth, const TR *__restrict__ Tph, double2 *__restrict__ Fraw, RadixPlanArg rp,
+    const double2 *__restrict__ tw, int L, int nlat, int ncol)
+{
+    extern __shared__ double2 sm_fft[];
+    const int n = rp.n;
+    const int ring = blockIdx.x;               // b * nlat + j
+    const int j = ring % nlat, b = ring / nlat;
+    const TR *st = Tth + (size_t)ring * n, *sp = Tph + (size_t)ring * n;
+    double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = make_double2((double)st[k], (double)sp[k]);
+    __syncthreads();
+    const double2 *out = stockham<false>(buf0, buf1, tw, rp);
+    const int q = b >> 1, f = b & 1;
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        const double2 z = out[m], zc = out[m == 0 ? 0 : n - m];
+        const double2 fth = make_double2(0.5 * (z.x + zc.x), 0.5 * (z.y - zc.y));
+        const double2 fph = make_double2(0.5 * (z.y + zc.y), 0.5 * (zc.x - z.x));
+        const size_t base = (size_t)m * ncol;
+        Fraw[(base + (q * 2 + 0) * 2 + f) * nlat + j] = fth;
+        Fraw[(base + (q * 2 + 1) * 2 + f) * nlat + j] = fph;
+    }
+}
+
+// Real fields, inverse: the synthesis leaves G_c(j, m), m = 0..L, in row b*2 + c; the
+// spectrum of z = T_th + i T_ph is Z(m) = G_th(m) + i G_ph(m), Z(-m) = conj G_th(m) +
+// i conj G_ph(m) (m >= 1), Z(0) = Re G_th(0) + i Re G_ph(0), and the Nyquist bin 0.
+template <typename TR>
+__global__ void __launch_bounds__(256) k_rfft_inv_fp64(
+    const double2 *__restrict__ G, TR *__restrict__ Tth, TR *__restrict__ Tph, RadixPlanArg rp,
+    const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat)
+{
+    extern __shared__ double2 sm_fft[];
+    const int n = rp.n;
+    const int ring = blockIdx.x;               // b * nlat + j
+    const int j = ring % nlat, b = ring / nlat;
+    const double2 *gt = G + ((size_t)(b * 2 + 0) * nlat + j) * n;
+    const double2 *gp = G + ((size_t)(b * 2 + 1) * nlat + j) * n;
+    double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double2 v = make_double2(0.0, 0.0);
+        if (k == 0) {
+            v = make_double2(gt[0].x, gp[0].x);
+        } else if (k <= L) {
+            const double2 a = gt[k], c = gp[k];
+            v = make_double2(a.x - c.y, a.y + c.x);
+        } else if (k > L + 1) {
+            const double2 a = gt[n - k], c = gp[n - k];
+            v = make_double2(a.x + c.y, c.x - a.y);
+        }
+        buf0[k] = v;
+    }
+    __syncthreads();
+    const double2 *out = stockham<true>(buf0, buf1, tw, rp);
+    const double w = wring ? wring[j] : 1.0;
+    TR *dt = Tth + (size_t)ring * n, *dp = Tph + (size_t)ring * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        dt[k] = (TR)(w * out[k].x);
+        dp[k] = (TR)(w * out[k].y);
+    }
+}
+
 int fft_threads(int n) { return n >= 512 ? 256 : (n >= 128 ? 128 : 64); }
 
 }  // namespace
@@ -95,6 +162,22 @@ int fft_threads(int n) { return n >= 512 ? 256 : (n >= 128 ? 128 : 64); }
 cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
+    if (p.real) {
+        const size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
+        const int th = fft_threads(p.nphi);
+        if (p.io == FAVEST_IO_R64) {
+            auto k = k_rfft_fwd_fp64<double>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<p.B * p.nlat, th, smem, s>>>((const double *)Tth, (const double *)Tph, (double2 *)p.d_F, rp,
+                                             p.fft.tw64, p.L, p.nlat, p.ncol);
+        } else {
+            auto k = k_rfft_fwd_fp64<float>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<p.B * p.nlat, th, smem, s>>>((const float *)Tth, (const float *)Tph, (double2 *)p.d_F, rp,
+                                             p.fft.tw64, p.L, p.nlat, p.ncol);
+        }
+        return cudaGetLastError();
+    }
     int grid = p.ncol / 4 * 2 * p.nlat;        // rings: 2 per group of 4 columns (b, c)
     size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
     int th = fft_threads(p.nphi);
@@ -115,6 +198,23 @@ cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph,
 cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
+    if (p.real) {
+        const size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
+        const int th = fft_threads(p.nphi);
+        const double *wr = p.adj_weighted ? p.d_wring : nullptr;
+        if (p.io == FAVEST_IO_R64) {
+            auto k = k_rfft_inv_fp64<double>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<p.B * p.nlat, th, smem, s>>>((const double2 *)p.d_G, (double *)Tth, (double *)Tph, rp, p.fft.tw64,
+                                             wr, p.L, p.nlat);
+        } else {
+            auto k = k_rfft_inv_fp64<float>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k<<<p.B * p.nlat, th, smem, s>>>((const double2 *)p.d_G, (float *)Tth, (float *)Tph, rp, p.fft.tw64,
+                                             wr, p.L, p.nlat);
+        }
+        return cudaGetLastError();
+    }
     int grid = p.ncol / 4 * 2 * p.nlat;
     size_t smem = 2 * (size_t)p.nphi * sizeof(double2);
     int th = fft_threads(p.nphi);

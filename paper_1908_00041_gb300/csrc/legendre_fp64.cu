@@ -146,12 +146,13 @@ constexpr int kSynJpt = 2;        // J <= 512
 // Adjoint Legendre stage.  gtab: [tab][ncol] scaled coefficients; G: [B][2][nlat][nphi].
 // Vector mode divides the sums by sin(theta_j).  Scalar mode (the Clebsch-Gordan route)
 // does not, and order L+1 exists there: its orders +-(L+1) share the Nyquist bin, so the
-// two sign columns are added into it.
+// two sign columns are added into it.  Real fields (real != 0): column (q*2 + c)*2 + f is
+// component c of field 2q + f at m = +mu, written to row (2q + f)*2 + c at bin mu.
 template <int CT>
 __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     const double2 *__restrict__ gtab, double2 *__restrict__ G, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
-    int L, int nlat, int nphi, int J, int has_eq, int ncol, int ng, int scalar)
+    int L, int nlat, int nphi, int J, int has_eq, int ncol, int ng, int scalar, int real)
 {
     extern __shared__ double sm_syn[];
     const int mu = blockIdx.x / ng, g = blockIdx.x % ng;
@@ -226,9 +227,10 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
 #pragma unroll
         for (int ct = 0; ct < CT; ++ct) {
             const int col = g * CT + ct;
-            const int s = col & 1, bc = col >> 1;     // bc = b*2 + component
-            if ((mu == 0 || nyq) && s == 1) continue;
-            const int bin = s ? nphi - mu : mu;
+            const int s = col & 1;
+            const int bc = real ? ((col >> 2) * 2 + s) * 2 + ((col >> 1) & 1) : col >> 1;   // output row
+            if (!real && (mu == 0 || nyq) && s == 1) continue;
+            const int bin = (s && !real) ? nphi - mu : mu;
             double2 e = accE[i][ct], o = accO[i][ct];
             if (nyq && ct + 1 < CT) {                 // add the m = -(L+1) column (ct + 1)
                 e.x += accE[i][ct + 1].x;
@@ -284,7 +286,7 @@ cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
                                           p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng, p.nscal > 0);
+                                          p.ng, p.nscal > 0, p.real);
     } else {
         constexpr int CT = 4;
         size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
@@ -292,7 +294,7 @@ cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
                                           p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng, p.nscal > 0);
+                                          p.ng, p.nscal > 0, p.real);
     }
     return cudaGetLastError();
 }

@@ -167,3 +167,58 @@ def test_real_l1023_vs_fp64_complex(decay):
     assert normwise_err(got_p, _h(cp).real.reshape(len(pick), -1)) < TOL
     assert normwise_err(_h(ra)[pick], half_of_full(_h(ca), L)) < TOL
     assert normwise_err(_h(rb)[pick], half_of_full(_h(cb), L)) < TOL
+
+
+# ---------------------------------------------------------------------------
+# FP64 path on real fields (FAVEST_IO_R64 and FAVEST_IO_R32): bar 1e-12 against the FP64
+# complex path on the same input
+# ---------------------------------------------------------------------------
+def _f64(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(torch.float64).cuda().contiguous()
+
+
+def _c128(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(torch.complex128).cuda().contiguous()
+
+
+@pytest.mark.parametrize("L,B", [(1, 1), (2, 3), (16, 5), (31, 2), (100, 3), (255, 4)])
+def test_fp64_real_vs_complex(L, B):
+    tt, tp = synthetic.real_grid_field(L, B, 1300 + L)
+    a, b = synthetic.half_coefficients(L, B, 1400 + L)
+    pr = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_R64)
+    pc = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_C128)
+    ra, rb = pr.fwd(_f64(tt), _f64(tp))
+    ca, cb = pc.fwd(_c128(tt + 0j), _c128(tp + 0j))
+    st, sp = pr.adj(_c128(a), _c128(b))
+    ct, cp = pc.adj(_c128(full_of_half(a, L)), _c128(full_of_half(b, L)))
+    torch.cuda.synchronize()
+    assert pr.status() == 0 and pc.status() == 0
+    assert normwise_err(_h(ra), half_of_full(_h(ca), L)) < 1e-12
+    assert normwise_err(_h(rb), half_of_full(_h(cb), L)) < 1e-12
+    assert normwise_err(st.cpu().numpy().reshape(B, -1), _h(ct).real.reshape(B, -1)) < 1e-12
+    assert normwise_err(sp.cpu().numpy().reshape(B, -1), _h(cp).real.reshape(B, -1)) < 1e-12
+    # roundtrip on the exact grid, and R32 I/O (float fields, complex64 coefficients)
+    a2, b2 = pr.fwd(st, sp)
+    p32 = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_R32)
+    t32, q32 = p32.adj(_c64(a), _c64(b))
+    torch.cuda.synchronize()
+    assert normwise_err(_h(a2), a) < 1e-12 and normwise_err(_h(b2), b) < 1e-12
+    assert normwise_err(t32.cpu().numpy().astype(np.float64).reshape(B, -1), st.cpu().numpy().reshape(B, -1)) < 1e-6
+
+
+def test_fp64_real_vs_oracle(orc):
+    L, B = 24, 2
+    x, W, theta, phi = orc.grid(L)
+    tt, tp = synthetic.real_grid_field(L, B, 1500)
+    pr = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_R64)
+    ra, rb = pr.fwd(_f64(tt), _f64(tp))
+    a, b = synthetic.half_coefficients(L, B, 1501)
+    st, sp = pr.adj(_c128(a), _c128(b))
+    torch.cuda.synchronize()
+    for f in range(B):
+        oa, ob = orc.fwd_sep(L, x, W, tt[f] + 0j, tp[f] + 0j)
+        assert normwise_err(_h(ra)[f], half_of_full(oa, L)) < 1e-12
+        assert normwise_err(_h(rb)[f], half_of_full(ob, L)) < 1e-12
+        ot, op = orc.adj_sep(L, x, full_of_half(a[f], L), full_of_half(b[f], L), len(phi))
+        assert normwise_err(st.cpu().numpy()[f].ravel(), ot.real.ravel()) < 1e-12
+        assert normwise_err(sp.cpu().numpy()[f].ravel(), op.real.ravel()) < 1e-12
