@@ -76,3 +76,25 @@ def test_null_plan_calls(lib):
     assert L.favest_set_weights_unit(nul, 0) == api.FAVEST_EINVAL
     assert L.favest_status(nul, nul) == api.FAVEST_EINVAL
     L.favest_plan_destroy(nul)
+
+
+def test_new_entry_points_reject_bad_arguments(lib):
+    """Entry points of the real-field, Clebsch-Gordan and batch forms: NULL plans and
+    invalid requests come back as status codes without touching a device."""
+    L = api.lib()
+    nul = ctypes.c_void_p(None)
+    h = ctypes.c_void_p()
+    assert L.favest_fwd_cart(nul, nul, nul, nul, nul) == api.FAVEST_EINVAL
+    assert L.favest_adj_cart(nul, nul, nul, nul, nul) == api.FAVEST_EINVAL
+    assert L.favest_fwd_ex(nul, nul, nul, nul, nul, 0, nul) == api.FAVEST_EINVAL
+    assert L.favest_adj_ex(nul, nul, nul, nul, nul, 0, nul) == api.FAVEST_EINVAL
+    assert L.favest_cg_plan_create(16, 1, None, None, None) == api.FAVEST_EINVAL
+    assert L.favest_cg_plan_create(0, 1, None, None, ctypes.byref(h)) == api.FAVEST_EINVAL
+    assert L.favest_cg_plan_create(16, 5000, None, None, ctypes.byref(h)) == api.FAVEST_EINVAL
+    # real fields with the CG route, complex128 or real double with split precision
+    assert _create(16, 1, prec=api.FAVEST_BF16X6, io=api.FAVEST_IO_C128)[0] == api.FAVEST_EUNSUPPORTED
+    assert _create(16, 1, prec=api.FAVEST_BF16X6, io=api.FAVEST_IO_R64)[0] == api.FAVEST_EUNSUPPORTED
+    Ls = (ctypes.c_int * 2)(16, 31)
+    assert L.favest_batch_create(2, Ls, None, None, api.FAVEST_BF16X6, api.FAVEST_IO_R32, 0,
+                                 ctypes.byref(h)) == api.FAVEST_EUNSUPPORTED
+    assert L.favest_kernel_work(nul, b"fft_fwd", None, None, None) == api.FAVEST_EINVAL
