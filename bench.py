@@ -168,6 +168,23 @@ def kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B):
 # the other forms: FP64 path at the same workload, the two FP64 configurations, the
 # ragged batch (each a few CUDA-event-timed steps after warm-up)
 # ---------------------------------------------------------------------------
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (replicas: the job takes as long as its slowest
+    rank); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank units
+    in at most `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def time_steps(fn, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -600,12 +617,8 @@ def main():
     prof = plan.profile_read()
     plan.profile(False)
     assert plan.status() == 0
-    ms = e0.elapsed_time(e1) / steps
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
+    value = replica_throughput(B, world, ms * 1e-3)
     launches = steps * (plan.launches_per_call(0) + plan.launches_per_call(1))
 
     # roofline: every kernel's algorithmic work (favest_kernel_work) per launch over its
@@ -664,14 +677,10 @@ def main():
         for k in range(ke):
             e2e_step(k)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / ke
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / ke, dist, "cuda")
         nbytes = ha.numel() * 8 * 2
         assert torch.equal(oa[(ke - 1) % 2], ra[(ke - 1) % 2].cpu())
-        e2e = {"value": world * B / dt, "unit": "fields/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": replica_throughput(B, world, dt), "unit": "fields/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": ke,
                "pipelined": "copy-in / compute / copy-out on three streams, two buffer slots"}
         del da, db, ra, rb
