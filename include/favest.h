@@ -186,10 +186,19 @@ int favest_set_weights_unit(favest_plan plan, int flag);
  *                        which multiplies the synthesised field by W in the inverse
  *                        longitude DFT stage;
  *   d/dc of AdjVSHT  is  A^H:              favest_fwd_ex with FAVEST_FLAG_UNIT_WEIGHTS.
+ * Real-field plans (FAVEST_IO_R32/R64) map real fields to half spectra, and their
+ * transposes for the real inner products (Re sum conj(u) v on coefficients) add a factor
+ * per order, which FAVEST_FLAG_REAL_TRANSPOSE applies:
+ *   favest_adj_ex: orders m > 0 of a, b enter with weight 1/2, so that with
+ *     FAVEST_FLAG_WEIGHTED the call computes W Re sum_{m >= 0} (a_lm Y^div + b_lm Y^curl),
+ *     the transpose of the real FwdVSHT;
+ *   favest_fwd_ex: orders m > 0 of the result are doubled, so that with
+ *     FAVEST_FLAG_UNIT_WEIGHTS the call is the transpose of the real AdjVSHT.
+ * The factors 1/2 and 2 are exact.  On complex plans the flag is FAVEST_EINVAL.
  * Any other flag bit is FAVEST_EINVAL.  Calls on one plan must not overlap in time on
  * the host (the flags live in the plan for the duration of the call).
  */
-enum { FAVEST_FLAG_UNIT_WEIGHTS = 1, FAVEST_FLAG_WEIGHTED = 2 };
+enum { FAVEST_FLAG_UNIT_WEIGHTS = 1, FAVEST_FLAG_WEIGHTED = 2, FAVEST_FLAG_REAL_TRANSPOSE = 4 };
 int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags,
                   void *stream);
 int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags,

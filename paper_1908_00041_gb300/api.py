@@ -30,6 +30,7 @@ FAVEST_IO_R32 = 2
 FAVEST_IO_R64 = 3
 FAVEST_FLAG_UNIT_WEIGHTS = 1
 FAVEST_FLAG_WEIGHTED = 2
+FAVEST_FLAG_REAL_TRANSPOSE = 4
 FAVEST_BATCH_AUTOTUNE = 1
 FAVEST_BATCH_GRAPH = 2
 
@@ -290,7 +291,7 @@ class Plan:
             favest_set_weights_unit(self.handle, flag)
             self._unit = flag
 
-    def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False):
+    def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False, real_transpose=False):
         import torch
         self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
         self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
@@ -300,10 +301,11 @@ class Plan:
             b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=Tth.device)
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
-        favest_fwd_ex(self.handle, Tth, Tph, a, b, FAVEST_FLAG_UNIT_WEIGHTS if unit_weights else 0, stream)
+        flags = (FAVEST_FLAG_UNIT_WEIGHTS if unit_weights else 0) | (FAVEST_FLAG_REAL_TRANSPOSE if real_transpose else 0)
+        favest_fwd_ex(self.handle, Tth, Tph, a, b, flags, stream)
         return a, b
 
-    def adj(self, a, b, Tth=None, Tph=None, stream=None, weighted=False):
+    def adj(self, a, b, Tth=None, Tph=None, stream=None, weighted=False, real_transpose=False):
         import torch
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
@@ -313,7 +315,8 @@ class Plan:
             Tph = torch.empty(self.field_shape(), dtype=self.fdtype, device=a.device)
         self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
         self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
-        favest_adj_ex(self.handle, a, b, Tth, Tph, FAVEST_FLAG_WEIGHTED if weighted else 0, stream)
+        flags = (FAVEST_FLAG_WEIGHTED if weighted else 0) | (FAVEST_FLAG_REAL_TRANSPOSE if real_transpose else 0)
+        favest_adj_ex(self.handle, a, b, Tth, Tph, flags, stream)
         return Tth, Tph
 
     def status(self, stream=None):

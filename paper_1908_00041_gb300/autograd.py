@@ -14,6 +14,12 @@ Both backward passes run the library's own kernels (favest_adj_ex with
 FAVEST_FLAG_WEIGHTED, favest_fwd_ex with FAVEST_FLAG_UNIT_WEIGHTS); the Legendre
 values are regenerated by the recurrence inside those kernels, nothing is stored
 between the forward and the backward pass.
+
+Real-field plans map real fields to half spectra (orders m >= 0).  Their vector-Jacobian
+products are the transposes for the real inner products, which add per-order factors
+(FAVEST_FLAG_REAL_TRANSPOSE): FwdVSHT back-propagates by W Re sum_{m>=0} g_lm Y_lm (the
+weighted real adjoint with orders m > 0 halved), AdjVSHT by the unit-weight real forward
+with orders m > 0 doubled.
 """
 import torch
 
@@ -21,6 +27,7 @@ from . import api
 
 
 def _contig(t, dtype):
+    """t as a contiguous tensor of the plan's dtype (None stays None)."""
     if t is None:
         return None
     return t.to(dtype).contiguous()
@@ -30,8 +37,8 @@ class _FwdVSHT(torch.autograd.Function):
     @staticmethod
     def forward(ctx, Tth, Tph, plan):
         ctx.plan = plan
-        a, b = plan.fwd(_contig(Tth, plan.cdtype), _contig(Tph, plan.cdtype),
-                        stream=torch.cuda.current_stream().cuda_stream)
+        fd = getattr(plan, "fdtype", plan.cdtype)
+        a, b = plan.fwd(_contig(Tth, fd), _contig(Tph, fd), stream=torch.cuda.current_stream().cuda_stream)
         return a, b
 
     @staticmethod
@@ -42,6 +49,7 @@ class _FwdVSHT(torch.autograd.Function):
         if gb is None:
             gb = torch.zeros(plan.coef_shape(), dtype=plan.cdtype, device="cuda")
         gt, gp = plan.adj(_contig(ga, plan.cdtype), _contig(gb, plan.cdtype), weighted=True,
+                          real_transpose=getattr(plan, "real", False),
                           stream=torch.cuda.current_stream().cuda_stream)
         return gt, gp, None
 
@@ -57,27 +65,23 @@ class _AdjVSHT(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gt, gp):
         plan = ctx.plan
+        fd = getattr(plan, "fdtype", plan.cdtype)
         if gt is None:
-            gt = torch.zeros(plan.field_shape(), dtype=plan.cdtype, device="cuda")
+            gt = torch.zeros(plan.field_shape(), dtype=fd, device="cuda")
         if gp is None:
-            gp = torch.zeros(plan.field_shape(), dtype=plan.cdtype, device="cuda")
-        ga, gb = plan.fwd(_contig(gt, plan.cdtype), _contig(gp, plan.cdtype), unit_weights=True,
+            gp = torch.zeros(plan.field_shape(), dtype=fd, device="cuda")
+        ga, gb = plan.fwd(_contig(gt, fd), _contig(gp, fd), unit_weights=True,
+                          real_transpose=getattr(plan, "real", False),
                           stream=torch.cuda.current_stream().cuda_stream)
         return ga, gb, None
 
 
-def _complex_plan(plan):
-    if getattr(plan, "real", False):
-        raise NotImplementedError("differentiation is provided for complex-field plans only")
-
-
 def fwd_vsht(plan, Tth, Tph):
-    """Differentiable FwdVSHT: (Tth, Tph) [batch, L+1, 2(L+1)] -> (a, b) [batch, L^2+2L]."""
-    _complex_plan(plan)
+    """Differentiable FwdVSHT: (Tth, Tph) [batch, L+1, 2(L+1)] -> (a, b) [batch, K]
+    (K = L^2+2L, or L(L+3)/2 for a real-field plan)."""
     return _FwdVSHT.apply(Tth, Tph, plan)
 
 
 def adj_vsht(plan, a, b):
-    """Differentiable AdjVSHT: (a, b) [batch, L^2+2L] -> (Tth, Tph) [batch, L+1, 2(L+1)]."""
-    _complex_plan(plan)
+    """Differentiable AdjVSHT: (a, b) [batch, K] -> (Tth, Tph) [batch, L+1, 2(L+1)]."""
     return _AdjVSHT.apply(a, b, plan)

@@ -100,7 +100,7 @@ __global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict_
 template <typename TO>
 __global__ void k_combine_fp64_real(const double2 *__restrict__ Q, TO *__restrict__ a, TO *__restrict__ b,
                                     const double *__restrict__ P, const double *__restrict__ M,
-                                    const double *__restrict__ R, int L, int KR, int ncol, int B)
+                                    const double *__restrict__ R, int L, int KR, int ncol, int B, double ps)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)B * KR) return;
@@ -123,8 +123,9 @@ __global__ void k_combine_fp64_real(const double2 *__restrict__ Q, TO *__restric
     }
     double2 av = make_double2(Pl * qt1.x - Ml * qtm.x + Rl * qp0.y, Pl * qt1.y - Ml * qtm.y - Rl * qp0.x);
     double2 bv = make_double2(-Rl * qt0.y + Pl * qp1.x - Ml * qpm.x, Rl * qt0.x + Pl * qp1.y - Ml * qpm.y);
-    a[(size_t)bf * KR + k] = from_d2<TO>(av);
-    b[(size_t)bf * KR + k] = from_d2<TO>(bv);
+    const double sc = mu > 0 ? ps : 1.0;   // real transpose: orders m > 0 doubled
+    a[(size_t)bf * KR + k] = from_d2<TO>(make_double2(sc * av.x, sc * av.y));
+    b[(size_t)bf * KR + k] = from_d2<TO>(make_double2(sc * bv.x, sc * bv.y));
 }
 
 template <typename TI>
@@ -138,7 +139,7 @@ __device__ __forceinline__ double2 coef_half(const TI *__restrict__ c, int L, in
 template <typename TI>
 __global__ void k_uncombine_fp64_real(const TI *__restrict__ a, const TI *__restrict__ b, double2 *__restrict__ g,
                                       const double *__restrict__ P, const double *__restrict__ M,
-                                      const double *__restrict__ R, int L, int KR, int ncol)
+                                      const double *__restrict__ R, int L, int KR, int ncol, double ps)
 {
     const int mu = blockIdx.x, bf = blockIdx.y;
     const long long t0 = tab_off(L, mu);
@@ -154,10 +155,11 @@ __global__ void k_uncombine_fp64_real(const TI *__restrict__ a, const TI *__rest
         double2 am1 = coef_half(a, L, l - 1, mu, cb), ap1 = coef_half(a, L, l + 1, mu, cb);
         double2 bm1 = coef_half(b, L, l - 1, mu, cb), bp1 = coef_half(b, L, l + 1, mu, cb);
         double2 a0 = coef_half(a, L, l, mu, cb), b0 = coef_half(b, L, l, mu, cb);
-        g[(size_t)(t0 + r) * ncol + cth] = make_double2(Pm * am1.x - Mp * ap1.x + Rl * b0.y,
-                                                        Pm * am1.y - Mp * ap1.y - Rl * b0.x);
-        g[(size_t)(t0 + r) * ncol + cph] = make_double2(-Rl * a0.y + Pm * bm1.x - Mp * bp1.x,
-                                                        Rl * a0.x + Pm * bm1.y - Mp * bp1.y);
+        const double sc = mu > 0 ? ps : 1.0;   // real transpose: orders m > 0 halved
+        g[(size_t)(t0 + r) * ncol + cth] = make_double2(sc * (Pm * am1.x - Mp * ap1.x + Rl * b0.y),
+                                                        sc * (Pm * am1.y - Mp * ap1.y - Rl * b0.x));
+        g[(size_t)(t0 + r) * ncol + cph] = make_double2(sc * (-Rl * a0.y + Pm * bm1.x - Mp * bp1.x),
+                                                        sc * (Rl * a0.x + Pm * bm1.y - Mp * bp1.y));
     }
 }
 
@@ -171,10 +173,12 @@ cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s)
         const unsigned grid = (unsigned)((n + 255) / 256);
         if (p.io == FAVEST_IO_R64)
             k_combine_fp64_real<double2><<<grid, 256, 0, s>>>((const double2 *)p.d_Q, (double2 *)a, (double2 *)b,
-                                                             p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B);
+                                                             p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B,
+                                                             p.real_transpose ? 2.0 : 1.0);
         else
             k_combine_fp64_real<float2><<<grid, 256, 0, s>>>((const double2 *)p.d_Q, (float2 *)a, (float2 *)b,
-                                                            p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B);
+                                                            p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B,
+                                                            p.real_transpose ? 2.0 : 1.0);
         return cudaGetLastError();
     }
     const int K = p.L * p.L + 2 * p.L;
@@ -201,11 +205,11 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
         if (p.io == FAVEST_IO_R64)
             k_uncombine_fp64_real<double2><<<grid, th, 0, s>>>((const double2 *)a, (const double2 *)b,
                                                                (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, KR,
-                                                               p.ncol);
+                                                               p.ncol, p.real_transpose ? 0.5 : 1.0);
         else
             k_uncombine_fp64_real<float2><<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b,
                                                               (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, KR,
-                                                              p.ncol);
+                                                              p.ncol, p.real_transpose ? 0.5 : 1.0);
         return cudaGetLastError();
     }
     const int K = p.L * p.L + 2 * p.L;

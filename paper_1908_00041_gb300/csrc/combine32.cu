@@ -29,7 +29,8 @@ template <bool REAL>
 __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ Q, float2 *__restrict__ a,
                                                       float2 *__restrict__ bo, const float *__restrict__ P,
                                                       const float *__restrict__ M, const float *__restrict__ R,
-                                                      int L, int K, const long long *__restrict__ coff, int B)
+                                                      int L, int K, const long long *__restrict__ coff, int B,
+                                                      float ps)
 {
     // [order][(degree - (l0 - 1)) * 2 + half]; the odd row length (69 x 16 B) spreads the
     // lanes (orders) of a quarter-warp over distinct bank groups
@@ -90,8 +91,10 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
             const float by = sg * fmaf(Pl, q1[cp + 1], fmaf(-Ml, pmy, Rm * q0[ct]));
             const size_t k = REAL ? (size_t)(2 * bi + s) * K + (size_t)l * (l + 1) / 2 - 1 + mu
                                   : cb + (size_t)l * l + l + m - 1;
-            a[k] = make_float2(ax, ay);
-            bo[k] = make_float2(bx, by);
+            // real fields, transpose for the real inner product: orders m > 0 doubled
+            const float sc = (REAL && mu > 0) ? ps : 1.f;
+            a[k] = make_float2(sc * ax, sc * ay);
+            bo[k] = make_float2(sc * bx, sc * by);
         }
     }
 }
@@ -135,7 +138,8 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
                                                         const long long *__restrict__ g_off,
                                                         const float *__restrict__ P, const float *__restrict__ M,
                                                         const float *__restrict__ R, const float *__restrict__ k1tab,
-                                                        int L, int K, int N, const long long *__restrict__ coff, int B)
+                                                        int L, int K, int N, const long long *__restrict__ coff, int B,
+                                                        float ps)
 {
     // cs[(l - (l0 - 1)) * kUS + q * (kCT + 1) + order], q = (a+, a-, b+, b-); real fields:
     // (a of field 2q, a of 2q+1, b of 2q, b of 2q+1), all at m = +mu
@@ -155,8 +159,10 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
         float2 v = make_float2(0.f, 0.f);
         if (REAL) {
             const int bf = 2 * bi + (q & 1);
-            if (l >= 1 && l <= L && mu <= l && bf < B)
+            if (l >= 1 && l <= L && mu <= l && bf < B) {
                 v = __ldg(((q & 2) ? b : a) + (size_t)bf * K + (size_t)l * (l + 1) / 2 - 1 + mu);
+                if (mu > 0) v = make_float2(ps * v.x, ps * v.y);   // real transpose: m > 0 halved
+            }
         } else {
             const int m = (q & 1) ? -mu : mu;
             if (l >= 1 && l <= L && mu <= l && !(mu == 0 && (q & 1)))
@@ -244,7 +250,7 @@ cudaError_t launch_combine_bf16(const Plan &p, void *a, void *b, cudaStream_t s)
     dim3 grid(nb * (nb + 1) / 2, p.ncg);
     auto k = p.real ? k_combine_bf16<true> : k_combine_bf16<false>;
     k<<<grid, 256, 0, s>>>((const float *)p.d_Q32, (float2 *)a, (float2 *)b, p.d_P32, p.d_M32, p.d_R32, p.L, K,
-                           p.d_coff, p.B);
+                           p.d_coff, p.B, p.real_transpose ? 2.f : 1.f);
     return cudaGetLastError();
 }
 
@@ -257,7 +263,8 @@ cudaError_t launch_uncombine_bf16(const Plan &p, const void *a, const void *b, c
     (void)ob_n;
     auto k = p.real ? k_uncombine_bf16<true> : k_uncombine_bf16<false>;
     k<<<grid, 256, 0, s>>>((const float2 *)a, (const float2 *)b, (unsigned char *)p.d_gb, p.d_g_off, p.d_P32,
-                           p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n, p.d_coff, p.B);
+                           p.d_M32, p.d_R32, p.d_k1, p.L, K, p.gemm_n, p.d_coff, p.B,
+                           p.real_transpose ? 0.5f : 1.f);
     return cudaGetLastError();
 }
 

@@ -720,10 +720,12 @@ struct FlagScope {
 int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags, void *stream)
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
-    if (flags & ~FAVEST_FLAG_UNIT_WEIGHTS) return FAVEST_EINVAL;
+    if (flags & ~(FAVEST_FLAG_UNIT_WEIGHTS | FAVEST_FLAG_REAL_TRANSPOSE)) return FAVEST_EINVAL;
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;     // Clebsch-Gordan plans take favest_fwd_cart
+    if ((flags & FAVEST_FLAG_REAL_TRANSPOSE) && !p.real) return FAVEST_EINVAL;
     FlagScope unit(p.unit_weights, p.unit_weights | ((flags & FAVEST_FLAG_UNIT_WEIGHTS) ? 1 : 0));
+    FlagScope rtr(p.real_transpose, (flags & FAVEST_FLAG_REAL_TRANSPOSE) ? 1 : 0);
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6 || p.real) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);
@@ -746,10 +748,12 @@ int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, v
 int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags, void *stream)
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
-    if (flags & ~FAVEST_FLAG_WEIGHTED) return FAVEST_EINVAL;
+    if (flags & ~(FAVEST_FLAG_WEIGHTED | FAVEST_FLAG_REAL_TRANSPOSE)) return FAVEST_EINVAL;
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;
+    if ((flags & FAVEST_FLAG_REAL_TRANSPOSE) && !p.real) return FAVEST_EINVAL;
     FlagScope weighted(p.adj_weighted, (flags & FAVEST_FLAG_WEIGHTED) ? 1 : 0);
+    FlagScope rtr(p.real_transpose, (flags & FAVEST_FLAG_REAL_TRANSPOSE) ? 1 : 0);
     size_t el = (p.io == FAVEST_IO_C128 || p.precision == FAVEST_BF16X6 || p.real) ? 16 : 8;
     if (!aligned(Tth, el) || !aligned(Tph, el) || !aligned(a, el) || !aligned(b, el)) return FAVEST_EINVAL;
     int st = check_device(p);

@@ -91,6 +91,7 @@ struct Plan {
     int ct = 0, ng = 0;       // FP64 column group width and count
     int unit_weights = 0;
     int adj_weighted = 0;         // set for the duration of a weighted adjoint call
+    int real_transpose = 0;       // set for the duration of a FAVEST_FLAG_REAL_TRANSPOSE call
     int device = 0;
     int num_sms = 0;
     long long ntab = 0;       // sum_mu (L + 2 - mu): rows of every per-(l, mu) table

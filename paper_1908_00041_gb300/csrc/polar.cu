@@ -59,7 +59,7 @@ template <bool REAL>
 __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
     const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
-    const long long *__restrict__ coff, int B)
+    const long long *__restrict__ coff, int B, float ps)
 {
     __shared__ float part[kPolarWarps][kPolarJ * 16][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -102,11 +102,16 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
             if (l < mu || l > L) continue;
             float2 ap, am, bp, bm;
             if (REAL) {
+                // (ps = 1/2 for the real transpose: every order here is > 0)
                 const size_t c0 = (size_t)l * (l + 1) / 2 - 1 + mu;
                 ap = af[c0];
                 bp = bf[c0];
                 am = has1 ? af[K + c0] : make_float2(0.f, 0.f);
                 bm = has1 ? bf[K + c0] : make_float2(0.f, 0.f);
+                ap = make_float2(ps * ap.x, ps * ap.y);
+                bp = make_float2(ps * bp.x, ps * bp.y);
+                am = make_float2(ps * am.x, ps * am.y);
+                bm = make_float2(ps * bm.x, ps * bm.y);
             } else {
                 const size_t c0 = (size_t)l * l + l - 1;
                 ap = af[c0 + mu];
@@ -264,7 +269,7 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
     dim3 grid(p.pol_muc / 32, p.ncg, (p.pol_jc + kPolarJ - 1) / kPolarJ);
     auto k = p.real ? k_polar_patch<true> : k_polar_patch<false>;
     k<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin, p.d_S32, p.L, K,
-                                        p.pol_jc, p.pol_muc, p.JP, p.d_coff, p.B);
+                                        p.pol_jc, p.pol_muc, p.JP, p.d_coff, p.B, p.real_transpose ? 0.5f : 1.f);
     return cudaGetLastError();
 }
 

@@ -192,3 +192,79 @@ def test_bf16x6_backward_matches_fp64():
         grads.append((ta.grad.cpu().numpy().astype(np.complex128), tb.grad.cpu().numpy().astype(np.complex128)))
     assert normwise_err(grads[1][0], grads[0][0]) < 2e-6
     assert normwise_err(grads[1][1], grads[0][1]) < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# Real fields: the backward operators are the transposes for the real inner products
+# ---------------------------------------------------------------------------
+def _rdot(u, v):
+    """Re sum conj(u) v (the real inner product of complex or real tensors)."""
+    return float(torch.sum(torch.conj(u.to(torch.complex128)) * v.to(torch.complex128)).real.item())
+
+
+@pytest.mark.parametrize("prec,io,tol", [(api.FAVEST_FP64, api.FAVEST_IO_R64, 1e-13),
+                                         (api.FAVEST_BF16X6, api.FAVEST_IO_R32, 2e-6)])
+def test_real_transposes(prec, io, tol):
+    """<F(T), g> = <T, F^T g> and <S(c), h> = <c, S^T h> for the real FwdVSHT F and the
+    real AdjVSHT S, with F^T, S^T computed by the FAVEST_FLAG_REAL_TRANSPOSE calls."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Ls, Bs = 63, 3
+    plan = api.Plan(Ls, Bs, prec, io)
+    tt, tp = synthetic.real_grid_field(Ls, Bs, seed=31)
+    ga, gb = synthetic.half_coefficients(Ls, Bs, seed=32)
+    T = [torch.as_tensor(v).to(plan.fdtype).cuda().contiguous() for v in (tt, tp)]
+    g = [torch.as_tensor(v).to(plan.cdtype).cuda().contiguous() for v in (ga, gb)]
+    Fa, Fb = plan.fwd(*T)
+    Ft, Fp = plan.adj(*g, weighted=True, real_transpose=True)
+    Sa, Sb = plan.adj(*g)
+    St = plan.fwd(*T, unit_weights=True, real_transpose=True)
+    torch.cuda.synchronize()
+    lhs, rhs = _rdot(Fa, g[0]) + _rdot(Fb, g[1]), _rdot(T[0], Ft) + _rdot(T[1], Fp)
+    assert abs(lhs - rhs) <= tol * abs(rhs)
+    lhs, rhs = _rdot(Sa, T[0]) + _rdot(Sb, T[1]), _rdot(g[0], St[0]) + _rdot(g[1], St[1])
+    assert abs(lhs - rhs) <= tol * abs(rhs)
+
+
+def test_real_grad_fd():
+    """Autograd through real-field FP64 plans: L(c) = sum |F(S(c) g)|^2 and
+    L(T) = sum |F(T g)|^2 against central differences (h = 1e-2; the losses are
+    quadratic) along random directions."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Ls, Bs = 47, 2
+    plan = api.Plan(Ls, Bs, api.FAVEST_FP64, api.FAVEST_IO_R64)
+    rng = np.random.default_rng(41)
+    a, b = synthetic.half_coefficients(Ls, Bs, seed=None, rng=rng)
+    gmask = torch.as_tensor(synthetic.mask(Ls, rng)).cuda()
+    tt, tp = synthetic.real_grid_field(Ls, Bs, seed=42)
+
+    def loss_c(ca, cb):
+        xt, xp = adj_vsht(plan, ca, cb)
+        ra, rb = fwd_vsht(plan, xt * gmask, xp * gmask)
+        return (ra.abs() ** 2).sum() + (rb.abs() ** 2).sum()
+
+    def loss_t(xt, xp):
+        ra, rb = fwd_vsht(plan, xt * gmask, xp * gmask)
+        return (ra.abs() ** 2).sum() + (rb.abs() ** 2).sum()
+
+    ca = torch.as_tensor(a).cuda().requires_grad_(True)
+    cb = torch.as_tensor(b).cuda().requires_grad_(True)
+    loss_c(ca, cb).backward()
+    xt = torch.as_tensor(tt).cuda().requires_grad_(True)
+    xp = torch.as_tensor(tp).cuda().requires_grad_(True)
+    loss_t(xt, xp).backward()
+    h = 1e-2
+    for _ in range(8):
+        da = torch.as_tensor(rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape)).cuda()
+        db = torch.as_tensor(rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape)).cuda()
+        with torch.no_grad():
+            fd = (loss_c(ca + h * da, cb + h * db) - loss_c(ca - h * da, cb - h * db)).item() / (2 * h)
+        an = _rdot(ca.grad, da) + _rdot(cb.grad, db)
+        assert abs(fd - an) <= 1e-9 * max(abs(an), 1e-3 * (ca.grad.norm() * da.norm()).item())
+        dt = torch.as_tensor(rng.standard_normal(tt.shape)).cuda()
+        dp = torch.as_tensor(rng.standard_normal(tp.shape)).cuda()
+        with torch.no_grad():
+            fd = (loss_t(xt + h * dt, xp + h * dp) - loss_t(xt - h * dt, xp - h * dp)).item() / (2 * h)
+        an = _rdot(xt.grad, dt) + _rdot(xp.grad, dp)
+        assert abs(fd - an) <= 1e-9 * max(abs(an), 1e-3 * (xt.grad.norm() * dt.norm()).item())
