@@ -240,9 +240,9 @@ int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
  * Ragged batches: nfields fields of individual degrees L[i] (host array), each on its
  * own (L[i]+1) x 2(L[i]+1) Gauss-Legendre grid.  The caller's buffers hold the fields
  * packed: component plane of field i at element offset field_off[i] of Tth and of Tph
- * (complex elements, even offsets), its coefficients (L[i]^2 + 2 L[i] of each family)
+ * (elements of the io type, starting on 16 bytes), its coefficients (L[i]^2 + 2 L[i] of each family)
  * at element offset coef_off[i] of a and of b; null offset arrays mean packed in field
- * order.  favest_batch_field_elems / favest_batch_coef_elems give the buffer lengths.
+ * order (each plane rounded up to 16 bytes).  favest_batch_field_elems / favest_batch_coef_elems give the buffer lengths.
  *
  * Fields are grouped by degree.  In the split-precision form the tensor-core Legendre
  * stage of all groups is one persistent kernel launch over a merged work queue of
@@ -254,7 +254,8 @@ int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
  *                          launch sequence, later ones launch the captured graph
  * Errors as for the single-field calls; favest_batch_status reads and clears the device
  * status words of all groups.  Calls on one batch must not overlap on the host.
- * Real fields (FAVEST_IO_R32) are not batched in this version: FAVEST_EUNSUPPORTED.
+ * Real fields (FAVEST_IO_R32, FAVEST_IO_R64): real planes and half-spectrum coefficient
+ * sets (L(L+3)/2 per family); field offsets must then be multiples of 16 bytes.
  */
 typedef struct favest_batch_s *favest_batch;
 enum { FAVEST_BATCH_AUTOTUNE = 1, FAVEST_BATCH_GRAPH = 2 };

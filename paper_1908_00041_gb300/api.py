@@ -444,7 +444,9 @@ class BatchPlan:
         import torch
         self.Ls = [int(x) for x in Ls]
         self.precision, self.io_type = precision, io_type
-        self.cdtype = torch.complex128 if io_type == FAVEST_IO_C128 else torch.complex64
+        self.real = io_type in (FAVEST_IO_R32, FAVEST_IO_R64)
+        self.cdtype = torch.complex128 if io_type in (FAVEST_IO_C128, FAVEST_IO_R64) else torch.complex64
+        self.fdtype = {FAVEST_IO_R32: torch.float32, FAVEST_IO_R64: torch.float64}.get(io_type, self.cdtype)
         n = len(self.Ls)
         Larr = (ctypes.c_int * n)(*self.Ls)
         fo = (ctypes.c_longlong * n)(*field_off) if field_off is not None else None
@@ -458,11 +460,15 @@ class BatchPlan:
         self.coef_elems = lib().favest_batch_coef_elems(ctypes.c_void_p(self.handle))
         self.field_off, self.coef_off = [], []
         f = c = 0
+        align = {FAVEST_IO_R32: 4, FAVEST_IO_C128: 1}.get(io_type, 2)   # elements per 16 bytes
         for i, L in enumerate(self.Ls):
             self.field_off.append(field_off[i] if field_off is not None else f)
             self.coef_off.append(coef_off[i] if coef_off is not None else c)
-            f += (L + 1) * 2 * (L + 1)
-            c += L * L + 2 * L
+            f += -(-(L + 1) * 2 * (L + 1) // align) * align
+            c += self._ncoef(L)
+
+    def _ncoef(self, L):
+        return L * (L + 3) // 2 if self.real else L * L + 2 * L
 
     def close(self):
         if getattr(self, "handle", None):
@@ -493,7 +499,7 @@ class BatchPlan:
     def coef(self, buf, i):
         L = self.Ls[i]
         o = self.coef_off[i]
-        return buf[o:o + L * L + 2 * L]
+        return buf[o:o + self._ncoef(L)]
 
     def fwd(self, Tth, Tph, a=None, b=None, stream=None):
         import torch
@@ -508,9 +514,9 @@ class BatchPlan:
     def adj(self, a, b, Tth=None, Tph=None, stream=None):
         import torch
         if Tth is None:
-            Tth = torch.empty(self.field_elems, dtype=self.cdtype, device=a.device)
+            Tth = torch.empty(self.field_elems, dtype=self.fdtype, device=a.device)
         if Tph is None:
-            Tph = torch.empty(self.field_elems, dtype=self.cdtype, device=a.device)
+            Tph = torch.empty(self.field_elems, dtype=self.fdtype, device=a.device)
         _check(lib().favest_adj_batched(ctypes.c_void_p(self.handle), _ptr(a), _ptr(b), _ptr(Tth), _ptr(Tph),
                                         _stream(stream)), "favest_adj_batched")
         return Tth, Tph

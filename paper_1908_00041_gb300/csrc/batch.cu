@@ -113,7 +113,7 @@ int run_batched(favest_batch bp, bool adjoint, const void *Tth, const void *Tph,
                 void *stream)
 {
     if (!bp || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
-    const size_t al = (bp->precision == FAVEST_BF16X6 || bp->io == FAVEST_IO_C128) ? 16 : 8;
+    const size_t al = (bp->precision == FAVEST_BF16X6 || bp->io != FAVEST_IO_C64) ? 16 : 8;
     if ((((uintptr_t)Tth | (uintptr_t)Tph) % al) || (((uintptr_t)a | (uintptr_t)b) % 8)) return FAVEST_EINVAL;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != bp->device) return FAVEST_EINVAL;
@@ -233,8 +233,12 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
     *out = nullptr;
     if (nfields < 1 || !L) return FAVEST_EINVAL;
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
-    if (io_type == FAVEST_IO_R32) return FAVEST_EUNSUPPORTED;
-    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64) return FAVEST_EINVAL;
+    if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64 && io_type != FAVEST_IO_R32 &&
+        io_type != FAVEST_IO_R64)
+        return FAVEST_EINVAL;
+    const bool real = io_type == FAVEST_IO_R32 || io_type == FAVEST_IO_R64;
+    // field planes start on 16 bytes: offsets in elements of the io type
+    const long long align = io_type == FAVEST_IO_R32 ? 4 : (io_type == FAVEST_IO_C128 ? 1 : 2);
     if (flags & ~(FAVEST_BATCH_AUTOTUNE | FAVEST_BATCH_GRAPH)) return FAVEST_EINVAL;
     for (int i = 0; i < nfields; ++i)
         if (L[i] < 1) return FAVEST_EINVAL;
@@ -249,16 +253,17 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
     bp->coff.resize(nfields);
     long long fo = 0, co = 0;
     for (int i = 0; i < nfields; ++i) {
-        const long long fe = (long long)(L[i] + 1) * 2 * (L[i] + 1), ce = (long long)L[i] * L[i] + 2LL * L[i];
+        const long long fe = (long long)(L[i] + 1) * 2 * (L[i] + 1);
+        const long long ce = real ? (long long)L[i] * (L[i] + 3) / 2 : (long long)L[i] * L[i] + 2LL * L[i];
         bp->toff[i] = field_off ? field_off[i] : fo;
         bp->coff[i] = coef_off ? coef_off[i] : co;
-        if (bp->toff[i] < 0 || bp->coff[i] < 0 || (bp->toff[i] & 1)) {
+        if (bp->toff[i] < 0 || bp->coff[i] < 0 || (bp->toff[i] % align)) {
             delete bp;
-            return FAVEST_EINVAL;   // field planes must start on 16 bytes (even offsets)
+            return FAVEST_EINVAL;   // field planes must start on 16 bytes
         }
         bp->field_elems = std::max(bp->field_elems, bp->toff[i] + fe);
         bp->coef_elems = std::max(bp->coef_elems, bp->coff[i] + ce);
-        fo += fe;
+        fo += (fe + align - 1) / align * align;   // default packing keeps planes on 16 bytes
         co += ce;
     }
     if (cudaGetDevice(&bp->device) != cudaSuccess) {

@@ -100,7 +100,8 @@ __global__ void k_uncombine_fp64(const TI *__restrict__ a, const TI *__restrict_
 template <typename TO>
 __global__ void k_combine_fp64_real(const double2 *__restrict__ Q, TO *__restrict__ a, TO *__restrict__ b,
                                     const double *__restrict__ P, const double *__restrict__ M,
-                                    const double *__restrict__ R, int L, int KR, int ncol, int B, double ps)
+                                    const double *__restrict__ R, int L, int KR, int ncol, int B, double ps,
+                                    const long long *__restrict__ coff)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)B * KR) return;
@@ -124,8 +125,9 @@ __global__ void k_combine_fp64_real(const double2 *__restrict__ Q, TO *__restric
     double2 av = make_double2(Pl * qt1.x - Ml * qtm.x + Rl * qp0.y, Pl * qt1.y - Ml * qtm.y - Rl * qp0.x);
     double2 bv = make_double2(-Rl * qt0.y + Pl * qp1.x - Ml * qpm.x, Rl * qt0.x + Pl * qp1.y - Ml * qpm.y);
     const double sc = mu > 0 ? ps : 1.0;   // real transpose: orders m > 0 doubled
-    a[(size_t)bf * KR + k] = from_d2<TO>(make_double2(sc * av.x, sc * av.y));
-    b[(size_t)bf * KR + k] = from_d2<TO>(make_double2(sc * bv.x, sc * bv.y));
+    const size_t cb = coff ? (size_t)coff[bf] : (size_t)bf * KR;
+    a[cb + k] = from_d2<TO>(make_double2(sc * av.x, sc * av.y));
+    b[cb + k] = from_d2<TO>(make_double2(sc * bv.x, sc * bv.y));
 }
 
 template <typename TI>
@@ -139,14 +141,15 @@ __device__ __forceinline__ double2 coef_half(const TI *__restrict__ c, int L, in
 template <typename TI>
 __global__ void k_uncombine_fp64_real(const TI *__restrict__ a, const TI *__restrict__ b, double2 *__restrict__ g,
                                       const double *__restrict__ P, const double *__restrict__ M,
-                                      const double *__restrict__ R, int L, int KR, int ncol, double ps)
+                                      const double *__restrict__ R, int L, int KR, int ncol, double ps,
+                                      const long long *__restrict__ coff)
 {
     const int mu = blockIdx.x, bf = blockIdx.y;
     const long long t0 = tab_off(L, mu);
     const int nrow = L + 2 - mu;
     const int q = bf >> 1, f = bf & 1;
     const int cth = (q * 2 + 0) * 2 + f, cph = (q * 2 + 1) * 2 + f;
-    const size_t cb = (size_t)bf * KR;
+    const size_t cb = coff ? (size_t)coff[bf] : (size_t)bf * KR;
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
         const int l = mu + r;
         const double Pm = (r > 0) ? P[t0 + r - 1] : 0.0;
@@ -174,11 +177,11 @@ cudaError_t launch_combine_fp64(const Plan &p, void *a, void *b, cudaStream_t s)
         if (p.io == FAVEST_IO_R64)
             k_combine_fp64_real<double2><<<grid, 256, 0, s>>>((const double2 *)p.d_Q, (double2 *)a, (double2 *)b,
                                                              p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B,
-                                                             p.real_transpose ? 2.0 : 1.0);
+                                                             p.real_transpose ? 2.0 : 1.0, p.d_coff);
         else
             k_combine_fp64_real<float2><<<grid, 256, 0, s>>>((const double2 *)p.d_Q, (float2 *)a, (float2 *)b,
                                                             p.d_P, p.d_M, p.d_R, p.L, KR, p.ncol, p.B,
-                                                            p.real_transpose ? 2.0 : 1.0);
+                                                            p.real_transpose ? 2.0 : 1.0, p.d_coff);
         return cudaGetLastError();
     }
     const int K = p.L * p.L + 2 * p.L;
@@ -205,11 +208,11 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
         if (p.io == FAVEST_IO_R64)
             k_uncombine_fp64_real<double2><<<grid, th, 0, s>>>((const double2 *)a, (const double2 *)b,
                                                                (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, KR,
-                                                               p.ncol, p.real_transpose ? 0.5 : 1.0);
+                                                               p.ncol, p.real_transpose ? 0.5 : 1.0, p.d_coff);
         else
             k_uncombine_fp64_real<float2><<<grid, th, 0, s>>>((const float2 *)a, (const float2 *)b,
                                                               (double2 *)p.d_Q, p.d_P, p.d_M, p.d_R, p.L, KR,
-                                                              p.ncol, p.real_transpose ? 0.5 : 1.0);
+                                                              p.ncol, p.real_transpose ? 0.5 : 1.0, p.d_coff);
         return cudaGetLastError();
     }
     const int K = p.L * p.L + 2 * p.L;

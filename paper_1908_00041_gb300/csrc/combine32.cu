@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
     const int ob = t;
     const int mu0 = ob * kCT, l0 = lb * kCT;
     const int bi = blockIdx.y;
-    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
+    const size_t cb = (coff && !REAL) ? (size_t)coff[bi] : (size_t)bi * K;
     const float *qb = Q + (size_t)bi * tab_off(L, L + 1) * 8;
     // phase 1: records (order i, degree l0 - 1 + d), d = 0 .. 33, for l in [mu, L+1]
     for (int e = threadIdx.x; e < kCT * kCTRows * 2; e += blockDim.x) {
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
             const float ay = sg * fmaf(Pl, q1[ct + 1], fmaf(-Ml, tmy, -Rm * q0[cp]));
             const float bx = sg * fmaf(Pl, q1[cp], fmaf(-Ml, pmx, -Rm * q0[ct + 1]));
             const float by = sg * fmaf(Pl, q1[cp + 1], fmaf(-Ml, pmy, Rm * q0[ct]));
-            const size_t k = REAL ? (size_t)(2 * bi + s) * K + (size_t)l * (l + 1) / 2 - 1 + mu
+            const size_t k = REAL ? (coff ? (size_t)coff[2 * bi + s] : (size_t)(2 * bi + s) * K) +
+                                        (size_t)l * (l + 1) / 2 - 1 + mu
                                   : cb + (size_t)l * l + l + m - 1;
             // real fields, transpose for the real inner product: orders m > 0 doubled
             const float sc = (REAL && mu > 0) ? ps : 1.f;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
     const int ob = t;
     const int mu0 = ob * kCT, l0 = lb * kCT;
     const int bi = blockIdx.y;
-    const size_t cb = coff ? (size_t)coff[bi] : (size_t)bi * K;
+    const size_t cb = (coff && !REAL) ? (size_t)coff[bi] : (size_t)bi * K;
     for (int e = threadIdx.x; e < kCTRows * 4 * kCT; e += blockDim.x) {
         const int i = e % kCT, q = (e / kCT) & 3, d = e / (4 * kCT);
         const int mu = mu0 + i, l = l0 - 1 + d;
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
         if (REAL) {
             const int bf = 2 * bi + (q & 1);
             if (l >= 1 && l <= L && mu <= l && bf < B) {
-                v = __ldg(((q & 2) ? b : a) + (size_t)bf * K + (size_t)l * (l + 1) / 2 - 1 + mu);
+                const size_t fcb = coff ? (size_t)coff[bf] : (size_t)bf * K;
+                v = __ldg(((q & 2) ? b : a) + fcb + (size_t)l * (l + 1) / 2 - 1 + mu);
                 if (mu > 0) v = make_float2(ps * v.x, ps * v.y);   // real transpose: m > 0 halved
             }
         } else {

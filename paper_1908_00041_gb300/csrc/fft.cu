@@ -95,13 +95,14 @@ __global__ void __launch_bounds__(256) k_fft_inv_fp64(
 template <typename TR>
 __global__ void __launch_bounds__(256) k_rfft_fwd_fp64(
     const TR *__restrict__ Tth, const TR *__restrict__ Tph, double2 *__restrict__ Fraw, RadixPlanArg rp,
-    const double2 *__restrict__ tw, int L, int nlat, int ncol)
+    const double2 *__restrict__ tw, int L, int nlat, int ncol, const long long *__restrict__ toff)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
     const int ring = blockIdx.x;               // b * nlat + j
     const int j = ring % nlat, b = ring / nlat;
-    const TR *st = Tth + (size_t)ring * n, *sp = Tph + (size_t)ring * n;
+    const size_t fb = (toff ? (size_t)toff[b] : (size_t)b * nlat * n) + (size_t)j * n;
+    const TR *st = Tth + fb, *sp = Tph + fb;
     double2 *buf0 = sm_fft, *buf1 = sm_fft + n;
     for (int k = threadIdx.x; k < n; k += blockDim.x) buf0[k] = make_double2((double)st[k], (double)sp[k]);
     __syncthreads();
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(256) k_rfft_fwd_fp64(
 template <typename TR>
 __global__ void __launch_bounds__(256) k_rfft_inv_fp64(
     const double2 *__restrict__ G, TR *__restrict__ Tth, TR *__restrict__ Tph, RadixPlanArg rp,
-    const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat)
+    const double2 *__restrict__ tw, const double *__restrict__ wring, int L, int nlat,
+    const long long *__restrict__ toff)
 {
     extern __shared__ double2 sm_fft[];
     const int n = rp.n;
@@ -148,7 +150,8 @@ __global__ void __launch_bounds__(256) k_rfft_inv_fp64(
     __syncthreads();
     const double2 *out = stockham<true>(buf0, buf1, tw, rp);
     const double w = wring ? wring[j] : 1.0;
-    TR *dt = Tth + (size_t)ring * n, *dp = Tph + (size_t)ring * n;
+    const size_t fb = (toff ? (size_t)toff[b] : (size_t)b * nlat * n) + (size_t)j * n;
+    TR *dt = Tth + fb, *dp = Tph + fb;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         dt[k] = (TR)(w * out[k].x);
         dp[k] = (TR)(w * out[k].y);
@@ -169,12 +172,12 @@ cudaError_t launch_fft_fwd_fp64(const Plan &p, const void *Tth, const void *Tph,
             auto k = k_rfft_fwd_fp64<double>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k<<<p.B * p.nlat, th, smem, s>>>((const double *)Tth, (const double *)Tph, (double2 *)p.d_F, rp,
-                                             p.fft.tw64, p.L, p.nlat, p.ncol);
+                                             p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
         } else {
             auto k = k_rfft_fwd_fp64<float>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k<<<p.B * p.nlat, th, smem, s>>>((const float *)Tth, (const float *)Tph, (double2 *)p.d_F, rp,
-                                             p.fft.tw64, p.L, p.nlat, p.ncol);
+                                             p.fft.tw64, p.L, p.nlat, p.ncol, p.d_toff);
         }
         return cudaGetLastError();
     }
@@ -206,12 +209,12 @@ cudaError_t launch_fft_inv_fp64(const Plan &p, void *Tth, void *Tph, cudaStream_
             auto k = k_rfft_inv_fp64<double>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k<<<p.B * p.nlat, th, smem, s>>>((const double2 *)p.d_G, (double *)Tth, (double *)Tph, rp, p.fft.tw64,
-                                             wr, p.L, p.nlat);
+                                             wr, p.L, p.nlat, p.d_toff);
         } else {
             auto k = k_rfft_inv_fp64<float>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k<<<p.B * p.nlat, th, smem, s>>>((const double2 *)p.d_G, (float *)Tth, (float *)Tph, rp, p.fft.tw64,
-                                             wr, p.L, p.nlat);
+                                             wr, p.L, p.nlat, p.d_toff);
         }
         return cudaGetLastError();
     }

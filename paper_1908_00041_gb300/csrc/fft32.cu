@@ -490,7 +490,8 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rfft_fwd_bf16(
     const float *__restrict__ Tth, const float *__restrict__ Tph, unsigned char *__restrict__ Fb,
     RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
-    const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B)
+    const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf, int B,
+    const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_r4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_r4);
@@ -513,7 +514,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                 const int ring = idx / nv, kv = idx % nv;
                 const int bf = 2 * q + (ring & 1);
                 if (bf < B) {
-                    const size_t off = ((size_t)bf * nlat + (ring < 2 ? j : jm)) * n + (size_t)kv * V;
+                    const size_t fb = toff ? (size_t)toff[bf] : (size_t)bf * nlat * n;   // field's plane
+                    const size_t off = fb + (size_t)(ring < 2 ? j : jm) * n + (size_t)kv * V;
                     load_v<V>(Tth + off, th[u]);
                     load_v<V>(Tph + off, ph[u]);
                 }
@@ -585,7 +587,7 @@ template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rfft_inv_bf16(
     const float *__restrict__ S32, float *__restrict__ Tth, float *__restrict__ Tph, RadixPlanArg rp,
     const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
-    int nlat, int J, int has_eq, int JP, int B)
+    int nlat, int J, int has_eq, int JP, int B, const long long *__restrict__ toff)
 {
     extern __shared__ float4 sm_s4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_s4);
@@ -665,7 +667,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
             th[i] = z.x;
             ph[i] = z.y;
         }
-        const size_t off = ((size_t)bf * nlat + (ring < 2 ? j : jm)) * n + (size_t)kv * V;
+        const size_t fb = toff ? (size_t)toff[bf] : (size_t)bf * nlat * n;
+        const size_t off = fb + (size_t)(ring < 2 ? j : jm) * n + (size_t)kv * V;
         store_v<V>(Tth + off, th);
         store_v<V>(Tph + off, ph);
     }
@@ -684,7 +687,7 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
         k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)Tth, (const float *)Tph, (unsigned char *)p.d_Fb,
                                                  rp, p.fft.tw32, p.d_perm,
                                                  p.unit_weights ? p.d_omega_unit32 : p.d_omega32, p.L, p.nlat,
-                                                 p.J, p.has_eq, p.nf, p.B);
+                                                 p.J, p.has_eq, p.nf, p.B, p.d_toff);
         return cudaGetLastError();
     }
     auto k = k_fft_fwd_bf16<LOG2N>;
@@ -706,7 +709,7 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float *)Tth, (float *)Tph, rp,
                                                  p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0),
-                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B);
+                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff);
         return cudaGetLastError();
     }
     auto k = k_fft_inv_bf16<LOG2N>;

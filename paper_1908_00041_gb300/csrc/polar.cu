@@ -71,10 +71,14 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
     const int mulim = (int)ceil(1.5 * (L + 1) * sin_j[jlast]) + 16;
     if (mu0 >= mulim) return;                          // uniform over the CTA
     const bool active = mu >= 1 && mu <= L && mu < muc;
-    const size_t cb = REAL ? (size_t)(2 * f) * K : coff ? (size_t)coff[f] : (size_t)f * K;
+    const bool has1 = !REAL || 2 * f + 1 < B;       // the pair's second field exists
+    // coefficient offsets: field f (complex), or the pair's fields 2f and 2f+1 (real)
+    const size_t cb = REAL ? (coff ? (size_t)coff[2 * f] : (size_t)(2 * f) * K)
+                           : (coff ? (size_t)coff[f] : (size_t)f * K);
+    const size_t cb1 = (REAL && has1) ? (coff ? (size_t)coff[2 * f + 1] : (size_t)(2 * f + 1) * K) : cb;
     const float2 *af = a + cb;
     const float2 *bf = b + cb;
-    const bool has1 = !REAL || 2 * f + 1 < B;       // the pair's second field exists
+    const float2 *af1 = a + cb1, *bf1 = b + cb1;
     const float w = (float)mu;
     float sum[kPolarJ][2][8], cmp[kPolarJ][2][8];
 #pragma unroll
@@ -106,8 +110,8 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
                 const size_t c0 = (size_t)l * (l + 1) / 2 - 1 + mu;
                 ap = af[c0];
                 bp = bf[c0];
-                am = has1 ? af[K + c0] : make_float2(0.f, 0.f);
-                bm = has1 ? bf[K + c0] : make_float2(0.f, 0.f);
+                am = has1 ? af1[c0] : make_float2(0.f, 0.f);
+                bm = has1 ? bf1[c0] : make_float2(0.f, 0.f);
                 ap = make_float2(ps * ap.x, ps * ap.y);
                 bp = make_float2(ps * bp.x, ps * bp.y);
                 am = make_float2(ps * am.x, ps * am.y);

@@ -95,6 +95,9 @@ def test_new_entry_points_reject_bad_arguments(lib):
     assert _create(16, 1, prec=api.FAVEST_BF16X6, io=api.FAVEST_IO_C128)[0] == api.FAVEST_EUNSUPPORTED
     assert _create(16, 1, prec=api.FAVEST_BF16X6, io=api.FAVEST_IO_R64)[0] == api.FAVEST_EUNSUPPORTED
     Ls = (ctypes.c_int * 2)(16, 31)
-    assert L.favest_batch_create(2, Ls, None, None, api.FAVEST_BF16X6, api.FAVEST_IO_R32, 0,
-                                 ctypes.byref(h)) == api.FAVEST_EUNSUPPORTED
+    assert L.favest_batch_create(2, Ls, None, None, api.FAVEST_BF16X6, 9, 0, ctypes.byref(h)) == api.FAVEST_EINVAL
+    # real planes must start on 16 bytes: float offsets multiple of 4
+    off = (ctypes.c_longlong * 2)(0, 578)
+    assert L.favest_batch_create(2, Ls, off, None, api.FAVEST_BF16X6, api.FAVEST_IO_R32, 0,
+                                 ctypes.byref(h)) == api.FAVEST_EINVAL
     assert L.favest_kernel_work(nul, b"fft_fwd", None, None, None) == api.FAVEST_EINVAL

@@ -171,3 +171,46 @@ def test_batching_form_config_vs_fp64():
             assert normwise_err(_h(bp.field(tp, i)).ravel(), _h(sp[k]).ravel()) < TOL
             assert normwise_err(_h(bp.coef(ra, i)), _h(fa[k])) < TOL
             assert normwise_err(_h(bp.coef(rb, i)), _h(fb[k])) < TOL
+
+
+# ---------------------------------------------------------------------------
+# Real fields in ragged batches (half-spectrum coefficients, real planes)
+# ---------------------------------------------------------------------------
+LS_REAL = [63, 31, 127, 63, 16, 31, 63]        # L = 16: mixed-radix DFT, odd plane lengths
+
+
+def _half_coefs(Ls, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for L in Ls:
+        a, b = synthetic.half_coefficients(L, 1, seed=None, rng=rng)
+        out.append((a[0], b[0]))
+    return out
+
+
+@pytest.mark.parametrize("prec,io,tol", [(api.FAVEST_BF16X6, api.FAVEST_IO_R32, 1e-6),
+                                         (api.FAVEST_FP64, api.FAVEST_IO_R64, 1e-13)])
+def test_real_batch_matches_single_plans(prec, io, tol):
+    coefs = _half_coefs(LS_REAL, 61)
+    bp = api.BatchPlan(LS_REAL, prec, io, graph=(prec == api.FAVEST_BF16X6))
+    a, b = _pack_coefs(bp, coefs, bp.cdtype)
+    for _ in range(3 if prec == api.FAVEST_BF16X6 else 1):   # eager, capture, replay
+        tt, tp = bp.adj(a, b)
+        ra, rb = bp.fwd(tt, tp)
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    for i, L in enumerate(LS_REAL):
+        p = api.Plan(L, 1, prec, io)
+        ca = torch.as_tensor(coefs[i][0]).to(bp.cdtype).cuda().view(1, -1).contiguous()
+        cb = torch.as_tensor(coefs[i][1]).to(bp.cdtype).cuda().view(1, -1).contiguous()
+        st, sp = p.adj(ca, cb)
+        sa, sb = p.fwd(st, sp)
+        torch.cuda.synchronize()
+        ft = bp.field(tt, i).cpu().numpy().astype(np.float64).ravel()
+        fp = bp.field(tp, i).cpu().numpy().astype(np.float64).ravel()
+        assert normwise_err(ft, st[0].cpu().numpy().astype(np.float64).ravel()) < tol
+        assert normwise_err(fp, sp[0].cpu().numpy().astype(np.float64).ravel()) < tol
+        assert normwise_err(_h(bp.coef(ra, i)), _h(sa[0])) < tol
+        assert normwise_err(_h(bp.coef(rb, i)), _h(sb[0])) < tol
+        # and the roundtrip recovers the coefficients
+        assert normwise_err(_h(bp.coef(ra, i)), coefs[i][0]) < 2e-6
