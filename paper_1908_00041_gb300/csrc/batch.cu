@@ -48,6 +48,12 @@ struct favest_batch_s {
     int num_sms = 0, device = 0;
     cudaStream_t cap = nullptr;               // capture stream
     GraphCache graph[2];                      // forward, adjoint
+    // one stream per degree group for the per-group kernels, forked from and joined back
+    // into the call's stream around the merged tensor-core launch (parallel branches of
+    // the captured graph)
+    std::vector<cudaStream_t> gstream;
+    std::vector<cudaEvent_t> gjoin;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -68,43 +74,61 @@ cudaError_t upload_vec(T **d, const std::vector<T> &h)
     return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Runs fn(g, stream) for every degree group on the group's own stream, largest degree
+// first, after all work queued so far on s, and makes s wait for all of them.
+template <typename Fn>
+cudaError_t per_group(favest_batch_s &bp, cudaStream_t s, Fn fn)
+{
+    const int G = (int)bp.groups.size();
+    cudaError_t e = cudaEventRecord(bp.fork, s);
+    for (int g = G - 1; g >= 0 && e == cudaSuccess; --g) {
+        e = cudaStreamWaitEvent(bp.gstream[g], bp.fork, 0);
+        if (e == cudaSuccess) e = fn(g, bp.gstream[g]);
+        if (e == cudaSuccess) e = cudaEventRecord(bp.gjoin[g], bp.gstream[g]);
+    }
+    for (int g = 0; g < G && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(s, bp.gjoin[g], 0);
+    return e;
+}
+
 // The launch sequence of one batched transform on stream s.
 cudaError_t enqueue(favest_batch_s &bp, bool adjoint, const void *Tth, const void *Tph, const void *a,
                     const void *b, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    const size_t G = bp.groups.size();
     if (bp.precision != FAVEST_BF16X6) {
-        for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
-            int st = adjoint ? favest_adj(bp.groups[g], a, b, (void *)Tth, (void *)Tph, s)
-                             : favest_fwd(bp.groups[g], Tth, Tph, (void *)a, (void *)b, s);
-            if (st != FAVEST_OK) e = cudaErrorLaunchFailure;
-        }
-        return e;
+        // no shared stage: each group's whole transform is one branch
+        return per_group(bp, s, [&](int g, cudaStream_t gs) {
+            int st = adjoint ? favest_adj(bp.groups[g], a, b, (void *)Tth, (void *)Tph, gs)
+                             : favest_fwd(bp.groups[g], Tth, Tph, (void *)a, (void *)b, gs);
+            return st == FAVEST_OK ? cudaSuccess : cudaErrorLaunchFailure;
+        });
     }
     if (!adjoint) {
-        for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
+        e = per_group(bp, s, [&](int g, cudaStream_t gs) {
             const Plan &p = bp.groups[g]->p;
-            e = launch_fft_fwd_bf16(p, Tth, Tph, s);
-            if (e == cudaSuccess) e = launch_gen_lambda(p, true, s);
-        }
+            cudaError_t r = launch_fft_fwd_bf16(p, Tth, Tph, gs);
+            return r == cudaSuccess ? launch_gen_lambda(p, true, gs) : r;
+        });
         if (e == cudaSuccess)
             e = launch_tc_gemm_items(256, bp.d_gg, bp.d_items_f, bp.n_items_f, 1, bp.d_status, bp.num_sms, s);
-        for (size_t g = 0; g < G && e == cudaSuccess; ++g)
-            e = launch_combine_bf16(bp.groups[g]->p, (void *)a, (void *)b, s);
+        if (e == cudaSuccess)
+            e = per_group(bp, s, [&](int g, cudaStream_t gs) {
+                return launch_combine_bf16(bp.groups[g]->p, (void *)a, (void *)b, gs);
+            });
     } else {
-        for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
+        e = per_group(bp, s, [&](int g, cudaStream_t gs) {
             const Plan &p = bp.groups[g]->p;
-            e = launch_uncombine_bf16(p, a, b, s);
-            if (e == cudaSuccess) e = launch_gen_lambda(p, false, s);
-        }
+            cudaError_t r = launch_uncombine_bf16(p, a, b, gs);
+            return r == cudaSuccess ? launch_gen_lambda(p, false, gs) : r;
+        });
         if (e == cudaSuccess)
             e = launch_tc_gemm_items(256, bp.d_gg, bp.d_items_a, bp.n_items_a, 0, bp.d_status, bp.num_sms, s);
-        for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
-            const Plan &p = bp.groups[g]->p;
-            if (p.pol_jc > 0) e = launch_polar_patch(p, a, b, s);
-            if (e == cudaSuccess) e = launch_fft_inv_bf16(p, (void *)Tth, (void *)Tph, s);
-        }
+        if (e == cudaSuccess)
+            e = per_group(bp, s, [&](int g, cudaStream_t gs) {
+                const Plan &p = bp.groups[g]->p;
+                cudaError_t r = p.pol_jc > 0 ? launch_polar_patch(p, a, b, gs) : cudaSuccess;
+                return r == cudaSuccess ? launch_fft_inv_bf16(p, (void *)Tth, (void *)Tph, gs) : r;
+            });
     }
     return e;
 }
@@ -168,6 +192,11 @@ void destroy_batch(favest_batch_s *bp)
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (bp->cap) cudaStreamDestroy(bp->cap);
+    for (auto q : bp->gstream)
+        if (q) cudaStreamDestroy(q);
+    for (auto ev : bp->gjoin)
+        if (ev) cudaEventDestroy(ev);
+    if (bp->fork) cudaEventDestroy(bp->fork);
     delete bp;
 }
 
@@ -342,6 +371,16 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
     }
     if (st == FAVEST_OK && cudaStreamCreateWithFlags(&bp->cap, cudaStreamNonBlocking) != cudaSuccess)
         st = FAVEST_ECUDA;
+    if (st == FAVEST_OK && cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) != cudaSuccess)
+        st = FAVEST_ECUDA;
+    for (size_t g = 0; st == FAVEST_OK && g < bp->groups.size(); ++g) {
+        cudaStream_t q = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) st = FAVEST_ECUDA;
+        else bp->gstream.push_back(q);
+        if (st == FAVEST_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) st = FAVEST_ECUDA;
+        else if (st == FAVEST_OK) bp->gjoin.push_back(ev);
+    }
     if (st == FAVEST_OK && cudaDeviceSynchronize() != cudaSuccess) st = FAVEST_ECUDA;
     if (st != FAVEST_OK) {
         cudaGetLastError();
