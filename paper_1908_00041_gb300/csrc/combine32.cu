@@ -8,8 +8,7 @@
 // slots the complex layout gives to m = +mu and m = -mu; coefficients are stored for
 // m >= 0 only, at l(l+1)/2 - 1 + m of a field's KR = L(L+3)/2.
 #include "favest_internal.h"
-
-#include <cuda_bf16.h>
+#include "bf16_split.cuh"
 
 namespace favest {
 
@@ -105,18 +104,6 @@ __device__ __forceinline__ float2 cf(const float2 *__restrict__ c, int L, int l,
     int am = m < 0 ? -m : m;
     if (l < 1 || l > L || am > l) return make_float2(0.f, 0.f);
     return c[cb + l * l + l + m - 1];
-}
-
-__device__ __forceinline__ void split3u(float f, unsigned short &h, unsigned short &m, unsigned short &l)
-{
-    __nv_bfloat16 bh = __float2bfloat16_rn(f);
-    float r1 = f - __bfloat162float(bh);
-    __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-    float r2 = r1 - __bfloat162float(bm);
-    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-    h = __bfloat16_as_ushort(bh);
-    m = __bfloat16_as_ushort(bm);
-    l = __bfloat16_as_ushort(bl);
 }
 
 constexpr int kUS = 4 * (kCT + 1) + 1;  // shared row stride (float2, odd) of the uncombine tile
@@ -227,19 +214,10 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
         // chunk [K/8][N/8][8 k][8 n]: row group rr/8, column group = this field
         unsigned char *dst = gb + g_off[mu * 2 + p] + ((long long)nt * nka + kc) * chunk +
                              (long long)(rr / 8) * (fpt * 128) + bg * 128 + (rr % 8) * 16;
-        unsigned w[3][4];
+        uint4 w[3];
+        pack_row3(v, w);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            unsigned short h0, m0, l0s, h1, m1, l1s;
-            split3u(v[2 * k], h0, m0, l0s);
-            split3u(v[2 * k + 1], h1, m1, l1s);
-            w[0][k] = (unsigned)h0 | ((unsigned)h1 << 16);
-            w[1][k] = (unsigned)m0 | ((unsigned)m1 << 16);
-            w[2][k] = (unsigned)l0s | ((unsigned)l1s << 16);
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            *reinterpret_cast<uint4 *>(dst + q * piece) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4 *>(dst + q * piece) = w[q];
     }
 }
 

@@ -6,6 +6,7 @@
 //   inverse: gathers the even/odd Legendre sums E, O of every order, forms
 //            G_j = (E + O) / sin(theta_j), G_j' = (E - O) / sin(theta_j), inverse FFT.
 #include "favest_internal.h"
+#include "bf16_split.cuh"
 #include "fft_device.cuh"
 
 #include <cuda_bf16.h>
@@ -206,33 +207,46 @@ __device__ void fft_p2(float2 *x, const float2 *__restrict__ tw, int nr)
     dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
 }
 
-__device__ __forceinline__ void split3f(float f, unsigned short &h, unsigned short &m, unsigned short &l)
+// The same transform with the first radix-16 stage (block length n) fed straight from
+// global memory: src.row(r) locates ring r and src.load(row, i) returns its point i.  Each
+// thread keeps the 16 inputs of two butterflies in registers (32 independent loads in
+// flight; across a warp every load covers consecutive addresses), so the input needs no
+// pass through shared memory.
+template <int LOG2N, bool INV, typename Src>
+__device__ void fft_p2_from_global(float2 *x, const float2 *__restrict__ tw, int nr, const Src &src)
 {
-    __nv_bfloat16 bh = __float2bfloat16_rn(f);
-    float r1 = f - __bfloat162float(bh);
-    __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-    float r2 = r1 - __bfloat162float(bm);
-    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-    h = __bfloat16_as_ushort(bh);
-    m = __bfloat16_as_ushort(bm);
-    l = __bfloat16_as_ushort(bl);
-}
-
-// 8 floats (one core-matrix row) as three bf16 pieces of 16 bytes
-__device__ __forceinline__ void pack_row3(const float (&v)[8], uint4 (&out)[3])
-{
-    unsigned w[3][4];
+    constexpr int n = 1 << LOG2N, n16 = LOG2N / 4, rem = LOG2N % 4, R = 16, h = n / R;
+    constexpr int nfull = rem ? n16 : n16 - 1;
+    static_assert(nfull >= 1 && nfull <= 2, "a first radix-16 stage is required");
+    constexpr int kPer = 2;
+    for (int t0 = threadIdx.x; t0 < h * nr; t0 += kPer * kFftThreads) {
+        float2 v[kPer][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        unsigned short h0, m0, l0, h1, m1, l1;
-        split3f(v[2 * i], h0, m0, l0);
-        split3f(v[2 * i + 1], h1, m1, l1);
-        w[0][i] = (unsigned)h0 | ((unsigned)h1 << 16);
-        w[1][i] = (unsigned)m0 | ((unsigned)m1 << 16);
-        w[2][i] = (unsigned)l0 | ((unsigned)l1 << 16);
+        for (int u = 0; u < kPer; ++u) {
+            const int t = t0 + u * kFftThreads;
+            if (t < h * nr) {
+                const auto rw = src.row(t >> (LOG2N - 4));
+                const int k = t & (h - 1);
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[u][q] = src.load(rw, k + q * h);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int t = t0 + u * kFftThreads;
+            if (t < h * nr) {
+                const int ring = t >> (LOG2N - 4), k = t & (h - 1);
+                dft_reg<R, INV>(v[u]);
+                const int base = ring * n + k;
+                x[padi(base)] = v[u][0];
+#pragma unroll
+                for (int q = 1; q < R; ++q) x[padi(base + q * h)] = cmulf(v[u][bitrev(q, 4)], twf<INV>(tw, q * k));
+            }
+        }
     }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) out[q] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    __syncthreads();
+    if constexpr (nfull >= 2) dif_stage16<LOG2N, n / 16, INV>(x, tw, nr);
+    dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
 }
 
 // The forward DFT's B-operand records (96 bytes per order: parity x piece x 16 bytes)
@@ -249,26 +263,17 @@ __device__ __forceinline__ void flush_records(unsigned char *__restrict__ dst, c
     __syncwarp();
 }
 
-// write 8 floats (one core-matrix row) as three bf16 pieces
-__device__ __forceinline__ void store_row3(unsigned char *dst, const float (&v)[8], int piece_bytes)
+// One 32-byte load (a whole sector per lane) through the read-only path; p 32-byte aligned.
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
 {
-    unsigned w[3][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        unsigned short h0, m0, l0, h1, m1, l1;
-        split3f(v[2 * i], h0, m0, l0);
-        split3f(v[2 * i + 1], h1, m1, l1);
-        w[0][i] = (unsigned)h0 | ((unsigned)h1 << 16);
-        w[1][i] = (unsigned)m0 | ((unsigned)m1 << 16);
-        w[2][i] = (unsigned)l0 | ((unsigned)l1 << 16);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-        *reinterpret_cast<uint4 *>(dst + q * piece_bytes) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
 }
 
-
 constexpr int kLoadBatch = 8;    // independent global loads per thread in flight
+constexpr int kInvOrders = 2;    // orders per thread whose inverse-DFT inputs are loaded at once
+                                 // (4 measured slower at n = 2048 and spill at 3 blocks per SM)
 
 // bytes of the DFT buffer of 4 rings of n points (padded for the power-of-two engine)
 template <int LOG2N>
@@ -282,7 +287,37 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 // the 111 registers they need at 2 (inverse DFT at L = 1023: 1.05 -> 0.79 ms), and the
 // forward kernel's 24 KB record staging allows only 2 of them per SM there anyway.
 template <int LOG2N>
-constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
+__host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
+
+// ring sources of the forward kernels: complex rows (T_th, T_ph of one field), or the
+// packed z = T_th + i T_ph of a real field (zero for the missing second field of a pair)
+struct ComplexRows {
+    const float2 *th, *ph;
+    size_t fb;
+    int j, jm, n;
+    __device__ __forceinline__ const float2 *row(int ring) const
+    {
+        return ((ring & 1) ? ph : th) + fb + (size_t)(ring < 2 ? j : jm) * n;
+    }
+    __device__ __forceinline__ float2 load(const float2 *r, int i) const { return __ldg(r + i); }
+};
+struct RealPairRows {
+    const float *th, *ph;
+    const long long *toff;
+    int q, B, nlat, j, jm, n;
+    struct Row { const float *th, *ph; bool ok; };
+    __device__ __forceinline__ Row row(int ring) const
+    {
+        const int bf = 2 * q + (ring & 1);
+        if (bf >= B) return {th, ph, false};
+        const size_t off = (toff ? (size_t)toff[bf] : (size_t)bf * nlat * n) + (size_t)(ring < 2 ? j : jm) * n;
+        return {th + off, ph + off, true};
+    }
+    __device__ __forceinline__ float2 load(const Row &r, int i) const
+    {
+        return r.ok ? make_float2(__ldg(r.th + i), __ldg(r.ph + i)) : make_float2(0.f, 0.f);
+    }
+};
 
 // grid: B * J CTAs (field-major); shared: 4 * n float2 (+ padding for LOG2N > 0) and the
 // record staging.  LOG2N > 0 selects the power-of-two engine, 0 the generic one.
@@ -302,8 +337,11 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     const int jm = nlat - 1 - j;
     const int n2 = n / 2;         // float4 per ring
     const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
-    // loads are issued in batches of kLoadBatch per thread before any is stored
-    for (int i0 = threadIdx.x; i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
+    if constexpr (LOG2N > 0) {
+        fft_p2_from_global<LOG2N, false>(buf, tw, nr, ComplexRows{Tth, Tph, fb, j, jm, n});
+    }
+    // generic lengths: loads are issued in batches of kLoadBatch per thread before any is stored
+    for (int i0 = threadIdx.x; LOG2N == 0 && i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
         float4 v[kLoadBatch];
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
@@ -319,18 +357,14 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         for (int u = 0; u < kLoadBatch; ++u) {
             const int idx = i0 + u * kFftThreads;
             if (idx < nr * n2) {
-                if (LOG2N > 0) {
-                    buf[padi(2 * idx)] = make_float2(v[u].x, v[u].y);
-                    buf[padi(2 * idx + 1)] = make_float2(v[u].z, v[u].w);
-                } else {
-                    sm_f4[idx] = v[u];
-                }
+                sm_f4[idx] = v[u];
             }
         }
     }
-    __syncthreads();
-    if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
-    else dif_f32<false>(buf, tw, rp, nr);
+    if constexpr (LOG2N == 0) {
+        __syncthreads();
+        dif_f32<false>(buf, tw, rp, nr);
+    }
     const float w = omega[j];
     // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 96;
@@ -395,24 +429,22 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += 2 * blockDim.x) {
-        // two orders per iteration: the 8 loads are issued before any is used
-        float4 ld[2][4];
+    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += kInvOrders * blockDim.x) {
+        // kInvOrders orders per iteration: their loads are issued before any is used
+        float4 ld[kInvOrders][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kInvOrders; ++h) {
             const int mu = mu0 + h * blockDim.x;
             if (mu <= L) {
                 const float4 *e = reinterpret_cast<const float4 *>(
                     S32 + ((((size_t)b * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
                 const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
-                ld[h][0] = __ldg(e);
-                ld[h][1] = __ldg(e + 1);
-                ld[h][2] = __ldg(o);
-                ld[h][3] = __ldg(o + 1);
+                ldg_v8(e, ld[h][0], ld[h][1]);
+                ldg_v8(o, ld[h][2], ld[h][3]);
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kInvOrders; ++h) {
             const int mu = mu0 + h * blockDim.x;
             if (mu > L) break;
             // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
@@ -463,8 +495,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
 // 2q+1 at the folded latitude pair (j, nlat-1-j): four complex rings, the same shared
 // memory and transform count as one complex field.  The B-operand record of the pair
 // holds columns c*4 + f*2 + (re, im) for component c and field f of the pair, at +mu.
-// Rows are read with float4 loads when nphi is a power of two (rows are then 16-byte
-// aligned) and float2 loads otherwise.
+// For power-of-two nphi the first radix-16 stage reads the rows itself (float loads, a warp
+// covering 128 consecutive bytes per load); other lengths stage them with float2 loads.
 // ---------------------------------------------------------------------------
 template <int V>
 __device__ __forceinline__ void load_v(const float *p, float (&v)[V])
@@ -495,7 +527,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
 {
     extern __shared__ float4 sm_r4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_r4);
-    constexpr int V = LOG2N > 0 ? 4 : 2;
+    constexpr int V = 2;
     constexpr int kU = kLoadBatch / 2;             // vector pairs (th, ph) in flight per thread
     const int n = rp.n;
     const int q = blockIdx.x / J, j = blockIdx.x % J;
@@ -503,7 +535,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
     const int nr = eq ? 2 : 4;    // rings: (2q, j), (2q+1, j), (2q, j'), (2q+1, j')
     const int jm = nlat - 1 - j;
     const int nv = n / V;
-    for (int i0 = threadIdx.x; i0 < nr * nv; i0 += kU * kFftThreads) {
+    if constexpr (LOG2N > 0)
+        fft_p2_from_global<LOG2N, false>(buf, tw, nr, RealPairRows{Tth, Tph, toff, q, B, nlat, j, jm, n});
+    // generic lengths: kU vector pairs in flight per thread
+    for (int i0 = threadIdx.x; LOG2N == 0 && i0 < nr * nv; i0 += kU * kFftThreads) {
         float th[kU][V], ph[kU][V];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -527,16 +562,14 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
             if (idx < nr * nv) {
                 const int ring = idx / nv, kv = idx % nv;
 #pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    const int e = ring * n + kv * V + i;
-                    buf[LOG2N > 0 ? padi(e) : e] = make_float2(th[u][i], ph[u][i]);
-                }
+                for (int i = 0; i < V; ++i) buf[ring * n + kv * V + i] = make_float2(th[u][i], ph[u][i]);
             }
         }
     }
-    __syncthreads();
-    if constexpr (LOG2N > 0) fft_p2<LOG2N, false>(buf, tw, nr);
-    else dif_f32<false>(buf, tw, rp, nr);
+    if constexpr (LOG2N == 0) {
+        __syncthreads();
+        dif_f32<false>(buf, tw, rp, nr);
+    }
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -604,23 +637,21 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += 2 * blockDim.x) {
-        float4 ld[2][4];
+    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += kInvOrders * blockDim.x) {
+        float4 ld[kInvOrders][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kInvOrders; ++h) {
             const int mu = mu0 + h * blockDim.x;
             if (mu <= L) {
                 const float4 *e = reinterpret_cast<const float4 *>(
                     S32 + ((((size_t)q * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
                 const float4 *o = e + 8;
-                ld[h][0] = __ldg(e);
-                ld[h][1] = __ldg(e + 1);
-                ld[h][2] = __ldg(o);
-                ld[h][3] = __ldg(o + 1);
+                ldg_v8(e, ld[h][0], ld[h][1]);
+                ldg_v8(o, ld[h][2], ld[h][3]);
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kInvOrders; ++h) {
             const int mu = mu0 + h * blockDim.x;
             if (mu > L) break;
             const float sc = mu == 0 ? w0 : is;
