@@ -289,6 +289,87 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 template <int LOG2N>
 __host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
 
+// Inverse-side engine: the transpose of fft_p2's factorisation (the DFT matrix is
+// symmetric, so the stages taken in reverse order, each transposed, give the same
+// transform).  dit_first reads the natural-order points nibble_reverse(blk) + q n / RL and
+// writes block blk's RL outputs consecutively; each radix-16 stage multiplies its inputs
+// by the twiddles before the butterfly; the last stage (block length n) produces the
+// outputs in natural order, thread k holding points k + q n / 16, and hands them to
+// sink.store(ring, position, value) instead of shared memory: across a warp each store
+// covers consecutive positions.
+template <int LOG2N, int RL, bool INV>
+__device__ __forceinline__ void dit_first(float2 *x, int nr)
+{
+    constexpr int n = 1 << LOG2N, LB = Log2c<RL>::v;
+    constexpr int nblk = n / RL, ndig = (LOG2N - LB) / 4;
+    static_assert(nblk <= kFftThreads && (LOG2N - LB) % 4 == 0, "unsupported length");
+    constexpr int rings_per_round = kFftThreads / nblk;
+    const int t = threadIdx.x;
+    for (int r0 = 0; r0 < nr; r0 += rings_per_round) {
+        const int ring = r0 + t / nblk, blk = t & (nblk - 1);
+        const bool act = t < nblk * rings_per_round && ring < nr;
+        float2 v[RL];
+        if (act) {
+            int m0 = 0;
+#pragma unroll
+            for (int d = 0; d < ndig; ++d) m0 |= ((blk >> (4 * d)) & 15) << (4 * (ndig - 1 - d));
+#pragma unroll
+            for (int q = 0; q < RL; ++q) v[q] = x[padi(ring * n + m0 + q * nblk)];
+            dft_reg<RL, INV>(v);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < RL; ++q) x[padi(ring * n + blk * RL + q)] = v[bitrev(q, LB)];
+        }
+        __syncthreads();
+    }
+}
+
+// transposed radix-16 stage at block length NB (twiddles, then butterfly), in place
+template <int LOG2N, int NB, bool INV>
+__device__ __forceinline__ void dit_stage16(float2 *x, const float2 *__restrict__ tw, int nr)
+{
+    constexpr int n = 1 << LOG2N, R = 16;
+    constexpr int h = NB / R, ts = n / NB, nbf = n / R;
+    for (int t = threadIdx.x; t < nbf * nr; t += kFftThreads) {
+        const int ring = t >> (LOG2N - 4);
+        const int i = t & (nbf - 1);
+        const int k = i & (h - 1);
+        const int base = ring * n + (i - k) * R + k;
+        float2 v[R];
+        v[0] = x[padi(base)];
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(base + q * h)], twf<INV>(tw, q * k * ts));
+        dft_reg<R, INV>(v);
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[padi(base + q * h)] = v[bitrev(q, 4)];
+    }
+    __syncthreads();
+}
+
+// full transform of nr rings held in natural order in shared memory, outputs to sink
+template <int LOG2N, bool INV, typename Sink>
+__device__ void fft_p2_to_global(float2 *x, const float2 *__restrict__ tw, int nr, const Sink &sink)
+{
+    constexpr int n = 1 << LOG2N, n16 = LOG2N / 4, rem = LOG2N % 4, R = 16, h = n / R;
+    constexpr int nfull = rem ? n16 : n16 - 1;
+    static_assert(nfull >= 1 && nfull <= 2, "a radix-16 stage of block length n is required");
+    dit_first<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
+    if constexpr (nfull >= 2) dit_stage16<LOG2N, n / 16, INV>(x, tw, nr);
+    for (int t = threadIdx.x; t < h * nr; t += kFftThreads) {
+        const int ring = t >> (LOG2N - 4), k = t & (h - 1);
+        float2 v[R];
+        v[0] = x[padi(ring * n + k)];
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(ring * n + k + q * h)], twf<INV>(tw, q * k));
+        dft_reg<R, INV>(v);
+        const auto rw = sink.row(ring);
+#pragma unroll
+        for (int q = 0; q < R; ++q) sink.store(rw, k + q * h, v[bitrev(q, 4)]);
+    }
+}
+
 // ring sources of the forward kernels: complex rows (T_th, T_ph of one field), or the
 // packed z = T_th + i T_ph of a real field (zero for the missing second field of a pair)
 struct ComplexRows {
@@ -316,6 +397,38 @@ struct RealPairRows {
     __device__ __forceinline__ float2 load(const Row &r, int i) const
     {
         return r.ok ? make_float2(__ldg(r.th + i), __ldg(r.ph + i)) : make_float2(0.f, 0.f);
+    }
+};
+
+// ring sinks of the inverse kernels, the counterparts of the sources above
+struct ComplexRowsOut {
+    float2 *th, *ph;
+    size_t fb;
+    int j, jm, n;
+    __device__ __forceinline__ float2 *row(int ring) const
+    {
+        return ((ring & 1) ? ph : th) + fb + (size_t)(ring < 2 ? j : jm) * n;
+    }
+    __device__ __forceinline__ void store(float2 *r, int i, float2 v) const { r[i] = v; }
+};
+struct RealPairRowsOut {
+    float *th, *ph;
+    const long long *toff;
+    int q, B, nlat, j, jm, n;
+    struct Row { float *th, *ph; bool ok; };
+    __device__ __forceinline__ Row row(int ring) const
+    {
+        const int bf = 2 * q + (ring & 1);
+        if (bf >= B) return {th, ph, false};
+        const size_t off = (toff ? (size_t)toff[bf] : (size_t)bf * nlat * n) + (size_t)(ring < 2 ? j : jm) * n;
+        return {th + off, ph + off, true};
+    }
+    __device__ __forceinline__ void store(const Row &r, int i, float2 v) const
+    {
+        if (r.ok) {
+            r.th[i] = v.x;
+            r.ph[i] = v.y;
+        }
     }
 };
 
@@ -470,20 +583,21 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         }
     }
     __syncthreads();
-    if constexpr (LOG2N > 0) fft_p2<LOG2N, true>(buf, tw, nr);
-    else dif_f32<true>(buf, tw, rp, nr);
     const int jm = nlat - 1 - j;
-    const int n2 = n / 2;
-    for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
-        const int ring = idx / n2, k2 = idx % n2;
-        const int i0 = ring * n + (LOG2N > 0 ? 2 * k2 : __ldg(perm + 2 * k2));
-        const int i1 = ring * n + (LOG2N > 0 ? 2 * k2 + 1 : __ldg(perm + 2 * k2 + 1));
-        const float2 v0 = buf[LOG2N > 0 ? padi(i0) : i0];
-        const float2 v1 = buf[LOG2N > 0 ? padi(i1) : i1];
-        float2 *dst = (ring & 1) ? Tph : Tth;
-        const int jj = (ring < 2) ? j : jm;
-        const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
-        reinterpret_cast<float4 *>(dst + fb + (size_t)jj * n)[k2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+    if constexpr (LOG2N > 0) {
+        fft_p2_to_global<LOG2N, true>(buf, tw, nr, ComplexRowsOut{Tth, Tph, fb, j, jm, n});
+    } else {
+        dif_f32<true>(buf, tw, rp, nr);
+        const int n2 = n / 2;
+        for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
+            const int ring = idx / n2, k2 = idx % n2;
+            const float2 v0 = buf[ring * n + __ldg(perm + 2 * k2)];
+            const float2 v1 = buf[ring * n + __ldg(perm + 2 * k2 + 1)];
+            float2 *dst = (ring & 1) ? Tph : Tth;
+            const int jj = (ring < 2) ? j : jm;
+            reinterpret_cast<float4 *>(dst + fb + (size_t)jj * n)[k2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        }
     }
 }
 
@@ -624,7 +738,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
 {
     extern __shared__ float4 sm_s4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_s4);
-    constexpr int V = LOG2N > 0 ? 4 : 2;
+    constexpr int V = 2;
     const int n = rp.n;
     const int q = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
@@ -681,9 +795,12 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         }
     }
     __syncthreads();
-    if constexpr (LOG2N > 0) fft_p2<LOG2N, true>(buf, tw, nr);
-    else dif_f32<true>(buf, tw, rp, nr);
     const int jm = nlat - 1 - j;
+    if constexpr (LOG2N > 0) {
+        fft_p2_to_global<LOG2N, true>(buf, tw, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
+        return;
+    }
+    dif_f32<true>(buf, tw, rp, nr);
     const int nv = n / V;
     for (int idx = threadIdx.x; idx < nr * nv; idx += blockDim.x) {
         const int ring = idx / nv, kv = idx % nv;
@@ -692,9 +809,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         float th[V], ph[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            const int k = kv * V + i;
-            const int e = ring * n + (LOG2N > 0 ? k : __ldg(perm + k));
-            const float2 z = buf[LOG2N > 0 ? padi(e) : e];
+            const float2 z = buf[ring * n + __ldg(perm + kv * V + i)];
             th[i] = z.x;
             ph[i] = z.y;
         }
