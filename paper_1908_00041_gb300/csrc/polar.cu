@@ -34,8 +34,6 @@ namespace favest {
 namespace {
 
 constexpr double kPolarSin = 0.06;   // rings with sin(theta_j) below this are patched
-constexpr int kPolarJ = 2;           // rings per thread
-constexpr int kPolarChunk = 8;       // degrees summed in plain FP32 before a compensated add
 
 double eps_pl(int l, int mu)
 {
@@ -44,42 +42,116 @@ double eps_pl(int l, int mu)
     return num > 0 ? std::sqrt(num / den) : 0.0;
 }
 
-constexpr int kPolarWarps = 8;       // warps per CTA, each over its own range of degrees
+constexpr int kPolarJ = 2;           // rings per warp
+constexpr int kPolarPairs = 10;      // ring pairs (warps) per block
+constexpr int kPolarChunk = 16;      // degrees per step; summed in plain FP32
+constexpr int kPolarThreads = 32 * kPolarPairs;
+constexpr int kPolarCoef = kPolarChunk * 4 * 32;                    // coefficient elements per step
+constexpr int kPolarCoefBytes = kPolarCoef * 8;                     // 16 KB
+constexpr int kPolarTabBytes = kPolarPairs * kPolarJ * kPolarChunk * 32 * 8;   // 80 KB
+constexpr int kPolarSmem = 2 * (kPolarCoefBytes + kPolarTabBytes);             // double-buffered
 
-// grid (pol_muc / 32, B, ceil(pol_jc / kPolarJ)), 256 threads.  Lane = order mu within the
-// tile; warp w sums degrees l in the w-th of 8 equal ranges.  Per ring the thread keeps
-// 2 banks x 8 columns: bank k collects, for even l, the D terms (k = 1) and Lambda terms
-// (k = 0), for odd l the reverse, so that bank k holds output parity k ^ (mu & 1).
-// Terms are summed in FP32 over chunks of kPolarChunk degrees, chunk sums go into a
-// Kahan-compensated running sum per warp, and the 8 warp sums are added in a fixed tree
-// order through shared memory (a plain FP32 running sum over ~L terms would lose about
-// sqrt(L) ulps).  Orders beyond the ring group's turning-point bound keep the tensor-core
-// values.
+// asynchronous copies global -> shared; src_bytes = 0 writes zeros without reading
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// first order whose tensor-core values ring j keeps (beyond its turning-point bound)
+__device__ __forceinline__ int polar_mulim(const double *__restrict__ sin_j, int L, int j)
+{
+    return (int)ceil(1.5 * (L + 1) * sin_j[j]) + 16;
+}
+
+// grid (pol_muc / 32, column groups, ceil(pol_jc / 20)), 320 threads, 192 KB of shared
+// memory.  Lane = order mu within the tile; warp w takes the rings j0 = 2w, 2w + 1 of the
+// block's 20 and sums over all degrees mu0..L in steps of 16.  Every step's operands are
+// staged in shared memory by asynchronous copies issued one step ahead: the coefficients
+// a, b at +-mu (once for all rings) and each warp's rows of the polar tables, so the sums
+// read no global memory.  Per ring the thread keeps 2 banks x 8 columns: bank k collects,
+// for even l, the D terms (k = 1) and Lambda terms (k = 0), for odd l the reverse, so that
+// bank k holds output parity k ^ (mu & 1).  Terms are summed in FP32 over a step, step sums
+// go into a Kahan-compensated running sum (a plain FP32 running sum over ~L terms would lose
+// about sqrt(L) ulps).  Ring pairs whose turning-point bound lies below the tile keep the
+// tensor-core values.  (The real transpose's factor ps, common to every term here since all
+// orders are > 0, is applied to the final sums.)
 template <bool REAL>
-__global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
+__global__ void __launch_bounds__(kPolarThreads, 1) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
     const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
     const long long *__restrict__ coff, int B, float ps)
 {
-    __shared__ float part[kPolarWarps][kPolarJ * 16][32];
+    extern __shared__ float4 pol_sm[];
+    typedef float2 CoefStep[kPolarChunk][4][32];                 // [degree][a+, a-, b+, b-][lane]
+    typedef float2 TabStep[kPolarPairs][kPolarJ][kPolarChunk][32];   // [warp][ring][degree][lane]
+    CoefStep *csb = reinterpret_cast<CoefStep *>(pol_sm);
+    TabStep *tsb = reinterpret_cast<TabStep *>(reinterpret_cast<unsigned char *>(pol_sm) + 2 * kPolarCoefBytes);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int mu0 = blockIdx.x * 32;
     const int mu = mu0 + lane;
     const int f = blockIdx.y;
-    const int j0 = blockIdx.z * kPolarJ;
-    const int jlast = (j0 + kPolarJ < jc ? j0 + kPolarJ : jc) - 1;
-    const int mulim = (int)ceil(1.5 * (L + 1) * sin_j[jlast]) + 16;
-    if (mu0 >= mulim) return;                          // uniform over the CTA
+    const int jb = blockIdx.z * kPolarPairs * kPolarJ;
+    const int je = jb + kPolarPairs * kPolarJ < jc ? jb + kPolarPairs * kPolarJ : jc;
+    if (mu0 >= polar_mulim(sin_j, L, je - 1)) return;   // uniform: the last ring has the largest bound
+    const int j0 = jb + warp * kPolarJ;
+    const int nring = j0 < jc ? (jc - j0 < kPolarJ ? jc - j0 : kPolarJ) : 0;
+    const bool wact = nring > 0 && mu0 < polar_mulim(sin_j, L, j0 + nring - 1);
     const bool active = mu >= 1 && mu <= L && mu < muc;
     const bool has1 = !REAL || 2 * f + 1 < B;       // the pair's second field exists
     // coefficient offsets: field f (complex), or the pair's fields 2f and 2f+1 (real)
     const size_t cb = REAL ? (coff ? (size_t)coff[2 * f] : (size_t)(2 * f) * K)
                            : (coff ? (size_t)coff[f] : (size_t)f * K);
     const size_t cb1 = (REAL && has1) ? (coff ? (size_t)coff[2 * f + 1] : (size_t)(2 * f + 1) * K) : cb;
-    const float2 *af = a + cb;
-    const float2 *bf = b + cb;
-    const float2 *af1 = a + cb1, *bf1 = b + cb1;
-    const float w = (float)mu;
+    const int nstep = (L + 1 - mu0 + kPolarChunk - 1) / kPolarChunk;
+
+    // one step's copies: coefficient element e = (degree e / 128, kind (e / 32) % 4, lane
+    // e % 32), zero outside the coefficient triangle; the warp's table rows (ring, degree)
+    // as 16 chunks of 16 bytes each (rows of degrees beyond L are left as they are: unused)
+    auto load_step = [&](int st) {
+        CoefStep &cs = csb[st & 1];
+        for (int e = threadIdx.x; e < kPolarCoef; e += kPolarThreads) {
+            const int i = e & 31, q = (e >> 5) & 3, d = e >> 7;
+            const int m = mu0 + i, l = mu0 + st * kPolarChunk + d;
+            const float2 *src = a;
+            int nb = 0;
+            if (m >= 1 && m < muc && l >= m && l <= L) {
+                if (REAL) {
+                    if (!(q & 1) || has1) {
+                        src = ((q & 2) ? b : a) + ((q & 1) ? cb1 : cb) + (size_t)l * (l + 1) / 2 - 1 + m;
+                        nb = 8;
+                    }
+                } else {
+                    const size_t c0 = cb + (size_t)l * l + l - 1;
+                    src = ((q & 2) ? b : a) + ((q & 1) ? c0 - m : c0 + m);
+                    nb = 8;
+                }
+            }
+            cp_async8(&cs[d][q][i], src, nb);
+        }
+        if (wact) {
+            float2(*ts)[kPolarChunk][32] = tsb[st & 1][warp];
+#pragma unroll
+            for (int u = 0; u < kPolarJ * kPolarChunk / 2; ++u) {
+                const int c = u * 32 + lane;                         // chunk: row c / 16, part c % 16
+                const int r = c >> 4, part = c & 15, q = r / kPolarChunk, d = r % kPolarChunk;
+                const int l = mu0 + st * kPolarChunk + d;
+                if (q < nring && l <= L)
+                    cp_async16(&ts[q][d][part * 2], tab + ((size_t)(j0 + q) * (L + 1) + l) * muc + mu0 + part * 2);
+            }
+        }
+        cp_async_commit();
+    };
     float sum[kPolarJ][2][8], cmp[kPolarJ][2][8];
 #pragma unroll
     for (int q = 0; q < kPolarJ; ++q)
@@ -87,111 +159,93 @@ __global__ void __launch_bounds__(kPolarWarps * 32) k_polar_patch(
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int c = 0; c < 8; ++c) sum[q][k][c] = cmp[q][k][c] = 0.f;
+    const float w = (float)mu;
 
-    // this warp's degrees: [lo, hi), lo even, length a multiple of kPolarChunk
-    const int span = L + 1 - mu0;
-    const int per = ((span + kPolarWarps - 1) / kPolarWarps + kPolarChunk - 1) / kPolarChunk * kPolarChunk;
-    const int lo = mu0 + warp * per, hi = lo + per;
-    for (int lc = lo; active && lc < hi && lc <= L; lc += kPolarChunk) {
-        float acc[kPolarJ][2][8];
-#pragma unroll
-        for (int q = 0; q < kPolarJ; ++q)
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) acc[q][k][c] = 0.f;
-#pragma unroll
-        for (int h = 0; h < kPolarChunk; ++h) {
-            const int l = lc + h;
-            if (l < mu || l > L) continue;
-            float2 ap, am, bp, bm;
-            if (REAL) {
-                // (ps = 1/2 for the real transpose: every order here is > 0)
-                const size_t c0 = (size_t)l * (l + 1) / 2 - 1 + mu;
-                ap = af[c0];
-                bp = bf[c0];
-                am = has1 ? af1[c0] : make_float2(0.f, 0.f);
-                bm = has1 ? bf1[c0] : make_float2(0.f, 0.f);
-                ap = make_float2(ps * ap.x, ps * ap.y);
-                bp = make_float2(ps * bp.x, ps * bp.y);
-                am = make_float2(ps * am.x, ps * am.y);
-                bm = make_float2(ps * bm.x, ps * bm.y);
-            } else {
-                const size_t c0 = (size_t)l * l + l - 1;
-                ap = af[c0 + mu];
-                am = af[c0 - mu];
-                bp = bf[c0 + mu];
-                bm = bf[c0 - mu];
-            }
-            const int kd = (h & 1) ? 0 : 1, kl = (h & 1) ? 1 : 0;   // banks of the D and Lambda terms
-#pragma unroll
-            for (int q = 0; q < kPolarJ; ++q) {
-                if (j0 + q >= jc) break;
-                const float2 t = tab[((size_t)(j0 + q) * (L + 1) + l) * muc + mu];
-                const float D = t.x, wl = w * t.y;
-                const float wl1 = REAL ? wl : -wl;      // m of slot 1: +mu (real) or -mu
-                float *ad = acc[q][kd], *al = acc[q][kl];
-                ad[0] = fmaf(ap.x, D, ad[0]);
-                ad[1] = fmaf(ap.y, D, ad[1]);
-                ad[2] = fmaf(am.x, D, ad[2]);
-                ad[3] = fmaf(am.y, D, ad[3]);
-                ad[4] = fmaf(bp.x, D, ad[4]);
-                ad[5] = fmaf(bp.y, D, ad[5]);
-                ad[6] = fmaf(bm.x, D, ad[6]);
-                ad[7] = fmaf(bm.y, D, ad[7]);
-                // theta: -i m b Lambda ; phi: +i m a Lambda  (m = +mu for s = 0, -mu for s = 1)
-                al[0] = fmaf(wl, bp.y, al[0]);
-                al[1] = fmaf(-wl, bp.x, al[1]);
-                al[2] = fmaf(wl1, bm.y, al[2]);
-                al[3] = fmaf(-wl1, bm.x, al[3]);
-                al[4] = fmaf(-wl, ap.y, al[4]);
-                al[5] = fmaf(wl, ap.x, al[5]);
-                al[6] = fmaf(-wl1, am.y, al[6]);
-                al[7] = fmaf(wl1, am.x, al[7]);
-            }
+    load_step(0);
+    for (int st = 0; st < nstep; ++st) {
+        if (st + 1 < nstep) {
+            load_step(st + 1);                       // in flight during this step's sums
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
+        __syncthreads();                             // every thread's copies of step st landed
+        const CoefStep &cs = csb[st & 1];
+        const float2(*ts)[kPolarChunk][32] = tsb[st & 1][warp];
+        const int lb = mu0 + st * kPolarChunk;       // even: mu0 and kPolarChunk are
+        if (wact) {
+            float acc[kPolarJ][2][8];
 #pragma unroll
-        for (int q = 0; q < kPolarJ; ++q)
+            for (int q = 0; q < kPolarJ; ++q)
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float y = acc[q][k][c] - cmp[q][k][c];
-                    const float t = sum[q][k][c] + y;
-                    cmp[q][k][c] = (t - sum[q][k][c]) - y;
-                    sum[q][k][c] = t;
+                    for (int c = 0; c < 8; ++c) acc[q][k][c] = 0.f;
+#pragma unroll
+            for (int d = 0; d < kPolarChunk; ++d) {
+                if (lb + d > L) break;
+                const float2 ap = cs[d][0][lane], am = cs[d][1][lane];
+                const float2 bp = cs[d][2][lane], bm = cs[d][3][lane];
+                const int kd = (d & 1) ? 0 : 1, kl = (d & 1) ? 1 : 0;   // banks of the D and Lambda terms
+#pragma unroll
+                for (int q = 0; q < kPolarJ; ++q) {
+                    if (q >= nring) break;
+                    const float2 t = ts[q][d][lane];
+                    const float D = t.x, wl = w * t.y;
+                    const float wl1 = REAL ? wl : -wl;      // m of slot 1: +mu (real) or -mu
+                    float *ad = acc[q][kd], *al = acc[q][kl];
+                    ad[0] = fmaf(ap.x, D, ad[0]);
+                    ad[1] = fmaf(ap.y, D, ad[1]);
+                    ad[2] = fmaf(am.x, D, ad[2]);
+                    ad[3] = fmaf(am.y, D, ad[3]);
+                    ad[4] = fmaf(bp.x, D, ad[4]);
+                    ad[5] = fmaf(bp.y, D, ad[5]);
+                    ad[6] = fmaf(bm.x, D, ad[6]);
+                    ad[7] = fmaf(bm.y, D, ad[7]);
+                    // theta: -i m b Lambda ; phi: +i m a Lambda  (m = +mu for s = 0, -mu for s = 1)
+                    al[0] = fmaf(wl, bp.y, al[0]);
+                    al[1] = fmaf(-wl, bp.x, al[1]);
+                    al[2] = fmaf(wl1, bm.y, al[2]);
+                    al[3] = fmaf(-wl1, bm.x, al[3]);
+                    al[4] = fmaf(-wl, ap.y, al[4]);
+                    al[5] = fmaf(wl, ap.x, al[5]);
+                    al[6] = fmaf(-wl1, am.y, al[6]);
+                    al[7] = fmaf(wl1, am.x, al[7]);
                 }
-    }
+            }
 #pragma unroll
-    for (int q = 0; q < kPolarJ; ++q)
+            for (int q = 0; q < kPolarJ; ++q)
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < 2; ++k)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) part[warp][q * 16 + k * 8 + c][lane] = sum[q][k][c] - cmp[q][k][c];
-    __syncthreads();
-    // thread -> (lane, 4 consecutive values of one ring and bank)
-    constexpr int kGroups = kPolarJ * 4;               // groups of 4 values
-    for (int g = warp; g < kGroups; g += kPolarWarps) {
-        const int q = g >> 2, k = (g >> 1) & 1, c4 = (g & 1) * 4;
-        float v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int vi = q * 16 + k * 8 + c4 + i;
-            float t[kPolarWarps];
-#pragma unroll
-            for (int ww = 0; ww < kPolarWarps; ++ww) t[ww] = part[ww][vi][lane];
-#pragma unroll
-            for (int st = 1; st < kPolarWarps; st *= 2)
-#pragma unroll
-                for (int ww = 0; ww < kPolarWarps; ww += 2 * st) t[ww] += t[ww + st];
-            v[i] = t[0];
+                    for (int c = 0; c < 8; ++c) {
+                        const float y = acc[q][k][c] - cmp[q][k][c];
+                        const float t = sum[q][k][c] + y;
+                        cmp[q][k][c] = (t - sum[q][k][c]) - y;
+                        sum[q][k][c] = t;
+                    }
         }
-        if (active && j0 + q < jc) {
+        __syncthreads();                             // before step st + 2 refills these buffers
+    }
+    if (!wact || !active) return;
+#pragma unroll
+    for (int q = 0; q < kPolarJ; ++q) {
+        if (q >= nring) break;
+        const int j = j0 + q;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                v[c] = sum[q][k][c] - cmp[q][k][c];
+                if (REAL) v[c] *= ps;                // real transpose: every order here is > 0
+            }
             const int par = k ^ (mu & 1);
             const float sg = (!REAL && (mu & 1)) ? -1.f : 1.f;     // columns of m = -mu
-            const int j = j0 + q;
-            float *dst = S32 + ((((size_t)f * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2 + par) * 32 + (j & 3) * 8 + c4;
-            *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
+            float4 *dst = reinterpret_cast<float4 *>(
+                S32 + ((((size_t)f * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2 + par) * 32 + (j & 3) * 8);
+            dst[0] = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
+            dst[1] = make_float4(v[4], v[5], sg * v[6], sg * v[7]);
         }
     }
 }
@@ -270,9 +324,10 @@ int build_polar_tables(Plan &p)
 cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cudaStream_t s)
 {
     const int K = p.real ? p.L * (p.L + 3) / 2 : p.L * p.L + 2 * p.L;
-    dim3 grid(p.pol_muc / 32, p.ncg, (p.pol_jc + kPolarJ - 1) / kPolarJ);
+    dim3 grid(p.pol_muc / 32, p.ncg, (p.pol_jc + kPolarPairs * kPolarJ - 1) / (kPolarPairs * kPolarJ));
     auto k = p.real ? k_polar_patch<true> : k_polar_patch<false>;
-    k<<<grid, kPolarWarps * 32, 0, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin, p.d_S32, p.L, K,
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPolarSmem);
+    k<<<grid, kPolarThreads, kPolarSmem, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin, p.d_S32, p.L, K,
                                         p.pol_jc, p.pol_muc, p.JP, p.d_coff, p.B, p.real_transpose ? 0.5f : 1.f);
     return cudaGetLastError();
 }
