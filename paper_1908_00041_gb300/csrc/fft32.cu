@@ -250,16 +250,38 @@ __device__ void fft_p2_from_global(float2 *x, const float2 *__restrict__ tw, int
 }
 
 // The forward DFT's B-operand records (96 bytes per order: parity x piece x 16 bytes)
-// are staged per warp in shared memory and stored as consecutive 16-byte chunks: the
-// records of a warp's 32 consecutive orders are 3 KB of consecutive bytes, which a direct
-// per-thread store would touch at a 96-byte stride (24 cache lines per instruction).
+// are staged per warp in shared memory: the records of a warp's 32 consecutive orders are
+// 3 KB of consecutive bytes in global memory, which a direct per-thread store would touch
+// at a 96-byte stride (24 cache lines per instruction).  One lane hands the staged block to
+// a bulk asynchronous copy (shared -> global), so the copy takes no load/store-unit
+// instructions; before the warp stages its next records it waits until the copy has read
+// the staging buffer.
 constexpr int kRecUint4 = 6;                               // 16-byte chunks per record
 constexpr int kStageBytes = (kFftThreads / 32) * 32 * kRecUint4 * 16;   // 24 KB
 
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// stage -> global: nrec records (16-byte aligned addresses, 96 nrec bytes)
 __device__ __forceinline__ void flush_records(unsigned char *__restrict__ dst, const uint4 *stg, int nrec, int lane)
 {
+    // the generic-proxy writes of the staging buffer become visible to the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    for (int i = lane; i < nrec * kRecUint4; i += 32) reinterpret_cast<uint4 *>(dst)[i] = stg[i];
+    if (lane == 0 && nrec > 0) {
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                     "r"((uint32_t)__cvta_generic_to_shared(stg)), "r"(nrec * kRecUint4 * 16)
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+}
+
+// before the staging buffer is written again (and before the block exits)
+__device__ __forceinline__ void staging_free(int lane)
+{
+    if (lane == 0) bulk_wait_read();
     __syncwarp();
 }
 
@@ -486,6 +508,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
                  warp * 32 * kRecUint4;
     for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
         const int mu = mu0 + lane;
+        uint4 rec_p[3], rec_m[3];
         if (mu <= L) {
             float vp[8], vm[8];
             // n % 8 = c*4 + s*2 + im ; s = 0: +mu (bin mu), s = 1: -mu (bin n - mu, or 0 at mu = 0)
@@ -505,17 +528,21 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
                     vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
                 }
             }
-            uint4 pk[3];
-            pack_row3(vp, pk);
+            pack_row3(vp, rec_p);
+            pack_row3(vm, rec_m);
+        }
+        staging_free(lane);                          // the previous round's copy has read it
+        if (mu <= L) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) stg[lane * kRecUint4 + q] = pk[q];
-            pack_row3(vm, pk);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) stg[lane * kRecUint4 + 3 + q] = pk[q];
+            for (int q = 0; q < 3; ++q) {
+                stg[lane * kRecUint4 + q] = rec_p[q];
+                stg[lane * kRecUint4 + 3 + q] = rec_m[q];
+            }
         }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
         flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
     }
+    staging_free(lane);                              // shared memory stays until the copies read it
 }
 
 // grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
@@ -691,6 +718,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                  warp * 32 * kRecUint4;
     for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
         const int mu = mu0 + lane;
+        uint4 rec_p[3], rec_m[3];
         if (mu <= L) {
             const int bp = mu, bm = mu == 0 ? 0 : n - mu;
             const int pp = LOG2N > 0 ? bp : __ldg(perm + bp), pm = LOG2N > 0 ? bm : __ldg(perm + bm);
@@ -713,17 +741,21 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                 vm[4 + f * 2] = eq ? 0.f : w * (pjx - pkx);
                 vm[4 + f * 2 + 1] = eq ? 0.f : w * (pjy - pky);
             }
-            uint4 pk[3];
-            pack_row3(vp, pk);
+            pack_row3(vp, rec_p);
+            pack_row3(vm, rec_m);
+        }
+        staging_free(lane);                          // the previous round's copy has read it
+        if (mu <= L) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) stg[lane * kRecUint4 + c] = pk[c];
-            pack_row3(vm, pk);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) stg[lane * kRecUint4 + 3 + c] = pk[c];
+            for (int c = 0; c < 3; ++c) {
+                stg[lane * kRecUint4 + c] = rec_p[c];
+                stg[lane * kRecUint4 + 3 + c] = rec_m[c];
+            }
         }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
         flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
     }
+    staging_free(lane);                              // shared memory stays until the copies read it
 }
 
 // Real fields, inverse: for field f of the pair, the spectrum of z = T_th + i T_ph is
