@@ -254,6 +254,31 @@ int make_fb_tensor_map(Plan &p)
     return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
 }
 
+// Tensor map of the adjoint GEMM output S32[group][JP/4][L+1][parity][4][8] (fp32) as the
+// inverse DFT reads it: dimensions (32 floats of a latitude group, parity, mu, latitude
+// group, column group); a box {8, 2, kInvChunk, 1, 1} at (8 (j % 4), 0, mu0, j / 4, group)
+// lands in shared memory as [order][parity][8 floats]: the sum records of latitude j for
+// kInvChunk consecutive orders (orders beyond L are filled with zeros).
+int make_s32_tensor_map(Plan &p)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return FAVEST_EUNSUPPORTED;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t L1 = (cuuint64_t)(p.L + 1), G = (cuuint64_t)(p.JP / 4);
+    cuuint64_t dims[5] = {32, 2, L1, G, (cuuint64_t)p.nf};
+    cuuint64_t strides[4] = {128, 256, 256 * L1, 256 * L1 * G};
+    cuuint32_t box[5] = {8, 2, (cuuint32_t)kInvChunk, 1, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = encode(&p.tmap_s32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, p.d_S32, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
+}
+
 // A GEMM operand buffer as seen by the TMA: a 2-D array of 512-byte rows (256 bf16 each),
 // loaded in boxes of box_rows whole rows (one operand chunk).
 int make_row_tensor_map(void *base, size_t bytes, int box_rows, CUtensorMap *out)
@@ -487,6 +512,7 @@ int alloc_workspace_bf16(Plan &p)
     int st = make_row_tensor_map(p.d_lam_f, lamf_bytes, (int)(CHA / 512), &p.tmap_lam_f);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_lam_a, lama_bytes, (int)(CHA / 512), &p.tmap_lam_a);
     if (st == FAVEST_OK) st = make_fb_tensor_map(p);
+    if (st == FAVEST_OK) st = make_s32_tensor_map(p);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_gb, (size_t)gsz, (int)(CHB / 512), &p.tmap_gb);
     if (st != FAVEST_OK) return st;
     std::vector<GemmGroup> gg(2);

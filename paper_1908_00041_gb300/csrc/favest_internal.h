@@ -42,6 +42,7 @@ struct FftPlan {
 };
 
 constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk
+constexpr int kInvChunk = 256;    // orders per TMA box of the inverse DFT's sum records (16 KB)
 
 // One tensor-core GEMM work item: out[rows][N] = sum over nk K-chunks of A_c * B_c, each
 // chunk three bf16 pieces.  Chunk c of A starts a_off + c * a_stride bytes into the A
@@ -137,6 +138,9 @@ struct Plan {
     // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
     // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
     CUtensorMap tmap_lam_f, tmap_lam_a, tmap_fb, tmap_gb;
+    // the inverse DFT's view of S32: (32 floats, parity, mu, latitude group, column group),
+    // boxes of 8 floats x 2 parities x kInvChunk orders
+    CUtensorMap tmap_s32;
     GemmGroup *d_ggroups = nullptr;   // [2]: forward (Lam, Fb, Q32), adjoint (Lam, g, S32)
     std::vector<TcItem> h_items_f, h_items_a;   // host copies (merged by ragged batches)
     int gen_lt = 128, gen_mb = 1;  // generator shape: latitudes per block, orders per thread

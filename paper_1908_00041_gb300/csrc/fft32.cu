@@ -8,6 +8,7 @@
 #include "favest_internal.h"
 #include "bf16_split.cuh"
 #include "fft_device.cuh"
+#include "tc.cuh"
 
 #include <cuda_bf16.h>
 
@@ -545,12 +546,89 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     staging_free(lane);                              // shared memory stays until the copies read it
 }
 
+// The inverse kernels' sum records: the 32-byte records of latitude j (parities 0 and 1)
+// for every order mu, from S32[group][JP/4][L+1][parity][4][8].  For power-of-two lengths
+// they stream through shared memory in TMA boxes of kInvChunk orders ([order][parity][8],
+// 16 KB), two buffers deep: the next box is in flight while each thread spreads one order
+// of the current one onto its frequency bins.  Other lengths (or a shared-memory block
+// not aligned for the TMA) read them with 256-bit loads, kInvOrders orders per thread at
+// a time.  put(mu, ev, ov) receives the even- and odd-parity sums of order mu.
+constexpr int kInvStageBytes = 2 * kInvChunk * 64 + 16;      // two boxes and their barriers
+
+template <int LOG2N, typename Put>
+__device__ __forceinline__ void stream_records(const float *__restrict__ S32, const CUtensorMap *tmap,
+                                               unsigned char *stage, int *status, int grp, int j, int L, int JP,
+                                               Put put)
+{
+    const bool tma = LOG2N > 0 && (__cvta_generic_to_shared(stage) & 127) == 0;   // uniform
+    if (tma) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * kInvChunk * 64);
+        const int nch = (L + kInvChunk) / kInvChunk;             // boxes covering orders 0..L
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&bars[0], 1);
+            tc::mbar_init(&bars[1], 1);
+            tc::mbar_fence_init();
+        }
+        __syncthreads();
+        auto issue = [&](int c) {
+            tc::mbar_arrive_expect_tx(&bars[c & 1], kInvChunk * 64);
+            tc::tma_load_5d(stage + (c & 1) * kInvChunk * 64, tmap, 8 * (j & 3), 0, c * kInvChunk, j >> 2, grp,
+                            &bars[c & 1]);
+        };
+        if (threadIdx.x == 0) issue(0);
+        for (int c = 0; c < nch; ++c) {
+            // box c + 1 refills the buffer that box c - 1 used (released by the barrier below)
+            if (threadIdx.x == 0 && c + 1 < nch) issue(c + 1);
+            if (!tc::mbar_wait(&bars[c & 1], (c >> 1) & 1)) atomicCAS(status, 0, FAVEST_ETIMEOUT);
+            const float4 *rec = reinterpret_cast<const float4 *>(stage + (c & 1) * kInvChunk * 64);
+            for (int i = threadIdx.x; i < kInvChunk; i += blockDim.x) {
+                const int mu = c * kInvChunk + i;
+                if (mu > L) break;
+                const float4 e0 = rec[4 * i], e1 = rec[4 * i + 1], o0 = rec[4 * i + 2], o1 = rec[4 * i + 3];
+                const float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+                const float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                put(mu, ev, ov);
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += kInvOrders * blockDim.x) {
+        // kInvOrders orders per iteration: their loads are issued before any is used
+        float4 ld[kInvOrders][4];
+#pragma unroll
+        for (int h = 0; h < kInvOrders; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu <= L) {
+                const float4 *e = reinterpret_cast<const float4 *>(
+                    S32 + ((((size_t)grp * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
+                const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
+                ldg_v8(e, ld[h][0], ld[h][1]);
+                ldg_v8(o, ld[h][2], ld[h][3]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < kInvOrders; ++h) {
+            const int mu = mu0 + h * blockDim.x;
+            if (mu > L) break;
+            const float ev[8] = {ld[h][0].x, ld[h][0].y, ld[h][0].z, ld[h][0].w,
+                                 ld[h][1].x, ld[h][1].y, ld[h][1].z, ld[h][1].w};
+            const float ov[8] = {ld[h][2].x, ld[h][2].y, ld[h][2].z, ld[h][2].w,
+                                 ld[h][3].x, ld[h][3].y, ld[h][3].z, ld[h][3].w};
+            put(mu, ev, ov);
+        }
+    }
+    __syncthreads();
+}
+
 // grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
+// and, for power-of-two n, the record stream's two boxes
 template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft_inv_bf16(
-    const float *__restrict__ S32, float2 *__restrict__ Tth, float2 *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
-    int nlat, int J, int has_eq, int JP, const long long *__restrict__ toff)
+    const float *__restrict__ S32, const __grid_constant__ CUtensorMap tmap_s, float2 *__restrict__ Tth,
+    float2 *__restrict__ Tph, RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
+    const float2 *__restrict__ isc, int L, int nlat, int J, int has_eq, int JP, const long long *__restrict__ toff,
+    int *status)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -569,47 +647,25 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += kInvOrders * blockDim.x) {
-        // kInvOrders orders per iteration: their loads are issued before any is used
-        float4 ld[kInvOrders][4];
+    auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
+        // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
+        const float sc = mu == 0 ? w0 : is;
 #pragma unroll
-        for (int h = 0; h < kInvOrders; ++h) {
-            const int mu = mu0 + h * blockDim.x;
-            if (mu <= L) {
-                const float4 *e = reinterpret_cast<const float4 *>(
-                    S32 + ((((size_t)b * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
-                const float4 *o = e + 8;                 // parity 1: the next 4 x 8 floats
-                ldg_v8(e, ld[h][0], ld[h][1]);
-                ldg_v8(o, ld[h][2], ld[h][3]);
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                if (mu == 0 && sgn == 1) continue;
+                const int bin = sgn ? n - mu : mu;
+                const int k = c * 4 + sgn * 2;
+                const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
+                buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
+                if (!eq)
+                    buf[LOG2N > 0 ? padi(i1) : i1] = make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
             }
         }
-#pragma unroll
-        for (int h = 0; h < kInvOrders; ++h) {
-            const int mu = mu0 + h * blockDim.x;
-            if (mu > L) break;
-            // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
-            const float sc = mu == 0 ? w0 : is;
-            const float ev[8] = {ld[h][0].x, ld[h][0].y, ld[h][0].z, ld[h][0].w,
-                                 ld[h][1].x, ld[h][1].y, ld[h][1].z, ld[h][1].w};
-            const float ov[8] = {ld[h][2].x, ld[h][2].y, ld[h][2].z, ld[h][2].w,
-                                 ld[h][3].x, ld[h][3].y, ld[h][3].z, ld[h][3].w};
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-#pragma unroll
-                for (int sgn = 0; sgn < 2; ++sgn) {
-                    if (mu == 0 && sgn == 1) continue;
-                    const int bin = sgn ? n - mu : mu;
-                    const int k = c * 4 + sgn * 2;
-                    const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
-                    buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
-                    if (!eq)
-                        buf[LOG2N > 0 ? padi(i1) : i1] =
-                            make_float2((ev[k] - ov[k]) * sc, (ev[k + 1] - ov[k + 1]) * sc);
-                }
-            }
-        }
-    }
-    __syncthreads();
+    };
+    stream_records<LOG2N>(S32, &tmap_s, reinterpret_cast<unsigned char *>(sm_i4) + fft_smem_bytes<LOG2N>(n), status, b,
+                          j, L, JP, put);
     const int jm = nlat - 1 - j;
     const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
     if constexpr (LOG2N > 0) {
@@ -764,9 +820,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
 // so one inverse transform per field and ring yields both real components.
 template <int LOG2N>
 __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rfft_inv_bf16(
-    const float *__restrict__ S32, float *__restrict__ Tth, float *__restrict__ Tph, RadixPlanArg rp,
-    const float2 *__restrict__ tw, const int *__restrict__ perm, const float2 *__restrict__ isc, int L,
-    int nlat, int J, int has_eq, int JP, int B, const long long *__restrict__ toff)
+    const float *__restrict__ S32, const __grid_constant__ CUtensorMap tmap_s, float *__restrict__ Tth,
+    float *__restrict__ Tph, RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
+    const float2 *__restrict__ isc, int L, int nlat, int J, int has_eq, int JP, int B,
+    const long long *__restrict__ toff, int *status)
 {
     extern __shared__ float4 sm_s4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_s4);
@@ -783,50 +840,30 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
         __syncthreads();
     }
-    for (int mu0 = threadIdx.x; mu0 <= L; mu0 += kInvOrders * blockDim.x) {
-        float4 ld[kInvOrders][4];
+    auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
+        const float sc = mu == 0 ? w0 : is;
 #pragma unroll
-        for (int h = 0; h < kInvOrders; ++h) {
-            const int mu = mu0 + h * blockDim.x;
-            if (mu <= L) {
-                const float4 *e = reinterpret_cast<const float4 *>(
-                    S32 + ((((size_t)q * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2) * 32 + (j & 3) * 8);
-                const float4 *o = e + 8;
-                ldg_v8(e, ld[h][0], ld[h][1]);
-                ldg_v8(o, ld[h][2], ld[h][3]);
-            }
-        }
+        for (int f = 0; f < 2; ++f) {
 #pragma unroll
-        for (int h = 0; h < kInvOrders; ++h) {
-            const int mu = mu0 + h * blockDim.x;
-            if (mu > L) break;
-            const float sc = mu == 0 ? w0 : is;
-            const float ev[8] = {ld[h][0].x, ld[h][0].y, ld[h][0].z, ld[h][0].w,
-                                 ld[h][1].x, ld[h][1].y, ld[h][1].z, ld[h][1].w};
-            const float ov[8] = {ld[h][2].x, ld[h][2].y, ld[h][2].z, ld[h][2].w,
-                                 ld[h][3].x, ld[h][3].y, ld[h][3].z, ld[h][3].w};
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    if (side == 1 && eq) continue;
-                    const float sg = side ? -1.f : 1.f;   // ring j: E + O, ring j': E - O
-                    const int kt = f * 2, kp = 4 + f * 2;
-                    const float gtx = (ev[kt] + sg * ov[kt]) * sc, gty = (ev[kt + 1] + sg * ov[kt + 1]) * sc;
-                    const float gpx = (ev[kp] + sg * ov[kp]) * sc, gpy = (ev[kp + 1] + sg * ov[kp + 1]) * sc;
-                    const int rb = (2 * side + f) * n;
-                    if (mu == 0) {
-                        buf[LOG2N > 0 ? padi(rb) : rb] = make_float2(gtx, gpx);
-                    } else {
-                        const int i0 = rb + mu, i1 = rb + n - mu;
-                        buf[LOG2N > 0 ? padi(i0) : i0] = make_float2(gtx - gpy, gty + gpx);
-                        buf[LOG2N > 0 ? padi(i1) : i1] = make_float2(gtx + gpy, gpx - gty);
-                    }
+            for (int side = 0; side < 2; ++side) {
+                if (side == 1 && eq) continue;
+                const float sg = side ? -1.f : 1.f;   // ring j: E + O, ring j': E - O
+                const int kt = f * 2, kp = 4 + f * 2;
+                const float gtx = (ev[kt] + sg * ov[kt]) * sc, gty = (ev[kt + 1] + sg * ov[kt + 1]) * sc;
+                const float gpx = (ev[kp] + sg * ov[kp]) * sc, gpy = (ev[kp + 1] + sg * ov[kp + 1]) * sc;
+                const int rb = (2 * side + f) * n;
+                if (mu == 0) {
+                    buf[LOG2N > 0 ? padi(rb) : rb] = make_float2(gtx, gpx);
+                } else {
+                    const int i0 = rb + mu, i1 = rb + n - mu;
+                    buf[LOG2N > 0 ? padi(i0) : i0] = make_float2(gtx - gpy, gty + gpx);
+                    buf[LOG2N > 0 ? padi(i1) : i1] = make_float2(gtx + gpy, gpx - gty);
                 }
             }
         }
-    }
-    __syncthreads();
+    };
+    stream_records<LOG2N>(S32, &tmap_s, reinterpret_cast<unsigned char *>(sm_s4) + fft_smem_bytes<LOG2N>(n), status, q,
+                          j, L, JP, put);
     const int jm = nlat - 1 - j;
     if constexpr (LOG2N > 0) {
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
@@ -880,21 +917,20 @@ template <int LOG2N>
 cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const int ne = 4 * p.nphi;
-    const size_t smem = (size_t)(LOG2N > 0 ? ne + ne / 16 : ne) * sizeof(float2);
+    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (LOG2N > 0 ? kInvStageBytes : 0);
     if (p.real) {
         auto k = k_rfft_inv_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float *)Tth, (float *)Tph, rp,
+        k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, p.tmap_s32, (float *)Tth, (float *)Tph, rp,
                                                  p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0),
-                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff);
+                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff, p.d_status);
         return cudaGetLastError();
     }
     auto k = k_fft_inv_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, (float2 *)Tth, (float2 *)Tph, rp, p.fft.tw32,
-                                   p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0), p.L, p.nlat, p.J,
-                                   p.has_eq, p.JP, p.d_toff);
+    k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, p.tmap_s32, (float2 *)Tth, (float2 *)Tph, rp,
+                                   p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0), p.L, p.nlat,
+                                   p.J, p.has_eq, p.JP, p.d_toff, p.d_status);
     return cudaGetLastError();
 }
 
