@@ -43,7 +43,7 @@ double eps_pl(int l, int mu)
 }
 
 constexpr int kPolarJ = 2;           // rings per warp
-constexpr int kPolarPairs = 10;      // ring pairs (warps) per block
+constexpr int kPolarPairs = 5;       // ring pairs (warps) per block
 constexpr int kPolarChunk = 16;      // degrees per step; summed in plain FP32
 constexpr int kPolarThreads = 32 * kPolarPairs;
 constexpr int kPolarCoef = kPolarChunk * 4 * 32;                    // coefficient elements per step
@@ -74,9 +74,9 @@ __device__ __forceinline__ int polar_mulim(const double *__restrict__ sin_j, int
     return (int)ceil(1.5 * (L + 1) * sin_j[j]) + 16;
 }
 
-// grid (pol_muc / 32, column groups, ceil(pol_jc / 20)), 320 threads, 192 KB of shared
-// memory.  Lane = order mu within the tile; warp w takes the rings j0 = 2w, 2w + 1 of the
-// block's 20 and sums over all degrees mu0..L in steps of 16.  Every step's operands are
+// grid (pol_muc / 32, column groups, ceil(pol_jc / 10)), 160 threads, 112 KB of shared
+// memory (two blocks per SM).  Lane = order mu within the tile; warp w takes the rings
+// j0 = 2w, 2w + 1 of the block's 10 and sums over all degrees mu0..L in steps of 16.  Every step's operands are
 // staged in shared memory by asynchronous copies issued one step ahead: the coefficients
 // a, b at +-mu (once for all rings) and each warp's rows of the polar tables, so the sums
 // read no global memory.  Per ring the thread keeps 2 banks x 8 columns: bank k collects,
@@ -87,7 +87,7 @@ __device__ __forceinline__ int polar_mulim(const double *__restrict__ sin_j, int
 // tensor-core values.  (The real transpose's factor ps, common to every term here since all
 // orders are > 0, is applied to the final sums.)
 template <bool REAL>
-__global__ void __launch_bounds__(kPolarThreads, 1) k_polar_patch(
+__global__ void __launch_bounds__(kPolarThreads, 2) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
     const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
     const long long *__restrict__ coff, int B, float ps)
