@@ -45,18 +45,27 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
     const int bi = blockIdx.y;
     const size_t cb = (coff && !REAL) ? (size_t)coff[bi] : (size_t)bi * K;
     const float *qb = Q + (size_t)bi * tab_off(L, L + 1) * 8;
-    // phase 1: records (order i, degree l0 - 1 + d), d = 0 .. 33, for l in [mu, L+1]
-    for (int e = threadIdx.x; e < kCT * kCTRows * 2; e += blockDim.x) {
+    // phase 1: records (order i, degree l0 - 1 + d), d = 0 .. 33, for l in [mu, L+1]; all of a
+    // thread's loads are issued before any is stored
+    constexpr int kE = kCT * kCTRows * 2, kPer = (kE + 255) / 256;
+    float4 v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * 256;
         const int half = e & 1, d = (e >> 1) % kCTRows, i = (e >> 1) / kCTRows;
         const int mu = mu0 + i, l = l0 - 1 + d;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (mu <= L && l >= mu && l <= L + 1) {
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < kE && mu <= L && l >= mu && l <= L + 1) {
             const int r = l - mu, n0 = (L + 3 - mu) / 2;
             const float4 *src = reinterpret_cast<const float4 *>(
                 qb + (tab_off(L, mu) + ((r & 1) ? n0 : 0) + (r >> 1)) * 8);
-            v = __ldg(src + half);
+            v[u] = __ldg(src + half);
         }
-        qs[i][d * 2 + half] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * 256;
+        if (e < kE) qs[(e >> 1) / kCTRows][((e >> 1) % kCTRows) * 2 + (e & 1)] = v[u];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -141,23 +150,36 @@ __global__ void __launch_bounds__(256) k_uncombine_bf16(const float2 *__restrict
     const int mu0 = ob * kCT, l0 = lb * kCT;
     const int bi = blockIdx.y;
     const size_t cb = (coff && !REAL) ? (size_t)coff[bi] : (size_t)bi * K;
-    for (int e = threadIdx.x; e < kCTRows * 4 * kCT; e += blockDim.x) {
+    // all of a thread's loads are issued before any is stored
+    constexpr int kE = kCTRows * 4 * kCT, kPer = (kE + 255) / 256;
+    float2 v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * 256;
         const int i = e % kCT, q = (e / kCT) & 3, d = e / (4 * kCT);
         const int mu = mu0 + i, l = l0 - 1 + d;
-        float2 v = make_float2(0.f, 0.f);
+        v[u] = make_float2(0.f, 0.f);
+        if (e >= kE) continue;
         if (REAL) {
             const int bf = 2 * bi + (q & 1);
             if (l >= 1 && l <= L && mu <= l && bf < B) {
                 const size_t fcb = coff ? (size_t)coff[bf] : (size_t)bf * K;
-                v = __ldg(((q & 2) ? b : a) + fcb + (size_t)l * (l + 1) / 2 - 1 + mu);
-                if (mu > 0) v = make_float2(ps * v.x, ps * v.y);   // real transpose: m > 0 halved
+                v[u] = __ldg(((q & 2) ? b : a) + fcb + (size_t)l * (l + 1) / 2 - 1 + mu);
             }
         } else {
             const int m = (q & 1) ? -mu : mu;
             if (l >= 1 && l <= L && mu <= l && !(mu == 0 && (q & 1)))
-                v = __ldg(((q & 2) ? b : a) + cb + (size_t)l * l + l + m - 1);
+                v[u] = __ldg(((q & 2) ? b : a) + cb + (size_t)l * l + l + m - 1);
         }
-        cs[d * kUS + q * (kCT + 1) + i] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * 256;
+        if (e >= kE) continue;
+        const int i = e % kCT, q = (e / kCT) & 3, d = e / (4 * kCT);
+        float2 x = v[u];
+        if (REAL && mu0 + i > 0) x = make_float2(ps * x.x, ps * x.y);   // real transpose: m > 0 halved
+        cs[d * kUS + q * (kCT + 1) + i] = x;
     }
     __syncthreads();
     constexpr int KC = kGemmChunkK;
