@@ -68,7 +68,7 @@ struct TcItem {
 
 // Operand tensor maps and output buffer shared by the items of one group (one plan and
 // one direction); a launch may serve the items of several groups (ragged batches).
-struct __align__(64) GemmGroup {
+struct GemmGroup {             // aligned as CUtensorMap requires
     CUtensorMap tmap_a, tmap_b;
     float *out;
 };

@@ -196,23 +196,12 @@ __device__ __forceinline__ void dif_last(float2 *x, int nr)
     }
 }
 
-// full transform of nr rings: natural order in, natural order out
-template <int LOG2N, bool INV>
-__device__ void fft_p2(float2 *x, const float2 *__restrict__ tw, int nr)
-{
-    constexpr int n = 1 << LOG2N, n16 = LOG2N / 4, rem = LOG2N % 4;
-    constexpr int nfull = rem ? n16 : n16 - 1;           // radix-16 stages before the last
-    static_assert(nfull <= 2, "lengths above 4096 are not instantiated");
-    if constexpr (nfull >= 1) dif_stage16<LOG2N, n, INV>(x, tw, nr);
-    if constexpr (nfull >= 2) dif_stage16<LOG2N, n / 16, INV>(x, tw, nr);
-    dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
-}
-
-// The same transform with the first radix-16 stage (block length n) fed straight from
-// global memory: src.row(r) locates ring r and src.load(row, i) returns its point i.  Each
-// thread keeps the 16 inputs of two butterflies in registers (32 independent loads in
-// flight; across a warp every load covers consecutive addresses), so the input needs no
-// pass through shared memory.
+// Full transform of nr rings, natural order in and out, by the factorisation
+//   radix-16 at block length n, [radix-16 at n/16,] radix-2^r blocks (dif_last),
+// with the first radix-16 stage fed straight from global memory: src.row(r) locates ring r
+// and src.load(row, i) returns its point i.  Each thread keeps the 16 inputs of two
+// butterflies in registers (32 independent loads in flight; across a warp every load covers
+// consecutive addresses), so the input needs no pass through shared memory.
 template <int LOG2N, bool INV, typename Src>
 __device__ void fft_p2_from_global(float2 *x, const float2 *__restrict__ tw, int nr, const Src &src)
 {
@@ -312,7 +301,7 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 template <int LOG2N>
 __host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
 
-// Inverse-side engine: the transpose of fft_p2's factorisation (the DFT matrix is
+// Inverse-side engine: the transpose of fft_p2_from_global's factorisation (the DFT matrix is
 // symmetric, so the stages taken in reverse order, each transposed, give the same
 // transform).  dit_first reads the natural-order points nibble_reverse(blk) + q n / RL and
 // writes block blk's RL outputs consecutively; each radix-16 stage multiplies its inputs

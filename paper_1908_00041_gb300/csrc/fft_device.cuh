@@ -47,12 +47,32 @@ __device__ __forceinline__ double2 twid(const double2 *__restrict__ tw, int q)
 
 // One Stockham pass of radix R over n points: y[(i/Ns)*Ns*R + i%Ns + q*Ns] =
 //   sum_r x[i + r n/R] w^{(i%Ns) r n/(Ns R)} w_R^{q r}
+// Radices 2 and 4: one thread per butterfly.  Other (odd prime) radices: one thread per
+// output (butterfly i, q); its twiddle exponent r ((i%Ns) n/(Ns R) + q n/R) mod n advances
+// by one addition per term (the step is below n), summed over r in order.
 template <bool INV>
 __device__ __forceinline__ void stockham_pass(const double2 *__restrict__ x, double2 *__restrict__ y,
                                               const double2 *__restrict__ tw, int n, int R, int Ns)
 {
     const int nb = n / R;
     const int tstep = n / (Ns * R);
+    if (R != 2 && R != 4) {
+        const int rstep = n / R;
+        for (int t = threadIdx.x; t < nb * R; t += blockDim.x) {
+            const int i = t % nb, q = t / nb;
+            const int k = i % Ns;
+            const int d = k * tstep + q * rstep;       // < n / R + (R - 1) n / R = n
+            double2 acc = make_double2(0.0, 0.0);
+            int tq = 0;
+            for (int r = 0; r < R; ++r) {
+                acc = cadd(acc, cmul(x[i + r * nb], twid<INV>(tw, tq)));
+                tq += d;
+                if (tq >= n) tq -= n;
+            }
+            y[(i / Ns) * Ns * R + k + q * Ns] = acc;
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const int k = i % Ns;
         const int obase = (i / Ns) * Ns * R + k;
@@ -73,20 +93,6 @@ __device__ __forceinline__ void stockham_pass(const double2 *__restrict__ x, dou
             y[obase + Ns] = cadd(d02, rot);
             y[obase + 2 * Ns] = csub(s02, s13);
             y[obase + 3 * Ns] = csub(d02, rot);
-        } else {
-            const int rstep = n / R;
-            for (int q = 0; q < R; ++q) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int r = 0; r < R; ++r) {
-                    double2 v = x[i + r * nb];
-                    int t1 = (int)(((long long)k * r * tstep) % n);
-                    int t2 = ((q * r) % R) * rstep;
-                    int tq = t1 + t2;
-                    if (tq >= n) tq -= n;
-                    acc = cadd(acc, cmul(v, twid<INV>(tw, tq)));
-                }
-                y[obase + q * Ns] = acc;
-            }
         }
     }
 }

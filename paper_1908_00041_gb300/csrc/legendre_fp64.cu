@@ -9,8 +9,10 @@ namespace favest {
 
 namespace {
 
-// Eight warps per CTA: the FP64 units sit in the SM's four sub-partitions, so fewer
-// than four resident warps cannot keep the FP64 pipe full.
+// Up to eight warps per CTA: the FP64 units sit in the SM's four sub-partitions, so fewer
+// than four resident warps cannot keep the FP64 pipe full.  Small grids (J below 512) take
+// ceil(J / 64) warps, two latitudes per thread: warps without latitudes would still issue
+// their FP64 instructions (and the analysis its reductions) into the same pipe.
 constexpr int kAnaThreads = 256;
 constexpr int kAnaWarps = kAnaThreads / 32;
 constexpr int kAnaJpt = 2;        // latitudes per thread (J <= 512)
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
     const double cm = cmu[mu];
 #pragma unroll
     for (int i = 0; i < kAnaJpt; ++i) {
-        int j = threadIdx.x + i * kAnaThreads;
+        int j = threadIdx.x + i * blockDim.x;
         x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;   // inactive lanes stay silent
         if (j < J) {
             x[i] = xj[j];
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
                 const int p = w & 1;          // parity of l + mu = parity of r (r0 even)
 #pragma unroll
                 for (int i = 0; i < kAnaJpt; ++i) {
-                    const int j = threadIdx.x + i * kAnaThreads;
+                    const int j = threadIdx.x + i * blockDim.x;
                     if (j < J) {
                         double yl = y1[i];
                         if (r > 0) {
@@ -124,11 +126,10 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
 #pragma unroll
         for (int q = 0; q < per; ++q) red[warp * V + lane * per + q] = acc[q];
         __syncthreads();
-        if (threadIdx.x < V) {
-            const int vi = threadIdx.x;
+        const int nw = blockDim.x >> 5;
+        for (int vi = threadIdx.x; vi < V; vi += blockDim.x) {
             double tot = 0.0;
-#pragma unroll
-            for (int wq = 0; wq < kAnaWarps; ++wq) tot += red[wq * V + vi];
+            for (int wq = 0; wq < nw; ++wq) tot += red[wq * V + vi];
             const int w = vi / (CT * 2), ct = (vi / 2) % CT, im = vi & 1;
             const int r = r0 + w;
             if (r < nrow) {
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     const double cm = cmu[mu];
 #pragma unroll
     for (int i = 0; i < kSynJpt; ++i) {
-        int j = threadIdx.x + i * kSynThreads;
+        int j = threadIdx.x + i * blockDim.x;
         x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;
         if (j < J) {
             x[i] = xj[j];
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     }
 #pragma unroll
     for (int i = 0; i < kSynJpt; ++i) {
-        const int j = threadIdx.x + i * kSynThreads;
+        const int j = threadIdx.x + i * blockDim.x;
         if (j >= J) continue;
         const double is = scalar ? 1.0 : 1.0 / sj[j];
         const bool eq = has_eq && j == J - 1;
@@ -248,11 +249,30 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
 
 }  // namespace
 
+// Threads per CTA of the FP64 Legendre kernels: the warps that J latitudes fill at two per
+// thread, raised (up to one latitude per thread) while the grid would leave fewer than about
+// 24 warps per SM to hide the FP64 latency (min_warps_grid = 24 x SMs / CTAs; 0: none).
+int fp64_threads(int J, int maxthreads, int min_warps_grid)
+{
+    int w = (J + 63) / 64;
+    const int wmax = (J + 31) / 32;
+    if (w < min_warps_grid) w = min_warps_grid < wmax ? min_warps_grid : wmax;
+    if (w < 1) w = 1;
+    return w * 32 < maxthreads ? w * 32 : maxthreads;
+}
+
 cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 {
     if (p.J > kAnaThreads * kAnaJpt) return cudaErrorInvalidValue;
     // orders 0..L, and L+1 for the scalar transforms of degree L+1 (Clebsch-Gordan route)
     int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
+    // Two latitudes per thread halve the per-latitude cost of the warp reductions; with 4
+    // columns per CTA the analysis still wants the warps of one latitude per thread when
+    // the grid is small (L = 511, one field, 512 CTAs: 1.40 ms with 8 warps, 1.46 with 4),
+    // with 8 columns it does not (Clebsch-Gordan route, L = 511: 2.86 ms with 8 warps,
+    // 2.12 with 4).  The synthesis takes two latitudes per thread throughout (L = 511, one
+    // field: 1.40 ms with 8 warps, 0.99 with 4).
+    const int nt = fp64_threads(p.J, kAnaThreads, p.ct == 8 ? 0 : (24 * p.num_sms + grid - 1) / grid);
     const double *omega = p.nscal > 0 ? p.d_wring : p.unit_weights ? p.d_omega_unit : p.d_omega;
     int nrowmax = p.L + 2;
     size_t smem;
@@ -261,15 +281,15 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
         smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega,
-                                          p.d_cmu, p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+        k<<<grid, nt, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
+                                 p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
     } else {
         constexpr int CT = 4, V = kWin * CT * 2;
         smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
         auto k = k_analysis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega,
-                                          p.d_cmu, p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
+        k<<<grid, nt, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
+                                 p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
     }
     return cudaGetLastError();
 }
@@ -277,6 +297,7 @@ cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
 {
     if (p.J > kSynThreads * kSynJpt) return cudaErrorInvalidValue;
+    const int nt = fp64_threads(p.J, kSynThreads, 0);
     int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
     int nrowmax = p.L + 2;
     if (p.ct == 8) {
@@ -284,17 +305,15 @@ cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
         size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
         auto k = k_synthesis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
-                                          p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng, p.nscal > 0, p.real);
+        k<<<grid, nt, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin, p.d_cmu, p.d_A,
+                                 p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol, p.ng, p.nscal > 0, p.real);
     } else {
         constexpr int CT = 4;
         size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
         auto k = k_synthesis_fp64<CT>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kSynThreads, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin,
-                                          p.d_cmu, p.d_A, p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol,
-                                          p.ng, p.nscal > 0, p.real);
+        k<<<grid, nt, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin, p.d_cmu, p.d_A,
+                                 p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol, p.ng, p.nscal > 0, p.real);
     }
     return cudaGetLastError();
 }
