@@ -228,10 +228,12 @@ int favest_launches_per_call(favest_plan plan, int adjoint);
 /*
  * Autotuner of the split-precision path's FP64 recurrence generator.  The generator
  * runs 128 threads per block as (128 / lt) orders x lt latitudes (lt = 32, 64, 128),
- * each block covering mb order groups in turn (mb = 1, 2, 4).  favest_plan_tune times
- * the candidate (lt, mb) shapes for this plan's degree on `stream` (synchronising it,
- * a few milliseconds) and keeps the fastest; favest_plan_gen_shape reports the shape in
- * use.  Plans start with (128, 1).  FP64 plans have nothing to tune (returns FAVEST_OK).
+ * each block covering mb order groups in turn (mb = 1, 2, 4), each thread running the
+ * recurrences of 1 or 2 latitudes (lt apart) side by side.  favest_plan_tune times the
+ * candidate shapes for this plan's degree on `stream` (synchronising it, a few
+ * milliseconds) and keeps the fastest; favest_plan_gen_shape reports (lt, mb) of the
+ * shape in use.  Plans start with (128, 1) and 2 latitudes per thread.  The generated
+ * values do not depend on the shape.  FP64 plans have nothing to tune (returns FAVEST_OK).
  */
 int favest_plan_tune(favest_plan plan, void *stream);
 int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);

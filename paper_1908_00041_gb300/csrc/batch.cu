@@ -210,7 +210,9 @@ int favest_plan_tune(favest_plan plan, void *stream)
     Plan &p = plan->p;
     if (p.precision != FAVEST_BF16X6) return FAVEST_OK;   // nothing tunable on the FP64 path
     cudaStream_t s = (cudaStream_t)stream;
-    const int cand[][2] = {{128, 1}, {64, 1}, {32, 1}, {128, 2}, {64, 2}, {32, 2}, {32, 4}};
+    // (latitudes per block, order groups per block, latitude chains per thread)
+    const int cand[][3] = {{128, 1, 2}, {64, 1, 2}, {32, 1, 2}, {128, 2, 2}, {64, 2, 2}, {32, 2, 2}, {32, 4, 2},
+                           {128, 1, 1}, {64, 1, 1}, {32, 1, 1}, {128, 2, 1}, {64, 2, 1}, {32, 2, 1}, {32, 4, 1}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FAVEST_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -218,14 +220,14 @@ int favest_plan_tune(favest_plan plan, void *stream)
         return FAVEST_ECUDA;
     }
     float best = 1e30f;
-    int blt = p.gen_lt, bmb = p.gen_mb, st = FAVEST_OK;
+    int blt = p.gen_lt, bmb = p.gen_mb, bnj = p.gen_nj, st = FAVEST_OK;
     for (const auto &c : cand) {
-        if (launch_gen_lambda_shape(p, true, c[0], c[1], s) != cudaSuccess) {
+        if (launch_gen_lambda_shape(p, true, c[0], c[1], c[2], s) != cudaSuccess) {
             st = FAVEST_ECUDA;
             break;
         }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_gen_lambda_shape(p, true, c[0], c[1], s);
+        for (int r = 0; r < 3; ++r) launch_gen_lambda_shape(p, true, c[0], c[1], c[2], s);
         cudaEventRecord(e1, s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -236,6 +238,7 @@ int favest_plan_tune(favest_plan plan, void *stream)
             best = ms;
             blt = c[0];
             bmb = c[1];
+            bnj = c[2];
         }
     }
     cudaEventDestroy(e0);
@@ -243,6 +246,7 @@ int favest_plan_tune(favest_plan plan, void *stream)
     if (st == FAVEST_OK) {
         p.gen_lt = blt;
         p.gen_mb = bmb;
+        p.gen_nj = bnj;
     }
     return st;
 }

@@ -144,6 +144,7 @@ struct Plan {
     GemmGroup *d_ggroups = nullptr;   // [2]: forward (Lam, Fb, Q32), adjoint (Lam, g, S32)
     std::vector<TcItem> h_items_f, h_items_a;   // host copies (merged by ragged batches)
     int gen_lt = 128, gen_mb = 1;  // generator shape: latitudes per block, orders per thread
+    int gen_nj = 2;                // latitude chains per generator thread (1 or 2)
     int force_gemm_n = 0;          // 256: use 256-column GEMM tiles whatever the batch
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
@@ -194,7 +195,7 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
 cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s);
 cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
 cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
-cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s);
+cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, int nj, cudaStream_t s);
 // failure-path self-test: one GEMM item with no operand loads and the given wait bound
 cudaError_t launch_gemm_selftest(const Plan &p, uint32_t poll_limit, cudaStream_t s);
 // one persistent GEMM launch over an explicit item list (items[i].group indexes groups)

@@ -62,107 +62,142 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 
 // Generator: 128 threads per CTA arranged as (128 / lt) orders x lt latitudes (lt = 32,
 // 64 or 128, a multiple of the warp so each warp runs one order); a CTA covers mb such
-// order groups in turn.  One thread runs the scaled FP64 recurrence of one (order,
-// latitude) over all rows l = mu..L+1 and packs, per parity, 8 consecutive rows into
-// one 16-byte core-matrix row per piece.  (lt, mb) is the block shape the autotuner
-// picks per degree.  Latitudes below jc0 (the order's turning bound rounded down to a
-// K-chunk: every value there is below 1e-13) and padding latitudes are not generated;
-// their operand positions were zeroed when the plan was created.
+// order groups in turn.  A thread runs the scaled FP64 recurrences of one order at NJ
+// (1 or 2) latitudes lt apart (the block covers NJ lt consecutive latitudes) over all rows
+// l = mu..L+1, interleaved step by step: each step of a recurrence depends on the one
+// before, so independent chains in the same thread keep more FP64 work in flight per warp
+// (at the price of registers and of fewer, longer blocks for small grids).
+// Per parity it packs 8 consecutive rows into one 16-byte core-matrix row per piece.
+// (lt, mb) is the block shape the autotuner picks per degree.  Latitudes below jc0 (the
+// order's turning bound rounded down to a K-chunk: every value there is below 1e-13) and
+// padding latitudes are not stored; their operand positions were zeroed when the plan was
+// created.
 //   fwd = true : forward A layout, item (mu, p, m_tile) at lam_off[mu*2+p] + m_tile*nkf*48KB
 //   fwd = false: adjoint A layout, item (mu, p, j_tile) at lam_off[mu*2+p] + j_tile*nka*48KB
-template <bool FWD>
+template <bool FWD, int kGenJ>
 __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const long long *__restrict__ lam_off,
                                           const double *__restrict__ xj, const double *__restrict__ sj,
                                           const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
-                                          int J, int JP, int mu, int j, int jc0)
+                                          int J, int JP, int mu, const int (&jv)[kGenJ], int jc0)
 {
     const int nrow = L + 2 - mu;
     const double *As = Atab + tab_off(L, mu);   // recurrence multipliers of this order
 
-    if (j >= J || j < jc0) return;
-    double y1 = 0.0, y2 = 0.0;
-    int c = 1 << 20;
-    const double x = xj[j];
-    sectoral_start(cmu[mu], sj[j], mu, y1, c);
+    bool act[kGenJ];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < kGenJ; ++i) {
+        act[i] = jv[i] < J && jv[i] >= jc0;
+        any |= act[i];
+    }
+    if (!any) return;
+    double y1[kGenJ], y2[kGenJ], x[kGenJ];
+    int c[kGenJ];
+#pragma unroll
+    for (int i = 0; i < kGenJ; ++i) {
+        y1[i] = 0.0;
+        y2[i] = 0.0;
+        c[i] = 1 << 20;                            // inactive chains stay silent
+        x[i] = 0.0;
+        if (act[i]) {
+            x[i] = xj[jv[i]];
+            sectoral_start(cmu[mu], sj[jv[i]], mu, y1[i], c[i]);
+        }
+    }
     const int nk_f = JP / kChunkK;                 // forward K chunks (latitudes)
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
     const int nk_a0 = (nrow_p0 + kChunkK - 1) / kChunkK, nk_a1 = (nrow_p1 + kChunkK - 1) / kChunkK;
 
-    unsigned pk[2][kPieces][4];   // [parity][piece][4 x 2 bf16]
+    unsigned pk[kGenJ][2][kPieces][4];   // [chain][parity][piece][4 x 2 bf16]
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int i = 0; i < kGenJ; ++i)
 #pragma unroll
-        for (int q = 0; q < kPieces; ++q)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int w = 0; w < 4; ++w) pk[p][q][w] = 0u;
+            for (int q = 0; q < kPieces; ++q)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) pk[i][p][q][w] = 0u;
 
     for (int r0 = 0; r0 < nrow; r0 += 16) {
 #pragma unroll
         for (int w = 0; w < 16; ++w) {
             const int r = r0 + w;
             if (r < nrow) {
-                double yl = y1;
-                if (r > 0) {
-                    yl = fma(__ldg(As + r) * x, y1, -y2);
-                    y2 = y1;
-                    y1 = yl;
+                const double a = __ldg(As + r);
+#pragma unroll
+                for (int i = 0; i < kGenJ; ++i) {
+                    if (!act[i]) continue;                 // no FP64 work for inactive chains
+                    double yl = y1[i];
+                    if (r > 0) {
+                        yl = fma(a * x[i], y1[i], -y2[i]);
+                        y2[i] = y1[i];
+                        y1[i] = yl;
+                    }
+                    const float f = (c[i] == 0) ? d2f_trunc(yl) : 0.0f;
+                    unsigned short h, m, l;
+                    split3(f, h, m, l);
+                    const int p = w & 1, slot = w >> 1;         // r0 is a multiple of 16
+                    const int word = slot >> 1, half = slot & 1;
+                    pk[i][p][0][word] |= (unsigned)h << (16 * half);
+                    pk[i][p][1][word] |= (unsigned)m << (16 * half);
+                    pk[i][p][2][word] |= (unsigned)l << (16 * half);
                 }
-                const float f = (c == 0) ? d2f_trunc(yl) : 0.0f;
-                unsigned short h, m, l;
-                split3(f, h, m, l);
-                const int p = w & 1, slot = w >> 1;         // r0 is a multiple of 16
-                const int word = slot >> 1, half = slot & 1;
-                pk[p][0][word] |= (unsigned)h << (16 * half);
-                pk[p][1][word] |= (unsigned)m << (16 * half);
-                pk[p][2][word] |= (unsigned)l << (16 * half);
             }
         }
-        renorm(y1, y2, c);   // growth over 16 rows stays far below 2^700
+#pragma unroll
+        for (int i = 0; i < kGenJ; ++i) renorm(y1[i], y2[i], c[i]);   // growth over 16 rows stays far below 2^700
         // flush: rows r0/2 .. r0/2+7 of each parity
         const int rp = r0 >> 1;                        // multiple of 8
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const int np = p ? nrow_p1 : nrow_p0;
-            if (rp < np) {
-                const long long base = lam_off[mu * 2 + p];
-                long long off;
-                if (FWD) {
-                    const int mt = rp / kTileM, mi = rp % kTileM;
-                    const int kc = j / kChunkK, jj = j % kChunkK;
-                    off = base + ((long long)mt * nk_f + kc) * kChunkBytes +
-                          (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
-                } else {
-                    const int nka = p ? nk_a1 : nk_a0;
-                    const int jt = j / kTileM, jj = j % kTileM;
-                    const int kc = rp / kChunkK, rr = rp % kChunkK;
-                    off = base + ((long long)jt * nka + kc) * kChunkBytes +
-                          (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
+        for (int i = 0; i < kGenJ; ++i) {
+            const int j = jv[i];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int np = p ? nrow_p1 : nrow_p0;
+                if (act[i] && rp < np) {
+                    const long long base = lam_off[mu * 2 + p];
+                    long long off;
+                    if (FWD) {
+                        const int mt = rp / kTileM, mi = rp % kTileM;
+                        const int kc = j / kChunkK, jj = j % kChunkK;
+                        off = base + ((long long)mt * nk_f + kc) * kChunkBytes +
+                              (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
+                    } else {
+                        const int nka = p ? nk_a1 : nk_a0;
+                        const int jt = j / kTileM, jj = j % kTileM;
+                        const int kc = rp / kChunkK, rr = rp % kChunkK;
+                        off = base + ((long long)jt * nka + kc) * kChunkBytes +
+                              (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kPieces; ++q) {
+                        uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
+                        *reinterpret_cast<uint4 *>(lam + off + q * kPieceBytes) = v;
+                    }
                 }
 #pragma unroll
-                for (int q = 0; q < kPieces; ++q) {
-                    uint4 v = make_uint4(pk[p][q][0], pk[p][q][1], pk[p][q][2], pk[p][q][3]);
-                    *reinterpret_cast<uint4 *>(lam + off + q * kPieceBytes) = v;
-                    pk[p][q][0] = pk[p][q][1] = pk[p][q][2] = pk[p][q][3] = 0u;
-                }
+                for (int q = 0; q < kPieces; ++q) pk[i][p][q][0] = pk[i][p][q][1] = pk[i][p][q][2] = pk[i][p][q][3] = 0u;
             }
         }
     }
 }
 
-template <bool FWD>
+template <bool FWD, int kGenJ>
 __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
     const int *__restrict__ jcmin, int L, int J, int JP, int lt, int mb)
 {
     const int olanes = kGenThreads / lt;
-    const int jblocks = JP / lt;
+    const int jblocks = (JP + kGenJ * lt - 1) / (kGenJ * lt);
     const int jb = blockIdx.x % jblocks, og = blockIdx.x / jblocks;
-    const int j = jb * lt + threadIdx.x % lt;
+    int jv[kGenJ];
+#pragma unroll
+    for (int i = 0; i < kGenJ; ++i) jv[i] = (jb * kGenJ + i) * lt + threadIdx.x % lt;
     for (int k = 0; k < mb; ++k) {
         const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
         if (mu > L) break;
-        gen_order<FWD>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, j, __ldg(jcmin + mu));
+        gen_order<FWD, kGenJ>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, jv, __ldg(jcmin + mu));
     }
 }
 
@@ -427,24 +462,34 @@ cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nite
 
 }  // namespace
 
-cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s)
+template <int NJ>
+cudaError_t launch_gen_t(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s)
 {
-    if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
     const int olanes = kGenThreads / lt;
     const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
-    const int grid = (p.JP / lt) * ogroups;
+    const int grid = ((p.JP + NJ * lt - 1) / (NJ * lt)) * ogroups;
     if (fwd)
-        k_gen_lambda<true><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f, p.d_x,
-                                                        p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
+        k_gen_lambda<true, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f, p.d_x,
+                                                            p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt,
+                                                            mb);
     else
-        k_gen_lambda<false><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x,
-                                                         p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
+        k_gen_lambda<false, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x,
+                                                             p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt,
+                                                             mb);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, int nj, cudaStream_t s)
+{
+    if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
+    if (nj == 1) return launch_gen_t<1>(p, fwd, lt, mb, s);
+    if (nj == 2) return launch_gen_t<2>(p, fwd, lt, mb, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s)
 {
-    return launch_gen_lambda_shape(p, fwd, p.gen_lt, p.gen_mb, s);
+    return launch_gen_lambda_shape(p, fwd, p.gen_lt, p.gen_mb, p.gen_nj, s);
 }
 
 cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,
