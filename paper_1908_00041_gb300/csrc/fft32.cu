@@ -36,7 +36,84 @@ constexpr int kMaxInlineRadix = 128;   // largest odd prime factor of nphi suppo
 // Stage s (radix R, block length Nb, h = Nb/R): for every block and k < h the R points
 // x[k + t h] are replaced by their R-point DFT, output q scaled by w_Nb^{q k}.  Frequency m
 // ends at position perm[m] (mixed-radix digit reversal, precomputed on the host).  Each
-// butterfly reads and writes the same addresses, so one buffer suffices.
+// butterfly reads and writes the same addresses, and the butterflies of a stage touch
+// disjoint positions, so one buffer suffices.
+// Radices 2 and 4, and the odd primes 3..13: one thread per butterfly, its R points in
+// registers and the R roots of unity w_R^j loaded once per stage.  Larger primes:
+// butterflies are dealt out to warps, one output (q) per lane (several per lane for
+// R > 32); each output reads its R inputs from shared memory, its twiddle exponent r q n/R
+// advancing by one addition per term, and the warp writes its outputs back after all of its
+// lanes have read (no block-wide barrier inside the stage).  The output twiddle exponent
+// q k n/Nb is below n (q < R, k < Nb/R): no reduction is needed.
+constexpr int kMaxOddOut = kMaxInlineRadix / 32;   // outputs per lane for R > 32
+
+template <int R, bool INV>
+__device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restrict__ tw, int n, int Nb, int nr)
+{
+    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
+    float2 wr[R];                                      // w_R^j = w_n^{j n / R}
+#pragma unroll
+    for (int j = 0; j < R; ++j) wr[j] = twf<INV>(tw, j * rstep);
+    for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+        const int ring = t / nbf, i = t - ring * nbf;
+        const int blk = i / h, k = i - blk * h;
+        float2 *xr = x + ring * n + blk * Nb + k;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = xr[r * h];
+        const int tk = k * ts;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float2 acc = v[0];
+#pragma unroll
+            for (int r = 1; r < R; ++r) acc = caddf(acc, cmulf(v[r], wr[(q * r) % R]));
+            xr[q * h] = q == 0 ? acc : cmulf(acc, twf<INV>(tw, q * tk));
+        }
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dif_stage_odd(float2 *x, const float2 *__restrict__ tw, int n, int R, int Nb,
+                                              int nr)
+{
+    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int per = R <= 32 ? 32 / R : 1;            // butterflies per warp pass
+    const int nout = (R + 31) / 32;                    // outputs per lane
+    const int lb = R <= 32 ? lane / R : 0, lq = R <= 32 ? lane % R : lane;
+    const bool lane_ok = R > 32 || lane < per * R;
+    const int total = nbf * nr;
+    for (int b0 = warp * per; b0 < total; b0 += nw * per) {
+        float2 res[kMaxOddOut];
+        int pos[kMaxOddOut];
+        const int bi = b0 + lb;
+        const int ring = bi / nbf, i = bi - ring * nbf;
+        const int blk = i / h, k = i - blk * h;
+        const int base = ring * n + blk * Nb + k;
+#pragma unroll
+        for (int u = 0; u < kMaxOddOut; ++u) {
+            pos[u] = -1;
+            const int q = lq + 32 * u;
+            if (u >= nout || !lane_ok || q >= R || bi >= total) continue;
+            float2 acc = make_float2(0.f, 0.f);
+            const int dq = q * rstep;                    // < n
+            int ti = 0;
+            for (int r = 0; r < R; ++r) {
+                acc = caddf(acc, cmulf(x[base + r * h], twf<INV>(tw, ti)));
+                ti += dq;
+                if (ti >= n) ti -= n;
+            }
+            res[u] = cmulf(acc, twf<INV>(tw, q * k * ts));
+            pos[u] = base + q * h;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kMaxOddOut; ++u)
+            if (pos[u] >= 0) x[pos[u]] = res[u];
+        __syncwarp();
+    }
+}
+
 template <bool INV>
 __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr)
 {
@@ -47,31 +124,36 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
         const int h = Nb / R;
         const int ts = n / Nb;
         const int nbf = n / R;
-        for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
-            const int ring = t / nbf, i = t % nbf;
-            const int blk = i / h, k = i % h;
-            float2 *xr = x + ring * n + blk * Nb + k;
-            if (R == 4) {
-                const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
-                const float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
-                const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
-                const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-                xr[0] = caddf(s02, s13);
-                xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
-                xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
-                xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
-            } else if (R == 2) {
-                const float2 v0 = xr[0], v1 = xr[h];
-                xr[0] = caddf(v0, v1);
-                xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
-            } else {
-                float2 v[kMaxInlineRadix];
-                for (int q = 0; q < R; ++q) v[q] = xr[q * h];
-                const int rstep = n / R;
-                for (int q = 0; q < R; ++q) {
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int r = 0; r < R; ++r) acc = caddf(acc, cmulf(v[r], twf<INV>(tw, ((q * r) % R) * rstep)));
-                    xr[q * h] = cmulf(acc, twf<INV>(tw, (int)(((long long)q * k * ts) % n)));
+        if (R == 3) {
+            dif_stage_small<3, INV>(x, tw, n, Nb, nr);
+        } else if (R == 5) {
+            dif_stage_small<5, INV>(x, tw, n, Nb, nr);
+        } else if (R == 7) {
+            dif_stage_small<7, INV>(x, tw, n, Nb, nr);
+        } else if (R == 11) {
+            dif_stage_small<11, INV>(x, tw, n, Nb, nr);
+        } else if (R == 13) {
+            dif_stage_small<13, INV>(x, tw, n, Nb, nr);
+        } else if (R != 2 && R != 4) {
+            dif_stage_odd<INV>(x, tw, n, R, Nb, nr);
+        } else {
+            for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+                const int ring = t / nbf, i = t - ring * nbf;
+                const int blk = i / h, k = i - blk * h;
+                float2 *xr = x + ring * n + blk * Nb + k;
+                if (R == 4) {
+                    const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
+                    const float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
+                    const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
+                    const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+                    xr[0] = caddf(s02, s13);
+                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
+                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
+                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
+                } else {
+                    const float2 v0 = xr[0], v1 = xr[h];
+                    xr[0] = caddf(v0, v1);
+                    xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
                 }
             }
         }
@@ -80,7 +162,6 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
     }
 }
 
-// ---------------------------------------------------------------------------
 // Power-of-two lengths n = 2^LOG2N (64..2048): in-place decimation in frequency with
 // radix-16 butterflies held in registers, then one last radix-2^r stage (r = LOG2N mod 4,
 // or 16 when that is 0).  The last stage has no twiddles and writes its outputs back in
@@ -297,9 +378,10 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 // Blocks per SM the DFT kernels are compiled for.  At 3 (85 registers) the n = 2048
 // instantiations spill about 128 bytes per thread in the first radix-16 stage; they get
 // the 111 registers they need at 2 (inverse DFT at L = 1023: 1.05 -> 0.79 ms), and the
-// forward kernel's 24 KB record staging allows only 2 of them per SM there anyway.
+// forward kernel's 24 KB record staging allows only 2 of them per SM there anyway.  The
+// generic lengths (LOG2N = 0) hold radix-13 butterflies and their roots in registers.
 template <int LOG2N>
-__host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 11 ? 2 : 3; }
+__host__ __device__ constexpr int fft_blocks_per_sm() { return (LOG2N == 11 || LOG2N == 0) ? 2 : 3; }
 
 // Inverse-side engine: the transpose of fft_p2_from_global's factorisation (the DFT matrix is
 // symmetric, so the stages taken in reverse order, each transposed, give the same
