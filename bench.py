@@ -200,6 +200,37 @@ def time_steps(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def measure_split_other_length(L, B, stream):
+    """The split path at a degree whose longitude count is not a power of two (L = 1000:
+    n_phi = 2002 = 2*7*11*13, the paper's nearest timing row), B complex64 fields, a few
+    CUDA-event-timed steps after warm-up; per-kernel times from the plan's own events."""
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    p = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+    shape = p.tune()
+    a, b = synthetic.coefficients(L, B, seed=5, decay=1.5)
+    a = torch.as_tensor(a).to(torch.complex64).cuda()
+    b = torch.as_tensor(b).to(torch.complex64).cuda()
+    tt = torch.empty(p.field_shape(), dtype=torch.complex64, device="cuda")
+    tp = torch.empty_like(tt)
+    a2 = torch.empty_like(a)
+    b2 = torch.empty_like(b)
+
+    def st():
+        p.adj(a, b, tt, tp, stream=stream)
+        p.fwd(tt, tp, a2, b2, stream=stream)
+    ms = time_steps(st, 5, 3, stream)
+    p.profile(True)
+    time_steps(st, 2, 0, stream)
+    prof = p.profile_read()
+    p.profile(False)
+    err = max(float((a2 - a).abs().max() / a.abs().max()), float((b2 - b).abs().max() / b.abs().max()))
+    p.close()
+    return {"value": B / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms, "L": L, "nphi": 2 * (L + 1),
+            "generator_shape": list(shape), "roundtrip_max_rel": err,
+            "kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+
+
 def measure_forms(L, B, a, b, split_value, fp64_peak):
     import numpy as np
     import torch
@@ -279,6 +310,7 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     forms["field_a_tables"] = measure_field_a()
     forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
     forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
+    forms["split_L1000_B32"] = measure_split_other_length(1000, B, stream)
     return forms
 
 
