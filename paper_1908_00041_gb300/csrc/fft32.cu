@@ -47,9 +47,14 @@ constexpr int kMaxInlineRadix = 128;   // largest odd prime factor of nphi suppo
 // q k n/Nb is below n (q < R, k < Nb/R): no reduction is needed.
 constexpr int kMaxOddOut = kMaxInlineRadix / 32;   // outputs per lane for R > 32
 
+// Odd prime R: with w_R^j = (c_j, y_j) and w_R^{-j} = (c_j, -y_j), the pairs r, R - r give
+//   out_q     = v_0 + sum_{r=1}^{H} [c_{qr} (v_r + v_{R-r}) + i y_{qr} (v_r - v_{R-r})] = A_q + i B_q,
+//   out_{R-q} = A_q - i B_q,   H = (R - 1) / 2,
+// 4 H^2 real multiply-adds per butterfly instead of R (R - 1) complex ones.
 template <int R, bool INV>
 __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restrict__ tw, int n, int Nb, int nr)
 {
+    constexpr int H = (R - 1) / 2;
     const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
     float2 wr[R];                                      // w_R^j = w_n^{j n / R}
 #pragma unroll
@@ -58,16 +63,33 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
         const int ring = t / nbf, i = t - ring * nbf;
         const int blk = i / h, k = i - blk * h;
         float2 *xr = x + ring * n + blk * Nb + k;
-        float2 v[R];
+        const float2 v0 = xr[0];
+        float2 sm[H], df[H];
+        float2 out0 = v0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = xr[r * h];
+        for (int r = 1; r <= H; ++r) {
+            const float2 a = xr[r * h], b = xr[(R - r) * h];
+            sm[r - 1] = caddf(a, b);
+            df[r - 1] = csubf(a, b);
+            out0 = caddf(out0, sm[r - 1]);
+        }
+        xr[0] = out0;
         const int tk = k * ts;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            float2 acc = v[0];
+        for (int q = 1; q <= H; ++q) {
+            float2 A = v0, Bq = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int r = 1; r < R; ++r) acc = caddf(acc, cmulf(v[r], wr[(q * r) % R]));
-            xr[q * h] = q == 0 ? acc : cmulf(acc, twf<INV>(tw, q * tk));
+            for (int r = 1; r <= H; ++r) {
+                const float2 w = wr[(q * r) % R];
+                A.x = fmaf(w.x, sm[r - 1].x, A.x);
+                A.y = fmaf(w.x, sm[r - 1].y, A.y);
+                Bq.x = fmaf(w.y, df[r - 1].x, Bq.x);
+                Bq.y = fmaf(w.y, df[r - 1].y, Bq.y);
+            }
+            const float2 op = make_float2(A.x - Bq.y, A.y + Bq.x);     // A + i B
+            const float2 om = make_float2(A.x + Bq.y, A.y - Bq.x);     // A - i B
+            xr[q * h] = cmulf(op, twf<INV>(tw, q * tk));
+            xr[(R - q) * h] = cmulf(om, twf<INV>(tw, (R - q) * tk));
         }
     }
 }
