@@ -418,8 +418,8 @@ int favest_batch_group(favest_batch batch, int g, int *L, int *nfields, int *gen
     return FAVEST_OK;
 }
 
-long long favest_batch_field_elems(favest_batch batch) { return batch ? batch->field_elems : FAVEST_EINVAL; }
-long long favest_batch_coef_elems(favest_batch batch) { return batch ? batch->coef_elems : FAVEST_EINVAL; }
+long long favest_batch_field_elems(favest_batch batch) { return batch ? batch->field_elems : (long long)FAVEST_EINVAL; }
+long long favest_batch_coef_elems(favest_batch batch) { return batch ? batch->coef_elems : (long long)FAVEST_EINVAL; }
 
 int favest_batch_status(favest_batch batch, void *stream)
 {

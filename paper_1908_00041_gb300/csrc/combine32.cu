@@ -108,13 +108,6 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
     }
 }
 
-__device__ __forceinline__ float2 cf(const float2 *__restrict__ c, int L, int l, int m, size_t cb)
-{
-    int am = m < 0 ? -m : m;
-    if (l < 1 || l > L || am > l) return make_float2(0.f, 0.f);
-    return c[cb + l * l + l + m - 1];
-}
-
 constexpr int kUS = 4 * (kCT + 1) + 1;  // shared row stride (float2, odd) of the uncombine tile
 
 // Tiled uncombine.  grid.x enumerates the tiles (order block ob <= row block lb) of the
