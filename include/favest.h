@@ -232,7 +232,8 @@ int favest_launches_per_call(favest_plan plan, int adjoint);
  * recurrences of 1 or 2 latitudes (lt apart) side by side.  favest_plan_tune times the
  * candidate shapes for this plan's degree on `stream` (synchronising it, a few
  * milliseconds) and keeps the fastest; favest_plan_gen_shape reports (lt, mb) of the
- * shape in use.  Plans start with (128, 1) and 2 latitudes per thread.  The generated
+ * shape in use.  Plans start with (128, 1), with 2 latitudes per thread from 384 folded
+ * latitudes (L >= 766) up and 1 below.  The generated
  * values do not depend on the shape.  FP64 plans have nothing to tune (returns FAVEST_OK).
  */
 int favest_plan_tune(favest_plan plan, void *stream);
