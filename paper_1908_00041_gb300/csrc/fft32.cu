@@ -2,9 +2,14 @@
 // twiddles rounded to FP32).  One CTA per (field b, folded latitude j) handles the four
 // rings theta/phi x (j, nlat-1-j) (real fields: see k_rfft_fwd_bf16):
 //   forward: T -> FFT -> weighted equatorial fold F+- = omega_j (F_j +- F_j') -> three
-//            bf16 pieces written straight into the tensor-core B-operand layout.
-//   inverse: gathers the even/odd Legendre sums E, O of every order, forms
-//            G_j = (E + O) / sin(theta_j), G_j' = (E - O) / sin(theta_j), inverse FFT.
+//            bf16 pieces staged per warp and stored into the tensor-core B-operand layout
+//            by bulk asynchronous copies.
+//   inverse: streams the even/odd Legendre sums E, O of every order through shared memory
+//            (TMA boxes), forms G_j = (E + O) / sin(theta_j), G_j' = (E - O) / sin(theta_j),
+//            inverse FFT whose last stage stores to global memory.
+// Power-of-two lengths run register radix-16 butterflies (forward: decimation in frequency
+// with the first stage fed from global memory; inverse: its transpose); other lengths a
+// generic mixed-radix decimation in frequency with a digit-reversal table.
 #include "favest_internal.h"
 #include "bf16_split.cuh"
 #include "fft_device.cuh"
