@@ -227,7 +227,7 @@ def measure_split_other_length(L, B, stream):
     err = max(float((a2 - a).abs().max() / a.abs().max()), float((b2 - b).abs().max() / b.abs().max()))
     p.close()
     return {"value": B / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms, "L": L, "nphi": 2 * (L + 1),
-            "generator_shape": list(shape), "roundtrip_max_rel": err,
+            "generator_shape": list(shape) + [p.gen_chains()], "roundtrip_max_rel": err,
             "kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
 
 
@@ -610,7 +610,7 @@ def main():
     # plan set-up (untimed): the generator's block shape picked by the autotuner
     gen_shape = None
     if prec == api.FAVEST_BF16X6:
-        gen_shape = plan.gen_shape() if args.no_tune else plan.tune()
+        gen_shape = list(plan.gen_shape() if args.no_tune else plan.tune()) + [plan.gen_chains()]
     a_h, b_h = synthetic.coefficients(L, B, seed=2, decay=1.5)
     a = torch.as_tensor(a_h).to(torch.complex64).cuda()
     b = torch.as_tensor(b_h).to(torch.complex64).cuda()

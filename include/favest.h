@@ -238,6 +238,9 @@ int favest_launches_per_call(favest_plan plan, int adjoint);
  */
 int favest_plan_tune(favest_plan plan, void *stream);
 int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
+/* Latitude recurrences per generator thread of the shape in use (1 or 2); FAVEST_EINVAL for
+ * a null plan. */
+int favest_plan_gen_chains(favest_plan plan);
 
 /*
  * Ragged batches: nfields fields of individual degrees L[i] (host array), each on its

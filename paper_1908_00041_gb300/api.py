@@ -90,6 +90,7 @@ def lib(build_if_missing=False):
             L.favest_plan_tune.argtypes = [vp, vp]
             L.favest_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint, d]
             L.favest_plan_gen_shape.argtypes = [vp, pi, pi]
+            L.favest_plan_gen_chains.argtypes = [vp]
             L.favest_batch_create.argtypes = [i, pi, pll, pll, i, i, i, ctypes.POINTER(vp)]
             L.favest_fwd_batched.argtypes = [vp, vp, vp, vp, vp, vp]
             L.favest_adj_batched.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -341,6 +342,12 @@ class Plan:
         _check(lib().favest_plan_gen_shape(ctypes.c_void_p(self.handle), ctypes.byref(lt), ctypes.byref(mb)),
                "favest_plan_gen_shape")
         return lt.value, mb.value
+
+    def gen_chains(self):
+        """Latitude recurrences per generator thread of the shape in use (1 or 2)."""
+        n = lib().favest_plan_gen_chains(ctypes.c_void_p(self.handle))
+        _check(n if n < 0 else 0, "favest_plan_gen_chains")
+        return n
 
     def launches_per_call(self, adjoint=0):
         return favest_launches_per_call(self.handle, adjoint)

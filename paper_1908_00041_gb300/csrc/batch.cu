@@ -251,6 +251,8 @@ int favest_plan_tune(favest_plan plan, void *stream)
     return st;
 }
 
+int favest_plan_gen_chains(favest_plan plan) { return plan ? plan->p.gen_nj : FAVEST_EINVAL; }
+
 int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb)
 {
     if (!plan || !lt || !mb) return FAVEST_EINVAL;

@@ -127,3 +127,25 @@ def test_bf16x6_polar_rings_flat_spectrum(decay):
         # the polar rings themselves, relative to the field's maximum
         pole = np.concatenate([g[:, :3] - r[:, :3], g[:, -3:] - r[:, -3:]], axis=1)
         assert np.abs(pole).max() < TOL * np.abs(r).max()
+
+
+@pytest.mark.parametrize("L,B", [(63, 2), (255, 3), (767, 1)])
+def test_generator_shape_does_not_change_results(L, B):
+    """The autotuner may pick another generator shape (latitudes per block, order groups,
+    one or two latitude recurrences per thread): the transforms stay bit-identical.  Untuned
+    plans start with two recurrences per thread from 384 folded latitudes (L >= 766) up."""
+    a, b = synthetic.coefficients(L, B, seed=3000 + L, decay=1.0)
+    plan = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+    assert plan.gen_chains() == (2 if L >= 766 else 1)
+    ca, cb = _c64(a), _c64(b)
+    t0, p0 = plan.adj(ca, cb)
+    f0, g0 = plan.fwd(t0, p0)
+    torch.cuda.synchronize()
+    plan.tune()
+    assert plan.gen_chains() in (1, 2) and plan.gen_shape()[0] in (32, 64, 128)
+    t1, p1 = plan.adj(ca, cb)
+    f1, g1 = plan.fwd(t0, p0)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(t0, t1) and torch.equal(p0, p1)
+    assert torch.equal(f0, f1) and torch.equal(g0, g1)
