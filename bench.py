@@ -571,6 +571,33 @@ def cpu_baseline(args):
                       "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (frac, dt)}
 
 
+def bind_to_gpu_cpus(dev):
+    """Run this process on the CPUs local to GPU `dev` (its PCI device's local_cpulist), so
+    that the pinned host buffers of the end-to-end measurement are allocated on the GPU's own
+    memory node; returns the number of CPUs kept, or None when the list is unavailable."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (
+            pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return len(cpus)
+    except Exception:
+        return None
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -588,6 +615,7 @@ def main():
     from paper_1908_00041_gb300 import api, synthetic
 
     torch.cuda.set_device(local)
+    host_cpus = bind_to_gpu_cpus(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -766,7 +794,8 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB per step vs 129 MB L2)"
                              % ((a.numel() * 16 + tt.numel() * 16) / 1e9),
                        "parallelism": "replicas x%d" % world, "workspace_bytes": ws,
-                       "generator_shape": list(gen_shape) if gen_shape else None},
+                       "generator_shape": list(gen_shape) if gen_shape else None,
+                       "host_cpus_local_to_gpu": host_cpus},
             "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "errors": errors, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
