@@ -225,9 +225,10 @@ def measure_split_other_length(L, B, stream):
     prof = p.profile_read()
     p.profile(False)
     err = max(float((a2 - a).abs().max() / a.abs().max()), float((b2 - b).abs().max() / b.abs().max()))
+    shape = list(shape) + [p.gen_chains()]
     p.close()
     return {"value": B / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms, "L": L, "nphi": 2 * (L + 1),
-            "generator_shape": list(shape) + [p.gen_chains()], "roundtrip_max_rel": err,
+            "generator_shape": shape, "roundtrip_max_rel": err,
             "kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
 
 
@@ -310,7 +311,7 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     forms["field_a_tables"] = measure_field_a()
     forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
     forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
-    forms["split_L1000_B32"] = measure_split_other_length(1000, B, stream)
+    forms["split_L1000_B%d" % B] = measure_split_other_length(1000, B, stream)
     return forms
 
 
