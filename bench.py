@@ -309,6 +309,7 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     for Br in (B, 2 * B):
         forms["real_fields_B%d" % Br] = measure_real(L, Br, stream)
     forms["field_a_tables"] = measure_field_a()
+    forms["cg_stability_ratios"] = measure_stability()
     forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
     forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
     forms["split_L1000_B%d" % B] = measure_split_other_length(1000, B, stream)
@@ -382,6 +383,34 @@ def measure_cg_route(L, stream):
            "input": "coefficients N(0,1)(l+1)^-1, seed 1; T = the theta/phi FP64 adjoint in Cartesian components"}
     cp.close()
     p64.close()
+    return out
+
+
+def measure_stability():
+    """Stability ratios of the forward CG route (Sec. 5.5, eq. r_stable) at L = 5 and 10 for
+    N from 100 to 100,000 points, the ranges of the paper's stability figures.  Area-uniform
+    random points (cos(theta) uniform, seed 2019) stand in for the paper's spherical designs;
+    the ratios depend on the colatitude only.  Timed through the C-ABI call from host
+    arrays (copy, three kernels, read-back) at L = 10, N = 100,000."""
+    import numpy as np
+    from paper_1908_00041_gb300 import api
+    out = {"points": "cos(theta) uniform on (-1, 1), numpy default_rng(2019)", "series": {}}
+    for L, Ns in ((5, (100, 1000, 10000)), (10, (100, 1000, 10000, 100000))):
+        for N in Ns:
+            z = np.random.default_rng(2019).uniform(-1.0, 1.0, N)
+            r = api.favest_cg_stability(L, z)
+            out["series"]["L%d_N%d" % (L, N)] = {"r_hat": r[0], "kappa_hat": r[1], "r_tilde": r[2],
+                                                 "kappa_tilde": r[3], "r_hat_over_N": r[0] / N,
+                                                 "r_tilde_over_N": r[2] / N}
+    z = np.random.default_rng(2019).uniform(-1.0, 1.0, 100000)
+    api.favest_cg_stability(10, z)
+    reps = 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        api.favest_cg_stability(10, z)
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    out["L10_N100000_ms_per_call"] = ms
+    out["L10_N100000_point_coefficients_per_s"] = 100000 * 120 / (ms * 1e-3)
     return out
 
 

@@ -171,6 +171,31 @@ int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *str
 int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, void *stream);
 
 /*
+ * Stability ratios of the forward Clebsch-Gordan route (Sec. 5.5, eq. r_stable).  Thm. 1
+ * writes Y^div_lm(x)^* as six terms xi_q Y*_{l',m'}(x) u_q and Y^curl_lm(x)^* as three terms
+ * mu_q Y*_{l,m'}(x) u_q (u_q unit vectors).  Per point x_k and coefficient (l, m):
+ *   rho_hat   = |Y^div_lm(x_k)|  / Vhat,    Vhat   = sqrt2 sum_q |xi_q| |Y_{l',m'}(x_k)|,
+ *   rho_tilde = |Y^curl_lm(x_k)| / Vtilde,  Vtilde = sqrt2 sum_q |mu_q| |Y_{l,m'}(x_k)|,
+ * i.e. the printed ratio of the size of the sum to the sum of the sizes of its terms
+ * (|xi| taken since Clebsch-Gordan values can be negative; a point where V = 0 has no
+ * ratio and is skipped).  Both depend on the colatitude only.
+ *   L: 1..1023.  npts: 1..2^28.
+ *   cos_theta: host [npts], cos(theta_k) of the points, each strictly inside (-1, 1).
+ *   per_coef: host [4][L^2+2L] or NULL; receives per coefficient (l-major order) the
+ *     maximum and minimum over the points of rho_hat, then of rho_tilde (0 and +inf for a
+ *     coefficient no point gives a ratio).
+ *   ratios: host [4]: r_hat = max rho_hat, kappa_hat = max 1/rho_hat, r_tilde, kappa_tilde,
+ *     over l <= L, 1 <= |m| <= l (the range of eq. r_stable) and the points.  The printed
+ *     ratio is at most 1/sqrt2 (triangle inequality); kappa is the condition number of the
+ *     route's sums in the sense of Higham's summation analysis, which Sec. 5.5 cites.
+ * Copies the points to a device buffer of the library's own (freed before returning),
+ * runs on `stream` and synchronises it; FAVEST_EINVAL for bad arguments, FAVEST_ENOMEM
+ * if the buffer cannot be allocated, FAVEST_ECUDA if a copy or launch fails.
+ */
+int favest_cg_stability(int L, int npts, const double *cos_theta, double *per_coef, double *ratios,
+                        void *stream);
+
+/*
  * Weighting of the forward transform.  flag = 0 (default): the quadrature weights of
  * eq. fwdvsht2.  flag = 1: unit weights, i.e. favest_fwd computes A^H T, the exact
  * adjoint of favest_adj (used by reverse-mode differentiation of AdjVSHT).

@@ -107,6 +107,7 @@ def lib(build_if_missing=False):
             L.favest_cg_plan_create.argtypes = [i, i, d, d, ctypes.POINTER(vp)]
             L.favest_fwd_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_adj_cart.argtypes = [vp, vp, vp, vp, vp]
+            L.favest_cg_stability.argtypes = [i, i, d, d, d, vp]
             L.favest_profile_enable.argtypes = [vp, i]
             L.favest_profile_read.argtypes = [vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_longlong)]
@@ -242,6 +243,21 @@ def favest_probe_peaks():
     f32 = ctypes.c_double()
     _check(lib().favest_probe_peaks(ctypes.byref(f64), ctypes.byref(f32)), "favest_probe_peaks")
     return f64.value, f32.value
+
+
+def favest_cg_stability(L, cos_theta, stream=None, per_coef=False):
+    """Stability ratios of the forward CG route (Sec. 5.5, eq. r_stable) at points with the
+    given cos(theta) values (host array): (r_hat, kappa_hat, r_tilde, kappa_tilde), and with
+    per_coef the 4 x (L^2+2L) per-coefficient extremes as well."""
+    z = np.ascontiguousarray(np.asarray(cos_theta, dtype=np.float64).ravel())
+    K = L * L + 2 * L
+    r = np.empty(4)
+    ext = np.empty((4, K)) if per_coef else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().favest_cg_stability(int(L), int(z.size), z.ctypes.data_as(dp),
+                                     ext.ctypes.data_as(dp) if per_coef else None, r.ctypes.data_as(dp),
+                                     _stream(stream)), "favest_cg_stability")
+    return (tuple(float(v) for v in r), ext) if per_coef else tuple(float(v) for v in r)
 
 
 def favest_strerror(status):

@@ -164,6 +164,186 @@ __global__ void k_cg_uncombine(const double2 *__restrict__ a, const double2 *__r
     for (int c = 0; c < 3; ++c) Q[row * ncol + 2 * (3 * f + c) + (m < 0)] = cscale(kk, g[c]);
 }
 
+// ---------------------------------------------------------------------------------------
+// Stability ratios of the forward route (Sec. 5.5, eq. r_stable).  Thm. 1 writes
+// Y^div_lm(x)^* as six terms xi_q Y*_{l',m'}(x) u_q and Y^curl_lm(x)^* as three terms, with the
+// constant vectors u_- = (-1, i, 0)/sqrt2 (orders m-1), u_+ = (1, i, 0)/sqrt2 (orders m+1) and
+// e_3 (order m).  All terms of one sum carry the same phase e^{-i m phi} (e^{-i(m-/+1) phi} of
+// the scalar harmonic times the e^{+/-i phi} that u_-/+ contributes to e_theta and e_phi), so the
+// sizes depend on theta alone and are taken at phi = 0, where Y_{l',m'} = lambda_{l'}^{m'} is
+// real (lambda^{-mu} = (-1)^mu lambda^mu, one sign per order).  With
+//   A = xi1 lambda_{l-1}^{m-1} + xi2 lambda_{l+1}^{m-1},  C = xi3 lambda_{l-1}^{m+1} + xi4 lambda_{l+1}^{m+1},
+//   E = xi5 lambda_{l-1}^m + xi6 lambda_{l+1}^m,
+// the T^(1), T^(2), T^(3) weights are (C - A)/sqrt2, i (A + C)/sqrt2, E, so
+//   |Y^div_lm|^2 = A^2 + C^2 + E^2,    Vhat = sqrt2 (sum of the six |xi_q lambda_q|),
+// and with P = mu1 lambda_l^{m-1}, Q = mu3 lambda_l^{m+1}, R = mu2 lambda_l^m
+//   |Y^curl_lm|^2 = P^2 + Q^2 + R^2,   Vtilde = sqrt2 (|P| + |Q| + |R|).
+// rho = size / V (a point where V = 0 has no ratio).  Both ratios are invariant under a
+// common scale of the three orders' lambda columns, which the kernel exploits below.
+//
+// One thread per (point, order mu): the orders b, b+1, b+2 with b = max(mu-1, 0) cover
+// m = +mu (orders mu-1, mu, mu+1), m = -mu (the same three, mirrored) and, for mu = 0, m = 0
+// (orders 1, 0, 1).  The three columns run the normalised three-term recurrence in lockstep
+// over the degree n = b..L+1 from starts lambda_o^o / sin(theta)^b = c_o sin^(o-b) (the
+// common factor sin^b removed so nothing underflows near the poles); whenever the newest
+// values pass 2^400 all columns are scaled by 2^-400 together.  After degree n the window
+// holds degrees n-2, n-1, n and the thread forms the ratios of l = n-1.  The extremes over
+// the points are reduced per warp and merged with 64-bit atomics on the bit patterns, which
+// order like the values for non-negative doubles.
+
+constexpr int kStabThreads = 256;
+
+__device__ __forceinline__ double sel3(int j, double a0, double a1, double a2)
+{
+    return j == 0 ? a0 : (j == 1 ? a1 : a2);
+}
+
+__device__ __forceinline__ void warp_maxmin(double &mx, double &mn)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+}
+
+__global__ void k_stability_init(double *ext, int K)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    ext[i] = 0.0;
+    ext[K + i] = __longlong_as_double(0x7ff0000000000000LL);
+    ext[2 * K + i] = 0.0;
+    ext[3 * K + i] = __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// ext: [4][K] = max rho_hat, min rho_hat, max rho_tilde, min rho_tilde per coefficient
+__global__ void __launch_bounds__(kStabThreads) k_stability(const double *__restrict__ z, int npts, int L, int K,
+                                                           double *ext)
+{
+    const int k = blockIdx.x * kStabThreads + threadIdx.x;
+    const bool live = k < npts;                      // dead lanes follow the loop (warp shuffles)
+    const double x = live ? z[k] : 0.0;
+    const double s = sqrt((1.0 - x) * (1.0 + x));
+    const int mu = blockIdx.y, b = mu > 0 ? mu - 1 : 0;
+    const double r2 = 1.4142135623730951;
+
+    // c_o = |lambda_o^o| / sin^o = sqrt((2o+1)/(4 pi) (2o-1)!!/(2o)!!)
+    double cb = 0.28209479177387814;                 // 1/sqrt(4 pi)
+    for (int o = 1; o <= b; ++o) cb *= sqrt((2.0 * o + 1.0) / (2.0 * o));
+    const double start[3] = {cb, cb * sqrt((2.0 * b + 3.0) / (2.0 * b + 2.0)) * s,
+                             cb * sqrt((2.0 * b + 3.0) / (2.0 * b + 2.0)) * sqrt((2.0 * b + 5.0) / (2.0 * b + 4.0)) * s * s};
+    double w0[3] = {0.0, 0.0, 0.0}, w1[3] = {0.0, 0.0, 0.0}, w2[3] = {0.0, 0.0, 0.0};   // degrees n-2, n-1, n
+    double eprev[3] = {0.0, 0.0, 0.0};               // eps_{n-1}^o of the previous step
+    for (int n = b; n <= L + 1; ++n) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int o = b + j;
+            w0[j] = w1[j];
+            w1[j] = w2[j];
+            double v = 0.0;
+            if (n == o) {
+                v = start[j];
+            } else if (n == o + 1) {
+                v = sqrt(2.0 * o + 3.0) * x * w1[j];
+                eprev[j] = 1.0 / sqrt(2.0 * o + 3.0);                        // eps_{o+1}^o
+            } else if (n > o + 1) {
+                const double e = sqrt(((double)n * n - (double)o * o) / (4.0 * n * n - 1.0));   // eps_n^o
+                v = (x * w1[j] - eprev[j] * w0[j]) / e;
+                eprev[j] = e;
+            }
+            w2[j] = v;
+        }
+        const int l = n - 1;
+        if (l >= 1 && l >= mu && l <= L) {
+            const double cl = cl_of(l), dl = dl_of(l);
+            for (int sg = 0; sg < (mu > 0 ? 2 : 1); ++sg) {
+                const int m = sg ? -mu : mu;
+                // columns of the orders |m-1|, |m|, |m+1|
+                const int jm = mu == 0 ? 1 : (sg ? 2 : 0), j0 = mu == 0 ? 0 : 1, jp = mu == 0 ? 1 : (sg ? 0 : 2);
+                const double t1 = cl * clebsch(0, l, m) * sel3(jm, w0[0], w0[1], w0[2]);
+                const double t2 = dl * clebsch(1, l, m) * sel3(jm, w2[0], w2[1], w2[2]);
+                const double t3 = cl * clebsch(4, l, m) * sel3(jp, w0[0], w0[1], w0[2]);
+                const double t4 = dl * clebsch(5, l, m) * sel3(jp, w2[0], w2[1], w2[2]);
+                const double t5 = cl * clebsch(2, l, m) * sel3(j0, w0[0], w0[1], w0[2]);
+                const double t6 = dl * clebsch(3, l, m) * sel3(j0, w2[0], w2[1], w2[2]);
+                const double A = t1 + t2, C = t3 + t4, E = t5 + t6;
+                const double vh = r2 * (fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4) + fabs(t5) + fabs(t6));
+                const double P = clebsch(6, l, m) * sel3(jm, w1[0], w1[1], w1[2]);
+                const double Q = clebsch(7, l, m) * sel3(jp, w1[0], w1[1], w1[2]);
+                const double R = clebsch(8, l, m) * sel3(j0, w1[0], w1[1], w1[2]);
+                const double vt = r2 * (fabs(P) + fabs(Q) + fabs(R));
+                const double inf = __longlong_as_double(0x7ff0000000000000LL);
+                double hmx = 0.0, hmn = inf, tmx = 0.0, tmn = inf;
+                if (live && vh > 0.0) hmx = hmn = sqrt(A * A + C * C + E * E) / vh;
+                if (live && vt > 0.0) tmx = tmn = sqrt(P * P + Q * Q + R * R) / vt;
+                warp_maxmin(hmx, hmn);
+                warp_maxmin(tmx, tmn);
+                if ((threadIdx.x & 31) == 0) {
+                    unsigned long long *e = reinterpret_cast<unsigned long long *>(ext);
+                    const int i = l * l + l + m - 1;
+                    atomicMax(e + i, (unsigned long long)__double_as_longlong(hmx));
+                    atomicMin(e + K + i, (unsigned long long)__double_as_longlong(hmn));
+                    atomicMax(e + 2 * K + i, (unsigned long long)__double_as_longlong(tmx));
+                    atomicMin(e + 3 * K + i, (unsigned long long)__double_as_longlong(tmn));
+                }
+            }
+        }
+        if (n >= b + 2) {
+            double big = 0.0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) big = fmax(big, fmax(fabs(w1[j]), fabs(w2[j])));
+            if (big > 0x1p400) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    w1[j] *= 0x1p-400;
+                    w2[j] *= 0x1p-400;
+                }
+            }
+        }
+    }
+}
+
+// r[4] = r_hat, kappa_hat, r_tilde, kappa_tilde over l <= L, 1 <= |m| <= l; one block
+__global__ void __launch_bounds__(kStabThreads) k_stability_reduce(const double *__restrict__ ext, int K, double *r)
+{
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    double hmx = 0.0, hmn = inf, tmx = 0.0, tmn = inf;
+    for (int i = threadIdx.x; i < K; i += kStabThreads) {
+        int l = (int)sqrt((double)(i + 1));
+        while (l * l + 2 * l < i + 1) ++l;
+        while ((l - 1) * (l - 1) + 2 * (l - 1) >= i + 1) --l;
+        if (i - l * l - l + 1 == 0) continue;        // m = 0 is outside eq. r_stable
+        hmx = fmax(hmx, ext[i]);
+        hmn = fmin(hmn, ext[K + i]);
+        tmx = fmax(tmx, ext[2 * K + i]);
+        tmn = fmin(tmn, ext[3 * K + i]);
+    }
+    warp_maxmin(hmx, hmn);
+    warp_maxmin(tmx, tmn);
+    __shared__ double sh[4][kStabThreads / 32];
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][wid] = hmx;
+        sh[1][wid] = hmn;
+        sh[2][wid] = tmx;
+        sh[3][wid] = tmn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kStabThreads / 32; ++w) {
+            hmx = fmax(hmx, sh[0][w]);
+            hmn = fmin(hmn, sh[1][w]);
+            tmx = fmax(tmx, sh[2][w]);
+            tmn = fmin(tmn, sh[3][w]);
+        }
+        r[0] = hmx;
+        r[1] = 1.0 / hmn;
+        r[2] = tmx;
+        r[3] = 1.0 / tmn;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s)
@@ -185,3 +365,35 @@ cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cud
 }
 
 }  // namespace favest
+
+extern "C" int favest_cg_stability(int L, int npts, const double *cos_theta, double *per_coef, double *ratios,
+                                   void *stream)
+{
+    using namespace favest;
+    if (L < 1 || L > 1023 || npts < 1 || npts > (1 << 28) || !cos_theta || !ratios) return FAVEST_EINVAL;
+    for (int k = 0; k < npts; ++k)
+        if (!(fabs(cos_theta[k]) < 1.0)) return FAVEST_EINVAL;    // also rejects NaN
+    const int K = L * L + 2 * L;
+    const size_t nz = (size_t)npts, bytes = (nz + 4 * (size_t)K + 4) * sizeof(double);
+    double *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FAVEST_ENOMEM;
+    }
+    double *dz = d, *dext = d + nz, *dr = dext + 4 * (size_t)K;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t err = cudaMemcpyAsync(dz, cos_theta, nz * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) {
+        k_stability_init<<<(K + kStabThreads - 1) / kStabThreads, kStabThreads, 0, s>>>(dext, K);
+        k_stability<<<dim3((unsigned)((npts + kStabThreads - 1) / kStabThreads), (unsigned)(L + 1)), kStabThreads, 0,
+                      s>>>(dz, npts, L, K, dext);
+        k_stability_reduce<<<1, kStabThreads, 0, s>>>(dext, K, dr);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaMemcpyAsync(ratios, dr, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess && per_coef)
+        err = cudaMemcpyAsync(per_coef, dext, 4 * (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    cudaFree(d);
+    return err == cudaSuccess ? FAVEST_OK : FAVEST_ECUDA;
+}

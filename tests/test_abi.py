@@ -101,3 +101,20 @@ def test_new_entry_points_reject_bad_arguments(lib):
     assert L.favest_batch_create(2, Ls, off, None, api.FAVEST_BF16X6, api.FAVEST_IO_R32, 0,
                                  ctypes.byref(h)) == api.FAVEST_EINVAL
     assert L.favest_kernel_work(nul, b"fft_fwd", None, None, None) == api.FAVEST_EINVAL
+
+
+def test_cg_stability_rejects_bad_arguments(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    r = np.empty(4)
+
+    def call(L, z, ratios=True):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        return api.lib().favest_cg_stability(L, len(z), z.ctypes.data_as(dp) if len(z) else None, None,
+                                             r.ctypes.data_as(dp) if ratios else None, ctypes.c_void_p(0))
+    ok = np.array([0.1, -0.5])
+    assert call(0, ok) == api.FAVEST_EINVAL
+    assert call(1024, ok) == api.FAVEST_EINVAL
+    assert call(5, np.array([])) == api.FAVEST_EINVAL
+    assert call(5, ok, ratios=False) == api.FAVEST_EINVAL
+    for bad in (1.0, -1.0, 1.5, np.nan, np.inf):
+        assert call(5, np.array([0.2, bad])) == api.FAVEST_EINVAL
