@@ -52,6 +52,17 @@ constexpr int kMaxInlineRadix = 128;   // largest odd prime factor of nphi suppo
 // q k n/Nb is below n (q < R, k < Nb/R): no reduction is needed.
 constexpr int kMaxOddOut = kMaxInlineRadix / 32;   // outputs per lane for R > 32
 
+// Butterfly index -> (ring, block, k) without integer division: q = floor(x / d) for
+// 0 <= x < 2^15 and 1 <= d <= 4096 as the high word of x * m, m = floor((2^32 - 1) / d) + 1
+// (ceil(2^32 / d) unless d is a power of two, then exact): the excess x (m d - 2^32) / 2^32
+// stays below 1 while x d < 2^32, which these ranges (x < 4 rings * 1024, d <= 2048) keep.
+struct Recip {
+    unsigned m;
+    int d;
+};
+__device__ __forceinline__ Recip recip(int d) { return Recip{0xffffffffu / (unsigned)d + 1u, d}; }
+__device__ __forceinline__ int rdiv(int x, Recip r) { return r.d == 1 ? x : (int)__umulhi((unsigned)x, r.m); }
+
 // Odd prime R: with w_R^j = (c_j, y_j) and w_R^{-j} = (c_j, -y_j), the pairs r, R - r give
 //   out_q     = v_0 + sum_{r=1}^{H} [c_{qr} (v_r + v_{R-r}) + i y_{qr} (v_r - v_{R-r})] = A_q + i B_q,
 //   out_{R-q} = A_q - i B_q,   H = (R - 1) / 2,
@@ -64,9 +75,10 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
     float2 wr[R];                                      // w_R^j = w_n^{j n / R}
 #pragma unroll
     for (int j = 0; j < R; ++j) wr[j] = twf<INV>(tw, j * rstep);
+    const Recip rn = recip(nbf), rh = recip(h);
     for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
-        const int ring = t / nbf, i = t - ring * nbf;
-        const int blk = i / h, k = i - blk * h;
+        const int ring = rdiv(t, rn), i = t - ring * nbf;
+        const int blk = rdiv(i, rh), k = i - blk * h;
         float2 *xr = x + ring * n + blk * Nb + k;
         const float2 v0 = xr[0];
         float2 sm[H], df[H];
@@ -110,12 +122,13 @@ __device__ __forceinline__ void dif_stage_odd(float2 *x, const float2 *__restric
     const int lb = R <= 32 ? lane / R : 0, lq = R <= 32 ? lane % R : lane;
     const bool lane_ok = R > 32 || lane < per * R;
     const int total = nbf * nr;
+    const Recip rn = recip(nbf), rh = recip(h);
     for (int b0 = warp * per; b0 < total; b0 += nw * per) {
         float2 res[kMaxOddOut];
         int pos[kMaxOddOut];
         const int bi = b0 + lb;
-        const int ring = bi / nbf, i = bi - ring * nbf;
-        const int blk = i / h, k = i - blk * h;
+        const int ring = rdiv(bi, rn), i = bi - ring * nbf;
+        const int blk = rdiv(i, rh), k = i - blk * h;
         const int base = ring * n + blk * Nb + k;
 #pragma unroll
         for (int u = 0; u < kMaxOddOut; ++u) {
@@ -164,9 +177,10 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
         } else if (R != 2 && R != 4) {
             dif_stage_odd<INV>(x, tw, n, R, Nb, nr);
         } else {
+            const Recip rn = recip(nbf), rh = recip(h);
             for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
-                const int ring = t / nbf, i = t - ring * nbf;
-                const int blk = i / h, k = i - blk * h;
+                const int ring = rdiv(t, rn), i = t - ring * nbf;
+                const int blk = rdiv(i, rh), k = i - blk * h;
                 float2 *xr = x + ring * n + blk * Nb + k;
                 if (R == 4) {
                     const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
