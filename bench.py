@@ -572,8 +572,8 @@ def reference_arm(args, rank):
         "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "L=1023 GL 1024x2048, coefficients N(0,1)(l+1)^-1.5, seed 2 "
-                               "(bounded sample of the batch-32 precision form)",
+        "config": {"workload": "L=%d GL %dx%d, coefficients N(0,1)(l+1)^-1.5, seed 2 "
+                               "(bounded sample of the batch-32 precision form)" % (L, L + 1, 2 * (L + 1)),
                    "L": L, "batch": 1, "sample_orders_step": mstep},
         "cpu_baseline": {"value": val, "unit": "fields/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -817,9 +817,9 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x6" if prec_name == "bf16x6" else "f64",
             "data": "synthetic",
-            "config": {"workload": "precision form: L=1023, Gauss-Legendre grid 1024x2048, batch %d "
+            "config": {"workload": "precision form: L=%d, Gauss-Legendre grid %dx%d, batch %d "
                                    "fields, coefficients N(0,1)(l+1)^-1.5 seed 2, complex64 tangent "
-                                   "components; step = AdjVSHT then FwdVSHT" % B,
+                                   "components; step = AdjVSHT then FwdVSHT" % (L, L + 1, 2 * (L + 1), B),
                        "L": L, "batch": B, "precision": prec_name, "io": "complex64",
                        "l2": "inputs larger than L2 (%.2f GB per step vs 129 MB L2)"
                              % ((a.numel() * 16 + tt.numel() * 16) / 1e9),
