@@ -596,9 +596,23 @@ def cpu_baseline(args):
     oracle.fwd_sep_orders(L, x, W, tt, tp, 0, mstep)
     dt = time.perf_counter() - t0
     frac = len(range(0, nm, mstep)) / nm
-    return {"value": frac / dt, "unit": "fields/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "one field of the L=1023 workload, adjoint+forward over every 2nd order "
-                      "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (frac, dt)}
+    cores = oracle.num_threads()
+    # the same oracle on one thread, over every 32nd order (a sixteenth of the sample above)
+    m1 = 32
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        tt, tp = oracle.adj_sep_orders(L, x, a[0], b[0], 2 * (L + 1), 0, m1)
+        oracle.fwd_sep_orders(L, x, W, tt, tp, 0, m1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    frac1 = len(range(0, nm, m1)) / nm
+    return {"value": frac / dt, "unit": "fields/s", "cores": cores, "kind": "oracle",
+            "sample": "one field of the L=%d workload, adjoint+forward over every 2nd order "
+                      "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (L, frac, dt),
+            "single_thread": {"value": frac1 / dt1, "unit": "fields/s", "cores": 1,
+                              "sample": "every 32nd order (%.4f of the orders), %.1f s" % (frac1, dt1)}}
 
 
 def bind_to_gpu_cpus(dev):
