@@ -612,7 +612,49 @@ def cpu_baseline(args):
             "sample": "one field of the L=%d workload, adjoint+forward over every 2nd order "
                       "(%.4f of the orders) with the separable FP64 oracle, %.1f s" % (L, frac, dt),
             "single_thread": {"value": frac1 / dt1, "unit": "fields/s", "cores": 1,
-                              "sample": "every 32nd order (%.4f of the orders), %.1f s" % (frac1, dt1)}}
+                              "sample": "every 32nd order (%.4f of the orders), %.1f s" % (frac1, dt1)},
+            "small_configs": cpu_small_configs()}
+
+
+def cpu_small_configs():
+    """The oracle at the one-field FP64 configurations, L = 16 (17 x 34 grid) and L = 511
+    (512 x 1024), adjoint + forward in fields/s: the separable form (O3) and the direct
+    definition (every coefficient a sum over all grid points, every grid value a sum over all
+    coefficients) on samples scaled to the whole transform."""
+    import numpy as np
+    import oracle
+    from paper_1908_00041_gb300 import synthetic
+    out = {}
+    for L, mstep, ncoef_s, npts_s in ((16, 1, None, None), (511, 8, 16, 16)):
+        x, W, _, _ = oracle.grid(L)
+        nlat, nphi = L + 1, 2 * (L + 1)
+        a, b = synthetic.coefficients(L, 1, seed=1, decay=1.0)
+        nm = 2 * L + 1
+        t0 = time.perf_counter()
+        tt, tp = oracle.adj_sep_orders(L, x, a[0], b[0], nphi, 0, mstep)
+        oracle.fwd_sep_orders(L, x, W, tt, tp, 0, mstep)
+        t_sep = (time.perf_counter() - t0) / (len(range(0, nm, mstep)) / nm)
+        K = L * L + 2 * L
+        ls = np.array([l for l in range(1, L + 1) for _ in range(-l, l + 1)])
+        ms = np.array([m for l in range(1, L + 1) for m in range(-l, l + 1)])
+        js, ks = np.divmod(np.arange(nlat * nphi), nphi)
+        if ncoef_s:
+            pick = np.random.default_rng(0).choice(K, ncoef_s, replace=False)
+            ls, ms = ls[pick], ms[pick]
+            pt = np.random.default_rng(1).choice(nlat * nphi, npts_s, replace=False)
+            js, ks = js[pt], ks[pt]
+        t0 = time.perf_counter()
+        oracle.fwd_literal_grid_coefs(L, x, W, tt, tp, ls, ms)
+        t_f = (time.perf_counter() - t0) * K / len(ls)
+        t0 = time.perf_counter()
+        oracle.adj_literal_grid_points(L, nlat, nphi, x, a[0], b[0], js, ks)
+        t_a = (time.perf_counter() - t0) * nlat * nphi / len(js)
+        out["L%d" % L] = {"separable_fields_per_s": 1.0 / t_sep, "direct_fields_per_s": 1.0 / (t_f + t_a),
+                          "sample": "separable over every %d%s order; direct over %s" % (
+                              mstep, {1: "st", 8: "th"}[mstep],
+                              "all coefficients and grid points" if not ncoef_s else
+                              "%d coefficients and %d grid points, scaled" % (ncoef_s, npts_s))}
+    return out
 
 
 def bind_to_gpu_cpus(dev):
