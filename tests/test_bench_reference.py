@@ -28,3 +28,17 @@ def test_reference_arm_json_line():
     e2e = rec["e2e"]
     assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_block():
+    """The GPU arm's cpu_baseline object (all cores, one thread, the small configurations),
+    built on the host alone."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.cpu_baseline(argparse.Namespace(L=31))
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1 and "L=31" in cb["sample"]
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    sc = cb["small_configs"]
+    for k in ("L16", "L511"):
+        assert sc[k]["separable_fields_per_s"] > sc[k]["direct_fields_per_s"] > 0
