@@ -67,7 +67,7 @@ enum favest_status_code {
     FAVEST_EINVAL = -1,        /* bad argument (size, pointer, alignment, grid)   */
     FAVEST_ENOMEM = -2,        /* device or host allocation failed                */
     FAVEST_ECUDA = -3,         /* a CUDA runtime call failed                      */
-    FAVEST_EUNSUPPORTED = -4,  /* valid request this build or device cannot serve */
+    FAVEST_EUNSUPPORTED = -4,  /* valid request this library or device cannot serve */
     FAVEST_ETIMEOUT = -5,      /* a bounded device-side wait gave up              */
     FAVEST_EDEVICE = -6        /* a kernel recorded an internal error             */
 };
