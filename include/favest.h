@@ -268,6 +268,17 @@ int favest_plan_gen_shape(favest_plan plan, int *lt, int *mb);
 int favest_plan_gen_chains(favest_plan plan);
 
 /*
+ * Apply a generator shape without timing (e.g. one a previous favest_plan_tune chose for the
+ * same degree, batch, precision and GPU, kept in a cache): lt latitudes per block, mb order
+ * groups per block, nj latitude chains per thread.  Accepted shapes are exactly those the
+ * tuner times: (lt, mb, nj) with nj in {1, 2} and (lt, mb) in {(128, 1), (64, 1), (32, 1),
+ * (128, 2), (64, 2), (32, 2), (32, 4)}; anything else, or a NULL plan, returns FAVEST_EINVAL.
+ * On an FP64 plan (no generator) a valid shape is accepted and ignored.  Host-only; affects
+ * the plan's later calls, never its results (every shape computes identical values).
+ */
+int favest_plan_set_gen_shape(favest_plan plan, int lt, int mb, int nj);
+
+/*
  * Ragged batches: nfields fields of individual degrees L[i] (host array), each on its
  * own (L[i]+1) x 2(L[i]+1) Gauss-Legendre grid.  The caller's buffers hold the fields
  * packed: component plane of field i at element offset field_off[i] of Tth and of Tph

@@ -91,6 +91,7 @@ def lib(build_if_missing=False):
             L.favest_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint, d]
             L.favest_plan_gen_shape.argtypes = [vp, pi, pi]
             L.favest_plan_gen_chains.argtypes = [vp]
+            L.favest_plan_set_gen_shape.argtypes = [vp, i, i, i]
             L.favest_batch_create.argtypes = [i, pi, pll, pll, i, i, i, ctypes.POINTER(vp)]
             L.favest_fwd_batched.argtypes = [vp, vp, vp, vp, vp, vp]
             L.favest_adj_batched.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -358,6 +359,11 @@ class Plan:
         _check(lib().favest_plan_gen_shape(ctypes.c_void_p(self.handle), ctypes.byref(lt), ctypes.byref(mb)),
                "favest_plan_gen_shape")
         return lt.value, mb.value
+
+    def set_gen_shape(self, lt, mb, nj):
+        """Apply a generator shape the tuner offers, without timing (see tune_cache)."""
+        _check(lib().favest_plan_set_gen_shape(ctypes.c_void_p(self.handle), int(lt), int(mb), int(nj)),
+               "favest_plan_set_gen_shape")
 
     def gen_chains(self):
         """Latitude recurrences per generator thread of the shape in use (1 or 2)."""

@@ -200,9 +200,29 @@ void destroy_batch(favest_batch_s *bp)
     delete bp;
 }
 
+// Generator shapes the tuner times and favest_plan_set_gen_shape accepts:
+// (latitudes per block, order groups per block, latitude chains per thread)
+constexpr int kGenShapes[][3] = {{128, 1, 2}, {64, 1, 2}, {32, 1, 2}, {128, 2, 2}, {64, 2, 2}, {32, 2, 2},
+                                 {32, 4, 2},  {128, 1, 1}, {64, 1, 1}, {32, 1, 1}, {128, 2, 1}, {64, 2, 1},
+                                 {32, 2, 1},  {32, 4, 1}};
+
 }  // namespace
 
 extern "C" {
+
+int favest_plan_set_gen_shape(favest_plan plan, int lt, int mb, int nj)
+{
+    if (!plan) return FAVEST_EINVAL;
+    bool known = false;
+    for (const auto &c : kGenShapes) known = known || (c[0] == lt && c[1] == mb && c[2] == nj);
+    if (!known) return FAVEST_EINVAL;
+    Plan &p = plan->p;
+    if (p.precision != FAVEST_BF16X6) return FAVEST_OK;   // no generator on the FP64 path
+    p.gen_lt = lt;
+    p.gen_mb = mb;
+    p.gen_nj = nj;
+    return FAVEST_OK;
+}
 
 int favest_plan_tune(favest_plan plan, void *stream)
 {
@@ -210,9 +230,6 @@ int favest_plan_tune(favest_plan plan, void *stream)
     Plan &p = plan->p;
     if (p.precision != FAVEST_BF16X6) return FAVEST_OK;   // nothing tunable on the FP64 path
     cudaStream_t s = (cudaStream_t)stream;
-    // (latitudes per block, order groups per block, latitude chains per thread)
-    const int cand[][3] = {{128, 1, 2}, {64, 1, 2}, {32, 1, 2}, {128, 2, 2}, {64, 2, 2}, {32, 2, 2}, {32, 4, 2},
-                           {128, 1, 1}, {64, 1, 1}, {32, 1, 1}, {128, 2, 1}, {64, 2, 1}, {32, 2, 1}, {32, 4, 1}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FAVEST_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -221,7 +238,7 @@ int favest_plan_tune(favest_plan plan, void *stream)
     }
     float best = 1e30f;
     int blt = p.gen_lt, bmb = p.gen_mb, bnj = p.gen_nj, st = FAVEST_OK;
-    for (const auto &c : cand) {
+    for (const auto &c : kGenShapes) {
         if (launch_gen_lambda_shape(p, true, c[0], c[1], c[2], s) != cudaSuccess) {
             st = FAVEST_ECUDA;
             break;
