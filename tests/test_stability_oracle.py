@@ -1,7 +1,7 @@
 """Pins of the oracle's stability ratios (Sec. 5.5, eq. r_stable) against facts that do not
 come from the oracle's own construction: the size of the sum against the theta/phi closed
 form |grad* Y_lm| / sqrt(l(l+1)) (finite differences of the scalar functions), the printed
-sums of term sizes at (l, m) = (1, 1) from sympy's Clebsch-Gordan values and scipy's
+sums of term sizes for every (l, m) with l <= 3 from sympy's Clebsch-Gordan values and scipy's
 associated Legendre functions, a hand-derived closed form of rho_tilde at (1, 1), the
 triangle and Cauchy-Schwarz bounds, independence of the longitude and symmetry in m."""
 import math
@@ -61,6 +61,40 @@ def test_term_sums_at_l1_m1_from_sympy_and_scipy(orc):
         vtil = R2 * (abs(cg(1, 0, 1, 1, 1)) * ymag(1, 0, t) + abs(cg(1, 1, 0, 1, 1)) * ymag(1, 1, t))
         assert abs(vd[k, i] - vhat) < 1e-14
         assert abs(vc[k, i] - vtil) < 1e-14
+
+
+def test_term_sums_for_all_l_up_to_3_from_sympy_and_scipy(orc):
+    """Vhat and Vtilde written out from the printed formula with sympy's Clebsch-Gordan values
+    (<l' m'; 1 q | l m>) and scipy's associated Legendre functions, every (l, m), l <= 3."""
+    sympy_cg = pytest.importorskip("sympy.physics.quantum.cg")
+    special = pytest.importorskip("scipy.special")
+
+    def ymag(l, m, t):
+        if l < 0 or abs(m) > l:
+            return np.zeros_like(t)
+        m = abs(m)
+        nrm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+        return nrm * np.abs(special.lpmv(m, l, np.cos(t)))
+
+    def cg(l1, m1, q, l, m):
+        if l1 < 0 or abs(m1) > l1:
+            return 0.0
+        return float(sympy_cg.CG(l1, m1, 1, q, l, m).doit())
+
+    L = 3
+    th, ph = _points(7, 12)
+    _, vd, _, vc = stability.point_terms(L, th, ph)
+    for l in range(1, L + 1):
+        cl, dl = math.sqrt((l + 1.0) / (2 * l + 1)), math.sqrt(l / (2.0 * l + 1))
+        for m in range(-l, l + 1):
+            i = l * l + l + m - 1
+            div = [(cl, l - 1, m - 1, 1), (dl, l + 1, m - 1, 1), (cl, l - 1, m + 1, -1),
+                   (dl, l + 1, m + 1, -1), (cl, l - 1, m, 0), (dl, l + 1, m, 0)]
+            curl = [(1.0, l, m - 1, 1), (1.0, l, m + 1, -1), (1.0, l, m, 0)]
+            vhat = R2 * sum(c * abs(cg(l1, m1, q, l, m)) * ymag(l1, m1, th) for c, l1, m1, q in div)
+            vtil = R2 * sum(c * abs(cg(l1, m1, q, l, m)) * ymag(l1, m1, th) for c, l1, m1, q in curl)
+            assert np.max(np.abs(vd[:, i] - vhat)) < 1e-14, (l, m)
+            assert np.max(np.abs(vc[:, i] - vtil)) < 1e-14, (l, m)
 
 
 def test_rho_tilde_closed_form_at_l1_m1(orc):
