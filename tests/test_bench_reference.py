@@ -42,3 +42,17 @@ def test_cpu_baseline_block():
     sc = cb["small_configs"]
     for k in ("L16", "L511"):
         assert sc[k]["separable_fields_per_s"] > sc[k]["direct_fields_per_s"] > 0
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched like the multi-GPU driver runs (torchrun, 2 ranks): rank 0 alone prints the
+    line, the other rank exits 0 without work."""
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", "29531", os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--gpus", "2", "--L", "31", "--steps", "1", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
