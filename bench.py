@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 / small-degree / ragged-batch form measurements")
+    ap.add_argument("--no-share", action="store_true",
+                    help="regenerate the Legendre operand in both calls of a step "
+                         "(no FAVEST_FLAG_SHARE_LAMBDA)")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle comparison of one field (about 10-30 s of host time)")
     return ap.parse_args()
 
 
@@ -581,6 +586,32 @@ def reference_arm(args, rank):
     }
 
 
+def oracle_errors(L, a0, b0, tt0, tp0, ga0, gb0):
+    """Field 0 of the timed step against the FP64 oracle (separable form, every coefficient
+    and grid value): the adjoint's field against the oracle's synthesis of the drawn
+    coefficients, and the forward's coefficients against the oracle's analysis of the
+    field the adjoint wrote (the forward's own input).  Normwise maxima per family
+    (max |difference| / max |reference|), outside the timed region."""
+    import numpy as np
+    import oracle
+    x, W, _, _ = oracle.grid(L)
+    t0 = time.perf_counter()
+    rt, rp = oracle.adj_sep(L, x, a0, b0, 2 * (L + 1))
+    tt0 = tt0.astype(np.complex128)
+    tp0 = tp0.astype(np.complex128)
+    ra, rb = oracle.fwd_sep(L, x, W, tt0, tp0)
+
+    def nerr(g, r):
+        return float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
+
+    e_adj = max(nerr(tt0, rt), nerr(tp0, rp))
+    e_fwd = max(nerr(ga0, ra), nerr(gb0, rb))
+    return {"vs_oracle_max_rel": max(e_adj, e_fwd), "adj_vs_oracle_max_rel": e_adj,
+            "fwd_vs_oracle_max_rel": e_fwd,
+            "vs_oracle_sample": "field 0 of the batch, all coefficients and grid points, oracle O3 on %d "
+                                "host threads (%.1f s)" % (oracle.num_threads(), time.perf_counter() - t0)}
+
+
 def cpu_baseline(args):
     """Oracle O3 on the host cores, one field, every 2nd order (half of the work)."""
     import numpy as np
@@ -734,9 +765,13 @@ def main():
     b2 = torch.empty_like(b)
     stream = torch.cuda.current_stream()
 
+    # one recurrence pass per step: the adjoint generates the Legendre operand in the
+    # layouts of both directions and the forward call uses it (FAVEST_FLAG_SHARE_LAMBDA)
+    share = not args.no_share
+
     def step():
-        plan.adj(a, b, tt, tp, stream=stream)
-        plan.fwd(tt, tp, a2, b2, stream=stream)
+        plan.adj(a, b, tt, tp, stream=stream, share_lambda=share)
+        plan.fwd(tt, tp, a2, b2, stream=stream, share_lambda=share)
 
     args.warmup = max(args.warmup, 3)      # at least three untimed warm-up steps
     for _ in range(args.warmup):
@@ -765,7 +800,8 @@ def main():
     assert plan.status() == 0
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
     value = replica_throughput(B, world, ms * 1e-3)
-    launches = steps * (plan.launches_per_call(0) + plan.launches_per_call(1))
+    # the library's own kernel launches in the timed region, as its event records count them
+    launches = int(sum(n for _, n in prof.values()))
 
     # roofline: every kernel's algorithmic work (favest_kernel_work) per launch over its
     # CUDA-event duration, against the peak of the unit that binds it; the line's
@@ -807,8 +843,8 @@ def main():
             ev_in[q].record(s_in)
             stream.wait_event(ev_in[q])
             stream.wait_event(ev_out[q])           # slot q's results read back (step k-2)
-            plan.adj(da[q], db[q], tt, tp, stream=stream)
-            plan.fwd(tt, tp, ra[q], rb[q], stream=stream)
+            plan.adj(da[q], db[q], tt, tp, stream=stream, share_lambda=share)
+            plan.fwd(tt, tp, ra[q], rb[q], stream=stream, share_lambda=share)
             ev_comp[q].record(stream)
             s_out.wait_event(ev_comp[q])
             with torch.cuda.stream(s_out):
@@ -856,6 +892,9 @@ def main():
             errors["fwd_vs_fp64_max_rel"] = max(nerr(ra, fa), nerr(rb, fb))
             errors["fwd_vs_fp64_rms_rel"] = max(rerr(ra, fa), rerr(rb, fb))
             p64.close()
+        if not args.no_oracle_check:
+            errors.update(oracle_errors(L, a_h[0], b_h[0], tt[0].cpu().numpy(), tp[0].cpu().numpy(),
+                                        ra[0], rb[0]))
 
     forms = None
     if not args.no_forms and rank == 0 and prec_name == "bf16x6":

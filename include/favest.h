@@ -80,7 +80,7 @@ enum favest_precision {
                            tensor cores: both operands split into three bf16 pieces
                            (24 significant bits, full FP32 exponent range), the 6 piece
                            products of weight >= 2^-16 formed, the leading product
-                           accumulated over K blocks of 64 and summed in FP32 with
+                           accumulated over K blocks of 32 and summed in FP32 with
                            round-to-nearest; complex64 fields and coefficients only     */
 };
 
@@ -171,6 +171,40 @@ int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *str
 int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, void *stream);
 
 /*
+ * Transforms at arbitrary points, the paper's interface FaVeST_fwd(T, L, X, w) and
+ * FaVeST_adj(a, b, X) (Sec. 4.4; point sets of Sec. 5.1 such as spherical designs), FP64:
+ *   forward (Def. FwdVSHT, eq. fwdvsht2): a_lm = sum_k w_k Y^div_lm(x_k)^* T_k,
+ *                                         b_lm = sum_k w_k Y^curl_lm(x_k)^* T_k;
+ *   adjoint (Def. AdjVSHT, eq. SLvec):    T_k = S_L(a, b; x_k),
+ * for fields given by their Cartesian components at npts points x_k.  Both run the paper's
+ * route (Thm. 1, Thm. 2): scalar spherical harmonic transforms of degree L+1 of the three
+ * Cartesian components, here summed directly over the points (O(npts L^2) FP64 work; the
+ * paper uses NFFT-based fast transforms instead), combined with the Clebsch-Gordan values of
+ * eq. ninecoeff exactly as favest_fwd_cart / favest_adj_cart do.  No quadrature exactness is
+ * assumed: favest_scatter_fwd is the weighted sum itself, whatever the points and weights.
+ *
+ * favest_scatter_create: L = 1..1023, batch = 1..1366 fields, npts = 1..2^26 points.
+ *   X: host [npts][3], the points as unit vectors (|x_k| = 1 to 1e-10, FAVEST_EINVAL
+ *      otherwise; they are normalised); points at or near the poles are allowed.
+ *   w: host [npts] point weights, or NULL for unit weights (then the forward is A^H, the
+ *      exact adjoint of favest_scatter_adj).
+ *   Copies the points to device memory the plan owns (with its tables and workspace:
+ *   O(L^2 batch + npts) doubles).  *out receives the plan (NULL on failure).
+ * favest_scatter_fwd: T device [batch][npts][3] complex double (x, y, z components of each
+ *   point), read only; a, b device [batch][L^2+2L] complex double, written (l-major).
+ * favest_scatter_adj: a, b read; T written in the same layout (the tangent field S_L(a, b)
+ *   at the points, so T_k . x_k = 0 to rounding).
+ * Pointers 16-byte aligned; asynchronous on `stream`; calls on one plan must not overlap.
+ * Errors as for the grid transforms.  favest_scatter_npts returns the point count.
+ */
+typedef struct favest_scatter_s *favest_scatter;
+int favest_scatter_create(int L, int batch, int npts, const double *X, const double *w, favest_scatter *out);
+int favest_scatter_fwd(favest_scatter plan, const void *T, void *a, void *b, void *stream);
+int favest_scatter_adj(favest_scatter plan, const void *a, const void *b, void *T, void *stream);
+int favest_scatter_npts(favest_scatter plan);
+void favest_scatter_destroy(favest_scatter plan);
+
+/*
  * Stability ratios of the forward Clebsch-Gordan route (Sec. 5.5, eq. r_stable).  Thm. 1
  * writes Y^div_lm(x)^* as six terms xi_q Y*_{l',m'}(x) u_q and Y^curl_lm(x)^* as three terms
  * mu_q Y*_{l,m'}(x) u_q (u_q unit vectors).  Per point x_k and coefficient (l, m):
@@ -220,10 +254,24 @@ int favest_set_weights_unit(favest_plan plan, int flag);
  *   favest_fwd_ex: orders m > 0 of the result are doubled, so that with
  *     FAVEST_FLAG_UNIT_WEIGHTS the call is the transpose of the real AdjVSHT.
  * The factors 1/2 and 2 are exact.  On complex plans the flag is FAVEST_EINVAL.
+ *
+ * FAVEST_FLAG_SHARE_LAMBDA (both calls; split-precision plans, ignored by FP64 plans): an
+ * adjoint and a forward transform on the same plan and degree contract the same Legendre
+ * values lambda_l^m(theta_j) (Sec. 3, definition of Y_lm), which the split path
+ * regenerates by its FP64 recurrence in every call.  With this flag on two consecutive
+ * calls of opposite direction (adjoint then forward, or forward then adjoint), the first
+ * call's recurrence pass writes the values in the layouts of both directions and the second
+ * call uses them without a generator launch (one launch fewer, see
+ * favest_launches_per_call).  A flagged call that does not directly follow such a first
+ * call (no call on the plan in between) generates both layouts itself.  Results are bitwise
+ * identical with and without the flag.  The second call must be ordered after the first on
+ * the device (same stream, or synchronised), as every call on one plan must be.
+ *
  * Any other flag bit is FAVEST_EINVAL.  Calls on one plan must not overlap in time on
  * the host (the flags live in the plan for the duration of the call).
  */
-enum { FAVEST_FLAG_UNIT_WEIGHTS = 1, FAVEST_FLAG_WEIGHTED = 2, FAVEST_FLAG_REAL_TRANSPOSE = 4 };
+enum { FAVEST_FLAG_UNIT_WEIGHTS = 1, FAVEST_FLAG_WEIGHTED = 2, FAVEST_FLAG_REAL_TRANSPOSE = 4,
+       FAVEST_FLAG_SHARE_LAMBDA = 8 };
 int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags,
                   void *stream);
 int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags,
@@ -247,7 +295,9 @@ void favest_plan_destroy(favest_plan plan);
 /* Static description of a status code. */
 const char *favest_strerror(int status);
 
-/* Number of kernels each transform call launches (for launch accounting). */
+/* Number of kernels each transform call launches without FAVEST_FLAG_SHARE_LAMBDA (for
+ * launch accounting); the second call of a pair sharing the Legendre operand launches one
+ * fewer. */
 int favest_launches_per_call(favest_plan plan, int adjoint);
 
 /*
@@ -370,13 +420,20 @@ int favest_probe_peaks(double *fp64_tflops, double *fp32_tflops);
  * Scratch: a single file-scope device array of favest_noalloc_scratch_bytes() = 32 MB,
  * held by every GPU that loads the library until the process exits.  A request whose
  * scratch (grid and recurrence tables, spectra, scalar sums; about
- * 96 (L+1)^2 batch + 24 (L+1)^2 bytes) exceeds it, or L > 1023, returns
+ * 96 (L+1)^2 batch + 24 (L+1)^2 bytes) exceeds it (L = 511 fits for batch 1 only;
+ * L = 511 with batch 2, or L = 1023, does not), L > 1023 or batch > 4096 returns
  * FAVEST_EINVAL before anything is launched.  No cudaMalloc, cudaFree or other
- * allocating call is made.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call rewrites the tables it needs, but all calls
- * share the one array: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.
+ * allocating call is made.  The first call in a CUDA context looks up the array's
+ * device address (cudaGetSymbolAddress) with that context current, and looks it up
+ * again in a new context of the same device (e.g. after cudaDeviceReset); make the
+ * first call in each context before any stream capture.  Every call rewrites the tables
+ * it needs, but all calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors: FAVEST_EINVAL as above or for NULL or misaligned pointers; FAVEST_ECUDA if a
+ * launch fails, or if the CUDA runtime already holds an unread error from an earlier
+ * call on this host thread when the call starts (nothing is launched then, and that
+ * error is left for its owner to read with cudaGetLastError).  The kernels of this path
+ * record no device-side status (favest_status has no plan to read here).
  */
 int favest_fwd_fp64_noalloc(int L, int batch, const void *Tth, const void *Tph, void *a, void *b,
                             void *stream);

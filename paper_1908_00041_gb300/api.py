@@ -31,6 +31,7 @@ FAVEST_IO_R64 = 3
 FAVEST_FLAG_UNIT_WEIGHTS = 1
 FAVEST_FLAG_WEIGHTED = 2
 FAVEST_FLAG_REAL_TRANSPOSE = 4
+FAVEST_FLAG_SHARE_LAMBDA = 8
 FAVEST_BATCH_AUTOTUNE = 1
 FAVEST_BATCH_GRAPH = 2
 
@@ -109,6 +110,12 @@ def lib(build_if_missing=False):
             L.favest_fwd_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_adj_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_cg_stability.argtypes = [i, i, d, d, d, vp]
+            L.favest_scatter_create.argtypes = [i, i, i, d, d, ctypes.POINTER(vp)]
+            L.favest_scatter_fwd.argtypes = [vp, vp, vp, vp, vp]
+            L.favest_scatter_adj.argtypes = [vp, vp, vp, vp, vp]
+            L.favest_scatter_npts.argtypes = [vp]
+            L.favest_scatter_destroy.argtypes = [vp]
+            L.favest_scatter_destroy.restype = None
             L.favest_profile_enable.argtypes = [vp, i]
             L.favest_profile_read.argtypes = [vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_longlong)]
@@ -229,8 +236,20 @@ def favest_profile_read(plan, max_kernels=16):
 
 def favest_fwd_fp64_noalloc(L, batch, Tth, Tph, a, b, stream=None):
     """FP64 forward transform using only the library's static 32 MB device scratch
-    (no device allocation); see include/favest.h."""
-    _check(lib().favest_fwd_fp64_noalloc(int(L), int(batch), _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b),
+    (no device allocation); see include/favest.h.  Tth, Tph: contiguous complex128 CUDA
+    tensors [batch, L+1, 2(L+1)]; a, b: [batch, L^2+2L], all on the current device (the
+    C entry point sees raw pointers only, so shapes and types are checked here)."""
+    import torch
+    L, batch = int(L), int(batch)
+    shapes = {"Tth": (batch, L + 1, 2 * (L + 1)), "Tph": (batch, L + 1, 2 * (L + 1)),
+              "a": (batch, L * L + 2 * L), "b": (batch, L * L + 2 * L)}
+    dev = torch.cuda.current_device()
+    for name, t in (("Tth", Tth), ("Tph", Tph), ("a", a), ("b", b)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev
+                and t.dtype == torch.complex128 and t.is_contiguous() and tuple(t.shape) == shapes[name]):
+            raise ValueError("%s: expected a contiguous complex128 tensor of shape %s on cuda:%d, got %s"
+                             % (name, shapes[name], dev, getattr(t, "device", type(t))))
+    _check(lib().favest_fwd_fp64_noalloc(L, batch, _ptr(Tth), _ptr(Tph), _ptr(a), _ptr(b),
                                          _stream(stream)), "favest_fwd_fp64_noalloc")
 
 
@@ -309,7 +328,8 @@ class Plan:
             favest_set_weights_unit(self.handle, flag)
             self._unit = flag
 
-    def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False, real_transpose=False):
+    def fwd(self, Tth, Tph, a=None, b=None, stream=None, unit_weights=False, real_transpose=False,
+            share_lambda=False):
         import torch
         self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
         self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
@@ -320,10 +340,12 @@ class Plan:
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
         flags = (FAVEST_FLAG_UNIT_WEIGHTS if unit_weights else 0) | (FAVEST_FLAG_REAL_TRANSPOSE if real_transpose else 0)
+        flags |= FAVEST_FLAG_SHARE_LAMBDA if share_lambda else 0
         favest_fwd_ex(self.handle, Tth, Tph, a, b, flags, stream)
         return a, b
 
-    def adj(self, a, b, Tth=None, Tph=None, stream=None, weighted=False, real_transpose=False):
+    def adj(self, a, b, Tth=None, Tph=None, stream=None, weighted=False, real_transpose=False,
+            share_lambda=False):
         import torch
         self._check_tensor(a, self.coef_shape(), "a")
         self._check_tensor(b, self.coef_shape(), "b")
@@ -334,6 +356,7 @@ class Plan:
         self._check_tensor(Tth, self.field_shape(), "Tth", self.fdtype)
         self._check_tensor(Tph, self.field_shape(), "Tph", self.fdtype)
         flags = (FAVEST_FLAG_WEIGHTED if weighted else 0) | (FAVEST_FLAG_REAL_TRANSPOSE if real_transpose else 0)
+        flags |= FAVEST_FLAG_SHARE_LAMBDA if share_lambda else 0
         favest_adj_ex(self.handle, a, b, Tth, Tph, flags, stream)
         return Tth, Tph
 
@@ -461,6 +484,74 @@ class CgPlan:
 
     def profile_read(self):
         return favest_profile_read(self.handle)
+
+
+class ScatterPlan:
+    """Transforms at arbitrary points (the paper's FaVeST_fwd(T, L, X, w) / FaVeST_adj(a, b, X)):
+    X host [npts, 3] unit vectors, w host [npts] weights (None: unit weights); fields as
+    Cartesian components T [batch, npts, 3] complex128, coefficients [batch, L^2+2L]."""
+
+    def __init__(self, L, X, w=None, batch=1):
+        import torch
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        if X.ndim != 2 or X.shape[1] != 3:
+            raise ValueError("X: expected [npts, 3] points")
+        self.L, self.batch, self.npts = int(L), int(batch), int(X.shape[0])
+        self.K = L * L + 2 * L
+        self.cdtype = torch.complex128
+        dp = ctypes.POINTER(ctypes.c_double)
+        wp = None
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float64).ravel()
+            if w.size != self.npts:
+                raise ValueError("w: expected %d weights" % self.npts)
+            wp = w.ctypes.data_as(dp)
+        h = ctypes.c_void_p()
+        _check(lib().favest_scatter_create(self.L, self.batch, self.npts, X.ctypes.data_as(dp), wp, ctypes.byref(h)),
+               "favest_scatter_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().favest_scatter_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_shape(self):
+        return (self.batch, self.npts, 3)
+
+    def coef_shape(self):
+        return (self.batch, self.K)
+
+    def _check(self, t, shape, name):
+        if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError("%s: expected contiguous CUDA complex128 tensor of shape %s" % (name, shape))
+
+    def fwd(self, T, a=None, b=None, stream=None):
+        import torch
+        self._check(T, self.field_shape(), "T")
+        a = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if a is None else a
+        b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if b is None else b
+        self._check(a, self.coef_shape(), "a")
+        self._check(b, self.coef_shape(), "b")
+        _check(lib().favest_scatter_fwd(ctypes.c_void_p(self.handle), _ptr(T), _ptr(a), _ptr(b), _stream(stream)),
+               "favest_scatter_fwd")
+        return a, b
+
+    def adj(self, a, b, T=None, stream=None):
+        import torch
+        self._check(a, self.coef_shape(), "a")
+        self._check(b, self.coef_shape(), "b")
+        T = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device) if T is None else T
+        self._check(T, self.field_shape(), "T")
+        _check(lib().favest_scatter_adj(ctypes.c_void_p(self.handle), _ptr(a), _ptr(b), _ptr(T), _stream(stream)),
+               "favest_scatter_adj")
+        return T
 
 
 class BatchPlan:

@@ -107,7 +107,7 @@ cudaError_t enqueue(favest_batch_s &bp, bool adjoint, const void *Tth, const voi
         e = per_group(bp, s, [&](int g, cudaStream_t gs) {
             const Plan &p = bp.groups[g]->p;
             cudaError_t r = launch_fft_fwd_bf16(p, Tth, Tph, gs);
-            return r == cudaSuccess ? launch_gen_lambda(p, true, gs) : r;
+            return r == cudaSuccess ? launch_gen_lambda(p, kGenFwd, gs) : r;
         });
         if (e == cudaSuccess)
             e = launch_tc_gemm_items(256, bp.d_gg, bp.d_items_f, bp.n_items_f, 1, bp.d_status, bp.num_sms, s);
@@ -119,7 +119,7 @@ cudaError_t enqueue(favest_batch_s &bp, bool adjoint, const void *Tth, const voi
         e = per_group(bp, s, [&](int g, cudaStream_t gs) {
             const Plan &p = bp.groups[g]->p;
             cudaError_t r = launch_uncombine_bf16(p, a, b, gs);
-            return r == cudaSuccess ? launch_gen_lambda(p, false, gs) : r;
+            return r == cudaSuccess ? launch_gen_lambda(p, kGenAdj, gs) : r;
         });
         if (e == cudaSuccess)
             e = launch_tc_gemm_items(256, bp.d_gg, bp.d_items_a, bp.n_items_a, 0, bp.d_status, bp.num_sms, s);
@@ -239,12 +239,12 @@ int favest_plan_tune(favest_plan plan, void *stream)
     float best = 1e30f;
     int blt = p.gen_lt, bmb = p.gen_mb, bnj = p.gen_nj, st = FAVEST_OK;
     for (const auto &c : kGenShapes) {
-        if (launch_gen_lambda_shape(p, true, c[0], c[1], c[2], s) != cudaSuccess) {
+        if (launch_gen_lambda_shape(p, kGenFwd, c[0], c[1], c[2], s) != cudaSuccess) {
             st = FAVEST_ECUDA;
             break;
         }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_gen_lambda_shape(p, true, c[0], c[1], c[2], s);
+        for (int r = 0; r < 3; ++r) launch_gen_lambda_shape(p, kGenFwd, c[0], c[1], c[2], s);
         cudaEventRecord(e1, s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

@@ -531,12 +531,13 @@ int alloc_workspace_bf16(Plan &p)
 int alloc_workspace(Plan &p)
 {
     const int nmu = p.L + 1 + (p.nscal > 0 ? 1 : 0);
-    size_t fbytes = (size_t)nmu * p.ncol * p.nlat * sizeof(double2);
+    // scattered points: only the sums Q (the point kernels replace the grid stages)
+    size_t fbytes = p.scattered ? 0 : (size_t)nmu * p.ncol * p.nlat * sizeof(double2);
     size_t qbytes = (size_t)p.ntab * p.ncol * sizeof(double2);
     // inverse DFT rows: 2 per group of 4 columns, or 2 per real field (2 fields per group)
-    size_t gbytes = (size_t)(p.real ? p.ncol : p.ncol / 2) * p.nlat * p.nphi * sizeof(double2);
-    if (cudaMalloc(&p.d_F, fbytes) != cudaSuccess || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
-        cudaMalloc(&p.d_G, gbytes) != cudaSuccess ||
+    size_t gbytes = p.scattered ? 0 : (size_t)(p.real ? p.ncol : p.ncol / 2) * p.nlat * p.nphi * sizeof(double2);
+    if ((fbytes && cudaMalloc(&p.d_F, fbytes) != cudaSuccess) || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
+        (gbytes && cudaMalloc(&p.d_G, gbytes) != cudaSuccess) ||
         cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
@@ -544,7 +545,7 @@ int alloc_workspace(Plan &p)
     cudaMemset(p.d_status, 0, sizeof(int));
     // the padding columns (an odd count of scalar or real fields) read as zero
     if ((p.nscal > 0 || p.real) &&
-        (cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess || cudaMemset(p.d_F, 0, fbytes) != cudaSuccess))
+        (cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess || (fbytes && cudaMemset(p.d_F, 0, fbytes) != cudaSuccess)))
         return FAVEST_ECUDA;
     p.ws_bytes = fbytes + qbytes + gbytes;
     return FAVEST_OK;
@@ -564,6 +565,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_EC
 const char *kKernelNames[KID_COUNT] = {
     "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
     "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj", "polar_patch", "cg_combine", "cg_uncombine",
+    "gen_lambda_both",
 };
 
 cudaEvent_t take_event(Plan &p)
@@ -675,6 +677,7 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
         // 3 scalar fields per vector field, 2 per group of 4 columns (sign of m, re/im)
         p.nscal = 3 * batch;
         p.ncol = 4 * ((p.nscal + 1) / 2);
+        p.scattered = cg_route == 2;
     }
     p.ct = (p.ncol % 8 == 0) ? 8 : 4;
     p.ng = p.ncol / p.ct;
@@ -744,12 +747,32 @@ struct FlagScope {
     ~FlagScope() { ref = saved; }
 };
 
+// Generator launch of a split-precision call that needs the Legendre operand in layout
+// `mine` (kGenFwd or kGenAdj).  Without FAVEST_FLAG_SHARE_LAMBDA: generate that layout.
+// With it: if the previous call on the plan generated both layouts for this one, use them
+// (no launch); otherwise generate both and leave the other layout to the next call.  Any
+// call ends an earlier pairing, so an operand is used by at most the call right after the
+// one that generated it.
+cudaError_t legendre_operand(Plan &p, int mine, bool share, cudaStream_t s)
+{
+    const int pending = p.lam_pending;
+    p.lam_pending = 0;
+    if (share && pending == mine) return cudaSuccess;
+    if (share) {
+        cudaError_t e = timed(p, KID_GEN_BOTH, s, [&] { return launch_gen_lambda(p, kGenBoth, s); });
+        if (e == cudaSuccess) p.lam_pending = kGenBoth & ~mine;
+        return e;
+    }
+    return timed(p, mine == kGenFwd ? KID_GEN_FWD : KID_GEN_ADJ, s, [&] { return launch_gen_lambda(p, mine, s); });
+}
+
 }  // namespace
 
 int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, void *b, int flags, void *stream)
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
-    if (flags & ~(FAVEST_FLAG_UNIT_WEIGHTS | FAVEST_FLAG_REAL_TRANSPOSE)) return FAVEST_EINVAL;
+    if (flags & ~(FAVEST_FLAG_UNIT_WEIGHTS | FAVEST_FLAG_REAL_TRANSPOSE | FAVEST_FLAG_SHARE_LAMBDA))
+        return FAVEST_EINVAL;
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;     // Clebsch-Gordan plans take favest_fwd_cart
     if ((flags & FAVEST_FLAG_REAL_TRANSPOSE) && !p.real) return FAVEST_EINVAL;
@@ -763,7 +786,7 @@ int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, v
     cudaError_t e;
     if (p.precision == FAVEST_BF16X6) {
         e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_bf16(p, Tth, Tph, s); });
-        if (e == cudaSuccess) e = timed(p, KID_GEN_FWD, s, [&] { return launch_gen_lambda(p, true, s); });
+        if (e == cudaSuccess) e = legendre_operand(p, kGenFwd, (flags & FAVEST_FLAG_SHARE_LAMBDA) != 0, s);
         if (e == cudaSuccess) e = timed(p, KID_GEMM_FWD, s, [&] { return launch_tc_gemm(p, true, s); });
         if (e == cudaSuccess) e = timed(p, KID_COMBINE, s, [&] { return launch_combine_bf16(p, a, b, s); });
         return cuda_status(e);
@@ -777,7 +800,7 @@ int favest_fwd_ex(favest_plan plan, const void *Tth, const void *Tph, void *a, v
 int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, int flags, void *stream)
 {
     if (!plan || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
-    if (flags & ~(FAVEST_FLAG_WEIGHTED | FAVEST_FLAG_REAL_TRANSPOSE)) return FAVEST_EINVAL;
+    if (flags & ~(FAVEST_FLAG_WEIGHTED | FAVEST_FLAG_REAL_TRANSPOSE | FAVEST_FLAG_SHARE_LAMBDA)) return FAVEST_EINVAL;
     Plan &p = plan->p;
     if (p.nscal > 0) return FAVEST_EINVAL;
     if ((flags & FAVEST_FLAG_REAL_TRANSPOSE) && !p.real) return FAVEST_EINVAL;
@@ -791,7 +814,7 @@ int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, voi
     cudaError_t e;
     if (p.precision == FAVEST_BF16X6) {
         e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_bf16(p, a, b, s); });
-        if (e == cudaSuccess) e = timed(p, KID_GEN_ADJ, s, [&] { return launch_gen_lambda(p, false, s); });
+        if (e == cudaSuccess) e = legendre_operand(p, kGenAdj, (flags & FAVEST_FLAG_SHARE_LAMBDA) != 0, s);
         if (e == cudaSuccess) e = timed(p, KID_GEMM_ADJ, s, [&] { return launch_tc_gemm(p, false, s); });
         if (e == cudaSuccess && p.pol_jc > 0)
             e = timed(p, KID_POLAR, s, [&] { return launch_polar_patch(p, a, b, s); });
@@ -952,6 +975,7 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 96.0; *flops = fftf; }
         else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
         else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; *pipe = 1; }
+        else if (k == "gen_lambda_both") { *bytes = gv * 12.0; *flops = gv * 4.0; *pipe = 1; }
         else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 96.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
         else if (k == "tc_gemm_adj") { *bytes = pa * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * pa * 8.0 * G; }
         else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }

@@ -87,6 +87,9 @@ struct Plan {
     // weights, and d_kap holds kappa_l^mu for every table row; 0 for the other plans
     int nscal = 0;
     double *d_kap = nullptr;
+    // scalar sums at arbitrary points (favest_scatter_create): a Clebsch-Gordan plan whose
+    // sums Q are formed by the point kernels, so no grid workspace is allocated
+    int scattered = 0;
     int nlat = 0, nphi = 0, J = 0, has_eq = 0;
     int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
     int ct = 0, ng = 0;       // FP64 column group width and count
@@ -129,6 +132,10 @@ struct Plan {
     void *d_lam_f = nullptr, *d_lam_a = nullptr;
     int *d_jcmin = nullptr;       // [L+1] first latitude (multiple of 32) generated per order
     double gen_values = 0;        // recurrence values generated per direction
+    // Legendre operand shared by a pair of calls (FAVEST_FLAG_SHARE_LAMBDA): kGenFwd when
+    // the last call generated both layouts and the next forward call may use the forward
+    // one without generating it, kGenAdj likewise for the next adjoint call, 0 otherwise
+    int lam_pending = 0;
     double gemm_pairs_f = 0, gemm_pairs_a = 0;   // (row, latitude) pairs the GEMMs contract
     void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
@@ -177,7 +184,7 @@ struct Plan {
 enum KernelId {
     KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
     KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ, KID_POLAR, KID_CG_COMBINE, KID_CG_UNCOMBINE,
-    KID_COUNT
+    KID_GEN_BOTH, KID_COUNT
 };
 
 __host__ __device__ inline long long tab_off(int L, int mu) {
@@ -194,8 +201,10 @@ cudaError_t launch_uncombine_fp64(const Plan &p, const void *a, const void *b, c
 
 cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s);
 cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_t s);
-cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s);
-cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, int nj, cudaStream_t s);
+// Legendre operand layouts a generator launch writes (bit mask)
+constexpr int kGenFwd = 1, kGenAdj = 2, kGenBoth = 3;
+cudaError_t launch_gen_lambda(const Plan &p, int layouts, cudaStream_t s);
+cudaError_t launch_gen_lambda_shape(const Plan &p, int layouts, int lt, int mb, int nj, cudaStream_t s);
 // failure-path self-test: one GEMM item with no operand loads and the given wait bound
 cudaError_t launch_gemm_selftest(const Plan &p, uint32_t poll_limit, cudaStream_t s);
 // one persistent GEMM launch over an explicit item list (items[i].group indexes groups)

@@ -9,7 +9,7 @@
 // (those with combined weight >= 2^-16 of the leading one).  Because the tensor core
 // accumulates in FP32 with truncation (products below one ulp of the running sum are
 // dropped), the leading hi*hi product is accumulated in a fresh TMEM buffer for each
-// K-chunk of 64 and added to an FP32 register sum (round-to-nearest) by the epilogue;
+// K-chunk of 32 and added to an FP32 register sum (round-to-nearest) by the epilogue;
 // the five correction products, 2^-8 smaller, accumulate in TMEM over the whole K.
 //
 // One work item is a 128 x N output tile (N = 256 columns, i.e. 32 fields, or 128 for
@@ -72,10 +72,15 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 // order's turning bound rounded down to a K-chunk: every value there is below 1e-13) and
 // padding latitudes are not stored; their operand positions were zeroed when the plan was
 // created.
-//   fwd = true : forward A layout, item (mu, p, m_tile) at lam_off[mu*2+p] + m_tile*nkf*48KB
-//   fwd = false: adjoint A layout, item (mu, p, j_tile) at lam_off[mu*2+p] + j_tile*nka*48KB
-template <bool FWD, int kGenJ>
-__device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const long long *__restrict__ lam_off,
+// MODE selects the layouts written (bit 0: forward, bit 1: adjoint); both layouts are made
+// of the same 16-byte core-matrix rows (8 consecutive rows of one parity at one latitude)
+// and differ only in where a row goes, so MODE 3 serves an adjoint and a forward transform
+// from one pass of the recurrence:
+//   forward A layout: item (mu, p, m_tile) at lam_f_off[mu*2+p] + m_tile*nkf*24KB
+//   adjoint A layout: item (mu, p, j_tile) at lam_a_off[mu*2+p] + j_tile*nka*24KB
+template <int MODE, int kGenJ>
+__device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off,
+                                          unsigned char *__restrict__ lam_a, const long long *__restrict__ lam_a_off,
                                           const double *__restrict__ xj, const double *__restrict__ sj,
                                           const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
                                           int J, int JP, int mu, const int (&jv)[kGenJ], int jc0)
@@ -155,24 +160,28 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const
             for (int p = 0; p < 2; ++p) {
                 const int np = p ? nrow_p1 : nrow_p0;
                 if (act[i] && rp < np) {
-                    const long long base = lam_off[mu * 2 + p];
-                    long long off;
-                    if (FWD) {
+                    if (MODE & 1) {
                         const int mt = rp / kTileM, mi = rp % kTileM;
                         const int kc = j / kChunkK, jj = j % kChunkK;
-                        off = base + ((long long)mt * nk_f + kc) * kChunkBytes +
-                              (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
-                    } else {
+                        const long long off = lam_f_off[mu * 2 + p] + ((long long)mt * nk_f + kc) * kChunkBytes +
+                                              (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
+#pragma unroll
+                        for (int q = 0; q < kPieces; ++q) {
+                            uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
+                            *reinterpret_cast<uint4 *>(lam_f + off + q * kPieceBytes) = v;
+                        }
+                    }
+                    if (MODE & 2) {
                         const int nka = p ? nk_a1 : nk_a0;
                         const int jt = j / kTileM, jj = j % kTileM;
                         const int kc = rp / kChunkK, rr = rp % kChunkK;
-                        off = base + ((long long)jt * nka + kc) * kChunkBytes +
-                              (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
-                    }
+                        const long long off = lam_a_off[mu * 2 + p] + ((long long)jt * nka + kc) * kChunkBytes +
+                                              (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
 #pragma unroll
-                    for (int q = 0; q < kPieces; ++q) {
-                        uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
-                        *reinterpret_cast<uint4 *>(lam + off + q * kPieceBytes) = v;
+                        for (int q = 0; q < kPieces; ++q) {
+                            uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
+                            *reinterpret_cast<uint4 *>(lam_a + off + q * kPieceBytes) = v;
+                        }
                     }
                 }
 #pragma unroll
@@ -182,11 +191,12 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const
     }
 }
 
-template <bool FWD, int kGenJ>
+template <int MODE, int kGenJ>
 __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
-    unsigned char *__restrict__ lam, const long long *__restrict__ lam_off, const double *__restrict__ xj,
-    const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
-    const int *__restrict__ jcmin, int L, int J, int JP, int lt, int mb)
+    unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off, unsigned char *__restrict__ lam_a,
+    const long long *__restrict__ lam_a_off, const double *__restrict__ xj, const double *__restrict__ sj,
+    const double *__restrict__ cmu, const double *__restrict__ Atab, const int *__restrict__ jcmin, int L, int J,
+    int JP, int lt, int mb)
 {
     const int olanes = kGenThreads / lt;
     const int jblocks = (JP + kGenJ * lt - 1) / (kGenJ * lt);
@@ -197,7 +207,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     for (int k = 0; k < mb; ++k) {
         const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
         if (mu > L) break;
-        gen_order<FWD, kGenJ>(lam, lam_off, xj, sj, cmu, Atab, L, J, JP, mu, jv, __ldg(jcmin + mu));
+        gen_order<MODE, kGenJ>(lam_f, lam_f_off, lam_a, lam_a_off, xj, sj, cmu, Atab, L, J, JP, mu, jv,
+                               __ldg(jcmin + mu));
     }
 }
 
@@ -462,34 +473,38 @@ cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nite
 
 }  // namespace
 
-template <int NJ>
-cudaError_t launch_gen_t(const Plan &p, bool fwd, int lt, int mb, cudaStream_t s)
+template <int MODE, int NJ>
+void launch_gen_t(const Plan &p, int lt, int mb, cudaStream_t s)
 {
     const int olanes = kGenThreads / lt;
     const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
     const int grid = ((p.JP + NJ * lt - 1) / (NJ * lt)) * ogroups;
-    if (fwd)
-        k_gen_lambda<true, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f, p.d_x,
-                                                            p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt,
-                                                            mb);
-    else
-        k_gen_lambda<false, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x,
-                                                             p.d_sin, p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt,
-                                                             mb);
+    k_gen_lambda<MODE, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f,
+                                                        (unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x, p.d_sin,
+                                                        p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
+}
+
+template <int NJ>
+void launch_gen_nj(const Plan &p, int layouts, int lt, int mb, cudaStream_t s)
+{
+    if (layouts == kGenFwd) launch_gen_t<kGenFwd, NJ>(p, lt, mb, s);
+    else if (layouts == kGenAdj) launch_gen_t<kGenAdj, NJ>(p, lt, mb, s);
+    else launch_gen_t<kGenBoth, NJ>(p, lt, mb, s);
+}
+
+cudaError_t launch_gen_lambda_shape(const Plan &p, int layouts, int lt, int mb, int nj, cudaStream_t s)
+{
+    if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
+    if (layouts != kGenFwd && layouts != kGenAdj && layouts != kGenBoth) return cudaErrorInvalidValue;
+    if (nj == 1) launch_gen_nj<1>(p, layouts, lt, mb, s);
+    else if (nj == 2) launch_gen_nj<2>(p, layouts, lt, mb, s);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_lambda_shape(const Plan &p, bool fwd, int lt, int mb, int nj, cudaStream_t s)
+cudaError_t launch_gen_lambda(const Plan &p, int layouts, cudaStream_t s)
 {
-    if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
-    if (nj == 1) return launch_gen_t<1>(p, fwd, lt, mb, s);
-    if (nj == 2) return launch_gen_t<2>(p, fwd, lt, mb, s);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_gen_lambda(const Plan &p, bool fwd, cudaStream_t s)
-{
-    return launch_gen_lambda_shape(p, fwd, p.gen_lt, p.gen_mb, p.gen_nj, s);
+    return launch_gen_lambda_shape(p, layouts, p.gen_lt, p.gen_mb, p.gen_nj, s);
 }
 
 cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,

@@ -41,6 +41,9 @@ def test_bench_json_line_small_workload():
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert "sm_mhz" in rec["clocks"] and "reasons" in rec["clocks"]
     assert rec["errors"]["fwd_vs_fp64_max_rel"] < 1e-6
+    assert rec["errors"]["vs_oracle_max_rel"] < 1e-6
+    # one generator pass per step: adjoint, forward, 7 other kernels
+    assert rec["gpu_launches"] == rec["steps"] * 8
     for form in ("fp64_same_workload", "fp64_L16_one_field", "fp64_L511_one_field", "ragged_batch",
                  "real_fields_B8", "field_a_tables", "cg_route_L511_one_field", "fp64_real_vs_complex_L511_B8",
                  "split_L1000_B8", "cg_stability_ratios"):
