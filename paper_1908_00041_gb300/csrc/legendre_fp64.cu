@@ -18,25 +18,6 @@ constexpr int kAnaWarps = kAnaThreads / 32;
 constexpr int kAnaJpt = 2;        // latitudes per thread (J <= 512)
 constexpr int kWin = 4;           // rows per reduction window (even)
 
-template <int V>
-__device__ __forceinline__ void warp_transpose_reduce(double (&v)[V])
-{
-    // After the call lane l holds in v[0 .. V/32) the warp totals of the values with
-    // indices l*V/32 .. l*V/32 + V/32 - 1.
-#pragma unroll
-    for (int lev = 0; lev < 5; ++lev) {
-        const int o = 16 >> lev;
-        const int h = V >> (lev + 1);
-        const bool up = (threadIdx.x & o) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            double send = up ? v[i] : v[i + h];
-            double keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-}
-
 // Forward Legendre stage.  Fraw: [mu][ncol][nlat] raw longitude spectra; Q: [tab][ncol].
 template <int CT>
 __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(

@@ -71,4 +71,25 @@ __device__ __forceinline__ void renorm(double &y1, double &y2, int &c)
     }
 }
 
+// Sum V values (V a multiple of 32) over the 32 lanes of a warp: afterwards lane l holds in
+// v[0 .. V/32) the warp totals of the values with indices l*V/32 .. l*V/32 + V/32 - 1.
+// Each level halves the values a lane keeps and exchanges the other half with the lane o
+// apart, so the warp adds V*31/32 pairs instead of V*31 for a plain butterfly per value.
+template <int V>
+__device__ __forceinline__ void warp_transpose_reduce(double (&v)[V])
+{
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+        const int o = 16 >> lev;
+        const int h = V >> (lev + 1);
+        const bool up = (threadIdx.x & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            double send = up ? v[i] : v[i + h];
+            double keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
 }  // namespace favest
