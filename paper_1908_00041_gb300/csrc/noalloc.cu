@@ -10,11 +10,16 @@
 // loads the library until the process exits.  The caller passes only inputs, outputs
 // and a stream.
 //
-// Set-up: the first call on a device (with that device current) looks up the array's
-// device address with cudaGetSymbolAddress and caches it per device; make that first
-// call outside any stream capture.  Every call rebuilds the constant tables in the
-// array, so no state has to survive between calls, and calls that overlap on the GPU
-// (different streams, or different host threads) race on the shared array.
+// Set-up: the first call in a CUDA context (with that context's device current) looks
+// up the array's device address with cudaGetSymbolAddress and caches it with the
+// context's unique id; a later call in another context of the same device (after
+// cudaDeviceReset, or under a new primary context) looks it up again.  Make the first
+// call in a context outside any stream capture.  Every call rebuilds the constant tables
+// in the array, so no state has to survive between calls, and calls that overlap on the
+// GPU (different streams, or different host threads) race on the shared array.
+//
+// The kernels of this path have no device-side waits and record no status: a call
+// reports launch failures through its return code only.
 #include <cmath>
 #include <mutex>
 
@@ -24,11 +29,42 @@ namespace {
 
 constexpr size_t kScratchBytes = 32u << 20;   // 32 MB
 constexpr int kMaxDevices = 64;
+constexpr int kMaxBatch = 4096;
 
 static __device__ __align__(256) unsigned char g_favest_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;   // 0: not looked up yet (context ids start at 1)
+    void *ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext *);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (driver entry points reached
+// through the runtime, so the library does not link the driver library); 0 on failure.
+unsigned long long current_ctx_id()
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1 ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f2)
+            return 0;
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+        get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -135,38 +171,48 @@ extern "C" int favest_fwd_fp64_noalloc(int L, int batch, const void *Tth, const 
                                        void *stream)
 {
     using namespace favest;
-    if (L < 1 || batch < 1 || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
+    if (L < 1 || L > 1023 || batch < 1 || batch > kMaxBatch || !Tth || !Tph || !a || !b) return FAVEST_EINVAL;
     if (((uintptr_t)Tth | (uintptr_t)Tph | (uintptr_t)a | (uintptr_t)b) % 16) return FAVEST_EINVAL;
+    // the longitude spectra alone take 64 batch (L+1)^2 bytes: refuse early, before any
+    // layout arithmetic (all sizes below are size_t products of values this bounds)
+    if ((size_t)batch > kScratchBytes / (64 * (size_t)(L + 1) * (size_t)(L + 1))) return FAVEST_EINVAL;
     const int nlat = L + 1, nphi = 2 * (L + 1), J = (nlat + 1) / 2, ncol = 4 * batch;
-    if (J > 512) return FAVEST_EINVAL;
     const long long ntab = tab_off(L, L + 1);
     // scratch layout
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    const size_t o_x = take(J * 8), o_s = take(J * 8), o_om = take(J * 8), o_omu = take(J * 8);
-    const size_t o_cmu = take((L + 1) * 8);
-    const size_t o_A = take(ntab * 8), o_P = take(ntab * 8), o_M = take(ntab * 8), o_R = take(ntab * 8);
+    const size_t o_x = take((size_t)J * 8), o_s = take((size_t)J * 8), o_om = take((size_t)J * 8),
+                 o_omu = take((size_t)J * 8);
+    const size_t o_cmu = take((size_t)(L + 1) * 8);
+    const size_t o_A = take((size_t)ntab * 8), o_P = take((size_t)ntab * 8), o_M = take((size_t)ntab * 8),
+                 o_R = take((size_t)ntab * 8);
     const size_t o_kap = take((size_t)(L + 1) * (L + 3) * 8);
     const size_t o_tw = take((size_t)nphi * 16);
-    const size_t o_F = take((size_t)(L + 1) * ncol * nlat * 16);
-    const size_t o_Q = take((size_t)ntab * ncol * 16);
-    const size_t o_st = take(sizeof(int));
+    const size_t o_F = take((size_t)(L + 1) * (size_t)ncol * nlat * 16);
+    const size_t o_Q = take((size_t)ntab * (size_t)ncol * 16);
     if (off > kScratchBytes) return FAVEST_EINVAL;   // (L, batch) needs more than 32 MB of scratch
 
+    // An error left unread by an earlier runtime call on this thread would be returned by
+    // the launch checks below as if it were this call's: refuse without launching and
+    // leave it for its owner to read.
+    if (cudaPeekAtLastError() != cudaSuccess) return FAVEST_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FAVEST_ECUDA;
     unsigned char *base;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        const unsigned long long ctx = current_ctx_id();
+        if (ctx == 0) return FAVEST_ECUDA;
+        if (g_scratch[dev].ctx_id != ctx) {
             void *ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_favest_scratch) != cudaSuccess || !ptr) {
-                cudaGetLastError();
+                cudaGetLastError();   // the lookup's own error
                 return FAVEST_ECUDA;
             }
-            g_scratch_ptr[dev] = ptr;
+            g_scratch[dev].ptr = ptr;
+            g_scratch[dev].ctx_id = ctx;
         }
-        base = (unsigned char *)g_scratch_ptr[dev];
+        base = (unsigned char *)g_scratch[dev].ptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -197,7 +243,7 @@ extern "C" int favest_fwd_fp64_noalloc(int L, int batch, const void *Tth, const 
     p.d_R = (double *)(base + o_R);
     p.d_F = base + o_F;
     p.d_Q = base + o_Q;
-    p.d_status = (int *)(base + o_st);
+    p.d_status = nullptr;   // the FP64 kernels record no device-side status
     p.fft.n = nphi;
     p.fft.nstages = factorize_na(nphi, p.fft.radix);
     p.fft.tw64 = (double2 *)(base + o_tw);
@@ -205,11 +251,16 @@ extern "C" int favest_fwd_fp64_noalloc(int L, int batch, const void *Tth, const 
 
     // tables (rebuilt on every call: the array keeps whatever the previous call left)
     k_na_gl<<<(nlat / 2 + 1 + 127) / 128, 128, 0, s>>>(nlat, J, nphi, p.d_x, p.d_sin, p.d_omega, p.d_omega_unit);
-    k_na_tables<<<(L + 1 + 63) / 64, 64, 0, s>>>(L, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
-                                                (double *)(base + o_kap));
-    k_na_twiddles<<<(nphi + 255) / 256, 256, 0, s>>>(nphi, p.fft.tw64);
-    cudaError_t e = cudaMemsetAsync(p.d_status, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_na_tables<<<(L + 1 + 63) / 64, 64, 0, s>>>(L, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
+                                                    (double *)(base + o_kap));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_na_twiddles<<<(nphi + 255) / 256, 256, 0, s>>>(nphi, p.fft.tw64);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = launch_fft_fwd_fp64(p, Tth, Tph, s);
     if (e == cudaSuccess) e = launch_analysis_fp64(p, s);
     if (e == cudaSuccess) e = launch_combine_fp64(p, a, b, s);
