@@ -107,7 +107,7 @@ def test_grad_field_fd(setup):
     _loss_T(plan, xt, xp, gg).backward()
     gt, gp = xt.grad.detach().cpu().numpy(), xp.grad.detach().cpu().numpy()
     fdirs = []
-    for _ in range(16):
+    for _ in range(NDIR):
         dt = rng.standard_normal(tt.shape) + 1j * rng.standard_normal(tt.shape)
         dp = rng.standard_normal(tp.shape) + 1j * rng.standard_normal(tp.shape)
         nrm = np.sqrt(np.sum(np.abs(dt) ** 2) + np.sum(np.abs(dp) ** 2))
@@ -120,6 +120,26 @@ def test_grad_field_fd(setup):
     e_small, e_wide = _fd_errors(loss_at, (gt, gp), fdirs)
     assert e_small < 1e-6, e_small
     assert e_wide < 1e-7, e_wide
+
+
+def test_grad_field_analytic(setup, orc):
+    """grad_T = g W A (2 r), r = A^H W (g T) (W the point weights W_j 2 pi / nphi): the
+    oracle's synthesis of 2 r times the mask and the weights (2 fields)."""
+    plan, a, b, g, dirs = setup
+    gg = torch.as_tensor(g).cuda()
+    tt, tp = synthetic.grid_field(L, B, seed=SEED + 2)
+    xt = _cuda(tt).requires_grad_(True)
+    xp = _cuda(tp).requires_grad_(True)
+    _loss_T(plan, xt, xp, gg).backward()
+    gt, gp = xt.grad.detach().cpu().numpy(), xp.grad.detach().cpu().numpy()
+    x, W, theta, phi = orc.grid(L)
+    nphi = len(phi)
+    wpt = (W * (2 * np.pi / nphi))[:, None]
+    for f in (0, B - 1):
+        ra, rb = orc.fwd_sep(L, x, W, g * tt[f], g * tp[f])
+        t2, p2 = orc.adj_sep(L, x, 2 * ra, 2 * rb, nphi)
+        assert normwise_err(gt[f].ravel(), (g * wpt * t2).ravel()) < 1e-11
+        assert normwise_err(gp[f].ravel(), (g * wpt * p2).ravel()) < 1e-11
 
 
 def test_grad_coefficients_analytic(setup, orc):

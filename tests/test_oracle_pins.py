@@ -387,3 +387,39 @@ def test_field_a_closed_form_and_paper_bounds(orc):
     d_coef = max(np.max(np.abs(A1 - A)), np.max(np.abs(B1 - B)))
     d_T = max(np.max(np.abs(T2[0] - T1[0])), np.max(np.abs(T2[1] - T1[1])))
     assert d_coef <= t2[3] and d_T <= t2[2]
+
+
+@pytest.mark.parametrize("L,mstep", [(4, 2), (9, 3), (20, 7), (31, 64)])
+def test_strided_order_subsets_partition_the_transforms(orc, L, mstep):
+    """The order subsets the timed CPU baseline runs (orders m = mstart - L + k mstep) partition
+    the separable transforms: each forward subset fills exactly its own orders with the full
+    transform's values and leaves every other coefficient zero, and the adjoint subsets sum to
+    the full synthesis.  So a baseline timed on one subset and scaled by mstep counts the
+    work of the whole transform."""
+    rng = np.random.default_rng(300 + L)
+    x, W, theta, phi = orc.grid(L)
+    nlat, nphi = len(theta), len(phi)
+    Tth = rng.standard_normal((nlat, nphi)) + 1j * rng.standard_normal((nlat, nphi))
+    Tph = rng.standard_normal((nlat, nphi)) + 1j * rng.standard_normal((nlat, nphi))
+    a, b = orc.fwd_sep(L, x, W, Tth, Tph)
+    ms = np.concatenate([np.arange(-l, l + 1) for l in range(1, L + 1)])
+    sa = np.zeros_like(a)
+    sb = np.zeros_like(b)
+    for m0 in range(min(mstep, 2 * L + 1)):
+        pa, pb = orc.fwd_sep_orders(L, x, W, Tth, Tph, m0, mstep)
+        mine = ((ms + L - m0) % mstep) == 0
+        assert np.array_equal(pa[mine], a[mine]) and np.array_equal(pb[mine], b[mine])
+        assert not np.any(pa[~mine]) and not np.any(pb[~mine])
+        sa += pa
+        sb += pb
+    assert np.array_equal(sa, a) and np.array_equal(sb, b)
+    c1, c2 = _rand_coefs(L, rng)
+    tt, tp = orc.adj_sep(L, x, c1, c2, nphi)
+    st = np.zeros_like(tt)
+    sp = np.zeros_like(tp)
+    for m0 in range(min(mstep, 2 * L + 1)):
+        qt, qp = orc.adj_sep_orders(L, x, c1, c2, nphi, m0, mstep)
+        st += qt
+        sp += qp
+    sc = max(np.max(np.abs(tt)), np.max(np.abs(tp)))
+    assert np.max(np.abs(st - tt)) < 1e-13 * sc and np.max(np.abs(sp - tp)) < 1e-13 * sc
