@@ -9,31 +9,41 @@ namespace favest {
 
 namespace {
 
-// Up to eight warps per CTA: the FP64 units sit in the SM's four sub-partitions, so fewer
-// than four resident warps cannot keep the FP64 pipe full.  Small grids (J below 512) take
-// ceil(J / 64) warps, two latitudes per thread: warps without latitudes would still issue
-// their FP64 instructions (and the analysis its reductions) into the same pipe.
+// Eight warps per CTA: the FP64 units sit in the SM's four sub-partitions, so fewer than
+// four resident warps cannot keep the FP64 pipe full.  The synthesis takes ceil(J / 64)
+// warps on small grids, two latitudes per thread: warps without latitudes would still issue
+// their FP64 instructions into the same pipe.
 constexpr int kAnaThreads = 256;
-constexpr int kAnaWarps = kAnaThreads / 32;
 constexpr int kAnaJpt = 2;        // latitudes per thread (J <= 512)
-constexpr int kWin = 4;           // rows per reduction window (even)
+constexpr int kWin = 4;           // rows per renormalisation window of the synthesis (even)
 
 // Forward Legendre stage.  Fraw: [mu][ncol][nlat] raw longitude spectra; Q: [tab][ncol].
-template <int CT>
-__global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
+// The reduction over latitudes is what makes this stage costly if every thread keeps the
+// partial sums of its own latitudes: a warp reduction per window of rows then costs every
+// lane V*31/32 additions for V values (about 30% of the FP64 instructions at 4 columns; that
+// form ran at 0.62 of the FP64 rate at L = 1023).  Here the recurrence threads (two
+// latitudes each) write a window of R rows of values y_l(x_j) to
+// shared memory, and the contraction threads then each own one output (row, column) and a
+// strided subset of the latitudes, so the only reduction left is over the TPO threads of an
+// output (TPO - 1 adds per window and output).  Windows are double-buffered: one barrier per
+// window separates the recurrence of window k+1 from the contraction of window k.
+template <int CT, int R>
+__global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
     const double2 *__restrict__ Fraw, double2 *__restrict__ Q, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ omega, const double *__restrict__ cmu,
     const double *__restrict__ Atab, int L, int nlat, int J, int has_eq, int ncol, int ng)
 {
-    constexpr int V = kWin * CT * 2;
-    static_assert(V % 32 == 0, "window values must fill the warp");
+    constexpr int NOUT = R * CT, TPO = kAnaThreads / NOUT;
+    static_assert(kAnaThreads % NOUT == 0 && TPO >= 1 && TPO <= 32 && (TPO & (TPO - 1)) == 0, "output mapping");
+    // a warp's lanes then share one window row, so the shuffles below run warp-uniformly
+    static_assert(R <= 8 && 8 % R == 0, "window rows");
     extern __shared__ double sm_ana[];
     const int mu = blockIdx.x / ng, g = blockIdx.x % ng;
     const int nrow = L + 2 - mu;
     const long long t0 = tab_off(L, mu);
     double2 *Fs = reinterpret_cast<double2 *>(sm_ana);          // [2][CT][J]
-    double *As = sm_ana + 2 * 2 * CT * J;                       // [nrow]
-    double *red = As + ((nrow + 1) & ~1);                       // [warps][V]
+    double *Y = sm_ana + 2 * 2 * CT * J;                        // [2][R][J]
+    double *As = Y + 2 * R * J;                                 // [nrow]
 
     for (int idx = threadIdx.x; idx < CT * J; idx += blockDim.x) {
         int ct = idx / J, j = idx % J;
@@ -55,33 +65,33 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
     __syncthreads();
 
+    // recurrence role: latitudes threadIdx.x + i * kAnaThreads
     double x[kAnaJpt], y1[kAnaJpt], y2[kAnaJpt];
     int c[kAnaJpt];
     const double cm = cmu[mu];
 #pragma unroll
     for (int i = 0; i < kAnaJpt; ++i) {
-        int j = threadIdx.x + i * blockDim.x;
-        x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;   // inactive lanes stay silent
+        int j = threadIdx.x + i * kAnaThreads;
+        x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;
         if (j < J) {
             x[i] = xj[j];
             sectoral_start(cm, sj[j], mu, y1[i], c[i]);
         }
     }
+    // contraction role: output (row w of the window, column ct), latitudes jsub + k TPO
+    const int out = threadIdx.x / TPO, jsub = threadIdx.x % TPO;
+    const int wo = out / CT, cto = out % CT;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r0 = 0; r0 < nrow; r0 += kWin) {
-        double acc[V];
+    for (int r0 = 0, buf = 0; r0 < nrow; r0 += R, buf ^= 1) {
+        double *Yb = Y + buf * R * J;
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWin; ++w) {
+        for (int w = 0; w < R; ++w) {
             const int r = r0 + w;
             if (r < nrow) {
                 const double a = As[r];
-                const int p = w & 1;          // parity of l + mu = parity of r (r0 even)
 #pragma unroll
                 for (int i = 0; i < kAnaJpt; ++i) {
-                    const int j = threadIdx.x + i * blockDim.x;
+                    const int j = threadIdx.x + i * kAnaThreads;
                     if (j < J) {
                         double yl = y1[i];
                         if (r > 0) {
@@ -89,36 +99,43 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64(
                             y2[i] = y1[i];
                             y1[i] = yl;
                         }
-                        const double yv = (c[i] == 0) ? yl : 0.0;
-#pragma unroll
-                        for (int ct = 0; ct < CT; ++ct) {
-                            double2 f = Fs[(p * CT + ct) * J + j];
-                            acc[(w * CT + ct) * 2 + 0] = fma(yv, f.x, acc[(w * CT + ct) * 2 + 0]);
-                            acc[(w * CT + ct) * 2 + 1] = fma(yv, f.y, acc[(w * CT + ct) * 2 + 1]);
-                        }
+                        Yb[w * J + j] = (c[i] == 0) ? yl : 0.0;
                     }
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < kAnaJpt; ++i) renorm(y1[i], y2[i], c[i]);
-        warp_transpose_reduce<V>(acc);
-        constexpr int per = V / 32;
-#pragma unroll
-        for (int q = 0; q < per; ++q) red[warp * V + lane * per + q] = acc[q];
         __syncthreads();
-        const int nw = blockDim.x >> 5;
-        for (int vi = threadIdx.x; vi < V; vi += blockDim.x) {
-            double tot = 0.0;
-            for (int wq = 0; wq < nw; ++wq) tot += red[wq * V + vi];
-            const int w = vi / (CT * 2), ct = (vi / 2) % CT, im = vi & 1;
-            const int r = r0 + w;
-            if (r < nrow) {
-                double *dst = reinterpret_cast<double *>(Q + (size_t)(t0 + r) * ncol + g * CT + ct);
-                dst[im] = tot;
+        const int r = r0 + wo;
+        if (r < nrow) {                        // uniform over the TPO lanes of an output
+            const double *yr = Yb + wo * J;
+            const double2 *fr = Fs + ((r & 1) * CT + cto) * J;   // parity of l + mu = parity of r
+            double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+            int j = jsub;
+            for (; j + TPO < J; j += 2 * TPO) {
+                const double ya = yr[j], yb = yr[j + TPO];
+                const double2 fa = fr[j], fb = fr[j + TPO];
+                ax = fma(ya, fa.x, ax);
+                ay = fma(ya, fa.y, ay);
+                bx = fma(yb, fb.x, bx);
+                by = fma(yb, fb.y, by);
             }
+            if (j < J) {
+                const double ya = yr[j];
+                const double2 fa = fr[j];
+                ax = fma(ya, fa.x, ax);
+                ay = fma(ya, fa.y, ay);
+            }
+            ax += bx;
+            ay += by;
+#pragma unroll
+            for (int o = TPO / 2; o >= 1; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o, TPO);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o, TPO);
+            }
+            if (jsub == 0) Q[(size_t)(t0 + r) * ncol + g * CT + cto] = make_double2(ax, ay);
         }
-        __syncthreads();
     }
 }
 
@@ -242,37 +259,30 @@ int fp64_threads(int J, int maxthreads, int min_warps_grid)
     return w * 32 < maxthreads ? w * 32 : maxthreads;
 }
 
+template <int CT, int R>
+cudaError_t launch_analysis_t(const Plan &p, cudaStream_t s, const double *omega)
+{
+    const int ngt = p.ncol / CT;
+    const int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * ngt;
+    const int nrowmax = p.L + 2;
+    const size_t smem = (size_t)(4 * CT * p.J + 2 * R * p.J + ((nrowmax + 1) & ~1)) * sizeof(double);
+    auto k = k_analysis_fp64_t<CT, R>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
+                                      p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, ngt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 {
     if (p.J > kAnaThreads * kAnaJpt) return cudaErrorInvalidValue;
-    // orders 0..L, and L+1 for the scalar transforms of degree L+1 (Clebsch-Gordan route)
-    int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
-    // Two latitudes per thread halve the per-latitude cost of the warp reductions; with 4
-    // columns per CTA the analysis still wants the warps of one latitude per thread when
-    // the grid is small (L = 511, one field, 512 CTAs: 1.40 ms with 8 warps, 1.46 with 4),
-    // with 8 columns it does not (Clebsch-Gordan route, L = 511: 2.86 ms with 8 warps,
-    // 2.12 with 4).  The synthesis takes two latitudes per thread throughout (L = 511, one
-    // field: 1.40 ms with 8 warps, 0.99 with 4).
-    const int nt = fp64_threads(p.J, kAnaThreads, p.ct == 8 ? 0 : (24 * p.num_sms + grid - 1) / grid);
+    // orders 0..L, and L+1 for the scalar transforms of degree L+1 (Clebsch-Gordan route).
+    // Windows of 8 rows and 8 columns per CTA where the columns allow, else 4 (measured on
+    // GB300: L = 1023, 32 fields 214 -> 134 ms; L = 511, one field 1.34 -> 1.10 ms against the
+    // per-thread reduction form).
     const double *omega = p.nscal > 0 ? p.d_wring : p.unit_weights ? p.d_omega_unit : p.d_omega;
-    int nrowmax = p.L + 2;
-    size_t smem;
-    if (p.ct == 8) {
-        constexpr int CT = 8, V = kWin * CT * 2;
-        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
-        auto k = k_analysis_fp64<CT>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, nt, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
-                                 p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
-    } else {
-        constexpr int CT = 4, V = kWin * CT * 2;
-        smem = (size_t)(2 * 2 * CT * p.J + ((nrowmax + 1) & ~1) + kAnaWarps * V) * sizeof(double);
-        auto k = k_analysis_fp64<CT>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, nt, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
-                                 p.d_A, p.L, p.nlat, p.J, p.has_eq, p.ncol, p.ng);
-    }
-    return cudaGetLastError();
+    return p.ncol % 8 == 0 ? launch_analysis_t<8, 8>(p, s, omega) : launch_analysis_t<4, 8>(p, s, omega);
 }
 
 cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
