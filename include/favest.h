@@ -100,8 +100,8 @@ int favest_gl_grid(int nlat, double *x, double *w);
 
 /*
  * Create a plan for degree L and a batch of `batch` fields (1 <= batch <= 4096) on the
- * current CUDA device.  L >= 1; degrees beyond 1023 (more than 512 latitude pairs)
- * return FAVEST_EUNSUPPORTED in this version.  FAVEST_BF16X6
+ * current CUDA device.  1 <= L <= 2559 (up to 1280 latitude pairs); L = 2560..4095 returns
+ * FAVEST_EUNSUPPORTED, L < 1, L > 4095 or a batch outside 1..4096 FAVEST_EINVAL.  FAVEST_BF16X6
  * requires io_type FAVEST_IO_C64 or FAVEST_IO_R32 (FAVEST_EUNSUPPORTED otherwise) and
  * a device with tcgen05 tensor cores (sm_100 family), and its FP32 longitude DFT takes
  * nphi = 2(L+1) with prime factors up to 128 only (FAVEST_EUNSUPPORTED otherwise, e.g.
@@ -183,7 +183,7 @@ int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, voi
  * eq. ninecoeff exactly as favest_fwd_cart / favest_adj_cart do.  No quadrature exactness is
  * assumed: favest_scatter_fwd is the weighted sum itself, whatever the points and weights.
  *
- * favest_scatter_create: L = 1..1023, batch = 1..1366 fields, npts = 1..2^26 points.
+ * favest_scatter_create: L = 1..2047, batch = 1..1366 fields, npts = 1..2^26 points.
  *   X: host [npts][3], the points as unit vectors (|x_k| = 1 to 1e-10, FAVEST_EINVAL
  *      otherwise; they are normalised); points at or near the poles are allowed.
  *   w: host [npts] point weights, or NULL for unit weights (then the forward is A^H, the

@@ -109,11 +109,86 @@ void free_plan(Plan &p)
                     p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam_f, p.d_lam_a, p.d_Fb, p.d_gb,
                     p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
-                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups};
+                    p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups,
+                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
     std::free(p.h_w);
+}
+
+// In-place radix-2 FFT of M = 2^lg points, FP64, exp(-2 pi i / M) (host; natural order).
+void host_fft_pow2(std::vector<double2> &v, int lg)
+{
+    const int M = 1 << lg;
+    for (int i = 1, j = 0; i < M; ++i) {              // bit reversal
+        int bit = M >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(v[i], v[j]);
+    }
+    for (int len = 2; len <= M; len <<= 1) {
+        for (int i = 0; i < M; i += len) {
+            for (int k = 0; k < len / 2; ++k) {
+                const long double ang = -2.0L * 3.141592653589793238462643383279502884L * k / len;
+                const double c = (double)cosl(ang), sn = (double)sinl(ang);
+                const double2 a = v[i + k], b = v[i + k + len / 2];
+                const double2 t = make_double2(b.x * c - b.y * sn, b.x * sn + b.y * c);
+                v[i + k] = make_double2(a.x + t.x, a.y + t.y);
+                v[i + k + len / 2] = make_double2(a.x - t.x, a.y - t.y);
+            }
+        }
+    }
+}
+
+// Tables of the FP32 DFT's Bluestein stage for a prime radix above the direct forms (128):
+// chirp c_t = exp(-i pi t^2 / R) from the exactly reduced t^2 mod 2R, the spectrum of its
+// conjugate zero-padded to M = 2^lg >= 2R - 1 (FP64, scaled by 1/M, stored bit-reversed for
+// the device's decimation in frequency), and the M-point twiddles.  The scratch of M points
+// must fit beside the DFT buffer of 4 rings in one CTA's shared memory.
+int build_bluestein(Plan &p)
+{
+    int R = 0;
+    for (int st = 0; st < p.fft.nstages; ++st) {
+        const int r = p.fft.radix[st];
+        if (r <= 128) continue;
+        if (R != 0 && r != R) return FAVEST_EUNSUPPORTED;     // two large primes (n > 5120)
+        R = r;
+    }
+    if (R == 0) return FAVEST_OK;
+    int lg = 1;
+    while ((1 << lg) < 2 * R - 1) ++lg;
+    const int M = 1 << lg;
+    const size_t ring_bytes = (size_t)32 * p.nphi, scratch = (size_t)8 * M;
+    if (ring_bytes + (scratch > 24576 ? scratch : 24576) > 227 * 1024) return FAVEST_EUNSUPPORTED;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<float2> chirp(R), spec(M), twm(M / 2);
+    std::vector<double2> b(M, make_double2(0.0, 0.0));
+    for (int t = 0; t < R; ++t) {
+        const long long q = ((long long)t * t) % (2LL * R);
+        const long double ang = -pi * (long double)q / (long double)R;
+        const double c = (double)cosl(ang), sn = (double)sinl(ang);
+        chirp[t] = make_float2((float)c, (float)sn);
+        b[t] = make_double2(c, -sn);                          // conj(c_t)
+        if (t > 0) b[M - t] = make_double2(c, -sn);
+    }
+    host_fft_pow2(b, lg);
+    for (int i = 0; i < M; ++i) {
+        int r = 0;
+        for (int k = 0; k < lg; ++k) r |= ((i >> k) & 1) << (lg - 1 - k);
+        spec[i] = make_float2((float)(b[r].x / M), (float)(b[r].y / M));
+    }
+    for (int k = 0; k < M / 2; ++k) {
+        const long double ang = -2.0L * pi * k / M;
+        twm[k] = make_float2((float)cosl(ang), (float)sinl(ang));
+    }
+    cudaError_t e;
+    if ((e = upload(&p.fft.blue_chirp, chirp)) || (e = upload(&p.fft.blue_spec, spec)) ||
+        (e = upload(&p.fft.blue_tw, twm)))
+        return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
+    p.fft.blue_R = R;
+    p.fft.blue_log2m = lg;
+    return FAVEST_OK;
 }
 
 int build_tables(Plan &p)
@@ -195,9 +270,10 @@ int build_tables(Plan &p)
     p.fft.n = n;
     p.fft.nstages = factorize(n, p.fft.radix);
     if (p.fft.nstages < 0) return FAVEST_EUNSUPPORTED;
-    if (p.precision == FAVEST_BF16X6)
-        for (int st = 0; st < p.fft.nstages; ++st)
-            if (p.fft.radix[st] > 128) return FAVEST_EUNSUPPORTED;
+    if (p.precision == FAVEST_BF16X6) {
+        const int st = build_bluestein(p);
+        if (st != FAVEST_OK) return st;
+    }
     std::vector<double2> tw(n);
     std::vector<float2> tw32(n);
     for (int k = 0; k < n; ++k) {
@@ -635,7 +711,7 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     if (!out) return FAVEST_EINVAL;
     *out = nullptr;
     if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
-    if (L > 1023) return FAVEST_EUNSUPPORTED;
+    if (L > 2559) return FAVEST_EUNSUPPORTED;   // J <= 1280 latitudes per CTA in the FP64 kernels
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
     if (io_type != FAVEST_IO_C128 && io_type != FAVEST_IO_C64 && io_type != FAVEST_IO_R32 && io_type != FAVEST_IO_R64)
         return FAVEST_EINVAL;
@@ -698,7 +774,7 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     } else {
         gl_rule(nlat, p.h_x, p.h_w);
     }
-    if (p.J > 512) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
+    if (p.J > 1280) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
     int st = build_tables(p);
     if (st == FAVEST_OK) st = (precision == FAVEST_BF16X6) ? alloc_workspace_bf16(p) : alloc_workspace(p);
     if (st != FAVEST_OK) {

@@ -39,6 +39,12 @@ struct FftPlan {
     int radix[kMaxRadixStages];
     double2 *tw64 = nullptr;   // device, e^{-2 pi i k / n}, k = 0..n-1
     float2 *tw32 = nullptr;    // device, same rounded to float
+    // FP32 DFT stage of a prime radix above the in-register and per-warp forms (Bluestein's
+    // chirp transform, a cyclic convolution of power-of-two length M >= 2R - 1): 0 if none
+    int blue_R = 0, blue_log2m = 0;
+    float2 *blue_chirp = nullptr;   // [R] exp(-i pi t^2 / R), t^2 reduced mod 2R exactly
+    float2 *blue_spec = nullptr;    // [M] DFT_M of the conjugate chirp, / M, bit-reversed order
+    float2 *blue_tw = nullptr;      // [M/2] exp(-2 pi i k / M)
 };
 
 constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk

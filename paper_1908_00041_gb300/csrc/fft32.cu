@@ -35,7 +35,7 @@ __device__ __forceinline__ float2 twf(const float2 *__restrict__ tw, int q)
     return INV ? make_float2(t.x, -t.y) : t;
 }
 
-constexpr int kMaxInlineRadix = 128;   // largest odd prime factor of nphi supported
+constexpr int kMaxInlineRadix = 128;   // largest odd prime radix of the direct forms (Bluestein above)
 
 // In-place decimation-in-frequency FFT of `nr` rings of n points stored back to back.
 // Stage s (radix R, block length Nb, h = Nb/R): for every block and k < h the R points
@@ -154,8 +154,76 @@ __device__ __forceinline__ void dif_stage_odd(float2 *x, const float2 *__restric
     }
 }
 
+// Prime radix R above kMaxInlineRadix: Bluestein's identity q t = (q^2 + t^2 - (q - t)^2) / 2
+// turns each R-point DFT into a cyclic convolution,
+//   out_q = c_q sum_t (x_t c_t) conj(c_{q-t}),   c_t = exp(-i pi t^2 / R),
+// done at power-of-two length M >= 2R - 1 in the CTA's scratch: a radix-2 decimation in
+// frequency (natural order in, bit-reversed out), the product with the precomputed spectrum
+// of conj(c) (stored bit-reversed, scaled by 1/M), a radix-2 decimation in time with
+// conjugate twiddles (bit-reversed in, natural out).  The inverse transform is the
+// conjugate of the forward one of the conjugated input.  Butterflies run one after another,
+// each with all threads of the CTA; a butterfly reads its R points before any is rewritten.
+// Error in FP32 about 2e-7 of the largest output for R up to 2251 (checked against a library
+// FFT on the host before the kernel was written).
 template <bool INV>
-__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr)
+__device__ void dif_stage_bluestein(float2 *x, const float2 *__restrict__ tw, int n, int R, int Nb, int nr,
+                                    const RadixPlanArg &rp, float2 *sc)
+{
+    const int h = Nb / R, ts = n / Nb, nbf = n / R;
+    const int lg = rp.blue_log2m, M = 1 << lg;
+    const float2 *__restrict__ ch = rp.blue_chirp;
+    const float2 *__restrict__ sp = rp.blue_spec;
+    const float2 *__restrict__ tm = rp.blue_tw;
+    for (int bi = 0; bi < nbf * nr; ++bi) {
+        const int ring = bi / nbf, i = bi - ring * nbf;
+        const int blk = i / h, k = i - blk * h;
+        const int base = ring * n + blk * Nb + k;
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+            float2 v = make_float2(0.f, 0.f);
+            if (t < R) {
+                float2 xv = x[base + t * h];
+                if (INV) xv.y = -xv.y;
+                v = cmulf(xv, __ldg(ch + t));
+            }
+            sc[t] = v;
+        }
+        __syncthreads();
+        for (int lgs = lg - 1; lgs >= 0; --lgs) {          // half-block s = 2^lgs
+            const int s = 1 << lgs;
+            for (int u = threadIdx.x; u < M / 2; u += blockDim.x) {
+                const int j = u & (s - 1), i0 = ((u >> lgs) << (lgs + 1)) + j;
+                const float2 a = sc[i0], b = sc[i0 + s];
+                sc[i0] = caddf(a, b);
+                sc[i0 + s] = cmulf(csubf(a, b), __ldg(tm + (j << (lg - 1 - lgs))));
+            }
+            __syncthreads();
+        }
+        for (int t = threadIdx.x; t < M; t += blockDim.x) sc[t] = cmulf(sc[t], __ldg(sp + t));
+        __syncthreads();
+        for (int lgs = 0; lgs < lg; ++lgs) {
+            const int s = 1 << lgs;
+            for (int u = threadIdx.x; u < M / 2; u += blockDim.x) {
+                const int j = u & (s - 1), i0 = ((u >> lgs) << (lgs + 1)) + j;
+                float2 w = __ldg(tm + (j << (lg - 1 - lgs)));
+                w.y = -w.y;
+                const float2 a = sc[i0], b = cmulf(sc[i0 + s], w);
+                sc[i0] = caddf(a, b);
+                sc[i0 + s] = csubf(a, b);
+            }
+            __syncthreads();
+        }
+        for (int q = threadIdx.x; q < R; q += blockDim.x) {
+            float2 v = cmulf(sc[q], __ldg(ch + q));
+            if (INV) v.y = -v.y;
+            x[base + q * h] = cmulf(v, twf<INV>(tw, q * k * ts));
+        }
+        __syncthreads();
+    }
+}
+
+// sc: scratch of 2^blue_log2m points when the plan has a Bluestein radix (else unused)
+template <bool INV>
+__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc)
 {
     const int n = rp.n;
     int Nb = n;
@@ -174,6 +242,8 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
             dif_stage_small<11, INV>(x, tw, n, Nb, nr);
         } else if (R == 13) {
             dif_stage_small<13, INV>(x, tw, n, Nb, nr);
+        } else if (R == rp.blue_R) {
+            dif_stage_bluestein<INV>(x, tw, n, R, Nb, nr, rp, sc);
         } else if (R != 2 && R != 4) {
             dif_stage_odd<INV>(x, tw, n, R, Nb, nr);
         } else {
@@ -611,7 +681,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     }
     if constexpr (LOG2N == 0) {
         __syncthreads();
-        dif_f32<false>(buf, tw, rp, nr);
+        dif_f32<false>(buf, tw, rp, nr,
+                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = omega[j];
     // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
@@ -783,7 +854,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     if constexpr (LOG2N > 0) {
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, ComplexRowsOut{Tth, Tph, fb, j, jm, n});
     } else {
-        dif_f32<true>(buf, tw, rp, nr);
+        dif_f32<true>(buf, tw, rp, nr,
+                      reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_i4) + fft_smem_bytes<LOG2N>(n)));
         const int n2 = n / 2;
         for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
             const int ring = idx / n2, k2 = idx % n2;
@@ -877,7 +949,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
     }
     if constexpr (LOG2N == 0) {
         __syncthreads();
-        dif_f32<false>(buf, tw, rp, nr);
+        dif_f32<false>(buf, tw, rp, nr,
+                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
@@ -981,7 +1054,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
         return;
     }
-    dif_f32<true>(buf, tw, rp, nr);
+    dif_f32<true>(buf, tw, rp, nr,
+                  reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_s4) + fft_smem_bytes<LOG2N>(n)));
     const int nv = n / V;
     for (int idx = threadIdx.x; idx < nr * nv; idx += blockDim.x) {
         const int ring = idx / nv, kv = idx % nv;
@@ -1007,7 +1081,9 @@ template <int LOG2N>
 cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + kStageBytes;
+    // record staging after the DFT; the Bluestein scratch (during the DFT) shares its space
+    const size_t blue = p.fft.blue_R ? (size_t)8 << p.fft.blue_log2m : 0;
+    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (blue > kStageBytes ? blue : kStageBytes);
     if (p.real) {
         auto k = k_rfft_fwd_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1029,7 +1105,8 @@ template <int LOG2N>
 cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (LOG2N > 0 ? kInvStageBytes : 0);
+    const size_t blue = p.fft.blue_R ? (size_t)8 << p.fft.blue_log2m : 0;
+    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (LOG2N > 0 ? kInvStageBytes : blue);
     if (p.real) {
         auto k = k_rfft_inv_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,6 +10,8 @@ struct RadixPlanArg {
     int n;
     int nstages;
     int radix[kMaxRadixStages];
+    int blue_R, blue_log2m;             // see FftPlan
+    const float2 *blue_chirp, *blue_spec, *blue_tw;
 };
 
 inline RadixPlanArg make_radix_arg(const FftPlan &f)
@@ -18,6 +20,11 @@ inline RadixPlanArg make_radix_arg(const FftPlan &f)
     r.n = f.n;
     r.nstages = f.nstages;
     for (int i = 0; i < kMaxRadixStages; ++i) r.radix[i] = i < f.nstages ? f.radix[i] : 1;
+    r.blue_R = f.blue_R;
+    r.blue_log2m = f.blue_log2m;
+    r.blue_chirp = f.blue_chirp;
+    r.blue_spec = f.blue_spec;
+    r.blue_tw = f.blue_tw;
     return r;
 }
 

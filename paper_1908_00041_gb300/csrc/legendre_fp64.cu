@@ -14,7 +14,8 @@ namespace {
 // warps on small grids, two latitudes per thread: warps without latitudes would still issue
 // their FP64 instructions into the same pipe.
 constexpr int kAnaThreads = 256;
-constexpr int kAnaJpt = 2;        // latitudes per thread (J <= 512)
+constexpr int kAnaJpt = 2;        // latitudes per recurrence thread up to J = 512 (L <= 1023)
+constexpr int kBigJpt = 5;        // beyond: J <= 1280 (L <= 2559)
 constexpr int kWin = 4;           // rows per renormalisation window of the synthesis (even)
 
 // Forward Legendre stage.  Fraw: [mu][ncol][nlat] raw longitude spectra; Q: [tab][ncol].
@@ -27,7 +28,7 @@ constexpr int kWin = 4;           // rows per renormalisation window of the synt
 // strided subset of the latitudes, so the only reduction left is over the TPO threads of an
 // output (TPO - 1 adds per window and output).  Windows are double-buffered: one barrier per
 // window separates the recurrence of window k+1 from the contraction of window k.
-template <int CT, int R>
+template <int CT, int R, int JPT>
 __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
     const double2 *__restrict__ Fraw, double2 *__restrict__ Q, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ omega, const double *__restrict__ cmu,
@@ -66,11 +67,11 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
     __syncthreads();
 
     // recurrence role: latitudes threadIdx.x + i * kAnaThreads
-    double x[kAnaJpt], y1[kAnaJpt], y2[kAnaJpt];
-    int c[kAnaJpt];
+    double x[JPT], y1[JPT], y2[JPT];
+    int c[JPT];
     const double cm = cmu[mu];
 #pragma unroll
-    for (int i = 0; i < kAnaJpt; ++i) {
+    for (int i = 0; i < JPT; ++i) {
         int j = threadIdx.x + i * kAnaThreads;
         x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;
         if (j < J) {
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
             if (r < nrow) {
                 const double a = As[r];
 #pragma unroll
-                for (int i = 0; i < kAnaJpt; ++i) {
+                for (int i = 0; i < JPT; ++i) {
                     const int j = threadIdx.x + i * kAnaThreads;
                     if (j < J) {
                         double yl = y1[i];
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
             }
         }
 #pragma unroll
-        for (int i = 0; i < kAnaJpt; ++i) renorm(y1[i], y2[i], c[i]);
+        for (int i = 0; i < JPT; ++i) renorm(y1[i], y2[i], c[i]);
         __syncthreads();
         const int r = r0 + wo;
         if (r < nrow) {                        // uniform over the TPO lanes of an output
@@ -140,14 +141,13 @@ __global__ void __launch_bounds__(kAnaThreads) k_analysis_fp64_t(
 }
 
 constexpr int kSynThreads = 256;
-constexpr int kSynJpt = 2;        // J <= 512
 
 // Adjoint Legendre stage.  gtab: [tab][ncol] scaled coefficients; G: [B][2][nlat][nphi].
 // Vector mode divides the sums by sin(theta_j).  Scalar mode (the Clebsch-Gordan route)
 // does not, and order L+1 exists there: its orders +-(L+1) share the Nyquist bin, so the
 // two sign columns are added into it.  Real fields (real != 0): column (q*2 + c)*2 + f is
 // component c of field 2q + f at m = +mu, written to row (2q + f)*2 + c at bin mu.
-template <int CT>
+template <int CT, int JPT>
 __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     const double2 *__restrict__ gtab, double2 *__restrict__ G, const double *__restrict__ xj,
     const double *__restrict__ sj, const double *__restrict__ cmu, const double *__restrict__ Atab,
@@ -166,12 +166,12 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) As[r] = Atab[t0 + r];
     __syncthreads();
 
-    double x[kSynJpt], y1[kSynJpt], y2[kSynJpt];
-    int c[kSynJpt];
-    double2 accE[kSynJpt][CT], accO[kSynJpt][CT];
+    double x[JPT], y1[JPT], y2[JPT];
+    int c[JPT];
+    double2 accE[JPT][CT], accO[JPT][CT];
     const double cm = cmu[mu];
 #pragma unroll
-    for (int i = 0; i < kSynJpt; ++i) {
+    for (int i = 0; i < JPT; ++i) {
         int j = threadIdx.x + i * blockDim.x;
         x[i] = 0.0; y1[i] = 0.0; y2[i] = 0.0; c[i] = 1 << 20;
         if (j < J) {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
             if (r < nrow) {
                 const double a = As[r];
 #pragma unroll
-                for (int i = 0; i < kSynJpt; ++i) {
+                for (int i = 0; i < JPT; ++i) {
                     double yl = y1[i];
                     if (r > 0) {
                         yl = fma(a * x[i], y1[i], -y2[i]);
@@ -214,10 +214,10 @@ __global__ void __launch_bounds__(kSynThreads) k_synthesis_fp64(
             }
         }
 #pragma unroll
-        for (int i = 0; i < kSynJpt; ++i) renorm(y1[i], y2[i], c[i]);
+        for (int i = 0; i < JPT; ++i) renorm(y1[i], y2[i], c[i]);
     }
 #pragma unroll
-    for (int i = 0; i < kSynJpt; ++i) {
+    for (int i = 0; i < JPT; ++i) {
         const int j = threadIdx.x + i * blockDim.x;
         if (j >= J) continue;
         const double is = scalar ? 1.0 : 1.0 / sj[j];
@@ -259,14 +259,14 @@ int fp64_threads(int J, int maxthreads, int min_warps_grid)
     return w * 32 < maxthreads ? w * 32 : maxthreads;
 }
 
-template <int CT, int R>
+template <int CT, int R, int JPT>
 cudaError_t launch_analysis_t(const Plan &p, cudaStream_t s, const double *omega)
 {
     const int ngt = p.ncol / CT;
     const int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * ngt;
     const int nrowmax = p.L + 2;
     const size_t smem = (size_t)(4 * CT * p.J + 2 * R * p.J + ((nrowmax + 1) & ~1)) * sizeof(double);
-    auto k = k_analysis_fp64_t<CT, R>;
+    auto k = k_analysis_fp64_t<CT, R, JPT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kAnaThreads, smem, s>>>((const double2 *)p.d_F, (double2 *)p.d_Q, p.d_x, p.d_sin, omega, p.d_cmu,
@@ -274,39 +274,51 @@ cudaError_t launch_analysis_t(const Plan &p, cudaStream_t s, const double *omega
     return cudaGetLastError();
 }
 
+// Shared memory of one analysis CTA (bytes) and the largest a CTA may take on sm_100-class
+// parts.
+size_t analysis_smem(int CT, int R, int J, int L) { return (size_t)(4 * CT * J + 2 * R * J + L + 3) * 8; }
+constexpr size_t kMaxSmem = 227 * 1024;
+
 cudaError_t launch_analysis_fp64(const Plan &p, cudaStream_t s)
 {
-    if (p.J > kAnaThreads * kAnaJpt) return cudaErrorInvalidValue;
+    if (p.J > kAnaThreads * kBigJpt) return cudaErrorInvalidValue;
     // orders 0..L, and L+1 for the scalar transforms of degree L+1 (Clebsch-Gordan route).
     // Windows of 8 rows and 8 columns per CTA where the columns allow, else 4 (measured on
     // GB300: L = 1023, 32 fields 214 -> 134 ms; L = 511, one field 1.34 -> 1.10 ms against the
-    // per-thread reduction form).
+    // per-thread reduction form).  Beyond 512 latitudes the staged spectra and windows must
+    // still fit one CTA's shared memory: 4 columns with 2-row windows, else 2 columns with
+    // 4-row windows (J <= 1280).
     const double *omega = p.nscal > 0 ? p.d_wring : p.unit_weights ? p.d_omega_unit : p.d_omega;
-    return p.ncol % 8 == 0 ? launch_analysis_t<8, 8>(p, s, omega) : launch_analysis_t<4, 8>(p, s, omega);
+    if (p.J <= kAnaThreads * kAnaJpt)
+        return p.ncol % 8 == 0 ? launch_analysis_t<8, 8, kAnaJpt>(p, s, omega)
+                               : launch_analysis_t<4, 8, kAnaJpt>(p, s, omega);
+    if (analysis_smem(4, 2, p.J, p.L) <= kMaxSmem) return launch_analysis_t<4, 2, kBigJpt>(p, s, omega);
+    return launch_analysis_t<2, 4, kBigJpt>(p, s, omega);
+}
+
+template <int CT, int JPT>
+cudaError_t launch_synthesis_t(const Plan &p, cudaStream_t s)
+{
+    const int nt = fp64_threads(p.J, kSynThreads, 0);
+    const int ngt = p.ncol / CT;
+    const int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * ngt;
+    const int nrowmax = p.L + 2;
+    const size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
+    auto k = k_synthesis_fp64<CT, JPT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, nt, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin, p.d_cmu, p.d_A, p.L,
+                             p.nlat, p.nphi, p.J, p.has_eq, p.ncol, ngt, p.nscal > 0, p.real);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_synthesis_fp64(const Plan &p, cudaStream_t s)
 {
-    if (p.J > kSynThreads * kSynJpt) return cudaErrorInvalidValue;
-    const int nt = fp64_threads(p.J, kSynThreads, 0);
-    int grid = (p.L + 1 + (p.nscal > 0 ? 1 : 0)) * p.ng;
-    int nrowmax = p.L + 2;
-    if (p.ct == 8) {
-        constexpr int CT = 8;
-        size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
-        auto k = k_synthesis_fp64<CT>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, nt, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin, p.d_cmu, p.d_A,
-                                 p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol, p.ng, p.nscal > 0, p.real);
-    } else {
-        constexpr int CT = 4;
-        size_t smem = (size_t)(2 * CT * nrowmax + nrowmax) * sizeof(double);
-        auto k = k_synthesis_fp64<CT>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, nt, smem, s>>>((const double2 *)p.d_Q, (double2 *)p.d_G, p.d_x, p.d_sin, p.d_cmu, p.d_A,
-                                 p.L, p.nlat, p.nphi, p.J, p.has_eq, p.ncol, p.ng, p.nscal > 0, p.real);
-    }
-    return cudaGetLastError();
+    if (p.J > kSynThreads * kBigJpt) return cudaErrorInvalidValue;
+    // beyond 512 latitudes: five per thread and two columns per CTA (the accumulators of
+    // JPT latitudes x CT columns live in registers)
+    if (p.J > kSynThreads * kAnaJpt) return launch_synthesis_t<2, kBigJpt>(p, s);
+    return p.ct == 8 ? launch_synthesis_t<8, kAnaJpt>(p, s) : launch_synthesis_t<4, kAnaJpt>(p, s);
 }
 
 }  // namespace favest

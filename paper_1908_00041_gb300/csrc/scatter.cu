@@ -308,7 +308,8 @@ int favest_scatter_create(int L, int batch, int npts, const double *X, const dou
     using namespace favest;
     if (!out) return FAVEST_EINVAL;
     *out = nullptr;
-    if (L < 1 || L > 1023 || batch < 1 || batch > 1366 || npts < 1 || npts > (1 << 26) || !X) return FAVEST_EINVAL;
+    // L <= 2047: one order's staged coefficients (and sums) fit a CTA's shared memory
+    if (L < 1 || L > 2047 || batch < 1 || batch > 1366 || npts < 1 || npts > (1 << 26) || !X) return FAVEST_EINVAL;
     std::vector<double> hx(npts), hs(npts), hphi(npts), hw(npts);
     for (int k = 0; k < npts; ++k) {
         const double a = X[3 * k], b = X[3 * k + 1], z = X[3 * k + 2];

@@ -126,7 +126,7 @@ def test_scatter_unit_weights_is_exact_adjoint():
 
 def test_scatter_argument_errors():
     X = _points(10, 1)
-    for L, B, pts in [(0, 1, X), (1024, 1, X), (4, 0, X), (4, 1, X * 1.001)]:
+    for L, B, pts in [(0, 1, X), (2048, 1, X), (4, 0, X), (4, 1, X * 1.001)]:
         with pytest.raises(api.FavestError) as e:
             api.ScatterPlan(L, pts, None, batch=B)
         assert e.value.status == api.FAVEST_EINVAL
