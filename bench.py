@@ -140,12 +140,31 @@ def ncu_traffic(kernel, L, B):
         return None
 
 
-def kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B):
+def alu_peaks():
+    """FP64 and FP32 FMA peaks (TFLOP/s) from unit counts and the maximum SM clock: 152 SMs x
+    2 FP64 FMA per clock (NVIDIA's 1.25 TFLOP/s FP64 figure for GB300 at 2.07 GHz: 1.25e12 /
+    (2 x 152 x 2.07e9) = 1.99) and 128 FP32 FMA per clock per SM, an FMA counted as 2."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sms * 2 * 2 * mhz * 1e6 / 1e12, sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def kernel_rooflines(plan, prof, fp64_probe, fp32_probe, L, B):
     hbm, bf16, src = measured_peaks()
+    f64, f32, sms, mhz = alu_peaks()
     units = {0: ("hbm", "GB/s", hbm, "HBM copy bandwidth, MEASURED_PEAKS.json (%s)" % src),
-             1: ("alu", "TFLOP/s", fp64_peak, "FP64 FMA throughput measured live by favest_probe_peaks"),
+             1: ("alu", "TFLOP/s", f64, "FP64 FMA peak from unit counts: %d SMs x 2 FMA/clk x 2 flop x %.0f MHz "
+                                        "(derived; probe-measured FMA stream %.3f)" % (sms, mhz, fp64_probe)),
              2: ("tensor", "TFLOP/s", bf16, "bf16 dense sustained, MEASURED_PEAKS.json (%s)" % src),
-             3: ("alu", "TFLOP/s", fp32_peak, "FP32 FMA throughput measured live by favest_probe_peaks")}
+             3: ("alu", "TFLOP/s", f32, "FP32 FMA peak from unit counts: %d SMs x 128 FMA/clk x 2 flop x %.0f MHz "
+                                        "(derived; probe-measured FMA stream %.2f)" % (sms, mhz, fp32_probe))}
+    probes = {1: fp64_probe, 3: fp32_probe}
     total = sum(v[0] for v in prof.values())
     kernels = {}
     for name, (tot_ms, n) in prof.items():
@@ -158,6 +177,8 @@ def kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B):
                          "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                          "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
                          "hbm_frac": nbytes / t / 1e9 / hbm}
+        if pipe in probes:
+            kernels[name]["frac_of_probe"] = achieved / probes[pipe]
     top = max(kernels, key=lambda k: kernels[k]["share"])
     k = kernels[top]
     roofline = {"kernel": top, "bound": k["bound"], "achieved": k["achieved"], "peak": k["peak"],
@@ -235,6 +256,65 @@ def measure_split_other_length(L, B, stream):
     return {"value": B / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms, "L": L, "nphi": 2 * (L + 1),
             "generator_shape": shape, "roundtrip_max_rel": err,
             "kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+
+
+# Table 3 of the paper (one field, CPU with MATLAB + NFFT): seconds per FwdVSHT and AdjVSHT
+PAPER_TABLE3 = {250: (0.40, 0.83), 500: (1.81, 3.87), 750: (4.22, 9.52), 1000: (7.2903, 17.89),
+                1250: (15.16, 33.97), 1500: (22.30, 50.32), 1750: (32.87, 73.94), 2000: (41.51, 97.32),
+                2250: (62.74, 144.70)}
+
+
+def measure_table3(stream, batch=32):
+    """The paper's timing degrees (Table 3: L = 250 .. 2250; nphi = 2(L+1) with prime factors
+    151..2251 above 128 for most of them, taken by the Bluestein stage of the FP32 DFT).  Per
+    degree: the split path on one field (adjoint and forward each with its own generator
+    pass, like the paper's per-transform times), the split path's throughput on `batch`
+    fields (adjoint + forward sharing one generator pass), and the FP64 path on one field;
+    roundtrip errors of the batch; the paper's CPU seconds beside them for context."""
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    out = {}
+    for L in sorted(PAPER_TABLE3):
+        row = {"nphi": 2 * (L + 1), "paper_cpu_s": {"fwd": PAPER_TABLE3[L][0], "adj": PAPER_TABLE3[L][1]}}
+        for B, key in ((1, "split_one_field"), (batch, "split_batch")):
+            p = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+            p.tune()
+            a, b = synthetic.coefficients(L, B, seed=7, decay=1.5)
+            a = torch.as_tensor(a).to(torch.complex64).cuda()
+            b = torch.as_tensor(b).to(torch.complex64).cuda()
+            tt = torch.empty(p.field_shape(), dtype=torch.complex64, device="cuda")
+            tp = torch.empty_like(tt)
+            a2 = torch.empty_like(a)
+            b2 = torch.empty_like(b)
+            if B == 1:
+                adj_ms = time_steps(lambda: p.adj(a, b, tt, tp, stream=stream), 5, 2, stream)
+                fwd_ms = time_steps(lambda: p.fwd(tt, tp, a2, b2, stream=stream), 5, 2, stream)
+                row[key] = {"adj_ms": adj_ms, "fwd_ms": fwd_ms}
+            else:
+                def st():
+                    p.adj(a, b, tt, tp, stream=stream, share_lambda=True)
+                    p.fwd(tt, tp, a2, b2, stream=stream, share_lambda=True)
+                ms = time_steps(st, 5, 2, stream)
+                err = max(float((a2 - a).abs().max() / a.abs().max()), float((b2 - b).abs().max() / b.abs().max()))
+                row[key] = {"fields": B, "ms_per_step": ms, "fields_per_s": B / (ms * 1e-3), "roundtrip_max_rel": err}
+            p.close()
+            del a, b, tt, tp, a2, b2
+            torch.cuda.empty_cache()
+        p64 = api.Plan(L, 1, api.FAVEST_FP64, api.FAVEST_IO_C128)
+        a, b = synthetic.coefficients(L, 1, seed=7)
+        a = torch.as_tensor(a).cuda()
+        b = torch.as_tensor(b).cuda()
+        tt = torch.empty(p64.field_shape(), dtype=torch.complex128, device="cuda")
+        tp = torch.empty_like(tt)
+        a2 = torch.empty_like(a)
+        b2 = torch.empty_like(b)
+        adj_ms = time_steps(lambda: p64.adj(a, b, tt, tp, stream=stream), 2, 1, stream)
+        fwd_ms = time_steps(lambda: p64.fwd(tt, tp, a2, b2, stream=stream), 2, 1, stream)
+        err = max(float((a2 - a).abs().max() / a.abs().max()), float((b2 - b).abs().max() / b.abs().max()))
+        row["fp64_one_field"] = {"adj_ms": adj_ms, "fwd_ms": fwd_ms, "roundtrip_max_rel": err}
+        p64.close()
+        out["L%d" % L] = row
+    return out
 
 
 def measure_forms(L, B, a, b, split_value, fp64_peak):
@@ -318,6 +398,7 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     forms["cg_route_L511_one_field"] = measure_cg_route(511, stream)
     forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
     forms["split_L1000_B%d" % B] = measure_split_other_length(1000, B, stream)
+    forms["table3_degrees"] = measure_table3(stream, B)
     return forms
 
 
@@ -806,8 +887,9 @@ def main():
     # roofline: every kernel's algorithmic work (favest_kernel_work) per launch over its
     # CUDA-event duration, against the peak of the unit that binds it; the line's
     # roofline object is the kernel with the largest share of the timed region
-    fp64_peak, fp32_peak = api.favest_probe_peaks()
-    kernels, roofline = kernel_rooflines(plan, prof, fp64_peak, fp32_peak, L, B)
+    fp64_probe, fp32_probe = api.favest_probe_peaks()
+    kernels, roofline = kernel_rooflines(plan, prof, fp64_probe, fp32_probe, L, B)
+    fp64_peak, fp32_peak = alu_peaks()[:2]
 
     # end-to-end through the public API with host buffers (pinned), per step:
     # H2D of the coefficients, adjoint + forward, D2H of the recovered coefficients
@@ -924,6 +1006,7 @@ def main():
             "roofline": roofline, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "errors": errors, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
+            "fp64_probe_tflops": fp64_probe, "fp32_probe_tflops": fp32_probe,
             "forms": forms,
         }
         print(json.dumps(rec), flush=True)

@@ -388,6 +388,19 @@ int favest_profile_read(favest_plan plan, int max_kernels, char *names, double *
 int favest_selftest_wait_timeout(favest_plan plan, unsigned poll_limit, double *elapsed_ms);
 
 /*
+ * Allocation-failure test hook (no counterpart in the paper).  Every device allocation that
+ * plan, batch and scattered-point creation make is counted; favest_debug_fail_alloc(k)
+ * resets the count and makes the k-th allocation from now (k = 0 the first) fail as if the
+ * device were out of memory, or disarms the hook (k = -1).  A creation call that meets the
+ * failure returns FAVEST_ENOMEM after releasing everything it had allocated.
+ * favest_debug_alloc_count() returns the allocations counted since the last
+ * favest_debug_fail_alloc call.  FAVEST_EINVAL for k < -1.  Process-wide; not for use while
+ * other threads create plans.
+ */
+int favest_debug_fail_alloc(long long k);
+long long favest_debug_alloc_count(void);
+
+/*
  * Algorithmic work of one launch of a kernel of this plan, by the name that
  * favest_profile_read reports: *bytes = the minimum DRAM traffic (every operand read
  * once, every result written once, no re-reads, no padding), *flops = arithmetic

@@ -110,6 +110,8 @@ def lib(build_if_missing=False):
             L.favest_fwd_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_adj_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_cg_stability.argtypes = [i, i, d, d, d, vp]
+            L.favest_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+            L.favest_debug_alloc_count.restype = ctypes.c_longlong
             L.favest_scatter_create.argtypes = [i, i, i, d, d, ctypes.POINTER(vp)]
             L.favest_scatter_fwd.argtypes = [vp, vp, vp, vp, vp]
             L.favest_scatter_adj.argtypes = [vp, vp, vp, vp, vp]

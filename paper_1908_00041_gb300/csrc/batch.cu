@@ -69,7 +69,7 @@ template <typename T>
 cudaError_t upload_vec(T **d, const std::vector<T> &h)
 {
     if (h.empty()) return cudaSuccess;
-    cudaError_t e = cudaMalloc((void **)d, h.size() * sizeof(T));
+    cudaError_t e = plan_malloc((void **)d, h.size() * sizeof(T));
     if (e != cudaSuccess) return e;
     return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
@@ -388,7 +388,7 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
         bp->n_items_a = (int)ita.size();
         if (upload_vec(&bp->d_gg, gg) != cudaSuccess || upload_vec(&bp->d_items_f, itf) != cudaSuccess ||
             upload_vec(&bp->d_items_a, ita) != cudaSuccess ||
-            cudaMalloc((void **)&bp->d_status, sizeof(int)) != cudaSuccess ||
+            plan_malloc((void **)&bp->d_status, sizeof(int)) != cudaSuccess ||
             cudaMemset(bp->d_status, 0, sizeof(int)) != cudaSuccess)
             st = FAVEST_ENOMEM;
     }

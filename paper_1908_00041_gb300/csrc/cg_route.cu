@@ -376,7 +376,7 @@ extern "C" int favest_cg_stability(int L, int npts, const double *cos_theta, dou
     const int K = L * L + 2 * L;
     const size_t nz = (size_t)npts, bytes = (nz + 4 * (size_t)K + 4) * sizeof(double);
     double *d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    if (plan_malloc((void **)&d, bytes) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <new>
@@ -92,7 +93,7 @@ cudaError_t dalloc(T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) return cudaSuccess;
-    return cudaMalloc((void **)p, count * sizeof(T));
+    return plan_malloc((void **)p, count * sizeof(T));
 }
 
 template <typename T>
@@ -159,7 +160,14 @@ int build_bluestein(Plan &p)
     int lg = 1;
     while ((1 << lg) < 2 * R - 1) ++lg;
     const int M = 1 << lg;
-    const size_t ring_bytes = (size_t)32 * p.nphi, scratch = (size_t)8 * M;
+    // butterflies per round: at least one, more while the scratch stays within 32 KB (or one
+    // butterfly's M points) and the butterflies of a CTA's 4 rings last
+    const size_t ring_bytes = (size_t)32 * p.nphi;
+    const int nbf4 = 4 * (p.nphi / R);
+    int P = (int)(32768 / ((size_t)8 * M));
+    if (P < 1) P = 1;
+    if (P > nbf4) P = nbf4;
+    const size_t scratch = (size_t)8 * M * P;
     if (ring_bytes + (scratch > 24576 ? scratch : 24576) > 227 * 1024) return FAVEST_EUNSUPPORTED;
     const long double pi = 3.141592653589793238462643383279502884L;
     std::vector<float2> chirp(R), spec(M), twm(M / 2);
@@ -188,8 +196,12 @@ int build_bluestein(Plan &p)
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     p.fft.blue_R = R;
     p.fft.blue_log2m = lg;
+    p.fft.blue_P = P;
     return FAVEST_OK;
 }
+
+std::atomic<long long> g_alloc_calls{0};
+std::atomic<long long> g_alloc_fail_at{-1};
 
 int build_tables(Plan &p)
 {
@@ -561,11 +573,11 @@ int alloc_workspace_bf16(Plan &p)
     const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 96;
     const size_t q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
     const size_t s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
-    if (cudaMalloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || cudaMalloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
-        cudaMalloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
-        cudaMalloc(&p.d_gb, (size_t)gsz) != cudaSuccess || cudaMalloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
-        cudaMalloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
-        cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+    if (plan_malloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || plan_malloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
+        plan_malloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
+        plan_malloc(&p.d_gb, (size_t)gsz) != cudaSuccess || plan_malloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
+        plan_malloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
+        plan_malloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
@@ -612,9 +624,9 @@ int alloc_workspace(Plan &p)
     size_t qbytes = (size_t)p.ntab * p.ncol * sizeof(double2);
     // inverse DFT rows: 2 per group of 4 columns, or 2 per real field (2 fields per group)
     size_t gbytes = p.scattered ? 0 : (size_t)(p.real ? p.ncol : p.ncol / 2) * p.nlat * p.nphi * sizeof(double2);
-    if ((fbytes && cudaMalloc(&p.d_F, fbytes) != cudaSuccess) || cudaMalloc(&p.d_Q, qbytes) != cudaSuccess ||
-        (gbytes && cudaMalloc(&p.d_G, gbytes) != cudaSuccess) ||
-        cudaMalloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+    if ((fbytes && plan_malloc(&p.d_F, fbytes) != cudaSuccess) || plan_malloc(&p.d_Q, qbytes) != cudaSuccess ||
+        (gbytes && plan_malloc(&p.d_G, gbytes) != cudaSuccess) ||
+        plan_malloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
@@ -695,6 +707,17 @@ const char *favest_strerror(int status)
     return kErrStr[i];
 }
 
+int favest_debug_fail_alloc(long long k)
+{
+    if (k < -1) return FAVEST_EINVAL;
+    g_alloc_fail_at.store(-1);
+    g_alloc_calls.store(0);
+    g_alloc_fail_at.store(k);
+    return FAVEST_OK;
+}
+
+long long favest_debug_alloc_count(void) { return g_alloc_calls.load(); }
+
 int favest_gl_grid(int nlat, double *x, double *w)
 {
     if (nlat < 1 || !x || !w) return FAVEST_EINVAL;
@@ -704,6 +727,16 @@ int favest_gl_grid(int nlat, double *x, double *w)
 }  // extern "C"
 
 namespace favest {
+
+cudaError_t plan_malloc(void **p, size_t bytes)
+{
+    const long long k = g_alloc_calls.fetch_add(1);
+    if (k == g_alloc_fail_at.load()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
                          const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route)

@@ -42,6 +42,7 @@ struct FftPlan {
     // FP32 DFT stage of a prime radix above the in-register and per-warp forms (Bluestein's
     // chirp transform, a cyclic convolution of power-of-two length M >= 2R - 1): 0 if none
     int blue_R = 0, blue_log2m = 0;
+    int blue_P = 0;                 // butterflies per round: the scratch holds blue_P * M points
     float2 *blue_chirp = nullptr;   // [R] exp(-i pi t^2 / R), t^2 reduced mod 2R exactly
     float2 *blue_spec = nullptr;    // [M] DFT_M of the conjugate chirp, / M, bit-reversed order
     float2 *blue_tw = nullptr;      // [M/2] exp(-2 pi i k / M)
@@ -224,6 +225,11 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
 cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cudaStream_t s);
 int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
+
+// Every device allocation a plan (or batch, or scattered-point plan) makes goes through
+// plan_malloc: it counts the calls and fails the one favest_debug_fail_alloc chose, so that
+// tests can drive each allocation's error path without exhausting the device.
+cudaError_t plan_malloc(void **p, size_t bytes);
 
 int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
                          const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route = 0);

@@ -10,7 +10,7 @@ struct RadixPlanArg {
     int n;
     int nstages;
     int radix[kMaxRadixStages];
-    int blue_R, blue_log2m;             // see FftPlan
+    int blue_R, blue_log2m, blue_P;     // see FftPlan
     const float2 *blue_chirp, *blue_spec, *blue_tw;
 };
 
@@ -22,6 +22,7 @@ inline RadixPlanArg make_radix_arg(const FftPlan &f)
     for (int i = 0; i < kMaxRadixStages; ++i) r.radix[i] = i < f.nstages ? f.radix[i] : 1;
     r.blue_R = f.blue_R;
     r.blue_log2m = f.blue_log2m;
+    r.blue_P = f.blue_P;
     r.blue_chirp = f.blue_chirp;
     r.blue_spec = f.blue_spec;
     r.blue_tw = f.blue_tw;

@@ -232,6 +232,7 @@ struct GemmSmem {
     unsigned char b[kStages][kPieces * kChunkK * N * 2];
     uint64_t full[kStages], empty[kStages];
     uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
+    uint64_t drain;            // abort path: completion of the MMA warp's last issued MMAs
     uint32_t tmem_base;
     int abort;
 };
@@ -249,12 +250,13 @@ __device__ __forceinline__ void set_status(int *status, int code)
 // Polls of an mbarrier before a wait gives up (about a second).
 constexpr uint32_t kWaitPolls = 1u << 26;
 
-// Wait that also gives up after `limit` polls, or when another role aborted.
+// Wait that also gives up after `limit` polls, or when another role aborted (abort may be
+// null: the drain waits of the abort path itself, which only the limit ends).
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort, uint32_t limit)
 {
     for (uint32_t i = 0; i < limit; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023) == 1023 && *abort) return false;
+        if ((i & 1023) == 1023 && abort && *abort) return false;
     }
     return false;
 }
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
         tc::mbar_init(&S.dmain_empty, kEpiWarps);
         tc::mbar_init(&S.dcorr_full, 1);
         tc::mbar_init(&S.dcorr_empty, kEpiWarps);
+        tc::mbar_init(&S.drain, 1);
         S.abort = 0;
         tc::mbar_fence_init();
     }
@@ -296,6 +299,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
         // waits must run out, report FAVEST_ETIMEOUT and return)
         if (lane == 0 && !skip_loads) {
             uint32_t phase = 0;                     // bit s: parity of stage s's next use
+            uint32_t issued = 0;                    // bit s: stage s has been loaded at least once
             int stage = 0;
             for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const TcItem I = items[it];
@@ -321,9 +325,17 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                                         &S.full[stage]);
                     }
                     phase ^= 1u << stage;
+                    issued |= 1u << stage;
                     stage = (stage + 1) % kStages;
                 }
             }
+            // On abort, loads this warp issued may still be in flight: wait (bounded) until
+            // each stage's last load has landed, so that no copy writes this CTA's shared
+            // memory after the CTA has exited.  A load completes on its own; only a broken
+            // barrier could make this wait run out, and then nothing better can be done.
+            if (*abort)
+                for (int s = 0; s < kStages; ++s)
+                    if (issued & (1u << s)) wait_or_abort(&S.full[s], ((phase >> s) & 1) ^ 1, nullptr, poll_limit);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -389,6 +401,12 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                 if (*abort) break;
                 tc::mma_commit(&S.dcorr_full);
                 corr_use++;
+            }
+            // On abort, MMAs issued before it may still be running: wait (bounded) for all of
+            // them before the TMEM they write is released below.
+            if (*abort) {
+                tc::mma_commit(&S.drain);
+                wait_or_abort(&S.drain, 0, nullptr, poll_limit);
             }
         }
     } else {

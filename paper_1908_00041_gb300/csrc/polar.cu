@@ -312,7 +312,7 @@ int build_polar_tables(Plan &p)
             }
         }
     }
-    if (cudaMalloc((void **)&p.d_pol, tab.size() * sizeof(float2)) != cudaSuccess) {
+    if (plan_malloc((void **)&p.d_pol, tab.size() * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }

@@ -355,7 +355,7 @@ int favest_scatter_create(int L, int batch, int npts, const double *X, const dou
     const size_t adj_part = h->nsplit > 1 ? (size_t)h->nsplit * p.nscal * npts : 0;
     const size_t npart = fwd_part > adj_part ? fwd_part : adj_part;
     auto up = [&](double **d, const std::vector<double> &v) {
-        if (cudaMalloc(d, v.size() * sizeof(double)) != cudaSuccess) return FAVEST_ENOMEM;
+        if (plan_malloc((void **)d, v.size() * sizeof(double)) != cudaSuccess) return FAVEST_ENOMEM;
         return cudaMemcpy(*d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess
                    ? FAVEST_OK
                    : FAVEST_ECUDA;
@@ -365,7 +365,7 @@ int favest_scatter_create(int L, int batch, int npts, const double *X, const dou
         scatter_free(h);
         return st;
     }
-    if (npart && cudaMalloc(&h->d_part, npart * sizeof(double2)) != cudaSuccess) {
+    if (npart && plan_malloc((void **)&h->d_part, npart * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
         scatter_free(h);
         return FAVEST_ENOMEM;

@@ -118,3 +118,14 @@ def test_cg_stability_rejects_bad_arguments(lib):
     assert call(5, ok, ratios=False) == api.FAVEST_EINVAL
     for bad in (1.0, -1.0, 1.5, np.nan, np.inf):
         assert call(5, np.array([0.2, bad])) == api.FAVEST_EINVAL
+
+
+def test_alloc_failure_hook_host_side(lib):
+    """The allocation-failure hook's host logic (no device needed): arming resets the count,
+    bad arguments are refused."""
+    L = api.lib()
+    assert L.favest_debug_fail_alloc(-2) == api.FAVEST_EINVAL
+    assert L.favest_debug_fail_alloc(3) == api.FAVEST_OK
+    assert L.favest_debug_alloc_count() == 0
+    assert L.favest_debug_fail_alloc(-1) == api.FAVEST_OK
+    assert L.favest_debug_alloc_count() == 0

@@ -46,8 +46,11 @@ def test_bench_json_line_small_workload():
     assert rec["gpu_launches"] == rec["steps"] * 8
     for form in ("fp64_same_workload", "fp64_L16_one_field", "fp64_L511_one_field", "ragged_batch",
                  "real_fields_B8", "field_a_tables", "cg_route_L511_one_field", "fp64_real_vs_complex_L511_B8",
-                 "split_L1000_B8", "cg_stability_ratios"):
+                 "split_L1000_B8", "cg_stability_ratios", "table3_degrees"):
         assert form in rec["forms"], form
+    for L in (250, 500, 750, 1000, 1250, 1500, 1750, 2000, 2250):
+        row = rec["forms"]["table3_degrees"]["L%d" % L]
+        assert row["split_batch"]["roundtrip_max_rel"] < 1e-6 and row["fp64_one_field"]["roundtrip_max_rel"] < 1e-12
     assert rec["forms"]["split_L1000_B8"]["generator_shape"][2] in (1, 2)
     st = rec["forms"]["cg_stability_ratios"]["series"]["L10_N100000"]
     assert 0 < st["r_hat"] <= 0.7072 and 0 < st["r_tilde"] <= 0.7072 and st["kappa_tilde"] <= 2.4495
