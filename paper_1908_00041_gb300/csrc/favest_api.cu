@@ -142,61 +142,68 @@ void host_fft_pow2(std::vector<double2> &v, int lg)
     }
 }
 
-// Tables of the FP32 DFT's Bluestein stage for a prime radix above the direct forms (128):
-// chirp c_t = exp(-i pi t^2 / R) from the exactly reduced t^2 mod 2R, the spectrum of its
-// conjugate zero-padded to M = 2^lg >= 2R - 1 (FP64, scaled by 1/M, stored bit-reversed for
-// the device's decimation in frequency), and the M-point twiddles.  The scratch of M points
-// must fit beside the DFT buffer of 4 rings in one CTA's shared memory.
+// Tables of the FP32 DFT's Bluestein stages, one per prime radix R >= 17 (the radices the
+// in-register butterflies do not cover): chirp c_t = exp(-i pi t^2 / R) from the exactly
+// reduced t^2 mod 2R, the spectrum of its conjugate zero-padded to M = 2^lg >= 2R - 1 (FP64,
+// scaled by 1/M; natural order for the radix-16 engine, M <= 4096, bit-reversed for the radix-2
+// passes used at M = 8192), and the M-point twiddles.  P butterflies of a stage run per round
+// in a scratch of up to 32 KB (at least one butterfly), which with the DFT buffer of 4 rings
+// must fit one CTA's shared memory.
 int build_bluestein(Plan &p)
 {
-    int R = 0;
-    for (int st = 0; st < p.fft.nstages; ++st) {
-        const int r = p.fft.radix[st];
-        if (r <= 128) continue;
-        if (R != 0 && r != R) return FAVEST_EUNSUPPORTED;     // two large primes (n > 5120)
-        R = r;
-    }
-    if (R == 0) return FAVEST_OK;
-    int lg = 1;
-    while ((1 << lg) < 2 * R - 1) ++lg;
-    const int M = 1 << lg;
-    // butterflies per round: at least one, more while the scratch stays within 32 KB (or one
-    // butterfly's M points) and the butterflies of a CTA's 4 rings last
-    const size_t ring_bytes = (size_t)32 * p.nphi;
-    const int nbf4 = 4 * (p.nphi / R);
-    int P = (int)(32768 / ((size_t)8 * M));
-    if (P < 1) P = 1;
-    if (P > nbf4) P = nbf4;
-    const size_t scratch = (size_t)8 * M * P;
-    if (ring_bytes + (scratch > 24576 ? scratch : 24576) > 227 * 1024) return FAVEST_EUNSUPPORTED;
     const long double pi = 3.141592653589793238462643383279502884L;
-    std::vector<float2> chirp(R), spec(M), twm(M / 2);
-    std::vector<double2> b(M, make_double2(0.0, 0.0));
-    for (int t = 0; t < R; ++t) {
-        const long long q = ((long long)t * t) % (2LL * R);
-        const long double ang = -pi * (long double)q / (long double)R;
-        const double c = (double)cosl(ang), sn = (double)sinl(ang);
-        chirp[t] = make_float2((float)c, (float)sn);
-        b[t] = make_double2(c, -sn);                          // conj(c_t)
-        if (t > 0) b[M - t] = make_double2(c, -sn);
+    std::vector<float2> chirp, spec, twm;
+    size_t scratch = 0;
+    for (int st = 0; st < p.fft.nstages; ++st) {
+        const int R = p.fft.radix[st];
+        p.fft.blue_lg[st] = 0;
+        if (R < 17) continue;
+        int lg = 1;
+        while ((1 << lg) < 2 * R - 1) ++lg;
+        if (lg < 5) lg = 5;
+        if (lg > 13) return FAVEST_EUNSUPPORTED;
+        const int M = 1 << lg;
+        const size_t pts = lg <= 12 ? (size_t)M + M / 16 : (size_t)M;   // padded for the engine
+        const int nbf4 = 4 * (p.nphi / R);
+        int P = (int)(32768 / (8 * pts));
+        if (P < 1) P = 1;
+        if (P > nbf4) P = nbf4;
+        scratch = std::max(scratch, (size_t)8 * pts * P);
+        p.fft.blue_lg[st] = lg;
+        p.fft.blue_P[st] = P;
+        p.fft.blue_off[st] = (int)chirp.size();
+        p.fft.blue_moff[st] = (int)spec.size();
+        std::vector<double2> b(M, make_double2(0.0, 0.0));
+        for (int t = 0; t < R; ++t) {
+            const long long q = ((long long)t * t) % (2LL * R);
+            const long double ang = -pi * (long double)q / (long double)R;
+            const double c = (double)cosl(ang), sn = (double)sinl(ang);
+            chirp.push_back(make_float2((float)c, (float)sn));
+            b[t] = make_double2(c, -sn);                          // conj(c_t)
+            if (t > 0) b[M - t] = make_double2(c, -sn);
+        }
+        host_fft_pow2(b, lg);
+        for (int i = 0; i < M; ++i) {
+            int r = i;
+            if (lg > 12) {
+                r = 0;
+                for (int k = 0; k < lg; ++k) r |= ((i >> k) & 1) << (lg - 1 - k);
+            }
+            spec.push_back(make_float2((float)(b[r].x / M), (float)(b[r].y / M)));
+        }
+        for (int k = 0; k < M; ++k) {
+            const long double ang = -2.0L * pi * k / M;
+            twm.push_back(make_float2((float)cosl(ang), (float)sinl(ang)));
+        }
     }
-    host_fft_pow2(b, lg);
-    for (int i = 0; i < M; ++i) {
-        int r = 0;
-        for (int k = 0; k < lg; ++k) r |= ((i >> k) & 1) << (lg - 1 - k);
-        spec[i] = make_float2((float)(b[r].x / M), (float)(b[r].y / M));
-    }
-    for (int k = 0; k < M / 2; ++k) {
-        const long double ang = -2.0L * pi * k / M;
-        twm[k] = make_float2((float)cosl(ang), (float)sinl(ang));
-    }
+    if (chirp.empty()) return FAVEST_OK;
+    const size_t ring_bytes = (size_t)32 * p.nphi;
+    if (ring_bytes + std::max(scratch, (size_t)24576) > 227 * 1024) return FAVEST_EUNSUPPORTED;
     cudaError_t e;
     if ((e = upload(&p.fft.blue_chirp, chirp)) || (e = upload(&p.fft.blue_spec, spec)) ||
         (e = upload(&p.fft.blue_tw, twm)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
-    p.fft.blue_R = R;
-    p.fft.blue_log2m = lg;
-    p.fft.blue_P = P;
+    p.fft.blue_scratch = scratch;
     return FAVEST_OK;
 }
 
@@ -301,7 +308,7 @@ int build_tables(Plan &p)
     // The split path transforms power-of-two lengths 2^6..2^11 with its own radix-16
     // engine (natural order in and out); other lengths use the mixed-radix list and perm.
     p.fft_log2n = 0;
-    if (p.precision == FAVEST_BF16X6 && n >= 64 && n <= 2048 && (n & (n - 1)) == 0)
+    if (p.precision == FAVEST_BF16X6 && n >= 64 && n <= 4096 && (n & (n - 1)) == 0)
         while ((1 << p.fft_log2n) < n) ++p.fft_log2n;
     std::vector<int> perm(n);
     for (int m = 0; m < n; ++m) {

@@ -39,13 +39,18 @@ struct FftPlan {
     int radix[kMaxRadixStages];
     double2 *tw64 = nullptr;   // device, e^{-2 pi i k / n}, k = 0..n-1
     float2 *tw32 = nullptr;    // device, same rounded to float
-    // FP32 DFT stage of a prime radix above the in-register and per-warp forms (Bluestein's
-    // chirp transform, a cyclic convolution of power-of-two length M >= 2R - 1): 0 if none
-    int blue_R = 0, blue_log2m = 0;
-    int blue_P = 0;                 // butterflies per round: the scratch holds blue_P * M points
-    float2 *blue_chirp = nullptr;   // [R] exp(-i pi t^2 / R), t^2 reduced mod 2R exactly
-    float2 *blue_spec = nullptr;    // [M] DFT_M of the conjugate chirp, / M, bit-reversed order
-    float2 *blue_tw = nullptr;      // [M/2] exp(-2 pi i k / M)
+    // FP32 DFT stages of prime radices R >= 17 (above the in-register forms) run Bluestein's
+    // chirp transform, a cyclic convolution of power-of-two length M = 2^blue_lg >= 2R - 1;
+    // per stage st (blue_lg[st] = 0: not such a stage):
+    int blue_lg[kMaxRadixStages] = {0};
+    int blue_P[kMaxRadixStages] = {0};     // butterflies per round
+    int blue_off[kMaxRadixStages] = {0};   // stage's offset into the chirp table (points)
+    int blue_moff[kMaxRadixStages] = {0};  // stage's offset into the spectrum / twiddle tables
+    size_t blue_scratch = 0;               // bytes of shared-memory scratch the largest stage needs
+    float2 *blue_chirp = nullptr;   // [R] per stage: exp(-i pi t^2 / R), t^2 reduced mod 2R exactly
+    float2 *blue_spec = nullptr;    // [M] per stage: DFT_M of the conjugate chirp / M (natural
+                                    //     order; bit-reversed for M = 8192)
+    float2 *blue_tw = nullptr;      // [M] per stage: exp(-2 pi i k / M)
 };
 
 constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk

@@ -35,8 +35,6 @@ __device__ __forceinline__ float2 twf(const float2 *__restrict__ tw, int q)
     return INV ? make_float2(t.x, -t.y) : t;
 }
 
-constexpr int kMaxInlineRadix = 128;   // largest odd prime radix of the direct forms (Bluestein above)
-
 // In-place decimation-in-frequency FFT of `nr` rings of n points stored back to back.
 // Stage s (radix R, block length Nb, h = Nb/R): for every block and k < h the R points
 // x[k + t h] are replaced by their R-point DFT, output q scaled by w_Nb^{q k}.  Frequency m
@@ -44,13 +42,9 @@ constexpr int kMaxInlineRadix = 128;   // largest odd prime radix of the direct 
 // butterfly reads and writes the same addresses, and the butterflies of a stage touch
 // disjoint positions, so one buffer suffices.
 // Radices 2 and 4, and the odd primes 3..13: one thread per butterfly, its R points in
-// registers and the R roots of unity w_R^j loaded once per stage.  Larger primes:
-// butterflies are dealt out to warps, one output (q) per lane (several per lane for
-// R > 32); each output reads its R inputs from shared memory, its twiddle exponent r q n/R
-// advancing by one addition per term, and the warp writes its outputs back after all of its
-// lanes have read (no block-wide barrier inside the stage).  The output twiddle exponent
-// q k n/Nb is below n (q < R, k < Nb/R): no reduction is needed.
-constexpr int kMaxOddOut = kMaxInlineRadix / 32;   // outputs per lane for R > 32
+// registers and the R roots of unity w_R^j loaded once per stage.  Primes from 17 up: a
+// Bluestein convolution on the radix-16 engine (dif_stage_bluestein, after the engine).
+// The output twiddle exponent q k n/Nb is below n (q < R, k < Nb/R): no reduction is needed.
 
 // Butterfly index -> (ring, block, k) without integer division: q = floor(x / d) for
 // 0 <= x < 2^15 and 1 <= d <= 4096 as the high word of x * m, m = floor((2^32 - 1) / d) + 1
@@ -111,182 +105,7 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void dif_stage_odd(float2 *x, const float2 *__restrict__ tw, int n, int R, int Nb,
-                                              int nr)
-{
-    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int per = R <= 32 ? 32 / R : 1;            // butterflies per warp pass
-    const int nout = (R + 31) / 32;                    // outputs per lane
-    const int lb = R <= 32 ? lane / R : 0, lq = R <= 32 ? lane % R : lane;
-    const bool lane_ok = R > 32 || lane < per * R;
-    const int total = nbf * nr;
-    const Recip rn = recip(nbf), rh = recip(h);
-    for (int b0 = warp * per; b0 < total; b0 += nw * per) {
-        float2 res[kMaxOddOut];
-        int pos[kMaxOddOut];
-        const int bi = b0 + lb;
-        const int ring = rdiv(bi, rn), i = bi - ring * nbf;
-        const int blk = rdiv(i, rh), k = i - blk * h;
-        const int base = ring * n + blk * Nb + k;
-#pragma unroll
-        for (int u = 0; u < kMaxOddOut; ++u) {
-            pos[u] = -1;
-            const int q = lq + 32 * u;
-            if (u >= nout || !lane_ok || q >= R || bi >= total) continue;
-            float2 acc = make_float2(0.f, 0.f);
-            const int dq = q * rstep;                    // < n
-            int ti = 0;
-            for (int r = 0; r < R; ++r) {
-                acc = caddf(acc, cmulf(x[base + r * h], twf<INV>(tw, ti)));
-                ti += dq;
-                if (ti >= n) ti -= n;
-            }
-            res[u] = cmulf(acc, twf<INV>(tw, q * k * ts));
-            pos[u] = base + q * h;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < kMaxOddOut; ++u)
-            if (pos[u] >= 0) x[pos[u]] = res[u];
-        __syncwarp();
-    }
-}
-
-// Prime radix R above kMaxInlineRadix: Bluestein's identity q t = (q^2 + t^2 - (q - t)^2) / 2
-// turns each R-point DFT into a cyclic convolution,
-//   out_q = c_q sum_t (x_t c_t) conj(c_{q-t}),   c_t = exp(-i pi t^2 / R),
-// done at power-of-two length M >= 2R - 1 in the CTA's scratch: a radix-2 decimation in
-// frequency (natural order in, bit-reversed out), the product with the precomputed spectrum
-// of conj(c) (stored bit-reversed, scaled by 1/M), a radix-2 decimation in time with
-// conjugate twiddles (bit-reversed in, natural out).  The inverse transform is the
-// conjugate of the forward one of the conjugated input.  The CTA's threads take the P
-// butterflies of a round together (P convolutions of M points side by side in the scratch);
-// a round reads all its points before any is rewritten, and the butterflies of a stage
-// touch disjoint positions.
-// Error in FP32 about 2e-7 of the largest output for R up to 2251 (checked against a library
-// FFT on the host before the kernel was written).
-template <bool INV>
-__device__ void dif_stage_bluestein(float2 *x, const float2 *__restrict__ tw, int n, int R, int Nb, int nr,
-                                    const RadixPlanArg &rp, float2 *sc)
-{
-    const int h = Nb / R, ts = n / Nb, nbf = n / R, total = nbf * nr;
-    const int lg = rp.blue_log2m, M = 1 << lg, hm = M >> 1;
-    const int P = rp.blue_P;                            // butterflies per round (scratch = P M points)
-    const float2 *__restrict__ ch = rp.blue_chirp;
-    const float2 *__restrict__ sp = rp.blue_spec;
-    const float2 *__restrict__ tm = rp.blue_tw;
-    auto base_of = [&](int bi) {
-        const int ring = bi / nbf, i = bi - ring * nbf;
-        const int blk = i / h, k = i - blk * h;
-        return ring * n + blk * Nb + k;
-    };
-    for (int b0 = 0; b0 < total; b0 += P) {
-        const int np = total - b0 < P ? total - b0 : P;
-        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x) {
-            const int bb = idx >> lg, t = idx & (M - 1);
-            float2 v = make_float2(0.f, 0.f);
-            if (t < R) {
-                float2 xv = x[base_of(b0 + bb) + t * h];
-                if (INV) xv.y = -xv.y;
-                v = cmulf(xv, __ldg(ch + t));
-            }
-            sc[idx] = v;
-        }
-        __syncthreads();
-        for (int lgs = lg - 1; lgs >= 0; --lgs) {          // half-block s = 2^lgs
-            const int s = 1 << lgs;
-            for (int u = threadIdx.x; u < np * hm; u += blockDim.x) {
-                const int uu = u & (hm - 1), j = uu & (s - 1);
-                const int i0 = ((u >> (lg - 1)) << lg) + ((uu >> lgs) << (lgs + 1)) + j;
-                const float2 a = sc[i0], b = sc[i0 + s];
-                sc[i0] = caddf(a, b);
-                sc[i0 + s] = cmulf(csubf(a, b), __ldg(tm + (j << (lg - 1 - lgs))));
-            }
-            __syncthreads();
-        }
-        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x)
-            sc[idx] = cmulf(sc[idx], __ldg(sp + (idx & (M - 1))));
-        __syncthreads();
-        for (int lgs = 0; lgs < lg; ++lgs) {
-            const int s = 1 << lgs;
-            for (int u = threadIdx.x; u < np * hm; u += blockDim.x) {
-                const int uu = u & (hm - 1), j = uu & (s - 1);
-                const int i0 = ((u >> (lg - 1)) << lg) + ((uu >> lgs) << (lgs + 1)) + j;
-                float2 w = __ldg(tm + (j << (lg - 1 - lgs)));
-                w.y = -w.y;
-                const float2 a = sc[i0], b = cmulf(sc[i0 + s], w);
-                sc[i0] = caddf(a, b);
-                sc[i0 + s] = csubf(a, b);
-            }
-            __syncthreads();
-        }
-        for (int idx = threadIdx.x; idx < np * R; idx += blockDim.x) {
-            const int bb = idx / R, q = idx - bb * R;
-            const int bi = b0 + bb;
-            const int k = (bi - (bi / nbf) * nbf) % h;
-            float2 v = cmulf(sc[(bb << lg) + q], __ldg(ch + q));
-            if (INV) v.y = -v.y;
-            x[base_of(bi) + q * h] = cmulf(v, twf<INV>(tw, q * k * ts));
-        }
-        __syncthreads();
-    }
-}
-
-// sc: scratch of blue_P 2^blue_log2m points when the plan has a Bluestein radix (else unused)
-template <bool INV>
-__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc)
-{
-    const int n = rp.n;
-    int Nb = n;
-    for (int st = 0; st < rp.nstages; ++st) {
-        const int R = rp.radix[st];
-        const int h = Nb / R;
-        const int ts = n / Nb;
-        const int nbf = n / R;
-        if (R == 3) {
-            dif_stage_small<3, INV>(x, tw, n, Nb, nr);
-        } else if (R == 5) {
-            dif_stage_small<5, INV>(x, tw, n, Nb, nr);
-        } else if (R == 7) {
-            dif_stage_small<7, INV>(x, tw, n, Nb, nr);
-        } else if (R == 11) {
-            dif_stage_small<11, INV>(x, tw, n, Nb, nr);
-        } else if (R == 13) {
-            dif_stage_small<13, INV>(x, tw, n, Nb, nr);
-        } else if (R == rp.blue_R) {
-            dif_stage_bluestein<INV>(x, tw, n, R, Nb, nr, rp, sc);
-        } else if (R != 2 && R != 4) {
-            dif_stage_odd<INV>(x, tw, n, R, Nb, nr);
-        } else {
-            const Recip rn = recip(nbf), rh = recip(h);
-            for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
-                const int ring = rdiv(t, rn), i = t - ring * nbf;
-                const int blk = rdiv(i, rh), k = i - blk * h;
-                float2 *xr = x + ring * n + blk * Nb + k;
-                if (R == 4) {
-                    const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
-                    const float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
-                    const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
-                    const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-                    xr[0] = caddf(s02, s13);
-                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
-                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
-                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
-                } else {
-                    const float2 v0 = xr[0], v1 = xr[h];
-                    xr[0] = caddf(v0, v1);
-                    xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
-                }
-            }
-        }
-        __syncthreads();
-        Nb = h;
-    }
-}
-
-// Power-of-two lengths n = 2^LOG2N (64..2048): in-place decimation in frequency with
+// Power-of-two lengths n = 2^LOG2N (64..4096): in-place decimation in frequency with
 // radix-16 butterflies held in registers, then one last radix-2^r stage (r = LOG2N mod 4,
 // or 16 when that is 0).  The last stage has no twiddles and writes its outputs back in
 // natural frequency order, so no digit-reversal table is needed on either side.  All
@@ -401,6 +220,207 @@ __device__ __forceinline__ void dif_last(float2 *x, int nr)
     }
 }
 
+// Bluestein stage of a prime radix R >= 17 (stage st of the plan): Bluestein's identity
+// q t = (q^2 + t^2 - (q - t)^2) / 2 turns each R-point DFT into a cyclic convolution,
+//   out_q = c_q sum_t (x_t c_t) conj(c_{q-t}),   c_t = exp(-i pi t^2 / R),
+// done at power-of-two length M >= 2R - 1 in the CTA's shared-memory scratch, P butterflies
+// side by side per round: M <= 4096 runs both FFTs on the radix-16 engine above (natural order
+// in and out, padded layout), the product with the precomputed spectrum of conj(c) (scaled by
+// 1/M) between them; M = 8192 (R > 2048) uses radix-2 passes, a decimation in frequency
+// (natural in, bit-reversed out), the spectrum stored bit-reversed, and a decimation in time
+// with conjugate twiddles (bit-reversed in, natural out).  The inverse transform is the
+// conjugate of the forward one of the conjugated input.  A round reads all its points before
+// any is rewritten, and the butterflies of a stage touch disjoint positions.  FP32 error of the
+// stage about 2e-7 of its largest output for R up to 2251 (checked on the host against a
+// library FFT before the kernel was written).
+template <int LG, bool INV>
+__device__ __forceinline__ void fft_p2_smem(float2 *x, const float2 *__restrict__ tw, int nr)
+{
+    constexpr int n16 = LG / 4, rem = LG % 4, nfull = rem ? n16 : n16 - 1;
+    static_assert(nfull >= 1 && nfull <= 2, "radix-16 engine lengths 2^5 .. 2^12");
+    dif_stage16<LG, (1 << LG), INV>(x, tw, nr);
+    if constexpr (nfull >= 2) dif_stage16<LG, (1 << LG) / 16, INV>(x, tw, nr);
+    dif_last<LG, (rem ? (1 << rem) : 16), INV>(x, nr);
+}
+
+struct BlueStage {
+    int n, R, Nb, nr, P;
+    const float2 *ch, *sp, *tm;
+    __device__ __forceinline__ int base_of(int bi) const
+    {
+        const int h = Nb / R, nbf = n / R;
+        const int ring = bi / nbf, i = bi - ring * nbf;
+        const int blk = i / h, k = i - blk * h;
+        return ring * n + blk * Nb + k;
+    }
+};
+
+template <int LG, bool INV>
+__device__ __noinline__ void bluestein_rounds(float2 *x, const float2 *__restrict__ tw, const BlueStage b, float2 *sc)
+{
+    constexpr int M = 1 << LG;
+    const int R = b.R, h = b.Nb / b.R, ts = b.n / b.Nb, nbf = b.n / b.R, total = nbf * b.nr;
+    for (int b0 = 0; b0 < total; b0 += b.P) {
+        const int np = total - b0 < b.P ? total - b0 : b.P;
+        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x) {
+            const int bb = idx >> LG, t = idx & (M - 1);
+            float2 v = make_float2(0.f, 0.f);
+            if (t < R) {
+                float2 xv = x[b.base_of(b0 + bb) + t * h];
+                if (INV) xv.y = -xv.y;
+                v = cmulf(xv, __ldg(b.ch + t));
+            }
+            sc[padi(idx)] = v;
+        }
+        __syncthreads();
+        fft_p2_smem<LG, false>(sc, b.tm, np);
+        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x)
+            sc[padi(idx)] = cmulf(sc[padi(idx)], __ldg(b.sp + (idx & (M - 1))));
+        __syncthreads();
+        fft_p2_smem<LG, true>(sc, b.tm, np);
+        for (int idx = threadIdx.x; idx < np * R; idx += blockDim.x) {
+            const int bb = idx / R, q = idx - bb * R;
+            const int bi = b0 + bb;
+            const int k = (bi - (bi / nbf) * nbf) % h;
+            float2 v = cmulf(sc[padi((bb << LG) + q)], __ldg(b.ch + q));
+            if (INV) v.y = -v.y;
+            x[b.base_of(bi) + q * h] = cmulf(v, twf<INV>(tw, q * k * ts));
+        }
+        __syncthreads();
+    }
+}
+
+// M = 8192: radix-2 passes (the engine stops at 2^12)
+template <bool INV>
+__device__ __noinline__ void bluestein_rounds_r2(float2 *x, const float2 *__restrict__ tw, const BlueStage b, int lg,
+                                                 float2 *sc)
+{
+    const int M = 1 << lg, hm = M >> 1;
+    const int R = b.R, h = b.Nb / b.R, ts = b.n / b.Nb, nbf = b.n / b.R, total = nbf * b.nr;
+    for (int b0 = 0; b0 < total; b0 += b.P) {
+        const int np = total - b0 < b.P ? total - b0 : b.P;
+        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x) {
+            const int bb = idx >> lg, t = idx & (M - 1);
+            float2 v = make_float2(0.f, 0.f);
+            if (t < R) {
+                float2 xv = x[b.base_of(b0 + bb) + t * h];
+                if (INV) xv.y = -xv.y;
+                v = cmulf(xv, __ldg(b.ch + t));
+            }
+            sc[idx] = v;
+        }
+        __syncthreads();
+        for (int lgs = lg - 1; lgs >= 0; --lgs) {          // half-block s = 2^lgs
+            const int s = 1 << lgs;
+            for (int u = threadIdx.x; u < np * hm; u += blockDim.x) {
+                const int uu = u & (hm - 1), j = uu & (s - 1);
+                const int i0 = ((u >> (lg - 1)) << lg) + ((uu >> lgs) << (lgs + 1)) + j;
+                const float2 a = sc[i0], c = sc[i0 + s];
+                sc[i0] = caddf(a, c);
+                sc[i0 + s] = cmulf(csubf(a, c), __ldg(b.tm + (j << (lg - 1 - lgs))));
+            }
+            __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < np * M; idx += blockDim.x)
+            sc[idx] = cmulf(sc[idx], __ldg(b.sp + (idx & (M - 1))));
+        __syncthreads();
+        for (int lgs = 0; lgs < lg; ++lgs) {
+            const int s = 1 << lgs;
+            for (int u = threadIdx.x; u < np * hm; u += blockDim.x) {
+                const int uu = u & (hm - 1), j = uu & (s - 1);
+                const int i0 = ((u >> (lg - 1)) << lg) + ((uu >> lgs) << (lgs + 1)) + j;
+                float2 w = __ldg(b.tm + (j << (lg - 1 - lgs)));
+                w.y = -w.y;
+                const float2 a = sc[i0], c = cmulf(sc[i0 + s], w);
+                sc[i0] = caddf(a, c);
+                sc[i0 + s] = csubf(a, c);
+            }
+            __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < np * R; idx += blockDim.x) {
+            const int bb = idx / R, q = idx - bb * R;
+            const int bi = b0 + bb;
+            const int k = (bi - (bi / nbf) * nbf) % h;
+            float2 v = cmulf(sc[(bb << lg) + q], __ldg(b.ch + q));
+            if (INV) v.y = -v.y;
+            x[b.base_of(bi) + q * h] = cmulf(v, twf<INV>(tw, q * k * ts));
+        }
+        __syncthreads();
+    }
+}
+
+// The rounds are out of line: inlined into the generic DFT kernels (128 registers at two CTAs
+// per SM) the engine code made them spill.
+template <bool INV>
+__device__ __forceinline__ void dif_stage_bluestein(float2 *x, const float2 *__restrict__ tw, int n, int R, int Nb,
+                                                 int nr, int lg, int P, const float2 *ch, const float2 *sp,
+                                                 const float2 *tm, float2 *sc)
+{
+    const BlueStage b{n, R, Nb, nr, P, ch, sp, tm};
+    switch (lg) {
+    case 5: bluestein_rounds<5, INV>(x, tw, b, sc); break;
+    case 6: bluestein_rounds<6, INV>(x, tw, b, sc); break;
+    case 7: bluestein_rounds<7, INV>(x, tw, b, sc); break;
+    case 8: bluestein_rounds<8, INV>(x, tw, b, sc); break;
+    case 9: bluestein_rounds<9, INV>(x, tw, b, sc); break;
+    case 10: bluestein_rounds<10, INV>(x, tw, b, sc); break;
+    case 11: bluestein_rounds<11, INV>(x, tw, b, sc); break;
+    case 12: bluestein_rounds<12, INV>(x, tw, b, sc); break;
+    default: bluestein_rounds_r2<INV>(x, tw, b, lg, sc); break;
+    }
+}
+
+// sc: the Bluestein scratch (FftPlan::blue_scratch bytes) when the plan has such stages
+template <bool INV>
+__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc)
+{
+    const int n = rp.n;
+    int Nb = n;
+    for (int st = 0; st < rp.nstages; ++st) {
+        const int R = rp.radix[st];
+        const int h = Nb / R;
+        const int ts = n / Nb;
+        const int nbf = n / R;
+        if (R == 3) {
+            dif_stage_small<3, INV>(x, tw, n, Nb, nr);
+        } else if (R == 5) {
+            dif_stage_small<5, INV>(x, tw, n, Nb, nr);
+        } else if (R == 7) {
+            dif_stage_small<7, INV>(x, tw, n, Nb, nr);
+        } else if (R == 11) {
+            dif_stage_small<11, INV>(x, tw, n, Nb, nr);
+        } else if (R == 13) {
+            dif_stage_small<13, INV>(x, tw, n, Nb, nr);
+        } else if (R != 2 && R != 4) {                 // primes >= 17 (build_bluestein marks them all)
+            dif_stage_bluestein<INV>(x, tw, n, R, Nb, nr, rp.blue_lg[st], rp.blue_P[st], rp.blue_chirp + rp.blue_off[st],
+                                     rp.blue_spec + rp.blue_moff[st], rp.blue_tw + rp.blue_moff[st], sc);
+        } else {
+            const Recip rn = recip(nbf), rh = recip(h);
+            for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+                const int ring = rdiv(t, rn), i = t - ring * nbf;
+                const int blk = rdiv(i, rh), k = i - blk * h;
+                float2 *xr = x + ring * n + blk * Nb + k;
+                if (R == 4) {
+                    const float2 v0 = xr[0], v1 = xr[h], v2 = xr[2 * h], v3 = xr[3 * h];
+                    const float2 s02 = caddf(v0, v2), d02 = csubf(v0, v2);
+                    const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
+                    const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+                    xr[0] = caddf(s02, s13);
+                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
+                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
+                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
+                } else {
+                    const float2 v0 = xr[0], v1 = xr[h];
+                    xr[0] = caddf(v0, v1);
+                    xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
+                }
+            }
+        }
+        __syncthreads();
+        Nb = h;
+    }
+}
+
 // Full transform of nr rings, natural order in and out, by the factorisation
 //   radix-16 at block length n, [radix-16 at n/16,] radix-2^r blocks (dif_last),
 // with the first radix-16 stage fed straight from global memory: src.row(r) locates ring r
@@ -505,7 +525,7 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 // forward kernel's 24 KB record staging allows only 2 of them per SM there anyway.  The
 // generic lengths (LOG2N = 0) hold radix-13 butterflies and their roots in registers.
 template <int LOG2N>
-__host__ __device__ constexpr int fft_blocks_per_sm() { return (LOG2N == 11 || LOG2N == 0) ? 2 : 3; }
+__host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 12 ? 1 : (LOG2N == 11 || LOG2N == 0) ? 2 : 3; }
 
 // Inverse-side engine: the transpose of fft_p2_from_global's factorisation (the DFT matrix is
 // symmetric, so the stages taken in reverse order, each transposed, give the same
@@ -1095,7 +1115,7 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
     // record staging after the DFT; the Bluestein scratch (during the DFT) shares its space
-    const size_t blue = p.fft.blue_R ? (size_t)8 * p.fft.blue_P << p.fft.blue_log2m : 0;
+    const size_t blue = p.fft.blue_scratch;
     const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (blue > kStageBytes ? blue : kStageBytes);
     if (p.real) {
         auto k = k_rfft_fwd_bf16<LOG2N>;
@@ -1118,7 +1138,7 @@ template <int LOG2N>
 cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
 {
     RadixPlanArg rp = make_radix_arg(p.fft);
-    const size_t blue = p.fft.blue_R ? (size_t)8 * p.fft.blue_P << p.fft.blue_log2m : 0;
+    const size_t blue = p.fft.blue_scratch;
     const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (LOG2N > 0 ? kInvStageBytes : blue);
     if (p.real) {
         auto k = k_rfft_inv_bf16<LOG2N>;
@@ -1145,6 +1165,7 @@ cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph,
     case 9: return launch_fwd_t<9>(p, Tth, Tph, s);
     case 10: return launch_fwd_t<10>(p, Tth, Tph, s);
     case 11: return launch_fwd_t<11>(p, Tth, Tph, s);
+    case 12: return launch_fwd_t<12>(p, Tth, Tph, s);
     default: return launch_fwd_t<0>(p, Tth, Tph, s);
     }
 }
@@ -1158,6 +1179,7 @@ cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_
     case 9: return launch_inv_t<9>(p, Tth, Tph, s);
     case 10: return launch_inv_t<10>(p, Tth, Tph, s);
     case 11: return launch_inv_t<11>(p, Tth, Tph, s);
+    case 12: return launch_inv_t<12>(p, Tth, Tph, s);
     default: return launch_inv_t<0>(p, Tth, Tph, s);
     }
 }

@@ -10,7 +10,8 @@ struct RadixPlanArg {
     int n;
     int nstages;
     int radix[kMaxRadixStages];
-    int blue_R, blue_log2m, blue_P;     // see FftPlan
+    int blue_lg[kMaxRadixStages], blue_P[kMaxRadixStages];   // see FftPlan
+    int blue_off[kMaxRadixStages], blue_moff[kMaxRadixStages];
     const float2 *blue_chirp, *blue_spec, *blue_tw;
 };
 
@@ -20,9 +21,12 @@ inline RadixPlanArg make_radix_arg(const FftPlan &f)
     r.n = f.n;
     r.nstages = f.nstages;
     for (int i = 0; i < kMaxRadixStages; ++i) r.radix[i] = i < f.nstages ? f.radix[i] : 1;
-    r.blue_R = f.blue_R;
-    r.blue_log2m = f.blue_log2m;
-    r.blue_P = f.blue_P;
+    for (int i = 0; i < kMaxRadixStages; ++i) {
+        r.blue_lg[i] = f.blue_lg[i];
+        r.blue_P[i] = f.blue_P[i];
+        r.blue_off[i] = f.blue_off[i];
+        r.blue_moff[i] = f.blue_moff[i];
+    }
     r.blue_chirp = f.blue_chirp;
     r.blue_spec = f.blue_spec;
     r.blue_tw = f.blue_tw;
