@@ -326,9 +326,10 @@ int build_tables(Plan &p)
     return FAVEST_OK;
 }
 
-// Tensor map of the forward B operand Fb[j/8][field][j%8][mu][parity][piece][8] (bf16):
-// a box {8, 1, 8, 16, 8} at (x0 = (parity*3 + piece)*8, mu, 0, 16*field_tile, 8*K_chunk)
-// lands in shared memory as [K/8][N/8][8 j][8 n], the MN-major core-matrix layout.
+// Tensor map of the forward B operand Fb[j/8][field][j%8][mu][parity][8] (FP32 records of
+// 64 bytes): a box {8, 1, 8, N/8, 4} at (x0 = parity*8, mu, 0, (N/8)*field_tile, 4*K_chunk)
+// lands in shared memory as [K/8][N/8][8 j][8 n] floats, the element order of the MN-major
+// core-matrix layout that the GEMM's converter warps then write as three bf16 pieces.
 int make_fb_tensor_map(Plan &p)
 {
     void *fn = nullptr;
@@ -339,11 +340,11 @@ int make_fb_tensor_map(Plan &p)
         return FAVEST_EUNSUPPORTED;
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     const cuuint64_t L1 = (cuuint64_t)(p.L + 1);
-    cuuint64_t dims[5] = {48, L1, 8, (cuuint64_t)p.nf, (cuuint64_t)(p.JP / 8)};
-    cuuint64_t strides[4] = {96, 96 * L1, 768 * L1, 768 * L1 * (cuuint64_t)p.nf};
+    cuuint64_t dims[5] = {16, L1, 8, (cuuint64_t)p.nf, (cuuint64_t)(p.JP / 8)};
+    cuuint64_t strides[4] = {64, 64 * L1, 512 * L1, 512 * L1 * (cuuint64_t)p.nf};
     cuuint32_t box[5] = {8, 1, 8, (cuuint32_t)(p.gemm_n / 8), (cuuint32_t)(kGemmChunkK / 8)};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    CUresult r = encode(&p.tmap_fb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, p.d_Fb, dims, strides, box, estr,
+    CUresult r = encode(&p.tmap_fb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, p.d_Fb, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
@@ -521,7 +522,7 @@ int alloc_workspace_bf16(Plan &p)
                     I.a_off = off_f[idx] + ((long long)m * p.nk_f + kc0) * CHA;
                     I.a_stride = (int)CHA;
                     I.b_box = 1;
-                    I.bx = par * 3 * 8;
+                    I.bx = par * 8;
                     I.by = fpt * nt;
                     I.bw = mu;
                     I.bk = kc0;
@@ -577,7 +578,7 @@ int alloc_workspace_bf16(Plan &p)
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
     const size_t lamf_bytes = (size_t)lam_f, lama_bytes = (size_t)lam_a;
-    const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 96;
+    const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 64;
     const size_t q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
     const size_t s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
     if (plan_malloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || plan_malloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
@@ -1088,11 +1089,11 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         // generator and GEMMs: the values and (row, latitude) pairs above the turning
         // bound, i.e. the work these kernels are given (the rest is below 1e-13)
         const double gv = p.gen_values, pf = p.gemm_pairs_f, pa = p.gemm_pairs_a;
-        if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 96.0; *flops = fftf; }
+        if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 64.0; *flops = fftf; }
         else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
         else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; *pipe = 1; }
         else if (k == "gen_lambda_both") { *bytes = gv * 12.0; *flops = gv * 4.0; *pipe = 1; }
-        else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 96.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
+        else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 64.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
         else if (k == "tc_gemm_adj") { *bytes = pa * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * pa * 8.0 * G; }
         else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }
         else if (k == "uncombine") { *bytes = coef + rows * G * 48.0; *flops = 24.0 * B * kc; }

@@ -60,7 +60,8 @@ constexpr int kInvChunk = 256;    // orders per TMA box of the inverse DFT's sum
 // chunk three bf16 pieces.  Chunk c of A starts a_off + c * a_stride bytes into the A
 // buffer (a multiple of 512: the TMA addresses the buffer as rows of 512 bytes); B
 // likewise (b_box = 0), or (b_box = 1) through the forward operand's 5-D tensor map at
-// coordinates (bx + 8 * piece, bw, 0, by, 4 * (bk + c)).  Output row r (< rows) of field
+// coordinates (bx, bw, 0, by, 4 * (bk + c)) (FP32 records; the forward GEMM splits them
+// into the bf16 pieces).  Output row r (< rows) of field
 // column group g (8 floats) is written at
 //   out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs.
 struct TcItem {
@@ -73,7 +74,7 @@ struct TcItem {
     int a_stride;       // bytes between consecutive A chunks
     int b_stride;       // bytes between consecutive B chunks
     int b_box;          // 1: B through the 5-D tensor map
-    int bx, by, bw;     // 5-D box coordinates: x of piece 0, first field, order
+    int bx, by, bw;     // 5-D box coordinates: x of the parity's 8 floats, first field, order
     int bk;             // 5-D box: first K-chunk (chunks below it are skipped)
     int group;          // index into the launch's GemmGroup array
 };
@@ -149,7 +150,7 @@ struct Plan {
     // one without generating it, kGenAdj likewise for the next adjoint call, 0 otherwise
     int lam_pending = 0;
     double gemm_pairs_f = 0, gemm_pairs_a = 0;   // (row, latitude) pairs the GEMMs contract
-    void *d_Fb = nullptr;         // forward B operand (bf16 x 3)
+    void *d_Fb = nullptr;         // forward B operand (FP32 records, split into bf16 x 3 by the GEMM)
     void *d_gb = nullptr;         // adjoint B operand (bf16 x 3)
     float *d_Q32 = nullptr;       // forward GEMM output [group][l][mu][8]
     float *d_S32 = nullptr;       // adjoint GEMM output [group][JP/4][mu][parity][4][8]

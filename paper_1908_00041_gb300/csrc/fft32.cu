@@ -1,9 +1,9 @@
 // Longitude DFT stage of the split-precision path (FP32 arithmetic, FP64-derived
 // twiddles rounded to FP32).  One CTA per (field b, folded latitude j) handles the four
 // rings theta/phi x (j, nlat-1-j) (real fields: see k_rfft_fwd_bf16):
-//   forward: T -> FFT -> weighted equatorial fold F+- = omega_j (F_j +- F_j') -> three
-//            bf16 pieces staged per warp and stored into the tensor-core B-operand layout
-//            by bulk asynchronous copies.
+//   forward: T -> FFT -> weighted equatorial fold F+- = omega_j (F_j +- F_j') -> FP32
+//            records staged per warp and stored into the tensor-core GEMM's field-operand
+//            layout by bulk asynchronous copies (the GEMM splits them into bf16 pieces).
 //   inverse: streams the even/odd Legendre sums E, O of every order through shared memory
 //            (TMA boxes), forms G_j = (E + O) / sin(theta_j), G_j' = (E - O) / sin(theta_j),
 //            inverse FFT whose last stage stores to global memory.
@@ -464,22 +464,29 @@ __device__ void fft_p2_from_global(float2 *x, const float2 *__restrict__ tw, int
     dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
 }
 
-// The forward DFT's B-operand records (96 bytes per order: parity x piece x 16 bytes)
-// are staged per warp in shared memory: the records of a warp's 32 consecutive orders are
-// 3 KB of consecutive bytes in global memory, which a direct per-thread store would touch
-// at a 96-byte stride (24 cache lines per instruction).  One lane hands the staged block to
+// The forward DFT's B-operand records (64 bytes per order: parity x 8 floats) are staged per
+// warp in shared memory: the records of a warp's 32 consecutive orders are 2 KB of
+// consecutive bytes in global memory, which a direct per-thread store would touch at a
+// 64-byte stride.  One lane hands the staged block to
 // a bulk asynchronous copy (shared -> global), so the copy takes no load/store-unit
 // instructions; before the warp stages its next records it waits until the copy has read
 // the staging buffer.
-constexpr int kRecUint4 = 6;                               // 16-byte chunks per record
-constexpr int kStageBytes = (kFftThreads / 32) * 32 * kRecUint4 * 16;   // 24 KB
+constexpr int kRecUint4 = 4;                               // 16-byte chunks per record
+constexpr int kStageBytes = (kFftThreads / 32) * 32 * kRecUint4 * 16;   // 16 KB
+
+// 8 floats of one parity as two 16-byte chunks of a record
+__device__ __forceinline__ void pack_row_f32(const float (&v)[8], uint4 (&out)[2])
+{
+    out[0] = make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+    out[1] = make_uint4(__float_as_uint(v[4]), __float_as_uint(v[5]), __float_as_uint(v[6]), __float_as_uint(v[7]));
+}
 
 __device__ __forceinline__ void bulk_wait_read()
 {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// stage -> global: nrec records (16-byte aligned addresses, 96 nrec bytes)
+// stage -> global: nrec records (16-byte aligned addresses, 64 nrec bytes)
 __device__ __forceinline__ void flush_records(unsigned char *__restrict__ dst, const uint4 *stg, int nrec, int lane)
 {
     // the generic-proxy writes of the staging buffer become visible to the async proxy
@@ -718,14 +725,15 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
                        reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = omega[j];
-    // Fb[j/8][field][j%8][mu][parity][piece][8]: this CTA's block is contiguous over mu
-    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 96;
+    // Fb[j/8][field][j%8][mu][parity][8 floats]: this CTA's block is contiguous over mu (the
+    // tensor-core GEMM splits the values into bf16 pieces as it loads them)
+    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 64;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint4 *stg = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)) +
                  warp * 32 * kRecUint4;
     for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
         const int mu = mu0 + lane;
-        uint4 rec_p[3], rec_m[3];
+        uint4 rec_p[2], rec_m[2];
         if (mu <= L) {
             float vp[8], vm[8];
             // n % 8 = c*4 + s*2 + im ; s = 0: +mu (bin mu), s = 1: -mu (bin n - mu, or 0 at mu = 0)
@@ -745,19 +753,19 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
                     vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
                 }
             }
-            pack_row3(vp, rec_p);
-            pack_row3(vm, rec_m);
+            pack_row_f32(vp, rec_p);
+            pack_row_f32(vm, rec_m);
         }
         staging_free(lane);                          // the previous round's copy has read it
         if (mu <= L) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 stg[lane * kRecUint4 + q] = rec_p[q];
-                stg[lane * kRecUint4 + 3 + q] = rec_m[q];
+                stg[lane * kRecUint4 + 2 + q] = rec_m[q];
             }
         }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
-        flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
+        flush_records(dst_base + (size_t)mu0 * 64, stg, nrec, lane);
     }
     staging_free(lane);                              // shared memory stays until the copies read it
 }
@@ -986,13 +994,13 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                        reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
-    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 96;
+    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 64;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint4 *stg = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)) +
                  warp * 32 * kRecUint4;
     for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
         const int mu = mu0 + lane;
-        uint4 rec_p[3], rec_m[3];
+        uint4 rec_p[2], rec_m[2];
         if (mu <= L) {
             const int bp = mu, bm = mu == 0 ? 0 : n - mu;
             const int pp = LOG2N > 0 ? bp : __ldg(perm + bp), pm = LOG2N > 0 ? bm : __ldg(perm + bm);
@@ -1015,19 +1023,19 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                 vm[4 + f * 2] = eq ? 0.f : w * (pjx - pkx);
                 vm[4 + f * 2 + 1] = eq ? 0.f : w * (pjy - pky);
             }
-            pack_row3(vp, rec_p);
-            pack_row3(vm, rec_m);
+            pack_row_f32(vp, rec_p);
+            pack_row_f32(vm, rec_m);
         }
         staging_free(lane);                          // the previous round's copy has read it
         if (mu <= L) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < 2; ++c) {
                 stg[lane * kRecUint4 + c] = rec_p[c];
-                stg[lane * kRecUint4 + 3 + c] = rec_m[c];
+                stg[lane * kRecUint4 + 2 + c] = rec_m[c];
             }
         }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
-        flush_records(dst_base + (size_t)mu0 * 96, stg, nrec, lane);
+        flush_records(dst_base + (size_t)mu0 * 64, stg, nrec, lane);
     }
     staging_free(lane);                              // shared memory stays until the copies read it
 }

@@ -4,9 +4,10 @@
 //   forward : Q[rows, n]   = sum_j  Lam[rows, j] * Fb[j, n]      (rows = l - mu of parity p)
 //   adjoint : S_p[j, n]    = sum_r  Lam[r, j]   * g[r, n]
 // Lam (the FP64 recurrence values) is produced by a generator kernel and stored as
-// three bf16 pieces (hi + mid + lo = the FP64 value truncated to 24 bits); Fb and g
-// carry three bf16 pieces as well.  The GEMM kernel forms 6 of the 9 piece products
-// (those with combined weight >= 2^-16 of the leading one).  Because the tensor core
+// three bf16 pieces (hi + mid + lo = the FP64 value truncated to 24 bits); g carries three
+// bf16 pieces as well, and Fb (FP32 records from the forward DFT) is split into three pieces
+// by converter warps of the forward GEMM as it is loaded.  The GEMM kernels form 6 of the 9
+// piece products (those with combined weight >= 2^-16 of the leading one).  Because the tensor core
 // accumulates in FP32 with truncation (products below one ulp of the running sum are
 // dropped), the leading hi*hi product is accumulated in a fresh TMEM buffer for each
 // K-chunk of 32 and added to an FP32 register sum (round-to-nearest) by the epilogue;
@@ -18,10 +19,11 @@
 // shared-memory core-matrix layout (see tc.cuh):
 //   forward A (Lam, M = rows, K = j, MN-major): [K/8 groups][M/8 groups][8 j][8 rows]  8 KB
 //   adjoint A (Lam^T, M = j, K = rows, K-major): [M/8][K/8][8 j][8 rows]               8 KB
-//   B (Fb or g, K x N, MN-major):               [K/8][N/8][8 k][8 n]           K32 x N x 2 B
+//   B (pieces of Fb or g, K x N, MN-major):     [K/8][N/8][8 k][8 n]           K32 x N x 2 B
 #include "favest_internal.h"
 #include "recurrence.cuh"
 #include "tc.cuh"
+#include "bf16_split.cuh"
 
 #include <cuda_bf16.h>
 
@@ -475,6 +477,284 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Forward GEMM with an FP32 field operand.  The forward DFT stores its spectra as FP32
+// records ([parity][8 floats] per latitude, field group and order, 64 bytes), so a K-chunk
+// of the field operand arrives through TMA as rows of 32 bytes (8 floats), a third of the
+// rows and two thirds of the bytes of three bf16 pieces.  Converter warps split it in shared
+// memory into the three bf16 pieces the MMAs read (the same split the DFT made before, so
+// results are bitwise unchanged); the element order of the FP32 box, [K/8][N/8][8 k][8 n],
+// is already the pieces' core-matrix order.
+// Warps, by warpgroup (the register split below acts on whole warpgroups): 0 producer (TMA of
+// the Legendre chunk and the FP32 field chunk) and 1 MMA issuer (2, 3 idle); 4..7 converters;
+// 8..15 epilogue (lane quadrant warp % 4, column half (warp - 8) / 4).
+// Per stage: full (TMA landed) -> converters -> ready (pieces written) -> MMA -> empty.
+// Registers: launched at 128 per thread (512 threads); warpgroups 0-1 (producer, MMA,
+// converters) drop to 80 and the two epilogue warpgroups rise to 176, which the epilogue's
+// 128 FP32 running sums per thread need: 256 x 80 + 256 x 176 = 512 x 128.
+// ---------------------------------------------------------------------------
+constexpr int kFStages = 2;
+constexpr int kConvWarps = 4;
+constexpr int kFThreads = 512;
+
+template <int N>
+struct GemmSmemF {
+    unsigned char a[kFStages][kChunkBytes];
+    unsigned char b[kFStages][kPieces * kChunkK * N * 2];
+    unsigned char bf[kFStages][kChunkK * N * 4];
+    uint64_t full[kFStages], ready[kFStages], empty[kFStages];
+    uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+template <int N>
+__global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
+    const GemmGroup *__restrict__ groups, const TcItem *__restrict__ items, int nitems, int *__restrict__ status,
+    uint32_t poll_limit)
+{
+    constexpr int kEpiWarps = 4 * (N / kEpiCols);
+    constexpr int kPieceB = kChunkK * N * 2;
+    constexpr int kChunkBF = kChunkK * N * 4;       // FP32 field chunk
+    extern __shared__ __align__(1024) unsigned char sm_raw_f[];
+    GemmSmemF<N> &S = *reinterpret_cast<GemmSmemF<N> *>(sm_raw_f);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) tc::tmem_alloc(&S.tmem_base, kTmemCols);
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kFStages; ++s) {
+            tc::mbar_init(&S.full[s], 1);
+            tc::mbar_init(&S.ready[s], kConvWarps);
+            tc::mbar_init(&S.empty[s], 1);
+        }
+        tc::mbar_init(&S.dmain_full, 1);
+        tc::mbar_init(&S.dmain_empty, kEpiWarps);
+        tc::mbar_init(&S.dcorr_full, 1);
+        tc::mbar_init(&S.dcorr_empty, kEpiWarps);
+        tc::mbar_init(&S.drain, 1);
+        S.abort = 0;
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem_base;
+    volatile int *abort = &S.abort;
+    const int wg = warp >> 2;
+
+    if (wg == 0) {
+      tc::setmaxnreg_dec<80>();
+      if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            uint32_t phase = 0, issued = 0;
+            int stage = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const TcItem I = items[it];
+                const CUtensorMap *tmap_a = &groups[I.group].tmap_a, *tmap_b = &groups[I.group].tmap_b;
+                for (int c = 0; c < I.nk; ++c) {
+                    if (!wait_or_abort(&S.empty[stage], ((phase >> stage) & 1) ^ 1, abort, poll_limit)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkBF);
+                    tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
+                                    &S.full[stage]);
+                    tc::tma_load_5d(S.bf[stage], tmap_b, I.bx, I.bw, 0, I.by, (kChunkK / 8) * (I.bk + c),
+                                    &S.full[stage]);
+                    phase ^= 1u << stage;
+                    issued |= 1u << stage;
+                    stage = (stage + 1) % kFStages;
+                }
+            }
+            // on abort: let this warp's loads land before the CTA can exit (bounded)
+            if (*abort)
+                for (int s = 0; s < kFStages; ++s)
+                    if (issued & (1u << s)) wait_or_abort(&S.full[s], ((phase >> s) & 1) ^ 1, nullptr, poll_limit);
+        }
+      } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16(kTileM, N, 1, 1) | (1u << 7) | (1u << 10);
+            uint32_t phase = 0, main_use = 0, corr_use = 0;
+            int stage = 0;
+            const uint32_t dmain = tmem, dcorr = tmem + N;
+            constexpr uint32_t a_step = 4096u, a_lbo = 2048u, a_sbo = 128u;     // A MN-major
+            constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
+            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const TcItem I = items[it];
+                if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort, poll_limit)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                for (int c = 0; c < I.nk; ++c) {
+                    if (!wait_or_abort(&S.ready[stage], (phase >> stage) & 1, abort, poll_limit)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(S.a[stage]), b0 = tc::smem_u32(S.b[stage]);
+#pragma unroll
+                    for (int s = 0; s < kChunkK / 16; ++s) {
+                        const uint32_t as = a0 + s * a_step, bs = b0 + s * b_step;
+                        const uint64_t A0 = tc::sdesc(as, a_lbo, a_sbo);
+                        const uint64_t A1 = tc::sdesc(as + kPieceBytes, a_lbo, a_sbo);
+                        const uint64_t A2 = tc::sdesc(as + 2 * kPieceBytes, a_lbo, a_sbo);
+                        const uint64_t B0 = tc::sdesc(bs, b_lbo, 128);
+                        const uint64_t B1 = tc::sdesc(bs + kPieceB, b_lbo, 128);
+                        const uint64_t B2 = tc::sdesc(bs + 2 * kPieceB, b_lbo, 128);
+                        tc::mma_f16(dcorr, A0, B1, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                        tc::mma_f16(dcorr, A1, B0, idesc, 1);
+                        tc::mma_f16(dcorr, A0, B2, idesc, 1);
+                        tc::mma_f16(dcorr, A1, B1, idesc, 1);
+                        tc::mma_f16(dcorr, A2, B0, idesc, 1);
+                    }
+                    if (!wait_or_abort(&S.dmain_empty, (main_use & 1) ^ 1, abort, poll_limit)) {
+                        set_status(status, FAVEST_ETIMEOUT);
+                        *abort = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int s = 0; s < kChunkK / 16; ++s)
+                        tc::mma_f16(dmain, tc::sdesc(a0 + s * a_step, a_lbo, a_sbo),
+                                    tc::sdesc(b0 + s * b_step, b_lbo, 128), idesc, s > 0);
+                    tc::mma_commit(&S.empty[stage]);
+                    tc::mma_commit(&S.dmain_full);
+                    phase ^= 1u << stage;
+                    main_use++;
+                    stage = (stage + 1) % kFStages;
+                }
+                if (*abort) break;
+                tc::mma_commit(&S.dcorr_full);
+                corr_use++;
+            }
+            if (*abort) {
+                tc::mma_commit(&S.drain);
+                wait_or_abort(&S.drain, 0, nullptr, poll_limit);
+            }
+        }
+      }
+    } else if (wg == 1) {
+        tc::setmaxnreg_dec<80>();
+        // ---------------- converters: FP32 field chunk -> three bf16 pieces ----------------
+        const int ct = threadIdx.x - 128;                // 0 .. 32 * kConvWarps - 1
+        uint32_t phase = 0;
+        int stage = 0;
+        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            const int nk = __ldg(&items[it].nk);
+            bool ok = true;
+            for (int c = 0; c < nk; ++c) {
+                if (!wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort, poll_limit)) { ok = false; break; }
+                const float4 *src = reinterpret_cast<const float4 *>(S.bf[stage]);
+                uint4 *dst = reinterpret_cast<uint4 *>(S.b[stage]);
+                // row r: 8 consecutive floats -> 16 bytes of each piece at the same position
+                for (int r = ct; r < kChunkK * N / 8; r += 32 * kConvWarps) {
+                    const float4 lo = src[2 * r], hi = src[2 * r + 1];
+                    const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                    uint4 pc[3];
+                    pack_row3(v, pc);
+#pragma unroll
+                    for (int q = 0; q < kPieces; ++q) dst[q * (kPieceB / 16) + r] = pc[q];
+                }
+                tc::fence_proxy_async_smem();            // the MMAs read the pieces through the async proxy
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.ready[stage]);
+                phase ^= 1u << stage;
+                stage = (stage + 1) % kFStages;
+            }
+            if (!ok) {
+                set_status(status, FAVEST_ETIMEOUT);
+                *abort = 1;
+                break;
+            }
+        }
+    } else {
+      tc::setmaxnreg_inc<176>();
+      if (warp - 8 < kEpiWarps) {
+        // ------ epilogue (lane quadrant warp % 4, columns 128 * ((warp - 8) / 4) ..) ------
+        const int quad = warp & 3;
+        const int part = (warp - 8) >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        uint32_t main_use = 0, corr_use = 0;
+        float acc[kEpiCols];
+        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            const int nk = __ldg(&items[it].nk);
+#pragma unroll
+            for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
+            bool ok = true;
+            for (int c = 0; c < nk; ++c) {
+                if (!wait_or_abort(&S.dmain_full, main_use & 1, abort, poll_limit)) { ok = false; break; }
+                tc::fence_after_sync();
+                const uint32_t col0 = tmem + lane_base + part * kEpiCols;
+#pragma unroll
+                for (int q = 0; q < kEpiCols / 16; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(col0 + q * 16, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[q * 16 + i] += v[i];
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.dmain_empty);
+                main_use++;
+            }
+            if (!ok || !wait_or_abort(&S.dcorr_full, corr_use & 1, abort, poll_limit)) {
+                set_status(status, FAVEST_ETIMEOUT);
+                *abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int q = 0; q < kEpiCols / 16; ++q) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + N + part * kEpiCols + q * 16, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[q * 16 + i] += v[i];
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&S.dcorr_empty);
+            corr_use++;
+            if (row < __ldg(&items[it].rows)) {
+                const long long col_gs = __ldg(&items[it].col_gs);
+                float *dst = groups[__ldg(&items[it].group)].out + __ldg(&items[it].out_off) +
+                             (long long)(row >> 2) * __ldg(&items[it].out_ld) + (row & 3) * 8 +
+                             (long long)(part * (kEpiCols / 8)) * col_gs;
+#pragma unroll
+                for (int g = 0; g < kEpiCols / 8; ++g) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dst + g * col_gs);
+                    d4[0] = make_float4(acc[8 * g], acc[8 * g + 1], acc[8 * g + 2], acc[8 * g + 3]);
+                    d4[1] = make_float4(acc[8 * g + 4], acc[8 * g + 5], acc[8 * g + 6], acc[8 * g + 7]);
+                }
+            }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int N>
+cudaError_t launch_gemm_f(const GemmGroup *groups, const TcItem *items, int nitems, int *status, int num_sms,
+                          cudaStream_t s)
+{
+    const size_t smem = sizeof(GemmSmemF<N>) + 1024;
+    auto k = k_tc_gemm_f<N>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = nitems < num_sms ? nitems : num_sms;
+    if (grid <= 0) return cudaSuccess;
+    k<<<grid, kFThreads, smem, s>>>(groups, items, nitems, status, kWaitPolls);
+    return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nitems, int a_mn_major, int *status,
                           int num_sms, cudaStream_t s, uint32_t poll_limit = kWaitPolls, int skip_loads = 0)
@@ -528,6 +808,10 @@ cudaError_t launch_gen_lambda(const Plan &p, int layouts, cudaStream_t s)
 cudaError_t launch_tc_gemm_items(int gemm_n, const GemmGroup *groups, const TcItem *items, int nitems,
                                  int a_mn_major, int *status, int num_sms, cudaStream_t s)
 {
+    // the forward items (MN-major Legendre operand) read the FP32 field operand
+    if (a_mn_major)
+        return gemm_n == 256 ? launch_gemm_f<256>(groups, items, nitems, status, num_sms, s)
+                             : launch_gemm_f<128>(groups, items, nitems, status, num_sms, s);
     return gemm_n == 256 ? launch_gemm_n<256>(groups, items, nitems, a_mn_major, status, num_sms, s)
                          : launch_gemm_n<128>(groups, items, nitems, a_mn_major, status, num_sms, s);
 }
