@@ -488,20 +488,21 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
 // Warps, by warpgroup (the register split below acts on whole warpgroups): 0 producer (TMA of
 // the Legendre chunk and the FP32 field chunk) and 1 MMA issuer (2, 3 idle); 4..7 converters;
 // 8..15 epilogue (lane quadrant warp % 4, column half (warp - 8) / 4).
-// Per stage: full (TMA landed) -> converters -> ready (pieces written) -> MMA -> empty.
-// Registers: launched at 128 per thread (512 threads); warpgroups 0-1 (producer, MMA,
-// converters) drop to 80 and the two epilogue warpgroups rise to 176, which the epilogue's
-// 128 FP32 running sums per thread need: 256 x 80 + 256 x 176 = 512 x 128.
+// Per stage (three of 72 KB): full (TMA landed) -> converters -> ready (pieces written) ->
+// MMA -> empty.  Registers: launched at 128 per thread (512 threads); warpgroup 0 (producer,
+// MMA) drops to 56, the converters to 104 (their rows in registers) and the two epilogue
+// warpgroups rise to 176, which the epilogue's 128 FP32 running sums per thread need:
+// 128 x 56 + 128 x 104 + 256 x 176 = 512 x 128.
 // ---------------------------------------------------------------------------
-constexpr int kFStages = 2;
+constexpr int kFStages = 3;
 constexpr int kConvWarps = 4;
 constexpr int kFThreads = 512;
+constexpr int kConvRows = kChunkK * 256 / 8 / (32 * kConvWarps);   // 8-float rows per converter thread (N = 256)
 
 template <int N>
 struct GemmSmemF {
     unsigned char a[kFStages][kChunkBytes];
-    unsigned char b[kFStages][kPieces * kChunkK * N * 2];
-    unsigned char bf[kFStages][kChunkK * N * 4];
+    unsigned char b[kFStages][kPieces * kChunkK * N * 2];   // FP32 chunk lands in its first 2/3
     uint64_t full[kFStages], ready[kFStages], empty[kFStages];
     uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
     uint64_t drain;
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);
     constexpr int kPieceB = kChunkK * N * 2;
-    constexpr int kChunkBF = kChunkK * N * 4;       // FP32 field chunk
+    constexpr int kChunkBF = kChunkK * N * 4;       // FP32 field chunk (first 2/3 of a piece buffer)
     extern __shared__ __align__(1024) unsigned char sm_raw_f[];
     GemmSmemF<N> &S = *reinterpret_cast<GemmSmemF<N> *>(sm_raw_f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
     const int wg = warp >> 2;
 
     if (wg == 0) {
-      tc::setmaxnreg_dec<80>();
+      tc::setmaxnreg_dec<56>();
       if (warp == 0) {
         // ---------------- producer ----------------
         if (lane == 0) {
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
                     tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkBF);
                     tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
                                     &S.full[stage]);
-                    tc::tma_load_5d(S.bf[stage], tmap_b, I.bx, I.bw, 0, I.by, (kChunkK / 8) * (I.bk + c),
+                    tc::tma_load_5d(S.b[stage], tmap_b, I.bx, I.bw, 0, I.by, (kChunkK / 8) * (I.bk + c),
                                     &S.full[stage]);
                     phase ^= 1u << stage;
                     issued |= 1u << stage;
@@ -640,22 +641,52 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
         }
       }
     } else if (wg == 1) {
-        tc::setmaxnreg_dec<80>();
-        // ---------------- converters: FP32 field chunk -> three bf16 pieces ----------------
+        tc::setmaxnreg_dec<104>();
+        // ---------------- converters: FP32 field chunk -> three bf16 pieces, in place ----------------
+        // The FP32 rows (8 floats, 32 bytes) occupy the first 2/3 of the stage's piece buffer and
+        // the pieces (16 bytes per row each) all of it, so every converter thread first reads
+        // its rows into registers and the converter warps meet at a named barrier before any
+        // piece is written.
+        constexpr int kRows = kChunkK * N / 8 / (32 * kConvWarps);
+        static_assert(kRows * 32 * kConvWarps * 8 == kChunkK * N && kRows <= kConvRows, "converter rows");
+        // Each thread waits on the stage on its own, so whether a chunk goes ahead is agreed
+        // at the named barrier itself (an OR over the converter threads of "my wait gave up"):
+        // every converter thread then passes the same number of barriers and leaves together.
         const int ct = threadIdx.x - 128;                // 0 .. 32 * kConvWarps - 1
         uint32_t phase = 0;
         int stage = 0;
-        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+        bool ok = true;
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
             const int nk = __ldg(&items[it].nk);
-            bool ok = true;
             for (int c = 0; c < nk; ++c) {
-                if (!wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort, poll_limit)) { ok = false; break; }
-                const float4 *src = reinterpret_cast<const float4 *>(S.bf[stage]);
+                const uint32_t gave_up =
+                    wait_or_abort(&S.full[stage], (phase >> stage) & 1, abort, poll_limit) ? 0u : 1u;
+                const float4 *src = reinterpret_cast<const float4 *>(S.b[stage]);
                 uint4 *dst = reinterpret_cast<uint4 *>(S.b[stage]);
+                float4 v4[kRows][2];
+                if (!gave_up) {
+#pragma unroll
+                    for (int k = 0; k < kRows; ++k) {
+                        const int r = ct + k * 32 * kConvWarps;
+                        v4[k][0] = src[2 * r];
+                        v4[k][1] = src[2 * r + 1];
+                    }
+                }
+                uint32_t any_gave_up;
+                asm volatile("{\n\t.reg .pred q, p;\n\t"
+                             "setp.ne.u32 q, %1, 0;\n\t"
+                             "bar.red.or.pred p, 1, %2, q;\n\t"
+                             "selp.u32 %0, 1, 0, p;\n\t}"
+                             : "=r"(any_gave_up)
+                             : "r"(gave_up), "n"(32 * kConvWarps)
+                             : "memory");
+                if (any_gave_up) { ok = false; break; }
                 // row r: 8 consecutive floats -> 16 bytes of each piece at the same position
-                for (int r = ct; r < kChunkK * N / 8; r += 32 * kConvWarps) {
-                    const float4 lo = src[2 * r], hi = src[2 * r + 1];
-                    const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int k = 0; k < kRows; ++k) {
+                    const int r = ct + k * 32 * kConvWarps;
+                    const float v[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
+                                        v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
                     uint4 pc[3];
                     pack_row3(v, pc);
 #pragma unroll
@@ -667,11 +698,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
                 phase ^= 1u << stage;
                 stage = (stage + 1) % kFStages;
             }
-            if (!ok) {
-                set_status(status, FAVEST_ETIMEOUT);
-                *abort = 1;
-                break;
-            }
+        }
+        if (!ok) {
+            set_status(status, FAVEST_ETIMEOUT);
+            *abort = 1;
         }
     } else {
       tc::setmaxnreg_inc<176>();
