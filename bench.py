@@ -229,7 +229,8 @@ def time_steps(fn, steps, warmup, stream):
 def measure_split_other_length(L, B, stream):
     """The split path at a degree whose longitude count is not a power of two (L = 1000:
     n_phi = 2002 = 2*7*11*13, the paper's nearest timing row), B complex64 fields, a few
-    CUDA-event-timed steps after warm-up; per-kernel times from the plan's own events."""
+    CUDA-event-timed steps after warm-up (adjoint + forward sharing one generator pass, as in
+    the headline step); per-kernel times from the plan's own events."""
     import torch
     from paper_1908_00041_gb300 import api, synthetic
     p = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
@@ -243,8 +244,8 @@ def measure_split_other_length(L, B, stream):
     b2 = torch.empty_like(b)
 
     def st():
-        p.adj(a, b, tt, tp, stream=stream)
-        p.fwd(tt, tp, a2, b2, stream=stream)
+        p.adj(a, b, tt, tp, stream=stream, share_lambda=True)
+        p.fwd(tt, tp, a2, b2, stream=stream, share_lambda=True)
     ms = time_steps(st, 5, 3, stream)
     p.profile(True)
     time_steps(st, 2, 0, stream)
@@ -399,7 +400,42 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     forms["fp64_real_vs_complex_L511_B8"] = measure_fp64_real(511, 8, stream)
     forms["split_L1000_B%d" % B] = measure_split_other_length(1000, B, stream)
     forms["table3_degrees"] = measure_table3(stream, B)
+    forms["scatter_L127_N32768_B2"] = measure_scatter(127, 32768, 2, stream)
     return forms
+
+
+def measure_scatter(L, npts, B, stream):
+    """Transforms at arbitrary points (Sec. 4.4's FaVeST_fwd(T, L, X, w) / FaVeST_adj(a, b, X)):
+    npts area-uniform random points (z ~ U[-1, 1], phi ~ U[0, 2 pi), seed 4), unit weights,
+    B fields of Cartesian components; CUDA-event times of the forward and the adjoint, the
+    rate in point x coefficient pairs per second (both families), and the adjoint identity
+    <A c, T> = <c, A^H T> of the measured pair as a check."""
+    import numpy as np
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1.0, 1.0, npts)
+    ph = rng.uniform(0.0, 2.0 * np.pi, npts)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    X = np.stack([r * np.cos(ph), r * np.sin(ph), z], -1)
+    p = api.ScatterPlan(L, X, None, batch=B)
+    a, b = synthetic.coefficients(L, B, seed=6)
+    a = torch.as_tensor(a).cuda()
+    b = torch.as_tensor(b).cuda()
+    T = torch.as_tensor(rng.standard_normal((B, npts, 3)) + 1j * rng.standard_normal((B, npts, 3))).cuda()
+    ga = torch.empty_like(a)
+    gb = torch.empty_like(b)
+    gT = torch.empty_like(T)
+    fwd_ms = time_steps(lambda: p.fwd(T, ga, gb, stream=stream), 5, 2, stream)
+    adj_ms = time_steps(lambda: p.adj(a, b, gT, stream=stream), 5, 2, stream)
+    lhs = torch.vdot(gT.ravel(), T.ravel())
+    rhs = torch.vdot(a.ravel(), ga.ravel()) + torch.vdot(b.ravel(), gb.ravel())
+    pairs = 2.0 * B * npts * (L * L + 2 * L)
+    p.close()
+    return {"L": L, "points": npts, "fields": B, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
+            "fwd_pairs_per_s": pairs / (fwd_ms * 1e-3), "adj_pairs_per_s": pairs / (adj_ms * 1e-3),
+            "adjoint_identity_rel": float(abs(lhs - rhs) / abs(rhs)), "points_recipe":
+            "area-uniform random, numpy default_rng(4), unit weights"}
 
 
 def measure_fp64_real(L, B, stream):
@@ -555,7 +591,8 @@ def measure_field_a():
 
 def measure_real(L, B, stream):
     """Split form on real fields: B fields, coefficients m >= 0 drawn as for the main
-    workload ((l+1)^-1.5, seed 2, m = 0 entries real), adj + fwd per step; errors of two
+    workload ((l+1)^-1.5, seed 2, m = 0 entries real), adj + fwd per step sharing one
+    generator pass; errors of two
     sampled fields against the FP64 complex path on the Hermitian-extended input."""
     import numpy as np
     import torch
@@ -571,8 +608,8 @@ def measure_real(L, B, stream):
     rb = torch.empty_like(db)
 
     def step():
-        pr.adj(da, db, tt, tp, stream=stream)
-        pr.fwd(tt, tp, ra, rb, stream=stream)
+        pr.adj(da, db, tt, tp, stream=stream, share_lambda=True)
+        pr.fwd(tt, tp, ra, rb, stream=stream, share_lambda=True)
     ms = time_steps(step, 10, 3, stream)
     pr.profile(True)
     time_steps(step, 3, 0, stream)

@@ -370,8 +370,9 @@ __device__ __forceinline__ void dif_stage_bluestein(float2 *x, const float2 *__r
     }
 }
 
-// sc: the Bluestein scratch (FftPlan::blue_scratch bytes) when the plan has such stages
-template <bool INV>
+// sc: the Bluestein scratch (FftPlan::blue_scratch bytes) when the plan has such stages;
+// BLUE = false compiles without the Bluestein branch (plans whose radices are all <= 13)
+template <bool INV, bool BLUE>
 __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc)
 {
     const int n = rp.n;
@@ -391,7 +392,7 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
             dif_stage_small<11, INV>(x, tw, n, Nb, nr);
         } else if (R == 13) {
             dif_stage_small<13, INV>(x, tw, n, Nb, nr);
-        } else if (R != 2 && R != 4) {                 // primes >= 17 (build_bluestein marks them all)
+        } else if (BLUE && R != 2 && R != 4) {         // primes >= 17 (build_bluestein marks them all)
             dif_stage_bluestein<INV>(x, tw, n, R, Nb, nr, rp.blue_lg[st], rp.blue_P[st], rp.blue_chirp + rp.blue_off[st],
                                      rp.blue_spec + rp.blue_moff[st], rp.blue_tw + rp.blue_moff[st], sc);
         } else {
@@ -507,6 +508,38 @@ __device__ __forceinline__ void staging_free(int lane)
     __syncwarp();
 }
 
+// Records of the orders mu0 + lane (valid lanes; nrec of them from mu0 on) at dst = the
+// record of mu0: staged per warp and handed to one bulk copy (LOG2N >= 0), or (LOG2N < 0)
+// stored from registers, two 32-byte stores (a whole sector each) per lane.
+__device__ __forceinline__ void st_v8(unsigned char *p, const uint4 (&v)[2])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0].x), "r"(v[0].y),
+                 "r"(v[0].z), "r"(v[0].w), "r"(v[1].x), "r"(v[1].y), "r"(v[1].z), "r"(v[1].w)
+                 : "memory");
+}
+
+template <int LOG2N>
+__device__ __forceinline__ void put_records(unsigned char *__restrict__ dst, uint4 *stg, int lane, bool valid,
+                                            int nrec, const uint4 (&rec_p)[2], const uint4 (&rec_m)[2])
+{
+    if constexpr (LOG2N < 0) {
+        if (valid) {
+            st_v8(dst + (size_t)lane * 64, rec_p);
+            st_v8(dst + (size_t)lane * 64 + 32, rec_m);
+        }
+    } else {
+        staging_free(lane);                          // the previous round's copy has read it
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                stg[lane * kRecUint4 + q] = rec_p[q];
+                stg[lane * kRecUint4 + 2 + q] = rec_m[q];
+            }
+        }
+        flush_records(dst, stg, nrec, lane);
+    }
+}
+
 // One 32-byte load (a whole sector per lane) through the read-only path; p 32-byte aligned.
 __device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
 {
@@ -533,6 +566,11 @@ __host__ __device__ constexpr int fft_smem_bytes(int n)
 // generic lengths (LOG2N = 0) hold radix-13 butterflies and their roots in registers.
 template <int LOG2N>
 __host__ __device__ constexpr int fft_blocks_per_sm() { return LOG2N == 12 ? 1 : (LOG2N == 11 || LOG2N == 0) ? 2 : 3; }
+// LOG2N: 6..12 the power-of-two engine at n = 2^LOG2N; 0 the generic stages with Bluestein
+// stages for primes from 17 up (record staging after the DFT); -1 the generic stages with
+// radices <= 13 only, compiled for three blocks per SM: the four rings (64 KB at n = 2002)
+// are then the whole shared-memory block, the forward kernel storing its records straight
+// from registers (put_records).
 
 // Inverse-side engine: the transpose of fft_p2_from_global's factorisation (the DFT matrix is
 // symmetric, so the stages taken in reverse order, each transposed, give the same
@@ -699,7 +737,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         fft_p2_from_global<LOG2N, false>(buf, tw, nr, ComplexRows{Tth, Tph, fb, j, jm, n});
     }
     // generic lengths: loads are issued in batches of kLoadBatch per thread before any is stored
-    for (int i0 = threadIdx.x; LOG2N == 0 && i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
+    for (int i0 = threadIdx.x; LOG2N <= 0 && i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
         float4 v[kLoadBatch];
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
@@ -719,9 +757,9 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
             }
         }
     }
-    if constexpr (LOG2N == 0) {
+    if constexpr (LOG2N <= 0) {
         __syncthreads();
-        dif_f32<false>(buf, tw, rp, nr,
+        dif_f32<false, LOG2N == 0>(buf, tw, rp, nr,
                        reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = omega[j];
@@ -756,18 +794,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
             pack_row_f32(vp, rec_p);
             pack_row_f32(vm, rec_m);
         }
-        staging_free(lane);                          // the previous round's copy has read it
-        if (mu <= L) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                stg[lane * kRecUint4 + q] = rec_p[q];
-                stg[lane * kRecUint4 + 2 + q] = rec_m[q];
-            }
-        }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
-        flush_records(dst_base + (size_t)mu0 * 64, stg, nrec, lane);
+        put_records<LOG2N>(dst_base + (size_t)mu0 * 64, stg, lane, mu <= L, nrec, rec_p, rec_m);
     }
-    staging_free(lane);                              // shared memory stays until the copies read it
+    if (LOG2N >= 0) staging_free(lane);              // shared memory stays until the copies read it
 }
 
 // The inverse kernels' sum records: the 32-byte records of latitude j (parities 0 and 1)
@@ -895,7 +925,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     if constexpr (LOG2N > 0) {
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, ComplexRowsOut{Tth, Tph, fb, j, jm, n});
     } else {
-        dif_f32<true>(buf, tw, rp, nr,
+        dif_f32<true, LOG2N == 0>(buf, tw, rp, nr,
                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_i4) + fft_smem_bytes<LOG2N>(n)));
         const int n2 = n / 2;
         for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
@@ -960,7 +990,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
     if constexpr (LOG2N > 0)
         fft_p2_from_global<LOG2N, false>(buf, tw, nr, RealPairRows{Tth, Tph, toff, q, B, nlat, j, jm, n});
     // generic lengths: kU vector pairs in flight per thread
-    for (int i0 = threadIdx.x; LOG2N == 0 && i0 < nr * nv; i0 += kU * kFftThreads) {
+    for (int i0 = threadIdx.x; LOG2N <= 0 && i0 < nr * nv; i0 += kU * kFftThreads) {
         float th[kU][V], ph[kU][V];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -988,9 +1018,9 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
             }
         }
     }
-    if constexpr (LOG2N == 0) {
+    if constexpr (LOG2N <= 0) {
         __syncthreads();
-        dif_f32<false>(buf, tw, rp, nr,
+        dif_f32<false, LOG2N == 0>(buf, tw, rp, nr,
                        reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)));
     }
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
@@ -1026,18 +1056,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
             pack_row_f32(vp, rec_p);
             pack_row_f32(vm, rec_m);
         }
-        staging_free(lane);                          // the previous round's copy has read it
-        if (mu <= L) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                stg[lane * kRecUint4 + c] = rec_p[c];
-                stg[lane * kRecUint4 + 2 + c] = rec_m[c];
-            }
-        }
         const int nrec = L + 1 - mu0 < 32 ? L + 1 - mu0 : 32;
-        flush_records(dst_base + (size_t)mu0 * 64, stg, nrec, lane);
+        put_records<LOG2N>(dst_base + (size_t)mu0 * 64, stg, lane, mu <= L, nrec, rec_p, rec_m);
     }
-    staging_free(lane);                              // shared memory stays until the copies read it
+    if (LOG2N >= 0) staging_free(lane);              // shared memory stays until the copies read it
 }
 
 // Real fields, inverse: for field f of the pair, the spectrum of z = T_th + i T_ph is
@@ -1095,7 +1117,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
         return;
     }
-    dif_f32<true>(buf, tw, rp, nr,
+    dif_f32<true, LOG2N == 0>(buf, tw, rp, nr,
                   reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_s4) + fft_smem_bytes<LOG2N>(n)));
     const int nv = n / V;
     for (int idx = threadIdx.x; idx < nr * nv; idx += blockDim.x) {
@@ -1124,7 +1146,7 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
     RadixPlanArg rp = make_radix_arg(p.fft);
     // record staging after the DFT; the Bluestein scratch (during the DFT) shares its space
     const size_t blue = p.fft.blue_scratch;
-    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (blue > kStageBytes ? blue : kStageBytes);
+    const size_t smem = (size_t)fft_smem_bytes<LOG2N>(p.nphi) + (LOG2N < 0 ? 0 : blue > kStageBytes ? blue : kStageBytes);
     if (p.real) {
         auto k = k_rfft_fwd_bf16<LOG2N>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1174,7 +1196,7 @@ cudaError_t launch_fft_fwd_bf16(const Plan &p, const void *Tth, const void *Tph,
     case 10: return launch_fwd_t<10>(p, Tth, Tph, s);
     case 11: return launch_fwd_t<11>(p, Tth, Tph, s);
     case 12: return launch_fwd_t<12>(p, Tth, Tph, s);
-    default: return launch_fwd_t<0>(p, Tth, Tph, s);
+    default: return p.fft.blue_scratch ? launch_fwd_t<0>(p, Tth, Tph, s) : launch_fwd_t<-1>(p, Tth, Tph, s);
     }
 }
 
@@ -1188,7 +1210,7 @@ cudaError_t launch_fft_inv_bf16(const Plan &p, void *Tth, void *Tph, cudaStream_
     case 10: return launch_inv_t<10>(p, Tth, Tph, s);
     case 11: return launch_inv_t<11>(p, Tth, Tph, s);
     case 12: return launch_inv_t<12>(p, Tth, Tph, s);
-    default: return launch_inv_t<0>(p, Tth, Tph, s);
+    default: return p.fft.blue_scratch ? launch_inv_t<0>(p, Tth, Tph, s) : launch_inv_t<-1>(p, Tth, Tph, s);
     }
 }
 
