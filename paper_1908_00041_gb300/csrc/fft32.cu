@@ -66,9 +66,9 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
 {
     constexpr int H = (R - 1) / 2;
     const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
-    float2 wr[R];                                      // w_R^j = w_n^{j n / R}
+    float2 wr[H + 1];                                  // w_R^j = w_n^{j n / R}, j <= H
 #pragma unroll
-    for (int j = 0; j < R; ++j) wr[j] = twf<INV>(tw, j * rstep);
+    for (int j = 1; j <= H; ++j) wr[j] = twf<INV>(tw, j * rstep);
     const Recip rn = recip(nbf), rh = recip(h);
     for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
         const int ring = rdiv(t, rn), i = t - ring * nbf;
@@ -91,11 +91,14 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
             float2 A = v0, Bq = make_float2(0.f, 0.f);
 #pragma unroll
             for (int r = 1; r <= H; ++r) {
-                const float2 w = wr[(q * r) % R];
-                A.x = fmaf(w.x, sm[r - 1].x, A.x);
-                A.y = fmaf(w.x, sm[r - 1].y, A.y);
-                Bq.x = fmaf(w.y, df[r - 1].x, Bq.x);
-                Bq.y = fmaf(w.y, df[r - 1].y, Bq.y);
+                // w_R^{qr}: index e = qr mod R, and w_R^e = conj(w_R^{R-e}) above H
+                const int e = (q * r) % R;
+                const float wc = e <= H ? wr[e].x : wr[R - e].x;
+                const float ws = e <= H ? wr[e].y : -wr[R - e].y;
+                A.x = fmaf(wc, sm[r - 1].x, A.x);
+                A.y = fmaf(wc, sm[r - 1].y, A.y);
+                Bq.x = fmaf(ws, df[r - 1].x, Bq.x);
+                Bq.y = fmaf(ws, df[r - 1].y, Bq.y);
             }
             const float2 op = make_float2(A.x - Bq.y, A.y + Bq.x);     // A + i B
             const float2 om = make_float2(A.x + Bq.y, A.y - Bq.x);     // A - i B
@@ -372,12 +375,15 @@ __device__ __forceinline__ void dif_stage_bluestein(float2 *x, const float2 *__r
 
 // sc: the Bluestein scratch (FftPlan::blue_scratch bytes) when the plan has such stages;
 // BLUE = false compiles without the Bluestein branch (plans whose radices are all <= 13)
+// st0: the first stage to run (the stages before it already done, see first_stage_global)
 template <bool INV, bool BLUE>
-__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc)
+__device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, float2 *sc,
+                        int st0 = 0)
 {
     const int n = rp.n;
     int Nb = n;
-    for (int st = 0; st < rp.nstages; ++st) {
+    for (int st = 0; st < st0; ++st) Nb /= rp.radix[st];
+    for (int st = st0; st < rp.nstages; ++st) {
         const int R = rp.radix[st];
         const int h = Nb / R;
         const int ts = n / Nb;
@@ -420,6 +426,150 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
         __syncthreads();
         Nb = h;
     }
+}
+
+// Decimation in time, the transpose of dif_f32 (the DFT matrix is symmetric): with the
+// decimation-in-frequency transform written as F = P S_{S-1} .. S_1 S_0 (stage S_s:
+// butterflies, then the output twiddles; P: the digit-reversal gather), F = F^T =
+// S_0^T .. S_{S-1}^T P^T, where P^T scatters frequency m to position perm[m] and S_s^T
+// multiplies the same twiddles into a butterfly's inputs before the same R-point DFT.
+// dit_f32 runs S_{S-1}^T .. S_{st_end}^T in place; last_stage_global runs S_0^T (radix 2 or
+// 4, block length n), whose outputs k + q h are in natural order, straight to global memory.
+// Radices 2, 4 and the odd primes 3..13 (plans without Bluestein stages).
+template <int R, bool INV>
+__device__ __forceinline__ void dit_stage_small(float2 *x, const float2 *__restrict__ tw, int n, int Nb, int nr)
+{
+    constexpr int H = (R - 1) / 2;
+    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
+    float2 wr[H + 1];                                  // w_R^j, j <= H
+#pragma unroll
+    for (int j = 1; j <= H; ++j) wr[j] = twf<INV>(tw, j * rstep);
+    const Recip rn = recip(nbf), rh = recip(h);
+    for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+        const int ring = rdiv(t, rn), i = t - ring * nbf;
+        const int blk = rdiv(i, rh), k = i - blk * h;
+        float2 *xr = x + ring * n + blk * Nb + k;
+        const int tk = k * ts;
+        const float2 v0 = xr[0];
+        float2 sm[H], df[H];
+        float2 out0 = v0;
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            const float2 a = cmulf(xr[r * h], twf<INV>(tw, r * tk));
+            const float2 b = cmulf(xr[(R - r) * h], twf<INV>(tw, (R - r) * tk));
+            sm[r - 1] = caddf(a, b);
+            df[r - 1] = csubf(a, b);
+            out0 = caddf(out0, sm[r - 1]);
+        }
+        xr[0] = out0;
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            float2 A = v0, Bq = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 1; r <= H; ++r) {
+                const int e = (q * r) % R;
+                const float wc = e <= H ? wr[e].x : wr[R - e].x;
+                const float ws = e <= H ? wr[e].y : -wr[R - e].y;
+                A.x = fmaf(wc, sm[r - 1].x, A.x);
+                A.y = fmaf(wc, sm[r - 1].y, A.y);
+                Bq.x = fmaf(ws, df[r - 1].x, Bq.x);
+                Bq.y = fmaf(ws, df[r - 1].y, Bq.y);
+            }
+            xr[q * h] = make_float2(A.x - Bq.y, A.y + Bq.x);         // A + i B
+            xr[(R - q) * h] = make_float2(A.x + Bq.y, A.y - Bq.x);   // A - i B
+        }
+    }
+}
+
+// radix-4 / radix-2 butterflies of a decimation-in-time stage on inputs v (twiddled)
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 (&v)[4])
+{
+    const float2 s02 = caddf(v[0], v[2]), d02 = csubf(v[0], v[2]);
+    const float2 s13 = caddf(v[1], v[3]), d13 = csubf(v[1], v[3]);
+    const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+    v[0] = caddf(s02, s13);
+    v[1] = caddf(d02, rot);
+    v[2] = csubf(s02, s13);
+    v[3] = csubf(d02, rot);
+}
+
+template <bool INV>
+__device__ void dit_f32(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp, int nr, int st_end)
+{
+    const int n = rp.n;
+    for (int st = rp.nstages - 1; st >= st_end; --st) {
+        int Nb = n;
+        for (int s2 = 0; s2 < st; ++s2) Nb /= rp.radix[s2];
+        const int R = rp.radix[st];
+        if (R == 3) {
+            dit_stage_small<3, INV>(x, tw, n, Nb, nr);
+        } else if (R == 5) {
+            dit_stage_small<5, INV>(x, tw, n, Nb, nr);
+        } else if (R == 7) {
+            dit_stage_small<7, INV>(x, tw, n, Nb, nr);
+        } else if (R == 11) {
+            dit_stage_small<11, INV>(x, tw, n, Nb, nr);
+        } else if (R == 13) {
+            dit_stage_small<13, INV>(x, tw, n, Nb, nr);
+        } else {
+            const int h = Nb / R, ts = n / Nb, nbf = n / R;
+            const Recip rn = recip(nbf), rh = recip(h);
+            for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
+                const int ring = rdiv(t, rn), i = t - ring * nbf;
+                const int blk = rdiv(i, rh), k = i - blk * h;
+                float2 *xr = x + ring * n + blk * Nb + k;
+                if (R == 4) {
+                    float2 v[4] = {xr[0], cmulf(xr[h], twf<INV>(tw, k * ts)), cmulf(xr[2 * h], twf<INV>(tw, 2 * k * ts)),
+                                   cmulf(xr[3 * h], twf<INV>(tw, 3 * k * ts))};
+                    dft4<INV>(v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) xr[q * h] = v[q];
+                } else {
+                    const float2 v0 = xr[0], v1 = cmulf(xr[h], twf<INV>(tw, k * ts));
+                    xr[0] = caddf(v0, v1);
+                    xr[h] = csubf(v0, v1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// S_0^T (radix R1 = 4 or 2, block length n, h = n / R1) from shared memory to sink.store:
+// butterfly k of ring r writes the natural-order points k + q h, so across a warp every
+// store covers consecutive positions.
+template <int R1, bool INV, typename Sink>
+__device__ void last_stage_global(const float2 *x, const float2 *__restrict__ tw, int n, int nr, const Sink &sink)
+{
+    const int h = n / R1;
+    const Recip rh = recip(h);
+    for (int t = threadIdx.x; t < h * nr; t += kFftThreads) {
+        const int ring = rdiv(t, rh), k = t - ring * h;
+        const float2 *xr = x + ring * n + k;
+        const auto rw = sink.row(ring);
+        if constexpr (R1 == 4) {
+            float2 v[4] = {xr[0], cmulf(xr[h], twf<INV>(tw, k)), cmulf(xr[2 * h], twf<INV>(tw, 2 * k)),
+                           cmulf(xr[3 * h], twf<INV>(tw, 3 * k))};
+            dft4<INV>(v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sink.store(rw, k + q * h, v[q]);
+        } else {
+            const float2 v0 = xr[0], v1 = cmulf(xr[h], twf<INV>(tw, k));
+            sink.store(rw, k, caddf(v0, v1));
+            sink.store(rw, k + h, csubf(v0, v1));
+        }
+    }
+}
+
+template <bool INV, typename Sink>
+__device__ __forceinline__ void last_stage_global(const float2 *x, const float2 *__restrict__ tw,
+                                                  const RadixPlanArg &rp, int nr, const Sink &sink)
+{
+    if (rp.radix[0] == 4)
+        last_stage_global<4, INV>(x, tw, rp.n, nr, sink);
+    else
+        last_stage_global<2, INV>(x, tw, rp.n, nr, sink);
 }
 
 // Full transform of nr rings, natural order in and out, by the factorisation
@@ -548,7 +698,6 @@ __device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
                  : "l"(p));
 }
 
-constexpr int kLoadBatch = 8;    // independent global loads per thread in flight
 constexpr int kInvOrders = 2;    // orders per thread whose inverse-DFT inputs are loaded at once
                                  // (4 measured slower at n = 2048 and spill at 3 blocks per SM)
 
@@ -683,6 +832,64 @@ struct RealPairRows {
     }
 };
 
+// Generic lengths: the first decimation-in-frequency stage fed straight from global memory
+// through src (as fft_p2_from_global does for powers of two).  n = 2(L+1) is even, so the
+// factorisation (4s first, then a 2) always starts with radix R1 = 4 or 2; block length n,
+// h = n / R1, butterfly k of ring r takes the points k + q h and writes them back scaled
+// by w_n^{q k}.  kPer butterflies per thread have their loads in flight together.  Returns
+// after a barrier; dif_f32 continues from stage 1.
+template <int R1, bool INV, typename Src>
+__device__ void first_stage_global(float2 *x, const float2 *__restrict__ tw, int n, int nr, const Src &src)
+{
+    constexpr int kPer = 1;      // measured: 2 or 4 butterflies per thread spill at 80 registers and run slower
+    const int h = n / R1;
+    const Recip rh = recip(h);
+    for (int t0 = threadIdx.x; t0 < h * nr; t0 += kPer * kFftThreads) {
+        float2 v[kPer][R1];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int t = t0 + u * kFftThreads;
+            if (t < h * nr) {
+                const int ring = rdiv(t, rh), k = t - ring * h;
+                const auto rw = src.row(ring);
+#pragma unroll
+                for (int q = 0; q < R1; ++q) v[u][q] = src.load(rw, k + q * h);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int t = t0 + u * kFftThreads;
+            if (t < h * nr) {
+                const int ring = rdiv(t, rh), k = t - ring * h;
+                float2 *xr = x + ring * n + k;
+                if constexpr (R1 == 4) {
+                    const float2 s02 = caddf(v[u][0], v[u][2]), d02 = csubf(v[u][0], v[u][2]);
+                    const float2 s13 = caddf(v[u][1], v[u][3]), d13 = csubf(v[u][1], v[u][3]);
+                    const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+                    xr[0] = caddf(s02, s13);
+                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k));
+                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k));
+                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k));
+                } else {
+                    xr[0] = caddf(v[u][0], v[u][1]);
+                    xr[h] = cmulf(csubf(v[u][0], v[u][1]), twf<INV>(tw, k));
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <bool INV, typename Src>
+__device__ __forceinline__ void first_stage_global(float2 *x, const float2 *__restrict__ tw, const RadixPlanArg &rp,
+                                                   int nr, const Src &src)
+{
+    if (rp.radix[0] == 4)
+        first_stage_global<4, INV>(x, tw, rp.n, nr, src);
+    else
+        first_stage_global<2, INV>(x, tw, rp.n, nr, src);
+}
+
 // ring sinks of the inverse kernels, the counterparts of the sources above
 struct ComplexRowsOut {
     float2 *th, *ph;
@@ -731,36 +938,17 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;    // rings: (th, j), (ph, j), (th, j'), (ph, j')
     const int jm = nlat - 1 - j;
-    const int n2 = n / 2;         // float4 per ring
     const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;   // field b's plane
     if constexpr (LOG2N > 0) {
         fft_p2_from_global<LOG2N, false>(buf, tw, nr, ComplexRows{Tth, Tph, fb, j, jm, n});
     }
-    // generic lengths: loads are issued in batches of kLoadBatch per thread before any is stored
-    for (int i0 = threadIdx.x; LOG2N <= 0 && i0 < nr * n2; i0 += kLoadBatch * kFftThreads) {
-        float4 v[kLoadBatch];
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-            const int idx = i0 + u * kFftThreads;
-            if (idx < nr * n2) {
-                const int ring = idx / n2, k2 = idx % n2;
-                const float2 *src = (ring & 1) ? Tph : Tth;
-                const int jj = (ring < 2) ? j : jm;
-                v[u] = __ldg(reinterpret_cast<const float4 *>(src + fb + (size_t)jj * n) + k2);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-            const int idx = i0 + u * kFftThreads;
-            if (idx < nr * n2) {
-                sm_f4[idx] = v[u];
-            }
-        }
-    }
     if constexpr (LOG2N <= 0) {
-        __syncthreads();
+        // generic lengths: the first stage reads the rings, the others run in shared memory
+        first_stage_global<false>(buf, tw, rp, nr, ComplexRows{Tth, Tph, fb, j, jm, n});
         dif_f32<false, LOG2N == 0>(buf, tw, rp, nr,
-                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_f4) + fft_smem_bytes<LOG2N>(n)));
+                                   reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_f4) +
+                                                              fft_smem_bytes<LOG2N>(n)),
+                                   1);
     }
     const float w = omega[j];
     // Fb[j/8][field][j%8][mu][parity][8 floats]: this CTA's block is contiguous over mu (the
@@ -894,22 +1082,23 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     // weighted adjoint (isc[j] = (scale, weight))
     const float2 sc2 = __ldg(isc + j);
     const float is = sc2.x, w0 = sc2.y;
-    if (LOG2N > 0) {
-        // every bin but n/2 is written below
-        if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
-    } else {
-        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
-        __syncthreads();
+    // every bin but n/2 is written below (n = 2(L+1): orders 0..L at bins mu and n - mu);
+    // the decimation-in-time variant (LOG2N < 0) takes bin m at position perm[m]
+    if (threadIdx.x < nr) {
+        const int i = threadIdx.x * n + (LOG2N < 0 ? __ldg(perm + n / 2) : n / 2);
+        buf[LOG2N > 0 ? padi(i) : i] = make_float2(0.f, 0.f);
     }
     auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
         // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
         const float sc = mu == 0 ? w0 : is;
+        const int pp = LOG2N < 0 ? __ldg(perm + mu) : mu;
+        const int pm = LOG2N < 0 ? (mu == 0 ? 0 : __ldg(perm + n - mu)) : n - mu;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
             for (int sgn = 0; sgn < 2; ++sgn) {
                 if (mu == 0 && sgn == 1) continue;
-                const int bin = sgn ? n - mu : mu;
+                const int bin = sgn ? pm : pp;
                 const int k = c * 4 + sgn * 2;
                 const int i0 = c * n + bin, i1 = (2 + c) * n + bin;
                 buf[LOG2N > 0 ? padi(i0) : i0] = make_float2((ev[k] + ov[k]) * sc, (ev[k + 1] + ov[k + 1]) * sc);
@@ -924,12 +1113,16 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
     if constexpr (LOG2N > 0) {
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, ComplexRowsOut{Tth, Tph, fb, j, jm, n});
+    } else if constexpr (LOG2N < 0) {
+        dit_f32<true>(buf, tw, rp, nr, 1);
+        last_stage_global<true>(buf, tw, rp, nr, ComplexRowsOut{Tth, Tph, fb, j, jm, n});
     } else {
         dif_f32<true, LOG2N == 0>(buf, tw, rp, nr,
                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_i4) + fft_smem_bytes<LOG2N>(n)));
         const int n2 = n / 2;
+        const Recip rn2 = recip(n2);
         for (int idx = threadIdx.x; idx < nr * n2; idx += blockDim.x) {
-            const int ring = idx / n2, k2 = idx % n2;
+            const int ring = rdiv(idx, rn2), k2 = idx - ring * n2;
             const float2 v0 = buf[ring * n + __ldg(perm + 2 * k2)];
             const float2 v1 = buf[ring * n + __ldg(perm + 2 * k2 + 1)];
             float2 *dst = (ring & 1) ? Tph : Tth;
@@ -979,49 +1172,20 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
 {
     extern __shared__ float4 sm_r4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_r4);
-    constexpr int V = 2;
-    constexpr int kU = kLoadBatch / 2;             // vector pairs (th, ph) in flight per thread
     const int n = rp.n;
     const int q = blockIdx.x / J, j = blockIdx.x % J;
     const bool eq = has_eq && j == J - 1;
     const int nr = eq ? 2 : 4;    // rings: (2q, j), (2q+1, j), (2q, j'), (2q+1, j')
     const int jm = nlat - 1 - j;
-    const int nv = n / V;
     if constexpr (LOG2N > 0)
         fft_p2_from_global<LOG2N, false>(buf, tw, nr, RealPairRows{Tth, Tph, toff, q, B, nlat, j, jm, n});
-    // generic lengths: kU vector pairs in flight per thread
-    for (int i0 = threadIdx.x; LOG2N <= 0 && i0 < nr * nv; i0 += kU * kFftThreads) {
-        float th[kU][V], ph[kU][V];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int idx = i0 + u * kFftThreads;
-#pragma unroll
-            for (int i = 0; i < V; ++i) th[u][i] = ph[u][i] = 0.f;
-            if (idx < nr * nv) {
-                const int ring = idx / nv, kv = idx % nv;
-                const int bf = 2 * q + (ring & 1);
-                if (bf < B) {
-                    const size_t fb = toff ? (size_t)toff[bf] : (size_t)bf * nlat * n;   // field's plane
-                    const size_t off = fb + (size_t)(ring < 2 ? j : jm) * n + (size_t)kv * V;
-                    load_v<V>(Tth + off, th[u]);
-                    load_v<V>(Tph + off, ph[u]);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int idx = i0 + u * kFftThreads;
-            if (idx < nr * nv) {
-                const int ring = idx / nv, kv = idx % nv;
-#pragma unroll
-                for (int i = 0; i < V; ++i) buf[ring * n + kv * V + i] = make_float2(th[u][i], ph[u][i]);
-            }
-        }
-    }
     if constexpr (LOG2N <= 0) {
-        __syncthreads();
+        // generic lengths: the first stage reads the rings, the others run in shared memory
+        first_stage_global<false>(buf, tw, rp, nr, RealPairRows{Tth, Tph, toff, q, B, nlat, j, jm, n});
         dif_f32<false, LOG2N == 0>(buf, tw, rp, nr,
-                       reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_r4) + fft_smem_bytes<LOG2N>(n)));
+                                   reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_r4) +
+                                                              fft_smem_bytes<LOG2N>(n)),
+                                   1);
     }
     const float w = 0.5f * omega[j];             // the 1/2 of the component split folded in
     unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + q) * 8 + (j % 8)) * (L + 1)) * 64;
@@ -1082,14 +1246,15 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
     const int nr = eq ? 2 : 4;
     const float2 sc2 = __ldg(isc + j);
     const float is = sc2.x, w0 = sc2.y;
-    if (LOG2N > 0) {
-        if (threadIdx.x < nr) buf[padi(threadIdx.x * n + n / 2)] = make_float2(0.f, 0.f);
-    } else {
-        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf[idx] = make_float2(0.f, 0.f);
-        __syncthreads();
+    // every bin but n/2 is written below (at position perm[m] for LOG2N < 0, as above)
+    if (threadIdx.x < nr) {
+        const int i = threadIdx.x * n + (LOG2N < 0 ? __ldg(perm + n / 2) : n / 2);
+        buf[LOG2N > 0 ? padi(i) : i] = make_float2(0.f, 0.f);
     }
     auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
         const float sc = mu == 0 ? w0 : is;
+        const int pp = LOG2N < 0 ? __ldg(perm + mu) : mu;
+        const int pm = LOG2N < 0 ? (mu == 0 ? 0 : __ldg(perm + n - mu)) : n - mu;
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
 #pragma unroll
@@ -1101,9 +1266,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
                 const float gpx = (ev[kp] + sg * ov[kp]) * sc, gpy = (ev[kp + 1] + sg * ov[kp + 1]) * sc;
                 const int rb = (2 * side + f) * n;
                 if (mu == 0) {
-                    buf[LOG2N > 0 ? padi(rb) : rb] = make_float2(gtx, gpx);
+                    const int i0 = rb + pp;
+                    buf[LOG2N > 0 ? padi(i0) : i0] = make_float2(gtx, gpx);
                 } else {
-                    const int i0 = rb + mu, i1 = rb + n - mu;
+                    const int i0 = rb + pp, i1 = rb + pm;
                     buf[LOG2N > 0 ? padi(i0) : i0] = make_float2(gtx - gpy, gty + gpx);
                     buf[LOG2N > 0 ? padi(i1) : i1] = make_float2(gtx + gpy, gpx - gty);
                 }
@@ -1117,11 +1283,17 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         fft_p2_to_global<LOG2N, true>(buf, tw, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
         return;
     }
+    if constexpr (LOG2N < 0) {
+        dit_f32<true>(buf, tw, rp, nr, 1);
+        last_stage_global<true>(buf, tw, rp, nr, RealPairRowsOut{Tth, Tph, toff, q, B, nlat, j, jm, n});
+        return;
+    }
     dif_f32<true, LOG2N == 0>(buf, tw, rp, nr,
                   reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_s4) + fft_smem_bytes<LOG2N>(n)));
     const int nv = n / V;
+    const Recip rnv = recip(nv);
     for (int idx = threadIdx.x; idx < nr * nv; idx += blockDim.x) {
-        const int ring = idx / nv, kv = idx % nv;
+        const int ring = rdiv(idx, rnv), kv = idx - ring * nv;
         const int bf = 2 * q + (ring & 1);
         if (bf >= B) continue;
         float th[V], ph[V];
