@@ -388,8 +388,8 @@ int favest_batch_create(int nfields, const int *L, const long long *field_off, c
         bp->n_items_a = (int)ita.size();
         if (upload_vec(&bp->d_gg, gg) != cudaSuccess || upload_vec(&bp->d_items_f, itf) != cudaSuccess ||
             upload_vec(&bp->d_items_a, ita) != cudaSuccess ||
-            plan_malloc((void **)&bp->d_status, sizeof(int)) != cudaSuccess ||
-            cudaMemset(bp->d_status, 0, sizeof(int)) != cudaSuccess)
+            plan_malloc((void **)&bp->d_status, kStatusWords * sizeof(int)) != cudaSuccess ||
+            cudaMemset(bp->d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess)
             st = FAVEST_ENOMEM;
     }
     if (st == FAVEST_OK && cudaStreamCreateWithFlags(&bp->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -569,12 +569,30 @@ int alloc_workspace_bf16(Plan &p)
             }
         }
     }
-    // Heaviest adjoint items first (measured: better than keeping the latitude tiles of an
-    // order adjacent); the forward items keep (order, parity, row tile) order, so that the
-    // row tiles of one order, which read the same B operand, run at the same time on
-    // neighbouring CTAs and share it through L2 (measured: sorting them by K depth cost
-    // 30% of the forward GEMM's time).
-    std::stable_sort(ita.begin(), ita.end(), [](const TcItem &x, const TcItem &y) { return x.nk > y.nk; });
+    // The GEMMs' CTAs take the listed items in order as they free up (see legendre_tc.cu),
+    // so the order decides which items run together.  Forward: (order,
+    // parity, row tile), so that the row tiles of one order, which read the same B operand,
+    // run at the same time on neighbouring CTAs and share it through L2.  Adjoint: the
+    // latitude tiles of one (order, parity), which read the same coefficient operand over
+    // different K depths (turning-point skip), kept together, the groups in decreasing order
+    // of their deepest tile.
+    {
+        const size_t per = (size_t)(p.JP / 128) * p.n_tiles;   // items of one (order, parity)
+        const size_t ng = ita.size() / per;
+        std::vector<int> gmax(ng), gi(ng);
+        for (size_t g = 0; g < ng; ++g) {
+            int m = 0;
+            for (size_t u = 0; u < per; ++u) m = std::max(m, ita[g * per + u].nk);
+            gmax[g] = m;
+            gi[g] = (int)g;
+        }
+        std::stable_sort(gi.begin(), gi.end(), [&](int a, int b) { return gmax[a] > gmax[b]; });
+        std::vector<TcItem> grouped;
+        grouped.reserve(ita.size());
+        for (int g : gi)
+            for (size_t u = 0; u < per; ++u) grouped.push_back(ita[g * per + u]);
+        ita.swap(grouped);
+    }
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
     const size_t lamf_bytes = (size_t)lam_f, lama_bytes = (size_t)lam_a;
@@ -585,7 +603,7 @@ int alloc_workspace_bf16(Plan &p)
         plan_malloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         plan_malloc(&p.d_gb, (size_t)gsz) != cudaSuccess || plan_malloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
         plan_malloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
-        plan_malloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+        plan_malloc((void **)&p.d_status, kStatusWords * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
@@ -594,7 +612,8 @@ int alloc_workspace_bf16(Plan &p)
     // are never written afterwards
     if (cudaMemset(p.d_lam_f, 0, lamf_bytes) != cudaSuccess || cudaMemset(p.d_lam_a, 0, lama_bytes) != cudaSuccess ||
         cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
-        cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess || cudaMemset(p.d_status, 0, sizeof(int)) != cudaSuccess)
+        cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess ||
+        cudaMemset(p.d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess)
         return FAVEST_ECUDA;
     cudaError_t e;
     if ((e = upload(&p.d_lam_off_f, off_f)) || (e = upload(&p.d_lam_off_a, off_a)) ||
@@ -634,11 +653,11 @@ int alloc_workspace(Plan &p)
     size_t gbytes = p.scattered ? 0 : (size_t)(p.real ? p.ncol : p.ncol / 2) * p.nlat * p.nphi * sizeof(double2);
     if ((fbytes && plan_malloc(&p.d_F, fbytes) != cudaSuccess) || plan_malloc(&p.d_Q, qbytes) != cudaSuccess ||
         (gbytes && plan_malloc(&p.d_G, gbytes) != cudaSuccess) ||
-        plan_malloc((void **)&p.d_status, sizeof(int)) != cudaSuccess) {
+        plan_malloc((void **)&p.d_status, kStatusWords * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
-    cudaMemset(p.d_status, 0, sizeof(int));
+    cudaMemset(p.d_status, 0, kStatusWords * sizeof(int));
     // the padding columns (an odd count of scalar or real fields) read as zero
     if ((p.nscal > 0 || p.real) &&
         (cudaMemset(p.d_Q, 0, qbytes) != cudaSuccess || (fbytes && cudaMemset(p.d_F, 0, fbytes) != cudaSuccess)))

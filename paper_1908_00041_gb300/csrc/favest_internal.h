@@ -54,6 +54,11 @@ struct FftPlan {
 };
 
 constexpr int kGemmChunkK = 32;   // K depth of one tensor-core operand chunk
+// Device status words of a plan or ragged batch: [0] the status (0 or a FAVEST_E* code),
+// [1..2] the forward GEMM's item scheduler, [3..4] the adjoint's (next item, CTAs done;
+// zero between launches: the last CTA of a launch resets them).
+constexpr int kStatusWords = 5;
+inline int *gemm_sched(int *status, bool fwd) { return status + (fwd ? 1 : 3); }
 constexpr int kInvChunk = 256;    // orders per TMA box of the inverse DFT's sum records (16 KB)
 
 // One tensor-core GEMM work item: out[rows][N] = sum over nk K-chunks of A_c * B_c, each
@@ -130,7 +135,7 @@ struct Plan {
     double *d_P = nullptr;        // [ntab] combine coefficient P_l^mu
     double *d_M = nullptr;        // [ntab] combine coefficient M_l^mu
     double *d_R = nullptr;        // [ntab] combine coefficient R_l^mu
-    int *d_status = nullptr;      // device status word
+    int *d_status = nullptr;      // device status words (kStatusWords)
 
     // split-precision (BF16X6) path
     int JP = 0;               // folded latitudes padded to a multiple of 128

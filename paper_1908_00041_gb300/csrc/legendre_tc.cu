@@ -228,17 +228,6 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
 constexpr int kStages = 3;
 constexpr uint32_t kTmemCols = 512;
 
-template <int N>
-struct GemmSmem {
-    unsigned char a[kStages][kChunkBytes];
-    unsigned char b[kStages][kPieces * kChunkK * N * 2];
-    uint64_t full[kStages], empty[kStages];
-    uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
-    uint64_t drain;            // abort path: completion of the MMA warp's last issued MMAs
-    uint32_t tmem_base;
-    int abort;
-};
-
 constexpr int kEpiCols = 128;       // TMEM columns drained by one epilogue warp
 
 template <int N>
@@ -263,10 +252,84 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     return false;
 }
 
+// Work items are handed out at run time: the producer thread of each CTA takes the next
+// item index from a device counter (sched[0]) and publishes it in a ring of kItemSlots
+// shared-memory slots; every consumer role reads the indices from the ring in the same
+// order and releases a slot once it has read it.  A taken index at or past the item count
+// is published as -1, which ends every role's loop.  A CTA takes the next listed item as
+// soon as it is free (greedy list scheduling), so the load stays balanced whatever the
+// host's order, and the host lists items that share an operand next to each other (they
+// then run at the same time on the CTAs that free up together), heavier groups first.
+// The last CTA to finish resets sched[0..1] for the next launch.
+constexpr int kItemSlots = 4;
+
+struct ItemRing {
+    int q[kItemSlots];
+    uint64_t full[kItemSlots], empty[kItemSlots];
+};
+
+__device__ __forceinline__ void item_ring_init(ItemRing &R, int consumers)
+{
+    for (int s = 0; s < kItemSlots; ++s) {
+        tc::mbar_init(&R.full[s], 1);
+        tc::mbar_init(&R.empty[s], consumers);
+    }
+}
+
+// producer: publishes the n-th index of this CTA into slot n % kItemSlots; false if the
+// wait for the slot gave up
+__device__ __forceinline__ bool item_publish(ItemRing &R, uint32_t n, int *sched, int nitems, volatile int *abort,
+                                             uint32_t limit, int &it)
+{
+    const int s = n % kItemSlots;
+    if (!wait_or_abort(&R.empty[s], ((n / kItemSlots) & 1) ^ 1, abort, limit)) return false;
+    it = atomicAdd(sched, 1);
+    if (it >= nitems) it = -1;
+    R.q[s] = it;
+    tc::mbar_arrive(&R.full[s]);     // release: the index is visible to the slot's waiters
+    return true;
+}
+
+// consumer: waits for the n-th index (false if the wait gave up); the caller releases the
+// slot with item_release once every thread of its role has read it
+__device__ __forceinline__ bool item_take(ItemRing &R, uint32_t n, volatile int *abort, uint32_t limit, int &it)
+{
+    const int s = n % kItemSlots;
+    if (!wait_or_abort(&R.full[s], (n / kItemSlots) & 1, abort, limit)) return false;
+    it = *reinterpret_cast<volatile int *>(&R.q[s]);
+    return true;
+}
+
+__device__ __forceinline__ void item_release(ItemRing &R, uint32_t n) { tc::mbar_arrive(&R.empty[n % kItemSlots]); }
+
+// after the CTA's last item (called by the producer thread, after the final barrier): the
+// last CTA of the launch resets the counters; every CTA has taken its last index by then
+__device__ __forceinline__ void item_sched_done(int *sched)
+{
+    __threadfence();
+    if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
+        sched[0] = 0;
+        sched[1] = 0;
+        __threadfence();
+    }
+}
+
+template <int N>
+struct GemmSmem {
+    unsigned char a[kStages][kChunkBytes];
+    unsigned char b[kStages][kPieces * kChunkK * N * 2];
+    uint64_t full[kStages], empty[kStages];
+    uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
+    uint64_t drain;            // abort path: completion of the MMA warp's last issued MMAs
+    ItemRing ring;
+    uint32_t tmem_base;
+    int abort;
+};
+
 template <int N>
 __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     const GemmGroup *__restrict__ groups, const TcItem *__restrict__ items, int nitems, int a_mn_major,
-    int *__restrict__ status, uint32_t poll_limit, int skip_loads)
+    int *__restrict__ status, int *__restrict__ sched, uint32_t poll_limit, int skip_loads)
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);   // 4 lane quadrants x N / 128 column parts
     constexpr int kPieceB = kChunkK * N * 2;        // bytes of one B piece per chunk
@@ -286,6 +349,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
         tc::mbar_init(&S.dcorr_full, 1);
         tc::mbar_init(&S.dcorr_empty, kEpiWarps);
         tc::mbar_init(&S.drain, 1);
+        item_ring_init(S.ring, 1 + kEpiWarps);        // consumers: the MMA thread, the epilogue warps
         S.abort = 0;
         tc::mbar_fence_init();
     }
@@ -299,11 +363,19 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
         // ---------------- producer ----------------
         // (skip_loads: failure-path self-test -- nothing is loaded, so the MMA and epilogue
         // waits must run out, report FAVEST_ETIMEOUT and return)
-        if (lane == 0 && !skip_loads) {
+        if (lane == 0) {
             uint32_t phase = 0;                     // bit s: parity of stage s's next use
             uint32_t issued = 0;                    // bit s: stage s has been loaded at least once
             int stage = 0;
-            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            for (uint32_t n = 0; !*abort; ++n) {
+                int it;
+                if (!item_publish(S.ring, n, sched, nitems, abort, poll_limit, it)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                if (it < 0) break;
+                if (skip_loads) continue;
                 const TcItem I = items[it];
                 // the group's tensor maps live in global memory (generic addresses)
                 const CUtensorMap *tmap_a = &groups[I.group].tmap_a, *tmap_b = &groups[I.group].tmap_b;
@@ -352,7 +424,15 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
             const uint32_t a_step = a_mn_major ? 4096u : 256u;
             const uint32_t a_lbo = a_mn_major ? 2048u : 128u, a_sbo = a_mn_major ? 128u : kChunkK / 8 * 128u;
             constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
-            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            for (uint32_t n = 0; !*abort; ++n) {
+                int it;
+                if (!item_take(S.ring, n, abort, poll_limit, it)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                item_release(S.ring, n);
+                if (it < 0) break;
                 const TcItem I = items[it];
                 if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort, poll_limit)) {
                     set_status(status, FAVEST_ETIMEOUT);
@@ -419,7 +499,17 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t main_use = 0, corr_use = 0;
         float acc[kEpiCols];
-        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+        for (uint32_t n = 0; !*abort; ++n) {
+            int it = -1;
+            const bool got = __all_sync(0xffffffffu, item_take(S.ring, n, abort, poll_limit, it));
+            if (!got) {
+                set_status(status, FAVEST_ETIMEOUT);
+                *abort = 1;
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) item_release(S.ring, n);
+            if (it < 0) break;
             const int nk = __ldg(&items[it].nk);   // the rest of the item is read at the end
 #pragma unroll
             for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
@@ -475,6 +565,7 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (threadIdx.x == 0) item_sched_done(sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,6 +590,20 @@ constexpr int kConvWarps = 4;
 constexpr int kFThreads = 512;
 constexpr int kConvRows = kChunkK * 256 / 8 / (32 * kConvWarps);   // 8-float rows per converter thread (N = 256)
 
+// OR of a flag over the converter warps, at named barrier 1 (a barrier for all of them)
+__device__ __forceinline__ bool conv_any(uint32_t flag)
+{
+    uint32_t any;
+    asm volatile("{\n\t.reg .pred q, p;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, 1, %2, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(any)
+                 : "r"(flag), "n"(32 * kConvWarps)
+                 : "memory");
+    return any != 0;
+}
+
 template <int N>
 struct GemmSmemF {
     unsigned char a[kFStages][kChunkBytes];
@@ -506,6 +611,7 @@ struct GemmSmemF {
     uint64_t full[kFStages], ready[kFStages], empty[kFStages];
     uint64_t dmain_full, dmain_empty, dcorr_full, dcorr_empty;
     uint64_t drain;
+    ItemRing ring;
     uint32_t tmem_base;
     int abort;
 };
@@ -513,7 +619,7 @@ struct GemmSmemF {
 template <int N>
 __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
     const GemmGroup *__restrict__ groups, const TcItem *__restrict__ items, int nitems, int *__restrict__ status,
-    uint32_t poll_limit)
+    int *__restrict__ sched, uint32_t poll_limit)
 {
     constexpr int kEpiWarps = 4 * (N / kEpiCols);
     constexpr int kPieceB = kChunkK * N * 2;
@@ -534,6 +640,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
         tc::mbar_init(&S.dcorr_full, 1);
         tc::mbar_init(&S.dcorr_empty, kEpiWarps);
         tc::mbar_init(&S.drain, 1);
+        item_ring_init(S.ring, 1 + kConvWarps + kEpiWarps);   // the MMA thread, converter and epilogue warps
         S.abort = 0;
         tc::mbar_fence_init();
     }
@@ -551,7 +658,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
         if (lane == 0) {
             uint32_t phase = 0, issued = 0;
             int stage = 0;
-            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            for (uint32_t n = 0; !*abort; ++n) {
+                int it;
+                if (!item_publish(S.ring, n, sched, nitems, abort, poll_limit, it)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                if (it < 0) break;
                 const TcItem I = items[it];
                 const CUtensorMap *tmap_a = &groups[I.group].tmap_a, *tmap_b = &groups[I.group].tmap_b;
                 for (int c = 0; c < I.nk; ++c) {
@@ -584,7 +698,15 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
             const uint32_t dmain = tmem, dcorr = tmem + N;
             constexpr uint32_t a_step = 4096u, a_lbo = 2048u, a_sbo = 128u;     // A MN-major
             constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
-            for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            for (uint32_t n = 0; !*abort; ++n) {
+                int it;
+                if (!item_take(S.ring, n, abort, poll_limit, it)) {
+                    set_status(status, FAVEST_ETIMEOUT);
+                    *abort = 1;
+                    break;
+                }
+                item_release(S.ring, n);
+                if (it < 0) break;
                 const TcItem I = items[it];
                 if (!wait_or_abort(&S.dcorr_empty, (corr_use & 1) ^ 1, abort, poll_limit)) {
                     set_status(status, FAVEST_ETIMEOUT);
@@ -652,11 +774,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
         // Each thread waits on the stage on its own, so whether a chunk goes ahead is agreed
         // at the named barrier itself (an OR over the converter threads of "my wait gave up"):
         // every converter thread then passes the same number of barriers and leaves together.
+        // The item indices are agreed the same way.
         const int ct = threadIdx.x - 128;                // 0 .. 32 * kConvWarps - 1
         uint32_t phase = 0;
         int stage = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        for (uint32_t n = 0; ok; ++n) {
+            int it = -1;
+            const uint32_t take_gave_up = item_take(S.ring, n, abort, poll_limit, it) ? 0u : 1u;
+            if (conv_any(take_gave_up)) { ok = false; break; }
+            __syncwarp();
+            if (lane == 0) item_release(S.ring, n);
+            if (it < 0) break;
             const int nk = __ldg(&items[it].nk);
             for (int c = 0; c < nk; ++c) {
                 const uint32_t gave_up =
@@ -672,15 +801,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
                         v4[k][1] = src[2 * r + 1];
                     }
                 }
-                uint32_t any_gave_up;
-                asm volatile("{\n\t.reg .pred q, p;\n\t"
-                             "setp.ne.u32 q, %1, 0;\n\t"
-                             "bar.red.or.pred p, 1, %2, q;\n\t"
-                             "selp.u32 %0, 1, 0, p;\n\t}"
-                             : "=r"(any_gave_up)
-                             : "r"(gave_up), "n"(32 * kConvWarps)
-                             : "memory");
-                if (any_gave_up) { ok = false; break; }
+                if (conv_any(gave_up)) { ok = false; break; }
                 // row r: 8 consecutive floats -> 16 bytes of each piece at the same position
 #pragma unroll
                 for (int k = 0; k < kRows; ++k) {
@@ -713,7 +834,17 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t main_use = 0, corr_use = 0;
         float acc[kEpiCols];
-        for (int it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+        for (uint32_t n = 0; !*abort; ++n) {
+            int it = -1;
+            const bool got = __all_sync(0xffffffffu, item_take(S.ring, n, abort, poll_limit, it));
+            if (!got) {
+                set_status(status, FAVEST_ETIMEOUT);
+                *abort = 1;
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) item_release(S.ring, n);
+            if (it < 0) break;
             const int nk = __ldg(&items[it].nk);
 #pragma unroll
             for (int i = 0; i < kEpiCols; ++i) acc[i] = 0.f;
@@ -769,6 +900,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (threadIdx.x == 0) item_sched_done(sched);
 }
 
 template <int N>
@@ -781,7 +913,7 @@ cudaError_t launch_gemm_f(const GemmGroup *groups, const TcItem *items, int nite
     if (e != cudaSuccess) return e;
     const int grid = nitems < num_sms ? nitems : num_sms;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, kFThreads, smem, s>>>(groups, items, nitems, status, kWaitPolls);
+    k<<<grid, kFThreads, smem, s>>>(groups, items, nitems, status, gemm_sched(status, true), kWaitPolls);
     return cudaGetLastError();
 }
 
@@ -795,7 +927,8 @@ cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nite
     if (e != cudaSuccess) return e;
     const int grid = nitems < num_sms ? nitems : num_sms;
     if (grid <= 0) return cudaSuccess;
-    k<<<grid, gemm_threads<N>(), smem, s>>>(groups, items, nitems, a_mn_major, status, poll_limit, skip_loads);
+    k<<<grid, gemm_threads<N>(), smem, s>>>(groups, items, nitems, a_mn_major, status,
+                                           gemm_sched(status, a_mn_major != 0), poll_limit, skip_loads);
     return cudaGetLastError();
 }
 
