@@ -69,7 +69,9 @@ enum favest_status_code {
     FAVEST_ECUDA = -3,         /* a CUDA runtime call failed                      */
     FAVEST_EUNSUPPORTED = -4,  /* valid request this library or device cannot serve */
     FAVEST_ETIMEOUT = -5,      /* a bounded device-side wait gave up              */
-    FAVEST_EDEVICE = -6        /* a kernel recorded an internal error             */
+    FAVEST_EDEVICE = -6,       /* a kernel recorded an internal error             */
+    FAVEST_EINTERNAL = -7      /* a plan's own index tables failed their bounds check
+                                  (see favest_debug_check_layout)                   */
 };
 
 /* Arithmetic of the Legendre contraction.  The recurrence, its underflow scaling,
@@ -399,6 +401,30 @@ int favest_selftest_wait_timeout(favest_plan plan, unsigned poll_limit, double *
  */
 int favest_debug_fail_alloc(long long k);
 long long favest_debug_alloc_count(void);
+
+/*
+ * Bounds check of a plan's index tables without creating the plan (no counterpart in the
+ * paper; no CUDA call, so it runs on a host without a GPU).  Builds the host-side tables
+ * that favest_plan_create builds for (L, batch, precision, io_type) on the Gauss-Legendre
+ * grid -- for FAVEST_BF16X6 the tensor-core GEMM work items of both directions, the
+ * per-(order, parity) operand regions and the forward operand's TMA box coordinates, with
+ * gemm_n = 0 (the plan's own tile width) or 256 (the width ragged batches use) -- and
+ * checks every index the kernels take from them against the buffer it addresses: operand
+ * chunk ranges and their 512-byte row alignment, box coordinates against the tensor map's
+ * extents, output rows and column groups against the output buffer and the rows of the
+ * item's own order, regions in order and disjoint.  FP64 plans have no such tables and
+ * return FAVEST_OK once their arguments pass.  Returns FAVEST_OK; the argument errors of
+ * favest_plan_create (FAVEST_EINVAL, FAVEST_EUNSUPPORTED) and FAVEST_EINVAL for another
+ * gemm_n or msg_len < 0; or FAVEST_EINTERNAL with a description of the first violation
+ * written to msg (NUL-terminated, at most msg_len bytes; msg may be null when msg_len is
+ * 0).  favest_plan_create runs the same check and fails with FAVEST_EINTERNAL likewise.
+ * poison (tests of the check itself; 0 in normal use) corrupts the check's own copy of the
+ * tables first: 1 moves the first forward item to order L + 1, 2 gives the last adjoint
+ * item one K-chunk too many, 3 makes the first two forward operand regions overlap; other
+ * values give FAVEST_EINVAL.
+ */
+int favest_debug_check_layout(int L, int batch, int precision, int io_type, int gemm_n, int poison, char *msg,
+                              int msg_len);
 
 /*
  * Algorithmic work of one launch of a kernel of this plan, by the name that

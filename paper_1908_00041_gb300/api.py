@@ -21,6 +21,7 @@ FAVEST_ECUDA = -3
 FAVEST_EUNSUPPORTED = -4
 FAVEST_ETIMEOUT = -5
 FAVEST_EDEVICE = -6
+FAVEST_EINTERNAL = -7
 
 FAVEST_FP64 = 0
 FAVEST_BF16X6 = 1
@@ -112,6 +113,7 @@ def lib(build_if_missing=False):
             L.favest_cg_stability.argtypes = [i, i, d, d, d, vp]
             L.favest_debug_fail_alloc.argtypes = [ctypes.c_longlong]
             L.favest_debug_alloc_count.restype = ctypes.c_longlong
+            L.favest_debug_check_layout.argtypes = [i, i, i, i, i, i, ctypes.c_char_p, i]
             L.favest_scatter_create.argtypes = [i, i, i, d, d, ctypes.POINTER(vp)]
             L.favest_scatter_fwd.argtypes = [vp, vp, vp, vp, vp]
             L.favest_scatter_adj.argtypes = [vp, vp, vp, vp, vp]
@@ -149,6 +151,15 @@ def _stream(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def debug_check_layout(L, batch, precision=FAVEST_BF16X6, io_type=FAVEST_IO_C64, gemm_n=0, poison=0):
+    """Host-only bounds check of the index tables a plan of this shape would use
+    (favest_debug_check_layout; no GPU needed): returns (status, message)."""
+    buf = ctypes.create_string_buffer(256)
+    st = lib().favest_debug_check_layout(int(L), int(batch), int(precision), int(io_type), int(gemm_n), int(poison),
+                                         buf, len(buf))
+    return st, buf.value.decode()
 
 
 def favest_gl_grid(nlat):

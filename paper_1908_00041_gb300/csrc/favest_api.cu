@@ -27,6 +27,7 @@ const char *kErrStr[] = {
     "unsupported request",
     "device-side wait timed out",
     "device-side error",
+    "index table bounds check failed",
 };
 
 // ---------------------------------------------------------------------------
@@ -454,13 +455,26 @@ std::vector<int> turning_bounds(const Plan &p)
 // The GEMM epilogue stores 128-byte groups of 4 rows (one per 4 lanes of a warp); the
 // inverse FFT of latitude j reads the 32-byte record of j, and the blocks of the 4
 // latitudes of a group, adjacent in launch order, share each 128-byte line.
-int alloc_workspace_bf16(Plan &p)
+// Host-side layout of the split path: everything alloc_workspace_bf16 derives from (L,
+// batch, io, latitudes) before it touches the device, so that check_layout_bf16 and
+// favest_debug_check_layout can examine it without a GPU.
+struct SplitLayout {
+    std::vector<long long> off_f, off_a, off_g;   // per (mu, parity): operand offsets (bytes)
+    std::vector<int> jcmin;                       // per mu: first generated latitude chunk
+    std::vector<TcItem> itf, ita;                 // GEMM items, launch order
+    long long CHA = 0, CHB = 0;                   // bytes per A / B chunk
+    size_t lamf_bytes = 0, lama_bytes = 0, fb_bytes = 0, g_bytes = 0, q_bytes = 0, s_bytes = 0;
+};
+
+int layout_bf16(Plan &p, SplitLayout &Y)
 {
     const int L = p.L;
     const int KC = kGemmChunkK;
     const long long CHA = 3LL * 128 * KC * 2;    // bytes per A chunk (3 bf16 pieces of 128 x KC)
     p.gemm_n = (p.force_gemm_n == 256 || 8 * p.ncg > 128) ? 256 : 128;
     const long long CHB = 3LL * KC * p.gemm_n * 2;   // bytes per B chunk (3 pieces of KC x N)
+    Y.CHA = CHA;
+    Y.CHB = CHB;
     p.JP = (p.J + 127) / 128 * 128;
     p.ncolr = (8 * p.ncg + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
     p.n_tiles = p.ncolr / p.gemm_n;
@@ -468,11 +482,15 @@ int alloc_workspace_bf16(Plan &p)
     p.nk_f = p.JP / KC;
     const int fpt = p.gemm_n / 8;                  // column groups per column tile
     const long long L1 = L + 1;
-    std::vector<long long> off_f(2 * (L + 1)), off_a(2 * (L + 1)), off_g(2 * (L + 1));
+    std::vector<long long> &off_f = Y.off_f, &off_a = Y.off_a, &off_g = Y.off_g;
+    off_f.assign(2 * (L + 1), 0);
+    off_a.assign(2 * (L + 1), 0);
+    off_g.assign(2 * (L + 1), 0);
     const int J = p.J;
     const std::vector<int> lf = turning_bounds(p);
     // generator: first latitude per order, rounded down to a K-chunk of 32
-    std::vector<int> jcmin(L + 1);
+    std::vector<int> &jcmin = Y.jcmin;
+    jcmin.assign(L + 1, 0);
     p.gen_values = 0;
     for (int mu = 0; mu <= L; ++mu) {
         int jmin = J;
@@ -484,7 +502,9 @@ int alloc_workspace_bf16(Plan &p)
     }
     p.gemm_pairs_f = p.gemm_pairs_a = 0;
     long long lam_f = 0, lam_a = 0, gsz = 0;
-    std::vector<TcItem> itf, ita;
+    std::vector<TcItem> &itf = Y.itf, &ita = Y.ita;
+    itf.clear();
+    ita.clear();
     auto nrow_p = [&](int mu, int par) { const int n = L + 2 - mu; return par ? n / 2 : (n + 1) / 2; };
     // pass 1: operand storage offsets per (mu, parity)
     for (int mu = 0; mu <= L; ++mu) {
@@ -595,10 +615,106 @@ int alloc_workspace_bf16(Plan &p)
     }
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
-    const size_t lamf_bytes = (size_t)lam_f, lama_bytes = (size_t)lam_a;
-    const size_t fb_bytes = (size_t)p.JP * p.nf * L1 * 64;
-    const size_t q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
-    const size_t s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
+    Y.lamf_bytes = (size_t)lam_f;
+    Y.lama_bytes = (size_t)lam_a;
+    Y.fb_bytes = (size_t)p.JP * p.nf * L1 * 64;
+    Y.g_bytes = (size_t)gsz;
+    Y.q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
+    Y.s_bytes = (size_t)p.nf * (p.JP / 4) * L1 * 2 * 32 * sizeof(float);
+    return FAVEST_OK;
+}
+
+// Bounds of every index the split path's kernels take from the layout: each GEMM item's
+// operand chunks (byte ranges of the A and B buffers, 512-byte row alignment of the TMA
+// row boxes; the forward B operand's 5-D box coordinates against the tensor map's extents),
+// its output rows and column groups against the output buffer and against the rows of its
+// own order, and the per-order operand regions (in range, in order, not overlapping).
+// FAVEST_EINTERNAL with a description in msg (when given) on the first violation.
+int check_layout_bf16(const Plan &p, const SplitLayout &Y, char *msg, size_t msg_len)
+{
+    auto fail = [&](const char *what, long long a, long long b, long long c) {
+        if (msg && msg_len) std::snprintf(msg, msg_len, "%s (%lld, %lld, %lld)", what, a, b, c);
+        return FAVEST_EINTERNAL;
+    };
+    const int L = p.L, N = p.gemm_n, KC = kGemmChunkK;
+    const long long L1 = L + 1;
+    auto nrow_p = [&](int mu, int par) { const int n = L + 2 - mu; return par ? n / 2 : (n + 1) / 2; };
+    if (p.JP % 128 || p.JP < p.J || p.nf * 8 != p.ncolr || p.n_tiles * N != p.ncolr || p.nf < p.ncg)
+        return fail("grid or column padding", p.JP, p.nf, p.ncolr);
+    if ((int)Y.off_f.size() != 2 * L1 || (int)Y.off_a.size() != 2 * L1 || (int)Y.off_g.size() != 2 * L1 ||
+        (int)Y.jcmin.size() != L1)
+        return fail("table sizes", (long long)Y.off_f.size(), (long long)Y.jcmin.size(), L1);
+    // per-(mu, parity) regions, in order and inside their buffers
+    for (int idx = 0; idx < 2 * L1; ++idx) {
+        const int mu = idx / 2, par = idx % 2;
+        const int np = nrow_p(mu, par), npa = nrow_p(mu == 0 ? 1 : mu, par);
+        const long long ef = Y.off_f[idx] + (long long)((np + 127) / 128) * p.nk_f * Y.CHA;
+        const long long ea = Y.off_a[idx] + (long long)(p.JP / 128) * ((np + KC - 1) / KC) * Y.CHA;
+        const long long eg = Y.off_g[idx] + (long long)p.n_tiles * ((npa + KC - 1) / KC) * Y.CHB;
+        const long long nf_ = idx + 1 < 2 * L1 ? Y.off_f[idx + 1] : (long long)Y.lamf_bytes;
+        const long long na_ = idx + 1 < 2 * L1 ? Y.off_a[idx + 1] : (long long)Y.lama_bytes;
+        const long long ng_ = idx + 1 < 2 * L1 ? Y.off_g[idx + 1] : (long long)Y.g_bytes;
+        if (Y.off_f[idx] < 0 || ef > nf_) return fail("forward Legendre region", mu, par, ef);
+        if (Y.off_a[idx] < 0 || ea > na_) return fail("adjoint Legendre region", mu, par, ea);
+        if (Y.off_g[idx] < 0 || eg > ng_) return fail("coefficient operand region", mu, par, eg);
+        if (Y.off_f[idx] % 512 || Y.off_a[idx] % 512 || Y.off_g[idx] % 512)
+            return fail("operand region alignment", mu, par, Y.off_f[idx]);
+    }
+    for (int mu = 0; mu <= L; ++mu)
+        if (Y.jcmin[mu] < 0 || Y.jcmin[mu] % KC || Y.jcmin[mu] >= p.J) return fail("generator start", mu, Y.jcmin[mu], p.J);
+    const long long qf = (long long)(Y.q_bytes / sizeof(float)), sf = (long long)(Y.s_bytes / sizeof(float));
+    // the epilogue writes row r < rows, column group g < N/8 at out_off + (r/4) out_ld +
+    // (r%4) 8 + g col_gs (8 floats): the last row and group bound it from above
+    auto out_span = [&](const TcItem &I, long long &lo, long long &hi) {
+        const int r = I.rows - 1;
+        lo = I.out_off;
+        hi = I.out_off + (long long)(r / 4) * I.out_ld + (r % 4) * 8 + 7 + (long long)(N / 8 - 1) * I.col_gs;
+    };
+    for (size_t i = 0; i < Y.itf.size(); ++i) {
+        const TcItem &I = Y.itf[i];
+        if (I.nk < 1 || I.rows < 1 || I.rows > 128 || I.group != 0 || !I.b_box) return fail("forward item shape", (long long)i, I.nk, I.rows);
+        if (I.a_off < 0 || I.a_off % 512 || I.a_stride % 512 || I.a_off + (long long)(I.nk - 1) * I.a_stride + Y.CHA > (long long)Y.lamf_bytes)
+            return fail("forward item A chunks", (long long)i, I.a_off, I.nk);
+        // 5-D box {8, 1, 8, N/8, 4} at (bx, bw, 0, by, 4 (bk + c)) in dims {16, L+1, 8, nf, JP/8}
+        if ((I.bx != 0 && I.bx != 8) || I.bw < 0 || I.bw > L || I.by < 0 || I.by + N / 8 > p.nf || I.bk < 0 ||
+            (long long)(KC / 8) * (I.bk + I.nk) > p.JP / 8)
+            return fail("forward item B box", (long long)i, I.bw, I.bk + I.nk);
+        long long lo, hi;
+        out_span(I, lo, hi);
+        if (lo < 0 || hi >= qf) return fail("forward item output", (long long)i, lo, hi);
+        // rows of the item's own order and parity: Q32 rows tab_off(L, mu) .. tab_off(L, mu+1)
+        const long long qrow = (I.out_off / 8) % p.ntab;
+        const int mu = I.bw;
+        if (qrow < tab_off(L, mu) || qrow + I.rows > tab_off(L, mu + 1)) return fail("forward item rows", (long long)i, mu, qrow);
+    }
+    for (size_t i = 0; i < Y.ita.size(); ++i) {
+        const TcItem &I = Y.ita[i];
+        if (I.nk < 1 || I.rows != 128 || I.group != 1 || I.b_box) return fail("adjoint item shape", (long long)i, I.nk, I.rows);
+        if (I.a_off < 0 || I.a_off % 512 || I.a_stride % 512 || I.a_off + (long long)(I.nk - 1) * I.a_stride + Y.CHA > (long long)Y.lama_bytes)
+            return fail("adjoint item A chunks", (long long)i, I.a_off, I.nk);
+        if (I.b_off < 0 || I.b_off % 512 || I.b_stride % 512 || I.b_off + (long long)(I.nk - 1) * I.b_stride + Y.CHB > (long long)Y.g_bytes)
+            return fail("adjoint item B chunks", (long long)i, I.b_off, I.nk);
+        long long lo, hi;
+        out_span(I, lo, hi);
+        if (lo < 0 || hi >= sf) return fail("adjoint item output", (long long)i, lo, hi);
+    }
+    return FAVEST_OK;
+}
+
+int alloc_workspace_bf16(Plan &p)
+{
+    SplitLayout Y;
+    int st = layout_bf16(p, Y);
+    if (st == FAVEST_OK) st = check_layout_bf16(p, Y, nullptr, 0);
+    if (st != FAVEST_OK) return st;
+    const int L = p.L;
+    const long long CHA = Y.CHA, CHB = Y.CHB;
+    const std::vector<long long> &off_f = Y.off_f, &off_a = Y.off_a, &off_g = Y.off_g;
+    const std::vector<int> &jcmin = Y.jcmin;
+    const std::vector<TcItem> &itf = Y.itf, &ita = Y.ita;
+    const size_t lamf_bytes = Y.lamf_bytes, lama_bytes = Y.lama_bytes, fb_bytes = Y.fb_bytes, q_bytes = Y.q_bytes,
+                 s_bytes = Y.s_bytes;
+    const long long gsz = (long long)Y.g_bytes;
     if (plan_malloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || plan_malloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
         plan_malloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         plan_malloc(&p.d_gb, (size_t)gsz) != cudaSuccess || plan_malloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
@@ -624,7 +740,7 @@ int alloc_workspace_bf16(Plan &p)
     const int pst = build_polar_tables(p);
     if (pst != FAVEST_OK) return pst;
     p.ws_bytes += (size_t)p.pol_jc * (L + 1) * p.pol_muc * sizeof(float2);
-    int st = make_row_tensor_map(p.d_lam_f, lamf_bytes, (int)(CHA / 512), &p.tmap_lam_f);
+    st = make_row_tensor_map(p.d_lam_f, lamf_bytes, (int)(CHA / 512), &p.tmap_lam_f);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_lam_a, lama_bytes, (int)(CHA / 512), &p.tmap_lam_a);
     if (st == FAVEST_OK) st = make_fb_tensor_map(p);
     if (st == FAVEST_OK) st = make_s32_tensor_map(p);
@@ -765,11 +881,12 @@ cudaError_t plan_malloc(void **p, size_t bytes)
     return cudaMalloc(p, bytes);
 }
 
-int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
-                         const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route)
+// Argument checks and the host-side fields of a plan (grid sizes, column layout,
+// latitudes and weights in h_x / h_w, which the caller frees with std::free on failure
+// paths that do not go through free_plan); no CUDA call.
+int plan_init_host(Plan &p, int L, int batch, int precision, int io_type, const double *cos_theta,
+                   const double *w_lat, int force_gemm_n, int cg_route)
 {
-    if (!out) return FAVEST_EINVAL;
-    *out = nullptr;
     if (L < 1 || L > 4095 || batch < 1 || batch > 4096) return FAVEST_EINVAL;
     if (L > 2559) return FAVEST_EUNSUPPORTED;   // J <= 1280 latitudes per CTA in the FP64 kernels
     if (precision != FAVEST_FP64 && precision != FAVEST_BF16X6) return FAVEST_EINVAL;
@@ -789,10 +906,6 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     if (precision == FAVEST_BF16X6 && (io_type == FAVEST_IO_C128 || io_type == FAVEST_IO_R64)) return FAVEST_EUNSUPPORTED;
     const bool real_io = io_type == FAVEST_IO_R32 || io_type == FAVEST_IO_R64;
     if (real_io && cg_route) return FAVEST_EINVAL;
-
-    favest_plan_s *h = new (std::nothrow) favest_plan_s();
-    if (!h) return FAVEST_ENOMEM;
-    Plan &p = h->p;
     p.force_gemm_n = force_gemm_n;
     p.L = L;
     p.B = batch;
@@ -817,25 +930,44 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
     }
     p.ct = (p.ncol % 8 == 0) ? 8 : 4;
     p.ng = p.ncol / p.ct;
-    if (cudaGetDevice(&p.device) != cudaSuccess) { delete h; return FAVEST_ECUDA; }
-    cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
-    if (precision == FAVEST_BF16X6) {
-        int major = 0, minor = 0;
-        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p.device);
-        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p.device);
-        if (major != 10 || minor != 3) { delete h; return FAVEST_EUNSUPPORTED; }
-    }
+    if (p.J > 1280) return FAVEST_EUNSUPPORTED;
     p.h_x = (double *)std::malloc(sizeof(double) * nlat);
     p.h_w = (double *)std::malloc(sizeof(double) * nlat);
-    if (!p.h_x || !p.h_w) { free_plan(p); delete h; return FAVEST_ENOMEM; }
+    if (!p.h_x || !p.h_w) return FAVEST_ENOMEM;
     if (cos_theta) {
         std::memcpy(p.h_x, cos_theta, sizeof(double) * nlat);
         std::memcpy(p.h_w, w_lat, sizeof(double) * nlat);
     } else {
         gl_rule(nlat, p.h_x, p.h_w);
     }
-    if (p.J > 1280) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
-    int st = build_tables(p);
+    return FAVEST_OK;
+}
+
+int plan_create_internal(int L, int batch, int precision, int io_type, const double *cos_theta,
+                         const double *w_lat, int force_gemm_n, favest_plan *out, int cg_route)
+{
+    if (!out) return FAVEST_EINVAL;
+    *out = nullptr;
+    favest_plan_s *h = new (std::nothrow) favest_plan_s();
+    if (!h) return FAVEST_ENOMEM;
+    Plan &p = h->p;
+    int st = plan_init_host(p, L, batch, precision, io_type, cos_theta, w_lat, force_gemm_n, cg_route);
+    if (st != FAVEST_OK) {
+        std::free(p.h_x);
+        std::free(p.h_w);
+        p.h_x = p.h_w = nullptr;
+        delete h;
+        return st;
+    }
+    if (cudaGetDevice(&p.device) != cudaSuccess) { free_plan(p); delete h; return FAVEST_ECUDA; }
+    cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+    if (precision == FAVEST_BF16X6) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p.device);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p.device);
+        if (major != 10 || minor != 3) { free_plan(p); delete h; return FAVEST_EUNSUPPORTED; }
+    }
+    st = build_tables(p);
     if (st == FAVEST_OK) st = (precision == FAVEST_BF16X6) ? alloc_workspace_bf16(p) : alloc_workspace(p);
     if (st != FAVEST_OK) {
         cudaGetLastError();
@@ -851,6 +983,30 @@ int plan_create_internal(int L, int batch, int precision, int io_type, const dou
 }  // namespace favest
 
 extern "C" {
+
+int favest_debug_check_layout(int L, int batch, int precision, int io_type, int gemm_n, int poison, char *msg,
+                              int msg_len)
+{
+    if (msg && msg_len > 0) msg[0] = 0;
+    if (gemm_n != 0 && gemm_n != 256) return FAVEST_EINVAL;
+    if (poison < 0 || poison > 3) return FAVEST_EINVAL;
+    if (msg_len < 0 || (msg_len > 0 && !msg)) return FAVEST_EINVAL;
+    Plan p;
+    int st = plan_init_host(p, L, batch, precision, io_type, nullptr, nullptr, gemm_n, 0);
+    if (st == FAVEST_OK && precision == FAVEST_BF16X6) {
+        p.ntab = tab_off(L, L + 1);   // orders 0..L, as build_tables sets it
+        SplitLayout Y;
+        st = layout_bf16(p, Y);
+        if (st == FAVEST_OK && poison == 1 && !Y.itf.empty()) Y.itf[0].bw = L + 1;      // order out of range
+        if (st == FAVEST_OK && poison == 2 && !Y.ita.empty()) Y.ita.back().nk += 1;    // one chunk too many
+        if (st == FAVEST_OK && poison == 3 && L >= 2) Y.off_f[2] = Y.off_f[1];         // overlapping regions
+        if (st == FAVEST_OK) st = check_layout_bf16(p, Y, msg, msg_len > 0 ? (size_t)msg_len : 0);
+    }
+    std::free(p.h_x);
+    std::free(p.h_w);
+    p.h_x = p.h_w = nullptr;
+    return st;
+}
 
 int favest_plan_create(int L, int batch, int precision, int io_type, const double *cos_theta,
                        const double *w_lat, favest_plan *out)
