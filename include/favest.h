@@ -105,9 +105,9 @@ int favest_gl_grid(int nlat, double *x, double *w);
  * current CUDA device.  1 <= L <= 2559 (up to 1280 latitude pairs); L = 2560..4095 returns
  * FAVEST_EUNSUPPORTED, L < 1, L > 4095 or a batch outside 1..4096 FAVEST_EINVAL.  FAVEST_BF16X6
  * requires io_type FAVEST_IO_C64 or FAVEST_IO_R32 (FAVEST_EUNSUPPORTED otherwise) and
- * a device with tcgen05 tensor cores (sm_100 family), and its FP32 longitude DFT takes
- * nphi = 2(L+1) with prime factors up to 128 only (FAVEST_EUNSUPPORTED otherwise, e.g.
- * L = 150: nphi = 2 * 151); FAVEST_IO_R64 requires FAVEST_FP64 (FAVEST_EUNSUPPORTED
+ * a device with tcgen05 tensor cores (sm_100 family; its FP32 longitude DFT takes any
+ * nphi = 2(L+1), prime factors from 17 up through Bluestein stages); FAVEST_IO_R64 requires
+ * FAVEST_FP64 (FAVEST_EUNSUPPORTED
  * otherwise), FAVEST_IO_R32 works with both precisions.  Real-field plans take 16-byte
  * aligned pointers.
  *   cos_theta, w_lat: optional host arrays of nlat = L+1 latitude nodes (descending)
@@ -169,6 +169,19 @@ int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *
  */
 int favest_cg_plan_create(int L, int batch, const double *cos_theta, const double *w_lat,
                           favest_plan *out);
+/*
+ * favest_cg_plan_create_ex: as favest_cg_plan_create for io_type FAVEST_IO_C128; with
+ *   FAVEST_IO_R64 a plan for `batch` REAL fields (1 <= batch <= 2732; the paper's fields,
+ *   Sec. 3): favest_fwd_cart then takes T device [batch][3][nlat][nphi] double and writes
+ *   half-spectrum a, b device [batch][L(L+3)/2] complex double (m >= 0, the real-field
+ *   layout at the top of this file), favest_adj_cart the reverse.  Fields 2q and 2q+1 are
+ *   transformed together as the complex field T_2q + i T_2q+1 (the transforms are linear
+ *   and a real field's coefficients satisfy a_{l,-m} = (-1)^m conj(a_lm)), through pack
+ *   and unpack kernels around the complex route and a workspace of ceil(batch/2) complex
+ *   fields and coefficient sets.  Other io types: FAVEST_EINVAL.
+ */
+int favest_cg_plan_create_ex(int L, int batch, int io_type, const double *cos_theta, const double *w_lat,
+                             favest_plan *out);
 int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *stream);
 int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, void *stream);
 

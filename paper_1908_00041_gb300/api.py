@@ -108,6 +108,7 @@ def lib(build_if_missing=False):
             L.favest_fwd_fp64_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp]
             L.favest_noalloc_scratch_bytes.restype = ctypes.c_size_t
             L.favest_cg_plan_create.argtypes = [i, i, d, d, ctypes.POINTER(vp)]
+            L.favest_cg_plan_create_ex.argtypes = [i, i, i, d, d, ctypes.POINTER(vp)]
             L.favest_fwd_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_adj_cart.argtypes = [vp, vp, vp, vp, vp]
             L.favest_cg_stability.argtypes = [i, i, d, d, d, vp]
@@ -429,14 +430,17 @@ class Plan:
 
 class CgPlan:
     """FP64 plan of the Clebsch-Gordan route (Thm. 1, Thm. 2): fields as Cartesian
-    components, T [batch, 3, L+1, 2(L+1)] complex128; coefficients [batch, L^2+2L]."""
+    components, T [batch, 3, L+1, 2(L+1)] complex128, coefficients [batch, L^2+2L]
+    complex128; with real=True real fields, T float64, and half-spectrum coefficients
+    [batch, L(L+3)/2] complex128 (m >= 0)."""
 
-    def __init__(self, L, batch=1, cos_theta=None, w_lat=None):
+    def __init__(self, L, batch=1, cos_theta=None, w_lat=None, real=False):
         import torch
-        self.L, self.batch = int(L), int(batch)
+        self.L, self.batch, self.real = int(L), int(batch), bool(real)
         self.nlat, self.nphi = L + 1, 2 * (L + 1)
-        self.K = L * L + 2 * L
+        self.K = L * (L + 3) // 2 if self.real else L * L + 2 * L
         self.cdtype = torch.complex128
+        self.fdtype = torch.float64 if self.real else torch.complex128
         h = ctypes.c_void_p()
         dp = ctypes.POINTER(ctypes.c_double)
         xp = wp = None
@@ -444,7 +448,9 @@ class CgPlan:
             cos_theta = np.ascontiguousarray(cos_theta, dtype=np.float64)
             w_lat = np.ascontiguousarray(w_lat, dtype=np.float64)
             xp, wp = cos_theta.ctypes.data_as(dp), w_lat.ctypes.data_as(dp)
-        _check(lib().favest_cg_plan_create(self.L, self.batch, xp, wp, ctypes.byref(h)), "favest_cg_plan_create")
+        io = FAVEST_IO_R64 if self.real else FAVEST_IO_C128
+        _check(lib().favest_cg_plan_create_ex(self.L, self.batch, io, xp, wp, ctypes.byref(h)),
+               "favest_cg_plan_create_ex")
         self.handle = h.value
 
     def close(self):
@@ -464,13 +470,14 @@ class CgPlan:
     def coef_shape(self):
         return (self.batch, self.K)
 
-    def _check(self, t, shape, name):
-        if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == shape):
-            raise ValueError("%s: expected contiguous CUDA complex128 tensor of shape %s" % (name, shape))
+    def _check(self, t, shape, name, dtype=None):
+        dtype = self.cdtype if dtype is None else dtype
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError("%s: expected contiguous CUDA %s tensor of shape %s" % (name, dtype, shape))
 
     def fwd(self, T, a=None, b=None, stream=None):
         import torch
-        self._check(T, self.field_shape(), "T")
+        self._check(T, self.field_shape(), "T", self.fdtype)
         a = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if a is None else a
         b = torch.empty(self.coef_shape(), dtype=self.cdtype, device=T.device) if b is None else b
         self._check(a, self.coef_shape(), "a")
@@ -483,8 +490,8 @@ class CgPlan:
         import torch
         self._check(a, self.coef_shape(), "a")
         self._check(b, self.coef_shape(), "b")
-        T = torch.empty(self.field_shape(), dtype=self.cdtype, device=a.device) if T is None else T
-        self._check(T, self.field_shape(), "T")
+        T = torch.empty(self.field_shape(), dtype=self.fdtype, device=a.device) if T is None else T
+        self._check(T, self.field_shape(), "T", self.fdtype)
         _check(lib().favest_adj_cart(ctypes.c_void_p(self.handle), _ptr(a), _ptr(b), _ptr(T), _stream(stream)),
                "favest_adj_cart")
         return T

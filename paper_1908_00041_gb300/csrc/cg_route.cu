@@ -344,6 +344,96 @@ __global__ void __launch_bounds__(kStabThreads) k_stability_reduce(const double 
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Real fields on the Clebsch-Gordan route.  Real vector fields A = field 2q and B = field
+// 2q+1 are transformed as the complex field z = A + i B.  The transforms are linear and
+// the coefficients of a real field are Hermitian, alpha_{l,-m} = (-1)^m conj(alpha_lm)
+// (the header's real-field relation), so those of z, c = alpha + i beta, separate as
+//   alpha_lm = (c_lm + (-1)^m conj c_{l,-m}) / 2,  beta_lm = (c_lm - (-1)^m conj c_{l,-m}) / (2i),
+// and conversely c_lm = alpha_lm + i beta_lm, c_{l,-m} = (-1)^m (conj alpha_lm + i conj beta_lm)
+// for m >= 0; the synthesis of c is A + i B.  Half spectra: index l(l+1)/2 - 1 + m, m >= 0.
+
+// one thread per (pair q, component plane element): z = A + i B (B = 0 past the last field)
+__global__ void k_cg_pack_fields(const double *__restrict__ Tr, double2 *__restrict__ Tc, long long plane, int nreal,
+                                 int npair)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)npair * 3 * plane) return;
+    const int q = (int)(t / (3 * plane));
+    const long long r = t - (long long)q * 3 * plane;          // component * plane + point
+    const double A = Tr[(long long)(2 * q) * 3 * plane + r];
+    const double B = 2 * q + 1 < nreal ? Tr[(long long)(2 * q + 1) * 3 * plane + r] : 0.0;
+    Tc[t] = make_double2(A, B);
+}
+
+__global__ void k_cg_unpack_fields(const double2 *__restrict__ Tc, double *__restrict__ Tr, long long plane, int nreal,
+                                   int npair)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)npair * 3 * plane) return;
+    const int q = (int)(t / (3 * plane));
+    const long long r = t - (long long)q * 3 * plane;
+    const double2 z = Tc[t];
+    Tr[(long long)(2 * q) * 3 * plane + r] = z.x;
+    if (2 * q + 1 < nreal) Tr[(long long)(2 * q + 1) * 3 * plane + r] = z.y;
+}
+
+__device__ __forceinline__ void half_lm(int h, int &l, int &m)
+{
+    l = (int)((sqrt(8.0 * (h + 1) + 1.0) - 1.0) * 0.5);
+    while (l * (l + 1) / 2 - 1 > h) --l;
+    while ((l + 1) * (l + 2) / 2 - 1 <= h) ++l;
+    m = h - (l * (l + 1) / 2 - 1);
+}
+
+// one thread per (pair q, half-spectrum index (l, m >= 0)), both families
+__global__ void k_cg_unpack_coefs(const double2 *__restrict__ ac, const double2 *__restrict__ bc,
+                                  double2 *__restrict__ ah, double2 *__restrict__ bh, int L, int nreal, int npair)
+{
+    const int K = L * L + 2 * L, H = L * (L + 3) / 2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)npair * H) return;
+    const int q = (int)(t / H), h = (int)(t % H);
+    int l, m;
+    half_lm(h, l, m);
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    const long long ip = (long long)q * K + l * l + l + m - 1, im = (long long)q * K + l * l + l - m - 1;
+    const double2 *src[2] = {ac, bc};
+    double2 *dst[2] = {ah, bh};
+#pragma unroll
+    for (int fam = 0; fam < 2; ++fam) {
+        const double2 cp = src[fam][ip], cm = src[fam][im];
+        const double2 w = make_double2(sg * cm.x, -sg * cm.y);      // (-1)^m conj c_{l,-m}
+        dst[fam][(long long)(2 * q) * H + h] = make_double2(0.5 * (cp.x + w.x), 0.5 * (cp.y + w.y));
+        // (c - w) / (2i) = -i (c - w) / 2
+        if (2 * q + 1 < nreal)
+            dst[fam][(long long)(2 * q + 1) * H + h] = make_double2(0.5 * (cp.y - w.y), -0.5 * (cp.x - w.x));
+    }
+}
+
+__global__ void k_cg_pack_coefs(const double2 *__restrict__ ah, const double2 *__restrict__ bh,
+                                double2 *__restrict__ ac, double2 *__restrict__ bc, int L, int nreal, int npair)
+{
+    const int K = L * L + 2 * L, H = L * (L + 3) / 2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)npair * H) return;
+    const int q = (int)(t / H), h = (int)(t % H);
+    int l, m;
+    half_lm(h, l, m);
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    const long long ip = (long long)q * K + l * l + l + m - 1, im = (long long)q * K + l * l + l - m - 1;
+    const double2 *src[2] = {ah, bh};
+    double2 *dst[2] = {ac, bc};
+#pragma unroll
+    for (int fam = 0; fam < 2; ++fam) {
+        const double2 al = src[fam][(long long)(2 * q) * H + h];
+        const double2 be = 2 * q + 1 < nreal ? src[fam][(long long)(2 * q + 1) * H + h] : make_double2(0.0, 0.0);
+        dst[fam][ip] = make_double2(al.x - be.y, al.y + be.x);                  // alpha + i beta
+        if (m > 0)                                                            // (-1)^m (conj alpha + i conj beta)
+            dst[fam][im] = make_double2(sg * (al.x + be.y), sg * (be.x - al.y));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s)
@@ -361,6 +451,39 @@ cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cud
     const long long n = (long long)p.B * (p.L + 2) * (p.L + 2);
     k_cg_uncombine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)a, (const double2 *)b, p.d_kap,
                                                              (double2 *)p.d_Q, p.L, K, p.ncol, p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pack_fields(const Plan &p, const void *Tr, cudaStream_t s)
+{
+    const long long plane = (long long)p.nlat * p.nphi, n = (long long)p.B * 3 * plane;
+    k_cg_pack_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Tr, (double2 *)p.d_cgT, plane,
+                                                               p.cg_real, p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_unpack_fields(const Plan &p, void *Tr, cudaStream_t s)
+{
+    const long long plane = (long long)p.nlat * p.nphi, n = (long long)p.B * 3 * plane;
+    k_cg_unpack_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)p.d_cgT, (double *)Tr, plane,
+                                                                 p.cg_real, p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pack_coefs(const Plan &p, const void *a, const void *b, cudaStream_t s)
+{
+    const long long n = (long long)p.B * (p.L * (p.L + 3) / 2);
+    k_cg_pack_coefs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)a, (const double2 *)b,
+                                                              (double2 *)p.d_cga, (double2 *)p.d_cgb, p.L, p.cg_real,
+                                                              p.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_unpack_coefs(const Plan &p, void *a, void *b, cudaStream_t s)
+{
+    const long long n = (long long)p.B * (p.L * (p.L + 3) / 2);
+    k_cg_unpack_coefs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2 *)p.d_cga, (const double2 *)p.d_cgb,
+                                                                (double2 *)a, (double2 *)b, p.L, p.cg_real, p.B);
     return cudaGetLastError();
 }
 

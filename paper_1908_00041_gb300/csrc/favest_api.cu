@@ -112,7 +112,7 @@ void free_plan(Plan &p)
                     p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups,
-                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw};
+                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -796,7 +796,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FAVEST_OK : FAVEST_EC
 const char *kKernelNames[KID_COUNT] = {
     "fft_fwd", "legendre_analysis", "combine", "uncombine", "legendre_synthesis", "fft_inv",
     "gen_lambda_fwd", "tc_gemm_fwd", "gen_lambda_adj", "tc_gemm_adj", "polar_patch", "cg_combine", "cg_uncombine",
-    "gen_lambda_both",
+    "gen_lambda_both", "cg_pack", "cg_unpack",
 };
 
 cudaEvent_t take_event(Plan &p)
@@ -1025,6 +1025,32 @@ int favest_cg_plan_create(int L, int batch, const double *cos_theta, const doubl
     return favest::plan_create_internal(L, batch, FAVEST_FP64, FAVEST_IO_C128, cos_theta, w_lat, 0, out, 1);
 }
 
+int favest_cg_plan_create_ex(int L, int batch, int io_type, const double *cos_theta, const double *w_lat,
+                             favest_plan *out)
+{
+    if (io_type == FAVEST_IO_C128) return favest_cg_plan_create(L, batch, cos_theta, w_lat, out);
+    if (!out) return FAVEST_EINVAL;
+    *out = nullptr;
+    if (io_type != FAVEST_IO_R64 || batch < 1 || batch > 2 * (4096 / 3 + 1)) return FAVEST_EINVAL;
+    // real fields 2q, 2q+1 as the complex field q of a complex plan
+    favest_plan h = nullptr;
+    int st = favest::plan_create_internal(L, (batch + 1) / 2, FAVEST_FP64, FAVEST_IO_C128, cos_theta, w_lat, 0, &h, 1);
+    if (st != FAVEST_OK) return st;
+    favest::Plan &p = h->p;
+    p.cg_real = batch;
+    const size_t K = (size_t)L * L + 2 * (size_t)L;
+    const size_t tb = (size_t)p.B * 3 * p.nlat * p.nphi * sizeof(double2), cb = (size_t)p.B * K * sizeof(double2);
+    if (favest::plan_malloc(&p.d_cgT, tb) != cudaSuccess || favest::plan_malloc(&p.d_cga, cb) != cudaSuccess ||
+        favest::plan_malloc(&p.d_cgb, cb) != cudaSuccess) {
+        cudaGetLastError();
+        favest_plan_destroy(h);
+        return FAVEST_ENOMEM;
+    }
+    p.ws_bytes += tb + 2 * cb;
+    *out = h;
+    return FAVEST_OK;
+}
+
 int favest_adj(favest_plan plan, const void *a, const void *b, void *Tth, void *Tph, void *stream)
 {
     return favest_adj_ex(plan, a, b, Tth, Tph, 0, stream);
@@ -1128,10 +1154,21 @@ int favest_fwd_cart(favest_plan plan, const void *T, void *a, void *b, void *str
     int st = check_device(p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    // real fields: packed in pairs into the plan's complex fields, coefficients split after
+    const void *Tc = T;
+    void *ac = a, *bc = b;
+    if (p.cg_real) {
+        e = timed(p, KID_CG_PACK, s, [&] { return launch_cg_pack_fields(p, T, s); });
+        Tc = p.d_cgT;
+        ac = p.d_cga;
+        bc = p.d_cgb;
+    }
     // three scalar FwdSHTs of degree L+1 (DFT, analysis with the point weights), Thm. 1
-    cudaError_t e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, T, T, s); });
+    if (e == cudaSuccess) e = timed(p, KID_FFT_FWD, s, [&] { return launch_fft_fwd_fp64(p, Tc, Tc, s); });
     if (e == cudaSuccess) e = timed(p, KID_ANALYSIS, s, [&] { return launch_analysis_fp64(p, s); });
-    if (e == cudaSuccess) e = timed(p, KID_CG_COMBINE, s, [&] { return launch_cg_combine(p, a, b, s); });
+    if (e == cudaSuccess) e = timed(p, KID_CG_COMBINE, s, [&] { return launch_cg_combine(p, ac, bc, s); });
+    if (e == cudaSuccess && p.cg_real) e = timed(p, KID_CG_UNPACK, s, [&] { return launch_cg_unpack_coefs(p, a, b, s); });
     return cuda_status(e);
 }
 
@@ -1144,10 +1181,20 @@ int favest_adj_cart(favest_plan plan, const void *a, const void *b, void *T, voi
     int st = check_device(p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    const void *ac = a, *bc = b;
+    void *Tc = T;
+    if (p.cg_real) {
+        e = timed(p, KID_CG_PACK, s, [&] { return launch_cg_pack_coefs(p, a, b, s); });
+        ac = p.d_cga;
+        bc = p.d_cgb;
+        Tc = p.d_cgT;
+    }
     // Thm. 2: summed nu/eta coefficients, three scalar syntheses of degree L+1
-    cudaError_t e = timed(p, KID_CG_UNCOMBINE, s, [&] { return launch_cg_uncombine(p, a, b, s); });
+    if (e == cudaSuccess) e = timed(p, KID_CG_UNCOMBINE, s, [&] { return launch_cg_uncombine(p, ac, bc, s); });
     if (e == cudaSuccess) e = timed(p, KID_SYNTHESIS, s, [&] { return launch_synthesis_fp64(p, s); });
-    if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, T, T, s); });
+    if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_fp64(p, Tc, Tc, s); });
+    if (e == cudaSuccess && p.cg_real) e = timed(p, KID_CG_UNPACK, s, [&] { return launch_cg_unpack_fields(p, T, s); });
     return cuda_status(e);
 }
 
@@ -1159,7 +1206,7 @@ int favest_set_weights_unit(favest_plan plan, int flag)
 }
 
 int favest_plan_L(favest_plan plan) { return plan ? plan->p.L : FAVEST_EINVAL; }
-int favest_plan_batch(favest_plan plan) { return plan ? plan->p.B : FAVEST_EINVAL; }
+int favest_plan_batch(favest_plan plan) { return plan ? (plan->p.cg_real ? plan->p.cg_real : plan->p.B) : FAVEST_EINVAL; }
 int favest_plan_precision(favest_plan plan) { return plan ? plan->p.precision : FAVEST_EINVAL; }
 size_t favest_plan_workspace_bytes(favest_plan plan) { return plan ? plan->p.ws_bytes : 0; }
 

@@ -108,6 +108,12 @@ struct Plan {
     // scalar sums at arbitrary points (favest_scatter_create): a Clebsch-Gordan plan whose
     // sums Q are formed by the point kernels, so no grid workspace is allocated
     int scattered = 0;
+    // real-field Clebsch-Gordan plans: real vector fields 2q and 2q+1 travel as the complex
+    // field q = T_2q + i T_2q+1 of this (complex, B = ceil(cg_real / 2)) plan; d_cgT holds the
+    // packed fields [B][3][nlat][nphi] and d_cga, d_cgb their full coefficient sets [B][L^2+2L]
+    // (complex double)
+    int cg_real = 0;              // number of real fields (0: a complex plan)
+    void *d_cgT = nullptr, *d_cga = nullptr, *d_cgb = nullptr;
     int nlat = 0, nphi = 0, J = 0, has_eq = 0;
     int ncol = 0;             // complex columns per order: 4 per field (c, sign of m)
     int ct = 0, ng = 0;       // FP64 column group width and count
@@ -202,7 +208,7 @@ struct Plan {
 enum KernelId {
     KID_FFT_FWD = 0, KID_ANALYSIS, KID_COMBINE, KID_UNCOMBINE, KID_SYNTHESIS, KID_FFT_INV,
     KID_GEN_FWD, KID_GEMM_FWD, KID_GEN_ADJ, KID_GEMM_ADJ, KID_POLAR, KID_CG_COMBINE, KID_CG_UNCOMBINE,
-    KID_GEN_BOTH, KID_COUNT
+    KID_GEN_BOTH, KID_CG_PACK, KID_CG_UNPACK, KID_COUNT
 };
 
 __host__ __device__ inline long long tab_off(int L, int mu) {
@@ -235,6 +241,10 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
 // Clebsch-Gordan route (FP64): scalar sums -> a, b (Thm. 1); a, b -> scalar coefficients (Thm. 2)
 cudaError_t launch_cg_combine(const Plan &p, void *a, void *b, cudaStream_t s);
 cudaError_t launch_cg_uncombine(const Plan &p, const void *a, const void *b, cudaStream_t s);
+cudaError_t launch_cg_pack_fields(const Plan &p, const void *Tr, cudaStream_t s);
+cudaError_t launch_cg_unpack_fields(const Plan &p, void *Tr, cudaStream_t s);
+cudaError_t launch_cg_pack_coefs(const Plan &p, const void *a, const void *b, cudaStream_t s);
+cudaError_t launch_cg_unpack_coefs(const Plan &p, void *a, void *b, cudaStream_t s);
 int build_polar_tables(Plan &p);   // host: chooses pol_jc, pol_muc and uploads d_pol
 
 // Every device allocation a plan (or batch, or scattered-point plan) makes goes through

@@ -125,3 +125,76 @@ def test_cg_plan_rejects_other_calls():
     st = api.lib().favest_fwd_cart(ctypes.c_void_p(p.handle), api._ptr(T), api._ptr(c), api._ptr(c),
                                    api._stream(None))
     assert e1.value.status == api.FAVEST_EINVAL and st == api.FAVEST_EINVAL
+
+
+def _rdev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(torch.float64).cuda().contiguous()
+
+
+@pytest.mark.parametrize("L,B", [(1, 1), (2, 3), (8, 2), (16, 3), (31, 1)])
+def test_cg_route_real_fields_vs_oracle_theorems(orc, L, B):
+    """Real fields (the paper's, Sec. 3) on the CG route: the half spectra (m >= 0) of the
+    forward against the oracle's Thm. 1 on the same real field, whose full spectrum must be
+    Hermitian (a_{l,-m} = (-1)^m conj a_lm, the relation the pair packing rests on); the
+    adjoint of half-spectrum coefficients against the oracle's Thm. 2 of their Hermitian
+    extension, which is real.  Odd batches leave the second field of the last pair empty."""
+    from helpers import full_of_half, half_of_full
+    x, W, theta, phi, th, ph, w = _mesh(orc, L)
+    rng = np.random.default_rng(1300 + L)
+    T = rng.standard_normal((B, 3, len(theta), len(phi)))
+    cp = api.CgPlan(L, B, real=True)
+    a, b = cp.fwd(_rdev(T))
+    ha, hb = synthetic.half_coefficients(L, B, seed=1400 + L)
+    Tr = cp.adj(_dev(ha), _dev(hb))
+    torch.cuda.synchronize()
+    assert cp.status() == 0 and Tr.dtype == torch.float64
+    for f in range(B):
+        oa, ob = cg_route.fwd_cg(L, th, ph, w, T[f].reshape(3, -1).T.astype(np.complex128))
+        assert normwise_err(full_of_half(half_of_full(oa, L), L), oa) < TOL
+        assert normwise_err(a[f].cpu().numpy(), half_of_full(oa, L)) < TOL
+        assert normwise_err(b[f].cpu().numpy(), half_of_full(ob, L)) < TOL
+        oT = cg_route.adj_cg(L, full_of_half(ha[f], L), full_of_half(hb[f], L), th, ph)   # npts x 3
+        assert np.max(np.abs(oT.imag)) < TOL * np.max(np.abs(oT.real))
+        assert normwise_err(Tr[f].cpu().numpy().reshape(3, -1).T.ravel(), oT.real.ravel()) < TOL
+
+
+@pytest.mark.parametrize("L,B", [(63, 3), (255, 2)])
+def test_cg_route_real_equals_complex_route_and_theta_phi(orc, L, B):
+    """Real CG plans against the complex CG route on the same (real-valued) fields and
+    against the real theta/phi FP64 path (FAVEST_IO_R64) on tangent fields; roundtrip."""
+    from helpers import full_of_half, half_of_full
+    x, W, theta, phi, th, ph, w = _mesh(orc, L)
+    tt, tp = synthetic.grid_field(L, B, seed=1500 + L)
+    tt, tp = tt.real.copy(), tp.real.copy()
+    Tc = np.stack([_cart_planes(orc, th, ph, tt[f], tp[f]).real for f in range(B)])
+    cr = api.CgPlan(L, B, real=True)
+    cc = api.CgPlan(L, B)
+    pr = api.Plan(L, B, api.FAVEST_FP64, api.FAVEST_IO_R64)
+    ar, br = cr.fwd(_rdev(Tc))
+    ac, bc = cc.fwd(_dev(Tc))
+    at, bt = pr.fwd(_rdev(tt), _rdev(tp))
+    torch.cuda.synchronize()
+    assert normwise_err(ar.cpu().numpy(), half_of_full(ac.cpu().numpy(), L)) < TOL
+    assert normwise_err(br.cpu().numpy(), half_of_full(bc.cpu().numpy(), L)) < TOL
+    assert normwise_err(ar.cpu().numpy(), at.cpu().numpy()) < TOL
+    assert normwise_err(br.cpu().numpy(), bt.cpu().numpy()) < TOL
+    ha, hb = synthetic.half_coefficients(L, B, seed=1600 + L)
+    Tr = cr.adj(_dev(ha), _dev(hb))
+    Tx = cc.adj(_dev(full_of_half(ha, L)), _dev(full_of_half(hb, L)))
+    ra, rb = cr.fwd(Tr)
+    torch.cuda.synchronize()
+    assert normwise_err(Tr.cpu().numpy().ravel(), Tx.cpu().numpy().real.ravel()) < TOL
+    assert normwise_err(ra.cpu().numpy(), ha) < TOL
+    assert normwise_err(rb.cpu().numpy(), hb) < TOL
+
+
+def test_cg_real_plan_arguments():
+    with pytest.raises(api.FavestError) as e:
+        api.CgPlan(8, 0, real=True)
+    assert e.value.status == api.FAVEST_EINVAL
+    h = ctypes.c_void_p()
+    assert api.lib().favest_cg_plan_create_ex(8, 1, api.FAVEST_IO_C64, None, None, ctypes.byref(h)) == api.FAVEST_EINVAL
+    cp = api.CgPlan(8, 5, real=True)
+    assert api.lib().favest_plan_batch(ctypes.c_void_p(cp.handle)) == 5
+    with pytest.raises(ValueError):
+        cp.fwd(torch.zeros((5, 3, 9, 18), dtype=torch.complex128, device="cuda"))
