@@ -389,6 +389,7 @@ def measure_forms(L, B, a, b, split_value, fp64_peak):
     forms["ragged_batch"] = {"value": len(Ls) / (ms * 1e-3), "unit": "fields/s", "ms_per_step": ms,
                              "fields": len(Ls), "graph": True, "groups": bp.groups(),
                              "launches_per_step": None}
+    forms["ragged_batch"].update(ragged_bounds(bp.groups(), stream))
     bp.close()
     del ga, gb, gt, gp, fa, fb
     # real fields (half-spectrum coefficients), L as the main workload, 32 and 64 fields
@@ -436,6 +437,50 @@ def measure_scatter(L, npts, B, stream):
             "fwd_pairs_per_s": pairs / (fwd_ms * 1e-3), "adj_pairs_per_s": pairs / (adj_ms * 1e-3),
             "adjoint_identity_rel": float(abs(lhs - rhs) / abs(rhs)), "points_recipe":
             "area-uniform random, numpy default_rng(4), unit weights"}
+
+
+def ragged_bounds(groups, stream):
+    """Where a single persistent launch could take the ragged batch: each degree group as a
+    plan of its own, run alone (adj + fwd, tuned generator, every kernel on the whole GPU) one
+    after another, and a lower bound for ANY schedule of the same kernels: each launch at its
+    roofline (favest_kernel_work's algorithmic bytes at the measured HBM bandwidth, or its
+    flops at the derived FP64 / FP32 peak), summed over the groups."""
+    import torch
+    from paper_1908_00041_gb300 import api, synthetic
+    hbm, _, _ = measured_peaks()
+    f64, f32, _, _ = alu_peaks()
+    seq_ms, lb_ms, per = 0.0, 0.0, []
+    for g in groups:
+        Lg, ng = g["L"], g["fields"]
+        pg = api.Plan(Lg, ng, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+        pg.tune()
+        ca, cb = synthetic.coefficients(Lg, ng, seed=Lg, decay=1.0)
+        da = torch.as_tensor(ca).to(torch.complex64).cuda()
+        db = torch.as_tensor(cb).to(torch.complex64).cuda()
+        tt = torch.empty(pg.field_shape(), dtype=torch.complex64, device="cuda")
+        tp = torch.empty_like(tt)
+        ra = torch.empty_like(da)
+        rb = torch.empty_like(db)
+
+        def st():
+            pg.adj(da, db, tt, tp, stream=stream)
+            pg.fwd(tt, tp, ra, rb, stream=stream)
+        t = time_steps(st, 10, 3, stream)
+        pg.profile(True)
+        pg.profile_read()
+        st()
+        prof = pg.profile_read()
+        pg.profile(False)
+        lb = 0.0
+        for name, (_, n) in prof.items():
+            nb, fl, pipe = pg.kernel_work(name)
+            rate = {1: f64 * 1e12, 3: f32 * 1e12}.get(pipe)
+            lb += n * max(nb / (hbm * 1e9), fl / rate if rate else 0.0) * 1e3
+        seq_ms += t
+        lb_ms += lb
+        per.append({"L": Lg, "fields": ng, "alone_ms": t, "roofline_ms": lb})
+        pg.close()
+    return {"groups_one_after_another_ms": seq_ms, "every_kernel_at_roofline_ms": lb_ms, "per_group": per}
 
 
 def measure_fp64_real(L, B, stream):
@@ -983,9 +1028,33 @@ def main():
         dt = max_over_ranks((time.perf_counter() - t0) / ke, dist, "cuda")
         nbytes = ha.numel() * 8 * 2
         assert torch.equal(oa[(ke - 1) % 2], ra[(ke - 1) % 2].cpu())
+        # copy rates of this machine (outside the timed region): one step's H2D alone, its D2H
+        # alone, and both at once on their two streams, CUDA events on each stream
+        def copy_ms(h2d, d2h, reps=3):
+            evs = []
+            for _ in range(reps):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                if h2d:
+                    e[0].record(s_in)
+                    with torch.cuda.stream(s_in):
+                        da[0].copy_(ha, non_blocking=True)
+                        db[0].copy_(hb, non_blocking=True)
+                    e[1].record(s_in)
+                if d2h:
+                    e[2].record(s_out)
+                    with torch.cuda.stream(s_out):
+                        oa[0].copy_(ra[0], non_blocking=True)
+                        ob[0].copy_(rb[0], non_blocking=True)
+                    e[3].record(s_out)
+                torch.cuda.synchronize()
+                evs.append(max(e[0].elapsed_time(e[1]) if h2d else 0.0, e[2].elapsed_time(e[3]) if d2h else 0.0))
+            return min(evs)
+        h2d_ms, d2h_ms, both_ms = copy_ms(True, False), copy_ms(False, True), copy_ms(True, True)
         e2e = {"value": replica_throughput(B, world, dt), "unit": "fields/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": ke,
-               "pipelined": "copy-in / compute / copy-out on three streams, two buffer slots"}
+               "pipelined": "copy-in / compute / copy-out on three streams, two buffer slots",
+               "copy_ms": {"h2d": h2d_ms, "d2h": d2h_ms, "h2d_and_d2h_together": both_ms,
+                           "h2d_gbs": nbytes / h2d_ms * 1e-6, "d2h_gbs": nbytes / d2h_ms * 1e-6}}
         del da, db, ra, rb
 
     # accuracy (outside the timed region): recovered vs drawn coefficients, and the

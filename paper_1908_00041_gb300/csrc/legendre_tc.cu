@@ -217,9 +217,10 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
 // ---------------------------------------------------------------------------
 // Persistent GEMM: every item computes out[rows 0..127][cols 0..N-1] =
 //   sum_{c < nk} A_c * B_c  (three bf16 pieces each, 6 products)
-// Warp 0 loads operand chunks with TMA (whole 512-byte rows; the forward B operand as
-// 5-D boxes gathering the 16-byte rows of 8 latitudes),
-// warp 1 issues the MMAs, warps 2.. drain TMEM (each a 32-lane quadrant and 128 columns).
+// Warp 0 loads operand chunks with TMA (boxes of whole 512-byte rows), warp 1 issues the
+// MMAs, warps 4.. drain TMEM (each a 32-lane quadrant and 128 columns; warps 2-3 idle, so
+// that the roles sit in whole warpgroups for the register split).  This kernel serves the
+// adjoint (K-major Legendre operand, bf16 piece operands); the forward runs k_tc_gemm_f.
 // TMEM: columns [0, N) hold the hi*hi product of the current K-chunk (drained into FP32
 // register sums after every chunk), columns [N, 2N) accumulate the five correction
 // products over the whole item.  Per chunk the MMA warp issues the corrections first,
@@ -231,7 +232,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kEpiCols = 128;       // TMEM columns drained by one epilogue warp
 
 template <int N>
-constexpr int gemm_threads() { return 64 + 32 * 4 * (N / kEpiCols); }
+constexpr int gemm_threads() { return 128 + 32 * 4 * (N / kEpiCols); }
 
 __device__ __forceinline__ void set_status(int *status, int code)
 {
@@ -359,7 +360,12 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
     const uint32_t tmem = S.tmem_base;
     volatile int *abort = &S.abort;
 
-    if (warp == 0) {
+    if (warp < 4) {
+      // registers: launched at 168 per thread (384 threads); warpgroup 0 (producer, MMA
+      // issuer, two idle warps) drops to 56 and the two epilogue warpgroups rise to 224, which
+      // their 128 FP32 running sums per thread need: 128 x 56 + 256 x 224 = 384 x 168
+      if constexpr (N == 256) tc::setmaxnreg_dec<56>();
+      if (warp == 0) {
         // ---------------- producer ----------------
         // (skip_loads: failure-path self-test -- nothing is loaded, so the MMA and epilogue
         // waits must run out, report FAVEST_ETIMEOUT and return)
@@ -390,14 +396,8 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                     // of whole rows starting at its byte offset / 512
                     tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
                                     &S.full[stage]);
-                    if (I.b_box) {
-                        for (int q = 0; q < kPieces; ++q)
-                            tc::tma_load_5d(S.b[stage] + q * kPieceB, tmap_b, I.bx + 8 * q, I.bw, 0, I.by,
-                                            (kChunkK / 8) * (I.bk + c), &S.full[stage]);
-                    } else {
-                        tc::tma_load_2d(S.b[stage], tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
-                                        &S.full[stage]);
-                    }
+                    tc::tma_load_2d(S.b[stage], tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
+                                    &S.full[stage]);
                     phase ^= 1u << stage;
                     issued |= 1u << stage;
                     stage = (stage + 1) % kStages;
@@ -491,10 +491,12 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                 wait_or_abort(&S.drain, 0, nullptr, poll_limit);
             }
         }
+      }
     } else {
-        // ------ epilogue (warp w >= 2: TMEM lane quadrant w % 4, columns 128 * ((w-2) / 4) ..) ------
+      if constexpr (N == 256) tc::setmaxnreg_inc<224>();
+        // ------ epilogue (warp w >= 4: TMEM lane quadrant w % 4, columns 128 * ((w-4) / 4) ..) ------
         const int quad = warp & 3;
-        const int part = (warp - 2) >> 2;
+        const int part = (warp - 4) >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t main_use = 0, corr_use = 0;
