@@ -75,10 +75,12 @@ enum favest_status_code {
 };
 
 /* Arithmetic of the Legendre contraction.  The recurrence, its underflow scaling,
- * the normalisation constants and the quadrature weights are FP64 in every mode. */
+ * the normalisation constants and the quadrature weights are FP64 in every mode (the
+ * split-precision generator runs the recurrence in double-float arithmetic, pairs of FP32
+ * numbers of about 44 significant bits, seeded from FP64 values). */
 enum favest_precision {
     FAVEST_FP64 = 0,    /* FP64 everywhere (FFT, recurrence, contraction)                */
-    FAVEST_BF16X6 = 1   /* FP32 FFT; FP64 recurrence; Legendre contraction on tcgen05
+    FAVEST_BF16X6 = 1   /* FP32 FFT; double-float recurrence; Legendre contraction on tcgen05
                            tensor cores: both operands split into three bf16 pieces
                            (24 significant bits, full FP32 exponent range), the 6 piece
                            products of weight >= 2^-16 formed, the leading product
@@ -273,7 +275,7 @@ int favest_set_weights_unit(favest_plan plan, int flag);
  * FAVEST_FLAG_SHARE_LAMBDA (both calls; split-precision plans, ignored by FP64 plans): an
  * adjoint and a forward transform on the same plan and degree contract the same Legendre
  * values lambda_l^m(theta_j) (Sec. 3, definition of Y_lm), which the split path
- * regenerates by its FP64 recurrence in every call.  With this flag on two consecutive
+ * regenerates by its recurrence in every call.  With this flag on two consecutive
  * calls of opposite direction (adjoint then forward, or forward then adjoint), the first
  * call's recurrence pass writes the values in the layouts of both directions and the second
  * call uses them without a generator launch (one launch fewer, see
@@ -316,7 +318,7 @@ const char *favest_strerror(int status);
 int favest_launches_per_call(favest_plan plan, int adjoint);
 
 /*
- * Autotuner of the split-precision path's FP64 recurrence generator.  The generator
+ * Autotuner of the split-precision path's recurrence generator.  The generator
  * runs 128 threads per block as (128 / lt) orders x lt latitudes (lt = 32, 64, 128),
  * each block covering mb order groups in turn (mb = 1, 2, 4), each thread running the
  * recurrences of 1 or 2 latitudes (lt apart) side by side.  favest_plan_tune times the
@@ -443,8 +445,8 @@ int favest_debug_check_layout(int L, int batch, int precision, int io_type, int 
  * Algorithmic work of one launch of a kernel of this plan, by the name that
  * favest_profile_read reports: *bytes = the minimum DRAM traffic (every operand read
  * once, every result written once, no re-reads, no padding), *flops = arithmetic
- * (an FMA counted as 2; for the FP64 recurrence every FP64 instruction is counted as
- * one FMA slot, i.e. 2), *pipe = the unit that bounds it in this design
+ * (an FMA counted as 2; for a recurrence every multiply-add of the exact recurrence
+ * counts as 2), *pipe = the unit that bounds it in this design
  * (0 = HBM, 1 = FP64 pipe, 2 = tensor pipe, 3 = FP32 pipe).  Host-only, no GPU work.
  * Returns FAVEST_OK, or FAVEST_EINVAL for an unknown name.
  */

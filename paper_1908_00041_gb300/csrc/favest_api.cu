@@ -112,7 +112,7 @@ void free_plan(Plan &p)
                     p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups,
-                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb};
+                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb, p.d_Adf, p.d_xdf};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     std::free(p.h_x);
@@ -279,6 +279,19 @@ int build_tables(Plan &p)
             isc[j] = make_float2((float)(1.0 / s[j]), 1.0f);
             isc[J + j] = make_float2((float)(wring[j] / s[j]), (float)wring[j]);
         }
+        // the generator's double-float operands: hi = the nearest float, lo = the nearest float
+        // to the remainder (together about 48 bits of the FP64 value)
+        std::vector<float2> Adf(ntab), xdf(J);
+        for (long long t = 0; t < ntab; ++t) {
+            const float h = (float)A[t];
+            Adf[t] = make_float2(h, (float)(A[t] - (double)h));
+        }
+        for (int j = 0; j < J; ++j) {
+            const float h = (float)x[j];
+            xdf[j] = make_float2(h, (float)(x[j] - (double)h));
+        }
+        if ((e = upload(&p.d_Adf, Adf)) || (e = upload(&p.d_xdf, xdf)))
+            return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
         if ((e = upload(&p.d_P32, P32)) || (e = upload(&p.d_M32, M32)) || (e = upload(&p.d_R32, R32)) ||
             (e = upload(&p.d_k1, k1)) || (e = upload(&p.d_omega32, om32)) ||
             (e = upload(&p.d_omega_unit32, omu32)) || (e = upload(&p.d_isc32, isc)))
@@ -1313,8 +1326,10 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         const double gv = p.gen_values, pf = p.gemm_pairs_f, pa = p.gemm_pairs_a;
         if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 64.0; *flops = fftf; }
         else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
-        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; *pipe = 1; }
-        else if (k == "gen_lambda_both") { *bytes = gv * 12.0; *flops = gv * 4.0; *pipe = 1; }
+        // the generator runs its recurrence in double-float FP32 arithmetic and is bound by
+        // its writes (6 bytes per value and layout)
+        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; }
+        else if (k == "gen_lambda_both") { *bytes = gv * 12.0; *flops = gv * 4.0; }
         else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 64.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
         else if (k == "tc_gemm_adj") { *bytes = pa * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * pa * 8.0 * G; }
         else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }

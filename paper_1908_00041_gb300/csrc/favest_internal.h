@@ -180,6 +180,8 @@ struct Plan {
     long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
     float *d_k1 = nullptr;        // [L+1] kappa of order 1 (order-0 adjoint on order-1 tiles)
+    float2 *d_Adf = nullptr;      // [ntab] A_l^mu as double-float pairs (hi, lo) for the generator
+    float2 *d_xdf = nullptr;      // [J] cos(theta_j) as double-float pairs
     // FP32 copies of the per-latitude factors the DFT stages apply ([J] each):
     float *d_omega32 = nullptr, *d_omega_unit32 = nullptr;   // omega_j, 1 / sin(theta_j)
     float2 *d_isc32 = nullptr;    // [2][J] (1/sin, 1) and (w_j/sin, w_j): inverse DFT scales

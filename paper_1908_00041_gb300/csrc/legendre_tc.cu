@@ -3,8 +3,8 @@
 // Per order mu and parity p the Legendre stage is a dense product:
 //   forward : Q[rows, n]   = sum_j  Lam[rows, j] * Fb[j, n]      (rows = l - mu of parity p)
 //   adjoint : S_p[j, n]    = sum_r  Lam[r, j]   * g[r, n]
-// Lam (the FP64 recurrence values) is produced by a generator kernel and stored as
-// three bf16 pieces (hi + mid + lo = the FP64 value truncated to 24 bits); g carries three
+// Lam (the recurrence values, run in double-float arithmetic) is produced by a generator
+// kernel and stored as three bf16 pieces (hi + mid + lo = the value rounded to FP32); g carries three
 // bf16 pieces as well, and Fb (FP32 records from the forward DFT) is split into three pieces
 // by converter warps of the forward GEMM as it is loaded.  The GEMM kernels form 6 of the 9
 // piece products (those with combined weight >= 2^-16 of the leading one).  Because the tensor core
@@ -38,18 +38,8 @@ constexpr int kPieceBytes = kTileM * kChunkK * 2;  // 8 KB: one bf16 piece of an
 constexpr int kPieces = 3;
 constexpr int kChunkBytes = kPieces * kPieceBytes;  // 24 KB
 
-// FP64 value -> three bf16 pieces.  The value is first truncated to FP32 with integer
-// operations (FP64->FP32 conversion instructions run on the FP64 pipe), then split
-// exactly: hi = bf16(f), mid = bf16(f - hi), lo = bf16(f - hi - mid).
-__device__ __forceinline__ float d2f_trunc(double y)
-{
-    const unsigned hi = (unsigned)__double2hiint(y), lo = (unsigned)__double2loint(y);
-    const unsigned ab = hi & 0x7fffffffu;
-    unsigned fb = ((ab - (896u << 20)) << 3) | (lo >> 29);
-    fb = (ab >= (897u << 20)) ? fb : 0u;          // |y| < 2^-126 -> 0
-    return __uint_as_float(fb | (hi & 0x80000000u));
-}
-
+// FP32 value -> three bf16 pieces, split exactly: hi = bf16(f), mid = bf16(f - hi),
+// lo = bf16(f - hi - mid).
 __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned short &m, unsigned short &l)
 {
     __nv_bfloat16 bh = __float2bfloat16_rn(f);
@@ -64,11 +54,12 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 
 // Generator: 128 threads per CTA arranged as (128 / lt) orders x lt latitudes (lt = 32,
 // 64 or 128, a multiple of the warp so each warp runs one order); a CTA covers mb such
-// order groups in turn.  A thread runs the scaled FP64 recurrences of one order at NJ
-// (1 or 2) latitudes lt apart (the block covers NJ lt consecutive latitudes) over all rows
-// l = mu..L+1, interleaved step by step: each step of a recurrence depends on the one
-// before, so independent chains in the same thread keep more FP64 work in flight per warp
-// (at the price of registers and of fewer, longer blocks for small grids).
+// order groups in turn.  A thread runs the scaled recurrences of one order (double-float
+// FP32 pairs, recurrence.cuh) at NJ (1 or 2) latitudes lt apart (the block covers NJ lt
+// consecutive latitudes) over all rows l = mu..L+1, interleaved step by step: each step of
+// a recurrence depends on the one before, so independent chains in the same thread keep
+// more work in flight per warp (at the price of registers and of fewer, longer blocks for
+// small grids).  The high part of each value, its FP32 rounding, is split into the pieces.
 // Per parity it packs 8 consecutive rows into one 16-byte core-matrix row per piece.
 // (lt, mb) is the block shape the autotuner picks per degree.  Latitudes below jc0 (the
 // order's turning bound rounded down to a K-chunk: every value there is below 1e-13) and
@@ -83,12 +74,12 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 template <int MODE, int kGenJ>
 __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off,
                                           unsigned char *__restrict__ lam_a, const long long *__restrict__ lam_a_off,
-                                          const double *__restrict__ xj, const double *__restrict__ sj,
-                                          const double *__restrict__ cmu, const double *__restrict__ Atab, int L,
+                                          const float2 *__restrict__ xdf, const double *__restrict__ sj,
+                                          const double *__restrict__ cmu, const float2 *__restrict__ Adf, int L,
                                           int J, int JP, int mu, const int (&jv)[kGenJ], int jc0)
 {
     const int nrow = L + 2 - mu;
-    const double *As = Atab + tab_off(L, mu);   // recurrence multipliers of this order
+    const float2 *As = Adf + tab_off(L, mu);    // recurrence multipliers of this order (double-float)
 
     bool act[kGenJ];
     bool any = false;
@@ -98,17 +89,18 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
         any |= act[i];
     }
     if (!any) return;
-    double y1[kGenJ], y2[kGenJ], x[kGenJ];
+    Df y1[kGenJ], y2[kGenJ], x[kGenJ];
     int c[kGenJ];
 #pragma unroll
     for (int i = 0; i < kGenJ; ++i) {
-        y1[i] = 0.0;
-        y2[i] = 0.0;
+        y1[i] = Df{0.f, 0.f};
+        y2[i] = Df{0.f, 0.f};
         c[i] = 1 << 20;                            // inactive chains stay silent
-        x[i] = 0.0;
+        x[i] = Df{0.f, 0.f};
         if (act[i]) {
-            x[i] = xj[jv[i]];
-            sectoral_start(cmu[mu], sj[jv[i]], mu, y1[i], c[i]);
+            const float2 xv = __ldg(xdf + jv[i]);
+            x[i] = Df{xv.x, xv.y};
+            sectoral_start_df(cmu[mu], sj[jv[i]], mu, y1[i], c[i]);
         }
     }
     const int nk_f = JP / kChunkK;                 // forward K chunks (latitudes)
@@ -130,17 +122,18 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
         for (int w = 0; w < 16; ++w) {
             const int r = r0 + w;
             if (r < nrow) {
-                const double a = __ldg(As + r);
+                const float2 av = __ldg(As + r);
+                const Df a{av.x, av.y};
 #pragma unroll
                 for (int i = 0; i < kGenJ; ++i) {
-                    if (!act[i]) continue;                 // no FP64 work for inactive chains
-                    double yl = y1[i];
+                    if (!act[i]) continue;                 // no work for inactive chains
+                    Df yl = y1[i];
                     if (r > 0) {
-                        yl = fma(a * x[i], y1[i], -y2[i]);
+                        yl = df_sub(df_mul(df_mul(a, x[i]), y1[i]), y2[i]);
                         y2[i] = y1[i];
                         y1[i] = yl;
                     }
-                    const float f = (c[i] == 0) ? d2f_trunc(yl) : 0.0f;
+                    const float f = (c[i] == 0) ? yl.h : 0.0f;
                     unsigned short h, m, l;
                     split3(f, h, m, l);
                     const int p = w & 1, slot = w >> 1;         // r0 is a multiple of 16
@@ -152,7 +145,7 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
             }
         }
 #pragma unroll
-        for (int i = 0; i < kGenJ; ++i) renorm(y1[i], y2[i], c[i]);   // growth over 16 rows stays far below 2^700
+        for (int i = 0; i < kGenJ; ++i) renorm_df(y1[i], y2[i], c[i]);   // growth over 16 rows stays below 2^26
         // flush: rows r0/2 .. r0/2+7 of each parity
         const int rp = r0 >> 1;                        // multiple of 8
 #pragma unroll
@@ -196,8 +189,8 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
 template <int MODE, int kGenJ>
 __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off, unsigned char *__restrict__ lam_a,
-    const long long *__restrict__ lam_a_off, const double *__restrict__ xj, const double *__restrict__ sj,
-    const double *__restrict__ cmu, const double *__restrict__ Atab, const int *__restrict__ jcmin, int L, int J,
+    const long long *__restrict__ lam_a_off, const float2 *__restrict__ xdf, const double *__restrict__ sj,
+    const double *__restrict__ cmu, const float2 *__restrict__ Adf, const int *__restrict__ jcmin, int L, int J,
     int JP, int lt, int mb)
 {
     const int olanes = kGenThreads / lt;
@@ -209,7 +202,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     for (int k = 0; k < mb; ++k) {
         const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
         if (mu > L) break;
-        gen_order<MODE, kGenJ>(lam_f, lam_f_off, lam_a, lam_a_off, xj, sj, cmu, Atab, L, J, JP, mu, jv,
+        gen_order<MODE, kGenJ>(lam_f, lam_f_off, lam_a, lam_a_off, xdf, sj, cmu, Adf, L, J, JP, mu, jv,
                                __ldg(jcmin + mu));
     }
 }
@@ -943,8 +936,8 @@ void launch_gen_t(const Plan &p, int lt, int mb, cudaStream_t s)
     const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
     const int grid = ((p.JP + NJ * lt - 1) / (NJ * lt)) * ogroups;
     k_gen_lambda<MODE, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f,
-                                                        (unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_x, p.d_sin,
-                                                        p.d_cmu, p.d_A, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
+                                                        (unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_xdf, p.d_sin,
+                                                        p.d_cmu, p.d_Adf, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
 }
 
 template <int NJ>

@@ -71,6 +71,87 @@ __device__ __forceinline__ void renorm(double &y1, double &y2, int &c)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// The same recurrence in double-float arithmetic (value = h + l, two FP32 numbers, about
+// 44 significant bits) for the split path's generator, whose output keeps 24 bits: the
+// FP32 pipe issues 64 times the FP64 one on this GPU.  The products and sums are the
+// error-free transformations of Dekker (product through an FMA) and Knuth (two-sum), with
+// _rn intrinsics so that no multiply-add is contracted behind their backs.
+//   y_l = (A_l x) y_{l-1} - y_{l-2} with A_l and x given as double-float pairs.
+// FP32 has an 8-bit exponent, so the scaling runs in steps of 2^100: values are lifted to at
+// least 2^-60 at the start and stepped down by 2^-100 when they reach 2^40 (checked every 16
+// rows, over which they grow by less than 3^16 < 2^26); while c > 0 the true value is below
+// 2^-60 and is emitted as zero.
+struct Df {
+    float h, l;
+};
+
+__device__ __forceinline__ Df df_mul(Df a, Df b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);                 // exact low part of a.h b.h
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const float s = __fadd_rn(p, e);
+    return Df{s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ Df df_sub(Df a, Df b)
+{
+    const float s = __fsub_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);                 // two-sum of a.h and -b.h
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(-b.h, bb));
+    e = __fadd_rn(e, __fsub_rn(a.l, b.l));
+    const float r = __fadd_rn(s, e);
+    return Df{r, __fsub_rn(e, __fsub_rn(r, s))};
+}
+
+constexpr int kDfScaleBits = 100;     // one scale step = 2^100
+constexpr int kDfStartFloor = -60;    // start values are lifted to >= 2^-60
+constexpr int kDfRenormAt = 40;       // scaled values >= 2^40 are stepped down
+
+// lambda_mu^mu(theta) = (-1)^mu cmu sin(theta)^mu as a double-float (y, c): true = y 2^(-100 c)
+__device__ __forceinline__ void sectoral_start_df(double cmu, double s, int mu, Df &y, int &c)
+{
+    double f = 1.0, base = s;
+    int e = 0, eb = 0;
+    frexp_acc(base, eb);
+    int n = mu;
+    while (n) {
+        if (n & 1) {
+            f *= base;
+            e += eb;
+            frexp_acc(f, e);
+        }
+        n >>= 1;
+        if (n) {
+            base *= base;
+            eb *= 2;
+            frexp_acc(base, eb);
+        }
+    }
+    const double v = (mu & 1) ? -cmu * f : cmu * f;
+    int cc = 0;
+    if (e < kDfStartFloor) cc = (kDfStartFloor - e + kDfScaleBits - 1) / kDfScaleBits;
+    const double d = ldexp(v, e + kDfScaleBits * cc);
+    const float h = (float)d;
+    y = Df{h, (float)(d - (double)h)};
+    c = cc;
+}
+
+// Step a scaled pair down by 2^100 when the newest value reached 2^40.
+__device__ __forceinline__ void renorm_df(Df &y1, Df &y2, int &c)
+{
+    if (c > 0) {
+        const int ex = (__float_as_int(y1.h) >> 23) & 0xff;
+        if (ex >= 127 + kDfRenormAt) {
+            y1 = Df{y1.h * 0x1p-100f, y1.l * 0x1p-100f};
+            y2 = Df{y2.h * 0x1p-100f, y2.l * 0x1p-100f};
+            c -= 1;
+        }
+    }
+}
+
 // Sum V values (V a multiple of 32) over the 32 lanes of a warp: afterwards lane l holds in
 // v[0 .. V/32) the warp totals of the values with indices l*V/32 .. l*V/32 + V/32 - 1.
 // Each level halves the values a lane keeps and exchanges the other half with the lane o
