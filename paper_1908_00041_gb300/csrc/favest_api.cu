@@ -112,9 +112,13 @@ void free_plan(Plan &p)
                     p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
                     p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups,
-                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb, p.d_Adf, p.d_xdf};
+                    p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb, p.d_Adf, p.d_xdf,
+                    p.d_pol_lim, p.d_polS};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (p.pol_fork) cudaEventDestroy(p.pol_fork);
+    if (p.pol_join) cudaEventDestroy(p.pol_join);
+    if (p.pol_stream) cudaStreamDestroy(p.pol_stream);
     std::free(p.h_x);
     std::free(p.h_w);
 }
@@ -1144,11 +1148,21 @@ int favest_adj_ex(favest_plan plan, const void *a, const void *b, void *Tth, voi
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (p.precision == FAVEST_BF16X6) {
-        e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_bf16(p, a, b, s); });
+        // the polar patch reads only the coefficients and its tables and writes a buffer of
+        // its own: it runs on the plan's side stream next to the uncombine, generator and
+        // GEMM, forked from and joined back into the caller's stream (graph capture follows)
+        e = cudaSuccess;
+        if (p.pol_jc > 0) {
+            e = cudaEventRecord(p.pol_fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(p.pol_stream, p.pol_fork, 0);
+            if (e == cudaSuccess)
+                e = timed(p, KID_POLAR, p.pol_stream, [&] { return launch_polar_patch(p, a, b, p.pol_stream); });
+            if (e == cudaSuccess) e = cudaEventRecord(p.pol_join, p.pol_stream);
+        }
+        if (e == cudaSuccess) e = timed(p, KID_UNCOMBINE, s, [&] { return launch_uncombine_bf16(p, a, b, s); });
         if (e == cudaSuccess) e = legendre_operand(p, kGenAdj, (flags & FAVEST_FLAG_SHARE_LAMBDA) != 0, s);
         if (e == cudaSuccess) e = timed(p, KID_GEMM_ADJ, s, [&] { return launch_tc_gemm(p, false, s); });
-        if (e == cudaSuccess && p.pol_jc > 0)
-            e = timed(p, KID_POLAR, s, [&] { return launch_polar_patch(p, a, b, s); });
+        if (e == cudaSuccess && p.pol_jc > 0) e = cudaStreamWaitEvent(s, p.pol_join, 0);
         if (e == cudaSuccess) e = timed(p, KID_FFT_INV, s, [&] { return launch_fft_inv_bf16(p, Tth, Tph, s); });
         return cuda_status(e);
     }

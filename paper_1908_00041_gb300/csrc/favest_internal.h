@@ -190,6 +190,11 @@ struct Plan {
     // polar patch of the split adjoint: rings j < pol_jc, orders 1 <= mu < pol_muc
     int pol_jc = 0, pol_muc = 0;
     float2 *d_pol = nullptr;      // [pol_jc][L+1][pol_muc] (D_l, Lambda_l) in fp32
+    int *d_pol_lim = nullptr;     // [pol_jc] first order beyond ring j's turning bound (+16)
+    float *d_polS = nullptr;      // [ncg][pol_jc][pol_muc][2][8] patched even/odd sums
+    // the patch runs on a stream of its own next to the adjoint's other stages
+    cudaStream_t pol_stream = nullptr;
+    cudaEvent_t pol_fork = nullptr, pol_join = nullptr;
     TcItem *d_items_f = nullptr, *d_items_a = nullptr;
 
     // workspace

@@ -1063,6 +1063,30 @@ __device__ __forceinline__ void stream_records(const float *__restrict__ S32, co
     __syncthreads();
 }
 
+// The even/odd sums of ring j, order mu: the polar patch's (its own buffer
+// polS[group][pol_jc][pol_muc][parity][8], written next to the GEMM) for the pairs it
+// recomputed -- rings j < pol_jc, orders 1 <= mu < pol_muc whose tile of 32 starts below
+// lim, the bound of the last ring of j's pair -- else the GEMM's, as streamed.
+__device__ __forceinline__ void polar_or_gemm(const float *__restrict__ polS, int lim, int muc, size_t base, int mu,
+                                              const float (&ev_in)[8], const float (&ov_in)[8], float (&ev)[8],
+                                              float (&ov)[8])
+{
+    if (polS && mu >= 1 && mu < muc && (mu & ~31) < lim) {
+        const float4 *src = reinterpret_cast<const float4 *>(polS + (base + mu) * 16);
+        const float4 v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2), v3 = __ldg(src + 3);
+        ev[0] = v0.x; ev[1] = v0.y; ev[2] = v0.z; ev[3] = v0.w;
+        ev[4] = v1.x; ev[5] = v1.y; ev[6] = v1.z; ev[7] = v1.w;
+        ov[0] = v2.x; ov[1] = v2.y; ov[2] = v2.z; ov[3] = v2.w;
+        ov[4] = v3.x; ov[5] = v3.y; ov[6] = v3.z; ov[7] = v3.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            ev[k] = ev_in[k];
+            ov[k] = ov_in[k];
+        }
+    }
+}
+
 // grid: B * J; S32 = [field][JP/4][L+1][parity][4][8] fp32; shared 4 * n float2 (+ padding)
 // and, for power-of-two n, the record stream's two boxes
 template <int LOG2N>
@@ -1070,7 +1094,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     const float *__restrict__ S32, const __grid_constant__ CUtensorMap tmap_s, float2 *__restrict__ Tth,
     float2 *__restrict__ Tph, RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
     const float2 *__restrict__ isc, int L, int nlat, int J, int has_eq, int JP, const long long *__restrict__ toff,
-    int *status)
+    int *status, const float *__restrict__ polS, const int *__restrict__ plim, int pol_jc, int pol_muc)
 {
     extern __shared__ float4 sm_i4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_i4);
@@ -1088,7 +1112,12 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
         const int i = threadIdx.x * n + (LOG2N < 0 ? __ldg(perm + n / 2) : n / 2);
         buf[LOG2N > 0 ? padi(i) : i] = make_float2(0.f, 0.f);
     }
-    auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
+    const bool polar = j < pol_jc;
+    const int plim_j = polar ? __ldg(plim + ((j | 1) < pol_jc ? (j | 1) : pol_jc - 1)) : 0;
+    const size_t pbase = ((size_t)b * (polar ? pol_jc : 0) + j) * pol_muc;
+    auto put = [&](int mu, const float (&ev_in)[8], const float (&ov_in)[8]) {
+        float ev[8], ov[8];
+        polar_or_gemm(polar ? polS : nullptr, plim_j, pol_muc, pbase, mu, ev_in, ov_in, ev, ov);
         // order 0 arrives already divided by sin(theta) (synthesised on lambda^1)
         const float sc = mu == 0 ? w0 : is;
         const int pp = LOG2N < 0 ? __ldg(perm + mu) : mu;
@@ -1235,7 +1264,8 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
     const float *__restrict__ S32, const __grid_constant__ CUtensorMap tmap_s, float *__restrict__ Tth,
     float *__restrict__ Tph, RadixPlanArg rp, const float2 *__restrict__ tw, const int *__restrict__ perm,
     const float2 *__restrict__ isc, int L, int nlat, int J, int has_eq, int JP, int B,
-    const long long *__restrict__ toff, int *status)
+    const long long *__restrict__ toff, int *status, const float *__restrict__ polS, const int *__restrict__ plim,
+    int pol_jc, int pol_muc)
 {
     extern __shared__ float4 sm_s4[];
     float2 *buf = reinterpret_cast<float2 *>(sm_s4);
@@ -1251,7 +1281,12 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_rff
         const int i = threadIdx.x * n + (LOG2N < 0 ? __ldg(perm + n / 2) : n / 2);
         buf[LOG2N > 0 ? padi(i) : i] = make_float2(0.f, 0.f);
     }
-    auto put = [&](int mu, const float (&ev)[8], const float (&ov)[8]) {
+    const bool polar = j < pol_jc;
+    const int plim_j = polar ? __ldg(plim + ((j | 1) < pol_jc ? (j | 1) : pol_jc - 1)) : 0;
+    const size_t pbase = ((size_t)q * (polar ? pol_jc : 0) + j) * pol_muc;
+    auto put = [&](int mu, const float (&ev_in)[8], const float (&ov_in)[8]) {
+        float ev[8], ov[8];
+        polar_or_gemm(polar ? polS : nullptr, plim_j, pol_muc, pbase, mu, ev_in, ov_in, ev, ov);
         const float sc = mu == 0 ? w0 : is;
         const int pp = LOG2N < 0 ? __ldg(perm + mu) : mu;
         const int pm = LOG2N < 0 ? (mu == 0 ? 0 : __ldg(perm + n - mu)) : n - mu;
@@ -1347,14 +1382,16 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<p.ncg * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, p.tmap_s32, (float *)Tth, (float *)Tph, rp,
                                                  p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0),
-                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff, p.d_status);
+                                                 p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff, p.d_status,
+                                                 p.d_polS, p.d_pol_lim, p.pol_jc, p.pol_muc);
         return cudaGetLastError();
     }
     auto k = k_fft_inv_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<p.B * p.J, kFftThreads, smem, s>>>((const float *)p.d_S32, p.tmap_s32, (float2 *)Tth, (float2 *)Tph, rp,
                                    p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0), p.L, p.nlat,
-                                   p.J, p.has_eq, p.JP, p.d_toff, p.d_status);
+                                   p.J, p.has_eq, p.JP, p.d_toff, p.d_status, p.d_polS, p.d_pol_lim, p.pol_jc,
+                                   p.pol_muc);
     return cudaGetLastError();
 }
 

@@ -19,8 +19,10 @@
 // exponentially small, so their error is negligible.
 //
 // Only the theta/phi structure of the combine stage and the E/O parity split of the
-// folded grid are used; the output goes to the same buffer S32 the GEMM writes,
-//   S32[group][JP/4][mu][parity][4][8], columns c*4 + s*2 + (re, im): c = theta/phi,
+// folded grid are used; the output goes to a buffer of its own, which the inverse DFT reads
+// in place of the GEMM's sums for the patched (ring, order) pairs (so the patch does not
+// wait for the GEMM),
+//   polS[group][pol_jc][pol_muc][parity][8], columns c*4 + s*2 + (re, im): c = theta/phi,
 //   s = 0: m = +mu, s = 1: m = -mu (with the factor (-1)^mu of lambda^{-mu}); for real
 //   fields (REAL = true) slot s holds field 2q + s of the pair q at m = +mu, with the
 //   half-spectrum coefficients (index l(l+1)/2 - 1 + mu of a field's K).
@@ -68,11 +70,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// first order whose tensor-core values ring j keeps (beyond its turning-point bound)
-__device__ __forceinline__ int polar_mulim(const double *__restrict__ sin_j, int L, int j)
-{
-    return (int)ceil(1.5 * (L + 1) * sin_j[j]) + 16;
-}
 
 // grid (pol_muc / 32, column groups, ceil(pol_jc / 10)), 160 threads, 112 KB of shared
 // memory (two blocks per SM).  Lane = order mu within the tile; warp w takes the rings
@@ -89,7 +86,7 @@ __device__ __forceinline__ int polar_mulim(const double *__restrict__ sin_j, int
 template <bool REAL>
 __global__ void __launch_bounds__(kPolarThreads, 2) k_polar_patch(
     const float2 *__restrict__ a, const float2 *__restrict__ b, const float2 *__restrict__ tab,
-    const double *__restrict__ sin_j, float *__restrict__ S32, int L, int K, int jc, int muc, int JP,
+    const int *__restrict__ plim, float *__restrict__ polS, int L, int K, int jc, int muc,
     const long long *__restrict__ coff, int B, float ps)
 {
     extern __shared__ float4 pol_sm[];
@@ -103,10 +100,10 @@ __global__ void __launch_bounds__(kPolarThreads, 2) k_polar_patch(
     const int f = blockIdx.y;
     const int jb = blockIdx.z * kPolarPairs * kPolarJ;
     const int je = jb + kPolarPairs * kPolarJ < jc ? jb + kPolarPairs * kPolarJ : jc;
-    if (mu0 >= polar_mulim(sin_j, L, je - 1)) return;   // uniform: the last ring has the largest bound
+    if (mu0 >= __ldg(plim + je - 1)) return;   // uniform: the last ring has the largest bound
     const int j0 = jb + warp * kPolarJ;
     const int nring = j0 < jc ? (jc - j0 < kPolarJ ? jc - j0 : kPolarJ) : 0;
-    const bool wact = nring > 0 && mu0 < polar_mulim(sin_j, L, j0 + nring - 1);
+    const bool wact = nring > 0 && mu0 < __ldg(plim + j0 + nring - 1);
     const bool active = mu >= 1 && mu <= L && mu < muc;
     const bool has1 = !REAL || 2 * f + 1 < B;       // the pair's second field exists
     // coefficient offsets: field f (complex), or the pair's fields 2f and 2f+1 (real)
@@ -242,8 +239,7 @@ __global__ void __launch_bounds__(kPolarThreads, 2) k_polar_patch(
             }
             const int par = k ^ (mu & 1);
             const float sg = (!REAL && (mu & 1)) ? -1.f : 1.f;     // columns of m = -mu
-            float4 *dst = reinterpret_cast<float4 *>(
-                S32 + ((((size_t)f * (JP / 4) + (j >> 2)) * (L + 1) + mu) * 2 + par) * 32 + (j & 3) * 8);
+            float4 *dst = reinterpret_cast<float4 *>(polS + ((((size_t)f * jc + j) * muc + mu) * 2 + par) * 8);
             dst[0] = make_float4(v[0], v[1], sg * v[2], sg * v[3]);
             dst[1] = make_float4(v[4], v[5], sg * v[6], sg * v[7]);
         }
@@ -312,10 +308,28 @@ int build_polar_tables(Plan &p)
             }
         }
     }
-    if (plan_malloc((void **)&p.d_pol, tab.size() * sizeof(float2)) != cudaSuccess) {
+    // per ring the first order whose tensor-core values it keeps (beyond its turning-point
+    // bound); the inverse DFT takes the patched sums of ring j for the orders 1 <= mu < muc
+    // whose tile of 32 starts below the bound of the last ring of j's warp pair (j | 1)
+    std::vector<int> lim(jc);
+    for (int j = 0; j < jc; ++j) {
+        const double x = p.h_x[j];
+        lim[j] = (int)std::ceil(1.5 * (L + 1) * std::sqrt((1.0 - x) * (1.0 + x))) + 16;
+    }
+    const size_t sbytes = (size_t)p.ncg * jc * muc * 16 * sizeof(float);
+    if (plan_malloc((void **)&p.d_pol, tab.size() * sizeof(float2)) != cudaSuccess ||
+        plan_malloc((void **)&p.d_pol_lim, lim.size() * sizeof(int)) != cudaSuccess ||
+        plan_malloc((void **)&p.d_polS, sbytes) != cudaSuccess) {
         cudaGetLastError();
         return FAVEST_ENOMEM;
     }
+    if (cudaMemcpy(p.d_pol_lim, lim.data(), lim.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p.d_polS, 0, sbytes) != cudaSuccess)
+        return FAVEST_ECUDA;
+    if (cudaStreamCreateWithFlags(&p.pol_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p.pol_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p.pol_join, cudaEventDisableTiming) != cudaSuccess)
+        return FAVEST_ECUDA;
     if (cudaMemcpy(p.d_pol, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
         return FAVEST_ECUDA;
     return FAVEST_OK;
@@ -327,8 +341,8 @@ cudaError_t launch_polar_patch(const Plan &p, const void *a, const void *b, cuda
     dim3 grid(p.pol_muc / 32, p.ncg, (p.pol_jc + kPolarPairs * kPolarJ - 1) / (kPolarPairs * kPolarJ));
     auto k = p.real ? k_polar_patch<true> : k_polar_patch<false>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPolarSmem);
-    k<<<grid, kPolarThreads, kPolarSmem, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_sin, p.d_S32, p.L, K,
-                                        p.pol_jc, p.pol_muc, p.JP, p.d_coff, p.B, p.real_transpose ? 0.5f : 1.f);
+    k<<<grid, kPolarThreads, kPolarSmem, s>>>((const float2 *)a, (const float2 *)b, p.d_pol, p.d_pol_lim, p.d_polS,
+                                        p.L, K, p.pol_jc, p.pol_muc, p.d_coff, p.B, p.real_transpose ? 0.5f : 1.f);
     return cudaGetLastError();
 }
 
