@@ -424,10 +424,11 @@ long long favest_debug_alloc_count(void);
  * grid -- for FAVEST_BF16X6 the tensor-core GEMM work items of both directions, the
  * per-(order, parity) operand regions and the forward operand's TMA box coordinates, with
  * gemm_n = 0 (the plan's own tile width) or 256 (the width ragged batches use) -- and
- * checks every index the kernels take from them against the buffer it addresses: operand
- * chunk ranges and their 512-byte row alignment, box coordinates against the tensor map's
- * extents, output rows and column groups against the output buffer and the rows of the
- * item's own order, regions in order and disjoint.  FP64 plans have no such tables and
+ * checks every index the kernels take from them against the buffer it addresses: the
+ * Legendre operand's boxes (row and latitude blocks) against the rows of the item's own
+ * order and the tensor's extents, the other operands' chunk ranges, 512-byte row
+ * alignment and box coordinates, output rows and column groups against the output buffer
+ * and the rows of the item's own order, regions in order and disjoint.  FP64 plans have no such tables and
  * return FAVEST_OK once their arguments pass.  Returns FAVEST_OK; the argument errors of
  * favest_plan_create (FAVEST_EINVAL, FAVEST_EUNSUPPORTED) and FAVEST_EINVAL for another
  * gemm_n or msg_len < 0; or FAVEST_EINTERNAL with a description of the first violation
@@ -435,8 +436,8 @@ long long favest_debug_alloc_count(void);
  * 0).  favest_plan_create runs the same check and fails with FAVEST_EINTERNAL likewise.
  * poison (tests of the check itself; 0 in normal use) corrupts the check's own copy of the
  * tables first: 1 moves the first forward item to order L + 1, 2 gives the last adjoint
- * item one K-chunk too many, 3 makes the first two forward operand regions overlap; other
- * values give FAVEST_EINVAL.
+ * item one K-chunk too many, 3 makes the Legendre row blocks of the first two (order,
+ * parity) regions overlap; other values give FAVEST_EINVAL.
  */
 int favest_debug_check_layout(int L, int batch, int precision, int io_type, int gemm_n, int poison, char *msg,
                               int msg_len);

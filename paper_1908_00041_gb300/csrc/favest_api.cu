@@ -108,9 +108,9 @@ cudaError_t upload(T **p, const std::vector<T> &h)
 void free_plan(Plan &p)
 {
     void *ptrs[] = {p.d_x, p.d_sin, p.d_omega, p.d_omega_unit, p.d_cmu, p.d_A, p.d_P, p.d_M, p.d_R,
-                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam_f, p.d_lam_a, p.d_Fb, p.d_gb,
+                    p.d_status, p.d_F, p.d_Q, p.d_G, p.fft.tw64, p.fft.tw32, p.d_lam, p.d_Fb, p.d_gb,
                     p.d_jcmin, p.d_omega32, p.d_omega_unit32, p.d_isc32, p.d_kap,
-                    p.d_Q32, p.d_S32, p.d_lam_off_f, p.d_lam_off_a, p.d_g_off, p.d_items_f, p.d_items_a,
+                    p.d_Q32, p.d_S32, p.d_lam_rb, p.d_g_off, p.d_items_f, p.d_items_a,
                     p.d_P32, p.d_M32, p.d_R32, p.d_k1, p.d_perm, p.d_pol, p.d_wring, p.d_ggroups,
                     p.fft.blue_chirp, p.fft.blue_spec, p.fft.blue_tw, p.d_cgT, p.d_cga, p.d_cgb, p.d_Adf, p.d_xdf,
                     p.d_pol_lim, p.d_polS};
@@ -395,6 +395,31 @@ int make_s32_tensor_map(Plan &p)
 
 // A GEMM operand buffer as seen by the TMA: a 2-D array of 512-byte rows (256 bf16 each),
 // loaded in boxes of box_rows whole rows (one operand chunk).
+// Tensor map of the Legendre operand [piece][row block][JP latitudes][8 rows] (bf16) as
+// (256 = 32 latitudes x 8 rows, latitude block, row block, piece): a box {256, yb, zb, 3}
+// lands in shared memory as [piece][zb row blocks][32 yb latitudes][8 rows], each piece a
+// core-matrix layout of the MMA (8 consecutive latitudes x 8 rows per 128-byte matrix).
+// Boxes past the last row block read zeros.
+int make_lam_tensor_map(Plan &p, int yb, int zb, CUtensorMap *out)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return FAVEST_EUNSUPPORTED;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t JP = (cuuint64_t)p.JP, RB = (cuuint64_t)p.lam_rb_total;
+    cuuint64_t dims[4] = {256, JP / 32, RB, 3};
+    cuuint64_t strides[3] = {512, JP * 16, RB * JP * 16};
+    cuuint32_t box[4] = {256, (cuuint32_t)yb, (cuuint32_t)zb, 3};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p.d_lam, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FAVEST_OK : FAVEST_EUNSUPPORTED;
+}
+
 int make_row_tensor_map(void *base, size_t bytes, int box_rows, CUtensorMap *out)
 {
     void *fn = nullptr;
@@ -476,21 +501,21 @@ std::vector<int> turning_bounds(const Plan &p)
 // batch, io, latitudes) before it touches the device, so that check_layout_bf16 and
 // favest_debug_check_layout can examine it without a GPU.
 struct SplitLayout {
-    std::vector<long long> off_f, off_a, off_g;   // per (mu, parity): operand offsets (bytes)
+    std::vector<int> rb;                          // per (mu, parity): first row block of Lam
+    std::vector<long long> off_g;                 // per (mu, parity): coefficient operand offset (bytes)
     std::vector<int> jcmin;                       // per mu: first generated latitude chunk
     std::vector<TcItem> itf, ita;                 // GEMM items, launch order
-    long long CHA = 0, CHB = 0;                   // bytes per A / B chunk
-    size_t lamf_bytes = 0, lama_bytes = 0, fb_bytes = 0, g_bytes = 0, q_bytes = 0, s_bytes = 0;
+    long long CHB = 0;                            // bytes per B chunk (adjoint)
+    long long rb_total = 0;                       // row blocks of Lam in all
+    size_t lam_bytes = 0, fb_bytes = 0, g_bytes = 0, q_bytes = 0, s_bytes = 0;
 };
 
 int layout_bf16(Plan &p, SplitLayout &Y)
 {
     const int L = p.L;
     const int KC = kGemmChunkK;
-    const long long CHA = 3LL * 128 * KC * 2;    // bytes per A chunk (3 bf16 pieces of 128 x KC)
     p.gemm_n = (p.force_gemm_n == 256 || 8 * p.ncg > 128) ? 256 : 128;
     const long long CHB = 3LL * KC * p.gemm_n * 2;   // bytes per B chunk (3 pieces of KC x N)
-    Y.CHA = CHA;
     Y.CHB = CHB;
     p.JP = (p.J + 127) / 128 * 128;
     p.ncolr = (8 * p.ncg + p.gemm_n - 1) / p.gemm_n * p.gemm_n;
@@ -499,9 +524,9 @@ int layout_bf16(Plan &p, SplitLayout &Y)
     p.nk_f = p.JP / KC;
     const int fpt = p.gemm_n / 8;                  // column groups per column tile
     const long long L1 = L + 1;
-    std::vector<long long> &off_f = Y.off_f, &off_a = Y.off_a, &off_g = Y.off_g;
-    off_f.assign(2 * (L + 1), 0);
-    off_a.assign(2 * (L + 1), 0);
+    std::vector<int> &rb = Y.rb;
+    std::vector<long long> &off_g = Y.off_g;
+    rb.assign(2 * (L + 1), 0);
     off_g.assign(2 * (L + 1), 0);
     const int J = p.J;
     const std::vector<int> lf = turning_bounds(p);
@@ -518,7 +543,7 @@ int layout_bf16(Plan &p, SplitLayout &Y)
         p.gen_values += (double)(L + 2 - mu) * (J - jcmin[mu]);
     }
     p.gemm_pairs_f = p.gemm_pairs_a = 0;
-    long long lam_f = 0, lam_a = 0, gsz = 0;
+    long long nrb = 0, gsz = 0;
     std::vector<TcItem> &itf = Y.itf, &ita = Y.ita;
     itf.clear();
     ita.clear();
@@ -530,11 +555,9 @@ int layout_bf16(Plan &p, SplitLayout &Y)
             // the adjoint of order 0 runs on the order-1 Legendre functions (see uncombine)
             const int npa = nrow_p(mu == 0 ? 1 : mu, par);
             const int idx = mu * 2 + par;
-            off_f[idx] = lam_f;
-            off_a[idx] = lam_a;
+            rb[idx] = (int)nrb;
             off_g[idx] = gsz;
-            lam_f += (long long)((np + 127) / 128) * p.nk_f * CHA;
-            lam_a += (long long)(p.JP / 128) * ((np + KC - 1) / KC) * CHA;
+            nrb += (np + 7) / 8;                 // row blocks of 8 rows of this parity
             gsz += (long long)p.n_tiles * ((npa + KC - 1) / KC) * CHB;
         }
     }
@@ -556,8 +579,11 @@ int layout_bf16(Plan &p, SplitLayout &Y)
                 p.gemm_pairs_f += (double)trows * (J - kc0 * KC > 0 ? J - kc0 * KC : 0);
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_f[idx] + ((long long)m * p.nk_f + kc0) * CHA;
-                    I.a_stride = (int)CHA;
+                    // A: latitude block kc0 + c (32 latitudes), row blocks 16 m .. 16 m + 15
+                    I.ay = kc0;
+                    I.ady = 1;
+                    I.az = rb[idx] + 16 * m;
+                    I.adz = 0;
                     I.b_box = 1;
                     I.bx = par * 8;
                     I.by = fpt * nt;
@@ -591,9 +617,13 @@ int layout_bf16(Plan &p, SplitLayout &Y)
                 p.gemm_pairs_a += (double)(tl > 0 ? tl : 0) * (npa - KC * kc0);
                 for (int nt = 0; nt < p.n_tiles; ++nt) {
                     TcItem I{};
-                    I.a_off = off_a[amu * 2 + par] + ((long long)t * nka + kc0) * CHA;
+                    // A: latitude blocks 4 t .. 4 t + 3 (128 latitudes), row blocks of chunk
+                    // kc0 + c: 4 (kc0 + c) .. + 3 of (amu, par)
+                    I.ay = 4 * t;
+                    I.ady = 0;
+                    I.az = rb[amu * 2 + par] + 4 * kc0;
+                    I.adz = 4;
                     I.b_off = off_g[idx] + ((long long)nt * nka + kc0) * CHB;
-                    I.a_stride = (int)CHA;
                     I.b_stride = (int)CHB;
                     I.out_off = ((((long long)fpt * nt * (p.JP / 4) + 32LL * t) * L1 + mu) * 2 + par) * 32;
                     I.out_ld = L1 * 2 * 32;
@@ -632,8 +662,8 @@ int layout_bf16(Plan &p, SplitLayout &Y)
     }
     p.n_items_f = (int)itf.size();
     p.n_items_a = (int)ita.size();
-    Y.lamf_bytes = (size_t)lam_f;
-    Y.lama_bytes = (size_t)lam_a;
+    Y.rb_total = nrb;
+    Y.lam_bytes = (size_t)3 * nrb * p.JP * 16;
     Y.fb_bytes = (size_t)p.JP * p.nf * L1 * 64;
     Y.g_bytes = (size_t)gsz;
     Y.q_bytes = (size_t)p.nf * p.ntab * 8 * sizeof(float);
@@ -658,24 +688,21 @@ int check_layout_bf16(const Plan &p, const SplitLayout &Y, char *msg, size_t msg
     auto nrow_p = [&](int mu, int par) { const int n = L + 2 - mu; return par ? n / 2 : (n + 1) / 2; };
     if (p.JP % 128 || p.JP < p.J || p.nf * 8 != p.ncolr || p.n_tiles * N != p.ncolr || p.nf < p.ncg)
         return fail("grid or column padding", p.JP, p.nf, p.ncolr);
-    if ((int)Y.off_f.size() != 2 * L1 || (int)Y.off_a.size() != 2 * L1 || (int)Y.off_g.size() != 2 * L1 ||
-        (int)Y.jcmin.size() != L1)
-        return fail("table sizes", (long long)Y.off_f.size(), (long long)Y.jcmin.size(), L1);
-    // per-(mu, parity) regions, in order and inside their buffers
+    if ((int)Y.rb.size() != 2 * L1 || (int)Y.off_g.size() != 2 * L1 || (int)Y.jcmin.size() != L1)
+        return fail("table sizes", (long long)Y.rb.size(), (long long)Y.jcmin.size(), L1);
+    if (Y.lam_bytes != (size_t)3 * Y.rb_total * p.JP * 16) return fail("Legendre buffer size", Y.rb_total, p.JP, 0);
+    // per-(mu, parity) regions: Legendre row blocks and coefficient operand, in order, inside
+    // their buffers
     for (int idx = 0; idx < 2 * L1; ++idx) {
         const int mu = idx / 2, par = idx % 2;
         const int np = nrow_p(mu, par), npa = nrow_p(mu == 0 ? 1 : mu, par);
-        const long long ef = Y.off_f[idx] + (long long)((np + 127) / 128) * p.nk_f * Y.CHA;
-        const long long ea = Y.off_a[idx] + (long long)(p.JP / 128) * ((np + KC - 1) / KC) * Y.CHA;
+        const long long er = (long long)Y.rb[idx] + (np + 7) / 8;
         const long long eg = Y.off_g[idx] + (long long)p.n_tiles * ((npa + KC - 1) / KC) * Y.CHB;
-        const long long nf_ = idx + 1 < 2 * L1 ? Y.off_f[idx + 1] : (long long)Y.lamf_bytes;
-        const long long na_ = idx + 1 < 2 * L1 ? Y.off_a[idx + 1] : (long long)Y.lama_bytes;
+        const long long nr_ = idx + 1 < 2 * L1 ? Y.rb[idx + 1] : Y.rb_total;
         const long long ng_ = idx + 1 < 2 * L1 ? Y.off_g[idx + 1] : (long long)Y.g_bytes;
-        if (Y.off_f[idx] < 0 || ef > nf_) return fail("forward Legendre region", mu, par, ef);
-        if (Y.off_a[idx] < 0 || ea > na_) return fail("adjoint Legendre region", mu, par, ea);
+        if (Y.rb[idx] < 0 || er > nr_) return fail("Legendre row blocks", mu, par, er);
         if (Y.off_g[idx] < 0 || eg > ng_) return fail("coefficient operand region", mu, par, eg);
-        if (Y.off_f[idx] % 512 || Y.off_a[idx] % 512 || Y.off_g[idx] % 512)
-            return fail("operand region alignment", mu, par, Y.off_f[idx]);
+        if (Y.off_g[idx] % 512) return fail("operand region alignment", mu, par, Y.off_g[idx]);
     }
     for (int mu = 0; mu <= L; ++mu)
         if (Y.jcmin[mu] < 0 || Y.jcmin[mu] % KC || Y.jcmin[mu] >= p.J) return fail("generator start", mu, Y.jcmin[mu], p.J);
@@ -690,12 +717,20 @@ int check_layout_bf16(const Plan &p, const SplitLayout &Y, char *msg, size_t msg
     for (size_t i = 0; i < Y.itf.size(); ++i) {
         const TcItem &I = Y.itf[i];
         if (I.nk < 1 || I.rows < 1 || I.rows > 128 || I.group != 0 || !I.b_box) return fail("forward item shape", (long long)i, I.nk, I.rows);
-        if (I.a_off < 0 || I.a_off % 512 || I.a_stride % 512 || I.a_off + (long long)(I.nk - 1) * I.a_stride + Y.CHA > (long long)Y.lamf_bytes)
-            return fail("forward item A chunks", (long long)i, I.a_off, I.nk);
         // 5-D box {8, 1, 8, N/8, 4} at (bx, bw, 0, by, 4 (bk + c)) in dims {16, L+1, 8, nf, JP/8}
         if ((I.bx != 0 && I.bx != 8) || I.bw < 0 || I.bw > L || I.by < 0 || I.by + N / 8 > p.nf || I.bk < 0 ||
             (long long)(KC / 8) * (I.bk + I.nk) > p.JP / 8)
             return fail("forward item B box", (long long)i, I.bw, I.bk + I.nk);
+        // A: latitude blocks ay .. ay + nk - 1 (of JP / 32), row blocks az .. az + 15: the
+        // tile's first row block and its valid rows lie in the row blocks of its own
+        // (order, parity) (rows beyond them are read but their outputs are not written)
+        {
+            const int mu = I.bw, par = I.bx / 8, idx = mu * 2 + par;
+            const long long r0 = Y.rb[idx], r1 = r0 + (nrow_p(mu, par) + 7) / 8;
+            if (I.ady != 1 || I.adz != 0 || I.ay < 0 || (long long)I.ay + I.nk > p.JP / 32 || I.az < r0 ||
+                (long long)I.az + (I.rows + 7) / 8 > r1)
+                return fail("forward item A box", (long long)i, I.ay, I.az);
+        }
         long long lo, hi;
         out_span(I, lo, hi);
         if (lo < 0 || hi >= qf) return fail("forward item output", (long long)i, lo, hi);
@@ -707,8 +742,17 @@ int check_layout_bf16(const Plan &p, const SplitLayout &Y, char *msg, size_t msg
     for (size_t i = 0; i < Y.ita.size(); ++i) {
         const TcItem &I = Y.ita[i];
         if (I.nk < 1 || I.rows != 128 || I.group != 1 || I.b_box) return fail("adjoint item shape", (long long)i, I.nk, I.rows);
-        if (I.a_off < 0 || I.a_off % 512 || I.a_stride % 512 || I.a_off + (long long)(I.nk - 1) * I.a_stride + Y.CHA > (long long)Y.lama_bytes)
-            return fail("adjoint item A chunks", (long long)i, I.a_off, I.nk);
+        // A: latitude blocks ay .. ay + 3, row blocks az + 4 c .. + 3: the chunks start in the
+        // row blocks of the item's own (order, parity) (order 1 for order 0) and run past
+        // them by less than one chunk (those rows meet zero coefficient rows)
+        {
+            const long long q = I.out_off / 32;
+            const int par = (int)(q % 2), mu = (int)((q / 2) % L1), amu = mu == 0 ? 1 : mu;
+            const long long r0 = Y.rb[amu * 2 + par], nb = (nrow_p(amu, par) + 7) / 8;
+            if (I.ady != 0 || I.adz != 4 || I.ay < 0 || I.ay % 4 || (long long)I.ay + 4 > p.JP / 32 || I.az < r0 ||
+                (I.az - r0) % 4 || (long long)I.az + 4LL * I.nk > r0 + (nb + 3) / 4 * 4)
+                return fail("adjoint item A box", (long long)i, I.ay, I.az);
+        }
         if (I.b_off < 0 || I.b_off % 512 || I.b_stride % 512 || I.b_off + (long long)(I.nk - 1) * I.b_stride + Y.CHB > (long long)Y.g_bytes)
             return fail("adjoint item B chunks", (long long)i, I.b_off, I.nk);
         long long lo, hi;
@@ -725,14 +769,14 @@ int alloc_workspace_bf16(Plan &p)
     if (st == FAVEST_OK) st = check_layout_bf16(p, Y, nullptr, 0);
     if (st != FAVEST_OK) return st;
     const int L = p.L;
-    const long long CHA = Y.CHA, CHB = Y.CHB;
-    const std::vector<long long> &off_f = Y.off_f, &off_a = Y.off_a, &off_g = Y.off_g;
+    const long long CHB = Y.CHB;
+    const std::vector<long long> &off_g = Y.off_g;
     const std::vector<int> &jcmin = Y.jcmin;
     const std::vector<TcItem> &itf = Y.itf, &ita = Y.ita;
-    const size_t lamf_bytes = Y.lamf_bytes, lama_bytes = Y.lama_bytes, fb_bytes = Y.fb_bytes, q_bytes = Y.q_bytes,
-                 s_bytes = Y.s_bytes;
+    const size_t lam_bytes = Y.lam_bytes, fb_bytes = Y.fb_bytes, q_bytes = Y.q_bytes, s_bytes = Y.s_bytes;
     const long long gsz = (long long)Y.g_bytes;
-    if (plan_malloc(&p.d_lam_f, lamf_bytes) != cudaSuccess || plan_malloc(&p.d_lam_a, lama_bytes) != cudaSuccess ||
+    p.lam_rb_total = Y.rb_total;
+    if (plan_malloc(&p.d_lam, lam_bytes) != cudaSuccess ||
         plan_malloc(&p.d_Fb, fb_bytes) != cudaSuccess ||
         plan_malloc(&p.d_gb, (size_t)gsz) != cudaSuccess || plan_malloc((void **)&p.d_Q32, q_bytes) != cudaSuccess ||
         plan_malloc((void **)&p.d_S32, s_bytes) != cudaSuccess ||
@@ -743,22 +787,21 @@ int alloc_workspace_bf16(Plan &p)
     // padded operand positions (latitudes >= J, fields >= B, rows beyond each order's
     // range) and the latitudes below each order's turning bound must hold zeros; they
     // are never written afterwards
-    if (cudaMemset(p.d_lam_f, 0, lamf_bytes) != cudaSuccess || cudaMemset(p.d_lam_a, 0, lama_bytes) != cudaSuccess ||
+    if (cudaMemset(p.d_lam, 0, lam_bytes) != cudaSuccess ||
         cudaMemset(p.d_Fb, 0, fb_bytes) != cudaSuccess ||
         cudaMemset(p.d_gb, 0, (size_t)gsz) != cudaSuccess ||
         cudaMemset(p.d_status, 0, kStatusWords * sizeof(int)) != cudaSuccess)
         return FAVEST_ECUDA;
     cudaError_t e;
-    if ((e = upload(&p.d_lam_off_f, off_f)) || (e = upload(&p.d_lam_off_a, off_a)) ||
-        (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)) ||
+    if ((e = upload(&p.d_lam_rb, Y.rb)) || (e = upload(&p.d_g_off, off_g)) || (e = upload(&p.d_items_f, itf)) || (e = upload(&p.d_items_a, ita)) ||
         (e = upload(&p.d_jcmin, jcmin)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
-    p.ws_bytes = lamf_bytes + lama_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
+    p.ws_bytes = lam_bytes + fb_bytes + (size_t)gsz + q_bytes + s_bytes;
     const int pst = build_polar_tables(p);
     if (pst != FAVEST_OK) return pst;
     p.ws_bytes += (size_t)p.pol_jc * (L + 1) * p.pol_muc * sizeof(float2);
-    st = make_row_tensor_map(p.d_lam_f, lamf_bytes, (int)(CHA / 512), &p.tmap_lam_f);
-    if (st == FAVEST_OK) st = make_row_tensor_map(p.d_lam_a, lama_bytes, (int)(CHA / 512), &p.tmap_lam_a);
+    st = make_lam_tensor_map(p, 1, 16, &p.tmap_lam_f);         // forward: 32 latitudes x 16 row blocks
+    if (st == FAVEST_OK) st = make_lam_tensor_map(p, 4, 4, &p.tmap_lam_a);   // adjoint: 128 x 4
     if (st == FAVEST_OK) st = make_fb_tensor_map(p);
     if (st == FAVEST_OK) st = make_s32_tensor_map(p);
     if (st == FAVEST_OK) st = make_row_tensor_map(p.d_gb, (size_t)gsz, (int)(CHB / 512), &p.tmap_gb);
@@ -1016,7 +1059,7 @@ int favest_debug_check_layout(int L, int batch, int precision, int io_type, int 
         st = layout_bf16(p, Y);
         if (st == FAVEST_OK && poison == 1 && !Y.itf.empty()) Y.itf[0].bw = L + 1;      // order out of range
         if (st == FAVEST_OK && poison == 2 && !Y.ita.empty()) Y.ita.back().nk += 1;    // one chunk too many
-        if (st == FAVEST_OK && poison == 3 && L >= 2) Y.off_f[2] = Y.off_f[1];         // overlapping regions
+        if (st == FAVEST_OK && poison == 3 && L >= 2) Y.rb[2] = Y.rb[1];               // overlapping regions
         if (st == FAVEST_OK) st = check_layout_bf16(p, Y, msg, msg_len > 0 ? (size_t)msg_len : 0);
     }
     std::free(p.h_x);
@@ -1341,9 +1384,11 @@ int favest_kernel_work(favest_plan plan, const char *kernel, double *bytes, doub
         if (k == "fft_fwd") { *bytes = grid + J * G * L1 * 64.0; *flops = fftf; }
         else if (k == "fft_inv") { *bytes = J * G * L1 * 64.0 + grid; *flops = fftf; }
         // the generator runs its recurrence in double-float FP32 arithmetic and is bound by
-        // its writes (6 bytes per value and layout)
-        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj") { *bytes = gv * 6.0; *flops = gv * 4.0; }
-        else if (k == "gen_lambda_both") { *bytes = gv * 12.0; *flops = gv * 4.0; }
+        // its writes (6 bytes per value, in the one layout both directions read)
+        else if (k == "gen_lambda_fwd" || k == "gen_lambda_adj" || k == "gen_lambda_both") {
+            *bytes = gv * 6.0;          // one layout serves both directions
+            *flops = gv * 4.0;
+        }
         else if (k == "tc_gemm_fwd") { *bytes = pf * 6.0 + J * G * L1 * 64.0 + rows * G * 32.0; *flops = 12.0 * pf * 8.0 * G; }
         else if (k == "tc_gemm_adj") { *bytes = pa * 6.0 + rows * G * 48.0 + J * G * L1 * 64.0; *flops = 12.0 * pa * 8.0 * G; }
         else if (k == "combine") { *bytes = rows * G * 32.0 + coef; *flops = 16.0 * B * kc; }

@@ -62,21 +62,25 @@ inline int *gemm_sched(int *status, bool fwd) { return status + (fwd ? 1 : 3); }
 constexpr int kInvChunk = 256;    // orders per TMA box of the inverse DFT's sum records (16 KB)
 
 // One tensor-core GEMM work item: out[rows][N] = sum over nk K-chunks of A_c * B_c, each
-// chunk three bf16 pieces.  Chunk c of A starts a_off + c * a_stride bytes into the A
-// buffer (a multiple of 512: the TMA addresses the buffer as rows of 512 bytes); B
-// likewise (b_box = 0), or (b_box = 1) through the forward operand's 5-D tensor map at
-// coordinates (bx, bw, 0, by, 4 * (bk + c)) (FP32 records; the forward GEMM splits them
-// into the bf16 pieces).  Output row r (< rows) of field
-// column group g (8 floats) is written at
+// chunk three bf16 pieces.  A (the Legendre operand, one layout for both directions) is
+// read through a 4-D tensor map (256 bf16 = 32 latitudes x 8 rows, latitude block of 32,
+// row block of 8, piece): chunk c is the box at (0, ay + c ady, az + c adz, 0), 32 x 128
+// (forward: one latitude block, 16 row blocks) or 128 x 32 (adjoint: 4 latitude blocks,
+// 4 row blocks).  B: chunk c starts b_off + c * b_stride bytes into the B buffer (a
+// multiple of 512: the TMA addresses the buffer as rows of 512 bytes) (b_box = 0), or
+// (b_box = 1) is the forward operand's 5-D box at (bx, bw, 0, by, 4 * (bk + c)) (FP32
+// records; the forward GEMM splits them into the bf16 pieces).  Output row r (< rows) of
+// field column group g (8 floats) is written at
 //   out + out_off + (r / 4) * out_ld + (r % 4) * 8 + g * col_gs.
 struct TcItem {
-    long long a_off, b_off;
+    long long b_off;
     long long out_off;  // floats
     long long out_ld;   // floats between groups of 4 rows
     long long col_gs;   // floats between field column groups
     int nk;             // K-chunks
     int rows;           // valid output rows (<= 128)
-    int a_stride;       // bytes between consecutive A chunks
+    int ay, ady;        // A box: latitude block of chunk 0, step per chunk
+    int az, adz;        // A box: row block of chunk 0, step per chunk
     int b_stride;       // bytes between consecutive B chunks
     int b_box;          // 1: B through the 5-D tensor map
     int bx, by, bw;     // 5-D box coordinates: x of the parity's 8 floats, first field, order
@@ -150,10 +154,14 @@ struct Plan {
     int n_tiles = 0;          // ncolr / gemm_n
     int nk_f = 0;             // forward K-chunks: JP / kGemmChunkK
     int n_items_f = 0, n_items_a = 0;
-    // Legendre operand tiles (bf16 x 3), forward and adjoint layouts.  Both buffers are
-    // zeroed at plan creation; the generator never writes the latitudes below an
-    // order's turning bound (jc_min), which therefore stay zero.
-    void *d_lam_f = nullptr, *d_lam_a = nullptr;
+    // Legendre operand (bf16 x 3), one layout that both directions' GEMMs read:
+    // [piece][row block][JP latitudes][8 rows] (16-byte units of 8 consecutive rows of one
+    // parity at one latitude), the row blocks of (mu, parity) from lam_rb[mu*2+p] on
+    // (lam_rb_total in all).  Zeroed at plan creation; the generator never writes the
+    // latitudes below an order's turning bound (jc_min), which therefore stay zero.
+    void *d_lam = nullptr;
+    int *d_lam_rb = nullptr;
+    long long lam_rb_total = 0;
     int *d_jcmin = nullptr;       // [L+1] first latitude (multiple of 32) generated per order
     double gen_values = 0;        // recurrence values generated per direction
     // Legendre operand shared by a pair of calls (FAVEST_FLAG_SHARE_LAMBDA): kGenFwd when
@@ -166,8 +174,9 @@ struct Plan {
     float *d_Q32 = nullptr;       // forward GEMM output [group][l][mu][8]
     float *d_S32 = nullptr;       // adjoint GEMM output [group][JP/4][mu][parity][4][8]
     int nf = 0;                   // column groups padded to a multiple of gemm_n / 8 (ncolr / 8)
-    // Legendre and adjoint B operands as seen by the GEMM's TMA: 2-D arrays of 512-byte
-    // rows (every chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
+    // The Legendre operand as the GEMMs' TMA sees it: one 4-D map per direction (the same
+    // tensor, a 32 x 128 or 128 x 32 box); adjoint B: a 2-D array of 512-byte rows (every
+    // chunk starts on a row and spans whole rows); forward B: 5-D map of Fb.
     CUtensorMap tmap_lam_f, tmap_lam_a, tmap_fb, tmap_gb;
     // the inverse DFT's view of S32: (32 floats, parity, mu, latitude group, column group),
     // boxes of 8 floats x 2 parities x kInvChunk orders
@@ -177,7 +186,7 @@ struct Plan {
     int gen_lt = 128, gen_mb = 1;  // generator shape: latitudes per block, orders per thread
     int gen_nj = 2;                // latitude chains per generator thread (1 or 2)
     int force_gemm_n = 0;          // 256: use 256-column GEMM tiles whatever the batch
-    long long *d_lam_off_f = nullptr, *d_lam_off_a = nullptr, *d_g_off = nullptr;  // [mu*2+p]
+    long long *d_g_off = nullptr;  // [mu*2+p] coefficient operand offsets
     float *d_P32 = nullptr, *d_M32 = nullptr, *d_R32 = nullptr;   // FP32 copies of P, M, R
     float *d_k1 = nullptr;        // [L+1] kappa of order 1 (order-0 adjoint on order-1 tiles)
     float2 *d_Adf = nullptr;      // [ntab] A_l^mu as double-float pairs (hi, lo) for the generator

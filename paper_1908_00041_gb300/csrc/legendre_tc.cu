@@ -65,16 +65,13 @@ __device__ __forceinline__ void split3(float f, unsigned short &h, unsigned shor
 // order's turning bound rounded down to a K-chunk: every value there is below 1e-13) and
 // padding latitudes are not stored; their operand positions were zeroed when the plan was
 // created.
-// MODE selects the layouts written (bit 0: forward, bit 1: adjoint); both layouts are made
-// of the same 16-byte core-matrix rows (8 consecutive rows of one parity at one latitude)
-// and differ only in where a row goes, so MODE 3 serves an adjoint and a forward transform
-// from one pass of the recurrence:
-//   forward A layout: item (mu, p, m_tile) at lam_f_off[mu*2+p] + m_tile*nkf*24KB
-//   adjoint A layout: item (mu, p, j_tile) at lam_a_off[mu*2+p] + j_tile*nka*24KB
-template <int MODE, int kGenJ>
-__device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off,
-                                          unsigned char *__restrict__ lam_a, const long long *__restrict__ lam_a_off,
-                                          const float2 *__restrict__ xdf, const double *__restrict__ sj,
+// Output: the one Legendre layout both GEMM directions read, [piece][row block][JP][8 rows]:
+// the 16-byte unit of the 8 rows rp .. rp + 7 of parity p at latitude j goes to
+//   lam + piece * rb_total JP 16 + ((lam_rb[mu*2+p] + rp / 8) JP + j) 16,
+// so a warp (32 consecutive latitudes) stores 512 consecutive bytes per piece.
+template <int kGenJ>
+__device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const int *__restrict__ lam_rb,
+                                          long long rb_total, const float2 *__restrict__ xdf, const double *__restrict__ sj,
                                           const double *__restrict__ cmu, const float2 *__restrict__ Adf, int L,
                                           int J, int JP, int mu, const int (&jv)[kGenJ], int jc0)
 {
@@ -103,9 +100,7 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
             sectoral_start_df(cmu[mu], sj[jv[i]], mu, y1[i], c[i]);
         }
     }
-    const int nk_f = JP / kChunkK;                 // forward K chunks (latitudes)
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
-    const int nk_a0 = (nrow_p0 + kChunkK - 1) / kChunkK, nk_a1 = (nrow_p1 + kChunkK - 1) / kChunkK;
 
     unsigned pk[kGenJ][2][kPieces][4];   // [chain][parity][piece][4 x 2 bf16]
 #pragma unroll
@@ -155,28 +150,11 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
             for (int p = 0; p < 2; ++p) {
                 const int np = p ? nrow_p1 : nrow_p0;
                 if (act[i] && rp < np) {
-                    if (MODE & 1) {
-                        const int mt = rp / kTileM, mi = rp % kTileM;
-                        const int kc = j / kChunkK, jj = j % kChunkK;
-                        const long long off = lam_f_off[mu * 2 + p] + ((long long)mt * nk_f + kc) * kChunkBytes +
-                                              (jj / 8) * 2048 + (mi / 8) * 128 + (jj % 8) * 16;
+                    const size_t unit = ((size_t)(__ldg(lam_rb + mu * 2 + p) + rp / 8) * JP + j) * 16;
 #pragma unroll
-                        for (int q = 0; q < kPieces; ++q) {
-                            uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
-                            *reinterpret_cast<uint4 *>(lam_f + off + q * kPieceBytes) = v;
-                        }
-                    }
-                    if (MODE & 2) {
-                        const int nka = p ? nk_a1 : nk_a0;
-                        const int jt = j / kTileM, jj = j % kTileM;
-                        const int kc = rp / kChunkK, rr = rp % kChunkK;
-                        const long long off = lam_a_off[mu * 2 + p] + ((long long)jt * nka + kc) * kChunkBytes +
-                                              (jj / 8) * (kChunkK / 8 * 128) + (rr / 8) * 128 + (jj % 8) * 16;
-#pragma unroll
-                        for (int q = 0; q < kPieces; ++q) {
-                            uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
-                            *reinterpret_cast<uint4 *>(lam_a + off + q * kPieceBytes) = v;
-                        }
+                    for (int q = 0; q < kPieces; ++q) {
+                        uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
+                        *reinterpret_cast<uint4 *>(lam + (size_t)q * rb_total * JP * 16 + unit) = v;
                     }
                 }
 #pragma unroll
@@ -186,10 +164,10 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam_f, con
     }
 }
 
-template <int MODE, int kGenJ>
+template <int kGenJ>
 __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
-    unsigned char *__restrict__ lam_f, const long long *__restrict__ lam_f_off, unsigned char *__restrict__ lam_a,
-    const long long *__restrict__ lam_a_off, const float2 *__restrict__ xdf, const double *__restrict__ sj,
+    unsigned char *__restrict__ lam, const int *__restrict__ lam_rb, long long rb_total,
+    const float2 *__restrict__ xdf, const double *__restrict__ sj,
     const double *__restrict__ cmu, const float2 *__restrict__ Adf, const int *__restrict__ jcmin, int L, int J,
     int JP, int lt, int mb)
 {
@@ -202,8 +180,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_lambda(
     for (int k = 0; k < mb; ++k) {
         const int mu = (og * mb + k) * olanes + threadIdx.x / lt;   // uniform in the warp
         if (mu > L) break;
-        gen_order<MODE, kGenJ>(lam_f, lam_f_off, lam_a, lam_a_off, xdf, sj, cmu, Adf, L, J, JP, mu, jv,
-                               __ldg(jcmin + mu));
+        gen_order<kGenJ>(lam, lam_rb, rb_total, xdf, sj, cmu, Adf, L, J, JP, mu, jv, __ldg(jcmin + mu));
     }
 }
 
@@ -385,10 +362,10 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
                         break;
                     }
                     tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkB);
-                    // operand buffers are 2-D arrays of 512-byte rows: a chunk is a box
-                    // of whole rows starting at its byte offset / 512
-                    tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
-                                    &S.full[stage]);
+                    // the Legendre chunk: a 4-D box of the one layout; the coefficient operand
+                    // buffer is a 2-D array of 512-byte rows: a chunk is a box of whole rows
+                    // starting at its byte offset / 512
+                    tc::tma_load_4d(S.a[stage], tmap_a, 0, I.ay + c * I.ady, I.az + c * I.adz, 0, &S.full[stage]);
                     tc::tma_load_2d(S.b[stage], tmap_b, 0, (int)((I.b_off + (long long)c * I.b_stride) >> 9),
                                     &S.full[stage]);
                     phase ^= 1u << stage;
@@ -411,11 +388,14 @@ __global__ void __launch_bounds__(gemm_threads<N>(), 1) k_tc_gemm(
             uint32_t phase = 0, main_use = 0, corr_use = 0;
             int stage = 0;
             const uint32_t dmain = tmem, dcorr = tmem + N;
-            // A: MN-major (fwd): K-groups of 16 x 128 B, K-step = 2 groups;
-            //    K-major (adj):  [M/8][K/8] core matrices, K-step = 2 x 128 B.
+            // A, per piece [K/8 or M/8 row blocks][latitudes][8 rows] (the box of the one
+            // Legendre layout): MN-major (forward, [M/8 = 16][K = 32]): K-groups 128 B apart,
+            // M-blocks 512 B, K-step (2 groups) 256 B; K-major (adjoint, [K/8 = 4][M = 128]):
+            // M-groups 128 B apart, K-groups 2048 B, K-step 4096 B.  (Descriptor: leading
+            // byte offset = K-direction stride, stride byte offset = M/N-direction stride.)
             // B: MN-major, K-groups of N/8 x 128 B.
-            const uint32_t a_step = a_mn_major ? 4096u : 256u;
-            const uint32_t a_lbo = a_mn_major ? 2048u : 128u, a_sbo = a_mn_major ? 128u : kChunkK / 8 * 128u;
+            const uint32_t a_step = a_mn_major ? 256u : 4096u;
+            const uint32_t a_lbo = a_mn_major ? 128u : 2048u, a_sbo = a_mn_major ? 512u : 128u;
             constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
             for (uint32_t n = 0; !*abort; ++n) {
                 int it;
@@ -670,8 +650,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
                         break;
                     }
                     tc::mbar_arrive_expect_tx(&S.full[stage], kChunkBytes + kChunkBF);
-                    tc::tma_load_2d(S.a[stage], tmap_a, 0, (int)((I.a_off + (long long)c * I.a_stride) >> 9),
-                                    &S.full[stage]);
+                    tc::tma_load_4d(S.a[stage], tmap_a, 0, I.ay + c * I.ady, I.az + c * I.adz, 0, &S.full[stage]);
                     tc::tma_load_5d(S.b[stage], tmap_b, I.bx, I.bw, 0, I.by, (kChunkK / 8) * (I.bk + c),
                                     &S.full[stage]);
                     phase ^= 1u << stage;
@@ -691,7 +670,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_gemm_f(
             uint32_t phase = 0, main_use = 0, corr_use = 0;
             int stage = 0;
             const uint32_t dmain = tmem, dcorr = tmem + N;
-            constexpr uint32_t a_step = 4096u, a_lbo = 2048u, a_sbo = 128u;     // A MN-major
+            // A MN-major, per piece [M/8 = 16 row blocks][K = 32 latitudes][8 rows]: K-groups
+            // 128 B apart, M-blocks 512 B (leading byte offset = K-direction stride)
+            constexpr uint32_t a_step = 256u, a_lbo = 128u, a_sbo = 512u;
             constexpr uint32_t b_step = 2 * (N / 8) * 128, b_lbo = (N / 8) * 128;
             for (uint32_t n = 0; !*abort; ++n) {
                 int it;
@@ -929,31 +910,23 @@ cudaError_t launch_gemm_n(const GemmGroup *groups, const TcItem *items, int nite
 
 }  // namespace
 
-template <int MODE, int NJ>
+template <int NJ>
 void launch_gen_t(const Plan &p, int lt, int mb, cudaStream_t s)
 {
     const int olanes = kGenThreads / lt;
     const int ogroups = (p.L + 1 + olanes * mb - 1) / (olanes * mb);
     const int grid = ((p.JP + NJ * lt - 1) / (NJ * lt)) * ogroups;
-    k_gen_lambda<MODE, NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam_f, p.d_lam_off_f,
-                                                        (unsigned char *)p.d_lam_a, p.d_lam_off_a, p.d_xdf, p.d_sin,
-                                                        p.d_cmu, p.d_Adf, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
-}
-
-template <int NJ>
-void launch_gen_nj(const Plan &p, int layouts, int lt, int mb, cudaStream_t s)
-{
-    if (layouts == kGenFwd) launch_gen_t<kGenFwd, NJ>(p, lt, mb, s);
-    else if (layouts == kGenAdj) launch_gen_t<kGenAdj, NJ>(p, lt, mb, s);
-    else launch_gen_t<kGenBoth, NJ>(p, lt, mb, s);
+    k_gen_lambda<NJ><<<grid, kGenThreads, 0, s>>>((unsigned char *)p.d_lam, p.d_lam_rb, p.lam_rb_total, p.d_xdf,
+                                                  p.d_sin, p.d_cmu, p.d_Adf, p.d_jcmin, p.L, p.J, p.JP, lt, mb);
 }
 
 cudaError_t launch_gen_lambda_shape(const Plan &p, int layouts, int lt, int mb, int nj, cudaStream_t s)
 {
+    // one layout serves both directions: every request writes it
     if (lt != 32 && lt != 64 && lt != 128) return cudaErrorInvalidValue;
     if (layouts != kGenFwd && layouts != kGenAdj && layouts != kGenBoth) return cudaErrorInvalidValue;
-    if (nj == 1) launch_gen_nj<1>(p, layouts, lt, mb, s);
-    else if (nj == 2) launch_gen_nj<2>(p, layouts, lt, mb, s);
+    if (nj == 1) launch_gen_t<1>(p, lt, mb, s);
+    else if (nj == 2) launch_gen_t<2>(p, lt, mb, s);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -97,6 +97,15 @@ __device__ __forceinline__ void tma_load_5d(void *sdst, const void *tmap, int c0
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void *sdst, const void *tmap, int c0, int c1, int c2, int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(sdst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 2-D tiled TMA load (global -> shared) through a tensor map, completing on bar.
 __device__ __forceinline__ void tma_load_2d(void *sdst, const void *tmap, int c0, int c1, uint64_t *bar)
 {

@@ -1,7 +1,8 @@
 """Host-side bounds check of the split path's index tables (favest_debug_check_layout; no
 GPU): for a sweep of degrees, batches, field types and tile widths, every tensor-core GEMM
-work item's operand chunks, TMA box coordinates and output rows stay inside the buffers
-they address and inside the rows of their own order, and the per-(order, parity) operand
+work item's operand chunks and TMA box coordinates (the Legendre operand's row blocks and
+latitude blocks, the coefficient and field operands) and its output rows stay inside the
+buffers they address and inside the rows of their own order, and the per-(order, parity)
 regions are in range, aligned and disjoint.  Degrees: every L up to 160 (the small-tile,
 padding and equator cases), both sides of the latitude-tile boundaries (J = 128, 256, 384,
 512), the paper's timing degrees (Table 3) up to L = 1250, and L = 2047.  The check's own
@@ -61,7 +62,7 @@ def test_arguments_as_plan_create(lib):
 
 
 @pytest.mark.parametrize("poison,what", [(1, "forward item B box"), (2, "adjoint item"),
-                                         (3, "forward Legendre region")])
+                                         (3, "Legendre row blocks")])
 def test_check_reports_corrupted_tables(lib, poison, what):
     for L, B in ((16, 2), (255, 8), (1023, 32)):
         st, msg = api.debug_check_layout(L, B, poison=poison)
