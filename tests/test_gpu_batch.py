@@ -214,3 +214,35 @@ def test_real_batch_matches_single_plans(prec, io, tol):
         assert normwise_err(_h(bp.coef(rb, i)), _h(sb[0])) < tol
         # and the roundtrip recovers the coefficients
         assert normwise_err(_h(bp.coef(ra, i)), coefs[i][0]) < 2e-6
+
+
+def test_batching_form_one_field_per_degree_vs_oracle(orc):
+    """The C4 batch (256 fields, degrees 31 .. 511 drawn as in the bench form): the first
+    field of every degree against the oracle's separable transforms (Def. AdjVSHT eq. SLvec,
+    Def. FwdVSHT eq. fwdvsht2) on the same complex64-rounded coefficients, and the forward of
+    the batch's grid field against the oracle's forward of that field, bar 1e-6."""
+    Ls, rng = synthetic.ragged_degrees(256, [31, 63, 127, 255, 511], seed=3)
+    Ls = [int(x) for x in Ls]
+    coefs = []
+    for L in Ls:
+        ca, cb = synthetic.coefficients(L, 1, seed=None, decay=1.0, rng=rng)
+        coefs.append((ca[0].astype(np.complex64), cb[0].astype(np.complex64)))
+    bp = api.BatchPlan(Ls, api.FAVEST_BF16X6, api.FAVEST_IO_C64, graph=True)
+    a, b = _pack_coefs(bp, coefs, torch.complex64)
+    tt, tp = bp.adj(a, b)
+    ra, rb = bp.fwd(tt, tp)
+    tt, tp = bp.adj(a, b)        # a second call of each replays the captured graph
+    ra, rb = bp.fwd(tt, tp)
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    for L in sorted(set(Ls)):
+        i = Ls.index(L)
+        x, W, _, phi = orc.grid(L)
+        ca, cb = (c.astype(np.complex128) for c in coefs[i])
+        ot, op = orc.adj_sep(L, x, ca, cb, len(phi))
+        ht, hp = _h(bp.field(tt, i)), _h(bp.field(tp, i))
+        assert normwise_err(ht.ravel(), ot.ravel()) < TOL, L
+        assert normwise_err(hp.ravel(), op.ravel()) < TOL, L
+        oa, ob = orc.fwd_sep(L, x, W, ht, hp)
+        assert normwise_err(_h(bp.coef(ra, i)), oa) < TOL, L
+        assert normwise_err(_h(bp.coef(rb, i)), ob) < TOL, L

@@ -91,3 +91,49 @@ def test_pairing_rules():
     torch.cuda.synchronize()
     assert not _gens(prof) and p64.status() == 0
     p64.close()
+
+
+def test_pair_captured_in_a_cuda_graph():
+    """An adjoint and forward pair sharing one generator pass, with the polar patch on the
+    plan's side stream, captured into a CUDA graph by the caller and replayed: bitwise the
+    eager results, and again after new coefficients are copied into the captured buffers."""
+    L, B = 255, 8
+    plan = api.Plan(L, B, api.FAVEST_BF16X6, api.FAVEST_IO_C64)
+    a0, b0 = synthetic.coefficients(L, B, seed=41, decay=1.0)
+    a1, b1 = synthetic.coefficients(L, B, seed=42, decay=1.0)
+    a = torch.as_tensor(a0).to(torch.complex64).cuda()
+    b = torch.as_tensor(b0).to(torch.complex64).cuda()
+    tt = torch.empty(plan.field_shape(), dtype=torch.complex64, device="cuda")
+    tp = torch.empty_like(tt)
+    ra = torch.empty_like(a)
+    rb = torch.empty_like(b)
+
+    def step():
+        plan.adj(a, b, tt, tp, share_lambda=True)
+        plan.fwd(tt, tp, ra, rb, share_lambda=True)
+
+    eager = []
+    for ca, cb in ((a0, b0), (a1, b1)):
+        a.copy_(torch.as_tensor(ca).to(torch.complex64))
+        b.copy_(torch.as_tensor(cb).to(torch.complex64))
+        step()
+        torch.cuda.synchronize()
+        eager.append((tt.clone(), tp.clone(), ra.clone(), rb.clone()))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()                                   # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        step()
+    for k, (ca, cb) in enumerate(((a0, b0), (a1, b1))):
+        a.copy_(torch.as_tensor(ca).to(torch.complex64))
+        b.copy_(torch.as_tensor(cb).to(torch.complex64))
+        g.replay()
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        for got, ref in zip((tt, tp, ra, rb), eager[k]):
+            assert torch.equal(got, ref)
+    plan.close()
