@@ -38,18 +38,70 @@ constexpr int kPieceBytes = kTileM * kChunkK * 2;  // 8 KB: one bf16 piece of an
 constexpr int kPieces = 3;
 constexpr int kChunkBytes = kPieces * kPieceBytes;  // 24 KB
 
-// FP32 value -> three bf16 pieces, split exactly: hi = bf16(f), mid = bf16(f - hi),
-// lo = bf16(f - hi - mid).
-__device__ __forceinline__ void split3(float f, unsigned short &h, unsigned short &m, unsigned short &l)
+// Two FP32 values -> three bf16x2 words (pieces hi, mid, lo; f0 in the low halves), split
+// exactly with round-to-nearest: hi = bf16(f), mid = bf16(f - hi), lo = bf16(f - hi - mid).
+// One conversion instruction rounds both values of a piece.
+__device__ __forceinline__ unsigned bf2_bits(__nv_bfloat162 v)
 {
-    __nv_bfloat16 bh = __float2bfloat16_rn(f);
-    float r1 = f - __bfloat162float(bh);
-    __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-    float r2 = r1 - __bfloat162float(bm);
-    __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-    h = __bfloat16_as_ushort(bh);
-    m = __bfloat16_as_ushort(bm);
-    l = __bfloat16_as_ushort(bl);
+    unsigned u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+
+__device__ __forceinline__ void split3x2(float f0, float f1, unsigned &h, unsigned &m, unsigned &l)
+{
+    const __nv_bfloat162 bh = __floats2bfloat162_rn(f0, f1);
+    const float2 fh = __bfloat1622float2(bh);
+    const float r0 = f0 - fh.x, r1 = f1 - fh.y;
+    const __nv_bfloat162 bm = __floats2bfloat162_rn(r0, r1);
+    const float2 fm = __bfloat1622float2(bm);
+    const __nv_bfloat162 bl = __floats2bfloat162_rn(r0 - fm.x, r1 - fm.y);
+    h = bf2_bits(bh);
+    m = bf2_bits(bm);
+    l = bf2_bits(bl);
+}
+
+// Rows r0 .. r0 + 15 of the NJ chains of one thread (r0 a multiple of 16).  Word k of parity
+// p holds rows 4k + p (low half) and 4k + 2 + p (high half) of the block, so each value waits
+// in fprev for its partner two rows on and the pair is split by split3x2.  kEdge: the block
+// holds row 0 (the start value, no step) or rows past the order's last (emitted as zero);
+// the checks are warp-uniform, and the blocks in between run without them.
+template <int kGenJ, bool kEdge>
+__device__ __forceinline__ void gen_block16(const float2 *__restrict__ As, int r0, int nrow,
+                                            const bool (&act)[kGenJ], const bool (&live)[kGenJ],
+                                            const Df (&x)[kGenJ], Df (&y1)[kGenJ], Df (&y2)[kGenJ],
+                                            unsigned (&pk)[kGenJ][2][3][4])
+{
+    float fprev[kGenJ][2];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        const int r = r0 + w;
+        float f[kGenJ];
+        if (!kEdge || r < nrow) {
+            const float2 av = __ldg(As + r);
+            const Df a{av.x, av.y};
+#pragma unroll
+            for (int i = 0; i < kGenJ; ++i) {
+                f[i] = 0.f;
+                if (!act[i]) continue;                     // no work for inactive chains
+                if (!kEdge || r > 0) {
+                    const Df yl = df_step(a, x[i], y1[i], y2[i]);
+                    y2[i] = y1[i];
+                    y1[i] = yl;
+                }
+                f[i] = live[i] ? y1[i].h : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kGenJ; ++i) f[i] = 0.f;
+        }
+        const int p = w & 1, k = w >> 2;
+#pragma unroll
+        for (int i = 0; i < kGenJ; ++i) {
+            if ((w & 2) == 0) fprev[i][p] = f[i];
+            else split3x2(fprev[i][p], f[i], pk[i][p][0][k], pk[i][p][1][k], pk[i][p][2][k]);
+        }
+    }
 }
 
 // Generator: 128 threads per CTA arranged as (128 / lt) orders x lt latitudes (lt = 32,
@@ -101,44 +153,21 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const
         }
     }
     const int nrow_p0 = (nrow + 1) / 2, nrow_p1 = nrow / 2;
+    int rbase[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) rbase[p] = __ldg(lam_rb + mu * 2 + p);
 
     unsigned pk[kGenJ][2][kPieces][4];   // [chain][parity][piece][4 x 2 bf16]
-#pragma unroll
-    for (int i = 0; i < kGenJ; ++i)
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int q = 0; q < kPieces; ++q)
-#pragma unroll
-                for (int w = 0; w < 4; ++w) pk[i][p][q][w] = 0u;
-
     for (int r0 = 0; r0 < nrow; r0 += 16) {
-#pragma unroll
-        for (int w = 0; w < 16; ++w) {
-            const int r = r0 + w;
-            if (r < nrow) {
-                const float2 av = __ldg(As + r);
-                const Df a{av.x, av.y};
-#pragma unroll
-                for (int i = 0; i < kGenJ; ++i) {
-                    if (!act[i]) continue;                 // no work for inactive chains
-                    Df yl = y1[i];
-                    if (r > 0) {
-                        yl = df_sub(df_mul(df_mul(a, x[i]), y1[i]), y2[i]);
-                        y2[i] = y1[i];
-                        y1[i] = yl;
-                    }
-                    const float f = (c[i] == 0) ? yl.h : 0.0f;
-                    unsigned short h, m, l;
-                    split3(f, h, m, l);
-                    const int p = w & 1, slot = w >> 1;         // r0 is a multiple of 16
-                    const int word = slot >> 1, half = slot & 1;
-                    pk[i][p][0][word] |= (unsigned)h << (16 * half);
-                    pk[i][p][1][word] |= (unsigned)m << (16 * half);
-                    pk[i][p][2][word] |= (unsigned)l << (16 * half);
-                }
-            }
+        if (r0 + 16 < nrow) {                          // the next block's multipliers into L1
+            asm volatile("prefetch.L1 [%0];" ::"l"(As + r0 + 16));
+            asm volatile("prefetch.L1 [%0];" ::"l"(As + min(r0 + 31, nrow - 1)));
         }
+        bool live[kGenJ];
+#pragma unroll
+        for (int i = 0; i < kGenJ; ++i) live[i] = c[i] == 0;
+        if (r0 > 0 && r0 + 16 <= nrow) gen_block16<kGenJ, false>(As, r0, nrow, act, live, x, y1, y2, pk);
+        else gen_block16<kGenJ, true>(As, r0, nrow, act, live, x, y1, y2, pk);
 #pragma unroll
         for (int i = 0; i < kGenJ; ++i) renorm_df(y1[i], y2[i], c[i]);   // growth over 16 rows stays below 2^26
         // flush: rows r0/2 .. r0/2+7 of each parity
@@ -150,15 +179,13 @@ __device__ __forceinline__ void gen_order(unsigned char *__restrict__ lam, const
             for (int p = 0; p < 2; ++p) {
                 const int np = p ? nrow_p1 : nrow_p0;
                 if (act[i] && rp < np) {
-                    const size_t unit = ((size_t)(__ldg(lam_rb + mu * 2 + p) + rp / 8) * JP + j) * 16;
+                    const size_t unit = ((size_t)(rbase[p] + rp / 8) * JP + j) * 16;
 #pragma unroll
                     for (int q = 0; q < kPieces; ++q) {
                         uint4 v = make_uint4(pk[i][p][q][0], pk[i][p][q][1], pk[i][p][q][2], pk[i][p][q][3]);
                         *reinterpret_cast<uint4 *>(lam + (size_t)q * rb_total * JP * 16 + unit) = v;
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < kPieces; ++q) pk[i][p][q][0] = pk[i][p][q][1] = pk[i][p][q][2] = pk[i][p][q][3] = 0u;
             }
         }
     }
