@@ -319,6 +319,18 @@ int build_tables(Plan &p)
         tw[k] = make_double2(cr, ci);
         tw32[k] = make_float2((float)cr, (float)ci);
     }
+    // Power-of-two lengths (the split path's radix-16 engine) append the twiddles of its two
+    // radix-16 stages in [q][k] order, q < 16: at block length n, w^(q k) for k < n/16, at
+    // n/16, w^(16 q k) for k < n/256; a warp's threads (consecutive k) then read consecutive
+    // entries instead of entries q apart.  Values are those of tw32, copied.
+    if (p.precision == FAVEST_BF16X6 && n >= 64 && n <= 4096 && (n & (n - 1)) == 0) {
+        const int hA = n / 16, hB = n / 256;
+        tw32.resize((size_t)n + 16 * hA + 16 * hB);
+        for (int q = 0; q < 16; ++q) {
+            for (int k = 0; k < hA; ++k) tw32[(size_t)n + q * hA + k] = tw32[q * k];
+            for (int k = 0; k < hB; ++k) tw32[(size_t)n + 16 * hA + q * hB + k] = tw32[16 * q * k];
+        }
+    }
     if ((e = upload(&p.fft.tw64, tw)) || (e = upload(&p.fft.tw32, tw32)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     // in-place decimation-in-frequency FFT leaves frequency m at position pos(m):

@@ -38,7 +38,8 @@ struct FftPlan {
     int nstages = 0;
     int radix[kMaxRadixStages];
     double2 *tw64 = nullptr;   // device, e^{-2 pi i k / n}, k = 0..n-1
-    float2 *tw32 = nullptr;    // device, same rounded to float
+    float2 *tw32 = nullptr;    // device, same rounded to float; powers of two 64..4096 append
+                               // the radix-16 stage tables ([q][k], 17 n / 16 entries)
     // FP32 DFT stages of prime radices R >= 17 (above the in-register forms) run Bluestein's
     // chirp transform, a cyclic convolution of power-of-two length M = 2^blue_lg >= 2R - 1;
     // per stage st (blue_lg[st] = 0: not such a stage):

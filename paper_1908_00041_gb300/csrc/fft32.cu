@@ -169,8 +169,9 @@ __host__ __device__ constexpr int bitrev(int x, int bits)
     return r;
 }
 
-// one in-place radix-16 stage at block length NB over nr rings
-template <int LOG2N, int NB, bool INV>
+// one in-place radix-16 stage at block length NB over nr rings; kTab: tw is the stage's
+// [q][k] table (entry q h + k = w_n^(q k n / NB)), else the plain w_n^i table
+template <int LOG2N, int NB, bool INV, bool kTab = false>
 __device__ __forceinline__ void dif_stage16(float2 *x, const float2 *__restrict__ tw, int nr)
 {
     constexpr int n = 1 << LOG2N, R = 16;
@@ -186,7 +187,8 @@ __device__ __forceinline__ void dif_stage16(float2 *x, const float2 *__restrict_
         dft_reg<R, INV>(v);
         x[padi(base)] = v[0];
 #pragma unroll
-        for (int q = 1; q < R; ++q) x[padi(base + q * h)] = cmulf(v[bitrev(q, 4)], twf<INV>(tw, q * k * ts));
+        for (int q = 1; q < R; ++q)
+            x[padi(base + q * h)] = cmulf(v[bitrev(q, 4)], twf<INV>(tw, kTab ? q * h + k : q * k * ts));
     }
     __syncthreads();
 }
@@ -575,7 +577,8 @@ __device__ __forceinline__ void last_stage_global(const float2 *x, const float2 
 // Full transform of nr rings, natural order in and out, by the factorisation
 //   radix-16 at block length n, [radix-16 at n/16,] radix-2^r blocks (dif_last),
 // with the first radix-16 stage fed straight from global memory: src.row(r) locates ring r
-// and src.load(row, i) returns its point i.  Each thread keeps the 16 inputs of two
+// and src.load(row, i) returns its point i.  tw: w_n^i (i < n), then the two radix-16 stages'
+// twiddles in [q][k] order (n and n / 16 entries), so that a warp reads them contiguously.  Each thread keeps the 16 inputs of two
 // butterflies in registers (32 independent loads in flight; across a warp every load covers
 // consecutive addresses), so the input needs no pass through shared memory.
 template <int LOG2N, bool INV, typename Src>
@@ -606,12 +609,13 @@ __device__ void fft_p2_from_global(float2 *x, const float2 *__restrict__ tw, int
                 const int base = ring * n + k;
                 x[padi(base)] = v[u][0];
 #pragma unroll
-                for (int q = 1; q < R; ++q) x[padi(base + q * h)] = cmulf(v[u][bitrev(q, 4)], twf<INV>(tw, q * k));
+                for (int q = 1; q < R; ++q)
+                    x[padi(base + q * h)] = cmulf(v[u][bitrev(q, 4)], twf<INV>(tw + n, q * h + k));
             }
         }
     }
     __syncthreads();
-    if constexpr (nfull >= 2) dif_stage16<LOG2N, n / 16, INV>(x, tw, nr);
+    if constexpr (nfull >= 2) dif_stage16<LOG2N, n / 16, INV, true>(x, tw + n + n, nr);
     dif_last<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
 }
 
@@ -758,12 +762,13 @@ __device__ __forceinline__ void dit_first(float2 *x, int nr)
     }
 }
 
-// transposed radix-16 stage at block length NB (twiddles, then butterfly), in place
+// transposed radix-16 stage at block length NB (twiddles, then butterfly), in place; tw is
+// the stage's [q][k] table
 template <int LOG2N, int NB, bool INV>
 __device__ __forceinline__ void dit_stage16(float2 *x, const float2 *__restrict__ tw, int nr)
 {
     constexpr int n = 1 << LOG2N, R = 16;
-    constexpr int h = NB / R, ts = n / NB, nbf = n / R;
+    constexpr int h = NB / R, nbf = n / R;
     for (int t = threadIdx.x; t < nbf * nr; t += kFftThreads) {
         const int ring = t >> (LOG2N - 4);
         const int i = t & (nbf - 1);
@@ -772,7 +777,7 @@ __device__ __forceinline__ void dit_stage16(float2 *x, const float2 *__restrict_
         float2 v[R];
         v[0] = x[padi(base)];
 #pragma unroll
-        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(base + q * h)], twf<INV>(tw, q * k * ts));
+        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(base + q * h)], twf<INV>(tw, q * h + k));
         dft_reg<R, INV>(v);
 #pragma unroll
         for (int q = 0; q < R; ++q) x[padi(base + q * h)] = v[bitrev(q, 4)];
@@ -780,7 +785,8 @@ __device__ __forceinline__ void dit_stage16(float2 *x, const float2 *__restrict_
     __syncthreads();
 }
 
-// full transform of nr rings held in natural order in shared memory, outputs to sink
+// full transform of nr rings held in natural order in shared memory, outputs to sink (tw as
+// for fft_p2_from_global)
 template <int LOG2N, bool INV, typename Sink>
 __device__ void fft_p2_to_global(float2 *x, const float2 *__restrict__ tw, int nr, const Sink &sink)
 {
@@ -788,13 +794,13 @@ __device__ void fft_p2_to_global(float2 *x, const float2 *__restrict__ tw, int n
     constexpr int nfull = rem ? n16 : n16 - 1;
     static_assert(nfull >= 1 && nfull <= 2, "a radix-16 stage of block length n is required");
     dit_first<LOG2N, (rem ? (1 << rem) : 16), INV>(x, nr);
-    if constexpr (nfull >= 2) dit_stage16<LOG2N, n / 16, INV>(x, tw, nr);
+    if constexpr (nfull >= 2) dit_stage16<LOG2N, n / 16, INV>(x, tw + n + n, nr);
     for (int t = threadIdx.x; t < h * nr; t += kFftThreads) {
         const int ring = t >> (LOG2N - 4), k = t & (h - 1);
         float2 v[R];
         v[0] = x[padi(ring * n + k)];
 #pragma unroll
-        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(ring * n + k + q * h)], twf<INV>(tw, q * k));
+        for (int q = 1; q < R; ++q) v[q] = cmulf(x[padi(ring * n + k + q * h)], twf<INV>(tw + n, q * h + k));
         dft_reg<R, INV>(v);
         const auto rw = sink.row(ring);
 #pragma unroll
