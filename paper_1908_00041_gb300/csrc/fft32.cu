@@ -994,6 +994,134 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
     if (LOG2N >= 0) staging_free(lane);              // shared memory stays until the copies read it
 }
 
+// ---------------------------------------------------------------------------
+// n = 2048 (L = 1023), complex fields: the transform above with the four rings brought
+// into shared memory by bulk asynchronous copies, so that no registers wait on loads in
+// flight and a CTA's copy proceeds while the other CTAs on the SM compute.  The copies
+// write whole rows, so the 64 KB ring buffer carries no padding: the first stage writes
+// point i of a ring to position swz(i) instead (its low three bits XORed with bits 4-6,
+// bit 3 with bit 7), which leaves every later access of the factorisation -- radix 16 at
+// block length 128, radix 8 at 8, the digit-reversed natural-order write, the bins read
+// for the records -- free of bank conflicts (enumerated on the host: test_dft_swizzle.py).  swz
+// changes only the low four bits, so the first stage's writes stay within the 16-point
+// groups its warp has read.  Records leave from registers as two 32-byte stores per order.
+// ---------------------------------------------------------------------------
+constexpr int kSwN = 2048;
+constexpr int kSwSmem = 4 * kSwN * 8 + 16;   // four rings and the copy's barrier
+constexpr int kSwBlocksPerSm = 2;
+
+__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 7) ^ (((a >> 7) & 1) << 3); }
+
+__global__ void __launch_bounds__(kFftThreads, kSwBlocksPerSm) k_fft_fwd_sw(
+    const float2 *__restrict__ Tth, const float2 *__restrict__ Tph, unsigned char *__restrict__ Fb,
+    const float2 *__restrict__ tw, const float *__restrict__ omega, int L, int nlat, int J, int has_eq, int nf,
+    const long long *__restrict__ toff, int *status)
+{
+    constexpr int n = kSwN;
+    extern __shared__ float4 sm_f4[];
+    float2 *X = reinterpret_cast<float2 *>(sm_f4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + 4 * n);
+    const int b = blockIdx.x / J, j = blockIdx.x % J;
+    const bool eq = has_eq && j == J - 1;
+    const int nr = eq ? 2 : 4;    // rings: (th, j), (ph, j), (th, j'), (ph, j')
+    const int jm = nlat - 1 - j;
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+    if (fb & 1) {                 // a row that does not start on 16 bytes cannot be copied
+        if (threadIdx.x == 0) atomicCAS(status, 0, FAVEST_EINVAL);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_fence_init();
+        tc::mbar_arrive_expect_tx(bar, nr * n * 8);
+        for (int r = 0; r < nr; ++r)
+            tc::bulk_g2s(X + r * n, ((r & 1) ? Tph : Tth) + fb + (size_t)(r < 2 ? j : jm) * n, n * 8, bar);
+    }
+    __syncthreads();              // the barrier is initialised before anyone waits on it
+    if (!tc::mbar_wait(bar, 0)) atomicCAS(status, 0, FAVEST_ETIMEOUT);
+
+    // radix 16 at block length n: rows in natural order, outputs to swz positions
+    const float2 *twA = tw + n, *twB = tw + 2 * n;
+    for (int t = threadIdx.x; t < 128 * nr; t += kFftThreads) {    // whole warps per ring
+        const int k = t & 127;
+        float2 *xr = X + (t >> 7) * n;
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = xr[k + 128 * q];
+        dft_reg<16, false>(v);
+        __syncwarp();             // the warp's reads are done before its writes
+        xr[swz(k)] = v[0];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) xr[swz(k + 128 * q)] = cmulf(v[bitrev(q, 4)], twf<false>(twA, q * 128 + k));
+    }
+    __syncthreads();
+    // radix 16 at block length 128
+    for (int t = threadIdx.x; t < 128 * nr; t += kFftThreads) {
+        const int i = t & 127, k = i & 7, base = (i >> 3) * 128 + k;
+        float2 *xr = X + (t >> 7) * n;
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = xr[swz(base + 8 * q)];
+        dft_reg<16, false>(v);
+        xr[swz(base)] = v[0];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) xr[swz(base + 8 * q)] = cmulf(v[bitrev(q, 4)], twf<false>(twB, q * 8 + k));
+    }
+    __syncthreads();
+    // radix 8 on blocks of 8 consecutive points, outputs to natural order (frequency
+    // nibble_reverse(blk) + 256 q); two rings per round, two blocks per thread
+    for (int r0 = 0; r0 < nr; r0 += 2) {
+        float2 v[2][8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int idx = threadIdx.x + u * kFftThreads, blk = idx & 255;
+            const float2 *xr = X + (r0 + (idx >> 8)) * n;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[u][q] = xr[swz(blk * 8 + q)];
+            dft_reg<8, false>(v[u]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int idx = threadIdx.x + u * kFftThreads, blk = idx & 255;
+            float2 *xr = X + (r0 + (idx >> 8)) * n;
+            const int m0 = ((blk & 15) << 4) | (blk >> 4);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xr[swz(m0 + 256 * q)] = v[u][bitrev(q, 3)];
+        }
+    }
+    __syncthreads();
+
+    // weighted fold and records, as in k_fft_fwd_bf16
+    const float w = omega[j];
+    unsigned char *dst_base = Fb + ((((size_t)(j / 8) * nf + b) * 8 + (j % 8)) * (L + 1)) * 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int mu0 = warp * 32; mu0 <= L; mu0 += blockDim.x) {
+        const int mu = mu0 + lane;
+        if (mu > L) continue;
+        float vp[8], vm[8];
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int bin = swz((sgn == 0 || mu == 0) ? mu : n - mu);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float2 a = X[c * n + bin];
+                const float2 z = eq ? make_float2(0.f, 0.f) : X[(2 + c) * n + bin];
+                const int base = c * 4 + sgn * 2;
+                vp[base] = w * (a.x + z.x);
+                vp[base + 1] = w * (a.y + z.y);
+                vm[base] = eq ? 0.f : w * (a.x - z.x);
+                vm[base + 1] = eq ? 0.f : w * (a.y - z.y);
+            }
+        }
+        uint4 rec_p[2], rec_m[2];
+        pack_row_f32(vp, rec_p);
+        pack_row_f32(vm, rec_m);
+        st_v8(dst_base + (size_t)mu * 64, rec_p);
+        st_v8(dst_base + (size_t)mu * 64 + 32, rec_m);
+    }
+}
+
 // The inverse kernels' sum records: the 32-byte records of latitude j (parities 0 and 1)
 // for every order mu, from S32[group][JP/4][L+1][parity][4][8].  For power-of-two lengths
 // they stream through shared memory in TMA boxes of kInvChunk orders ([order][parity][8],
@@ -1368,6 +1496,18 @@ cudaError_t launch_fwd_t(const Plan &p, const void *Tth, const void *Tph, cudaSt
                                                  p.unit_weights ? p.d_omega_unit32 : p.d_omega32, p.L, p.nlat,
                                                  p.J, p.has_eq, p.nf, p.B, p.d_toff);
         return cudaGetLastError();
+    }
+    if constexpr (LOG2N == 11) {
+        // whole rows by bulk copies: both planes 16-byte aligned (row starts then are, field
+        // offsets being even)
+        if ((((uintptr_t)Tth | (uintptr_t)Tph) & 15) == 0) {
+            cudaFuncSetAttribute(k_fft_fwd_sw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwSmem);
+            k_fft_fwd_sw<<<p.B * p.J, kFftThreads, kSwSmem, s>>>(
+                (const float2 *)Tth, (const float2 *)Tph, (unsigned char *)p.d_Fb, p.fft.tw32,
+                p.unit_weights ? p.d_omega_unit32 : p.d_omega32, p.L, p.nlat, p.J, p.has_eq, p.nf, p.d_toff,
+                p.d_status);
+            return cudaGetLastError();
+        }
     }
     auto k = k_fft_fwd_bf16<LOG2N>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
