@@ -1296,6 +1296,140 @@ __global__ void __launch_bounds__(kFftThreads, fft_blocks_per_sm<LOG2N>()) k_fft
 }
 
 // ---------------------------------------------------------------------------
+// n = 2048 (L = 1023), complex fields, inverse: the transpose of k_fft_fwd_sw.  The sum
+// records stream through shared memory in TMA boxes as in k_fft_inv_bf16, but a thread
+// takes one component (theta or phi) of one order: its two 16-byte chunks (even and odd
+// parity) are read in an order that alternates every two orders, which makes each
+// quarter-warp's loads cover all 32 banks (the one-order-per-thread reads of 64-byte
+// records met four-way conflicts).  The bins go to the swizzled layout of k_fft_fwd_sw,
+// with ring r shifted by 8 r complexes so that the theta and phi bins of the
+// same orders fall on different banks; the transposed stages then read and write without
+// conflicts, and the last stage stores rows from registers.
+// ---------------------------------------------------------------------------
+constexpr int kSwRingsFloat2 = 4 * kSwN + 24;                     // ring r shifted by 8 r
+constexpr int kSwInvSmem = kSwRingsFloat2 * 8 + 128 + 2 * kInvChunk * 64 + 16;
+
+__device__ __forceinline__ float2 *sw_ring(float2 *X, int r) { return X + r * (kSwN + 8); }
+
+__global__ void __launch_bounds__(kFftThreads, 2) k_fft_inv_sw(
+    const __grid_constant__ CUtensorMap tmap_s, float2 *__restrict__ Tth, float2 *__restrict__ Tph,
+    const float2 *__restrict__ tw, const float2 *__restrict__ isc, int L, int nlat, int J, int has_eq,
+    const long long *__restrict__ toff, int *status, const float *__restrict__ polS,
+    const int *__restrict__ plim, int pol_jc, int pol_muc)
+{
+    constexpr int n = kSwN;
+    extern __shared__ float4 sm_i4[];
+    float2 *X = reinterpret_cast<float2 *>(sm_i4);
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(X + kSwRingsFloat2);
+    unsigned char *stage = reinterpret_cast<unsigned char *>(X + kSwRingsFloat2) + (((s0 + 127) & ~127u) - s0);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * kInvChunk * 64);
+    const int b = blockIdx.x / J, j = blockIdx.x % J;
+    const bool eq = has_eq && j == J - 1;
+    const int nr = eq ? 2 : 4;
+    const float2 sc2 = __ldg(isc + j);      // 1/sin(theta_j) and the point weight (order 0)
+    const float is = sc2.x, w0 = sc2.y;
+    if (threadIdx.x < nr) sw_ring(X, threadIdx.x)[swz(n / 2)] = make_float2(0.f, 0.f);   // the unused bin
+    const bool polar = j < pol_jc;
+    const int plim_j = polar ? __ldg(plim + ((j | 1) < pol_jc ? (j | 1) : pol_jc - 1)) : 0;
+    const size_t pbase = ((size_t)b * (polar ? pol_jc : 0) + j) * pol_muc;
+
+    const int nch = (L + kInvChunk) / kInvChunk;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int c) {
+        tc::mbar_arrive_expect_tx(&bars[c & 1], kInvChunk * 64);
+        tc::tma_load_5d(stage + (c & 1) * kInvChunk * 64, &tmap_s, 8 * (j & 3), 0, c * kInvChunk, j >> 2, b,
+                        &bars[c & 1]);
+    };
+    if (threadIdx.x == 0) issue(0);
+    for (int c = 0; c < nch; ++c) {
+        if (threadIdx.x == 0 && c + 1 < nch) issue(c + 1);   // refills the buffer box c - 1 used
+        if (!tc::mbar_wait(&bars[c & 1], (c >> 1) & 1)) atomicCAS(status, 0, FAVEST_ETIMEOUT);
+        const float4 *rec = reinterpret_cast<const float4 *>(stage + (c & 1) * kInvChunk * 64);
+        for (int tsk = threadIdx.x; tsk < 2 * kInvChunk; tsk += kFftThreads) {
+            const int r = tsk >> 1, comp = tsk & 1, mu = c * kInvChunk + r;
+            if (mu > L) break;
+            const int p0 = (r >> 1) & 1;                      // which parity is read first
+            const float4 u0 = rec[r * 4 + p0 * 2 + comp], u1 = rec[r * 4 + (p0 ^ 1) * 2 + comp];
+            float4 e = p0 ? u1 : u0, o = p0 ? u0 : u1;        // even / odd sums, (+mu, -mu)
+            if (polar && mu >= 1 && mu < pol_muc && (mu & ~31) < plim_j) {
+                const float4 *src = reinterpret_cast<const float4 *>(polS + (pbase + mu) * 16);
+                e = __ldg(src + comp);
+                o = __ldg(src + 2 + comp);
+            }
+            const float sc = mu == 0 ? w0 : is;    // order 0 arrives divided by sin(theta)
+            float2 *r0 = sw_ring(X, comp), *r1 = sw_ring(X, 2 + comp);
+            const int bp = swz(mu);
+            r0[bp] = make_float2((e.x + o.x) * sc, (e.y + o.y) * sc);
+            if (!eq) r1[bp] = make_float2((e.x - o.x) * sc, (e.y - o.y) * sc);
+            if (mu != 0) {
+                const int bm = swz(n - mu);
+                r0[bm] = make_float2((e.z + o.z) * sc, (e.w + o.w) * sc);
+                if (!eq) r1[bm] = make_float2((e.z - o.z) * sc, (e.w - o.w) * sc);
+            }
+        }
+        __syncthreads();
+    }
+
+    // radix 8 (transposed last stage of the forward factorisation): natural-order points
+    // nibble_reverse(blk) + 256 q to block blk; two rings per round, two blocks per thread
+    for (int r0 = 0; r0 < nr; r0 += 2) {
+        float2 v[2][8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int idx = threadIdx.x + u * kFftThreads, blk = idx & 255;
+            const float2 *xr = sw_ring(X, r0 + (idx >> 8));
+            const int m0 = ((blk & 15) << 4) | (blk >> 4);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[u][q] = xr[swz(m0 + 256 * q)];
+            dft_reg<8, true>(v[u]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int idx = threadIdx.x + u * kFftThreads, blk = idx & 255;
+            float2 *xr = sw_ring(X, r0 + (idx >> 8));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xr[swz(blk * 8 + q)] = v[u][bitrev(q, 3)];
+        }
+    }
+    __syncthreads();
+    // transposed radix 16 at block length 128 (twiddles, then butterfly)
+    const float2 *twA = tw + n, *twB = tw + 2 * n;
+    for (int t = threadIdx.x; t < 128 * nr; t += kFftThreads) {
+        const int i = t & 127, k = i & 7, base = (i >> 3) * 128 + k;
+        float2 *xr = sw_ring(X, t >> 7);
+        float2 v[16];
+        v[0] = xr[swz(base)];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) v[q] = cmulf(xr[swz(base + 8 * q)], twf<true>(twB, q * 8 + k));
+        dft_reg<16, true>(v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xr[swz(base + 8 * q)] = v[bitrev(q, 4)];
+    }
+    __syncthreads();
+    // transposed radix 16 at block length n: natural-order outputs k + 128 q stored as rows
+    const int jm = nlat - 1 - j;
+    const size_t fb = toff ? (size_t)toff[b] : (size_t)b * nlat * n;
+    for (int t = threadIdx.x; t < 128 * nr; t += kFftThreads) {
+        const int ring = t >> 7, k = t & 127;
+        const float2 *xr = sw_ring(X, ring);
+        float2 v[16];
+        v[0] = xr[swz(k)];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) v[q] = cmulf(xr[swz(k + 128 * q)], twf<true>(twA, q * 128 + k));
+        dft_reg<16, true>(v);
+        float2 *dst = ((ring & 1) ? Tph : Tth) + fb + (size_t)(ring < 2 ? j : jm) * n;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dst[k + 128 * q] = v[bitrev(q, 4)];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Real fields.  A real field's two components are packed into one complex ring
 // z = T_th + i T_ph, whose spectrum Z gives both component spectra (T_th, T_ph real):
 //   F_th(m) = (Z(m) + conj Z(-m)) / 2,   F_ph(m) = (Z(m) - conj Z(-m)) / (2 i),
@@ -1530,6 +1664,13 @@ cudaError_t launch_inv_t(const Plan &p, void *Tth, void *Tph, cudaStream_t s)
                                                  p.fft.tw32, p.d_perm, p.d_isc32 + (p.adj_weighted ? p.J : 0),
                                                  p.L, p.nlat, p.J, p.has_eq, p.JP, p.B, p.d_toff, p.d_status,
                                                  p.d_polS, p.d_pol_lim, p.pol_jc, p.pol_muc);
+        return cudaGetLastError();
+    }
+    if constexpr (LOG2N == 11) {
+        cudaFuncSetAttribute(k_fft_inv_sw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwInvSmem);
+        k_fft_inv_sw<<<p.B * p.J, kFftThreads, kSwInvSmem, s>>>(
+            p.tmap_s32, (float2 *)Tth, (float2 *)Tph, p.fft.tw32, p.d_isc32 + (p.adj_weighted ? p.J : 0), p.L,
+            p.nlat, p.J, p.has_eq, p.d_toff, p.d_status, p.d_polS, p.d_pol_lim, p.pol_jc, p.pol_muc);
         return cudaGetLastError();
     }
     auto k = k_fft_inv_bf16<LOG2N>;

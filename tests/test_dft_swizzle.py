@@ -51,3 +51,50 @@ def test_record_bins():
         for c in range(4):
             assert wavefronts([swz(c * N + mu0 + l) for l in range(32)]) == 2
             assert wavefronts([swz(c * N + ((N - mu0 - l) if mu0 + l else 0)) for l in range(32)]) <= 4
+
+
+def quarter_wavefronts(addrs16):
+    """16-byte accesses: per quarter-warp, the largest number of distinct addresses that share
+    one of the 8 16-byte bank groups."""
+    tot = 0
+    for qw in range(4):
+        groups = {}
+        for a in set(addrs16[8 * qw:8 * qw + 8]):
+            groups.setdefault(a % 8, set()).add(a)
+        tot += max(len(v) for v in groups.values())
+    return tot
+
+
+def ring_base(r):
+    """k_fft_inv_sw: ring r shifted by 8 r complexes (the rings do not overlap)."""
+    return r * (N + 8)
+
+
+def test_inverse_rings_disjoint():
+    spans = [(ring_base(r), ring_base(r) + N) for r in range(4)]
+    assert all(spans[r][1] <= spans[r + 1][0] for r in range(3)) and spans[3][1] <= 4 * N + 24
+
+
+def test_inverse_record_reads_and_bin_writes():
+    # a thread takes component tsk & 1 of order tsk >> 1 of a 256-order box; the box holds
+    # [order][parity][2 components][4 floats] (16-byte units), read parity p0 first, p0 = (r >> 1) & 1
+    for w in range(8):
+        tsk = [32 * w + l for l in range(32)]
+        for step in range(2):
+            addrs = []
+            for t in tsk:
+                r, comp = t >> 1, t & 1
+                p0 = (r >> 1) & 1
+                addrs.append(r * 4 + (p0 ^ step) * 2 + comp)
+            assert quarter_wavefronts(addrs) == 4
+    # the bins +mu of rings comp and 2 + comp (8-byte writes)
+    for box in range(4):
+        for w in range(8):
+            for it in range(2):
+                lanes = [it * 256 + 32 * w + l for l in range(32)]
+                for rr in (0, 2):
+                    plus = [ring_base(rr + (t & 1)) + swz(box * 256 + (t >> 1)) for t in lanes]
+                    assert wavefronts(plus) == 2
+                    mus = [box * 256 + (t >> 1) for t in lanes]
+                    minus = [ring_base(rr + (t & 1)) + swz(N - mu) for t, mu in zip(lanes, mus) if mu]
+                    assert wavefronts(minus + [minus[-1]] * (32 - len(minus))) <= 4
