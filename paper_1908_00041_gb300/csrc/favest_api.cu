@@ -331,6 +331,24 @@ int build_tables(Plan &p)
             for (int k = 0; k < hB; ++k) tw32[(size_t)n + 16 * hA + q * hB + k] = tw32[16 * q * k];
         }
     }
+    // Other lengths of the split path: the same [q][k] order per mixed-radix stage (radices
+    // 2, 4 and the odd primes up to 13; Bluestein stages keep reading the plain table).
+    if (p.precision == FAVEST_BF16X6 && !(n >= 64 && n <= 4096 && (n & (n - 1)) == 0)) {
+        int Nb = n;
+        for (int st = 0; st < p.fft.nstages; ++st) {
+            const int R = p.fft.radix[st], h = Nb / R, ts = n / Nb;
+            p.fft.tw_off[st] = -1;
+            if (R <= 13 && !p.fft.blue_lg[st]) {
+                p.fft.tw_off[st] = (int)tw32.size();
+                for (int q = 0; q < R; ++q)
+                    for (int k = 0; k < h; ++k) {
+                        const float2 w = tw32[(size_t)q * k * ts];   // q k ts < R h ts = n
+                        tw32.push_back(w);
+                    }
+            }
+            Nb = h;
+        }
+    }
     if ((e = upload(&p.fft.tw64, tw)) || (e = upload(&p.fft.tw32, tw32)))
         return e == cudaErrorMemoryAllocation ? FAVEST_ENOMEM : FAVEST_ECUDA;
     // in-place decimation-in-frequency FFT leaves frequency m at position pos(m):

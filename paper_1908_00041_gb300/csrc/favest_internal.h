@@ -48,6 +48,10 @@ struct FftPlan {
     int blue_off[kMaxRadixStages] = {0};   // stage's offset into the chirp table (points)
     int blue_moff[kMaxRadixStages] = {0};  // stage's offset into the spectrum / twiddle tables
     size_t blue_scratch = 0;               // bytes of shared-memory scratch the largest stage needs
+    // split path, lengths other than powers of two: offset (complexes, into tw32) of stage st's
+    // twiddles in [q][k] order, entry q h + k = w_n^(q k n / Nb) for q < R, k < h = Nb / R
+    // (-1: a Bluestein stage, which reads the plain table)
+    int tw_off[kMaxRadixStages] = {0};
     float2 *blue_chirp = nullptr;   // [R] per stage: exp(-i pi t^2 / R), t^2 reduced mod 2R exactly
     float2 *blue_spec = nullptr;    // [M] per stage: DFT_M of the conjugate chirp / M (natural
                                     //     order; bit-reversed for M = 8192)

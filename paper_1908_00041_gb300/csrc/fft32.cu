@@ -61,11 +61,13 @@ __device__ __forceinline__ int rdiv(int x, Recip r) { return r.d == 1 ? x : (int
 //   out_q     = v_0 + sum_{r=1}^{H} [c_{qr} (v_r + v_{R-r}) + i y_{qr} (v_r - v_{R-r})] = A_q + i B_q,
 //   out_{R-q} = A_q - i B_q,   H = (R - 1) / 2,
 // 4 H^2 real multiply-adds per butterfly instead of R (R - 1) complex ones.
+// twS: the stage's twiddles in [q][k] order (entry q h + k = w_n^(q k n / Nb))
 template <int R, bool INV>
-__device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restrict__ tw, int n, int Nb, int nr)
+__device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restrict__ tw,
+                                                const float2 *__restrict__ twS, int n, int Nb, int nr)
 {
     constexpr int H = (R - 1) / 2;
-    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
+    const int h = Nb / R, nbf = n / R, rstep = n / R;
     float2 wr[H + 1];                                  // w_R^j = w_n^{j n / R}, j <= H
 #pragma unroll
     for (int j = 1; j <= H; ++j) wr[j] = twf<INV>(tw, j * rstep);
@@ -85,7 +87,6 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
             out0 = caddf(out0, sm[r - 1]);
         }
         xr[0] = out0;
-        const int tk = k * ts;
 #pragma unroll
         for (int q = 1; q <= H; ++q) {
             float2 A = v0, Bq = make_float2(0.f, 0.f);
@@ -102,8 +103,8 @@ __device__ __forceinline__ void dif_stage_small(float2 *x, const float2 *__restr
             }
             const float2 op = make_float2(A.x - Bq.y, A.y + Bq.x);     // A + i B
             const float2 om = make_float2(A.x + Bq.y, A.y - Bq.x);     // A - i B
-            xr[q * h] = cmulf(op, twf<INV>(tw, q * tk));
-            xr[(R - q) * h] = cmulf(om, twf<INV>(tw, (R - q) * tk));
+            xr[q * h] = cmulf(op, twf<INV>(twS + k, q * h));
+            xr[(R - q) * h] = cmulf(om, twf<INV>(twS + k, (R - q) * h));
         }
     }
 }
@@ -388,22 +389,22 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
     for (int st = st0; st < rp.nstages; ++st) {
         const int R = rp.radix[st];
         const int h = Nb / R;
-        const int ts = n / Nb;
         const int nbf = n / R;
         if (R == 3) {
-            dif_stage_small<3, INV>(x, tw, n, Nb, nr);
+            dif_stage_small<3, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 5) {
-            dif_stage_small<5, INV>(x, tw, n, Nb, nr);
+            dif_stage_small<5, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 7) {
-            dif_stage_small<7, INV>(x, tw, n, Nb, nr);
+            dif_stage_small<7, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 11) {
-            dif_stage_small<11, INV>(x, tw, n, Nb, nr);
+            dif_stage_small<11, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 13) {
-            dif_stage_small<13, INV>(x, tw, n, Nb, nr);
+            dif_stage_small<13, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (BLUE && R != 2 && R != 4) {         // primes >= 17 (build_bluestein marks them all)
             dif_stage_bluestein<INV>(x, tw, n, R, Nb, nr, rp.blue_lg[st], rp.blue_P[st], rp.blue_chirp + rp.blue_off[st],
                                      rp.blue_spec + rp.blue_moff[st], rp.blue_tw + rp.blue_moff[st], sc);
         } else {
+            const float2 *twS = tw + rp.tw_off[st];
             const Recip rn = recip(nbf), rh = recip(h);
             for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
                 const int ring = rdiv(t, rn), i = t - ring * nbf;
@@ -415,13 +416,13 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
                     const float2 s13 = caddf(v1, v3), d13 = csubf(v1, v3);
                     const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
                     xr[0] = caddf(s02, s13);
-                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(tw, k * ts));
-                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(tw, 2 * k * ts));
-                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(tw, 3 * k * ts));
+                    xr[h] = cmulf(caddf(d02, rot), twf<INV>(twS, h + k));
+                    xr[2 * h] = cmulf(csubf(s02, s13), twf<INV>(twS, 2 * h + k));
+                    xr[3 * h] = cmulf(csubf(d02, rot), twf<INV>(twS, 3 * h + k));
                 } else {
                     const float2 v0 = xr[0], v1 = xr[h];
                     xr[0] = caddf(v0, v1);
-                    xr[h] = cmulf(csubf(v0, v1), twf<INV>(tw, k * ts));
+                    xr[h] = cmulf(csubf(v0, v1), twf<INV>(twS, h + k));
                 }
             }
         }
@@ -439,10 +440,11 @@ __device__ void dif_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
 // 4, block length n), whose outputs k + q h are in natural order, straight to global memory.
 // Radices 2, 4 and the odd primes 3..13 (plans without Bluestein stages).
 template <int R, bool INV>
-__device__ __forceinline__ void dit_stage_small(float2 *x, const float2 *__restrict__ tw, int n, int Nb, int nr)
+__device__ __forceinline__ void dit_stage_small(float2 *x, const float2 *__restrict__ tw,
+                                                const float2 *__restrict__ twS, int n, int Nb, int nr)
 {
     constexpr int H = (R - 1) / 2;
-    const int h = Nb / R, ts = n / Nb, nbf = n / R, rstep = n / R;
+    const int h = Nb / R, nbf = n / R, rstep = n / R;
     float2 wr[H + 1];                                  // w_R^j, j <= H
 #pragma unroll
     for (int j = 1; j <= H; ++j) wr[j] = twf<INV>(tw, j * rstep);
@@ -451,14 +453,13 @@ __device__ __forceinline__ void dit_stage_small(float2 *x, const float2 *__restr
         const int ring = rdiv(t, rn), i = t - ring * nbf;
         const int blk = rdiv(i, rh), k = i - blk * h;
         float2 *xr = x + ring * n + blk * Nb + k;
-        const int tk = k * ts;
         const float2 v0 = xr[0];
         float2 sm[H], df[H];
         float2 out0 = v0;
 #pragma unroll
         for (int r = 1; r <= H; ++r) {
-            const float2 a = cmulf(xr[r * h], twf<INV>(tw, r * tk));
-            const float2 b = cmulf(xr[(R - r) * h], twf<INV>(tw, (R - r) * tk));
+            const float2 a = cmulf(xr[r * h], twf<INV>(twS, r * h + k));
+            const float2 b = cmulf(xr[(R - r) * h], twf<INV>(twS, (R - r) * h + k));
             sm[r - 1] = caddf(a, b);
             df[r - 1] = csubf(a, b);
             out0 = caddf(out0, sm[r - 1]);
@@ -505,30 +506,31 @@ __device__ void dit_f32(float2 *x, const float2 *__restrict__ tw, const RadixPla
         for (int s2 = 0; s2 < st; ++s2) Nb /= rp.radix[s2];
         const int R = rp.radix[st];
         if (R == 3) {
-            dit_stage_small<3, INV>(x, tw, n, Nb, nr);
+            dit_stage_small<3, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 5) {
-            dit_stage_small<5, INV>(x, tw, n, Nb, nr);
+            dit_stage_small<5, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 7) {
-            dit_stage_small<7, INV>(x, tw, n, Nb, nr);
+            dit_stage_small<7, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 11) {
-            dit_stage_small<11, INV>(x, tw, n, Nb, nr);
+            dit_stage_small<11, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else if (R == 13) {
-            dit_stage_small<13, INV>(x, tw, n, Nb, nr);
+            dit_stage_small<13, INV>(x, tw, tw + rp.tw_off[st], n, Nb, nr);
         } else {
-            const int h = Nb / R, ts = n / Nb, nbf = n / R;
+            const int h = Nb / R, nbf = n / R;
+            const float2 *twS = tw + rp.tw_off[st];
             const Recip rn = recip(nbf), rh = recip(h);
             for (int t = threadIdx.x; t < nbf * nr; t += blockDim.x) {
                 const int ring = rdiv(t, rn), i = t - ring * nbf;
                 const int blk = rdiv(i, rh), k = i - blk * h;
                 float2 *xr = x + ring * n + blk * Nb + k;
                 if (R == 4) {
-                    float2 v[4] = {xr[0], cmulf(xr[h], twf<INV>(tw, k * ts)), cmulf(xr[2 * h], twf<INV>(tw, 2 * k * ts)),
-                                   cmulf(xr[3 * h], twf<INV>(tw, 3 * k * ts))};
+                    float2 v[4] = {xr[0], cmulf(xr[h], twf<INV>(twS, h + k)), cmulf(xr[2 * h], twf<INV>(twS, 2 * h + k)),
+                                   cmulf(xr[3 * h], twf<INV>(twS, 3 * h + k))};
                     dft4<INV>(v);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) xr[q * h] = v[q];
                 } else {
-                    const float2 v0 = xr[0], v1 = cmulf(xr[h], twf<INV>(tw, k * ts));
+                    const float2 v0 = xr[0], v1 = cmulf(xr[h], twf<INV>(twS, h + k));
                     xr[0] = caddf(v0, v1);
                     xr[h] = csubf(v0, v1);
                 }

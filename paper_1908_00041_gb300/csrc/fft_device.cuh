@@ -12,6 +12,7 @@ struct RadixPlanArg {
     int radix[kMaxRadixStages];
     int blue_lg[kMaxRadixStages], blue_P[kMaxRadixStages];   // see FftPlan
     int blue_off[kMaxRadixStages], blue_moff[kMaxRadixStages];
+    int tw_off[kMaxRadixStages];                               // see FftPlan
     const float2 *blue_chirp, *blue_spec, *blue_tw;
 };
 
@@ -26,6 +27,7 @@ inline RadixPlanArg make_radix_arg(const FftPlan &f)
         r.blue_P[i] = f.blue_P[i];
         r.blue_off[i] = f.blue_off[i];
         r.blue_moff[i] = f.blue_moff[i];
+        r.tw_off[i] = f.tw_off[i];
     }
     r.blue_chirp = f.blue_chirp;
     r.blue_spec = f.blue_spec;
