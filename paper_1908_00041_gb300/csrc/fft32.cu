@@ -9,7 +9,11 @@
 //            inverse FFT whose last stage stores to global memory.
 // Power-of-two lengths run register radix-16 butterflies (forward: decimation in frequency
 // with the first stage fed from global memory; inverse: its transpose); other lengths a
-// generic mixed-radix decimation in frequency with a digit-reversal table.
+// generic mixed-radix decimation in frequency with a digit-reversal table.  At n = 2048
+// (L = 1023) complex fields take k_fft_fwd_sw / k_fft_inv_sw instead: rings brought in by
+// bulk copies, an XOR-swizzled layout in place of the padding, records to and from
+// registers without staging.  Every stage reads its twiddles from per-stage tables in
+// [q][k] order, so that a warp's threads read consecutive entries.
 #include "favest_internal.h"
 #include "bf16_split.cuh"
 #include "fft_device.cuh"
