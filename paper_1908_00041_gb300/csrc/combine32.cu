@@ -34,6 +34,10 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
     // [order][(degree - (l0 - 1)) * 2 + half]; the odd row length (69 x 16 B) spreads the
     // lanes (orders) of a quarter-warp over distinct bank groups
     __shared__ float4 qs[kCT][kCTRows * 2 + 1];
+    // the tile's P, M, R coefficients [table][order][degree - l0], rows padded to 33 so that
+    // the lanes (orders) of phase 2 read distinct banks; staged by coalesced loads (degrees
+    // of one order are consecutive in the tables) instead of one scattered load per lane
+    __shared__ float pmr[3][kCT][kCT + 1];
     // tile index -> (ob, lb), lb >= ob, row-major over lb
     int t = blockIdx.x, lb = 0;
     while (t > lb) {
@@ -62,10 +66,27 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
             v[u] = __ldg(src + half);
         }
     }
+    constexpr int kT = kCT * kCT, kTPer = 3 * kT / 256;
+    float tv[kTPer];
+#pragma unroll
+    for (int u = 0; u < kTPer; ++u) {
+        const int e = threadIdx.x + u * 256, tab = e / kT, i = (e % kT) / kCT, dl = e % kCT;
+        const int mu = mu0 + i, l = l0 + dl;
+        tv[u] = 0.f;
+        if (mu <= L && l >= 1 && l <= L && l >= mu) {
+            const float *src = tab == 0 ? P : tab == 1 ? M : R;
+            tv[u] = __ldg(src + tab_off(L, mu) + (l - mu));
+        }
+    }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int e = threadIdx.x + u * 256;
         if (e < kE) qs[(e >> 1) / kCTRows][((e >> 1) % kCTRows) * 2 + (e & 1)] = v[u];
+    }
+#pragma unroll
+    for (int u = 0; u < kTPer; ++u) {
+        const int e = threadIdx.x + u * 256;
+        pmr[e / kT][(e % kT) / kCT][e % kCT] = tv[u];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,8 +94,7 @@ __global__ void __launch_bounds__(256) k_combine_bf16(const float *__restrict__ 
     for (int l = l0 + warp; l < l0 + kCT; l += 8) {
         if (l < 1 || l > L || mu > l) continue;
         const int d = l - (l0 - 1);
-        const long long row = tab_off(L, mu) + (l - mu);
-        const float Pl = __ldg(P + row), Ml = __ldg(M + row), Rl = __ldg(R + row);
+        const float Pl = pmr[0][lane][l - l0], Ml = pmr[1][lane][l - l0], Rl = pmr[2][lane][l - l0];
         const bool has_m = l > mu;
         const float4 q1a = qs[lane][(d + 1) * 2], q1b = qs[lane][(d + 1) * 2 + 1];
         const float4 q0a = qs[lane][d * 2], q0b = qs[lane][d * 2 + 1];
